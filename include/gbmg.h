@@ -1,0 +1,205 @@
+/*
+ * gbmg.h -- C ABI of libgbmg.so: adaptive-multigrid coarse-grid operator
+ * (stencil apply and Galerkin construction) for the Wilson-clover Dirac
+ * matrix, on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Clark et al., "Accelerating Lattice QCD Multigrid on GPUs Using
+ * Fine-Grained Parallelization" (SC16).  Eq. (1) is the linear system
+ * M x = b, Eq. (2) the fine Wilson-clover matrix, Sec. II-D the adaptive
+ * setup (null vectors, aggregates, chiral split, block QR, Galerkin
+ * product), Eq. (3) the coarse operator, Sec. IV the coarse stencil
+ * kernel, Sec. IV-F the transfer operators, Sec. VI-A the K-cycle solver.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Lattice site index  s = x + Lx*(y + Ly*(z + Lz*t)), directions mu = 0..3
+ *                     for x, y, z, t; periodic, optionally antiperiodic in t
+ *                     for the fine fermion field.
+ * Fine spinor         [site][spin 4][colour 3] complex   (12 complex / site)
+ *                     in the DeGrand-Rossi chiral basis, gamma_5 =
+ *                     diag(1, 1, -1, -1): spins {0,1} = chirality 0.
+ * Coarse spinor       [site][dof] complex, dof = s*Nv + c, s the chirality
+ *                     (Sec. IV-B), 2*Nv dofs per site.
+ * Multi-RHS spinor    [site][dof][rhs] complex.
+ * Complex numbers     interleaved (re, im).
+ * Gauge field         [mu][site][3][3] complex double (row-major SU(3)).
+ * Coarse links        [site][slot 0..8][row][col] complex double, the
+ *                     nine blocks of Eq. (3): slot 0 = X (the dense site-
+ *                     diagonal block), slot 1+2mu = Y_{+mu} acting on
+ *                     x(site + mu), slot 2+2mu = Y_{-mu} acting on
+ *                     x(site - mu):  y(s) = sum_slot L[s][slot] x(nbr).
+ * Null vectors        [vec][site][dof] complex double.
+ *
+ * Vector precision.  Level l works in "vector precision" F64 when its
+ * operator precision is MG_F64 and F32 otherwise (also for the 16-bit
+ * link forms, whose arithmetic accumulates in FP32).  Vector arguments of
+ * mg_apply / mg_coarse_apply / mg_restrict / mg_prolong /
+ * mg_wilson_clover_apply are complex numbers in that precision
+ * (complex128 or complex64).  mg_gcr_solve always takes complex128.
+ *
+ * Memory.  Pointers named *_dev are device pointers owned by the caller
+ * (e.g. PyTorch tensors); the library reads or writes them only inside the
+ * call, stream-ordered on `stream` (a cudaStream_t passed as void*; NULL is
+ * the legacy default stream).  Everything the context holds (copies of the
+ * gauge field, clover term, null vectors, coarse links, solver workspace)
+ * is allocated by the library and freed by mg_destroy.
+ *
+ * Errors.  Every call returns an mg_status; mg_last_error(ctx) gives a
+ * human-readable reason.  No call exits, traps or falls back to the CPU.
+ */
+#ifndef GBMG_H
+#define GBMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MG_MAX_LEVELS 4
+
+typedef enum {
+  MG_OK = 0,
+  MG_ERR_ARG = -1,           /* invalid argument (sizes, pointers, levels)      */
+  MG_ERR_CUDA = -2,          /* a CUDA runtime call failed                       */
+  MG_ERR_OOM = -3,           /* device allocation failed                         */
+  MG_ERR_STATE = -4,         /* call out of order (e.g. apply before build)      */
+  MG_ERR_NOT_CONVERGED = -5, /* solver hit maxiter; stats are still filled       */
+  MG_ERR_NUMERICAL = -6,     /* NaN/Inf or a zero denominator in a solver        */
+  MG_ERR_TIMEOUT = -7,       /* a bounded device wait gave up                    */
+  MG_ERR_RANK = -8           /* a null-vector aggregate block is rank deficient  */
+} mg_status;
+
+typedef enum { MG_F64 = 0, MG_F32 = 1, MG_BF16 = 2, MG_F16 = 3 } mg_prec;
+
+typedef struct mg_ctx mg_ctx;
+
+/* Problem and solver parameters.  Eq. (2): dims, mass m, csw, boundary;
+ * Sec. II-D: blocks (aggregate extents), nvec (null vectors), setup
+ * sweeps; Sec. VI-A: GCR Krylov size, MR smoother, inner tolerances.      */
+typedef struct {
+  int dims[4];                      /* fine lattice extents Lx, Ly, Lz, Lt          */
+  int t_antiperiodic;               /* 1: antiperiodic fermion boundary in t        */
+  double mass;                      /* m of Eq. (2)                                  */
+  double csw;                       /* clover coefficient of A_x                    */
+  int nlevels;                      /* 2..MG_MAX_LEVELS (fine level included)       */
+  int block[MG_MAX_LEVELS][4];      /* aggregate extents of coarsening l -> l+1     */
+  int nvec[MG_MAX_LEVELS];          /* null vectors of coarsening l -> l+1          */
+  int setup_sweeps;                 /* minimal-residual sweeps on M x = 0           */
+  uint64_t seed;                    /* device Gaussian x0 when none is passed       */
+  mg_prec prec_fine;                /* MG_F64 or MG_F32                             */
+  mg_prec prec_coarse;              /* MG_F64, MG_F32, MG_BF16 or MG_F16 link store */
+  int mr_iters;                     /* MR pre- and post-smoothing steps (4)         */
+  double mr_omega;                  /* MR relaxation (1.0)                          */
+  int gcr_nkrylov;                  /* GCR Krylov space size (10)                   */
+  double inner_tol;                 /* intermediate-level GCR tolerance (0.25)      */
+  int inner_maxiter;                /* intermediate-level GCR iteration cap (10)    */
+  double coarse_tol;                /* coarsest-level GCR tolerance (0.1)           */
+  int coarse_maxiter;               /* coarsest-level GCR iteration cap (100)       */
+} mg_params;
+
+typedef struct {
+  int iters;                        /* outer GCR steps                              */
+  int restarts;                     /* true-residual recomputations                 */
+  int level_iters[MG_MAX_LEVELS];   /* GCR steps summed per level (0 = outer)       */
+  double true_residual;             /* |b - M x| / |b| in FP64 at return            */
+  double seconds;                   /* wall time of the call                        */
+  int history_len;                  /* entries written to history                   */
+  double history[512];              /* |r_k| / |b| after each outer step            */
+} mg_solve_stats;
+
+/* Fill *p with the defaults listed in the comments of mg_params (dims and
+ * blocks are zero and must be set).                                        */
+void mg_default_params(mg_params* p);
+
+/* Create a context.  gauge_dev: [4][V][3][3] complex double, read once and
+ * copied (with the t boundary sign folded into the last time slice) into
+ * the fine operator, which also computes the clover term A_x on the device.
+ * Fails with MG_ERR_ARG if an extent is not divisible by its block.        */
+mg_status mg_create(const mg_params* params, const void* gauge_dev, mg_ctx** out);
+mg_status mg_destroy(mg_ctx* ctx);
+
+/* Sec. II-D steps 1-3 for the coarsening level -> level+1: starting from
+ * init_dev ([nvec][V_l][nd_l] complex double; NULL draws Gaussian x0 on the
+ * device from params.seed) run setup_sweeps minimal-residual steps on
+ * A_l x = 0 in the level's vector precision, normalise every vector, then
+ * block-orthonormalise (chiral split, modified Gram-Schmidt done twice,
+ * FP64) per aggregate.  MG_ERR_RANK on a rank-deficient block.             */
+mg_status mg_setup_nullvecs(mg_ctx* ctx, int level, const void* init_dev, void* stream);
+
+/* Take the raw null vectors from vecs_dev ([nvec][V_l][nd_l] complex
+ * double) instead of running the sweeps, then block-orthonormalise.       */
+mg_status mg_set_nullvecs(mg_ctx* ctx, int level, const void* vecs_dev, void* stream);
+
+/* Copy null vectors out: kind 0 = raw (after sweeps), 1 = block-
+ * orthonormalised (the prolongator columns).  [nvec][V_l][nd_l] complex
+ * double; bytes must equal that size.                                      */
+mg_status mg_get_nullvecs(mg_ctx* ctx, int level, int kind, void* dst_dev, size_t bytes,
+                          void* stream);
+
+/* Sec. II-D step 4: Galerkin product P^dag A_l P of level l, stored as the
+ * nine blocks of Eq. (3) per coarse site of level l+1 (X and Y_{+-mu}),
+ * in prec_coarse.  Requires the null vectors of level l.                   */
+mg_status mg_build_coarse(mg_ctx* ctx, int level, void* stream);
+
+/* Eq. (3) on coarse level `level` >= 1:  y = X x + sum_mu Y_{+mu} x(.+mu)
+ * + Y_{-mu} x(.-mu).  nrhs = 1: x, y [V][n]; nrhs > 1: [V][n][nrhs].
+ * x and y are device arrays in the level's vector precision and must not
+ * overlap.                                                                 */
+mg_status mg_coarse_apply(mg_ctx* ctx, int level, void* y_dev, const void* x_dev, int nrhs,
+                          void* stream);
+
+/* The level-l operator on one vector: Eq. (2) for l = 0, Eq. (3) above.    */
+mg_status mg_apply(mg_ctx* ctx, int level, void* y_dev, const void* x_dev, void* stream);
+
+/* Eq. (2): out = M in on the fine lattice, vectors in the fine vector
+ * precision.                                                               */
+mg_status mg_wilson_clover_apply(mg_ctx* ctx, void* out_dev, const void* in_dev, void* stream);
+
+/* Sec. IV-F transfer operators between level l and l+1 (vector precision of
+ * each level):  coarse = P^dag fine  (restrict),  fine = P coarse (prolong). */
+mg_status mg_restrict(mg_ctx* ctx, int level, void* coarse_dev, const void* fine_dev,
+                      void* stream);
+mg_status mg_prolong(mg_ctx* ctx, int level, void* fine_dev, const void* coarse_dev,
+                     void* stream);
+
+/* Sec. VI-A: flexible GCR on the fine level, preconditioned by the K-cycle,
+ * to |b - M x| <= tol |b| (true residual, FP64).  x_dev, b_dev: fine
+ * vectors, complex double.  Synchronises `stream` for convergence checks.
+ * Returns MG_ERR_NOT_CONVERGED at maxiter (x holds the last iterate).      */
+mg_status mg_gcr_solve(mg_ctx* ctx, void* x_dev, const void* b_dev, double tol, int maxiter,
+                       mg_solve_stats* stats, void* stream);
+
+/* Coarse links of level l >= 1 in the external layout (see top), complex
+ * double, bytes = V_l * 9 * n_l^2 * 16.  set replaces the operator of the
+ * level (for apply-only use), converting to prec_coarse.                   */
+mg_status mg_get_coarse_links(mg_ctx* ctx, int level, void* dst_dev, size_t bytes, void* stream);
+mg_status mg_set_coarse_links(mg_ctx* ctx, int level, const void* src_dev, size_t bytes,
+                              void* stream);
+
+/* Geometry of level l: extents, volume, dofs per site, vector precision. */
+mg_status mg_level_info(mg_ctx* ctx, int level, int dims[4], int* volume, int* ndof,
+                        int* vec_prec);
+
+/* Device-side timing of the library's own kernels.  When enabled, every
+ * launch of kernel class `name` ("coarse_apply", "wilson_clover",
+ * "galerkin", "restrict", "prolong", "block_orth", "blas") on level
+ * `level` is bracketed by CUDA events on its stream.  query() sums the
+ * durations (waiting for them) and the algorithmic bytes and flops the
+ * launches moved; level -1 sums all levels.  reset() clears the record.   */
+mg_status mg_profile_enable(mg_ctx* ctx, int on);
+mg_status mg_profile_reset(mg_ctx* ctx);
+mg_status mg_profile_query(mg_ctx* ctx, const char* name, int level, int* launches,
+                           double* total_ms, double* bytes, double* flops);
+
+/* Number of kernels the library has launched since creation.              */
+long long mg_launch_count(mg_ctx* ctx);
+
+const char* mg_status_string(mg_status s);
+const char* mg_last_error(mg_ctx* ctx);   /* ctx may be NULL (creation errors) */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBMG_H */

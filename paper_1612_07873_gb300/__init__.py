@@ -1,0 +1,272 @@
+"""Python binding of libgbmg.so (C ABI in include/gbmg.h).
+
+Argument marshalling only: every step of the multigrid hot path runs in the
+library's CUDA kernels.  Functions carry the C names; tensors are PyTorch
+CUDA tensors (complex128 / complex64) whose data pointers are passed
+through, and the stream defaults to torch's current stream.  Importing
+this module loads the shared library and raises if it has not been built
+(``python -m paper_1612_07873_gb300.build``): there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+from . import build as _build
+
+MG_MAX_LEVELS = 4
+F64, F32, BF16, F16 = 0, 1, 2, 3
+STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "out of device memory",
+          -4: "call out of order", -5: "solver did not converge", -6: "numerical breakdown",
+          -7: "device wait timed out", -8: "rank-deficient null-vector block"}
+MG_ERR_NOT_CONVERGED = -5
+MG_ERR_RANK = -8
+MG_ERR_ARG = -1
+MG_ERR_STATE = -4
+
+
+class mg_params(C.Structure):
+    _fields_ = [
+        ("dims", C.c_int * 4),
+        ("t_antiperiodic", C.c_int),
+        ("mass", C.c_double),
+        ("csw", C.c_double),
+        ("nlevels", C.c_int),
+        ("block", (C.c_int * 4) * MG_MAX_LEVELS),
+        ("nvec", C.c_int * MG_MAX_LEVELS),
+        ("setup_sweeps", C.c_int),
+        ("seed", C.c_uint64),
+        ("prec_fine", C.c_int),
+        ("prec_coarse", C.c_int),
+        ("mr_iters", C.c_int),
+        ("mr_omega", C.c_double),
+        ("gcr_nkrylov", C.c_int),
+        ("inner_tol", C.c_double),
+        ("inner_maxiter", C.c_int),
+        ("coarse_tol", C.c_double),
+        ("coarse_maxiter", C.c_int),
+    ]
+
+
+class mg_solve_stats(C.Structure):
+    _fields_ = [
+        ("iters", C.c_int),
+        ("restarts", C.c_int),
+        ("level_iters", C.c_int * MG_MAX_LEVELS),
+        ("true_residual", C.c_double),
+        ("seconds", C.c_double),
+        ("history_len", C.c_int),
+        ("history", C.c_double * 512),
+    ]
+
+
+def _load():
+    path = _build.lib_path()
+    if not os.path.exists(path):
+        raise ImportError(f"libgbmg.so not built ({path}); run "
+                          "`python -m paper_1612_07873_gb300.build`")
+    lib = C.CDLL(path)
+    vp, i, d, sz = C.c_void_p, C.c_int, C.c_double, C.c_size_t
+    sig = {
+        "mg_default_params": (None, [C.POINTER(mg_params)]),
+        "mg_create": (i, [C.POINTER(mg_params), vp, C.POINTER(vp)]),
+        "mg_destroy": (i, [vp]),
+        "mg_setup_nullvecs": (i, [vp, i, vp, vp]),
+        "mg_set_nullvecs": (i, [vp, i, vp, vp]),
+        "mg_get_nullvecs": (i, [vp, i, i, vp, sz, vp]),
+        "mg_build_coarse": (i, [vp, i, vp]),
+        "mg_coarse_apply": (i, [vp, i, vp, vp, i, vp]),
+        "mg_apply": (i, [vp, i, vp, vp, vp]),
+        "mg_wilson_clover_apply": (i, [vp, vp, vp, vp]),
+        "mg_restrict": (i, [vp, i, vp, vp, vp]),
+        "mg_prolong": (i, [vp, i, vp, vp, vp]),
+        "mg_gcr_solve": (i, [vp, vp, vp, d, i, C.POINTER(mg_solve_stats), vp]),
+        "mg_get_coarse_links": (i, [vp, i, vp, sz, vp]),
+        "mg_set_coarse_links": (i, [vp, i, vp, sz, vp]),
+        "mg_level_info": (i, [vp, i, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                              C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "mg_profile_enable": (i, [vp, i]),
+        "mg_profile_reset": (i, [vp]),
+        "mg_profile_query": (i, [vp, C.c_char_p, i, C.POINTER(C.c_int), C.POINTER(d),
+                                 C.POINTER(d), C.POINTER(d)]),
+        "mg_launch_count": (C.c_longlong, [vp]),
+        "mg_status_string": (C.c_char_p, [i]),
+        "mg_last_error": (C.c_char_p, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+LIB = _load()
+LIB_PATH = _build.lib_path()
+
+
+class MGError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ok(st, ctx=None):
+    if st != 0:
+        msg = LIB.mg_last_error(ctx)
+        raise MGError(st, msg.decode() if msg else "")
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "expects a contiguous CUDA tensor"
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def default_params(**kw) -> mg_params:
+    p = mg_params()
+    LIB.mg_default_params(C.byref(p))
+    for k, v in kw.items():
+        if k == "dims":
+            p.dims[:] = list(v)
+        elif k == "block":
+            for l, b in enumerate(v):
+                p.block[l][:] = list(b)
+        elif k == "nvec":
+            for l, n in enumerate(v):
+                p.nvec[l] = n
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def mg_create(params: mg_params, gauge: torch.Tensor):
+    assert gauge.dtype == torch.complex128
+    h = C.c_void_p()
+    _ok(LIB.mg_create(C.byref(params), _ptr(gauge), C.byref(h)))
+    return h
+
+
+def mg_destroy(ctx):
+    _ok(LIB.mg_destroy(ctx))
+
+
+def mg_setup_nullvecs(ctx, level, init=None, stream=None):
+    _ok(LIB.mg_setup_nullvecs(ctx, level, _ptr(init), _stream(stream)), ctx)
+
+
+def mg_set_nullvecs(ctx, level, vecs, stream=None):
+    assert vecs.dtype == torch.complex128
+    _ok(LIB.mg_set_nullvecs(ctx, level, _ptr(vecs), _stream(stream)), ctx)
+
+
+def mg_get_nullvecs(ctx, level, out, kind=1, stream=None):
+    _ok(LIB.mg_get_nullvecs(ctx, level, kind, _ptr(out), out.numel() * out.element_size(),
+                            _stream(stream)), ctx)
+    return out
+
+
+def mg_build_coarse(ctx, level, stream=None):
+    _ok(LIB.mg_build_coarse(ctx, level, _stream(stream)), ctx)
+
+
+def mg_coarse_apply(ctx, level, y, x, nrhs=1, stream=None):
+    _ok(LIB.mg_coarse_apply(ctx, level, _ptr(y), _ptr(x), nrhs, _stream(stream)), ctx)
+
+
+def mg_apply(ctx, level, y, x, stream=None):
+    _ok(LIB.mg_apply(ctx, level, _ptr(y), _ptr(x), _stream(stream)), ctx)
+
+
+def mg_wilson_clover_apply(ctx, out, inp, stream=None):
+    _ok(LIB.mg_wilson_clover_apply(ctx, _ptr(out), _ptr(inp), _stream(stream)), ctx)
+
+
+def mg_restrict(ctx, level, coarse, fine, stream=None):
+    _ok(LIB.mg_restrict(ctx, level, _ptr(coarse), _ptr(fine), _stream(stream)), ctx)
+
+
+def mg_prolong(ctx, level, fine, coarse, stream=None):
+    _ok(LIB.mg_prolong(ctx, level, _ptr(fine), _ptr(coarse), _stream(stream)), ctx)
+
+
+def mg_gcr_solve(ctx, x, b, tol=1e-10, maxiter=200, stream=None, check=True):
+    s = mg_solve_stats()
+    st = LIB.mg_gcr_solve(ctx, _ptr(x), _ptr(b), tol, maxiter, C.byref(s), _stream(stream))
+    if check:
+        _ok(st, ctx)
+    return dict(status=st, iters=s.iters, restarts=s.restarts,
+                level_iters=list(s.level_iters), true_residual=s.true_residual,
+                seconds=s.seconds, history=list(s.history[:s.history_len]))
+
+
+def mg_get_coarse_links(ctx, level, out, stream=None):
+    _ok(LIB.mg_get_coarse_links(ctx, level, _ptr(out), out.numel() * out.element_size(),
+                                _stream(stream)), ctx)
+    return out
+
+
+def mg_set_coarse_links(ctx, level, links, stream=None):
+    assert links.dtype == torch.complex128
+    _ok(LIB.mg_set_coarse_links(ctx, level, _ptr(links), links.numel() * links.element_size(),
+                                _stream(stream)), ctx)
+
+
+def mg_level_info(ctx, level):
+    dims = (C.c_int * 4)()
+    vol, nd, vp = C.c_int(), C.c_int(), C.c_int()
+    _ok(LIB.mg_level_info(ctx, level, dims, C.byref(vol), C.byref(nd), C.byref(vp)), ctx)
+    return dict(dims=tuple(dims), volume=vol.value, ndof=nd.value,
+                dtype=torch.complex128 if vp.value == F64 else torch.complex64)
+
+
+def mg_profile_enable(ctx, on=True):
+    _ok(LIB.mg_profile_enable(ctx, int(on)), ctx)
+
+
+def mg_profile_reset(ctx):
+    _ok(LIB.mg_profile_reset(ctx), ctx)
+
+
+def mg_profile_query(ctx, name, level=-1):
+    n, ms, b, f = C.c_int(), C.c_double(), C.c_double(), C.c_double()
+    _ok(LIB.mg_profile_query(ctx, name.encode(), level, C.byref(n), C.byref(ms), C.byref(b),
+                             C.byref(f)), ctx)
+    return dict(launches=n.value, ms=ms.value, bytes=b.value, flops=f.value)
+
+
+def mg_launch_count(ctx) -> int:
+    return int(LIB.mg_launch_count(ctx))
+
+
+class Multigrid:
+    """Owner of an mg_ctx with the per-level vector shapes at hand."""
+
+    def __init__(self, params: mg_params, gauge: torch.Tensor):
+        self.params = params
+        self.ctx = mg_create(params, gauge)
+        self.levels = [mg_level_info(self.ctx, l) for l in range(params.nlevels)]
+
+    def close(self):
+        if self.ctx is not None:
+            mg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def vector(self, level, nrhs=1, dtype=None):
+        li = self.levels[level]
+        shape = (li["volume"], li["ndof"]) + ((nrhs,) if nrhs > 1 else ())
+        return torch.zeros(shape, dtype=dtype or li["dtype"], device="cuda")

@@ -1,0 +1,372 @@
+// extern "C" entry points of libgbmg.so (declared in include/gbmg.h):
+// argument checks, context lifecycle, error reporting, kernel timing.
+#include <cstring>
+#include <string>
+
+#include "kernels.cuh"
+
+using namespace gbmg;
+
+namespace {
+thread_local std::string g_last_error;
+
+mg_status fail(mg_ctx* c, mg_status s, const std::string& m) {
+  if (c) c->err = m;
+  g_last_error = m;
+  return s;
+}
+
+template <typename F>
+mg_status guarded(mg_ctx* c, F&& f) {
+  if (!c) return fail(nullptr, MG_ERR_ARG, "null context");
+  try {
+    f();
+    c->err.clear();
+    return MG_OK;
+  } catch (const Error& e) {
+    return fail(c, e.code, e.what());
+  } catch (const std::exception& e) {
+    return fail(c, MG_ERR_CUDA, e.what());
+  }
+}
+
+cudaStream_t S(void* s) { return static_cast<cudaStream_t>(s); }
+
+void check_level(mg_ctx* c, int level, int lo, int hi) {
+  GB_REQUIRE(level >= lo && level <= hi && level < c->nlevels, MG_ERR_ARG,
+             "level " + std::to_string(level) + " out of range");
+}
+}  // namespace
+
+// ------------------------------------------------------------------ profiler
+namespace gbmg {
+cudaEvent_t Profiler::get() {
+  if (!pool.empty()) {
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  GB_CHECK(cudaEventCreate(&e));
+  return e;
+}
+void Profiler::clear() {
+  for (auto& r : recs) {
+    pool.push_back(r.start);
+    pool.push_back(r.stop);
+  }
+  recs.clear();
+}
+Profiler::~Profiler() {
+  clear();
+  for (auto e : pool) cudaEventDestroy(e);
+}
+ProfScope::ProfScope(Profiler& p, cudaStream_t s, const char* name, int level, double bytes,
+                     double flops)
+    : prof(&p), st(s), active(p.on) {
+  if (!active) return;
+  rec.name = name;
+  rec.level = level;
+  rec.bytes = bytes;
+  rec.flops = flops;
+  rec.start = p.get();
+  rec.stop = p.get();
+  cudaEventRecord(rec.start, st);
+}
+ProfScope::~ProfScope() {
+  if (!active) return;
+  cudaEventRecord(rec.stop, st);
+  prof->recs.push_back(rec);
+}
+}  // namespace gbmg
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+void mg_default_params(mg_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->t_antiperiodic = 1;
+  p->mass = 0.0;
+  p->csw = 1.0;
+  p->nlevels = 2;
+  p->setup_sweeps = 10;
+  p->seed = 1;
+  p->prec_fine = MG_F64;
+  p->prec_coarse = MG_F64;
+  p->mr_iters = 4;
+  p->mr_omega = 1.0;
+  p->gcr_nkrylov = 10;
+  p->inner_tol = 0.25;
+  p->inner_maxiter = 10;
+  p->coarse_tol = 0.1;
+  p->coarse_maxiter = 100;
+}
+
+mg_status mg_create(const mg_params* p, const void* gauge_dev, mg_ctx** out) {
+  if (!p || !out) return fail(nullptr, MG_ERR_ARG, "mg_create: null argument");
+  *out = nullptr;
+  if (!gauge_dev) return fail(nullptr, MG_ERR_ARG, "mg_create: null gauge field");
+  if (p->nlevels < 2 || p->nlevels > MG_MAX_LEVELS)
+    return fail(nullptr, MG_ERR_ARG, "mg_create: nlevels must be 2..4");
+  if (p->prec_fine != MG_F64 && p->prec_fine != MG_F32)
+    return fail(nullptr, MG_ERR_ARG, "mg_create: prec_fine must be F64 or F32");
+  if (p->prec_coarse < MG_F64 || p->prec_coarse > MG_F16)
+    return fail(nullptr, MG_ERR_ARG, "mg_create: bad prec_coarse");
+  if (p->gcr_nkrylov < 1 || p->gcr_nkrylov > 64 || p->mr_iters < 0)
+    return fail(nullptr, MG_ERR_ARG, "mg_create: bad solver parameters");
+  int dims[4];
+  long long vol = 1;
+  for (int m = 0; m < 4; ++m) {
+    dims[m] = p->dims[m];
+    if (dims[m] < 1) return fail(nullptr, MG_ERR_ARG, "mg_create: lattice extent < 1");
+    vol *= dims[m];
+  }
+  if (vol > (1ll << 30)) return fail(nullptr, MG_ERR_ARG, "mg_create: lattice too large");
+  mg_ctx* c = new mg_ctx();
+  try {
+    c->p = *p;
+    c->nlevels = p->nlevels;
+    for (int l = 0; l < c->nlevels; ++l) {
+      Level& L = c->L[l];
+      L.index = l;
+      if (l == 0) {
+        L.g = make_geom(dims);
+        L.nd = 12;
+        L.prec = p->prec_fine;
+      } else {
+        Level& F = c->L[l - 1];
+        int cd[4];
+        for (int m = 0; m < 4; ++m) {
+          int b = p->block[l - 1][m];
+          GB_REQUIRE(b >= 1 && F.g.L[m] % b == 0, MG_ERR_ARG,
+                     "extent " + std::to_string(F.g.L[m]) + " of level " + std::to_string(l - 1) +
+                         " not divisible by block " + std::to_string(b));
+          cd[m] = F.g.L[m] / b;
+          F.block[m] = b;
+        }
+        GB_REQUIRE(p->nvec[l - 1] >= 1 && p->nvec[l - 1] <= 48, MG_ERR_ARG,
+                   "nvec must be 1..48");
+        F.nvec = p->nvec[l - 1];
+        L.g = make_geom(cd);
+        L.nd = 2 * F.nvec;
+        L.prec = p->prec_coarse;
+        GB_REQUIRE(!((L.prec == MG_BF16 || L.prec == MG_F16) && (L.nd % 4)), MG_ERR_ARG,
+                   "16-bit coarse links need an even number of null vectors");
+      }
+      L.vprec = vec_prec_of(L.prec);
+    }
+    GB_REQUIRE(!(c->L[0].vprec == MG_F32 && c->L[1].vprec == MG_F64), MG_ERR_ARG,
+               "FP64 coarse levels need an FP64 fine level");
+    c->red_partials.alloc(2 * 1024 * sizeof(double2));
+    c->scalars.alloc(SC_COUNT * sizeof(double2));
+    c->status.alloc(64);
+    GB_CHECK(cudaMallocHost(&c->h_scalars, SC_COUNT * sizeof(double2)));
+    GB_CHECK(cudaMemset(c->scalars.p, 0, c->scalars.bytes));
+    GB_CHECK(cudaMemset(c->status.p, 0, c->status.bytes));
+    fine_operator_build(c, gauge_dev, 0);
+    GB_CHECK(cudaDeviceSynchronize());
+  } catch (const Error& e) {
+    delete c;
+    return fail(nullptr, e.code, e.what());
+  } catch (const std::exception& e) {
+    delete c;
+    return fail(nullptr, MG_ERR_CUDA, e.what());
+  }
+  *out = c;
+  return MG_OK;
+}
+
+mg_status mg_destroy(mg_ctx* c) {
+  if (!c) return MG_ERR_ARG;
+  cudaDeviceSynchronize();
+  delete c;
+  return MG_OK;
+}
+
+mg_status mg_setup_nullvecs(mg_ctx* c, int level, const void* init, void* stream) {
+  return guarded(c, [&] {
+    check_level(c, level, 0, c->nlevels - 2);
+    GB_REQUIRE(level == 0 || c->L[level].have_op, MG_ERR_STATE,
+               "setup_nullvecs: operator of this level not built");
+    setup_sweeps(c, level, init, S(stream));
+    block_orthonormalise(c, level, S(stream));
+  });
+}
+
+mg_status mg_set_nullvecs(mg_ctx* c, int level, const void* vecs, void* stream) {
+  return guarded(c, [&] {
+    check_level(c, level, 0, c->nlevels - 2);
+    GB_REQUIRE(vecs, MG_ERR_ARG, "set_nullvecs: null pointer");
+    Level& L = c->L[level];
+    const size_t bytes = size_t(L.nvec) * L.vec_elems() * 16;
+    L.raw.alloc(bytes);
+    GB_CHECK(cudaMemcpyAsync(L.raw.p, vecs, bytes, cudaMemcpyDeviceToDevice, S(stream)));
+    L.have_raw = true;
+    block_orthonormalise(c, level, S(stream));
+  });
+}
+
+mg_status mg_get_nullvecs(mg_ctx* c, int level, int kind, void* dst, size_t bytes, void* stream) {
+  return guarded(c, [&] {
+    check_level(c, level, 0, c->nlevels - 2);
+    Level& L = c->L[level];
+    const size_t need = size_t(L.nvec) * L.vec_elems() * 16;
+    GB_REQUIRE(dst && bytes == need, MG_ERR_ARG, "get_nullvecs: size mismatch");
+    GB_REQUIRE(kind == 0 || kind == 1, MG_ERR_ARG, "get_nullvecs: kind must be 0 or 1");
+    const DevBuf& src = kind == 0 ? L.raw : L.orth64;
+    GB_REQUIRE(kind == 0 ? L.have_raw : L.have_V, MG_ERR_STATE, "get_nullvecs: not available");
+    GB_CHECK(cudaMemcpyAsync(dst, src.p, need, cudaMemcpyDeviceToDevice, S(stream)));
+  });
+}
+
+mg_status mg_build_coarse(mg_ctx* c, int level, void* stream) {
+  return guarded(c, [&] {
+    check_level(c, level, 0, c->nlevels - 2);
+    galerkin_build(c, level, S(stream));
+  });
+}
+
+mg_status mg_coarse_apply(mg_ctx* c, int level, void* y, const void* x, int nrhs, void* stream) {
+  return guarded(c, [&] {
+    check_level(c, level, 1, c->nlevels - 1);
+    GB_REQUIRE(x && y, MG_ERR_ARG, "coarse_apply: null vector");
+    const size_t bytes = c->L[level].vec_bytes() * size_t(nrhs > 0 ? nrhs : 1);
+    const char* xa = (const char*)x;
+    const char* ya = (const char*)y;
+    GB_REQUIRE(ya + bytes <= xa || xa + bytes <= ya, MG_ERR_ARG,
+               "coarse_apply: input and output overlap");
+    coarse_apply(c, level, y, x, nrhs, S(stream));
+  });
+}
+
+mg_status mg_apply(mg_ctx* c, int level, void* y, const void* x, void* stream) {
+  return guarded(c, [&] {
+    check_level(c, level, 0, c->nlevels - 1);
+    GB_REQUIRE(x && y, MG_ERR_ARG, "apply: null vector");
+    Level& L = c->L[level];
+    level_apply(c, level, level_vec(L, y), level_vec(L, const_cast<void*>(x)), S(stream));
+  });
+}
+
+mg_status mg_wilson_clover_apply(mg_ctx* c, void* out, const void* in, void* stream) {
+  return guarded(c, [&] {
+    GB_REQUIRE(in && out, MG_ERR_ARG, "wilson_clover_apply: null vector");
+    Level& L = c->L[0];
+    wilson_apply(c, level_vec(L, out), level_vec(L, const_cast<void*>(in)), 1, S(stream));
+  });
+}
+
+mg_status mg_restrict(mg_ctx* c, int level, void* coarse, const void* fine, void* stream) {
+  return guarded(c, [&] {
+    check_level(c, level, 0, c->nlevels - 2);
+    GB_REQUIRE(coarse && fine, MG_ERR_ARG, "restrict: null vector");
+    restrict_apply(c, level, level_vec(c->L[level + 1], coarse),
+                   level_vec(c->L[level], const_cast<void*>(fine)), S(stream));
+  });
+}
+
+mg_status mg_prolong(mg_ctx* c, int level, void* fine, const void* coarse, void* stream) {
+  return guarded(c, [&] {
+    check_level(c, level, 0, c->nlevels - 2);
+    GB_REQUIRE(coarse && fine, MG_ERR_ARG, "prolong: null vector");
+    prolong_apply(c, level, level_vec(c->L[level], fine),
+                  level_vec(c->L[level + 1], const_cast<void*>(coarse)), S(stream));
+  });
+}
+
+mg_status mg_gcr_solve(mg_ctx* c, void* x, const void* b, double tol, int maxiter,
+                       mg_solve_stats* stats, void* stream) {
+  return guarded(c, [&] {
+    GB_REQUIRE(x && b && x != b, MG_ERR_ARG, "gcr_solve: bad vectors");
+    GB_REQUIRE(tol > 0 && maxiter > 0, MG_ERR_ARG, "gcr_solve: bad tol/maxiter");
+    gcr_solve(c, x, b, tol, maxiter, stats, S(stream));
+  });
+}
+
+mg_status mg_get_coarse_links(mg_ctx* c, int level, void* dst, size_t bytes, void* stream) {
+  return guarded(c, [&] {
+    check_level(c, level, 1, c->nlevels - 1);
+    Level& L = c->L[level];
+    GB_REQUIRE(dst && bytes == size_t(L.g.vol) * 9 * L.nd * L.nd * 16, MG_ERR_ARG,
+               "get_coarse_links: size mismatch");
+    links_export(c, level, dst, S(stream));
+  });
+}
+
+mg_status mg_set_coarse_links(mg_ctx* c, int level, const void* src, size_t bytes, void* stream) {
+  return guarded(c, [&] {
+    check_level(c, level, 1, c->nlevels - 1);
+    Level& L = c->L[level];
+    GB_REQUIRE(src && bytes == size_t(L.g.vol) * 9 * L.nd * L.nd * 16, MG_ERR_ARG,
+               "set_coarse_links: size mismatch");
+    links_import(c, level, src, S(stream));
+  });
+}
+
+mg_status mg_level_info(mg_ctx* c, int level, int dims[4], int* volume, int* ndof, int* vprec) {
+  return guarded(c, [&] {
+    check_level(c, level, 0, c->nlevels - 1);
+    Level& L = c->L[level];
+    if (dims)
+      for (int m = 0; m < 4; ++m) dims[m] = L.g.L[m];
+    if (volume) *volume = L.g.vol;
+    if (ndof) *ndof = L.nd;
+    if (vprec) *vprec = int(L.vprec);
+  });
+}
+
+mg_status mg_profile_enable(mg_ctx* c, int on) {
+  return guarded(c, [&] { c->prof.on = on != 0; });
+}
+
+mg_status mg_profile_reset(mg_ctx* c) {
+  return guarded(c, [&] {
+    for (auto& r : c->prof.recs) GB_CHECK(cudaEventSynchronize(r.stop));
+    c->prof.clear();
+  });
+}
+
+mg_status mg_profile_query(mg_ctx* c, const char* name, int level, int* launches, double* ms,
+                           double* bytes, double* flops) {
+  return guarded(c, [&] {
+    GB_REQUIRE(name, MG_ERR_ARG, "profile_query: null name");
+    int n = 0;
+    double t = 0, b = 0, f = 0;
+    for (auto& r : c->prof.recs) {
+      if (r.name != name || (level >= 0 && r.level != level)) continue;
+      GB_CHECK(cudaEventSynchronize(r.stop));
+      float e = 0.f;
+      GB_CHECK(cudaEventElapsedTime(&e, r.start, r.stop));
+      ++n;
+      t += e;
+      b += r.bytes;
+      f += r.flops;
+    }
+    if (launches) *launches = n;
+    if (ms) *ms = t;
+    if (bytes) *bytes = b;
+    if (flops) *flops = f;
+  });
+}
+
+long long mg_launch_count(mg_ctx* c) { return c ? c->launches : 0; }
+
+const char* mg_status_string(mg_status s) {
+  switch (s) {
+    case MG_OK: return "ok";
+    case MG_ERR_ARG: return "invalid argument";
+    case MG_ERR_CUDA: return "CUDA error";
+    case MG_ERR_OOM: return "out of device memory";
+    case MG_ERR_STATE: return "call out of order";
+    case MG_ERR_NOT_CONVERGED: return "solver did not converge";
+    case MG_ERR_NUMERICAL: return "numerical breakdown";
+    case MG_ERR_TIMEOUT: return "device wait timed out";
+    case MG_ERR_RANK: return "rank-deficient null-vector block";
+  }
+  return "unknown status";
+}
+
+const char* mg_last_error(mg_ctx* c) { return c ? c->err.c_str() : g_last_error.c_str(); }
+
+}  // extern "C"

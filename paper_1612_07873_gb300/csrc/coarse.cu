@@ -1,0 +1,336 @@
+// Coarse-grid stencil apply of Eq. (3) and the coarse-link store.
+//
+//   y(s) = sum_{slot=0..8} L[s][slot] x(nbr(s, slot)),  n x n complex blocks
+//
+// Every link byte is used exactly once per apply, so the single-RHS apply is
+// an HBM stream (about 1 flop per byte in FP32).  Internal link layout per
+// site: [slot][col][row] -- a column of n rows is contiguous -- so the 9n
+// "columns" of a site form one contiguous run of 9n*n complex numbers.
+//
+// Thread mapping of the streaming kernel (Sec. IV-B..E exposed differently):
+//  * one CTA per coarse site;
+//  * a thread owns one 16-byte chunk of rows (RPC = 16 / sizeof(element)
+//    rows: 1 in FP64, 2 in FP32, 4 in 16-bit) -> TPC = n / RPC threads span a
+//    column, so consecutive threads read consecutive 16-byte chunks;
+//  * CG column groups split the 9n-long dot products (stencil direction and
+//    dot-product parallelism at once); the CG partial sums of every row are
+//    reduced through shared memory;
+//  * the 9 gathered neighbour spinors sit in shared memory (9n complex).
+// 16-bit links carry one FP32 scale per site (value = scale * stored); the
+// arithmetic accumulates in FP32.
+#include "kernels.cuh"
+
+namespace gbmg {
+
+namespace {
+
+template <typename S>
+struct Unpack;
+template <>
+struct Unpack<cpx<double>> {
+  static constexpr int RPC = 1;
+  __device__ static __forceinline__ void get(uint4 v, cpx<double> out[1]) {
+    out[0] = cpx<double>(__hiloint2double(int(v.y), int(v.x)), __hiloint2double(int(v.w), int(v.z)));
+  }
+};
+template <>
+struct Unpack<cpx<float>> {
+  static constexpr int RPC = 2;
+  __device__ static __forceinline__ void get(uint4 v, cpx<float> out[2]) {
+    out[0] = cpx<float>(__uint_as_float(v.x), __uint_as_float(v.y));
+    out[1] = cpx<float>(__uint_as_float(v.z), __uint_as_float(v.w));
+  }
+};
+template <>
+struct Unpack<bf16c> {
+  static constexpr int RPC = 4;
+  __device__ static __forceinline__ void get(uint4 v, cpx<float> out[4]) {
+    uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      out[i] = cpx<float>(__uint_as_float(w[i] << 16), __uint_as_float(w[i] & 0xffff0000u));
+    }
+  }
+};
+template <>
+struct Unpack<f16c> {
+  static constexpr int RPC = 4;
+  __device__ static __forceinline__ void get(uint4 v, cpx<float> out[4]) {
+    uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      __half2 h = *reinterpret_cast<__half2*>(&w[i]);
+      float2 f = __half22float2(h);
+      out[i] = cpx<float>(f.x, f.y);
+    }
+  }
+};
+
+constexpr int batch_of(int iters) {
+  for (int u = 8; u > 1; --u)
+    if (iters % u == 0) return u;
+  return 1;
+}
+
+template <typename S, int N, int CG>
+__global__ void __launch_bounds__(CG*(N / Unpack<S>::RPC))
+    k_coarse_stream(cpx<typename StoreTraits<S>::real>* __restrict__ y,
+                    const cpx<typename StoreTraits<S>::real>* __restrict__ x,
+                    const S* __restrict__ links, const float* __restrict__ scales, Geom g) {
+  using R = typename StoreTraits<S>::real;
+  constexpr int RPC = Unpack<S>::RPC;
+  constexpr int TPC = N / RPC;
+  constexpr int K = 9 * N;
+  constexpr int NT = CG * TPC;
+  constexpr int ITER = K / CG;
+  constexpr int U = batch_of(ITER);
+  static_assert(N % RPC == 0 && K % CG == 0, "tile shape");
+  __shared__ cpx<R> xs[K];
+  __shared__ cpx<R> red[CG][N];
+  __shared__ int nb[9];
+  const int site = blockIdx.x;
+  const int tid = threadIdx.x;
+  if (tid < 9) {
+    int c[4];
+    site_coords(g, site, c);
+    nb[tid] = neighbour(g, site, c, tid);
+  }
+  __syncthreads();
+  for (int i = tid; i < K; i += NT) {
+    int d = i / N;
+    xs[i] = x[size_t(nb[d]) * N + (i - d * N)];
+  }
+  __syncthreads();
+  const int rp = tid % TPC;
+  const int cg = tid / TPC;
+  cpx<R> acc[RPC];
+#pragma unroll
+  for (int r = 0; r < RPC; ++r) acc[r] = cpx<R>(R(0), R(0));
+  const uint4* L = reinterpret_cast<const uint4*>(links) + size_t(site) * K * TPC + rp;
+  for (int it = 0; it < ITER; it += U) {
+    uint4 v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = ld_stream16(L + size_t(cg + (it + u) * CG) * TPC);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      cpx<R> e[RPC];
+      Unpack<S>::get(v[u], e);
+      cpx<R> xv = xs[cg + (it + u) * CG];
+#pragma unroll
+      for (int r = 0; r < RPC; ++r) cmac(acc[r], e[r], xv);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < RPC; ++r) red[cg][rp * RPC + r] = acc[r];
+  __syncthreads();
+  for (int row = tid; row < N; row += NT) {
+    cpx<R> s = red[0][row];
+#pragma unroll
+    for (int q = 1; q < CG; ++q) s += red[q][row];
+    if (StoreTraits<S>::scaled) s = R(scales[site]) * s;
+    y[size_t(site) * N + row] = s;
+  }
+}
+
+// Any n, any number of right-hand sides: one CTA per site, threads over
+// (row, rhs); links are read column-wise (coalesced over rows).
+template <typename S>
+__global__ void k_coarse_generic(cpx<typename StoreTraits<S>::real>* __restrict__ y,
+                                 const cpx<typename StoreTraits<S>::real>* __restrict__ x,
+                                 const S* __restrict__ links, const float* __restrict__ scales,
+                                 Geom g, int n, int nrhs) {
+  using R = typename StoreTraits<S>::real;
+  __shared__ int nb[9];
+  const int site = blockIdx.x;
+  if (threadIdx.x < 9) {
+    int c[4];
+    site_coords(g, site, c);
+    nb[threadIdx.x] = neighbour(g, site, c, threadIdx.x);
+  }
+  __syncthreads();
+  const S* Ls = links + size_t(site) * 9 * n * n;
+  const R sc = StoreTraits<S>::scaled ? R(scales[site]) : R(1);
+  for (int t = threadIdx.x; t < n * nrhs; t += blockDim.x) {
+    int row = t / nrhs, rhs = t - row * nrhs;
+    cpx<R> acc(R(0), R(0));
+    for (int d = 0; d < 9; ++d) {
+      const cpx<R>* xn = x + size_t(nb[d]) * n * nrhs + rhs;
+      const S* Ld = Ls + size_t(d) * n * n + row;
+      for (int col = 0; col < n; ++col)
+        cmac(acc, StoreTraits<S>::load(Ld[size_t(col) * n]), xn[size_t(col) * nrhs]);
+    }
+    y[size_t(site) * n * nrhs + t] = sc * acc;
+  }
+}
+
+// ext [V][9][row][col] complex double -> internal [V][9][col][row] in R
+template <typename R>
+__global__ void k_links_import(cpx<R>* __restrict__ out, const cpx<double>* __restrict__ in,
+                               int vol, int n) {
+  size_t total = size_t(vol) * 9 * n * n;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < total;
+       i += size_t(gridDim.x) * blockDim.x) {
+    size_t blk = i / (size_t(n) * n);
+    int rem = int(i - blk * n * n);
+    int col = rem / n, row = rem - col * n;
+    out[i] = cpx<R>(in[blk * n * n + size_t(row) * n + col]);
+  }
+}
+
+template <typename S>
+__global__ void k_links_export(cpx<double>* __restrict__ out, const S* __restrict__ in,
+                               const float* __restrict__ scales, int vol, int n) {
+  size_t total = size_t(vol) * 9 * n * n;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < total;
+       i += size_t(gridDim.x) * blockDim.x) {
+    size_t blk = i / (size_t(n) * n);
+    int rem = int(i - blk * n * n);
+    int row = rem / n, col = rem - row * n;
+    size_t site = blk / 9;
+    double sc = StoreTraits<S>::scaled ? double(scales[site]) : 1.0;
+    cpx<double> v(StoreTraits<S>::load(in[blk * n * n + size_t(col) * n + row]));
+    out[i] = sc * v;
+  }
+}
+
+// per-site scale = max |component| over the nine blocks; stored = value/scale
+template <typename S>
+__global__ void k_links_pack16(S* __restrict__ out, float* __restrict__ scales,
+                               const cpx<float>* __restrict__ in, int n) {
+  __shared__ float sh[32];
+  const size_t per = size_t(9) * n * n;
+  const cpx<float>* src = in + blockIdx.x * per;
+  float m = 0.f;
+  for (size_t i = threadIdx.x; i < per; i += blockDim.x)
+    m = fmaxf(m, fmaxf(fabsf(src[i].re), fabsf(src[i].im)));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) sh[0] = m > 0.f ? m : 1.f;
+  }
+  __syncthreads();
+  const float sc = sh[0], inv = 1.f / sc;
+  if (threadIdx.x == 0) scales[blockIdx.x] = sc;
+  S* dst = out + blockIdx.x * per;
+  for (size_t i = threadIdx.x; i < per; i += blockDim.x)
+    dst[i] = StoreTraits<S>::pack(cpx<float>(src[i].re * inv, src[i].im * inv));
+}
+
+template <typename S, int N, int CG>
+void launch_stream(const Level& L, void* y, const void* x, const void* links, cudaStream_t st) {
+  using R = typename StoreTraits<S>::real;
+  constexpr int NT = CG * (N / Unpack<S>::RPC);
+  k_coarse_stream<S, N, CG><<<L.g.vol, NT, 0, st>>>((cpx<R>*)y, (const cpx<R>*)x, (const S*)links,
+                                                    L.scales.as<float>(), L.g);
+}
+
+template <typename S>
+bool try_stream(const Level& L, void* y, const void* x, const void* links, cudaStream_t st) {
+  constexpr int RPC = Unpack<S>::RPC;
+  constexpr int CG = RPC == 1 ? 4 : (RPC == 2 ? 8 : 16);
+  switch (L.nd) {
+    case 16: launch_stream<S, 16, CG>(L, y, x, links, st); return true;
+    case 32: launch_stream<S, 32, CG>(L, y, x, links, st); return true;
+    case 48: launch_stream<S, 48, CG>(L, y, x, links, st); return true;
+    case 64: launch_stream<S, 64, CG>(L, y, x, links, st); return true;
+    default: return false;
+  }
+}
+
+template <typename S>
+void dispatch_apply(const Level& L, void* y, const void* x, const void* links, int nrhs,
+                    cudaStream_t st) {
+  using R = typename StoreTraits<S>::real;
+  if (nrhs == 1 && try_stream<S>(L, y, x, links, st)) return;
+  int threads = L.nd * nrhs >= 256 ? 256 : ((L.nd * nrhs + 31) / 32) * 32;
+  k_coarse_generic<S><<<L.g.vol, threads, 0, st>>>((cpx<R>*)y, (const cpx<R>*)x, (const S*)links,
+                                                   L.scales.as<float>(), L.g, L.nd, nrhs);
+}
+
+}  // namespace
+
+void coarse_apply(mg_ctx* c, int level, void* y, const void* x, int nrhs, cudaStream_t st) {
+  Level& L = c->L[level];
+  GB_REQUIRE(level >= 1 && level < c->nlevels, MG_ERR_ARG, "coarse_apply: bad level");
+  GB_REQUIRE(L.have_op, MG_ERR_STATE, "coarse_apply: coarse operator not built");
+  GB_REQUIRE(nrhs >= 1, MG_ERR_ARG, "coarse_apply: nrhs < 1");
+  GB_REQUIRE(y != x, MG_ERR_ARG, "coarse_apply: output aliases input");
+  const double n = L.nd;
+  const double lbytes = double(L.g.vol) * 9 * n * n * (L.prec == MG_F64 ? 16 : L.prec == MG_F32 ? 8 : 4);
+  const double vbytes = double(L.g.vol) * 2 * n * nrhs * (L.vprec == MG_F64 ? 16 : 8);
+  ProfScope ps(c->prof, st, "coarse_apply", level, lbytes + vbytes,
+               8.0 * 9 * n * n * L.g.vol * nrhs);
+  switch (L.prec) {
+    case MG_F64: dispatch_apply<cpx<double>>(L, y, x, L.links.p, nrhs, st); break;
+    case MG_F32: dispatch_apply<cpx<float>>(L, y, x, L.links.p, nrhs, st); break;
+    case MG_BF16: dispatch_apply<bf16c>(L, y, x, L.links16.p, nrhs, st); break;
+    case MG_F16: dispatch_apply<f16c>(L, y, x, L.links16.p, nrhs, st); break;
+  }
+  GB_LAUNCH_CHECK();
+  c->launches++;
+}
+
+void links_pack16(mg_ctx* c, int level, cudaStream_t st) {
+  Level& L = c->L[level];
+  if (L.prec != MG_BF16 && L.prec != MG_F16) return;
+  const size_t per = size_t(9) * L.nd * L.nd;
+  L.links16.alloc(per * L.g.vol * 4);
+  L.scales.alloc(size_t(L.g.vol) * sizeof(float));
+  if (L.prec == MG_BF16)
+    k_links_pack16<bf16c><<<L.g.vol, 256, 0, st>>>(L.links16.as<bf16c>(), L.scales.as<float>(),
+                                                   L.links.as<cpx<float>>(), L.nd);
+  else
+    k_links_pack16<f16c><<<L.g.vol, 256, 0, st>>>(L.links16.as<f16c>(), L.scales.as<float>(),
+                                                  L.links.as<cpx<float>>(), L.nd);
+  GB_LAUNCH_CHECK();
+  c->launches++;
+}
+
+void links_import(mg_ctx* c, int level, const void* ext, cudaStream_t st) {
+  Level& L = c->L[level];
+  const size_t total = size_t(L.g.vol) * 9 * L.nd * L.nd;
+  L.links.alloc(total * prec_bytes_complex(L.vprec));
+  int blocks = ceil_div(total, 256);
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (L.vprec == MG_F64)
+    k_links_import<double><<<blocks, 256, 0, st>>>(L.links.as<cpx<double>>(),
+                                                   (const cpx<double>*)ext, L.g.vol, L.nd);
+  else
+    k_links_import<float><<<blocks, 256, 0, st>>>(L.links.as<cpx<float>>(),
+                                                  (const cpx<double>*)ext, L.g.vol, L.nd);
+  GB_LAUNCH_CHECK();
+  c->launches++;
+  links_pack16(c, level, st);
+  L.have_op = true;
+}
+
+void links_export(mg_ctx* c, int level, void* ext, cudaStream_t st) {
+  Level& L = c->L[level];
+  GB_REQUIRE(L.have_op, MG_ERR_STATE, "coarse links not built");
+  const size_t total = size_t(L.g.vol) * 9 * L.nd * L.nd;
+  int blocks = ceil_div(total, 256);
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  cpx<double>* o = (cpx<double>*)ext;
+  const float* sc = L.scales.as<float>();
+  switch (L.prec) {
+    case MG_F64:
+      k_links_export<cpx<double>><<<blocks, 256, 0, st>>>(o, L.links.as<cpx<double>>(), sc, L.g.vol, L.nd);
+      break;
+    case MG_F32:
+      k_links_export<cpx<float>><<<blocks, 256, 0, st>>>(o, L.links.as<cpx<float>>(), sc, L.g.vol, L.nd);
+      break;
+    case MG_BF16:
+      k_links_export<bf16c><<<blocks, 256, 0, st>>>(o, L.links16.as<bf16c>(), sc, L.g.vol, L.nd);
+      break;
+    case MG_F16:
+      k_links_export<f16c><<<blocks, 256, 0, st>>>(o, L.links16.as<f16c>(), sc, L.g.vol, L.nd);
+      break;
+  }
+  GB_LAUNCH_CHECK();
+  c->launches++;
+}
+
+}  // namespace gbmg

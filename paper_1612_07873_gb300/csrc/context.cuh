@@ -1,0 +1,124 @@
+// Internal state of an mg_ctx: per-level operators, null vectors, solver
+// workspace, kernel timing.  Host-side only.
+#pragma once
+
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace gbmg {
+
+// Owning device allocation.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  void alloc(size_t n) {
+    if (n == bytes && p) return;
+    release();
+    if (n == 0) return;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      throw Error(MG_ERR_OOM, "cudaMalloc of " + std::to_string(n) + " bytes failed");
+    }
+    bytes = n;
+  }
+  template <typename T>
+  T* as() const { return static_cast<T*>(p); }
+};
+
+// One recorded launch of an instrumented kernel class.
+struct ProfRecord {
+  std::string name;
+  int level;
+  cudaEvent_t start, stop;
+  double bytes, flops;
+};
+
+struct Profiler {
+  bool on = false;
+  std::vector<ProfRecord> recs;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t get();
+  void clear();
+  ~Profiler();
+};
+
+// Scoped timer: records start at construction, stop at destruction.
+struct ProfScope {
+  Profiler* prof;
+  cudaStream_t st;
+  ProfRecord rec;
+  bool active;
+  ProfScope(Profiler& p, cudaStream_t s, const char* name, int level, double bytes, double flops);
+  ~ProfScope();
+};
+
+struct Level {
+  int index = 0;
+  Geom g{};
+  int nd = 0;                  // dofs per site
+  mg_prec prec = MG_F64;       // operator storage precision
+  mg_prec vprec = MG_F64;      // vector precision (F64 or F32)
+
+  // fine operator (level 0): gauge [4][V][9] complex with the t boundary
+  // sign folded into the last slice; clover [V][2][36] packed Hermitian.
+  DevBuf gauge64, gauge32, clover64, clover32;
+  double diag = 0.0;           // 4 + m
+
+  // coarse operator (level >= 1): internal layout [V][9][col][row] in vprec;
+  // 16-bit store + per-site scale when prec is BF16/F16.
+  DevBuf links, links16, scales;
+  bool have_op = false;
+
+  // coarsening to level + 1
+  int nvec = 0;
+  int block[4] = {1, 1, 1, 1};
+  DevBuf raw;                  // FP64 [Nv][V][nd] raw null vectors
+  DevBuf orth64;               // FP64 [Nv][V][nd] block-orthonormalised
+  DevBuf Vp;                   // vprec [V][nd][Nv] (transfer operator layout)
+  bool have_raw = false, have_V = false;
+
+  size_t vec_elems() const { return size_t(g.vol) * nd; }
+  size_t vec_bytes() const { return vec_elems() * prec_bytes_complex(vprec); }
+};
+
+// Scalars that solver kernels exchange through device memory.
+enum ScalarSlot {
+  SC_DOT0 = 0,    // complex dot results ...
+  SC_NRM0 = 32,   // real norms ...
+  SC_COUNT = 64
+};
+
+}  // namespace gbmg
+
+struct mg_ctx {
+  mg_params p{};
+  int nlevels = 0;
+  gbmg::Level L[MG_MAX_LEVELS];
+  std::string err;
+  gbmg::Profiler prof;
+  long long launches = 0;
+  // reductions: per-block partials and final scalars (complex double)
+  gbmg::DevBuf red_partials;   // [slots][max_blocks] double2
+  gbmg::DevBuf scalars;        // [SC_COUNT] double2
+  gbmg::DevBuf status;         // device status words (int)
+  double* h_scalars = nullptr; // pinned host mirror
+  // solver workspace (allocated on first solve)
+  struct SolverWS;
+  std::unique_ptr<SolverWS> ws;
+  mg_ctx();
+  ~mg_ctx();
+};

@@ -1,0 +1,246 @@
+// Galerkin coarse operator, Sec. II-D step 4:  M_hat = P^dag M P, stored as
+// the nine blocks of Eq. (3) per coarse site.
+//
+// For coarse site xc and slot d:
+//   d != 0:  Y_d(xc) = sum_{x in A(xc), hop x->x+d leaves A} P(x)^dag H_d(x) P(x+d)
+//   d == 0:  X(xc)   = sum_{x in A(xc)} P(x)^dag [ D(x) P(x) + sum_{d' inside A} H_d'(x) P(x+d') ]
+// with H_d the fine operator's block in slot d and P(x) the nf x 2Nv local
+// prolongator (column (s, j) = null vector j on the chirality-s dofs).
+// A hop x -> x+mu leaves A exactly when x_mu mod b_mu = b_mu - 1 (x - mu:
+// when x_mu mod b_mu = 0), also when the coarse extent is 1.
+//
+// One CTA per (xc, d).  Per fine site x it builds T = (term) P in shared
+// memory and accumulates P(x)^dag T into per-thread output registers.
+// Fine level (Wilson-clover, nf = 12): each term applies a spin-projected
+// hop; terms go to separate shared slices and are summed in a fixed order,
+// so the result is deterministic.  Coarse level: T is a dense product with
+// the level's link blocks.
+#include "kernels.cuh"
+#include "wilson_ops.cuh"
+
+namespace gbmg {
+
+namespace {
+
+struct AggGeom {
+  Geom fine, coarse;
+  int b[4];
+  int per;
+};
+
+__device__ __forceinline__ int fine_site(const AggGeom& m, int xc, int ls, int lc[4]) {
+  int cc[4];
+  site_coords(m.coarse, xc, cc);
+  lc[0] = ls % m.b[0];
+  ls /= m.b[0];
+  lc[1] = ls % m.b[1];
+  ls /= m.b[1];
+  lc[2] = ls % m.b[2];
+  lc[3] = ls / m.b[2];
+  return (cc[0] * m.b[0] + lc[0]) + m.fine.stride[1] * (cc[1] * m.b[1] + lc[1]) +
+         m.fine.stride[2] * (cc[2] * m.b[2] + lc[2]) + m.fine.stride[3] * (cc[3] * m.b[3] + lc[3]);
+}
+
+__device__ __forceinline__ bool leaves(const AggGeom& m, const int lc[4], int d) {
+  int mu = (d - 1) >> 1;
+  bool fwd = ((d - 1) & 1) == 0;
+  return fwd ? (lc[mu] == m.b[mu] - 1) : (lc[mu] == 0);
+}
+
+template <typename R>
+struct WilsonOp {
+  static constexpr bool wilson = true;
+  const cpx<R>* U;   // [4][V][9]
+  const R* A;        // [V][72]
+  R diag;
+};
+
+template <typename R>
+struct CoarseOp {
+  static constexpr bool wilson = false;
+  const cpx<R>* links;  // [V][9][col][row]
+};
+
+// MAXO: output elements per thread (>= (2Nv)^2 / blockDim)
+template <typename R, typename Rout, typename Op, int MAXO>
+__global__ void __launch_bounds__(256) k_galerkin(Op op, const cpx<R>* __restrict__ Vp, AggGeom m,
+                                                  int nf, int nv, cpx<Rout>* __restrict__ out) {
+  extern __shared__ unsigned char smem_raw[];
+  const int n2 = 2 * nv;
+  const int halff = nf / 2;
+  cpx<R>* sV = reinterpret_cast<cpx<R>*>(smem_raw);  // [nf][nv]
+  cpx<R>* sT = sV + nf * nv;                          // [nf][n2]
+  cpx<R>* sSl = sT + nf * n2;                         // Wilson: [9][12][n2] term slices
+  __shared__ int s_nb[9];
+  __shared__ int s_act[9];
+
+  const int xc = blockIdx.x;
+  const int d = blockIdx.y;
+  const int tid = threadIdx.x, T = blockDim.x;
+
+  cpx<R> acc[MAXO];
+#pragma unroll
+  for (int k = 0; k < MAXO; ++k) acc[k] = cpx<R>(R(0), R(0));
+
+  for (int ls = 0; ls < m.per; ++ls) {
+    int lc[4];
+    const int x = fine_site(m, xc, ls, lc);
+    if (d != 0 && !leaves(m, lc, d)) continue;  // uniform over the CTA
+    __syncthreads();
+    if (tid < 9) {
+      int c[4];
+      site_coords(m.fine, x, c);
+      s_nb[tid] = neighbour(m.fine, x, c, tid);
+      // active terms: slot d alone for a face hop; for X the diagonal and every
+      // hop that stays inside the aggregate
+      s_act[tid] = (d != 0) ? (tid == d) : (tid == 0 || !leaves(m, lc, tid));
+    }
+    for (int k = tid; k < nf * nv; k += T) sV[k] = Vp[size_t(x) * nf * nv + k];
+    __syncthreads();
+
+    if constexpr (Op::wilson) {
+      // items (term e, column c): slice e, column c = H_e(x) P_c(x + e)
+      for (int it = tid; it < 9 * n2; it += T) {
+        const int e = it / n2, col = it - e * n2;
+        if (!s_act[e]) continue;
+        const int sp = col / nv, j = col - sp * nv;
+        const cpx<R>* src = Vp + size_t(s_nb[e]) * 12 * nv + j;
+        cpx<R> psi[12], o[12];
+#pragma unroll
+        for (int a = 0; a < 12; ++a) {
+          psi[a] = ((a / 6) == sp) ? src[a * nv] : cpx<R>(R(0), R(0));
+          o[a] = cpx<R>(R(0), R(0));
+        }
+        if (e == 0) {
+          clover_accum(op.A + size_t(x) * 72, op.diag, psi, o);
+        } else {
+          const int mu = (e - 1) >> 1;
+          const bool fwd = ((e - 1) & 1) == 0;
+          const int ls_ = fwd ? x : s_nb[e];
+          hop_accum_rt(mu, fwd, op.U + (size_t(mu) * m.fine.vol + ls_) * 9, psi, o);
+        }
+#pragma unroll
+        for (int a = 0; a < 12; ++a) sSl[(e * 12 + a) * n2 + col] = o[a];
+      }
+      __syncthreads();
+      for (int k = tid; k < 12 * n2; k += T) {
+        cpx<R> s(R(0), R(0));
+        for (int e = 0; e < 9; ++e)
+          if (s_act[e]) s += sSl[e * 12 * n2 + k];
+        sT[k] = s;
+      }
+    } else {
+      // T[a][c] = sum_e sum_{b in chi(c)} H_e(x)[a][b] P(x+e)[b][j]
+      for (int it = tid; it < nf * n2; it += T) {
+        const int col = it / nf, a = it - col * nf;
+        const int sp = col / nv, j = col - sp * nv;
+        cpx<R> s(R(0), R(0));
+        for (int e = 0; e < 9; ++e) {
+          if (!s_act[e]) continue;
+          const cpx<R>* H = op.links + (size_t(x) * 9 + e) * nf * nf + a;
+          const cpx<R>* src = Vp + size_t(s_nb[e]) * nf * nv + j;
+          for (int b = sp * halff; b < (sp + 1) * halff; ++b)
+            cmac(s, H[size_t(b) * nf], src[size_t(b) * nv]);
+        }
+        sT[a * n2 + col] = s;
+      }
+    }
+    __syncthreads();
+
+    // acc[(s,i),(s',j)] += sum_{a in chi s} conj(P(x)[a][i]) T[a][(s',j)]
+#pragma unroll
+    for (int k = 0; k < MAXO; ++k) {
+      const int o = tid + k * T;
+      if (o < n2 * n2) {
+        const int row = o / n2, col = o - row * n2;
+        const int s = row / nv, i = row - s * nv;
+        cpx<R> a_ = acc[k];
+        for (int a = s * halff; a < (s + 1) * halff; ++a)
+          cmac_conj(a_, sV[a * nv + i], sT[a * n2 + col]);
+        acc[k] = a_;
+      }
+    }
+  }
+  // internal layout [xc][d][col][row]
+  cpx<Rout>* dst = out + (size_t(xc) * 9 + d) * n2 * n2;
+#pragma unroll
+  for (int k = 0; k < MAXO; ++k) {
+    const int o = tid + k * T;
+    if (o < n2 * n2) {
+      const int row = o / n2, col = o - row * n2;
+      dst[size_t(col) * n2 + row] = cpx<Rout>(acc[k]);
+    }
+  }
+}
+
+template <typename R, typename Rout, typename Op>
+void launch_galerkin(const Op& op, const cpx<R>* Vp, const AggGeom& m, int nf, int nv,
+                     cpx<Rout>* out, cudaStream_t st) {
+  const int n2 = 2 * nv;
+  size_t smem = size_t(nf) * nv * sizeof(cpx<R>) + size_t(nf) * n2 * sizeof(cpx<R>);
+  if (Op::wilson) smem += size_t(9) * 12 * n2 * sizeof(cpx<R>);
+  dim3 grid(m.coarse.vol, 9);
+  const int per_thread = (n2 * n2 + 255) / 256;
+  auto go = [&](auto kern) {
+    GB_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    kern<<<grid, 256, smem, st>>>(op, Vp, m, nf, nv, out);
+  };
+  if (per_thread <= 4)
+    go(k_galerkin<R, Rout, Op, 4>);
+  else if (per_thread <= 9)
+    go(k_galerkin<R, Rout, Op, 9>);
+  else if (per_thread <= 16)
+    go(k_galerkin<R, Rout, Op, 16>);
+  else if (per_thread <= 36)
+    go(k_galerkin<R, Rout, Op, 36>);
+  else
+    throw Error(MG_ERR_ARG, "galerkin: too many null vectors (2Nv > 96)");
+  GB_LAUNCH_CHECK();
+}
+
+}  // namespace
+
+void galerkin_build(mg_ctx* c, int level, cudaStream_t st) {
+  Level& F = c->L[level];
+  Level& C = c->L[level + 1];
+  GB_REQUIRE(F.have_V, MG_ERR_STATE, "build_coarse: null vectors not set");
+  GB_REQUIRE(level == 0 || F.have_op, MG_ERR_STATE, "build_coarse: level operator missing");
+  AggGeom m;
+  m.fine = F.g;
+  m.coarse = C.g;
+  for (int i = 0; i < 4; ++i) m.b[i] = F.block[i];
+  m.per = F.g.vol / C.g.vol;
+  const int nf = F.nd, nv = F.nvec;
+  const size_t total = size_t(C.g.vol) * 9 * C.nd * C.nd;
+  C.links.alloc(total * prec_bytes_complex(C.vprec));
+  const double flops = 8.0 * F.g.vol * (9.0 * (2 * nv) * (2 * nv) * (nf / 2));
+  ProfScope ps(c->prof, st, "galerkin", level, double(F.g.vol) * nf * nv * 16.0, flops);
+  if (F.vprec == MG_F64) {
+    GB_REQUIRE(C.vprec == MG_F64, MG_ERR_ARG, "FP64 level above an FP32 level is not supported");
+    if (level == 0) {
+      WilsonOp<double> op{F.gauge64.as<cpx<double>>(), F.clover64.as<double>(), F.diag};
+      launch_galerkin<double, double>(op, F.Vp.as<cpx<double>>(), m, nf, nv,
+                                      C.links.as<cpx<double>>(), st);
+    } else {
+      CoarseOp<double> op{F.links.as<cpx<double>>()};
+      launch_galerkin<double, double>(op, F.Vp.as<cpx<double>>(), m, nf, nv,
+                                      C.links.as<cpx<double>>(), st);
+    }
+  } else {
+    GB_REQUIRE(C.vprec == MG_F32, MG_ERR_ARG, "FP64 level above an FP32 level is not supported");
+    if (level == 0) {
+      WilsonOp<float> op{F.gauge32.as<cpx<float>>(), F.clover32.as<float>(), float(F.diag)};
+      launch_galerkin<float, float>(op, F.Vp.as<cpx<float>>(), m, nf, nv, C.links.as<cpx<float>>(),
+                                    st);
+    } else {
+      CoarseOp<float> op{F.links.as<cpx<float>>()};
+      launch_galerkin<float, float>(op, F.Vp.as<cpx<float>>(), m, nf, nv, C.links.as<cpx<float>>(),
+                                    st);
+    }
+  }
+  c->launches++;
+  links_pack16(c, level + 1, st);
+  C.have_op = true;
+}
+
+}  // namespace gbmg

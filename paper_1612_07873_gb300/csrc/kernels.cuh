@@ -1,0 +1,83 @@
+// Host-side launchers of the library's kernels (one translation unit per
+// group: blas.cu, wilson.cu, coarse.cu, transfer.cu, galerkin.cu).
+#pragma once
+
+#include "context.cuh"
+
+namespace gbmg {
+
+// A device vector of n complex numbers in precision prec (F64 or F32).
+struct Vec {
+  void* p = nullptr;
+  mg_prec prec = MG_F64;
+  size_t n = 0;
+};
+
+// ---------------------------------------------------------------- blas.cu
+// Device scalars live in ctx->scalars as complex doubles, indexed by slot.
+void blas_zero(mg_ctx* c, Vec v, cudaStream_t st);
+void blas_copy(mg_ctx* c, Vec dst, Vec src, cudaStream_t st);        // converts precision
+void blas_axpy_host(mg_ctx* c, Vec y, Vec x, double are, double aim, cudaStream_t st);
+// y += sign * S[slot] * x
+void blas_axpy_slot(mg_ctx* c, Vec y, Vec x, int slot, double sign, cudaStream_t st);
+// out = b - ax
+void blas_sub(mg_ctx* c, Vec out, Vec b, Vec ax, cudaStream_t st);
+// S[slot] = <a, b> = sum conj(a) b ; S[slot].re = |a|^2
+void blas_dot(mg_ctx* c, Vec a, Vec b, int slot, cudaStream_t st);
+void blas_norm2(mg_ctx* c, Vec a, int slot, cudaStream_t st);
+// S[s_pr] = <p, r>, S[s_pp] = <p, p> in one pass
+void blas_dot2(mg_ctx* c, Vec p, Vec r, int s_pr, int s_pp, cudaStream_t st);
+// MR step: a = omega S[s_pr]/S[s_pp].re ; x += a r ; r -= a p
+void blas_mr_update(mg_ctx* c, Vec x, Vec r, Vec p, int s_pr, int s_pp, double omega,
+                    cudaStream_t st);
+// a *= 1/sqrt(S[slot].re), b likewise
+void blas_scale_invnorm(mg_ctx* c, Vec a, Vec b, int slot, cudaStream_t st);
+// x += S[slot] z ; r -= S[slot] w
+void blas_gcr_update(mg_ctx* c, Vec x, Vec r, Vec z, Vec w, int slot, cudaStream_t st);
+// setup sweep update: x -= (S[s_qt] / S[s_qq].re) t
+void blas_sweep_update(mg_ctx* c, Vec x, Vec t, int s_qt, int s_qq, cudaStream_t st);
+// copy slot values to the host (synchronises st)
+void blas_read_scalars(mg_ctx* c, int first, int count, double* out_re_im, cudaStream_t st);
+// complex Gaussian (Re, Im iid N(0,1)) from a counter-based Philox4x32-10
+void blas_gaussian(mg_ctx* c, Vec v, uint64_t seed, uint64_t offset, cudaStream_t st);
+// x /= sqrt(S[slot].re)
+void blas_normalise(mg_ctx* c, Vec x, int slot, cudaStream_t st);
+// a device status word check (host reads it; synchronises)
+int read_status(mg_ctx* c, cudaStream_t st);
+void clear_status(mg_ctx* c, cudaStream_t st);
+
+// ---------------------------------------------------------------- wilson.cu
+// Build the fine operator of level 0 from the external gauge field.
+void fine_operator_build(mg_ctx* c, const void* gauge_ext, cudaStream_t st);
+// out = M in on `nvec` vectors (stride vstride complex elements apart)
+void wilson_apply(mg_ctx* c, Vec out, Vec in, int nvec, cudaStream_t st);
+
+// ---------------------------------------------------------------- coarse.cu
+void coarse_apply(mg_ctx* c, int level, void* y, const void* x, int nrhs, cudaStream_t st);
+void links_import(mg_ctx* c, int level, const void* ext, cudaStream_t st);
+void links_export(mg_ctx* c, int level, void* ext, cudaStream_t st);
+void links_pack16(mg_ctx* c, int level, cudaStream_t st);
+
+// ---------------------------------------------------------------- transfer.cu
+void block_orthonormalise(mg_ctx* c, int level, cudaStream_t st);
+void restrict_apply(mg_ctx* c, int level, Vec coarse, Vec fine, cudaStream_t st);
+void prolong_apply(mg_ctx* c, int level, Vec fine, Vec coarse, cudaStream_t st);
+
+// ---------------------------------------------------------------- galerkin.cu
+void galerkin_build(mg_ctx* c, int level, cudaStream_t st);
+
+// ---------------------------------------------------------------- solver.cu
+void level_apply(mg_ctx* c, int level, Vec out, Vec in, cudaStream_t st);
+void setup_sweeps(mg_ctx* c, int level, const void* init, cudaStream_t st);
+void gcr_solve(mg_ctx* c, void* x, const void* b, double tol, int maxiter, mg_solve_stats* stats,
+               cudaStream_t st);
+
+inline Vec level_vec(const Level& L, void* p) {
+  Vec v;
+  v.p = p;
+  v.prec = L.vprec;
+  v.n = L.vec_elems();
+  return v;
+}
+
+}  // namespace gbmg

@@ -1,0 +1,315 @@
+// Adaptive setup iteration (Sec. II-D step 1) and the K-cycle multigrid
+// solver of Sec. VI-A: flexible GCR(nkrylov) on the fine and intermediate
+// levels, preconditioned by the next level; MR pre/post smoothing; GCR on
+// the coarsest level.
+//
+// Precision: the outer GCR keeps x and r in FP64 and recomputes the true
+// residual b - M x with the FP64 fine operator at every restart; its Krylov
+// vectors, the K-cycle and all coarse levels run in each level's vector
+// precision.  Inner products accumulate in FP64.  Scalars (MR and GCR
+// coefficients) stay on the device; the host reads one residual norm per
+// GCR step to decide convergence.
+#include <chrono>
+#include <cmath>
+
+#include "kernels.cuh"
+
+struct mg_ctx::SolverWS {
+  struct LevelWS {
+    std::vector<std::unique_ptr<gbmg::DevBuf>> Z, W;
+    gbmg::DevBuf r, x, rhs, tmp, kres, mrx, mrr, mrp;
+    gbmg::DevBuf r64, tmp64;  // level 0 only
+  };
+  LevelWS lv[MG_MAX_LEVELS];
+  int nk = 0;
+};
+
+mg_ctx::mg_ctx() = default;
+
+mg_ctx::~mg_ctx() {
+  ws.reset();
+  if (h_scalars) cudaFreeHost(h_scalars);
+}
+
+namespace gbmg {
+
+namespace {
+
+// scalar slots per level
+inline int slot(int level, int k) { return level * 8 + k; }
+enum { S_BETA = 0, S_NRM = 1, S_ALPHA = 2, S_R = 3, S_PR = 4, S_PP = 5 };
+
+Vec vbuf(DevBuf& b, mg_prec p, size_t n) {
+  Vec v;
+  v.p = b.p;
+  v.prec = p;
+  v.n = n;
+  return v;
+}
+
+void ensure(DevBuf& b, size_t bytes) {
+  if (b.bytes != bytes) b.alloc(bytes);
+}
+
+void ensure_ws(mg_ctx* c) {
+  if (!c->ws) c->ws.reset(new mg_ctx::SolverWS());
+  auto& ws = *c->ws;
+  const int nk = c->p.gcr_nkrylov;
+  for (int l = 0; l < c->nlevels; ++l) {
+    Level& L = c->L[l];
+    auto& w = ws.lv[l];
+    const size_t vb = L.vec_bytes();
+    if (int(w.Z.size()) != nk) {
+      w.Z.clear();
+      w.W.clear();
+      for (int k = 0; k < nk; ++k) {
+        w.Z.emplace_back(new DevBuf());
+        w.W.emplace_back(new DevBuf());
+      }
+    }
+    for (int k = 0; k < nk; ++k) {
+      ensure(*w.Z[k], vb);
+      ensure(*w.W[k], vb);
+    }
+    ensure(w.r, vb);
+    ensure(w.x, vb);
+    ensure(w.rhs, vb);
+    ensure(w.tmp, vb);
+    ensure(w.kres, vb);
+    ensure(w.mrx, vb);
+    ensure(w.mrr, vb);
+    ensure(w.mrp, vb);
+    if (l == 0) {
+      ensure(w.r64, L.vec_elems() * 16);
+      ensure(w.tmp64, L.vec_elems() * 16);
+    }
+  }
+  ws.nk = nk;
+}
+
+double read_norm2(mg_ctx* c, int s, cudaStream_t st) {
+  double v[2];
+  blas_read_scalars(c, s, 1, v, st);
+  return v[0];
+}
+
+// x = MR_k(b) from a zero guess
+void mr_smooth(mg_ctx* c, int l, Vec x, Vec b, cudaStream_t st) {
+  auto& w = c->ws->lv[l];
+  Level& L = c->L[l];
+  Vec r = vbuf(w.mrr, L.vprec, L.vec_elems());
+  Vec p = vbuf(w.mrp, L.vprec, L.vec_elems());
+  blas_zero(c, x, st);
+  blas_copy(c, r, b, st);
+  for (int k = 0; k < c->p.mr_iters; ++k) {
+    level_apply(c, l, p, r, st);
+    blas_dot2(c, p, r, slot(l, S_PR), slot(l, S_PP), st);
+    blas_mr_update(c, x, r, p, slot(l, S_PR), slot(l, S_PP), c->p.mr_omega, st);
+  }
+}
+
+struct GcrOut {
+  int iters = 0;
+  int restarts = 0;
+  double rel = 0.0;
+  bool converged = false;
+};
+
+void kcycle(mg_ctx* c, int l, Vec z, Vec r, cudaStream_t st, mg_solve_stats* stats);
+
+// Flexible GCR at level l.  x, b: level-0 -> FP64; inner levels -> vprec.
+GcrOut gcr(mg_ctx* c, int l, Vec x, Vec b, bool precond, double tol, int maxiter,
+           cudaStream_t st, mg_solve_stats* stats, bool record) {
+  auto& w = c->ws->lv[l];
+  Level& L = c->L[l];
+  const size_t n = L.vec_elems();
+  const bool outer = (l == 0);
+  Vec r = outer ? vbuf(w.r64, MG_F64, n) : vbuf(w.r, L.vprec, n);
+  Vec rK = vbuf(w.r, L.vprec, n);  // residual in level precision (outer level)
+  Vec tmp = outer ? vbuf(w.tmp64, MG_F64, n) : vbuf(w.tmp, L.vprec, n);
+  GcrOut out;
+  blas_norm2(c, b, slot(l, S_R), st);
+  const double b2 = read_norm2(c, slot(l, S_R), st);
+  blas_zero(c, x, st);
+  if (!(b2 > 0.0)) {
+    GB_REQUIRE(std::isfinite(b2), MG_ERR_NUMERICAL, "gcr: non-finite right-hand side");
+    out.converged = true;
+    return out;
+  }
+  blas_copy(c, r, b, st);
+  const double tol2 = tol * tol * b2;
+  const int nk = c->ws->nk;
+  while (true) {
+    double r2 = 0.0;
+    for (int k = 0; k < nk; ++k) {
+      Vec Zk = vbuf(*w.Z[k], L.vprec, n), Wk = vbuf(*w.W[k], L.vprec, n);
+      if (precond) {
+        if (outer && r.prec != L.vprec) {
+          blas_copy(c, rK, r, st);
+          kcycle(c, l, Zk, rK, st, stats);
+        } else {
+          kcycle(c, l, Zk, r, st, stats);
+        }
+      } else {
+        blas_copy(c, Zk, r, st);
+      }
+      level_apply(c, l, Wk, Zk, st);
+      for (int j = 0; j < k; ++j) {
+        Vec Zj = vbuf(*w.Z[j], L.vprec, n), Wj = vbuf(*w.W[j], L.vprec, n);
+        blas_dot(c, Wj, Wk, slot(l, S_BETA), st);
+        blas_axpy_slot(c, Wk, Wj, slot(l, S_BETA), -1.0, st);
+        blas_axpy_slot(c, Zk, Zj, slot(l, S_BETA), -1.0, st);
+      }
+      blas_norm2(c, Wk, slot(l, S_NRM), st);
+      blas_scale_invnorm(c, Wk, Zk, slot(l, S_NRM), st);
+      blas_dot(c, Wk, r, slot(l, S_ALPHA), st);
+      blas_gcr_update(c, x, r, Zk, Wk, slot(l, S_ALPHA), st);
+      blas_norm2(c, r, slot(l, S_R), st);
+      r2 = read_norm2(c, slot(l, S_R), st);
+      GB_REQUIRE(std::isfinite(r2), MG_ERR_NUMERICAL, "gcr: non-finite residual");
+      out.iters++;
+      if (record && stats && stats->history_len < 512)
+        stats->history[stats->history_len++] = std::sqrt(r2 / b2);
+      if (r2 <= tol2 || out.iters >= maxiter) break;
+    }
+    if (out.iters >= maxiter) {
+      out.rel = std::sqrt(r2 / b2);
+      out.converged = r2 <= tol2;
+      break;
+    }
+    // restart: true residual
+    level_apply(c, l, tmp, x, st);
+    blas_sub(c, r, b, tmp, st);
+    out.restarts++;
+    blas_norm2(c, r, slot(l, S_R), st);
+    r2 = read_norm2(c, slot(l, S_R), st);
+    GB_REQUIRE(std::isfinite(r2), MG_ERR_NUMERICAL, "gcr: non-finite true residual");
+    if (r2 <= tol2) {
+      out.rel = std::sqrt(r2 / b2);
+      out.converged = true;
+      break;
+    }
+  }
+  if (stats) stats->level_iters[l] += out.iters;
+  return out;
+}
+
+void kcycle(mg_ctx* c, int l, Vec z, Vec r, cudaStream_t st, mg_solve_stats* stats) {
+  auto& w = c->ws->lv[l];
+  Level& L = c->L[l];
+  const size_t n = L.vec_elems();
+  Vec tmp = vbuf(w.tmp, L.vprec, n), kres = vbuf(w.kres, L.vprec, n);
+  Vec mrx = vbuf(w.mrx, L.vprec, n);
+  const int nl = l + 1;
+  Level& C = c->L[nl];
+  auto& wc = c->ws->lv[nl];
+  Vec rc = vbuf(wc.rhs, C.vprec, C.vec_elems()), ec = vbuf(wc.x, C.vprec, C.vec_elems());
+  // pre-smooth
+  mr_smooth(c, l, z, r, st);
+  level_apply(c, l, tmp, z, st);
+  blas_sub(c, kres, r, tmp, st);
+  // coarse-grid correction
+  restrict_apply(c, l, rc, kres, st);
+  if (nl == c->nlevels - 1)
+    gcr(c, nl, ec, rc, false, c->p.coarse_tol, c->p.coarse_maxiter, st, stats, false);
+  else
+    gcr(c, nl, ec, rc, true, c->p.inner_tol, c->p.inner_maxiter, st, stats, false);
+  prolong_apply(c, l, tmp, ec, st);
+  blas_axpy_host(c, z, tmp, 1.0, 0.0, st);
+  // post-smooth
+  level_apply(c, l, tmp, z, st);
+  blas_sub(c, kres, r, tmp, st);
+  mr_smooth(c, l, mrx, kres, st);
+  blas_axpy_host(c, z, mrx, 1.0, 0.0, st);
+}
+
+}  // namespace
+
+void level_apply(mg_ctx* c, int level, Vec out, Vec in, cudaStream_t st) {
+  if (level == 0)
+    wilson_apply(c, out, in, 1, st);
+  else
+    coarse_apply(c, level, out.p, in.p, 1, st);
+}
+
+void setup_sweeps(mg_ctx* c, int l, const void* init, cudaStream_t st) {
+  Level& L = c->L[l];
+  const int nv = L.nvec;
+  const size_t n = L.vec_elems();
+  L.raw.alloc(size_t(nv) * n * 16);
+  DevBuf xb, tb, qb;
+  xb.alloc(n * prec_bytes_complex(L.vprec));
+  tb.alloc(n * prec_bytes_complex(L.vprec));
+  qb.alloc(n * prec_bytes_complex(L.vprec));
+  Vec x = vbuf(xb, L.vprec, n), t = vbuf(tb, L.vprec, n), q = vbuf(qb, L.vprec, n);
+  const int s_qt = slot(l, S_PR), s_qq = slot(l, S_PP), s_n = slot(l, S_NRM);
+  for (int i = 0; i < nv; ++i) {
+    Vec out;
+    out.p = L.raw.as<double2>() + size_t(i) * n;
+    out.prec = MG_F64;
+    out.n = n;
+    if (init) {
+      Vec in;
+      in.p = (void*)((const double2*)init + size_t(i) * n);
+      in.prec = MG_F64;
+      in.n = n;
+      blas_copy(c, x, in, st);
+    } else {
+      blas_gaussian(c, x, c->p.seed + 0x9E3779B97F4A7C15ull * uint64_t(l + 1),
+                    uint64_t(i) * n, st);
+    }
+    // minimal-residual steps on A x = 0:  t = A x, q = A t,
+    // x <- x - (<q, t> / <q, q>) t
+    for (int k = 0; k < c->p.setup_sweeps; ++k) {
+      level_apply(c, l, t, x, st);
+      level_apply(c, l, q, t, st);
+      blas_dot2(c, q, t, s_qt, s_qq, st);
+      blas_sweep_update(c, x, t, s_qt, s_qq, st);
+    }
+    blas_norm2(c, x, s_n, st);
+    blas_normalise(c, x, s_n, st);
+    blas_copy(c, out, x, st);
+  }
+  L.have_raw = true;
+  L.have_V = false;
+  GB_CHECK(cudaStreamSynchronize(st));
+}
+
+void gcr_solve(mg_ctx* c, void* xp, const void* bp, double tol, int maxiter,
+               mg_solve_stats* stats, cudaStream_t st) {
+  for (int l = 0; l + 1 < c->nlevels; ++l) {
+    GB_REQUIRE(c->L[l].have_V, MG_ERR_STATE, "solve: null vectors of a level missing");
+    GB_REQUIRE(c->L[l + 1].have_op, MG_ERR_STATE, "solve: coarse operator missing");
+  }
+  ensure_ws(c);
+  auto t0 = std::chrono::steady_clock::now();
+  mg_solve_stats local{};
+  mg_solve_stats* s = stats ? stats : &local;
+  *s = mg_solve_stats{};
+  Level& L = c->L[0];
+  const size_t n = L.vec_elems();
+  Vec x, b;
+  x.p = xp;
+  x.prec = MG_F64;
+  x.n = n;
+  b.p = const_cast<void*>(bp);
+  b.prec = MG_F64;
+  b.n = n;
+  GcrOut o = gcr(c, 0, x, b, true, tol, maxiter, st, s, true);
+  // true residual of the returned x, in FP64
+  auto& w = c->ws->lv[0];
+  Vec tmp = vbuf(w.tmp64, MG_F64, n), r = vbuf(w.r64, MG_F64, n);
+  level_apply(c, 0, tmp, x, st);
+  blas_sub(c, r, b, tmp, st);
+  blas_norm2(c, r, slot(0, S_R), st);
+  double r2 = read_norm2(c, slot(0, S_R), st);
+  blas_norm2(c, b, slot(0, S_R), st);
+  double b2 = read_norm2(c, slot(0, S_R), st);
+  s->iters = o.iters;
+  s->restarts = o.restarts;
+  s->true_residual = b2 > 0 ? std::sqrt(r2 / b2) : 0.0;
+  s->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (!o.converged) throw Error(MG_ERR_NOT_CONVERGED, "gcr: maxiter reached before tolerance");
+}
+
+}  // namespace gbmg

@@ -1,0 +1,351 @@
+// Null-vector block orthonormalisation (Sec. II-D step 3 with the chiral
+// split of its footnote) and the transfer operators of Sec. IV-F.
+//
+// For aggregate A and chirality s the (|A| * nd/2) x Nv block of chirality-s
+// components is orthonormalised by modified Gram-Schmidt with every
+// projection done twice, in FP64.  Rows are ordered (site of A in
+// lexicographic order, dof of chirality s).  The prolongator column (s, i)
+// is vector i of the result restricted to chirality s; coarse dof = s*Nv + i.
+//
+// Transfer layout Vp: [fine site][dof][Nv] in the level's vector precision,
+// so the Nv coefficients of one fine dof are contiguous.
+#include "kernels.cuh"
+
+namespace gbmg {
+
+namespace {
+
+struct AggMap {
+  Geom fine, coarse;
+  int b[4];
+  int per;  // fine sites per aggregate
+};
+
+__host__ __device__ __forceinline__ int agg_of(const AggMap& m, const int c[4]) {
+  return (c[0] / m.b[0]) + m.coarse.stride[1] * (c[1] / m.b[1]) +
+         m.coarse.stride[2] * (c[2] / m.b[2]) + m.coarse.stride[3] * (c[3] / m.b[3]);
+}
+__host__ __device__ __forceinline__ int local_of(const AggMap& m, const int c[4]) {
+  int l0 = c[0] % m.b[0], l1 = c[1] % m.b[1], l2 = c[2] % m.b[2], l3 = c[3] % m.b[3];
+  return l0 + m.b[0] * (l1 + m.b[1] * (l2 + m.b[2] * l3));
+}
+// fine site of local index ls inside aggregate xc
+__host__ __device__ __forceinline__ int fine_of(const AggMap& m, int xc, int ls) {
+  int cc[4], c[4];
+  site_coords(m.coarse, xc, cc);
+  c[0] = cc[0] * m.b[0] + ls % m.b[0];
+  ls /= m.b[0];
+  c[1] = cc[1] * m.b[1] + ls % m.b[1];
+  ls /= m.b[1];
+  c[2] = cc[2] * m.b[2] + ls % m.b[2];
+  c[3] = cc[3] * m.b[3] + ls / m.b[2];
+  return c[0] + m.fine.stride[1] * c[1] + m.fine.stride[2] * c[2] + m.fine.stride[3] * c[3];
+}
+
+AggMap make_map(const Level& f, const Level& c) {
+  AggMap m;
+  m.fine = f.g;
+  m.coarse = c.g;
+  for (int i = 0; i < 4; ++i) m.b[i] = f.block[i];
+  m.per = f.g.vol / c.g.vol;
+  return m;
+}
+
+// raw [Nv][V][nd] -> W [agg][chi][Nv][rows]
+__global__ void k_mgs_gather(double2* __restrict__ W, const double2* __restrict__ raw, AggMap m,
+                             int nd, int nv) {
+  const int half = nd / 2;
+  const int rows = m.per * half;
+  size_t total = size_t(nv) * m.fine.vol * nd;
+  for (size_t idx = blockIdx.x * size_t(blockDim.x) + threadIdx.x; idx < total;
+       idx += size_t(gridDim.x) * blockDim.x) {
+    int a = int(idx % nd);
+    size_t t = idx / nd;
+    int s = int(t % m.fine.vol);
+    int i = int(t / m.fine.vol);
+    int c[4];
+    site_coords(m.fine, s, c);
+    int ag = agg_of(m, c), ls = local_of(m, c);
+    int chi = a / half, ad = a - chi * half;
+    W[((size_t(ag) * 2 + chi) * nv + i) * rows + size_t(ls) * half + ad] = raw[idx];
+  }
+}
+
+__device__ __forceinline__ double2 blk_sum2(double2 v, double2* sh) {
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double2 r = make_double2(0.0, 0.0);
+  for (int k = 0; k < nw; ++k) {
+    r.x += sh[k].x;
+    r.y += sh[k].y;
+  }
+  return r;
+}
+
+// One CTA per (aggregate, chirality) block of `rows` x nv, in place.
+template <int RPT>
+__global__ void k_mgs(double2* __restrict__ W, int rows, int nv, int* status) {
+  __shared__ double2 sh[32];
+  double2* B = W + size_t(blockIdx.x) * nv * rows;
+  const int T = blockDim.x;
+  // Frobenius norm of the block for the rank test
+  double2 f = make_double2(0.0, 0.0);
+  for (size_t k = threadIdx.x; k < size_t(nv) * rows; k += T) {
+    double2 v = B[k];
+    f.x += v.x * v.x + v.y * v.y;
+  }
+  const double scale = sqrt(blk_sum2(f, sh).x);
+  for (int i = 0; i < nv; ++i) {
+    double2 v[RPT];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      int row = threadIdx.x + r * T;
+      v[r] = row < rows ? B[size_t(i) * rows + row] : make_double2(0.0, 0.0);
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int j = 0; j < i; ++j) {
+        const double2* q = B + size_t(j) * rows;
+        double2 d = make_double2(0.0, 0.0);
+        double2 qv[RPT];
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+          int row = threadIdx.x + r * T;
+          qv[r] = row < rows ? q[row] : make_double2(0.0, 0.0);
+          d.x += qv[r].x * v[r].x + qv[r].y * v[r].y;
+          d.y += qv[r].x * v[r].y - qv[r].y * v[r].x;
+        }
+        d = blk_sum2(d, sh);
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+          v[r].x -= d.x * qv[r].x - d.y * qv[r].y;
+          v[r].y -= d.x * qv[r].y + d.y * qv[r].x;
+        }
+      }
+    }
+    double2 nn = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) nn.x += v[r].x * v[r].x + v[r].y * v[r].y;
+    double nrm = sqrt(blk_sum2(nn, sh).x);
+    double inv = 0.0;
+    if (nrm <= 1e-12 * scale) {
+      if (threadIdx.x == 0) atomicOr(status, 1);
+    } else {
+      inv = 1.0 / nrm;
+    }
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      int row = threadIdx.x + r * T;
+      if (row < rows) B[size_t(i) * rows + row] = make_double2(v[r].x * inv, v[r].y * inv);
+    }
+    __syncthreads();
+  }
+}
+
+// W -> orth64 [Nv][V][nd] (FP64) and Vp [V][nd][Nv] (R)
+template <typename R>
+__global__ void k_mgs_scatter(double2* __restrict__ orth, cpx<R>* __restrict__ Vp,
+                              const double2* __restrict__ W, AggMap m, int nd, int nv) {
+  const int half = nd / 2;
+  const int rows = m.per * half;
+  size_t total = size_t(nv) * m.fine.vol * nd;
+  for (size_t idx = blockIdx.x * size_t(blockDim.x) + threadIdx.x; idx < total;
+       idx += size_t(gridDim.x) * blockDim.x) {
+    // idx enumerates Vp order: (site, dof, vec)
+    int i = int(idx % nv);
+    size_t t = idx / nv;
+    int a = int(t % nd);
+    int s = int(t / nd);
+    int c[4];
+    site_coords(m.fine, s, c);
+    int ag = agg_of(m, c), ls = local_of(m, c);
+    int chi = a / half, ad = a - chi * half;
+    double2 v = W[((size_t(ag) * 2 + chi) * nv + i) * rows + size_t(ls) * half + ad];
+    Vp[idx] = cpx<R>(R(v.x), R(v.y));
+    orth[(size_t(i) * m.fine.vol + s) * nd + a] = v;
+  }
+}
+
+// coarse[xc][chi*Nv + i] = sum_{x in A(xc), a in chi} conj(Vp[x][a][i]) fine[x][a]
+template <typename Rf, typename Rc>
+__global__ void k_restrict(cpx<Rc>* __restrict__ coarse, const cpx<Rf>* __restrict__ fine,
+                           const cpx<Rf>* __restrict__ Vp, AggMap m, int nd, int nv) {
+  extern __shared__ unsigned char smem_raw[];
+  cpx<Rf>* red = reinterpret_cast<cpx<Rf>*>(smem_raw);  // [G][2][nv]
+  const int xc = blockIdx.x;
+  const int G = blockDim.x / nv;
+  const int i = threadIdx.x % nv, g = threadIdx.x / nv;
+  const int half = nd / 2;
+  cpx<Rf> acc0(Rf(0), Rf(0)), acc1(Rf(0), Rf(0));
+  if (g < G) {
+    const int rows = m.per * nd;
+    for (int q = g; q < rows; q += G) {
+      int ls = q / nd, a = q - ls * nd;
+      int x = fine_of(m, xc, ls);
+      cpx<Rf> f = fine[size_t(x) * nd + a];
+      cpx<Rf> v = Vp[(size_t(x) * nd + a) * nv + i];
+      if (a < half)
+        cmac_conj(acc0, v, f);
+      else
+        cmac_conj(acc1, v, f);
+    }
+    red[(g * 2 + 0) * nv + i] = acc0;
+    red[(g * 2 + 1) * nv + i] = acc1;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < 2 * nv; t += blockDim.x) {
+    int chi = t / nv, ii = t - chi * nv;
+    cpx<Rf> s(Rf(0), Rf(0));
+    for (int k = 0; k < G; ++k) s += red[(k * 2 + chi) * nv + ii];
+    coarse[size_t(xc) * 2 * nv + t] = cpx<Rc>(s);
+  }
+}
+
+// fine[x][a] = sum_i Vp[x][a][i] coarse[agg(x)][chi(a)*Nv + i]
+template <typename Rf, typename Rc>
+__global__ void k_prolong(cpx<Rf>* __restrict__ fine, const cpx<Rc>* __restrict__ coarse,
+                          const cpx<Rf>* __restrict__ Vp, AggMap m, int nd, int nv) {
+  size_t total = size_t(m.fine.vol) * nd;
+  const int half = nd / 2;
+  for (size_t idx = blockIdx.x * size_t(blockDim.x) + threadIdx.x; idx < total;
+       idx += size_t(gridDim.x) * blockDim.x) {
+    int a = int(idx % nd);
+    int s = int(idx / nd);
+    int c[4];
+    site_coords(m.fine, s, c);
+    int ag = agg_of(m, c);
+    const cpx<Rc>* ec = coarse + size_t(ag) * 2 * nv + (a / half) * nv;
+    const cpx<Rf>* v = Vp + idx * nv;
+    cpx<Rf> acc(Rf(0), Rf(0));
+    for (int i = 0; i < nv; ++i) cmac(acc, v[i], cpx<Rf>(ec[i]));
+    fine[idx] = acc;
+  }
+}
+
+int grid_for(size_t n) {
+  long long b = (long long)((n + 255) / 256);
+  if (b > 152 * 32) b = 152 * 32;
+  return int(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+void block_orthonormalise(mg_ctx* c, int level, cudaStream_t st) {
+  Level& F = c->L[level];
+  Level& C = c->L[level + 1];
+  GB_REQUIRE(F.have_raw, MG_ERR_STATE, "block_orthonormalise: no null vectors");
+  const int nd = F.nd, nv = F.nvec;
+  AggMap m = make_map(F, C);
+  const int rows = m.per * nd / 2;
+  const size_t elems = size_t(nv) * F.g.vol * nd;
+  DevBuf W;
+  W.alloc(elems * sizeof(double2));
+  F.orth64.alloc(elems * sizeof(double2));
+  F.Vp.alloc(elems * prec_bytes_complex(F.vprec));
+  clear_status(c, st);
+  k_mgs_gather<<<grid_for(elems), 256, 0, st>>>(W.as<double2>(), F.raw.as<double2>(), m, nd, nv);
+  GB_LAUNCH_CHECK();
+  int threads = rows <= 256 * 16 ? 256 : 1024;
+  int rpt = (rows + threads - 1) / threads;
+  GB_REQUIRE(rpt <= 24, MG_ERR_ARG, "aggregate block too large (rows > 24576)");
+  const int nblk = C.g.vol * 2;
+  ProfScope ps(c->prof, st, "block_orth", level, double(elems) * 16.0 * 2,
+               8.0 * nv * (nv - 1) * 2.0 * rows * nblk);
+  if (rpt <= 1)
+    k_mgs<1><<<nblk, threads, 0, st>>>(W.as<double2>(), rows, nv, c->status.as<int>());
+  else if (rpt <= 2)
+    k_mgs<2><<<nblk, threads, 0, st>>>(W.as<double2>(), rows, nv, c->status.as<int>());
+  else if (rpt <= 4)
+    k_mgs<4><<<nblk, threads, 0, st>>>(W.as<double2>(), rows, nv, c->status.as<int>());
+  else if (rpt <= 8)
+    k_mgs<8><<<nblk, threads, 0, st>>>(W.as<double2>(), rows, nv, c->status.as<int>());
+  else if (rpt <= 16)
+    k_mgs<16><<<nblk, threads, 0, st>>>(W.as<double2>(), rows, nv, c->status.as<int>());
+  else
+    k_mgs<24><<<nblk, threads, 0, st>>>(W.as<double2>(), rows, nv, c->status.as<int>());
+  GB_LAUNCH_CHECK();
+  if (F.vprec == MG_F64)
+    k_mgs_scatter<double><<<grid_for(elems), 256, 0, st>>>(
+        F.orth64.as<double2>(), F.Vp.as<cpx<double>>(), W.as<double2>(), m, nd, nv);
+  else
+    k_mgs_scatter<float><<<grid_for(elems), 256, 0, st>>>(
+        F.orth64.as<double2>(), F.Vp.as<cpx<float>>(), W.as<double2>(), m, nd, nv);
+  GB_LAUNCH_CHECK();
+  c->launches += 3;
+  if (read_status(c, st) & 1) {
+    F.have_V = false;
+    throw Error(MG_ERR_RANK, "rank-deficient null-vector aggregate block");
+  }
+  F.have_V = true;
+}
+
+void restrict_apply(mg_ctx* c, int level, Vec coarse, Vec fine, cudaStream_t st) {
+  Level& F = c->L[level];
+  Level& C = c->L[level + 1];
+  GB_REQUIRE(F.have_V, MG_ERR_STATE, "restrict: null vectors not set");
+  GB_REQUIRE(fine.prec == F.vprec, MG_ERR_ARG, "restrict: fine vector precision");
+  AggMap m = make_map(F, C);
+  const int nv = F.nvec;
+  int G = 256 / nv;
+  if (G < 1) G = 1;
+  const int threads = G * nv;
+  const size_t smem = size_t(G) * 2 * nv * prec_bytes_complex(F.vprec);
+  const double vb = prec_bytes_complex(F.vprec);
+  ProfScope ps(c->prof, st, "restrict", level,
+               double(F.g.vol) * F.nd * (nv + 1) * vb + double(C.g.vol) * C.nd * vb,
+               8.0 * F.g.vol * F.nd * nv);
+  if (F.vprec == MG_F64) {
+    if (coarse.prec == MG_F64)
+      k_restrict<double, double><<<C.g.vol, threads, smem, st>>>(
+          (cpx<double>*)coarse.p, (const cpx<double>*)fine.p, F.Vp.as<cpx<double>>(), m, F.nd, nv);
+    else
+      k_restrict<double, float><<<C.g.vol, threads, smem, st>>>(
+          (cpx<float>*)coarse.p, (const cpx<double>*)fine.p, F.Vp.as<cpx<double>>(), m, F.nd, nv);
+  } else {
+    if (coarse.prec == MG_F64)
+      k_restrict<float, double><<<C.g.vol, threads, smem, st>>>(
+          (cpx<double>*)coarse.p, (const cpx<float>*)fine.p, F.Vp.as<cpx<float>>(), m, F.nd, nv);
+    else
+      k_restrict<float, float><<<C.g.vol, threads, smem, st>>>(
+          (cpx<float>*)coarse.p, (const cpx<float>*)fine.p, F.Vp.as<cpx<float>>(), m, F.nd, nv);
+  }
+  GB_LAUNCH_CHECK();
+  c->launches++;
+}
+
+void prolong_apply(mg_ctx* c, int level, Vec fine, Vec coarse, cudaStream_t st) {
+  Level& F = c->L[level];
+  Level& C = c->L[level + 1];
+  GB_REQUIRE(F.have_V, MG_ERR_STATE, "prolong: null vectors not set");
+  GB_REQUIRE(fine.prec == F.vprec, MG_ERR_ARG, "prolong: fine vector precision");
+  AggMap m = make_map(F, C);
+  const int nv = F.nvec;
+  const size_t n = size_t(F.g.vol) * F.nd;
+  const double vb = prec_bytes_complex(F.vprec);
+  ProfScope ps(c->prof, st, "prolong", level,
+               double(n) * (nv + 1) * vb + double(C.g.vol) * C.nd * vb, 8.0 * n * nv);
+  if (F.vprec == MG_F64) {
+    if (coarse.prec == MG_F64)
+      k_prolong<double, double><<<grid_for(n), 256, 0, st>>>(
+          (cpx<double>*)fine.p, (const cpx<double>*)coarse.p, F.Vp.as<cpx<double>>(), m, F.nd, nv);
+    else
+      k_prolong<double, float><<<grid_for(n), 256, 0, st>>>(
+          (cpx<double>*)fine.p, (const cpx<float>*)coarse.p, F.Vp.as<cpx<double>>(), m, F.nd, nv);
+  } else {
+    if (coarse.prec == MG_F64)
+      k_prolong<float, double><<<grid_for(n), 256, 0, st>>>(
+          (cpx<float>*)fine.p, (const cpx<double>*)coarse.p, F.Vp.as<cpx<float>>(), m, F.nd, nv);
+    else
+      k_prolong<float, float><<<grid_for(n), 256, 0, st>>>(
+          (cpx<float>*)fine.p, (const cpx<float>*)coarse.p, F.Vp.as<cpx<float>>(), m, F.nd, nv);
+  }
+  GB_LAUNCH_CHECK();
+  c->launches++;
+}
+
+}  // namespace gbmg

@@ -1,0 +1,239 @@
+// Fine Wilson-clover operator of Eq. (2): gauge import, clover term A_x
+// and the stencil apply (one thread per site and vector).
+#include "kernels.cuh"
+#include "wilson_ops.cuh"
+
+namespace gbmg {
+
+namespace {
+
+// gauge_int[mu][s] = gauge_ext[mu][s] * (t antiperiodic and mu = t and
+// t(s) = Lt - 1 ? -1 : 1): the fermion boundary sign lives on the link
+// that wraps, so hops need no special case.
+template <typename R>
+__global__ void k_gauge_import(cpx<R>* __restrict__ out, const cpx<double>* __restrict__ in,
+                               Geom g, int antiperiodic) {
+  size_t n = size_t(4) * g.vol * 9;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
+       i += size_t(gridDim.x) * blockDim.x) {
+    size_t link = i / 9;
+    int mu = int(link / g.vol);
+    int s = int(link % g.vol);
+    double sgn = 1.0;
+    if (antiperiodic && mu == 3 && s / g.stride[3] == g.L[3] - 1) sgn = -1.0;
+    out[i] = cpx<R>(sgn * in[i]);
+  }
+}
+
+struct M3 {
+  cpx<double> a[9];
+};
+
+__device__ __forceinline__ M3 mload(const cpx<double>* __restrict__ g, int mu, int s, int vol) {
+  M3 m;
+  const cpx<double>* p = g + (size_t(mu) * vol + s) * 9;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) m.a[i] = p[i];
+  return m;
+}
+__device__ __forceinline__ M3 mmul(const M3& x, const M3& y) {
+  M3 r;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      cpx<double> t(0.0, 0.0);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) cmac(t, x.a[i * 3 + k], y.a[k * 3 + j]);
+      r.a[i * 3 + j] = t;
+    }
+  return r;
+}
+__device__ __forceinline__ M3 mdag(const M3& x) {
+  M3 r;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) r.a[i * 3 + j] = conj(x.a[j * 3 + i]);
+  return r;
+}
+
+__device__ __forceinline__ int shifted(const Geom& g, const int c[4], int mu, int dm, int nu,
+                                       int dn) {
+  int cc[4] = {c[0], c[1], c[2], c[3]};
+  cc[mu] = (cc[mu] + dm + g.L[mu]) % g.L[mu];
+  cc[nu] = (cc[nu] + dn + g.L[nu]) % g.L[nu];
+  return cc[0] + g.stride[1] * cc[1] + g.stride[2] * cc[2] + g.stride[3] * cc[3];
+}
+
+// Fhat_{mu nu}(x) = (Q - Q^dag) / 8, Q the sum of the four plaquette
+// leaves at x, all oriented (+mu, +nu, -mu, -nu).
+__device__ M3 field_strength(const cpx<double>* __restrict__ U, const Geom& g, int s,
+                             const int c[4], int mu, int nu) {
+  const int V = g.vol;
+  int x = s;
+  int xpm = shifted(g, c, mu, 1, nu, 0), xpn = shifted(g, c, mu, 0, nu, 1);
+  int xmm = shifted(g, c, mu, -1, nu, 0), xmn = shifted(g, c, mu, 0, nu, -1);
+  int xmmpn = shifted(g, c, mu, -1, nu, 1), xmmmn = shifted(g, c, mu, -1, nu, -1);
+  int xpmmn = shifted(g, c, mu, 1, nu, -1);
+  M3 q = mmul(mmul(mload(U, mu, x, V), mload(U, nu, xpm, V)),
+              mmul(mdag(mload(U, mu, xpn, V)), mdag(mload(U, nu, x, V))));
+  M3 t = mmul(mmul(mload(U, nu, x, V), mdag(mload(U, mu, xmmpn, V))),
+              mmul(mdag(mload(U, nu, xmm, V)), mload(U, mu, xmm, V)));
+#pragma unroll
+  for (int i = 0; i < 9; ++i) q.a[i] += t.a[i];
+  t = mmul(mmul(mdag(mload(U, mu, xmm, V)), mdag(mload(U, nu, xmmmn, V))),
+           mmul(mload(U, mu, xmmmn, V), mload(U, nu, xmn, V)));
+#pragma unroll
+  for (int i = 0; i < 9; ++i) q.a[i] += t.a[i];
+  t = mmul(mmul(mdag(mload(U, nu, xmn, V)), mload(U, mu, xmn, V)),
+           mmul(mload(U, nu, xpmmn, V), mdag(mload(U, mu, x, V))));
+#pragma unroll
+  for (int i = 0; i < 9; ++i) q.a[i] += t.a[i];
+  M3 f;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) f.a[i * 3 + j] = 0.125 * (q.a[i * 3 + j] - conj(q.a[j * 3 + i]));
+  return f;
+}
+
+// A_x = c_sw (i/4) sum_{mu != nu} sigma_{mu nu} (x) Fhat_{mu nu}
+//     = c_sw (i/2) sum_{mu < nu} sigma_{mu nu} (x) Fhat_{mu nu}.
+// In the chiral basis sigma_{mu nu} = diag(s_up, s_lo) with Pauli blocks
+//   (01): s3, s3   (02): s2, s2   (03): -s1, s1
+//   (12): s1, s1   (13): s2, -s2  (23): -s3, s3
+// so per chirality A = c_sw (i/2) [s1 (x) G1 + s2 (x) G2 + s3 (x) G3].
+__global__ void k_clover(const cpx<double>* __restrict__ U, Geom g, double csw,
+                         double* __restrict__ out64, float* __restrict__ out32) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.vol) return;
+  int c[4];
+  site_coords(g, s, c);
+  M3 F01 = field_strength(U, g, s, c, 0, 1);
+  M3 F02 = field_strength(U, g, s, c, 0, 2);
+  M3 F03 = field_strength(U, g, s, c, 0, 3);
+  M3 F12 = field_strength(U, g, s, c, 1, 2);
+  M3 F13 = field_strength(U, g, s, c, 1, 3);
+  M3 F23 = field_strength(U, g, s, c, 2, 3);
+  const double h = 0.5 * csw;
+#pragma unroll
+  for (int chi = 0; chi < 2; ++chi) {
+    double sg = chi == 0 ? -1.0 : 1.0;
+    cpx<double> blk[6][6];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        int k = a * 3 + b;
+        cpx<double> G1 = F12.a[k] + sg * F03.a[k];
+        cpx<double> G2 = F02.a[k] - sg * F13.a[k];
+        cpx<double> G3 = F01.a[k] + sg * F23.a[k];
+        // (i/2) csw [[G3, G1 - i G2], [G1 + i G2, -G3]]
+        blk[a][b] = h * times_i(G3);
+        blk[a][3 + b] = h * (times_i(G1) + G2);
+        blk[3 + a][b] = h * (times_i(G1) - G2);
+        blk[3 + a][3 + b] = -(h * times_i(G3));
+      }
+    double* o64 = out64 + size_t(s) * 72 + chi * 36;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) o64[i] = blk[i][i].re;
+#pragma unroll
+    for (int i = 1; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j < i; ++j) {
+        int k = i * (i - 1) / 2 + j;
+        o64[6 + 2 * k] = blk[i][j].re;
+        o64[7 + 2 * k] = blk[i][j].im;
+      }
+    if (out32) {
+      float* o32 = out32 + size_t(s) * 72 + chi * 36;
+      for (int i = 0; i < 36; ++i) o32[i] = float(o64[i]);
+    }
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_wilson(cpx<R>* __restrict__ out, const cpx<R>* __restrict__ in,
+                                                const cpx<R>* __restrict__ U, const R* __restrict__ A,
+                                                Geom g, R diag, size_t vstride) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.vol) return;
+  in += blockIdx.y * vstride;
+  out += blockIdx.y * vstride;
+  int c[4];
+  site_coords(g, s, c);
+  cpx<R> psi[12], acc[12];
+#pragma unroll
+  for (int i = 0; i < 12; ++i) {
+    psi[i] = in[size_t(s) * 12 + i];
+    acc[i] = cpx<R>(R(0), R(0));
+  }
+  clover_accum(A + size_t(s) * 72, diag, psi, acc);
+  const size_t V = g.vol;
+#define GB_HOP(MU)                                                                  \
+  {                                                                                 \
+    int sf = neighbour(g, s, c, 1 + 2 * MU);                                        \
+    _Pragma("unroll") for (int i = 0; i < 12; ++i) psi[i] = in[size_t(sf) * 12 + i]; \
+    hop_accum<MU, true>(U + (MU * V + s) * 9, psi, acc);                            \
+    int sb = neighbour(g, s, c, 2 + 2 * MU);                                        \
+    _Pragma("unroll") for (int i = 0; i < 12; ++i) psi[i] = in[size_t(sb) * 12 + i]; \
+    hop_accum<MU, false>(U + (MU * V + sb) * 9, psi, acc);                          \
+  }
+  GB_HOP(0) GB_HOP(1) GB_HOP(2) GB_HOP(3)
+#undef GB_HOP
+#pragma unroll
+  for (int i = 0; i < 12; ++i) out[size_t(s) * 12 + i] = acc[i];
+}
+
+}  // namespace
+
+void fine_operator_build(mg_ctx* c, const void* gauge_ext, cudaStream_t st) {
+  Level& L = c->L[0];
+  const size_t n = size_t(4) * L.g.vol * 9;
+  L.gauge64.alloc(n * sizeof(cpx<double>));
+  k_gauge_import<double><<<ceil_div(n, 256), 256, 0, st>>>(
+      L.gauge64.as<cpx<double>>(), (const cpx<double>*)gauge_ext, L.g, c->p.t_antiperiodic);
+  GB_LAUNCH_CHECK();
+  L.clover64.alloc(size_t(L.g.vol) * 72 * sizeof(double));
+  float* c32 = nullptr;
+  if (L.prec == MG_F32) {
+    L.gauge32.alloc(n * sizeof(cpx<float>));
+    k_gauge_import<float><<<ceil_div(n, 256), 256, 0, st>>>(
+        L.gauge32.as<cpx<float>>(), (const cpx<double>*)gauge_ext, L.g, c->p.t_antiperiodic);
+    GB_LAUNCH_CHECK();
+    L.clover32.alloc(size_t(L.g.vol) * 72 * sizeof(float));
+    c32 = L.clover32.as<float>();
+  }
+  k_clover<<<ceil_div(L.g.vol, 128), 128, 0, st>>>(L.gauge64.as<cpx<double>>(), L.g, c->p.csw,
+                                                    L.clover64.as<double>(), c32);
+  GB_LAUNCH_CHECK();
+  c->launches += L.prec == MG_F32 ? 3 : 2;
+  L.diag = 4.0 + c->p.mass;
+}
+
+void wilson_apply(mg_ctx* c, Vec out, Vec in, int nvec, cudaStream_t st) {
+  Level& L = c->L[0];
+  GB_REQUIRE(out.prec == in.prec, MG_ERR_ARG, "wilson_apply: precision mismatch");
+  GB_REQUIRE(out.p != in.p, MG_ERR_ARG, "wilson_apply: output aliases input");
+  const size_t vs = size_t(L.g.vol) * 12;
+  dim3 grid(ceil_div(L.g.vol, 128), nvec);
+  // algorithmic bytes per site: spinor in + out (2 x 24 reals), four links
+  // (4 x 18 reals: each link serves two sites), clover (72 reals)
+  const double bytes = double(nvec) * L.g.vol * 192.0 * (out.prec == MG_F64 ? 8 : 4);
+  ProfScope ps(c->prof, st, "wilson_clover", 0, bytes, double(nvec) * L.g.vol * 1824.0);
+  if (out.prec == MG_F64) {
+    k_wilson<double><<<grid, 128, 0, st>>>((cpx<double>*)out.p, (const cpx<double>*)in.p,
+                                           L.gauge64.as<cpx<double>>(), L.clover64.as<double>(),
+                                           L.g, L.diag, vs);
+  } else {
+    GB_REQUIRE(L.gauge32.p, MG_ERR_STATE, "FP32 fine operator not built");
+    k_wilson<float><<<grid, 128, 0, st>>>((cpx<float>*)out.p, (const cpx<float>*)in.p,
+                                          L.gauge32.as<cpx<float>>(), L.clover32.as<float>(),
+                                          L.g, float(L.diag), vs);
+  }
+  GB_LAUNCH_CHECK();
+  c->launches++;
+}
+
+}  // namespace gbmg

@@ -1,0 +1,85 @@
+"""Host-side checks of the C ABI: the library builds and loads, exports every
+function include/gbmg.h declares, and the ctypes structures of the binding
+match the C layout (sizes and field offsets measured by a gcc probe)."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gbmg.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mg_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1612_07873_gb300 as gb
+    return C.CDLL(gb.LIB_PATH)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 20
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_function():
+    import paper_1612_07873_gb300 as gb
+    names = declared_functions()
+    missing = [n for n in names if n not in ("mg_default_params", "mg_status_string",
+                                             "mg_last_error") and not hasattr(gb, n)]
+    assert not missing, missing
+
+
+def test_struct_layout_matches_c(tmp_path):
+    import paper_1612_07873_gb300 as gb
+    fields_p = [f for f, _ in gb.mg_params._fields_]
+    fields_s = [f for f, _ in gb.mg_solve_stats._fields_]
+    body = ['#include <stdio.h>', '#include <stddef.h>', '#include "gbmg.h"', "int main(void){",
+            'printf("%zu %zu\\n", sizeof(mg_params), sizeof(mg_solve_stats));']
+    body += [f'printf("%zu\\n", offsetof(mg_params, {f}));' for f in fields_p]
+    body += [f'printf("%zu\\n", offsetof(mg_solve_stats, {f}));' for f in fields_s]
+    body += ["return 0;}"]
+    src = tmp_path / "probe.c"
+    src.write_text("\n".join(body))
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    vals = [int(v) for v in out]
+    assert vals[0] == C.sizeof(gb.mg_params)
+    assert vals[1] == C.sizeof(gb.mg_solve_stats)
+    offs = vals[2:]
+    want = [getattr(gb.mg_params, f).offset for f in fields_p] + \
+           [getattr(gb.mg_solve_stats, f).offset for f in fields_s]
+    assert offs == want
+
+
+def test_default_params_and_status_strings(lib):
+    import paper_1612_07873_gb300 as gb
+    p = gb.default_params(dims=(4, 4, 4, 4), block=[(2, 2, 2, 2)], nvec=[4], mass=-0.1)
+    assert p.gcr_nkrylov == 10 and p.mr_iters == 4 and p.coarse_maxiter == 100
+    assert tuple(p.dims) == (4, 4, 4, 4) and p.nvec[0] == 4
+    for code in range(-8, 1):
+        assert gb.LIB.mg_status_string(code)
+
+
+def test_create_rejects_bad_arguments_without_a_gpu(lib):
+    """Argument errors are reported before any device call."""
+    import paper_1612_07873_gb300 as gb
+    p = gb.default_params(dims=(4, 4, 4, 4), block=[(2, 2, 2, 2)], nvec=[4])
+    h = C.c_void_p()
+    assert gb.LIB.mg_create(C.byref(p), None, C.byref(h)) == gb.MG_ERR_ARG
+    p.nlevels = 9
+    assert gb.LIB.mg_create(C.byref(p), C.c_void_p(16), C.byref(h)) == gb.MG_ERR_ARG
+    assert b"nlevels" in gb.LIB.mg_last_error(None)
