@@ -1,0 +1,384 @@
+"""Benchmark of the adaptive-multigrid hot path on one GB300 (or N replicas).
+
+One step is one pass of the whole hot path on the production-shaped
+3-level workload (fine 32^3x64 Wilson-clover, 4^4 then 2^4 aggregates,
+24 then 32 null vectors, FP32 levels, FP64 outer GCR):
+
+    setup level 0 (MR sweeps on M x = 0, FP64 block Gram-Schmidt)
+    -> Galerkin build of level 1 -> setup level 1 -> Galerkin build of level 2
+    -> K-cycle GCR solve of M x = b to 1e-10.
+
+value = coarse-apply throughput (algorithmic bytes / kernel time) of every
+level-1 coarse apply inside the timed steps, timed by CUDA events that the
+library records on the launching stream.  The level-1 links are 1.36 GB, so
+inputs are larger than the 129 MB L2 and no flush is needed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--form fp32|bf16|fp16]
+    python bench.py --impl reference   # the CPU oracle timed on a bounded sample
+
+Under torchrun with N > 1 every rank runs its own replica (the method's
+lattice is not split across GPUs here: "replicas only"), a barrier brackets
+the timed region and the time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic as syn  # noqa: E402
+
+WORKLOAD = "c2_32^3x64_3lvl_fp32"
+METRIC = "coarse_apply GB/s (% HBM peak); MG-GCR s/solve at 1e-10, plain vs tuned forms"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- oracle leg
+def oracle_coarse_apply_sample(n=48, cdims=(8, 8, 8, 16), sites=1024, budget_s=12.0):
+    """The FP64 oracle stencil apply (Eq. 3) on a bounded sample of the
+    level-1 lattice: `sites` output sites per repetition, repeated for
+    about budget_s seconds.  Returns GB/s of FP64 algorithmic bytes."""
+    from oracle import dirac, lattice as lat
+    try:
+        from threadpoolctl import threadpool_limits
+        limiter = threadpool_limits(1)
+    except Exception:
+        limiter = None
+    vol = lat.volume(cdims)
+    rng = np.random.default_rng(5)
+    sel = np.sort(rng.choice(vol, size=sites, replace=False))
+    blocks = (rng.standard_normal((sites, 9, n, n)) + 1j * rng.standard_normal((sites, 9, n, n)))
+    psi = rng.standard_normal((vol, n)) + 1j * rng.standard_normal((vol, n))
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        dirac.apply_at(blocks, psi, cdims, sel)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    if limiter is not None:
+        limiter.unregister() if hasattr(limiter, "unregister") else None
+    bytes_per = sites * (9 * n * n * 16 + 2 * n * 16)
+    return dict(value=bytes_per * reps / el / 1e9, unit="GB/s", cores=1, kind="oracle",
+                sample=f"FP64 numpy Eq. (3) apply on {sites} of {vol} sites of the {cdims} n={n} "
+                       f"level-1 lattice, {reps} repetitions in {el:.1f} s; GB/s of FP64 "
+                       f"algorithmic bytes (links + in/out spinor)")
+
+
+def reference_main(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    samples = []
+    for _ in range(args.warmup):
+        oracle_coarse_apply_sample(budget_s=2.0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        samples.append(oracle_coarse_apply_sample(budget_s=max(2.0, 20.0 / args.steps)))
+    el = time.perf_counter() - t0
+    v = statistics.median(s["value"] for s in samples)
+    base = dict(samples[-1])
+    base["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "form": "oracle-fp64", "l2": "host"},
+            "cpu_baseline": base,
+            "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU leg
+def gpu_main(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    w = syn.WORKLOADS[WORKLOAD]
+    dims, blocks, nvecs = w["dims"], w["block"], w["nvec"]
+    form = args.form
+    prec_coarse = {"fp32": 1, "bf16": 2, "fp16": 3}[form]
+    t_gen = time.perf_counter()
+    U = syn.gauge_field(dims, w["eps"], w["seed"])
+    vol = syn.volume(dims)
+    b_host = syn.gaussian_field((vol, 12), w["seed"], stream=99)
+    t_gen = time.perf_counter() - t_gen
+
+    import paper_1612_07873_gb300 as gb
+    p = gb.default_params(dims=dims, block=blocks, nvec=nvecs, mass=w["mass"], csw=w["csw"],
+                          nlevels=3, prec_fine=1, prec_coarse=prec_coarse,
+                          setup_sweeps=w["sweeps"], t_antiperiodic=w["antiperiodic"],
+                          seed=w["seed"] + 1000 * rank)
+    mg = gb.Multigrid(p, torch.from_numpy(U).to(dev))
+    del U
+    ctx = mg.ctx
+    b = torch.from_numpy(b_host).to(dev)
+    x = torch.zeros_like(b)
+    stream = torch.cuda.current_stream()
+    l1 = mg.levels[1]
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def step(record):
+        es = [ev() for _ in range(6)]
+        es[0].record(stream)
+        gb.mg_setup_nullvecs(ctx, 0, None)
+        es[1].record(stream)
+        gb.mg_build_coarse(ctx, 0)
+        es[2].record(stream)
+        gb.mg_setup_nullvecs(ctx, 1, None)
+        es[3].record(stream)
+        gb.mg_build_coarse(ctx, 1)
+        es[4].record(stream)
+        st = gb.mg_gcr_solve(ctx, x, b, 1e-10, 500)
+        es[5].record(stream)
+        return es, st
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    gb.mg_profile_reset(ctx)
+    gb.mg_profile_enable(ctx, True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = gb.mg_launch_count(ctx)
+    t_start, t_stop = ev(), ev()
+    t_start.record(stream)
+    phases, stats = [], []
+    for _ in range(args.steps):
+        es, st = step(True)
+        phases.append(es)
+        stats.append(st)
+    t_stop.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = gb.mg_launch_count(ctx) - launches0
+    clk = clocks.stop()
+    gb.mg_profile_enable(ctx, False)
+    ms_total = t_start.elapsed_time(t_stop)
+    ph = np.array([[es[i].elapsed_time(es[i + 1]) for i in range(5)] for es in phases])
+    kern = {k: gb.mg_profile_query(ctx, k, -1) for k in
+            ("coarse_apply", "wilson_clover", "galerkin", "block_orth", "restrict", "prolong")}
+    ca = gb.mg_profile_query(ctx, "coarse_apply", 1)
+    ca_ms = ca["ms"]
+    ca_bytes = ca["bytes"]
+
+    # whole-job aggregation over ranks: bytes summed, time = max over ranks
+    if world > 1:
+        t = torch.tensor([ms_total, ca_ms, ca_bytes], dtype=torch.float64, device=dev)
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = t.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        ms_total, ca_ms, ca_bytes = float(mx[0]), float(mx[1]), float(sm[2])
+    gbs = ca_bytes / (ca_ms * 1e-3) / 1e9 if ca_ms > 0 else 0.0
+    per_launch_bytes = ca["bytes"] / max(ca["launches"], 1)
+    per_launch_ms = ca["ms"] / max(ca["launches"], 1)
+
+    # e2e: the level-1 coarse apply through the C ABI with host buffers
+    n1 = l1["ndof"]
+    xh = torch.randn((l1["volume"], n1), dtype=torch.complex64).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    xd = torch.empty_like(xh, device=dev)
+    yd = torch.empty_like(xd)
+    for _ in range(3):
+        xd.copy_(xh, non_blocking=True)
+        gb.mg_coarse_apply(ctx, 1, yd, xd)
+        yh.copy_(yd, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = ev(), ev()
+    reps = 20
+    e0.record(stream)
+    for _ in range(reps):
+        xd.copy_(xh, non_blocking=True)
+        gb.mg_coarse_apply(ctx, 1, yd, xd)
+        yh.copy_(yd, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / reps
+    e2e = {"value": per_launch_bytes / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
+           "h2d_bytes_per_step": xh.numel() * xh.element_size(),
+           "d2h_bytes_per_step": yh.numel() * yh.element_size(),
+           "ms_per_apply": e2e_ms}
+
+    peak, peak_kind = peaks()
+    solve_s = [s["seconds"] for s in stats]
+    line = {
+        "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if form == "fp32" else form,
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "fine": list(dims), "levels": 3,
+                   "blocks": [list(b_) for b_ in blocks], "nvec": nvecs, "form": form,
+                   "coarse_apply_lattice": list(l1["dims"]), "coarse_apply_ndof": n1,
+                   "l2": "inputs larger than L2 (level-1 links 1.36 GB)",
+                   "parallelism": "replicas" if world > 1 else "single-gpu"},
+        "roofline": {"bound": "hbm", "achieved": per_launch_bytes / (per_launch_ms * 1e-3) / 1e9,
+                     "peak": peak, "unit": "GB/s",
+                     "frac": per_launch_bytes / (per_launch_ms * 1e-3) / 1e9 / peak,
+                     "traffic": None, "kernel": "k_coarse_stream (level 1, n=48)",
+                     "peak_kind": peak_kind},
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "solve": {"s_per_solve_median": statistics.median(solve_s),
+                  "outer_iters": [s["iters"] for s in stats],
+                  "level_iters": stats[-1]["level_iters"],
+                  "true_residual": max(s["true_residual"] for s in stats)},
+        "phases_ms_median": dict(zip(["setup_l0", "build_l1", "setup_l1", "build_l2", "solve"],
+                                     [float(v) for v in np.median(ph, axis=0)])),
+        "kernels": {k: {"launches": v["launches"], "ms": v["ms"],
+                        "gbs": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else 0.0}
+                    for k, v in kern.items()},
+        "input_gen_s": t_gen,
+    }
+    if rank == 0 and world == 1:
+        try:
+            line["cpu_baseline"] = oracle_coarse_apply_sample()
+        except Exception as e:  # the baseline must not sink the GPU line
+            line["cpu_baseline"] = {"error": str(e)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    mg.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def coarse_apply_main(args):
+    """Only the level-1 coarse apply (8^3x16 lattice, n = 48) with random
+    links: `steps` timed applies, each on the same 1.36 GB (FP32) link set."""
+    import torch
+
+    import paper_1612_07873_gb300 as gb
+    prec = {"fp32": 1, "bf16": 2, "fp16": 3}[args.form]
+    fine = (16, 16, 16, 32)
+    U = syn.gauge_field(fine, 0.0, 1)
+    p = gb.default_params(dims=fine, block=[(2, 2, 2, 2)], nvec=[24], nlevels=2, prec_fine=1,
+                          prec_coarse=prec)
+    mg = gb.Multigrid(p, torch.from_numpy(U).cuda())
+    l1 = mg.levels[1]
+    vol, n = l1["volume"], l1["ndof"]
+    g = torch.Generator(device="cuda").manual_seed(3)
+    links = torch.randn((vol, 9, n, n), dtype=torch.complex128, device="cuda", generator=g)
+    gb.mg_set_coarse_links(mg.ctx, 1, links)
+    del links
+    x = torch.randn((vol, n), dtype=torch.complex64, device="cuda", generator=g)
+    y = torch.empty_like(x)
+    for _ in range(args.warmup):
+        gb.mg_coarse_apply(mg.ctx, 1, y, x)
+    torch.cuda.synchronize()
+    gb.mg_profile_reset(mg.ctx)
+    gb.mg_profile_enable(mg.ctx, True)
+    for _ in range(args.steps):
+        gb.mg_coarse_apply(mg.ctx, 1, y, x)
+    q = gb.mg_profile_query(mg.ctx, "coarse_apply", 1)
+    peak, kind = peaks()
+    gbs = q["bytes"] / (q["ms"] * 1e-3) / 1e9
+    print(json.dumps({"mode": "coarse-apply", "form": args.form, "lattice": list(l1["dims"]),
+                      "ndof": n, "launches": q["launches"], "us_per_apply": 1e3 * q["ms"] / q["launches"],
+                      "gbs": gbs, "frac": gbs / peak, "peak": peak, "peak_kind": kind,
+                      "bytes_per_apply": q["bytes"] / q["launches"]}), flush=True)
+    mg.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gbmg", choices=["gbmg", "reference"])
+    ap.add_argument("--form", default="fp32", choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--mode", default="pipeline", choices=["pipeline", "coarse-apply"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_main(args)
+    if args.mode == "coarse-apply":
+        return coarse_apply_main(args)
+    return gpu_main(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

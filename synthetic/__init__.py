@@ -21,6 +21,8 @@ Layouts (all complex128, C order):
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
 
 __all__ = ["gauge_field", "gaussian_field", "gauge_transform", "WORKLOADS", "volume"]
@@ -64,25 +66,44 @@ def _expm_i_herm(h: np.ndarray, eps: float) -> np.ndarray:
     return np.stack([r0, r1, r2], axis=-2)
 
 
-def gauge_field(dims, eps: float, seed: int, chunk: int = 1 << 18) -> np.ndarray:
+_CHUNK = 1 << 18
+
+
+def _gauge_chunk(args):
+    eps, seed, index, n = args
+    rng = np.random.Generator(np.random.PCG64([int(seed), 0x5A17, int(index)]))
+    g = rng.standard_normal((n, 3, 3, 2))
+    a = g[..., 0] + 1j * g[..., 1]
+    h = 0.5 * (a + np.conj(np.swapaxes(a, -1, -2)))
+    tr = np.trace(h, axis1=-2, axis2=-1).real / 3.0
+    h = h - tr[:, None, None] * np.eye(3)
+    if eps == 0.0:
+        return np.broadcast_to(np.eye(3, dtype=np.complex128), (n, 3, 3)).copy()
+    return _expm_i_herm(h, eps)
+
+
+def gauge_field(dims, eps: float, seed: int, workers: int | None = None) -> np.ndarray:
     """Weak-field SU(3) gauge field, complex128 [4][V][3][3].
 
     H = (A + A^dag)/2 - tr(.)/3, A with Re, Im iid N(0, 1); U = exp(i eps H).
-    eps = 0 gives the unit (free) field.
+    eps = 0 gives the unit (free) field.  The 4V links are drawn in chunks of
+    2^18 with one random stream per chunk, so the field does not depend on
+    how many worker processes generate it.
     """
     vol = volume(dims)
-    out = np.empty((4, vol, 3, 3), dtype=np.complex128)
-    rng = _rng(seed, 0x5A17)
-    flat = out.reshape(4 * vol, 3, 3)
-    for start in range(0, 4 * vol, chunk):
-        n = min(chunk, 4 * vol - start)
-        g = rng.standard_normal((n, 3, 3, 2))
-        a = g[..., 0] + 1j * g[..., 1]
-        h = 0.5 * (a + np.conj(np.swapaxes(a, -1, -2)))
-        tr = np.trace(h, axis1=-2, axis2=-1).real / 3.0
-        h = h - tr[:, None, None] * np.eye(3)
-        flat[start:start + n] = _expm_i_herm(h, eps) if eps != 0.0 else np.eye(3)
-    return out
+    total = 4 * vol
+    jobs = [(float(eps), seed, i, min(_CHUNK, total - i * _CHUNK))
+            for i in range((total + _CHUNK - 1) // _CHUNK)]
+    if workers is None:
+        workers = min(len(jobs), os.cpu_count() or 1, 16)
+    if workers > 1 and len(jobs) > 1:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+            parts = list(ex.map(_gauge_chunk, jobs))
+    else:
+        parts = [_gauge_chunk(j) for j in jobs]
+    return np.concatenate(parts).reshape(4, vol, 3, 3)
 
 
 def random_su3(n: int, seed: int) -> np.ndarray:
