@@ -41,6 +41,26 @@ WORKLOAD = "c2_32^3x64_3lvl_fp32"
 METRIC = "coarse_apply GB/s (% HBM peak); MG-GCR s/solve at 1e-10, plain vs tuned forms"
 
 
+# DRAM traffic per launch of the level-1 coarse apply from one ncu capture
+# (profiles/coarse_apply_8x8x8x16_n48.md), valid only for the kernel source
+# it was taken on; reported as null once that source changes.
+NCU_TRAFFIC = {
+    "fp32": {"bytes": 1.362170e9 + 4.534784e6, "src": "f559492012f8e757"},
+    "bf16": {"bytes": 0.682693e9 + 3.842816e6, "src": "f559492012f8e757"},
+}
+
+
+def coarse_traffic(form):
+    import hashlib
+    rec = NCU_TRAFFIC.get(form)
+    if rec is None:
+        return None
+    src = os.path.join(ROOT, "paper_1612_07873_gb300", "csrc", "coarse.cu")
+    with open(src, "rb") as fh:
+        h = hashlib.sha256(fh.read()).hexdigest()[:16]
+    return rec["bytes"] if h == rec["src"] else None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -297,7 +317,7 @@ def gpu_main(args):
         "roofline": {"bound": "hbm", "achieved": per_launch_bytes / (per_launch_ms * 1e-3) / 1e9,
                      "peak": peak, "unit": "GB/s",
                      "frac": per_launch_bytes / (per_launch_ms * 1e-3) / 1e9 / peak,
-                     "traffic": None, "kernel": "k_coarse_stream (level 1, n=48)",
+                     "traffic": coarse_traffic(form), "kernel": "k_coarse_stream (level 1, n=48)",
                      "peak_kind": peak_kind},
         "e2e": e2e,
         "gpu_launches": int(launches),
