@@ -193,6 +193,29 @@ mg_status mg_profile_reset(mg_ctx* ctx);
 mg_status mg_profile_query(mg_ctx* ctx, const char* name, int level, int* launches,
                            double* total_ms, double* bytes, double* flops);
 
+/* Block orthonormalisation that allocates no device memory.  The paper has
+ * no counterpart: this entry point exists for callers that cannot let a
+ * library call cudaMalloc -- programs whose device memory belongs to another
+ * allocator (e.g. a framework's caching allocator that reserved the device),
+ * programs under a fixed device-memory budget, and latency-critical loops
+ * that cannot take the implicit synchronisation of cudaMalloc / cudaFree.
+ * It computes what mg_set_nullvecs + mg_get_nullvecs(kind 1) compute:
+ * vecs_dev [nvec][V][ndof] complex double (V = dims[0]*..*dims[3], ndof even,
+ * first half of the dofs = chirality 0) is orthonormalised per aggregate
+ * (extents `block`) and chirality into out_dev (same layout, must not
+ * overlap vecs_dev).  No context is needed; dims and block are host arrays.
+ * Workspace: a file-scope device array of 2^21 complex doubles (32 MiB) that
+ * every GPU loading the library holds until exit; calls with
+ * nvec * V * ndof > 2^21 fail with MG_ERR_ARG.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All
+ * calls share the workspace and it keeps the last call's contents: calls
+ * that overlap on the GPU (other streams, other host threads) race.  The
+ * call synchronises `stream` to read the rank test; MG_ERR_RANK as for
+ * mg_set_nullvecs.  Error text: mg_last_error(NULL).                       */
+mg_status mg_block_orthonormalise_noalloc(const void* vecs_dev, void* out_dev, const int dims[4],
+                                          const int block[4], int ndof, int nvec, void* stream);
+
 /* Number of kernels the library has launched since creation.              */
 long long mg_launch_count(mg_ctx* ctx);
 

@@ -5,7 +5,7 @@ library's CUDA kernels.  Functions carry the C names; tensors are PyTorch
 CUDA tensors (complex128 / complex64) whose data pointers are passed
 through, and the stream defaults to torch's current stream.  Importing
 this module loads the shared library and raises if it has not been built
-(``python -m paper_1612_07873_gb300.build``): there is no fallback.
+(``python paper_1612_07873_gb300/build.py``): there is no fallback.
 """
 from __future__ import annotations
 
@@ -66,7 +66,7 @@ def _load():
     path = _build.lib_path()
     if not os.path.exists(path):
         raise ImportError(f"libgbmg.so not built ({path}); run "
-                          "`python -m paper_1612_07873_gb300.build`")
+                          "`python paper_1612_07873_gb300/build.py`")
     lib = C.CDLL(path)
     vp, i, d, sz = C.c_void_p, C.c_int, C.c_double, C.c_size_t
     sig = {
@@ -91,6 +91,8 @@ def _load():
         "mg_profile_reset": (i, [vp]),
         "mg_profile_query": (i, [vp, C.c_char_p, i, C.POINTER(C.c_int), C.POINTER(d),
                                  C.POINTER(d), C.POINTER(d)]),
+        "mg_block_orthonormalise_noalloc": (i, [vp, vp, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                                i, i, vp]),
         "mg_launch_count": (C.c_longlong, [vp]),
         "mg_status_string": (C.c_char_p, [i]),
         "mg_last_error": (C.c_char_p, [vp]),
@@ -241,6 +243,20 @@ def mg_profile_query(ctx, name, level=-1):
     _ok(LIB.mg_profile_query(ctx, name.encode(), level, C.byref(n), C.byref(ms), C.byref(b),
                              C.byref(f)), ctx)
     return dict(launches=n.value, ms=ms.value, bytes=b.value, flops=f.value)
+
+
+def mg_block_orthonormalise_noalloc(vecs, out, dims, block, stream=None):
+    """Context-free block orthonormalisation that allocates no device memory
+    (for callers that cannot let the library allocate); vecs, out:
+    [nvec][V][ndof] complex128 CUDA tensors."""
+    assert vecs.dtype == torch.complex128 and out.dtype == torch.complex128
+    nvec, vol, ndof = vecs.shape
+    d = (C.c_int * 4)(*dims)
+    b = (C.c_int * 4)(*block)
+    st = LIB.mg_block_orthonormalise_noalloc(_ptr(vecs), _ptr(out), d, b, ndof, nvec,
+                                             _stream(stream))
+    _ok(st, None)
+    return out
 
 
 def mg_launch_count(ctx) -> int:

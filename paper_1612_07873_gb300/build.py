@@ -1,7 +1,7 @@
 """Build libgbmg.so in-tree: every csrc/*.cu compiled in parallel for sm_103a,
 then linked into paper_1612_07873_gb300/lib/libgbmg.so.
 
-    python -m paper_1612_07873_gb300.build [--verbose-ptxas]
+    python paper_1612_07873_gb300/build.py [--force] [--verbose-ptxas]
 """
 from __future__ import annotations
 

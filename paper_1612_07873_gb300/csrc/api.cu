@@ -40,6 +40,8 @@ void check_level(mg_ctx* c, int level, int lo, int hi) {
 
 // ------------------------------------------------------------------ profiler
 namespace gbmg {
+void set_last_error(const char* msg) { g_last_error = msg; }
+
 cudaEvent_t Profiler::get() {
   if (!pool.empty()) {
     cudaEvent_t e = pool.back();

@@ -72,6 +72,9 @@ void setup_sweeps(mg_ctx* c, int level, const void* init, cudaStream_t st);
 void gcr_solve(mg_ctx* c, void* x, const void* b, double tol, int maxiter, mg_solve_stats* stats,
                cudaStream_t st);
 
+// message returned by mg_last_error(NULL) for calls without a context
+void set_last_error(const char* msg);
+
 inline Vec level_vec(const Level& L, void* p) {
   Vec v;
   v.p = p;

@@ -9,6 +9,8 @@
 //
 // Transfer layout Vp: [fine site][dof][Nv] in the level's vector precision,
 // so the Nv coefficients of one fine dof are contiguous.
+#include <mutex>
+
 #include "kernels.cuh"
 
 namespace gbmg {
@@ -348,4 +350,137 @@ void prolong_apply(mg_ctx* c, int level, Vec fine, Vec coarse, cudaStream_t st) 
   c->launches++;
 }
 
+// ---------------------------------------------------------------------------
+// Block orthonormalisation without device allocation.
+//
+// Some callers cannot let a library call cudaMalloc: programs whose device
+// memory is owned by another allocator (a framework's caching allocator that
+// has reserved the device), programs held to a fixed device-memory budget,
+// and latency-critical loops where the implicit synchronisation of
+// cudaMalloc / cudaFree is not acceptable.  mg_block_orthonormalise_noalloc
+// serves them: the caller passes the input and output vectors, and the
+// Gram-Schmidt workspace lives in the file-scope array below, which every
+// GPU that loads this library holds until the process exits.
+namespace {
+
+constexpr size_t kNoAllocMaxElems = size_t(1) << 21;  // complex doubles: 32 MiB
+
+static __device__ __align__(256) double2 g_noalloc_scratch[kNoAllocMaxElems];
+static __device__ __align__(256) int g_noalloc_status[64];
+
+struct NoAllocSlot {
+  bool ready = false;
+  double2* scratch = nullptr;
+  int* status = nullptr;
+};
+constexpr int kNoAllocMaxDevices = 64;
+NoAllocSlot g_noalloc_slots[kNoAllocMaxDevices];
+std::mutex g_noalloc_mutex;
+
+// W [agg][chi][Nv][rows] -> out [Nv][V][nd] (FP64)
+__global__ void k_noalloc_scatter(double2* __restrict__ out, const double2* __restrict__ W,
+                                  AggMap m, int nd, int nv) {
+  const int half = nd / 2;
+  const int rows = m.per * half;
+  size_t total = size_t(nv) * m.fine.vol * nd;
+  for (size_t idx = blockIdx.x * size_t(blockDim.x) + threadIdx.x; idx < total;
+       idx += size_t(gridDim.x) * blockDim.x) {
+    int a = int(idx % nd);
+    size_t t = idx / nd;
+    int s = int(t % m.fine.vol);
+    int i = int(t / m.fine.vol);
+    int c[4];
+    site_coords(m.fine, s, c);
+    int ag = agg_of(m, c), ls = local_of(m, c);
+    int chi = a / half, ad = a - chi * half;
+    out[idx] = W[((size_t(ag) * 2 + chi) * nv + i) * rows + size_t(ls) * half + ad];
+  }
+}
+
+}  // namespace
+
 }  // namespace gbmg
+
+extern "C" mg_status mg_block_orthonormalise_noalloc(const void* vecs_dev, void* out_dev,
+                                                     const int dims[4], const int block[4],
+                                                     int ndof, int nvec, void* stream) {
+  using namespace gbmg;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  auto fail = [](mg_status s, const char* msg) {
+    set_last_error(msg);
+    return s;
+  };
+  if (!vecs_dev || !out_dev || !dims || !block) return fail(MG_ERR_ARG, "noalloc: null argument");
+  if (vecs_dev == out_dev) return fail(MG_ERR_ARG, "noalloc: output aliases input");
+  if (nvec < 1 || ndof < 2 || (ndof & 1)) return fail(MG_ERR_ARG, "noalloc: bad nvec or ndof");
+  int cd[4];
+  long long vol = 1;
+  for (int m = 0; m < 4; ++m) {
+    if (dims[m] < 1 || block[m] < 1 || dims[m] % block[m])
+      return fail(MG_ERR_ARG, "noalloc: lattice extent not divisible by block");
+    cd[m] = dims[m] / block[m];
+    vol *= dims[m];
+  }
+  const unsigned long long elems = (unsigned long long)nvec * vol * ndof;
+  if (elems > kNoAllocMaxElems)
+    return fail(MG_ERR_ARG,
+                "noalloc: nvec * volume * ndof exceeds the 2^21 complex-double workspace (32 MiB)");
+  AggMap m;
+  m.fine = make_geom(dims);
+  m.coarse = make_geom(cd);
+  for (int k = 0; k < 4; ++k) m.b[k] = block[k];
+  m.per = m.fine.vol / m.coarse.vol;
+  const int rows = m.per * ndof / 2;
+  const int threads = rows <= 256 * 16 ? 256 : 1024;
+  const int rpt = (rows + threads - 1) / threads;
+  if (rpt > 24) return fail(MG_ERR_ARG, "noalloc: aggregate block too large (rows > 24576)");
+  // once per device, with that device current: device address of the workspace
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices)
+    return fail(MG_ERR_CUDA, "noalloc: cudaGetDevice failed");
+  NoAllocSlot slot;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mutex);
+    NoAllocSlot& s = g_noalloc_slots[dev];
+    if (!s.ready) {
+      void* p = nullptr;
+      void* q = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess ||
+          cudaGetSymbolAddress(&q, g_noalloc_status) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MG_ERR_CUDA, "noalloc: cudaGetSymbolAddress failed");
+      }
+      s.scratch = static_cast<double2*>(p);
+      s.status = static_cast<int*>(q);
+      s.ready = true;
+    }
+    slot = s;
+  }
+  // the workspace keeps the previous call's contents: clear the status word
+  if (cudaMemsetAsync(slot.status, 0, sizeof(int), st) != cudaSuccess)
+    return fail(MG_ERR_CUDA, "noalloc: cudaMemsetAsync failed");
+  k_mgs_gather<<<grid_for(elems), 256, 0, st>>>(slot.scratch, (const double2*)vecs_dev, m, ndof,
+                                                nvec);
+  const int nblk = m.coarse.vol * 2;
+  if (rpt <= 1)
+    k_mgs<1><<<nblk, threads, 0, st>>>(slot.scratch, rows, nvec, slot.status);
+  else if (rpt <= 2)
+    k_mgs<2><<<nblk, threads, 0, st>>>(slot.scratch, rows, nvec, slot.status);
+  else if (rpt <= 4)
+    k_mgs<4><<<nblk, threads, 0, st>>>(slot.scratch, rows, nvec, slot.status);
+  else if (rpt <= 8)
+    k_mgs<8><<<nblk, threads, 0, st>>>(slot.scratch, rows, nvec, slot.status);
+  else if (rpt <= 16)
+    k_mgs<16><<<nblk, threads, 0, st>>>(slot.scratch, rows, nvec, slot.status);
+  else
+    k_mgs<24><<<nblk, threads, 0, st>>>(slot.scratch, rows, nvec, slot.status);
+  k_noalloc_scatter<<<grid_for(elems), 256, 0, st>>>((double2*)out_dev, slot.scratch, m, ndof,
+                                                     nvec);
+  if (cudaGetLastError() != cudaSuccess) return fail(MG_ERR_CUDA, "noalloc: kernel launch failed");
+  int h = 0;
+  if (cudaMemcpyAsync(&h, slot.status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return fail(MG_ERR_CUDA, "noalloc: status read-back failed");
+  if (h & 1) return fail(MG_ERR_RANK, "noalloc: rank-deficient null-vector aggregate block");
+  return MG_OK;
+}
