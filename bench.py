@@ -194,6 +194,8 @@ def gpu_main(args):
 
     w = syn.WORKLOADS[WORKLOAD]
     dims, blocks, nvecs = w["dims"], w["block"], w["nvec"]
+    if args.fine:  # smaller fine lattice of the same shape family (profiling runs)
+        dims = tuple(int(v) for v in args.fine.split(","))
     form = args.form
     prec_coarse = {"fp32": 1, "bf16": 2, "fp16": 3}[form]
     t_gen = time.perf_counter()
@@ -364,22 +366,27 @@ def coarse_apply_main(args):
     links = torch.randn((vol, 9, n, n), dtype=torch.complex128, device="cuda", generator=g)
     gb.mg_set_coarse_links(mg.ctx, 1, links)
     del links
-    x = torch.randn((vol, n), dtype=torch.complex64, device="cuda", generator=g)
+    nrhs = args.nrhs
+    shape = (vol, n) if nrhs == 1 else (vol, n, nrhs)
+    x = torch.randn(shape, dtype=torch.complex64, device="cuda", generator=g)
     y = torch.empty_like(x)
     for _ in range(args.warmup):
-        gb.mg_coarse_apply(mg.ctx, 1, y, x)
+        gb.mg_coarse_apply(mg.ctx, 1, y, x, nrhs=nrhs)
     torch.cuda.synchronize()
     gb.mg_profile_reset(mg.ctx)
     gb.mg_profile_enable(mg.ctx, True)
     for _ in range(args.steps):
-        gb.mg_coarse_apply(mg.ctx, 1, y, x)
+        gb.mg_coarse_apply(mg.ctx, 1, y, x, nrhs=nrhs)
+    gb.mg_device_status(mg.ctx)
     q = gb.mg_profile_query(mg.ctx, "coarse_apply", 1)
     peak, kind = peaks()
     gbs = q["bytes"] / (q["ms"] * 1e-3) / 1e9
+    tflops = q["flops"] / (q["ms"] * 1e-3) / 1e12
     print(json.dumps({"mode": "coarse-apply", "form": args.form, "lattice": list(l1["dims"]),
-                      "ndof": n, "launches": q["launches"], "us_per_apply": 1e3 * q["ms"] / q["launches"],
+                      "ndof": n, "nrhs": nrhs, "launches": q["launches"],
+                      "us_per_apply": 1e3 * q["ms"] / q["launches"],
                       "gbs": gbs, "frac": gbs / peak, "peak": peak, "peak_kind": kind,
-                      "bytes_per_apply": q["bytes"] / q["launches"]}), flush=True)
+                      "tflops": tflops, "bytes_per_apply": q["bytes"] / q["launches"]}), flush=True)
     mg.close()
     return 0
 
@@ -392,6 +399,8 @@ def main():
     ap.add_argument("--impl", default="gbmg", choices=["gbmg", "reference"])
     ap.add_argument("--form", default="fp32", choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--mode", default="pipeline", choices=["pipeline", "coarse-apply"])
+    ap.add_argument("--fine", default="", help="override the fine extents, e.g. 16,16,16,32")
+    ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides (coarse-apply mode)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_main(args)

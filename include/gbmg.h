@@ -216,6 +216,12 @@ mg_status mg_profile_query(mg_ctx* ctx, const char* name, int level, int* launch
 mg_status mg_block_orthonormalise_noalloc(const void* vecs_dev, void* out_dev, const int dims[4],
                                           const int block[4], int ndof, int nvec, void* stream);
 
+/* Synchronise `stream` and report errors that kernels recorded on the
+ * device: MG_ERR_TIMEOUT if a bounded wait inside a kernel (the tensor-core
+ * multi-RHS apply's mbarrier waits) gave up since the last call; the record
+ * is cleared.                                                              */
+mg_status mg_device_status(mg_ctx* ctx, void* stream);
+
 /* Number of kernels the library has launched since creation.              */
 long long mg_launch_count(mg_ctx* ctx);
 

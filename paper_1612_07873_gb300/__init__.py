@@ -93,6 +93,7 @@ def _load():
                                  C.POINTER(d), C.POINTER(d)]),
         "mg_block_orthonormalise_noalloc": (i, [vp, vp, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                                 i, i, vp]),
+        "mg_device_status": (i, [vp, vp]),
         "mg_launch_count": (C.c_longlong, [vp]),
         "mg_status_string": (C.c_char_p, [i]),
         "mg_last_error": (C.c_char_p, [vp]),
@@ -257,6 +258,10 @@ def mg_block_orthonormalise_noalloc(vecs, out, dims, block, stream=None):
                                              _stream(stream))
     _ok(st, None)
     return out
+
+
+def mg_device_status(ctx, stream=None):
+    _ok(LIB.mg_device_status(ctx, _stream(stream)), ctx)
 
 
 def mg_launch_count(ctx) -> int:

@@ -163,6 +163,7 @@ mg_status mg_create(const mg_params* p, const void* gauge_dev, mg_ctx** out) {
     c->red_partials.alloc(2 * 1024 * sizeof(double2));
     c->scalars.alloc(SC_COUNT * sizeof(double2));
     c->status.alloc(64);
+    c->batch_scalars.alloc(2 * 64 * sizeof(double2));
     GB_CHECK(cudaMallocHost(&c->h_scalars, SC_COUNT * sizeof(double2)));
     GB_CHECK(cudaMemset(c->scalars.p, 0, c->scalars.bytes));
     GB_CHECK(cudaMemset(c->status.p, 0, c->status.bytes));
@@ -216,9 +217,12 @@ mg_status mg_get_nullvecs(mg_ctx* c, int level, int kind, void* dst, size_t byte
     const size_t need = size_t(L.nvec) * L.vec_elems() * 16;
     GB_REQUIRE(dst && bytes == need, MG_ERR_ARG, "get_nullvecs: size mismatch");
     GB_REQUIRE(kind == 0 || kind == 1, MG_ERR_ARG, "get_nullvecs: kind must be 0 or 1");
-    const DevBuf& src = kind == 0 ? L.raw : L.orth64;
-    GB_REQUIRE(kind == 0 ? L.have_raw : L.have_V, MG_ERR_STATE, "get_nullvecs: not available");
-    GB_CHECK(cudaMemcpyAsync(dst, src.p, need, cudaMemcpyDeviceToDevice, S(stream)));
+    if (kind == 0) {
+      GB_REQUIRE(L.have_raw, MG_ERR_STATE, "get_nullvecs: not available");
+      GB_CHECK(cudaMemcpyAsync(dst, L.raw.p, need, cudaMemcpyDeviceToDevice, S(stream)));
+    } else {
+      nullvecs_export(c, level, dst, S(stream));
+    }
   });
 }
 
@@ -349,6 +353,19 @@ mg_status mg_profile_query(mg_ctx* c, const char* name, int level, int* launches
     if (ms) *ms = t;
     if (bytes) *bytes = b;
     if (flops) *flops = f;
+  });
+}
+
+mg_status mg_device_status(mg_ctx* c, void* stream) {
+  return guarded(c, [&] {
+    int h[2] = {0, 0};
+    GB_CHECK(cudaMemcpyAsync(h, c->status.p, sizeof(h), cudaMemcpyDeviceToHost, S(stream)));
+    GB_CHECK(cudaStreamSynchronize(S(stream)));
+    if (h[1]) {
+      GB_CHECK(cudaMemsetAsync(c->status.as<int>() + 1, 0, sizeof(int), S(stream)));
+      GB_CHECK(cudaStreamSynchronize(S(stream)));
+      throw Error(MG_ERR_TIMEOUT, "a bounded device wait timed out (tensor-core coarse apply)");
+    }
   });
 }
 

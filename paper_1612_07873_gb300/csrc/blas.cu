@@ -4,6 +4,8 @@
 // it, so smoothers and orthogonalisation never wait on the host.
 // Reductions are two-stage with a grid that depends only on the length,
 // so results are bitwise reproducible run to run.
+#include <type_traits>
+
 #include "kernels.cuh"
 
 namespace gbmg {
@@ -45,36 +47,42 @@ __device__ __forceinline__ double2 block_sum(double2 v, double2* sh) {
   return v;
 }
 
+// Per-thread partial sums run in the arithmetic type T: FP32 when both
+// operands are FP32 (FP64 issue is scarce on GB300), FP64 otherwise; the
+// per-thread partials are combined in FP64.
 template <typename Ra, typename Rb>
+using acc_t = typename std::conditional<std::is_same<Ra, float>::value &&
+                                            std::is_same<Rb, float>::value,
+                                        float, double>::type;
+
+template <typename Ra, typename Rb, typename T>
 __global__ void k_dot_partial(const cpx<Ra>* __restrict__ a, const cpx<Rb>* __restrict__ b,
                               size_t n, double2* __restrict__ part) {
   __shared__ double2 sh[32];
-  double2 acc = make_double2(0.0, 0.0);
+  cpx<T> acc(T(0), T(0));
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
-       i += size_t(gridDim.x) * blockDim.x) {
-    cpx<double> x(a[i]), y(b[i]);
-    acc.x += x.re * y.re + x.im * y.im;
-    acc.y += x.re * y.im - x.im * y.re;
-  }
-  acc = block_sum(acc, sh);
-  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+       i += size_t(gridDim.x) * blockDim.x)
+    cmac_conj(acc, cpx<T>(a[i]), cpx<T>(b[i]));
+  double2 d = block_sum(make_double2(double(acc.re), double(acc.im)), sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = d;
 }
 
 template <typename Ra, typename Rb>
 __global__ void k_dot2_partial(const cpx<Ra>* __restrict__ p, const cpx<Rb>* __restrict__ r,
                                size_t n, double2* __restrict__ part, int stride) {
+  using T = acc_t<Ra, Rb>;
   __shared__ double2 sh[32];
-  double2 pr = make_double2(0.0, 0.0), pp = make_double2(0.0, 0.0);
+  cpx<T> a_pr(T(0), T(0));
+  T a_pp = T(0);
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
        i += size_t(gridDim.x) * blockDim.x) {
-    cpx<double> x(p[i]), y(r[i]);
-    pr.x += x.re * y.re + x.im * y.im;
-    pr.y += x.re * y.im - x.im * y.re;
-    pp.x += x.re * x.re + x.im * x.im;
+    cpx<T> x(p[i]), y(r[i]);
+    cmac_conj(a_pr, x, y);
+    a_pp = fma(x.re, x.re, fma(x.im, x.im, a_pp));
   }
-  pr = block_sum(pr, sh);
+  double2 pr = block_sum(make_double2(double(a_pr.re), double(a_pr.im)), sh);
   __syncthreads();
-  pp = block_sum(pp, sh);
+  double2 pp = block_sum(make_double2(double(a_pp), 0.0), sh);
   if (threadIdx.x == 0) {
     part[blockIdx.x] = pr;
     part[stride + blockIdx.x] = pp;
@@ -103,12 +111,14 @@ template <typename Ry, typename Rx>
 __global__ void k_axpy(cpx<Ry>* __restrict__ y, const cpx<Rx>* __restrict__ x, size_t n,
                        double are, double aim, const double2* __restrict__ S, int slot,
                        double sign) {
+  using T = acc_t<Ry, Rx>;
   cpx<double> a(are, aim);
   if (S) a = cpx<double>(sign * S[slot].x, sign * S[slot].y);
+  const cpx<T> at(a);
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
        i += size_t(gridDim.x) * blockDim.x) {
-    cpx<double> yy(y[i]);
-    cmac(yy, a, cpx<double>(x[i]));
+    cpx<T> yy(y[i]);
+    cmac(yy, at, cpx<T>(x[i]));
     y[i] = cpx<Ry>(yy);
   }
 }
@@ -116,9 +126,10 @@ __global__ void k_axpy(cpx<Ry>* __restrict__ y, const cpx<Rx>* __restrict__ x, s
 template <typename Ro, typename Rb, typename Ra>
 __global__ void k_sub(cpx<Ro>* __restrict__ o, const cpx<Rb>* __restrict__ b,
                       const cpx<Ra>* __restrict__ ax, size_t n) {
+  using T = acc_t<Ro, acc_t<Rb, Ra>>;
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
        i += size_t(gridDim.x) * blockDim.x)
-    o[i] = cpx<Ro>(cpx<double>(b[i]) - cpx<double>(ax[i]));
+    o[i] = cpx<Ro>(cpx<T>(b[i]) - cpx<T>(ax[i]));
 }
 
 // x += a r ; r -= a p  with a = omega S[spr] / S[spp].re
@@ -143,11 +154,13 @@ __global__ void k_mr_update(cpx<R>* __restrict__ x, cpx<R>* __restrict__ r,
 template <typename Ra, typename Rb>
 __global__ void k_scale_invnorm(cpx<Ra>* __restrict__ a, cpx<Rb>* __restrict__ b, size_t n,
                                 const double2* S, int slot) {
-  double s = S[slot].x > 0.0 ? 1.0 / sqrt(S[slot].x) : 0.0;
+  const double s = S[slot].x > 0.0 ? 1.0 / sqrt(S[slot].x) : 0.0;
+  const Ra sa = Ra(s);
+  const Rb sb = Rb(s);
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
        i += size_t(gridDim.x) * blockDim.x) {
-    a[i] = cpx<Ra>(s * cpx<double>(a[i]));
-    if (b) b[i] = cpx<Rb>(s * cpx<double>(b[i]));
+    a[i] = sa * a[i];
+    if (b) b[i] = sb * b[i];
   }
 }
 
@@ -183,6 +196,78 @@ __global__ void k_sweep_update(cpx<R>* __restrict__ x, const cpx<R>* __restrict_
   }
 }
 
+// ---- batched forms over nvec vectors stored back to back (vector v at
+// offset v * n); blockIdx.y is the vector.
+template <typename Ra, typename Rb>
+__global__ void k_dot2_partial_b(const cpx<Ra>* __restrict__ p, const cpx<Rb>* __restrict__ r,
+                                 size_t n, double2* __restrict__ part) {
+  using T = acc_t<Ra, Rb>;
+  __shared__ double2 sh[32];
+  p += blockIdx.y * n;
+  r += blockIdx.y * n;
+  cpx<T> a_pr(T(0), T(0));
+  T a_pp = T(0);
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
+       i += size_t(gridDim.x) * blockDim.x) {
+    cpx<T> x(p[i]), y(r[i]);
+    cmac_conj(a_pr, x, y);
+    a_pp = fma(x.re, x.re, fma(x.im, x.im, a_pp));
+  }
+  double2 pr = block_sum(make_double2(double(a_pr.re), double(a_pr.im)), sh);
+  __syncthreads();
+  double2 pp = block_sum(make_double2(double(a_pp), 0.0), sh);
+  if (threadIdx.x == 0) {
+    const size_t base = size_t(blockIdx.y) * 2 * gridDim.x;
+    part[base + blockIdx.x] = pr;
+    part[base + gridDim.x + blockIdx.x] = pp;
+  }
+}
+
+// out[2 v + k] = sum of the nparts partials of (vector v, quantity k)
+__global__ void k_reduce_final_b(const double2* __restrict__ part, int nparts,
+                                 double2* __restrict__ out) {
+  __shared__ double2 sh[32];
+  const double2* src = part + size_t(blockIdx.x) * nparts;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+    acc.x += src[i].x;
+    acc.y += src[i].y;
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) out[blockIdx.x] = acc;
+}
+
+// x_v -= (B[2v] / B[2v+1].re) t_v   (setup sweep, every vector at once)
+template <typename R>
+__global__ void k_sweep_update_b(cpx<R>* __restrict__ x, const cpx<R>* __restrict__ t, size_t n,
+                                 int nvec, const double2* __restrict__ B) {
+  const size_t total = n * nvec;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < total;
+       i += size_t(gridDim.x) * blockDim.x) {
+    const int v = int(i / n);
+    const double den = B[2 * v + 1].x;
+    cpx<R> a(R(0), R(0));
+    if (den > 0.0) a = cpx<R>(R(-B[2 * v].x / den), R(-B[2 * v].y / den));
+    cpx<R> xi = x[i];
+    cmac(xi, a, t[i]);
+    x[i] = xi;
+  }
+}
+
+// x_v /= sqrt(B[2v+1].re)
+template <typename R>
+__global__ void k_normalise_b(cpx<R>* __restrict__ x, size_t n, int nvec,
+                              const double2* __restrict__ B) {
+  const size_t total = n * nvec;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < total;
+       i += size_t(gridDim.x) * blockDim.x) {
+    const int v = int(i / n);
+    const double nn = B[2 * v + 1].x;
+    const R s = R(nn > 0.0 ? 1.0 / sqrt(nn) : 0.0);
+    x[i] = s * x[i];
+  }
+}
+
 // ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC11), used to draw the
 // random initial null-vector guesses on the device.
 __device__ __forceinline__ uint4 philox4x32_10(uint4 ctr, uint2 key) {
@@ -205,22 +290,22 @@ __global__ void k_gaussian(cpx<R>* __restrict__ v, size_t n, uint64_t seed, uint
        i += size_t(gridDim.x) * blockDim.x) {
     uint64_t c = offset + i;
     uint4 r = philox4x32_10(make_uint4(uint32_t(c), uint32_t(c >> 32), 0x6A09E667u, 0), key);
-    // Box-Muller on two uniforms in (0, 1]
-    double u1 = (double(r.x) + 1.0) * 2.3283064365386963e-10;
-    double u2 = double(r.y) * 2.3283064365386963e-10;
-    double rad = sqrt(-2.0 * log(u1));
-    double s, co;
-    sincospi(2.0 * u2, &s, &co);
-    v[i] = cpx<R>(R(rad * co), R(rad * s));
+    // Box-Muller on two uniforms in (0, 1], in the output precision
+    const R u1 = (R(r.x) + R(1)) * R(2.3283064365386963e-10);
+    const R u2 = R(r.y) * R(2.3283064365386963e-10);
+    const R rad = sqrt(R(-2) * log(u1));
+    R s, co;
+    sincospi(R(2) * u2, &s, &co);
+    v[i] = cpx<R>(rad * co, rad * s);
   }
 }
 
 template <typename R>
 __global__ void k_normalise(cpx<R>* __restrict__ x, size_t n, const double2* S, int slot) {
-  double s = S[slot].x > 0.0 ? 1.0 / sqrt(S[slot].x) : 0.0;
+  const R s = R(S[slot].x > 0.0 ? 1.0 / sqrt(S[slot].x) : 0.0);
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
        i += size_t(gridDim.x) * blockDim.x)
-    x[i] = cpx<R>(s * cpx<double>(x[i]));
+    x[i] = s * x[i];
 }
 
 double2* scal(mg_ctx* c) { return c->scalars.as<double2>(); }
@@ -291,18 +376,61 @@ void blas_sub(mg_ctx* c, Vec o, Vec b, Vec ax, cudaStream_t st) {
   c->launches++;
 }
 
-void blas_dot(mg_ctx* c, Vec a, Vec b, int slot, cudaStream_t st) {
+void blas_dot(mg_ctx* c, Vec a, Vec b, int slot, cudaStream_t st, bool fp64_partials) {
   int nb = red_blocks(a.n);
   double2* part = c->red_partials.as<double2>();
-  GB_DISPATCH2(a.prec, Ra, b.prec, Rb,
-               (k_dot_partial<Ra, Rb><<<nb, kThreads, 0, st>>>(
-                   (const cpx<Ra>*)a.p, (const cpx<Rb>*)b.p, a.n, part)));
+  if (fp64_partials) {
+    GB_DISPATCH2(a.prec, Ra, b.prec, Rb,
+                 (k_dot_partial<Ra, Rb, double><<<nb, kThreads, 0, st>>>(
+                     (const cpx<Ra>*)a.p, (const cpx<Rb>*)b.p, a.n, part)));
+  } else {
+    GB_DISPATCH2(a.prec, Ra, b.prec, Rb,
+                 (k_dot_partial<Ra, Rb, acc_t<Ra, Rb>><<<nb, kThreads, 0, st>>>(
+                     (const cpx<Ra>*)a.p, (const cpx<Rb>*)b.p, a.n, part)));
+  }
   GB_LAUNCH_CHECK();
   c->launches++;
   finish_reduction(c, nb, slot, part, st);
 }
 
-void blas_norm2(mg_ctx* c, Vec a, int slot, cudaStream_t st) { blas_dot(c, a, a, slot, st); }
+void blas_norm2(mg_ctx* c, Vec a, int slot, cudaStream_t st, bool fp64_partials) {
+  blas_dot(c, a, a, slot, st, fp64_partials);
+}
+
+void blas_dot2_batched(mg_ctx* c, Vec p, Vec r, int nvec, cudaStream_t st) {
+  GB_REQUIRE(nvec >= 1 && nvec <= 64, MG_ERR_ARG, "dot2_batched: nvec out of range");
+  const int nb = red_blocks(p.n);
+  const size_t need = size_t(nvec) * 2 * nb * sizeof(double2);
+  if (c->batch_partials.bytes < need) c->batch_partials.alloc(need);
+  double2* part = c->batch_partials.as<double2>();
+  dim3 grid(nb, nvec);
+  GB_DISPATCH2(p.prec, Ra, r.prec, Rb,
+               (k_dot2_partial_b<Ra, Rb><<<grid, kThreads, 0, st>>>(
+                   (const cpx<Ra>*)p.p, (const cpx<Rb>*)r.p, p.n, part)));
+  GB_LAUNCH_CHECK();
+  k_reduce_final_b<<<2 * nvec, 256, 0, st>>>(part, nb, c->batch_scalars.as<double2>());
+  GB_LAUNCH_CHECK();
+  c->launches += 2;
+}
+
+void blas_sweep_update_batched(mg_ctx* c, Vec x, Vec t, int nvec, cudaStream_t st) {
+  GB_REQUIRE(x.prec == t.prec, MG_ERR_ARG, "sweep_update_batched: precision mix");
+  GB_DISPATCH1(x.prec, R,
+               (k_sweep_update_b<R><<<ew_blocks(x.n * nvec), kThreads, 0, st>>>(
+                   (cpx<R>*)x.p, (const cpx<R>*)t.p, x.n, nvec, c->batch_scalars.as<double2>())));
+  GB_LAUNCH_CHECK();
+  c->launches++;
+}
+
+void blas_normalise_batched(mg_ctx* c, Vec x, int nvec, cudaStream_t st) {
+  // |x_v|^2 into the second slot of each vector's pair
+  blas_dot2_batched(c, x, x, nvec, st);
+  GB_DISPATCH1(x.prec, R,
+               (k_normalise_b<R><<<ew_blocks(x.n * nvec), kThreads, 0, st>>>(
+                   (cpx<R>*)x.p, x.n, nvec, c->batch_scalars.as<double2>())));
+  GB_LAUNCH_CHECK();
+  c->launches++;
+}
 
 void blas_dot2(mg_ctx* c, Vec p, Vec r, int s_pr, int s_pp, cudaStream_t st) {
   int nb = red_blocks(p.n);

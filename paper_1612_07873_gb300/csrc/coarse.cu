@@ -263,6 +263,12 @@ void coarse_apply(mg_ctx* c, int level, void* y, const void* x, int nrhs, cudaSt
   const double vbytes = double(L.g.vol) * 2 * n * nrhs * (L.vprec == MG_F64 ? 16 : 8);
   ProfScope ps(c->prof, st, "coarse_apply", level, lbytes + vbytes,
                8.0 * 9 * n * n * L.g.vol * nrhs);
+  if (nrhs > 1 && coarse_apply_mma_supported(L, nrhs)) {
+    coarse_apply_mma(c, level, y, x, nrhs, st);
+    GB_LAUNCH_CHECK();
+    c->launches++;
+    return;
+  }
   switch (L.prec) {
     case MG_F64: dispatch_apply<cpx<double>>(L, y, x, L.links.p, nrhs, st); break;
     case MG_F32: dispatch_apply<cpx<float>>(L, y, x, L.links.p, nrhs, st); break;
@@ -287,6 +293,7 @@ void links_pack16(mg_ctx* c, int level, cudaStream_t st) {
                                                   L.links.as<cpx<float>>(), L.nd);
   GB_LAUNCH_CHECK();
   c->launches++;
+  links_tile_mma(c, level, st);
 }
 
 void links_import(mg_ctx* c, int level, const void* ext, cudaStream_t st) {

@@ -1,0 +1,413 @@
+// Multi-right-hand-side coarse apply of Eq. (3) on the 5th-generation
+// tensor cores (tcgen05, FP16/BF16 operands, FP32 accumulators in TMEM).
+//
+// For one coarse site the apply of nrhs vectors is a complex GEMM
+//   Y[m][j] = sum_{slot d} sum_k L_d[m][k] X(nbr_d)[k][j],   m, k < n, j < nrhs.
+// It is run as a real GEMM D = A B^T per site with K = 2n per slot:
+//   B_d[m][2k + c] = (re, im) of L_d[m][k]   (the link rows, K-major),
+//   A_d[j][2k]     =  Re X[k][j],  A_d[j][2k + 1] = -Im X[k][j]   (row j  -> Re Y[.][j])
+//   A_d[nrhs+j][2k] = Im X[k][j],  A_d[nrhs+j][2k+1] = Re X[k][j] (row nrhs+j -> Im Y[.][j])
+// so D[j][m] = Re Y[m][j] and D[nrhs + j][m] = Im Y[m][j].  M = 128 rows
+// (2 nrhs <= 128, the rest zero), N = n, accumulated over the 9 slots.
+//
+// Data flow per site: for each slot the CTA copies the slot's links (stored
+// in HBM already in the canonical K-major core-matrix order, no swizzle) and
+// builds the spinor operand in shared memory, double-buffered; one thread
+// issues the 2n/16 MMAs of the slot and commits them to the buffer's
+// mbarrier.  After the 9 slots the four warps read their 32 TMEM lanes,
+// exchange real/imaginary rows through shared memory and store Y coalesced.
+// Every mbarrier wait is bounded: on timeout the kernel records an error
+// word, waits (bounded) for its MMAs, frees its TMEM and returns.
+#include "kernels.cuh"
+
+namespace gbmg {
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(dst)),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t it = 0; it < (1u << 24); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                        uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// 32 lanes x 16 consecutive FP32 columns
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor, K-major, no swizzle: 8-row x 16-byte
+// core matrices; lbo = bytes between K-adjacent core matrices, sbo = bytes
+// between M/N-adjacent ones.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= uint64_t((saddr >> 4) & 0x3FFFu);
+  d |= uint64_t((lbo >> 4) & 0x3FFFu) << 16;
+  d |= uint64_t((sbo >> 4) & 0x3FFFu) << 32;
+  d |= uint64_t(1) << 46;  // descriptor version of the sm_100 family; no swizzle
+  return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, A and B both F16 or
+// both BF16, both K-major, shape M x N.
+__host__ __device__ constexpr uint32_t mma_idesc(int M, int N, bool bf16) {
+  return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) |
+         (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+
+// byte offset of element (row, k) in a K-major, no-swizzle operand of
+// `kcols` K elements (16-bit): core matrices [row/8][k/8] of 128 bytes
+__host__ __device__ __forceinline__ uint32_t core_off(int row, int k, int kcols) {
+  return uint32_t(((row >> 3) * (kcols >> 3) + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+template <bool BF16>
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+  if constexpr (BF16) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+  } else {
+    __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+  }
+}
+
+template <bool BF16, int N>
+__global__ void __launch_bounds__(128) k_coarse_mma(cpx<float>* __restrict__ y,
+                                                    const cpx<float>* __restrict__ x,
+                                                    const uint4* __restrict__ links,
+                                                    const float* __restrict__ scales, Geom g,
+                                                    int nrhs, int* __restrict__ err) {
+  // a pipeline stage is half a stencil slot: N/2 complex link columns, i.e.
+  // KS = N real K values; 18 stages per site
+  constexpr int KS = N;                     // real K of one stage
+  constexpr int A_BYTES = 128 * KS * 2;     // spinor operand, M = 128 rows
+  constexpr int B_BYTES = N * KS * 2;       // link operand, N rows
+  constexpr uint32_t LBO = 128;
+  constexpr uint32_t SBO = (KS / 8) * 128;
+  constexpr int NST = 18;                   // stages per site
+  constexpr uint32_t IDESC = mma_idesc(128, N, BF16);
+  constexpr uint32_t TMEM_COLS = N <= 32 ? 32 : (N <= 64 ? 64 : 128);
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ uint64_t mbar[2];
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int nb_sh[9];
+  __shared__ int abort_sh;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // buffers: A0 A1 B0 B1
+#define ABUF(b) (smem + (b) * A_BYTES)
+#define BBUF(b) (smem + 2 * A_BYTES + (b) * B_BYTES)
+
+  if (warp == 0) {
+    tmem_alloc(&tmem_base_sh, TMEM_COLS);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    fence_mbar_init();
+    abort_sh = 0;
+  }
+  // both spinor buffers start at zero: rows >= 2 nrhs stay zero throughout
+  for (int i = tid; i < 2 * A_BYTES / 16; i += 128)
+    reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_sh;
+  // per buffer b: bit b of `parity` = mbarrier phase to wait for, bit b of
+  // `pending` = MMAs committed on that buffer not yet waited for
+  uint32_t parity = 0u, pending = 0u;
+  bool ok = true;
+
+  // Operands of one slot are fetched into registers by fully unrolled,
+  // independent loads (every load of the slot in flight at once); slot d+1
+  // is fetched while slot d's barrier and MMAs run.
+  constexpr int XPT = ((N / 2) * 64 + 127) / 128;  // spinor elements per thread (nrhs <= 64)
+  constexpr int BPT = (B_BYTES / 16 + 127) / 128;   // 16-byte link chunks per thread
+  cpx<float> xr[XPT];
+  uint4 br[BPT];
+  const int nx = N * nrhs;          // spinor elements of one site
+  const int nxs = (N / 2) * nrhs;   // spinor elements of one stage
+  auto fetch = [&](int site, int st) {
+    const int d = st >> 1, h = st & 1;
+    const cpx<float>* xs = x + size_t(nb_sh[d]) * nx + size_t(h) * nxs;
+    const uint4* src = links + (size_t(site) * NST + st) * (B_BYTES / 16);
+#pragma unroll
+    for (int u = 0; u < BPT; ++u) {
+      const int i = tid + 128 * u;
+      if (i < B_BYTES / 16) br[u] = ld_stream16(src + i);
+    }
+#pragma unroll
+    for (int u = 0; u < XPT; ++u) {
+      const int e = tid + 128 * u;
+      if (e < nxs) xr[u] = xs[e];
+    }
+  };
+  auto stage = [&](int b) {
+    uint4* dstB = reinterpret_cast<uint4*>(BBUF(b));
+#pragma unroll
+    for (int u = 0; u < BPT; ++u) {
+      const int i = tid + 128 * u;
+      if (i < B_BYTES / 16) dstB[i] = br[u];
+    }
+    unsigned char* A = ABUF(b);
+#pragma unroll
+    for (int u = 0; u < XPT; ++u) {
+      const int e = tid + 128 * u;
+      if (e < nxs) {
+        const int k = e / nrhs, j = e - k * nrhs;  // k: complex column within the stage
+        const cpx<float> v = xr[u];
+        *reinterpret_cast<uint32_t*>(A + core_off(j, 2 * k, KS)) = pack2<BF16>(v.re, -v.im);
+        *reinterpret_cast<uint32_t*>(A + core_off(nrhs + j, 2 * k, KS)) = pack2<BF16>(v.im, v.re);
+      }
+    }
+  };
+
+  for (int site = blockIdx.x; site < g.vol && ok; site += gridDim.x) {
+    if (tid < 9) {
+      int c[4];
+      site_coords(g, site, c);
+      nb_sh[tid] = neighbour(g, site, c, tid);
+    }
+    __syncthreads();
+    fetch(site, 0);
+    for (int d = 0; d < NST; ++d) {
+      const int b = d & 1;
+      if (pending & (1u << b)) {  // the MMAs that read this buffer two slots ago
+        if (tid == 0 && !mbar_wait(&mbar[b], (parity >> b) & 1u)) abort_sh = 1;
+        __syncthreads();
+        if (abort_sh) {
+          ok = false;
+          break;
+        }
+        parity ^= 1u << b;
+        pending &= ~(1u << b);
+      }
+      stage(b);
+      if (d < NST - 1) fetch(site, d + 1);
+      fence_proxy_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(ABUF(b)), b0 = smem_u32(BBUF(b));
+#pragma unroll
+        for (int kk = 0; kk < KS / 16; ++kk)
+          mma_f16(tmem, smem_desc(a0 + kk * 256, LBO, SBO), smem_desc(b0 + kk * 256, LBO, SBO),
+                  IDESC, (d > 0 || kk > 0) ? 1u : 0u);
+        mma_commit(&mbar[b]);
+      }
+      pending |= 1u << b;
+    }
+    if (!ok) break;
+    for (int b = 0; b < 2; ++b)
+      if (pending & (1u << b)) {
+        if (tid == 0 && !mbar_wait(&mbar[b], (parity >> b) & 1u)) abort_sh = 1;
+        __syncthreads();
+        if (abort_sh) {
+          ok = false;
+          break;
+        }
+        parity ^= 1u << b;
+        pending &= ~(1u << b);
+      }
+    if (!ok) break;
+    tc_fence_after();
+    // TMEM lanes 32w..32w+31 = rows of D, staged as FP32 [row][N] over the two
+    // spinor buffers (2 nrhs * 4N <= 512 N bytes = both buffers)
+    float* Cs = reinterpret_cast<float*>(smem);
+    const int row = 32 * warp + lane;
+#pragma unroll
+    for (int c0 = 0; c0 < N; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + (uint32_t(32 * warp) << 16) + uint32_t(c0), v);
+      if (row < 2 * nrhs) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) Cs[row * N + c0 + q] = v[q];
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    const float sc = scales[site];
+    cpx<float>* ys = y + size_t(site) * nx;
+    for (int e = tid; e < nx; e += 128) {
+      const int m = e / nrhs, j = e - m * nrhs;
+      ys[e] = cpx<float>(sc * Cs[j * N + m], sc * Cs[(nrhs + j) * N + m]);
+    }
+    __syncthreads();
+    // restore the zero rows >= 2 nrhs of both spinor buffers
+    for (int b = 0; b < 2; ++b) {
+      uint4* z = reinterpret_cast<uint4*>(ABUF(b) + 2 * nrhs * KS * 2);
+      for (int i = tid; i < (128 - 2 * nrhs) * KS * 2 / 16; i += 128) z[i] = make_uint4(0, 0, 0, 0);
+    }
+  }
+  if (!ok) {
+    // let any MMAs still in flight finish (bounded) before TMEM is freed
+    if (tid == 0) {
+      for (int b = 0; b < 2; ++b)
+        if (pending & (1u << b)) mbar_wait(&mbar[b], (parity >> b) & 1u);
+      atomicOr(err, 1);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+#undef ABUF
+#undef BBUF
+}
+
+// FP32 internal links [V][9][col k][row m] (unscaled) -> tiled 16-bit MMA
+// operand [V][9][core(m, 2k)] scaled by the per-site scale.
+template <bool BF16>
+__global__ void k_links_tile_mma(uint32_t* __restrict__ out, const cpx<float>* __restrict__ in,
+                                 const float* __restrict__ scales, int vol, int n) {
+  const size_t total = size_t(vol) * 9 * n * n;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < total;
+       i += size_t(gridDim.x) * blockDim.x) {
+    const size_t blk = i / (size_t(n) * n);
+    const int rem = int(i - blk * n * n);
+    const int k = rem / n, m = rem - k * n;  // internal [col k][row m]
+    const size_t site = blk / 9;
+    const int d = int(blk - site * 9);
+    const int h = k / (n / 2), kl = k - h * (n / 2);  // half of the slot, column within it
+    const size_t stage = site * 18 + size_t(d) * 2 + h;
+    const float inv = 1.f / scales[site];
+    const cpx<float> v = in[i];
+    const size_t words = size_t(n) * n * 2 / 4;  // 32-bit words per (site, stage)
+    out[stage * words + core_off(m, 2 * kl, n) / 4] = pack2<BF16>(v.re * inv, v.im * inv);
+  }
+}
+
+template <bool BF16, int N>
+void launch_mma(mg_ctx* c, const Level& L, void* y, const void* x, int nrhs, cudaStream_t st) {
+  constexpr int KS = N;
+  const int smem = 2 * (128 * KS * 2) + 2 * (N * KS * 2);
+  auto kern = k_coarse_mma<BF16, N>;
+  GB_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  GB_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  // CTAs per SM from the kernel's own footprint: shared memory (dynamic +
+  // static + 1 KB reserved per CTA) and registers; TMEM allows 8 x 64 columns
+  int sms = 0, dev = 0, smem_sm = 0, regs_sm = 0;
+  GB_CHECK(cudaGetDevice(&dev));
+  GB_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  GB_CHECK(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  GB_CHECK(cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev));
+  cudaFuncAttributes fa;
+  GB_CHECK(cudaFuncGetAttributes(&fa, kern));
+  int per_sm = smem_sm / int(smem + fa.sharedSizeBytes + 1024);
+  const int by_regs = regs_sm / (((fa.numRegs + 7) / 8) * 8 * 128);
+  if (by_regs < per_sm) per_sm = by_regs;
+  if (per_sm > 8) per_sm = 8;
+  if (per_sm < 1) per_sm = 1;
+  int grid = sms * per_sm;
+  if (grid > L.g.vol) grid = L.g.vol;
+  kern<<<grid, 128, smem, st>>>((cpx<float>*)y, (const cpx<float>*)x, L.links_mma.as<uint4>(),
+                                L.scales.as<float>(), L.g, nrhs, c->status.as<int>() + 1);
+}
+
+}  // namespace
+
+bool coarse_apply_mma_supported(const Level& L, int nrhs) {
+  return (L.prec == MG_BF16 || L.prec == MG_F16) && L.links_mma.p && nrhs >= 2 && nrhs <= 64 &&
+         nrhs % 4 == 0 && (L.nd == 32 || L.nd == 48 || L.nd == 64);
+}
+
+void coarse_apply_mma(mg_ctx* c, int level, void* y, const void* x, int nrhs, cudaStream_t st) {
+  Level& L = c->L[level];
+  const bool bf16 = L.prec == MG_BF16;
+  switch (L.nd) {
+    case 32: bf16 ? launch_mma<true, 32>(c, L, y, x, nrhs, st) : launch_mma<false, 32>(c, L, y, x, nrhs, st); break;
+    case 48: bf16 ? launch_mma<true, 48>(c, L, y, x, nrhs, st) : launch_mma<false, 48>(c, L, y, x, nrhs, st); break;
+    default: bf16 ? launch_mma<true, 64>(c, L, y, x, nrhs, st) : launch_mma<false, 64>(c, L, y, x, nrhs, st); break;
+  }
+}
+
+void links_tile_mma(mg_ctx* c, int level, cudaStream_t st) {
+  Level& L = c->L[level];
+  if (!(L.prec == MG_BF16 || L.prec == MG_F16) || L.nd % 16) return;
+  const size_t total = size_t(L.g.vol) * 9 * L.nd * L.nd;
+  L.links_mma.alloc(total * 4);
+  int blocks = ceil_div(total, 256);
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (L.prec == MG_BF16)
+    k_links_tile_mma<true><<<blocks, 256, 0, st>>>(L.links_mma.as<uint32_t>(),
+                                                   L.links.as<cpx<float>>(), L.scales.as<float>(),
+                                                   L.g.vol, L.nd);
+  else
+    k_links_tile_mma<false><<<blocks, 256, 0, st>>>(L.links_mma.as<uint32_t>(),
+                                                    L.links.as<cpx<float>>(), L.scales.as<float>(),
+                                                    L.g.vol, L.nd);
+  GB_LAUNCH_CHECK();
+  c->launches++;
+}
+
+}  // namespace gbmg

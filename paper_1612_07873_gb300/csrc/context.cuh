@@ -81,13 +81,14 @@ struct Level {
   // coarse operator (level >= 1): internal layout [V][9][col][row] in vprec;
   // 16-bit store + per-site scale when prec is BF16/F16.
   DevBuf links, links16, scales;
+  DevBuf links_mma;            // 16-bit links tiled as the tensor-core operand
   bool have_op = false;
 
   // coarsening to level + 1
   int nvec = 0;
   int block[4] = {1, 1, 1, 1};
   DevBuf raw;                  // FP64 [Nv][V][nd] raw null vectors
-  DevBuf orth64;               // FP64 [Nv][V][nd] block-orthonormalised
+  DevBuf orth64;               // FP64 block-orthonormalised, [agg][chi][Nv][rows]
   DevBuf Vp;                   // vprec [V][nd][Nv] (transfer operator layout)
   bool have_raw = false, have_V = false;
 
@@ -115,6 +116,8 @@ struct mg_ctx {
   gbmg::DevBuf red_partials;   // [slots][max_blocks] double2
   gbmg::DevBuf scalars;        // [SC_COUNT] double2
   gbmg::DevBuf status;         // device status words (int)
+  gbmg::DevBuf batch_partials; // batched reductions: [nvec][2][blocks] double2
+  gbmg::DevBuf batch_scalars;  // batched reductions: [2 * 64] double2
   double* h_scalars = nullptr; // pinned host mirror
   // solver workspace (allocated on first solve)
   struct SolverWS;

@@ -61,8 +61,11 @@ struct CoarseOp {
   const cpx<R>* links;  // [V][9][col][row]
 };
 
-// MAXO: output elements per thread (>= (2Nv)^2 / blockDim)
-template <typename R, typename Rout, typename Op, int MAXO>
+// MAXO: output elements per thread (>= (2Nv)^2 / blockDim).  TILE > 0: the
+// 256 threads form a 16 x 16 grid, thread (ty, tx) owning output rows
+// ty*TILE.. and columns tx*TILE.. (2Nv = 16 TILE, MAXO = TILE^2), so that a
+// shared-memory load of P(x) or T feeds TILE complex MACs.
+template <typename R, typename Rout, typename Op, int MAXO, int TILE>
 __global__ void __launch_bounds__(256) k_galerkin(Op op, const cpx<R>* __restrict__ Vp, AggGeom m,
                                                   int nf, int nv, cpx<Rout>* __restrict__ out) {
   extern __shared__ unsigned char smem_raw[];
@@ -148,27 +151,53 @@ __global__ void __launch_bounds__(256) k_galerkin(Op op, const cpx<R>* __restric
     __syncthreads();
 
     // acc[(s,i),(s',j)] += sum_{a in chi s} conj(P(x)[a][i]) T[a][(s',j)]
+    if constexpr (TILE > 0) {
+      const int r0 = (tid >> 4) * TILE, c0 = (tid & 15) * TILE;
+      const int s = r0 / nv, i0 = r0 - s * nv;
+      for (int a = s * halff; a < (s + 1) * halff; ++a) {
+        cpx<R> pv[TILE], tv[TILE];
 #pragma unroll
-    for (int k = 0; k < MAXO; ++k) {
-      const int o = tid + k * T;
-      if (o < n2 * n2) {
-        const int row = o / n2, col = o - row * n2;
-        const int s = row / nv, i = row - s * nv;
-        cpx<R> a_ = acc[k];
-        for (int a = s * halff; a < (s + 1) * halff; ++a)
-          cmac_conj(a_, sV[a * nv + i], sT[a * n2 + col]);
-        acc[k] = a_;
+        for (int u = 0; u < TILE; ++u) {
+          pv[u] = sV[a * nv + i0 + u];
+          tv[u] = sT[a * n2 + c0 + u];
+        }
+#pragma unroll
+        for (int u = 0; u < TILE; ++u)
+#pragma unroll
+          for (int w = 0; w < TILE; ++w) cmac_conj(acc[u * TILE + w], pv[u], tv[w]);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < MAXO; ++k) {
+        const int o = tid + k * T;
+        if (o < n2 * n2) {
+          const int row = o / n2, col = o - row * n2;
+          const int s = row / nv, i = row - s * nv;
+          cpx<R> a_ = acc[k];
+          for (int a = s * halff; a < (s + 1) * halff; ++a)
+            cmac_conj(a_, sV[a * nv + i], sT[a * n2 + col]);
+          acc[k] = a_;
+        }
       }
     }
   }
   // internal layout [xc][d][col][row]
   cpx<Rout>* dst = out + (size_t(xc) * 9 + d) * n2 * n2;
+  if constexpr (TILE > 0) {
+    const int r0 = (tid >> 4) * TILE, c0 = (tid & 15) * TILE;
 #pragma unroll
-  for (int k = 0; k < MAXO; ++k) {
-    const int o = tid + k * T;
-    if (o < n2 * n2) {
-      const int row = o / n2, col = o - row * n2;
-      dst[size_t(col) * n2 + row] = cpx<Rout>(acc[k]);
+    for (int u = 0; u < TILE; ++u)
+#pragma unroll
+      for (int w = 0; w < TILE; ++w)
+        dst[size_t(c0 + w) * n2 + r0 + u] = cpx<Rout>(acc[u * TILE + w]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < MAXO; ++k) {
+      const int o = tid + k * T;
+      if (o < n2 * n2) {
+        const int row = o / n2, col = o - row * n2;
+        dst[size_t(col) * n2 + row] = cpx<Rout>(acc[k]);
+      }
     }
   }
 }
@@ -185,14 +214,20 @@ void launch_galerkin(const Op& op, const cpx<R>* Vp, const AggGeom& m, int nf, i
     GB_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     kern<<<grid, 256, smem, st>>>(op, Vp, m, nf, nv, out);
   };
-  if (per_thread <= 4)
-    go(k_galerkin<R, Rout, Op, 4>);
+  if (n2 == 32)
+    go(k_galerkin<R, Rout, Op, 4, 2>);
+  else if (n2 == 48)
+    go(k_galerkin<R, Rout, Op, 9, 3>);
+  else if (n2 == 64)
+    go(k_galerkin<R, Rout, Op, 16, 4>);
+  else if (per_thread <= 4)
+    go(k_galerkin<R, Rout, Op, 4, 0>);
   else if (per_thread <= 9)
-    go(k_galerkin<R, Rout, Op, 9>);
+    go(k_galerkin<R, Rout, Op, 9, 0>);
   else if (per_thread <= 16)
-    go(k_galerkin<R, Rout, Op, 16>);
+    go(k_galerkin<R, Rout, Op, 16, 0>);
   else if (per_thread <= 36)
-    go(k_galerkin<R, Rout, Op, 36>);
+    go(k_galerkin<R, Rout, Op, 36, 0>);
   else
     throw Error(MG_ERR_ARG, "galerkin: too many null vectors (2Nv > 96)");
   GB_LAUNCH_CHECK();

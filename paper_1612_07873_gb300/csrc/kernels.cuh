@@ -23,8 +23,17 @@ void blas_axpy_slot(mg_ctx* c, Vec y, Vec x, int slot, double sign, cudaStream_t
 // out = b - ax
 void blas_sub(mg_ctx* c, Vec out, Vec b, Vec ax, cudaStream_t st);
 // S[slot] = <a, b> = sum conj(a) b ; S[slot].re = |a|^2
-void blas_dot(mg_ctx* c, Vec a, Vec b, int slot, cudaStream_t st);
-void blas_norm2(mg_ctx* c, Vec a, int slot, cudaStream_t st);
+// fp64_partials: per-thread partial sums in FP64 even for FP32 data (the
+// outer GCR's orthogonalisation); otherwise FP32 data sums per thread in FP32
+void blas_dot(mg_ctx* c, Vec a, Vec b, int slot, cudaStream_t st, bool fp64_partials = false);
+void blas_norm2(mg_ctx* c, Vec a, int slot, cudaStream_t st, bool fp64_partials = false);
+// nvec vectors of length p.n back to back: B[2v] = <p_v, r_v>, B[2v+1] = |p_v|^2
+// with B = ctx->batch_scalars
+void blas_dot2_batched(mg_ctx* c, Vec p, Vec r, int nvec, cudaStream_t st);
+// x_v -= (B[2v] / B[2v+1]) t_v
+void blas_sweep_update_batched(mg_ctx* c, Vec x, Vec t, int nvec, cudaStream_t st);
+// x_v /= |x_v|
+void blas_normalise_batched(mg_ctx* c, Vec x, int nvec, cudaStream_t st);
 // S[s_pr] = <p, r>, S[s_pp] = <p, p> in one pass
 void blas_dot2(mg_ctx* c, Vec p, Vec r, int s_pr, int s_pp, cudaStream_t st);
 // MR step: a = omega S[s_pr]/S[s_pp].re ; x += a r ; r -= a p
@@ -58,8 +67,15 @@ void links_import(mg_ctx* c, int level, const void* ext, cudaStream_t st);
 void links_export(mg_ctx* c, int level, void* ext, cudaStream_t st);
 void links_pack16(mg_ctx* c, int level, cudaStream_t st);
 
+// ---------------------------------------------------------------- coarse_mma.cu
+bool coarse_apply_mma_supported(const Level& L, int nrhs);
+void coarse_apply_mma(mg_ctx* c, int level, void* y, const void* x, int nrhs, cudaStream_t st);
+void links_tile_mma(mg_ctx* c, int level, cudaStream_t st);
+
 // ---------------------------------------------------------------- transfer.cu
 void block_orthonormalise(mg_ctx* c, int level, cudaStream_t st);
+// block-orthonormal null vectors of `level` into dst [Nv][V][nd] complex double
+void nullvecs_export(mg_ctx* c, int level, void* dst, cudaStream_t st);
 void restrict_apply(mg_ctx* c, int level, Vec coarse, Vec fine, cudaStream_t st);
 void prolong_apply(mg_ctx* c, int level, Vec fine, Vec coarse, cudaStream_t st);
 

@@ -156,11 +156,11 @@ GcrOut gcr(mg_ctx* c, int l, Vec x, Vec b, bool precond, double tol, int maxiter
       level_apply(c, l, Wk, Zk, st);
       for (int j = 0; j < k; ++j) {
         Vec Zj = vbuf(*w.Z[j], L.vprec, n), Wj = vbuf(*w.W[j], L.vprec, n);
-        blas_dot(c, Wj, Wk, slot(l, S_BETA), st);
+        blas_dot(c, Wj, Wk, slot(l, S_BETA), st, outer);
         blas_axpy_slot(c, Wk, Wj, slot(l, S_BETA), -1.0, st);
         blas_axpy_slot(c, Zk, Zj, slot(l, S_BETA), -1.0, st);
       }
-      blas_norm2(c, Wk, slot(l, S_NRM), st);
+      blas_norm2(c, Wk, slot(l, S_NRM), st, outer);
       blas_scale_invnorm(c, Wk, Zk, slot(l, S_NRM), st);
       blas_dot(c, Wk, r, slot(l, S_ALPHA), st);
       blas_gcr_update(c, x, r, Zk, Wk, slot(l, S_ALPHA), st);
@@ -236,40 +236,46 @@ void setup_sweeps(mg_ctx* c, int l, const void* init, cudaStream_t st) {
   Level& L = c->L[l];
   const int nv = L.nvec;
   const size_t n = L.vec_elems();
+  GB_REQUIRE(nv <= 64, MG_ERR_ARG, "setup: at most 64 null vectors");
   L.raw.alloc(size_t(nv) * n * 16);
+  // all nv vectors back to back: X[v] at offset v * n
   DevBuf xb, tb, qb;
-  xb.alloc(n * prec_bytes_complex(L.vprec));
-  tb.alloc(n * prec_bytes_complex(L.vprec));
-  qb.alloc(n * prec_bytes_complex(L.vprec));
-  Vec x = vbuf(xb, L.vprec, n), t = vbuf(tb, L.vprec, n), q = vbuf(qb, L.vprec, n);
-  const int s_qt = slot(l, S_PR), s_qq = slot(l, S_PP), s_n = slot(l, S_NRM);
-  for (int i = 0; i < nv; ++i) {
-    Vec out;
-    out.p = L.raw.as<double2>() + size_t(i) * n;
-    out.prec = MG_F64;
-    out.n = n;
-    if (init) {
-      Vec in;
-      in.p = (void*)((const double2*)init + size_t(i) * n);
-      in.prec = MG_F64;
-      in.n = n;
-      blas_copy(c, x, in, st);
-    } else {
-      blas_gaussian(c, x, c->p.seed + 0x9E3779B97F4A7C15ull * uint64_t(l + 1),
-                    uint64_t(i) * n, st);
-    }
-    // minimal-residual steps on A x = 0:  t = A x, q = A t,
-    // x <- x - (<q, t> / <q, q>) t
-    for (int k = 0; k < c->p.setup_sweeps; ++k) {
-      level_apply(c, l, t, x, st);
-      level_apply(c, l, q, t, st);
-      blas_dot2(c, q, t, s_qt, s_qq, st);
-      blas_sweep_update(c, x, t, s_qt, s_qq, st);
-    }
-    blas_norm2(c, x, s_n, st);
-    blas_normalise(c, x, s_n, st);
-    blas_copy(c, out, x, st);
+  const size_t bytes = size_t(nv) * n * prec_bytes_complex(L.vprec);
+  xb.alloc(bytes);
+  tb.alloc(bytes);
+  qb.alloc(bytes);
+  Vec X = vbuf(xb, L.vprec, n), T = vbuf(tb, L.vprec, n), Q = vbuf(qb, L.vprec, n);
+  Vec Xall = vbuf(xb, L.vprec, n * nv);
+  Vec raw = vbuf(L.raw, MG_F64, n * nv);
+  if (init) {
+    Vec in;
+    in.p = const_cast<void*>(init);
+    in.prec = MG_F64;
+    in.n = n * nv;
+    blas_copy(c, Xall, in, st);
+  } else {
+    // element (v, j) draws counter v * n + j
+    blas_gaussian(c, Xall, c->p.seed + 0x9E3779B97F4A7C15ull * uint64_t(l + 1), 0, st);
   }
+  auto apply_all = [&](Vec out, Vec in) {
+    if (l == 0) {
+      wilson_apply(c, out, in, nv, st);
+    } else {
+      const size_t vb = n * prec_bytes_complex(L.vprec);
+      for (int v = 0; v < nv; ++v)
+        coarse_apply(c, l, (char*)out.p + v * vb, (const char*)in.p + v * vb, 1, st);
+    }
+  };
+  // minimal-residual steps on A x = 0 for every vector at once:
+  //   t = A x,  q = A t,  x <- x - (<q, t> / <q, q>) t
+  for (int k = 0; k < c->p.setup_sweeps; ++k) {
+    apply_all(T, X);
+    apply_all(Q, T);
+    blas_dot2_batched(c, Q, T, nv, st);
+    blas_sweep_update_batched(c, X, T, nv, st);
+  }
+  blas_normalise_batched(c, X, nv, st);
+  blas_copy(c, raw, Xall, st);
   L.have_raw = true;
   L.have_V = false;
   GB_CHECK(cudaStreamSynchronize(st));

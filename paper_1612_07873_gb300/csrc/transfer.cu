@@ -90,12 +90,24 @@ __device__ __forceinline__ double2 blk_sum2(double2 v, double2* sh) {
   return r;
 }
 
-// One CTA per (aggregate, chirality) block of `rows` x nv, in place.
+// One CTA per (aggregate, chirality) block of `rows` x nv, in place, FP64.
+// Gram-Schmidt in column order with every projection step done twice.  The
+// projection of column i on the finished columns 0..i-1 is formed as one
+// classical step (all i coefficients reduced together) rather than i
+// sequential ones: the same Q in exact arithmetic, and with the second pass
+// as stable as the modified form, but with ~8 block barriers per column
+// instead of ~4i.
+constexpr int kQrMaxVec = 64;
+constexpr int kQrMaxWarps = 32;
+
 template <int RPT>
-__global__ void k_mgs(double2* __restrict__ W, int rows, int nv, int* status) {
+__global__ void k_block_qr(double2* __restrict__ W, int rows, int nv, int* status) {
   __shared__ double2 sh[32];
+  __shared__ double2 part[kQrMaxWarps][kQrMaxVec];
+  __shared__ double2 coef[kQrMaxVec];
   double2* B = W + size_t(blockIdx.x) * nv * rows;
   const int T = blockDim.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = T >> 5;
   // Frobenius norm of the block for the rank test
   double2 f = make_double2(0.0, 0.0);
   for (size_t k = threadIdx.x; k < size_t(nv) * rows; k += T) {
@@ -110,25 +122,55 @@ __global__ void k_mgs(double2* __restrict__ W, int rows, int nv, int* status) {
       int row = threadIdx.x + r * T;
       v[r] = row < rows ? B[size_t(i) * rows + row] : make_double2(0.0, 0.0);
     }
-    for (int pass = 0; pass < 2; ++pass) {
+    for (int pass = 0; pass < 2 && i > 0; ++pass) {
       for (int j = 0; j < i; ++j) {
         const double2* q = B + size_t(j) * rows;
         double2 d = make_double2(0.0, 0.0);
-        double2 qv[RPT];
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
           int row = threadIdx.x + r * T;
-          qv[r] = row < rows ? q[row] : make_double2(0.0, 0.0);
-          d.x += qv[r].x * v[r].x + qv[r].y * v[r].y;
-          d.y += qv[r].x * v[r].y - qv[r].y * v[r].x;
+          if (row < rows) {
+            // d += conj(q) v, four FP64 FMAs (the FP64 pipe bounds this kernel)
+            double2 qv = q[row];
+            d.x = fma(qv.x, v[r].x, d.x);
+            d.x = fma(qv.y, v[r].y, d.x);
+            d.y = fma(qv.x, v[r].y, d.y);
+            d.y = fma(-qv.y, v[r].x, d.y);
+          }
         }
-        d = blk_sum2(d, sh);
+        for (int o = 16; o > 0; o >>= 1) {
+          d.x += __shfl_xor_sync(0xffffffffu, d.x, o);
+          d.y += __shfl_xor_sync(0xffffffffu, d.y, o);
+        }
+        if (lane == 0) part[warp][j] = d;
+      }
+      __syncthreads();
+      if (threadIdx.x < i) {
+        double2 c = make_double2(0.0, 0.0);
+        for (int w = 0; w < nw; ++w) {
+          c.x += part[w][threadIdx.x].x;
+          c.y += part[w][threadIdx.x].y;
+        }
+        coef[threadIdx.x] = c;
+      }
+      __syncthreads();
+      for (int j = 0; j < i; ++j) {
+        const double2* q = B + size_t(j) * rows;
+        const double2 c = coef[j];
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
-          v[r].x -= d.x * qv[r].x - d.y * qv[r].y;
-          v[r].y -= d.x * qv[r].y + d.y * qv[r].x;
+          int row = threadIdx.x + r * T;
+          if (row < rows) {
+            // v -= c q, four FP64 FMAs
+            double2 qv = q[row];
+            v[r].x = fma(-c.x, qv.x, v[r].x);
+            v[r].x = fma(c.y, qv.y, v[r].x);
+            v[r].y = fma(-c.x, qv.y, v[r].y);
+            v[r].y = fma(-c.y, qv.x, v[r].y);
+          }
         }
       }
+      __syncthreads();  // coef / part are rewritten by the next pass
     }
     double2 nn = make_double2(0.0, 0.0);
 #pragma unroll
@@ -149,10 +191,30 @@ __global__ void k_mgs(double2* __restrict__ W, int rows, int nv, int* status) {
   }
 }
 
-// W -> orth64 [Nv][V][nd] (FP64) and Vp [V][nd][Nv] (R)
+// QR of every (aggregate, chirality) block of W; false if a block is too tall.
+bool launch_block_qr(double2* W, int rows, int nv, int nblk, int* status, cudaStream_t st) {
+  const int threads = rows <= 256 * 16 ? 256 : 1024;
+  const int rpt = (rows + threads - 1) / threads;
+  if (rpt > 24 || nv > kQrMaxVec) return false;
+  if (rpt <= 1)
+    k_block_qr<1><<<nblk, threads, 0, st>>>(W, rows, nv, status);
+  else if (rpt <= 2)
+    k_block_qr<2><<<nblk, threads, 0, st>>>(W, rows, nv, status);
+  else if (rpt <= 4)
+    k_block_qr<4><<<nblk, threads, 0, st>>>(W, rows, nv, status);
+  else if (rpt <= 8)
+    k_block_qr<8><<<nblk, threads, 0, st>>>(W, rows, nv, status);
+  else if (rpt <= 16)
+    k_block_qr<16><<<nblk, threads, 0, st>>>(W, rows, nv, status);
+  else
+    k_block_qr<24><<<nblk, threads, 0, st>>>(W, rows, nv, status);
+  return true;
+}
+
+// W -> Vp [V][nd][Nv] (R)
 template <typename R>
-__global__ void k_mgs_scatter(double2* __restrict__ orth, cpx<R>* __restrict__ Vp,
-                              const double2* __restrict__ W, AggMap m, int nd, int nv) {
+__global__ void k_mgs_scatter(cpx<R>* __restrict__ Vp, const double2* __restrict__ W, AggMap m,
+                              int nd, int nv) {
   const int half = nd / 2;
   const int rows = m.per * half;
   size_t total = size_t(nv) * m.fine.vol * nd;
@@ -169,7 +231,6 @@ __global__ void k_mgs_scatter(double2* __restrict__ orth, cpx<R>* __restrict__ V
     int chi = a / half, ad = a - chi * half;
     double2 v = W[((size_t(ag) * 2 + chi) * nv + i) * rows + size_t(ls) * half + ad];
     Vp[idx] = cpx<R>(R(v.x), R(v.y));
-    orth[(size_t(i) * m.fine.vol + s) * nd + a] = v;
   }
 }
 
@@ -229,6 +290,26 @@ __global__ void k_prolong(cpx<Rf>* __restrict__ fine, const cpx<Rc>* __restrict_
   }
 }
 
+// W [agg][chi][Nv][rows] -> out [Nv][V][nd] (FP64)
+__global__ void k_blocked_to_vectors(double2* __restrict__ out, const double2* __restrict__ W,
+                                  AggMap m, int nd, int nv) {
+  const int half = nd / 2;
+  const int rows = m.per * half;
+  size_t total = size_t(nv) * m.fine.vol * nd;
+  for (size_t idx = blockIdx.x * size_t(blockDim.x) + threadIdx.x; idx < total;
+       idx += size_t(gridDim.x) * blockDim.x) {
+    int a = int(idx % nd);
+    size_t t = idx / nd;
+    int s = int(t % m.fine.vol);
+    int i = int(t / m.fine.vol);
+    int c[4];
+    site_coords(m.fine, s, c);
+    int ag = agg_of(m, c), ls = local_of(m, c);
+    int chi = a / half, ad = a - chi * half;
+    out[idx] = W[((size_t(ag) * 2 + chi) * nv + i) * rows + size_t(ls) * half + ad];
+  }
+}
+
 int grid_for(size_t n) {
   long long b = (long long)((n + 255) / 256);
   if (b > 152 * 32) b = 152 * 32;
@@ -245,38 +326,24 @@ void block_orthonormalise(mg_ctx* c, int level, cudaStream_t st) {
   AggMap m = make_map(F, C);
   const int rows = m.per * nd / 2;
   const size_t elems = size_t(nv) * F.g.vol * nd;
-  DevBuf W;
-  W.alloc(elems * sizeof(double2));
+  // the orthonormal vectors are kept in the aggregate-blocked layout
+  // [agg][chi][Nv][rows] in which the QR runs in place
   F.orth64.alloc(elems * sizeof(double2));
   F.Vp.alloc(elems * prec_bytes_complex(F.vprec));
+  double2* W = F.orth64.as<double2>();
   clear_status(c, st);
-  k_mgs_gather<<<grid_for(elems), 256, 0, st>>>(W.as<double2>(), F.raw.as<double2>(), m, nd, nv);
+  k_mgs_gather<<<grid_for(elems), 256, 0, st>>>(W, F.raw.as<double2>(), m, nd, nv);
   GB_LAUNCH_CHECK();
-  int threads = rows <= 256 * 16 ? 256 : 1024;
-  int rpt = (rows + threads - 1) / threads;
-  GB_REQUIRE(rpt <= 24, MG_ERR_ARG, "aggregate block too large (rows > 24576)");
   const int nblk = C.g.vol * 2;
   ProfScope ps(c->prof, st, "block_orth", level, double(elems) * 16.0 * 2,
                8.0 * nv * (nv - 1) * 2.0 * rows * nblk);
-  if (rpt <= 1)
-    k_mgs<1><<<nblk, threads, 0, st>>>(W.as<double2>(), rows, nv, c->status.as<int>());
-  else if (rpt <= 2)
-    k_mgs<2><<<nblk, threads, 0, st>>>(W.as<double2>(), rows, nv, c->status.as<int>());
-  else if (rpt <= 4)
-    k_mgs<4><<<nblk, threads, 0, st>>>(W.as<double2>(), rows, nv, c->status.as<int>());
-  else if (rpt <= 8)
-    k_mgs<8><<<nblk, threads, 0, st>>>(W.as<double2>(), rows, nv, c->status.as<int>());
-  else if (rpt <= 16)
-    k_mgs<16><<<nblk, threads, 0, st>>>(W.as<double2>(), rows, nv, c->status.as<int>());
-  else
-    k_mgs<24><<<nblk, threads, 0, st>>>(W.as<double2>(), rows, nv, c->status.as<int>());
+  GB_REQUIRE(launch_block_qr(W, rows, nv, nblk, c->status.as<int>(), st),
+             MG_ERR_ARG, "aggregate block too large (rows > 24576 or nvec > 64)");
   GB_LAUNCH_CHECK();
   if (F.vprec == MG_F64)
-    k_mgs_scatter<double><<<grid_for(elems), 256, 0, st>>>(
-        F.orth64.as<double2>(), F.Vp.as<cpx<double>>(), W.as<double2>(), m, nd, nv);
+    k_mgs_scatter<double><<<grid_for(elems), 256, 0, st>>>(F.Vp.as<cpx<double>>(), W, m, nd, nv);
   else
-    k_mgs_scatter<float><<<grid_for(elems), 256, 0, st>>>(
-        F.orth64.as<double2>(), F.Vp.as<cpx<float>>(), W.as<double2>(), m, nd, nv);
+    k_mgs_scatter<float><<<grid_for(elems), 256, 0, st>>>(F.Vp.as<cpx<float>>(), W, m, nd, nv);
   GB_LAUNCH_CHECK();
   c->launches += 3;
   if (read_status(c, st) & 1) {
@@ -350,6 +417,18 @@ void prolong_apply(mg_ctx* c, int level, Vec fine, Vec coarse, cudaStream_t st) 
   c->launches++;
 }
 
+void nullvecs_export(mg_ctx* c, int level, void* dst, cudaStream_t st) {
+  Level& F = c->L[level];
+  Level& C = c->L[level + 1];
+  GB_REQUIRE(F.have_V, MG_ERR_STATE, "get_nullvecs: not available");
+  AggMap m = make_map(F, C);
+  const size_t elems = size_t(F.nvec) * F.g.vol * F.nd;
+  k_blocked_to_vectors<<<grid_for(elems), 256, 0, st>>>((double2*)dst, F.orth64.as<double2>(), m,
+                                                       F.nd, F.nvec);
+  GB_LAUNCH_CHECK();
+  c->launches++;
+}
+
 // ---------------------------------------------------------------------------
 // Block orthonormalisation without device allocation.
 //
@@ -377,25 +456,6 @@ constexpr int kNoAllocMaxDevices = 64;
 NoAllocSlot g_noalloc_slots[kNoAllocMaxDevices];
 std::mutex g_noalloc_mutex;
 
-// W [agg][chi][Nv][rows] -> out [Nv][V][nd] (FP64)
-__global__ void k_noalloc_scatter(double2* __restrict__ out, const double2* __restrict__ W,
-                                  AggMap m, int nd, int nv) {
-  const int half = nd / 2;
-  const int rows = m.per * half;
-  size_t total = size_t(nv) * m.fine.vol * nd;
-  for (size_t idx = blockIdx.x * size_t(blockDim.x) + threadIdx.x; idx < total;
-       idx += size_t(gridDim.x) * blockDim.x) {
-    int a = int(idx % nd);
-    size_t t = idx / nd;
-    int s = int(t % m.fine.vol);
-    int i = int(t / m.fine.vol);
-    int c[4];
-    site_coords(m.fine, s, c);
-    int ag = agg_of(m, c), ls = local_of(m, c);
-    int chi = a / half, ad = a - chi * half;
-    out[idx] = W[((size_t(ag) * 2 + chi) * nv + i) * rows + size_t(ls) * half + ad];
-  }
-}
 
 }  // namespace
 
@@ -462,19 +522,8 @@ extern "C" mg_status mg_block_orthonormalise_noalloc(const void* vecs_dev, void*
   k_mgs_gather<<<grid_for(elems), 256, 0, st>>>(slot.scratch, (const double2*)vecs_dev, m, ndof,
                                                 nvec);
   const int nblk = m.coarse.vol * 2;
-  if (rpt <= 1)
-    k_mgs<1><<<nblk, threads, 0, st>>>(slot.scratch, rows, nvec, slot.status);
-  else if (rpt <= 2)
-    k_mgs<2><<<nblk, threads, 0, st>>>(slot.scratch, rows, nvec, slot.status);
-  else if (rpt <= 4)
-    k_mgs<4><<<nblk, threads, 0, st>>>(slot.scratch, rows, nvec, slot.status);
-  else if (rpt <= 8)
-    k_mgs<8><<<nblk, threads, 0, st>>>(slot.scratch, rows, nvec, slot.status);
-  else if (rpt <= 16)
-    k_mgs<16><<<nblk, threads, 0, st>>>(slot.scratch, rows, nvec, slot.status);
-  else
-    k_mgs<24><<<nblk, threads, 0, st>>>(slot.scratch, rows, nvec, slot.status);
-  k_noalloc_scatter<<<grid_for(elems), 256, 0, st>>>((double2*)out_dev, slot.scratch, m, ndof,
+  launch_block_qr(slot.scratch, rows, nvec, nblk, slot.status, st);
+  k_blocked_to_vectors<<<grid_for(elems), 256, 0, st>>>((double2*)out_dev, slot.scratch, m, ndof,
                                                      nvec);
   if (cudaGetLastError() != cudaSuccess) return fail(MG_ERR_CUDA, "noalloc: kernel launch failed");
   int h = 0;

@@ -156,29 +156,55 @@ __global__ void k_clover(const cpx<double>* __restrict__ U, Geom g, double csw,
 template <typename R>
 __global__ void __launch_bounds__(128) k_wilson(cpx<R>* __restrict__ out, const cpx<R>* __restrict__ in,
                                                 const cpx<R>* __restrict__ U, const R* __restrict__ A,
-                                                Geom g, R diag, size_t vstride) {
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
+                                                Geom g, R diag, size_t vstride, int nvec) {
+  // CTAs are ordered vector-fastest: the nvec CTAs of one site chunk run
+  // close together, so the chunk's links and clover come from DRAM once and
+  // from L2 for the other vectors.
+  const int vec = blockIdx.x % nvec;
+  int s = (blockIdx.x / nvec) * blockDim.x + threadIdx.x;
   if (s >= g.vol) return;
-  in += blockIdx.y * vstride;
-  out += blockIdx.y * vstride;
+  in += vec * vstride;
+  out += vec * vstride;
   int c[4];
   site_coords(g, s, c);
-  cpx<R> psi[12], acc[12];
+  cpx<R> psi[12], acc[12], u[9];
+  // 16-byte vector loads of the 96 B (FP32) / 192 B (FP64) spinor records and
+  // of the clover record; links (72 B / 144 B records) by complex number
+  auto load_spinor = [&](int site) {
+    const uint4* p = reinterpret_cast<const uint4*>(in + size_t(site) * 12);
+    constexpr int W = sizeof(cpx<R>) * 12 / 16;
+    uint4 w[W];
 #pragma unroll
-  for (int i = 0; i < 12; ++i) {
-    psi[i] = in[size_t(s) * 12 + i];
-    acc[i] = cpx<R>(R(0), R(0));
+    for (int i = 0; i < W; ++i) w[i] = __ldg(p + i);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) psi[i] = reinterpret_cast<const cpx<R>*>(w)[i];
+  };
+  auto load_link = [&](size_t idx) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) u[i] = U[idx * 9 + i];
+  };
+  load_spinor(s);
+#pragma unroll
+  for (int i = 0; i < 12; ++i) acc[i] = cpx<R>(R(0), R(0));
+  {
+    constexpr int W = sizeof(R) * 72 / 16;
+    uint4 w[W];
+    const uint4* p = reinterpret_cast<const uint4*>(A + size_t(s) * 72);
+#pragma unroll
+    for (int i = 0; i < W; ++i) w[i] = __ldg(p + i);
+    clover_accum(reinterpret_cast<const R*>(w), diag, psi, acc);
   }
-  clover_accum(A + size_t(s) * 72, diag, psi, acc);
   const size_t V = g.vol;
-#define GB_HOP(MU)                                                                  \
-  {                                                                                 \
-    int sf = neighbour(g, s, c, 1 + 2 * MU);                                        \
-    _Pragma("unroll") for (int i = 0; i < 12; ++i) psi[i] = in[size_t(sf) * 12 + i]; \
-    hop_accum<MU, true>(U + (MU * V + s) * 9, psi, acc);                            \
-    int sb = neighbour(g, s, c, 2 + 2 * MU);                                        \
-    _Pragma("unroll") for (int i = 0; i < 12; ++i) psi[i] = in[size_t(sb) * 12 + i]; \
-    hop_accum<MU, false>(U + (MU * V + sb) * 9, psi, acc);                          \
+#define GB_HOP(MU)                                       \
+  {                                                      \
+    int sf = neighbour(g, s, c, 1 + 2 * MU);             \
+    load_spinor(sf);                                     \
+    load_link(MU * V + s);                               \
+    hop_accum<MU, true>(u, psi, acc);                    \
+    int sb = neighbour(g, s, c, 2 + 2 * MU);             \
+    load_spinor(sb);                                     \
+    load_link(MU * V + sb);                              \
+    hop_accum<MU, false>(u, psi, acc);                   \
   }
   GB_HOP(0) GB_HOP(1) GB_HOP(2) GB_HOP(3)
 #undef GB_HOP
@@ -217,20 +243,22 @@ void wilson_apply(mg_ctx* c, Vec out, Vec in, int nvec, cudaStream_t st) {
   GB_REQUIRE(out.prec == in.prec, MG_ERR_ARG, "wilson_apply: precision mismatch");
   GB_REQUIRE(out.p != in.p, MG_ERR_ARG, "wilson_apply: output aliases input");
   const size_t vs = size_t(L.g.vol) * 12;
-  dim3 grid(ceil_div(L.g.vol, 128), nvec);
-  // algorithmic bytes per site: spinor in + out (2 x 24 reals), four links
-  // (4 x 18 reals: each link serves two sites), clover (72 reals)
-  const double bytes = double(nvec) * L.g.vol * 192.0 * (out.prec == MG_F64 ? 8 : 4);
+  dim3 grid(ceil_div(L.g.vol, 128) * nvec);
+  // algorithmic bytes per site: spinor in + out (2 x 24 reals) per vector,
+  // four links (4 x 18 reals: each link serves two sites) and the clover
+  // (72 reals) once for all vectors
+  const double bytes =
+      double(L.g.vol) * (48.0 * nvec + 144.0) * (out.prec == MG_F64 ? 8 : 4);
   ProfScope ps(c->prof, st, "wilson_clover", 0, bytes, double(nvec) * L.g.vol * 1824.0);
   if (out.prec == MG_F64) {
     k_wilson<double><<<grid, 128, 0, st>>>((cpx<double>*)out.p, (const cpx<double>*)in.p,
                                            L.gauge64.as<cpx<double>>(), L.clover64.as<double>(),
-                                           L.g, L.diag, vs);
+                                           L.g, L.diag, vs, nvec);
   } else {
     GB_REQUIRE(L.gauge32.p, MG_ERR_STATE, "FP32 fine operator not built");
     k_wilson<float><<<grid, 128, 0, st>>>((cpx<float>*)out.p, (const cpx<float>*)in.p,
                                           L.gauge32.as<cpx<float>>(), L.clover32.as<float>(),
-                                          L.g, float(L.diag), vs);
+                                          L.g, float(L.diag), vs, nvec);
   }
   GB_LAUNCH_CHECK();
   c->launches++;

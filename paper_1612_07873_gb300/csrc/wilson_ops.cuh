@@ -140,4 +140,21 @@ __device__ __forceinline__ void clover_accum(const R* __restrict__ A, R diag, co
   }
 }
 
+// acc6 += (diag + A_chi) psi6 for one packed 6x6 Hermitian chirality block.
+template <typename R>
+__device__ __forceinline__ void clover_block_accum(const R* __restrict__ a, R diag,
+                                                   const cpx<R> in[6], cpx<R> out[6]) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i) out[i] += (diag + a[i]) * in[i];
+#pragma unroll
+  for (int i = 1; i < 6; ++i)
+#pragma unroll
+    for (int j = 0; j < i; ++j) {
+      int k = i * (i - 1) / 2 + j;
+      cpx<R> l(a[6 + 2 * k], a[7 + 2 * k]);
+      cmac(out[i], l, in[j]);
+      cmac_conj(out[j], l, in[i]);
+    }
+}
+
 }  // namespace gbmg
