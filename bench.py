@@ -209,7 +209,8 @@ def gpu_main(args):
                           nlevels=3, prec_fine=1, prec_coarse=prec_coarse,
                           setup_sweeps=w["sweeps"], t_antiperiodic=w["antiperiodic"],
                           seed=w["seed"] + 1000 * rank)
-    mg = gb.Multigrid(p, torch.from_numpy(U).to(dev))
+    gauge_dev = torch.from_numpy(U).to(dev)
+    mg = gb.Multigrid(p, gauge_dev)
     del U
     ctx = mg.ctx
     b = torch.from_numpy(b_host).to(dev)
@@ -304,6 +305,37 @@ def gpu_main(args):
            "d2h_bytes_per_step": yh.numel() * yh.element_size(),
            "ms_per_apply": e2e_ms}
 
+    # the 16-bit storage forms of the same problem: same gauge field, seeds
+    # and solver; setup untimed, s/solve over `nsolve` solves
+    forms = {}
+    if args.forms:
+        mg.close()
+        for fname, pc, slots in (("bf16", 2, 9), ("fp16", 3, 9), ("fp32_5blocks", 1, 5),
+                                 ("bf16_5blocks", 2, 5)):
+            if fname == form:
+                continue
+            pf = gb.default_params(dims=dims, block=blocks, nvec=nvecs, mass=w["mass"],
+                                   csw=w["csw"], nlevels=3, prec_fine=1, prec_coarse=pc,
+                                   setup_sweeps=w["sweeps"], t_antiperiodic=w["antiperiodic"],
+                                   seed=w["seed"] + 1000 * rank, link_slots=slots)
+            mf = gb.Multigrid(pf, gauge_dev)
+            t0 = ev()
+            t1 = ev()
+            t0.record(stream)
+            gb.mg_setup_nullvecs(mf.ctx, 0, None)
+            gb.mg_build_coarse(mf.ctx, 0)
+            gb.mg_setup_nullvecs(mf.ctx, 1, None)
+            gb.mg_build_coarse(mf.ctx, 1)
+            t1.record(stream)
+            xs = torch.zeros_like(b)
+            gb.mg_gcr_solve(mf.ctx, xs, b, 1e-10, 500)  # warm-up
+            sts = [gb.mg_gcr_solve(mf.ctx, xs, b, 1e-10, 500) for _ in range(3)]
+            torch.cuda.synchronize()
+            forms[fname] = {"s_per_solve_median": statistics.median(st["seconds"] for st in sts),
+                            "outer_iters": [st["iters"] for st in sts],
+                            "true_residual": max(st["true_residual"] for st in sts),
+                            "setup_ms": t0.elapsed_time(t1)}
+            mf.close()
     peak, peak_kind = peaks()
     solve_s = [s["seconds"] for s in stats]
     line = {
@@ -327,7 +359,8 @@ def gpu_main(args):
         "solve": {"s_per_solve_median": statistics.median(solve_s),
                   "outer_iters": [s["iters"] for s in stats],
                   "level_iters": stats[-1]["level_iters"],
-                  "true_residual": max(s["true_residual"] for s in stats)},
+                  "true_residual": max(s["true_residual"] for s in stats),
+                  "forms": forms},
         "phases_ms_median": dict(zip(["setup_l0", "build_l1", "setup_l1", "build_l2", "solve"],
                                      [float(v) for v in np.median(ph, axis=0)])),
         "kernels": {k: {"launches": v["launches"], "ms": v["ms"],
@@ -342,7 +375,8 @@ def gpu_main(args):
             line["cpu_baseline"] = {"error": str(e)}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    mg.close()
+    if mg.ctx is not None:
+        mg.close()
     if world > 1:
         dist.destroy_process_group()
     return 0
@@ -358,7 +392,7 @@ def coarse_apply_main(args):
     fine = (16, 16, 16, 32)
     U = syn.gauge_field(fine, 0.0, 1)
     p = gb.default_params(dims=fine, block=[(2, 2, 2, 2)], nvec=[24], nlevels=2, prec_fine=1,
-                          prec_coarse=prec)
+                          prec_coarse=prec, link_slots=args.slots)
     mg = gb.Multigrid(p, torch.from_numpy(U).cuda())
     l1 = mg.levels[1]
     vol, n = l1["volume"], l1["ndof"]
@@ -382,7 +416,8 @@ def coarse_apply_main(args):
     peak, kind = peaks()
     gbs = q["bytes"] / (q["ms"] * 1e-3) / 1e9
     tflops = q["flops"] / (q["ms"] * 1e-3) / 1e12
-    print(json.dumps({"mode": "coarse-apply", "form": args.form, "lattice": list(l1["dims"]),
+    print(json.dumps({"mode": "coarse-apply", "form": args.form, "slots": args.slots,
+                      "lattice": list(l1["dims"]),
                       "ndof": n, "nrhs": nrhs, "launches": q["launches"],
                       "us_per_apply": 1e3 * q["ms"] / q["launches"],
                       "gbs": gbs, "frac": gbs / peak, "peak": peak, "peak_kind": kind,
@@ -401,6 +436,10 @@ def main():
     ap.add_argument("--mode", default="pipeline", choices=["pipeline", "coarse-apply"])
     ap.add_argument("--fine", default="", help="override the fine extents, e.g. 16,16,16,32")
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides (coarse-apply mode)")
+    ap.add_argument("--slots", type=int, default=9, choices=[5, 9],
+                    help="coarse link blocks stored (coarse-apply mode)")
+    ap.add_argument("--no-forms", dest="forms", action="store_false",
+                    help="skip the 16-bit storage forms' s/solve")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_main(args)

@@ -97,6 +97,9 @@ typedef struct {
   int inner_maxiter;                /* intermediate-level GCR iteration cap (10)    */
   double coarse_tol;                /* coarsest-level GCR tolerance (0.1)           */
   int coarse_maxiter;               /* coarsest-level GCR iteration cap (100)       */
+  int link_slots;                   /* coarse link store: 9 (all blocks of Eq. 3) or
+                                       5 (X and Y_{+mu}; Y_{-mu}(x) is rebuilt as
+                                       g5 Y_{+mu}(x-mu)^dag g5 inside the apply) */
 } mg_params;
 
 typedef struct {
@@ -173,7 +176,10 @@ mg_status mg_gcr_solve(mg_ctx* ctx, void* x_dev, const void* b_dev, double tol, 
 
 /* Coarse links of level l >= 1 in the external layout (see top), complex
  * double, bytes = V_l * 9 * n_l^2 * 16.  set replaces the operator of the
- * level (for apply-only use), converting to prec_coarse.                   */
+ * level (for apply-only use), converting to prec_coarse.  With
+ * link_slots = 5 the apply uses only slots 0, 1, 3, 5, 7 and rebuilds the
+ * backward blocks, so set links should satisfy that relation (Galerkin
+ * links do).                                                               */
 mg_status mg_get_coarse_links(mg_ctx* ctx, int level, void* dst_dev, size_t bytes, void* stream);
 mg_status mg_set_coarse_links(mg_ctx* ctx, int level, const void* src_dev, size_t bytes,
                               void* stream);

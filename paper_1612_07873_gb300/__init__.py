@@ -47,6 +47,7 @@ class mg_params(C.Structure):
         ("inner_maxiter", C.c_int),
         ("coarse_tol", C.c_double),
         ("coarse_maxiter", C.c_int),
+        ("link_slots", C.c_int),
     ]
 
 

@@ -103,6 +103,7 @@ void mg_default_params(mg_params* p) {
   p->inner_maxiter = 10;
   p->coarse_tol = 0.1;
   p->coarse_maxiter = 100;
+  p->link_slots = 9;
 }
 
 mg_status mg_create(const mg_params* p, const void* gauge_dev, mg_ctx** out) {
@@ -153,6 +154,9 @@ mg_status mg_create(const mg_params* p, const void* gauge_dev, mg_ctx** out) {
         L.g = make_geom(cd);
         L.nd = 2 * F.nvec;
         L.prec = p->prec_coarse;
+        GB_REQUIRE(p->link_slots == 0 || p->link_slots == 9 || p->link_slots == 5, MG_ERR_ARG,
+                   "link_slots must be 9 or 5");
+        L.slots5 = p->link_slots == 5;
         GB_REQUIRE(!((L.prec == MG_BF16 || L.prec == MG_F16) && (L.nd % 4)), MG_ERR_ARG,
                    "16-bit coarse links need an even number of null vectors");
       }

@@ -268,6 +268,25 @@ __global__ void k_normalise_b(cpx<R>* __restrict__ x, size_t n, int nvec,
   }
 }
 
+// [nvec][n] <-> [n][nvec] layout change of complex vectors
+template <typename R>
+__global__ void k_transpose(cpx<R>* __restrict__ out, const cpx<R>* __restrict__ in, size_t n,
+                            int nvec, int to_interleaved) {
+  const size_t total = n * nvec;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < total;
+       i += size_t(gridDim.x) * blockDim.x) {
+    if (to_interleaved) {  // out[e][v] = in[v][e], i enumerates out
+      const size_t e = i / nvec;
+      const int v = int(i - e * nvec);
+      out[i] = in[size_t(v) * n + e];
+    } else {               // out[v][e] = in[e][v], i enumerates out
+      const int v = int(i / n);
+      const size_t e = i - size_t(v) * n;
+      out[i] = in[e * nvec + v];
+    }
+  }
+}
+
 // ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC11), used to draw the
 // random initial null-vector guesses on the device.
 __device__ __forceinline__ uint4 philox4x32_10(uint4 ctr, uint2 key) {
@@ -487,6 +506,15 @@ void blas_read_scalars(mg_ctx* c, int first, int count, double* out, cudaStream_
                            cudaMemcpyDeviceToHost, st));
   GB_CHECK(cudaStreamSynchronize(st));
   for (int i = 0; i < 2 * count; ++i) out[i] = c->h_scalars[i];
+}
+
+void blas_transpose(mg_ctx* c, Vec out, Vec in, int nvec, bool to_interleaved, cudaStream_t st) {
+  GB_REQUIRE(out.prec == in.prec && out.n == in.n, MG_ERR_ARG, "transpose: mismatch");
+  GB_DISPATCH1(out.prec, R,
+               (k_transpose<R><<<ew_blocks(out.n * nvec), kThreads, 0, st>>>(
+                   (cpx<R>*)out.p, (const cpx<R>*)in.p, out.n, nvec, to_interleaved ? 1 : 0)));
+  GB_LAUNCH_CHECK();
+  c->launches++;
 }
 
 void blas_gaussian(mg_ctx* c, Vec v, uint64_t seed, uint64_t offset, cudaStream_t st) {

@@ -18,6 +18,8 @@
 //  * the 9 gathered neighbour spinors sit in shared memory (9n complex).
 // 16-bit links carry one FP32 scale per site (value = scale * stored); the
 // arithmetic accumulates in FP32.
+#include <type_traits>
+
 #include "kernels.cuh"
 
 namespace gbmg {
@@ -132,6 +134,130 @@ __global__ void __launch_bounds__(CG*(N / Unpack<S>::RPC))
   }
 }
 
+// Five-block form (X and the four forward links stored): the backward
+// block is rebuilt from the -mu neighbour's forward link F = Y_{+mu}(x-mu),
+//   Y_{-mu}(x) v = g5 F^dag (g5 v),   g5 = diag(+1 on the first n/2 dofs, -1),
+// so its output row r is the dot product of the *stored column* r of F
+// (contiguous) with w = g5 v.  Forward terms stream as in k_coarse_stream
+// over K = 5n columns; backward terms: thread (part = t % TPC, column
+// group = t / TPC) reads chunk `part` of columns t/TPC + CG i and keeps N/CG
+// partial dot products, reduced over the TPC parts through shared memory.
+// The neighbour's forward block was (or will soon be) streamed by the
+// neighbour's own CTA, so most of these reads hit L2: HBM traffic is 5 of
+// the 9 blocks.  16-bit forms: each backward input is pre-scaled by the
+// neighbour's per-site scale.
+template <typename S, int N, int CG>
+__global__ void __launch_bounds__(CG*(N / Unpack<S>::RPC))
+    k_coarse_stream5(cpx<typename StoreTraits<S>::real>* __restrict__ y,
+                     const cpx<typename StoreTraits<S>::real>* __restrict__ x,
+                     const S* __restrict__ links5, const float* __restrict__ scales, Geom g) {
+  using R = typename StoreTraits<S>::real;
+  constexpr int RPC = Unpack<S>::RPC;
+  constexpr int TPC = N / RPC;
+  constexpr int K = 5 * N;
+  constexpr int NT = CG * TPC;
+  constexpr int ITER = K / CG;
+  constexpr int U = batch_of(ITER);
+  constexpr int CPT = N / CG;  // backward columns per thread
+  static_assert(N % RPC == 0 && K % CG == 0 && N % CG == 0, "tile shape");
+  __shared__ cpx<R> xs[K];          // forward inputs: x(site), x(site + mu)
+  __shared__ cpx<R> ws[4 * N];      // backward inputs: scale(site - mu) g5 x(site - mu)
+  __shared__ cpx<R> red[CG][N];
+  __shared__ cpx<R> redb[TPC][N];
+  __shared__ int nb[9];
+  const int site = blockIdx.x;
+  const int tid = threadIdx.x;
+  if (tid < 9) {
+    int c[4];
+    site_coords(g, site, c);
+    nb[tid] = neighbour(g, site, c, tid);
+  }
+  __syncthreads();
+  for (int i = tid; i < K; i += NT) {
+    const int q = i / N, col = i - q * N;  // q: 0 -> site, 1..4 -> +mu
+    const int slot = q == 0 ? 0 : 2 * q - 1;
+    xs[i] = x[size_t(nb[slot]) * N + col];
+  }
+  for (int i = tid; i < 4 * N; i += NT) {
+    const int mu = i / N, col = i - mu * N;
+    const int sb = nb[2 + 2 * mu];
+    R f = (col < N / 2) ? R(1) : R(-1);
+    if (StoreTraits<S>::scaled) f *= R(scales[sb]);
+    ws[i] = f * x[size_t(sb) * N + col];
+  }
+  __syncthreads();
+  const int rp = tid % TPC;
+  const int cg = tid / TPC;
+  // forward: X and Y_{+mu}(site)
+  cpx<R> acc[RPC];
+#pragma unroll
+  for (int r = 0; r < RPC; ++r) acc[r] = cpx<R>(R(0), R(0));
+  const uint4* L = reinterpret_cast<const uint4*>(links5) + size_t(site) * K * TPC + rp;
+  for (int it = 0; it < ITER; it += U) {
+    uint4 v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = ld_stream16(L + size_t(cg + (it + u) * CG) * TPC);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      cpx<R> e[RPC];
+      Unpack<S>::get(v[u], e);
+      cpx<R> xv = xs[cg + (it + u) * CG];
+#pragma unroll
+      for (int r = 0; r < RPC; ++r) cmac(acc[r], e[r], xv);
+    }
+  }
+  // backward: column dot products with the -mu neighbours' forward blocks
+  cpx<R> accb[CPT];
+#pragma unroll
+  for (int i = 0; i < CPT; ++i) accb[i] = cpx<R>(R(0), R(0));
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    const uint4* F = reinterpret_cast<const uint4*>(links5) +
+                     (size_t(nb[2 + 2 * mu]) * 5 + 1 + mu) * N * TPC + rp;
+    uint4 v[CPT];
+#pragma unroll
+    for (int i = 0; i < CPT; ++i) v[i] = __ldg(F + size_t(cg + CG * i) * TPC);
+#pragma unroll
+    for (int i = 0; i < CPT; ++i) {
+      cpx<R> e[RPC];
+      Unpack<S>::get(v[i], e);
+#pragma unroll
+      for (int r = 0; r < RPC; ++r) cmac_conj(accb[i], e[r], ws[mu * N + rp * RPC + r]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < RPC; ++r) red[cg][rp * RPC + r] = acc[r];
+#pragma unroll
+  for (int i = 0; i < CPT; ++i) redb[rp][cg + CG * i] = accb[i];
+  __syncthreads();
+  const R sc = StoreTraits<S>::scaled ? R(scales[site]) : R(1);
+  for (int row = tid; row < N; row += NT) {
+    cpx<R> f = red[0][row];
+#pragma unroll
+    for (int q = 1; q < CG; ++q) f += red[q][row];
+    cpx<R> b = redb[0][row];
+#pragma unroll
+    for (int q = 1; q < TPC; ++q) b += redb[q][row];
+    const R g5 = row < N / 2 ? R(1) : R(-1);
+    y[size_t(site) * N + row] = sc * f + g5 * b;
+  }
+}
+
+// [V][9][n][n] (any store type) -> [V][5][n][n]: slots 0, 1, 3, 5, 7
+template <typename S>
+__global__ void k_links_pick5(S* __restrict__ out, const S* __restrict__ in, int vol, int n) {
+  const size_t per = size_t(n) * n;
+  const size_t total = size_t(vol) * 5 * per;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < total;
+       i += size_t(gridDim.x) * blockDim.x) {
+    const size_t blk = i / per, e = i - blk * per;
+    const size_t site = blk / 5;
+    const int q = int(blk - site * 5);
+    const int slot = q == 0 ? 0 : 2 * q - 1;
+    out[i] = in[(site * 9 + slot) * per + e];
+  }
+}
+
 // Any n, any number of right-hand sides: one CTA per site, threads over
 // (row, rhs); links are read column-wise (coalesced over rows).
 template <typename S>
@@ -227,6 +353,30 @@ void launch_stream(const Level& L, void* y, const void* x, const void* links, cu
                                                     L.scales.as<float>(), L.g);
 }
 
+template <typename S, int N, int CG>
+void launch_stream5(const Level& L, void* y, const void* x, const void* links, cudaStream_t st) {
+  using R = typename StoreTraits<S>::real;
+  constexpr int NT = CG * (N / Unpack<S>::RPC);
+  k_coarse_stream5<S, N, CG><<<L.g.vol, NT, 0, st>>>((cpx<R>*)y, (const cpx<R>*)x,
+                                                     (const S*)links, L.scales.as<float>(), L.g);
+}
+
+template <typename S>
+bool try_stream5(const Level& L, void* y, const void* x, cudaStream_t st) {
+  // FP64 stores (parity runs) keep the nine-block kernel: the five-block
+  // form's reduction buffer would not fit its static shared memory
+  if (std::is_same<S, cpx<double>>::value) return false;
+  constexpr int RPC = Unpack<S>::RPC;
+  constexpr int CG = RPC == 1 ? 4 : (RPC == 2 ? 8 : 16);
+  const void* links = L.links5.p;
+  switch (L.nd) {
+    case 32: launch_stream5<S, 32, CG>(L, y, x, links, st); return true;
+    case 48: launch_stream5<S, 48, CG>(L, y, x, links, st); return true;
+    case 64: launch_stream5<S, 64, CG>(L, y, x, links, st); return true;
+    default: return false;
+  }
+}
+
 template <typename S>
 bool try_stream(const Level& L, void* y, const void* x, const void* links, cudaStream_t st) {
   constexpr int RPC = Unpack<S>::RPC;
@@ -244,6 +394,7 @@ template <typename S>
 void dispatch_apply(const Level& L, void* y, const void* x, const void* links, int nrhs,
                     cudaStream_t st) {
   using R = typename StoreTraits<S>::real;
+  if (nrhs == 1 && L.slots5 && L.links5.p && try_stream5<S>(L, y, x, st)) return;
   if (nrhs == 1 && try_stream<S>(L, y, x, links, st)) return;
   int threads = L.nd * nrhs >= 256 ? 256 : ((L.nd * nrhs + 31) / 32) * 32;
   k_coarse_generic<S><<<L.g.vol, threads, 0, st>>>((cpx<R>*)y, (const cpx<R>*)x, (const S*)links,
@@ -259,7 +410,10 @@ void coarse_apply(mg_ctx* c, int level, void* y, const void* x, int nrhs, cudaSt
   GB_REQUIRE(nrhs >= 1, MG_ERR_ARG, "coarse_apply: nrhs < 1");
   GB_REQUIRE(y != x, MG_ERR_ARG, "coarse_apply: output aliases input");
   const double n = L.nd;
-  const double lbytes = double(L.g.vol) * 9 * n * n * (L.prec == MG_F64 ? 16 : L.prec == MG_F32 ? 8 : 4);
+  const bool five = L.slots5 && L.links5.p && nrhs == 1 && L.prec != MG_F64 &&
+                    (L.nd == 32 || L.nd == 48 || L.nd == 64);
+  const double lbytes = double(L.g.vol) * (five ? 5 : 9) * n * n *
+                        (L.prec == MG_F64 ? 16 : L.prec == MG_F32 ? 8 : 4);
   const double vbytes = double(L.g.vol) * 2 * n * nrhs * (L.vprec == MG_F64 ? 16 : 8);
   ProfScope ps(c->prof, st, "coarse_apply", level, lbytes + vbytes,
                8.0 * 9 * n * n * L.g.vol * nrhs);
@@ -279,9 +433,39 @@ void coarse_apply(mg_ctx* c, int level, void* y, const void* x, int nrhs, cudaSt
   c->launches++;
 }
 
+void links_pick5(mg_ctx* c, int level, cudaStream_t st) {
+  Level& L = c->L[level];
+  if (!L.slots5) return;
+  const size_t total = size_t(L.g.vol) * 5 * L.nd * L.nd;
+  int blocks = ceil_div(total, 256);
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  switch (L.prec) {
+    case MG_F64:
+      L.links5.alloc(total * 16);
+      k_links_pick5<cpx<double>><<<blocks, 256, 0, st>>>(L.links5.as<cpx<double>>(),
+                                                         L.links.as<cpx<double>>(), L.g.vol, L.nd);
+      break;
+    case MG_F32:
+      L.links5.alloc(total * 8);
+      k_links_pick5<cpx<float>><<<blocks, 256, 0, st>>>(L.links5.as<cpx<float>>(),
+                                                        L.links.as<cpx<float>>(), L.g.vol, L.nd);
+      break;
+    default:
+      L.links5.alloc(total * 4);
+      k_links_pick5<bf16c><<<blocks, 256, 0, st>>>(L.links5.as<bf16c>(), L.links16.as<bf16c>(),
+                                                   L.g.vol, L.nd);
+      break;
+  }
+  GB_LAUNCH_CHECK();
+  c->launches++;
+}
+
 void links_pack16(mg_ctx* c, int level, cudaStream_t st) {
   Level& L = c->L[level];
-  if (L.prec != MG_BF16 && L.prec != MG_F16) return;
+  if (L.prec != MG_BF16 && L.prec != MG_F16) {
+    links_pick5(c, level, st);
+    return;
+  }
   const size_t per = size_t(9) * L.nd * L.nd;
   L.links16.alloc(per * L.g.vol * 4);
   L.scales.alloc(size_t(L.g.vol) * sizeof(float));
@@ -294,6 +478,7 @@ void links_pack16(mg_ctx* c, int level, cudaStream_t st) {
   GB_LAUNCH_CHECK();
   c->launches++;
   links_tile_mma(c, level, st);
+  links_pick5(c, level, st);
 }
 
 void links_import(mg_ctx* c, int level, const void* ext, cudaStream_t st) {

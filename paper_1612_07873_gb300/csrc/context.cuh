@@ -82,6 +82,8 @@ struct Level {
   // 16-bit store + per-site scale when prec is BF16/F16.
   DevBuf links, links16, scales;
   DevBuf links_mma;            // 16-bit links tiled as the tensor-core operand
+  bool slots5 = false;         // single-RHS apply from 5 stored blocks
+  DevBuf links5;               // [V][5][col][row]: slots 0, 1, 3, 5, 7 in the store type
   bool have_op = false;
 
   // coarsening to level + 1

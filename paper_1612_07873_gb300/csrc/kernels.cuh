@@ -47,6 +47,8 @@ void blas_gcr_update(mg_ctx* c, Vec x, Vec r, Vec z, Vec w, int slot, cudaStream
 void blas_sweep_update(mg_ctx* c, Vec x, Vec t, int s_qt, int s_qq, cudaStream_t st);
 // copy slot values to the host (synchronises st)
 void blas_read_scalars(mg_ctx* c, int first, int count, double* out_re_im, cudaStream_t st);
+// nvec vectors of out.n elements: [nvec][n] -> [n][nvec] (to_interleaved) or back
+void blas_transpose(mg_ctx* c, Vec out, Vec in, int nvec, bool to_interleaved, cudaStream_t st);
 // complex Gaussian (Re, Im iid N(0,1)) from a counter-based Philox4x32-10
 void blas_gaussian(mg_ctx* c, Vec v, uint64_t seed, uint64_t offset, cudaStream_t st);
 // x /= sqrt(S[slot].re)

@@ -257,9 +257,22 @@ void setup_sweeps(mg_ctx* c, int l, const void* init, cudaStream_t st) {
     // element (v, j) draws counter v * n + j
     blas_gaussian(c, Xall, c->p.seed + 0x9E3779B97F4A7C15ull * uint64_t(l + 1), 0, st);
   }
+  // 16-bit coarse levels apply the operator to all vectors at once on the
+  // tensor cores (interleaved [site][dof][vec] operand layout)
+  DevBuf ib, ob;
+  const bool mrhs = l > 0 && coarse_apply_mma_supported(L, nv);
+  if (mrhs) {
+    ib.alloc(bytes);
+    ob.alloc(bytes);
+  }
   auto apply_all = [&](Vec out, Vec in) {
     if (l == 0) {
       wilson_apply(c, out, in, nv, st);
+    } else if (mrhs) {
+      Vec vi = vbuf(ib, L.vprec, n), vo = vbuf(ob, L.vprec, n);
+      blas_transpose(c, vi, in, nv, true, st);
+      coarse_apply(c, l, vo.p, vi.p, nv, st);
+      blas_transpose(c, out, vo, nv, false, st);
     } else {
       const size_t vb = n * prec_bytes_complex(L.vprec);
       for (int v = 0; v < nv; ++v)
