@@ -179,6 +179,53 @@ def reference_main(args):
     return 0
 
 
+# ---------------------------------------------------------------- learned setup
+def run_learned(args, gb, torch, ev, stream, dev):
+    """Train the null-vector proposer on the plain setup's vectors of
+    `ntrain` 16^4 fields (eps uniform in [0.5, 0.6]) and compare, on a
+    held-out field of the production shape (32^3x64, eps 0.55), the 3-level
+    MG after the plain setup (Gaussian starts, 10 sweeps) with the MG after
+    learned starts and k sweeps.  Mass -0.90: near critical for these fields
+    (at -0.40 the MG iteration count does not depend on the setup)."""
+    from paper_1612_07873_gb300 import learned
+    mass, nv, tdims, tblock = -0.90, 24, (16, 16, 16, 16), (4, 4, 4, 4)
+    t0 = time.perf_counter()
+    samples = []
+    for s in range(args.learned_ntrain):
+        eps = 0.5 + 0.1 * np.random.default_rng(1000 + s).random()
+        U = torch.from_numpy(syn.gauge_field(tdims, eps, 1000 + s)).to(dev)
+        samples.append((tdims, U, learned.plain_vectors(U, tdims, tblock, nv, mass, 1.0, 10,
+                                                        5000 + s)))
+    t_targets = time.perf_counter() - t0
+    P = learned.Proposer(nv, seed=3)
+    t0 = time.perf_counter()
+    hist = P.train(samples, tblock, epochs=args.learned_epochs, lr=2e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del samples
+    w = syn.WORKLOADS[WORKLOAD]
+    dims = w["dims"]
+    Ue = torch.from_numpy(syn.gauge_field(dims, 0.55, 2000)).to(dev)
+    prop = P.propose(dims, Ue)
+    b = torch.from_numpy(syn.gaussian_field((syn.volume(dims), 12), 5, stream=99)).to(dev)
+    p3 = gb.default_params(dims=dims, block=w["block"], nvec=w["nvec"], mass=mass, csw=1.0,
+                           nlevels=3, prec_fine=1, prec_coarse=1, seed=9000)
+    plain = learned.mg_iterations(p3, Ue, None, 10, b)
+    rows = []
+    for k in (0, 2, 5):
+        st = learned.mg_iterations(p3, Ue, prop, k, b)
+        rows.append({"sweeps": k, "outer_iters": st["iters"], "s_per_solve": st["seconds"],
+                     "true_residual": st["true_residual"]})
+    saved = [10 - r["sweeps"] for r in rows if r["outer_iters"] <= plain["iters"]]
+    P.close()
+    return {"mass": mass, "train_fields": args.learned_ntrain, "train_lattice": list(tdims),
+            "epochs": args.learned_epochs, "targets_s": t_targets, "train_s": t_train,
+            "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1],
+            "eval_lattice": list(dims),
+            "plain": {"sweeps": 10, "outer_iters": plain["iters"], "s_per_solve": plain["seconds"]},
+            "learned": rows, "setup_sweeps_saved": max(saved) if saved else 0}
+
+
 # ---------------------------------------------------------------- GPU leg
 def gpu_main(args):
     import torch
@@ -336,6 +383,7 @@ def gpu_main(args):
                             "true_residual": max(st["true_residual"] for st in sts),
                             "setup_ms": t0.elapsed_time(t1)}
             mf.close()
+    learned_setup = run_learned(args, gb, torch, ev, stream, dev) if args.learned else None
     peak, peak_kind = peaks()
     solve_s = [s["seconds"] for s in stats]
     line = {
@@ -361,6 +409,7 @@ def gpu_main(args):
                   "level_iters": stats[-1]["level_iters"],
                   "true_residual": max(s["true_residual"] for s in stats),
                   "forms": forms},
+        "learned_setup": learned_setup,
         "phases_ms_median": dict(zip(["setup_l0", "build_l1", "setup_l1", "build_l2", "solve"],
                                      [float(v) for v in np.median(ph, axis=0)])),
         "kernels": {k: {"launches": v["launches"], "ms": v["ms"],
@@ -438,6 +487,10 @@ def main():
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides (coarse-apply mode)")
     ap.add_argument("--slots", type=int, default=9, choices=[5, 9],
                     help="coarse link blocks stored (coarse-apply mode)")
+    ap.add_argument("--no-learned", dest="learned", action="store_false",
+                    help="skip training / evaluating the learned setup")
+    ap.add_argument("--learned-ntrain", type=int, default=24)
+    ap.add_argument("--learned-epochs", type=int, default=10)
     ap.add_argument("--no-forms", dest="forms", action="store_false",
                     help="skip the 16-bit storage forms' s/solve")
     args = ap.parse_args()

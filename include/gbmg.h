@@ -222,6 +222,39 @@ mg_status mg_profile_query(mg_ctx* ctx, const char* name, int level, int* launch
 mg_status mg_block_orthonormalise_noalloc(const void* vecs_dev, void* out_dev, const int dims[4],
                                           const int block[4], int ndof, int nvec, void* stream);
 
+/* Number of minimal-residual sweeps the next mg_setup_nullvecs runs (the
+ * learned setup starts from proposed vectors and needs fewer).             */
+mg_status mg_set_setup_sweeps(mg_ctx* ctx, int sweeps);
+
+/* ---- Learned null-vector proposer.  The paper draws the setup's starting
+ * vectors x0 at random (Sec. II-D step 1); this addition proposes them with
+ * a three-layer network whose layers are nearest-neighbour stencils on the
+ * lattice: 72 link features (Re, Im of U_mu(x)) -> 32 -> 32 (tanh) ->
+ * 24 * nvec outputs = nvec complex 12-component vectors per site.  FP32
+ * parameters, flat order W1[9][32][72], b1[32], W2[9][32][32], b2[32],
+ * W3[24 nvec][32], b3[24 nvec].  Training minimises, per aggregate and
+ * chirality, 1 - |Q_pred^H Q_target|_F^2 / nvec (the share of the target
+ * null space outside the span of the proposed vectors), averaged over
+ * blocks, with Adam.  Vectors use the null-vector layout [vec][V][12]
+ * complex double; the gauge field the mg_create layout.                    */
+typedef struct mg_cnn mg_cnn;
+mg_status mg_cnn_create(int nvec, uint64_t seed, mg_cnn** out);
+mg_status mg_cnn_destroy(mg_cnn* net);
+mg_status mg_cnn_nparams(mg_cnn* net, int* count);
+/* parameters (which = 0) or the last gradient (which = 1), FP32, device   */
+mg_status mg_cnn_get_params(mg_cnn* net, void* dst_dev, size_t bytes, int which, void* stream);
+mg_status mg_cnn_set_params(mg_cnn* net, const void* src_dev, size_t bytes, void* stream);
+/* proposed vectors for the lattice `dims` and gauge field gauge_dev       */
+mg_status mg_cnn_forward(mg_cnn* net, const int dims[4], const void* gauge_dev, void* vecs_dev,
+                         void* stream);
+/* loss and gradient against target_dev (block-orthonormal null vectors of
+ * the same lattice, aggregates `block`); synchronises when loss != NULL    */
+mg_status mg_cnn_loss_grad(mg_cnn* net, const int dims[4], const int block[4],
+                           const void* gauge_dev, const void* target_dev, double* loss,
+                           void* stream);
+/* one Adam step (beta 0.9 / 0.999) with the last gradient                 */
+mg_status mg_cnn_adam_step(mg_cnn* net, float lr, void* stream);
+
 /* Synchronise `stream` and report errors that kernels recorded on the
  * device: MG_ERR_TIMEOUT if a bounded wait inside a kernel (the tensor-core
  * multi-RHS apply's mbarrier waits) gave up since the last call; the record

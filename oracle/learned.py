@@ -1,0 +1,143 @@
+"""Learned null-vector proposer (oracle, FP64).  Not in the paper: an
+addition that proposes the random starting vectors x0 of Sec. II-D step 1.
+
+Network (every layer a nearest-neighbour stencil on the lattice, the
+"4D convolution" of this build):
+  features  f(x)  = (Re, Im) of the four links U_mu(x)       72 channels
+  layer 1   h1(x) = tanh(b1 + sum_{d=0..8} W1[d] f(x + shift(d)))   72 -> 32
+  layer 2   h2(x) = tanh(b2 + sum_{d=0..8} W2[d] h1(x + shift(d)))  32 -> 32
+  layer 3   o(x)  = b3 + W3 h2(x)                                    32 -> 24 Nv
+  vector i at site x, dof a: o[x][24 i + 2a] + i o[x][24 i + 2a + 1].
+
+Loss (proposed reading; raw null vectors are not unique): for every
+aggregate A and chirality s, with B the (|A| nd/2) x Nv block of the
+predicted vectors and T the orthonormal block of the target vectors
+(the plain setup's block-orthonormalised null vectors),
+  l(A, s) = 1 - tr(C^H G^{-1} C) / Nv,  G = B^H B + delta I, C = B^H T,
+the fraction of the target subspace outside span(B); the loss is the mean
+over blocks.  delta = kappa |B|_F^2 with kappa = 1e-5 / Nv keeps G
+invertible at any scale of B; its derivative is part of the gradient:
+  d f / d B^* = T A^H - B A A^H - kappa |A|_F^2 B,  A = G^{-1} C.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import lattice as lat
+from .dirac import chirality_of_dof
+from .multigrid import aggregate_blocks
+
+NFEAT, NHID = 72, 32
+
+
+def param_shapes(nvec: int):
+    return [("W1", (9, NHID, NFEAT)), ("b1", (NHID,)), ("W2", (9, NHID, NHID)),
+            ("b2", (NHID,)), ("W3", (24 * nvec, NHID)), ("b3", (24 * nvec,))]
+
+
+def unflatten(theta, nvec):
+    out, k = {}, 0
+    for name, shp in param_shapes(nvec):
+        n = int(np.prod(shp))
+        out[name] = np.asarray(theta[k:k + n], dtype=np.float64).reshape(shp)
+        k += n
+    return out
+
+
+def flatten(p, nvec):
+    return np.concatenate([p[name].ravel() for name, _ in param_shapes(nvec)])
+
+
+def features(U):
+    """[V][72]: (Re, Im) of U_mu(x)[a][b], ordered (mu, a, b, re/im)."""
+    vol = U.shape[1]
+    u = np.transpose(U, (1, 0, 2, 3)).reshape(vol, 36)
+    return np.stack([u.real, u.imag], axis=-1).reshape(vol, 72)
+
+
+def conv9(inp, W, b, nbr):
+    """out(x) = b + sum_d W[d] in(x + shift(d))."""
+    out = np.broadcast_to(b, (inp.shape[0], W.shape[1])).copy()
+    for d in range(9):
+        out += inp[nbr[:, d]] @ W[d].T
+    return out
+
+
+def forward(theta, U, dims, nvec):
+    p = unflatten(theta, nvec)
+    nbr = lat.neighbours(dims)
+    f = features(U)
+    h1 = np.tanh(conv9(f, p["W1"], p["b1"], nbr))
+    h2 = np.tanh(conv9(h1, p["W2"], p["b2"], nbr))
+    o = h2 @ p["W3"].T + p["b3"]
+    return dict(f=f, h1=h1, h2=h2, o=o, nbr=nbr, p=p)
+
+
+def vectors(o, nvec):
+    """[Nv][V][12] complex from the output channels."""
+    vol = o.shape[0]
+    z = o.reshape(vol, nvec, 12, 2)
+    return np.transpose(z[..., 0] + 1j * z[..., 1], (1, 0, 2))
+
+
+def subspace_loss(V, T, dims, block):
+    """Mean over (aggregate, chirality) blocks of 1 - tr(C^H G^{-1} C)/Nv and its
+    gradient dL/dV* (same layout as V)."""
+    nv, vol, nd = V.shape
+    grad = np.zeros_like(V)
+    total, nblocks = 0.0, 0
+    for s in (0, 1):
+        B, order, dofs = aggregate_blocks(V, dims, block, s)   # [nagg][rows][Nv]
+        Tb, _, _ = aggregate_blocks(T, dims, block, s)
+        nagg = B.shape[0]
+        kappa = 1e-5 / nv
+        G = np.conj(np.swapaxes(B, 1, 2)) @ B
+        G = G + kappa * np.real(np.trace(G, axis1=1, axis2=2))[:, None, None] * np.eye(nv)
+        C = np.conj(np.swapaxes(B, 1, 2)) @ Tb
+        A = np.linalg.solve(G, C)
+        f = np.real(np.trace(np.conj(np.swapaxes(C, 1, 2)) @ A, axis1=1, axis2=2))
+        total += float(np.sum(1.0 - f / nv))
+        nblocks += nagg
+        AH = np.conj(np.swapaxes(A, 1, 2))
+        a2 = np.sum(np.abs(A) ** 2, axis=(1, 2))
+        gB = -(Tb @ AH - B @ (A @ AH) - kappa * a2[:, None, None] * B) / nv
+        tmp = np.zeros((nv, vol, len(dofs)), dtype=np.complex128)
+        tmp[:, order, :] = gB.transpose(2, 0, 1).reshape(nv, vol, len(dofs))
+        grad[:, :, dofs] += tmp
+    return total / nblocks, grad / nblocks
+
+
+def loss_and_grad(theta, U, dims, nvec, T, block):
+    """Loss and its gradient with respect to the flat parameter vector."""
+    fw = forward(theta, U, dims, nvec)
+    p, nbr = fw["p"], fw["nbr"]
+    V = vectors(fw["o"], nvec)
+    L, gV = subspace_loss(V, T, dims, block)
+    vol = V.shape[1]
+    # real-parameter gradient: dL/dRe z = 2 Re(dL/dz*), dL/dIm z = 2 Im(dL/dz*)
+    gz = np.transpose(gV, (1, 0, 2))                     # [V][Nv][12]
+    go = np.stack([2 * gz.real, 2 * gz.imag], axis=-1).reshape(vol, 24 * nvec)
+    g = {"W3": go.T @ fw["h2"], "b3": go.sum(0)}
+    gh2 = go @ p["W3"]
+    gp2 = gh2 * (1.0 - fw["h2"] ** 2)
+    g["b2"] = gp2.sum(0)
+    g["W2"] = np.stack([gp2.T @ fw["h1"][nbr[:, d]] for d in range(9)])
+    gh1 = np.zeros_like(fw["h1"])
+    for d in range(9):  # h1(x + d) feeds out(x): scatter back to the source site
+        np.add.at(gh1, nbr[:, d], gp2 @ p["W2"][d])
+    gp1 = gh1 * (1.0 - fw["h1"] ** 2)
+    g["b1"] = gp1.sum(0)
+    g["W1"] = np.stack([gp1.T @ fw["f"][nbr[:, d]] for d in range(9)])
+    return L, flatten(g, nvec)
+
+
+def init_params(nvec: int, seed: int):
+    rng = np.random.default_rng(seed)
+    p = {}
+    for name, shp in param_shapes(nvec):
+        if name.startswith("b"):
+            p[name] = np.zeros(shp)
+        else:
+            fan_in = shp[-1] * (9 if len(shp) == 3 else 1)
+            p[name] = rng.standard_normal(shp) / np.sqrt(fan_in)
+    return flatten(p, nvec)

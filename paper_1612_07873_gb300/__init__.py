@@ -95,6 +95,16 @@ def _load():
         "mg_block_orthonormalise_noalloc": (i, [vp, vp, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                                 i, i, vp]),
         "mg_device_status": (i, [vp, vp]),
+        "mg_set_setup_sweeps": (i, [vp, i]),
+        "mg_cnn_create": (i, [i, C.c_uint64, C.POINTER(vp)]),
+        "mg_cnn_destroy": (i, [vp]),
+        "mg_cnn_nparams": (i, [vp, C.POINTER(C.c_int)]),
+        "mg_cnn_get_params": (i, [vp, vp, sz, i, vp]),
+        "mg_cnn_set_params": (i, [vp, vp, sz, vp]),
+        "mg_cnn_forward": (i, [vp, C.POINTER(C.c_int), vp, vp, vp]),
+        "mg_cnn_loss_grad": (i, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), vp, vp,
+                                 C.POINTER(d), vp]),
+        "mg_cnn_adam_step": (i, [vp, C.c_float, vp]),
         "mg_launch_count": (C.c_longlong, [vp]),
         "mg_status_string": (C.c_char_p, [i]),
         "mg_last_error": (C.c_char_p, [vp]),
@@ -263,6 +273,56 @@ def mg_block_orthonormalise_noalloc(vecs, out, dims, block, stream=None):
 
 def mg_device_status(ctx, stream=None):
     _ok(LIB.mg_device_status(ctx, _stream(stream)), ctx)
+
+
+def mg_set_setup_sweeps(ctx, sweeps):
+    _ok(LIB.mg_set_setup_sweeps(ctx, sweeps), ctx)
+
+
+def _dims(d):
+    return (C.c_int * 4)(*[int(v) for v in d])
+
+
+def mg_cnn_create(nvec, seed=1):
+    h = C.c_void_p()
+    _ok(LIB.mg_cnn_create(nvec, seed, C.byref(h)))
+    return h
+
+
+def mg_cnn_destroy(net):
+    _ok(LIB.mg_cnn_destroy(net))
+
+
+def mg_cnn_nparams(net) -> int:
+    n = C.c_int()
+    _ok(LIB.mg_cnn_nparams(net, C.byref(n)))
+    return n.value
+
+
+def mg_cnn_get_params(net, out, which=0, stream=None):
+    _ok(LIB.mg_cnn_get_params(net, _ptr(out), out.numel() * 4, which, _stream(stream)))
+    return out
+
+
+def mg_cnn_set_params(net, params, stream=None):
+    assert params.dtype == torch.float32
+    _ok(LIB.mg_cnn_set_params(net, _ptr(params), params.numel() * 4, _stream(stream)))
+
+
+def mg_cnn_forward(net, dims, gauge, out, stream=None):
+    _ok(LIB.mg_cnn_forward(net, _dims(dims), _ptr(gauge), _ptr(out), _stream(stream)))
+    return out
+
+
+def mg_cnn_loss_grad(net, dims, block, gauge, target, stream=None) -> float:
+    loss = C.c_double()
+    _ok(LIB.mg_cnn_loss_grad(net, _dims(dims), _dims(block), _ptr(gauge), _ptr(target),
+                             C.byref(loss), _stream(stream)))
+    return loss.value
+
+
+def mg_cnn_adam_step(net, lr, stream=None):
+    _ok(LIB.mg_cnn_adam_step(net, lr, _stream(stream)))
 
 
 def mg_launch_count(ctx) -> int:

@@ -360,6 +360,13 @@ mg_status mg_profile_query(mg_ctx* c, const char* name, int level, int* launches
   });
 }
 
+mg_status mg_set_setup_sweeps(mg_ctx* c, int sweeps) {
+  return guarded(c, [&] {
+    GB_REQUIRE(sweeps >= 0 && sweeps <= 100000, MG_ERR_ARG, "setup sweeps out of range");
+    c->p.setup_sweeps = sweeps;
+  });
+}
+
 mg_status mg_device_status(mg_ctx* c, void* stream) {
   return guarded(c, [&] {
     int h[2] = {0, 0};

@@ -285,3 +285,42 @@ def test_three_level_mg_converges():
     b = syn.gaussian_field((vol, 12), 64)
     res = mg.solve(b, 1e-10, 100)
     assert res.true_residual <= 1e-10
+
+
+# ------------------------------------------------------------ learned proposer
+def test_learned_loss_limits():
+    """Subspace loss: 0 when the proposals span the target space, 1 when they
+    span its orthogonal complement inside every block."""
+    from oracle import learned as ol
+    dims, block, nv = (4, 2, 2, 2), (2, 2, 2, 2), 3
+    vol = lat.volume(dims)
+    T = mgo.block_orthonormalise(syn.gaussian_field((nv, vol, 12), 71), dims, block)
+    mix = _rand((nv, nv))
+    V = np.einsum("ij,jxa->ixa", mix, T)
+    L, _ = ol.subspace_loss(V, T, dims, block)
+    # V = T M blockwise (M = mix^T): loss = (1/Nv) sum_i delta / (s_i^2 + delta),
+    # delta = (1e-5 / Nv) |M|_F^2, s_i the singular values of M
+    s2 = np.linalg.svd(mix, compute_uv=False) ** 2
+    delta = 1e-5 / nv * s2.sum()
+    assert abs(L - np.mean(delta / (s2 + delta))) < 1e-12
+    W = syn.gaussian_field((nv, vol, 12), 72)
+    Bw = mgo.block_orthonormalise(np.concatenate([T, W]), dims, block)[nv:]
+    L, _ = ol.subspace_loss(Bw, T, dims, block)
+    assert abs(L - 1.0) < 1e-10
+
+
+def test_learned_gradient_matches_finite_differences():
+    from oracle import learned as ol
+    dims, block, nv = (4, 4, 2, 2), (2, 2, 2, 2), 3
+    U = syn.gauge_field(dims, 0.4, 73)
+    T = mgo.block_orthonormalise(syn.gaussian_field((nv, lat.volume(dims), 12), 74), dims, block)
+    th = ol.init_params(nv, 75)
+    L, g = ol.loss_and_grad(th, U, dims, nv, T, block)
+    rng = np.random.default_rng(76)
+    for i in rng.choice(th.size, 12, replace=False):
+        e = np.zeros_like(th)
+        e[i] = 1e-6
+        Lp, _ = ol.loss_and_grad(th + e, U, dims, nv, T, block)
+        Lm, _ = ol.loss_and_grad(th - e, U, dims, nv, T, block)
+        fd = (Lp - Lm) / 2e-6
+        assert abs(fd - g[i]) <= 1e-5 * max(abs(fd), 1e-3), (i, fd, g[i])
