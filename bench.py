@@ -244,7 +244,7 @@ def gpu_main(args):
     if args.fine:  # smaller fine lattice of the same shape family (profiling runs)
         dims = tuple(int(v) for v in args.fine.split(","))
     form = args.form
-    prec_coarse = {"fp32": 1, "bf16": 2, "fp16": 3}[form]
+    prec_coarse = {"fp32": 1, "bf16": 2, "fp16": 3, "int16": 4}[form]
     t_gen = time.perf_counter()
     U = syn.gauge_field(dims, w["eps"], w["seed"])
     vol = syn.volume(dims)
@@ -357,8 +357,8 @@ def gpu_main(args):
     forms = {}
     if args.forms:
         mg.close()
-        for fname, pc, slots in (("bf16", 2, 9), ("fp16", 3, 9), ("fp32_5blocks", 1, 5),
-                                 ("bf16_5blocks", 2, 5)):
+        for fname, pc, slots in (("bf16", 2, 9), ("fp16", 3, 9), ("int16", 4, 9),
+                                 ("fp32_5blocks", 1, 5), ("bf16_5blocks", 2, 5)):
             if fname == form:
                 continue
             pf = gb.default_params(dims=dims, block=blocks, nvec=nvecs, mass=w["mass"],
@@ -437,7 +437,7 @@ def coarse_apply_main(args):
     import torch
 
     import paper_1612_07873_gb300 as gb
-    prec = {"fp32": 1, "bf16": 2, "fp16": 3}[args.form]
+    prec = {"fp32": 1, "bf16": 2, "fp16": 3, "int16": 4}[args.form]
     fine = (16, 16, 16, 32)
     U = syn.gauge_field(fine, 0.0, 1)
     p = gb.default_params(dims=fine, block=[(2, 2, 2, 2)], nvec=[24], nlevels=2, prec_fine=1,
@@ -481,7 +481,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gbmg", choices=["gbmg", "reference"])
-    ap.add_argument("--form", default="fp32", choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--form", default="fp32", choices=["fp32", "bf16", "fp16", "int16"])
     ap.add_argument("--mode", default="pipeline", choices=["pipeline", "coarse-apply"])
     ap.add_argument("--fine", default="", help="override the fine extents, e.g. 16,16,16,32")
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides (coarse-apply mode)")

@@ -71,7 +71,9 @@ typedef enum {
   MG_ERR_RANK = -8           /* a null-vector aggregate block is rank deficient  */
 } mg_status;
 
-typedef enum { MG_F64 = 0, MG_F32 = 1, MG_BF16 = 2, MG_F16 = 3 } mg_prec;
+/* MG_I16: 16-bit fixed point (re, im) pairs, value = site scale * q / 32767,
+ * the paper's "half" storage (Sec. III).                                 */
+typedef enum { MG_F64 = 0, MG_F32 = 1, MG_BF16 = 2, MG_F16 = 3, MG_I16 = 4 } mg_prec;
 
 typedef struct mg_ctx mg_ctx;
 
@@ -89,7 +91,7 @@ typedef struct {
   int setup_sweeps;                 /* minimal-residual sweeps on M x = 0           */
   uint64_t seed;                    /* device Gaussian x0 when none is passed       */
   mg_prec prec_fine;                /* MG_F64 or MG_F32                             */
-  mg_prec prec_coarse;              /* MG_F64, MG_F32, MG_BF16 or MG_F16 link store */
+  mg_prec prec_coarse;              /* MG_F64, MG_F32, MG_BF16, MG_F16, MG_I16 links */
   int mr_iters;                     /* MR pre- and post-smoothing steps (4)         */
   double mr_omega;                  /* MR relaxation (1.0)                          */
   int gcr_nkrylov;                  /* GCR Krylov space size (10)                   */

@@ -17,7 +17,7 @@ import torch
 from . import build as _build
 
 MG_MAX_LEVELS = 4
-F64, F32, BF16, F16 = 0, 1, 2, 3
+F64, F32, BF16, F16, I16 = 0, 1, 2, 3, 4
 STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "out of device memory",
           -4: "call out of order", -5: "solver did not converge", -6: "numerical breakdown",
           -7: "device wait timed out", -8: "rank-deficient null-vector block"}

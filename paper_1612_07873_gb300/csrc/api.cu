@@ -114,7 +114,7 @@ mg_status mg_create(const mg_params* p, const void* gauge_dev, mg_ctx** out) {
     return fail(nullptr, MG_ERR_ARG, "mg_create: nlevels must be 2..4");
   if (p->prec_fine != MG_F64 && p->prec_fine != MG_F32)
     return fail(nullptr, MG_ERR_ARG, "mg_create: prec_fine must be F64 or F32");
-  if (p->prec_coarse < MG_F64 || p->prec_coarse > MG_F16)
+  if (p->prec_coarse < MG_F64 || p->prec_coarse > MG_I16)
     return fail(nullptr, MG_ERR_ARG, "mg_create: bad prec_coarse");
   if (p->gcr_nkrylov < 1 || p->gcr_nkrylov > 64 || p->mr_iters < 0)
     return fail(nullptr, MG_ERR_ARG, "mg_create: bad solver parameters");
@@ -157,7 +157,7 @@ mg_status mg_create(const mg_params* p, const void* gauge_dev, mg_ctx** out) {
         GB_REQUIRE(p->link_slots == 0 || p->link_slots == 9 || p->link_slots == 5, MG_ERR_ARG,
                    "link_slots must be 9 or 5");
         L.slots5 = p->link_slots == 5;
-        GB_REQUIRE(!((L.prec == MG_BF16 || L.prec == MG_F16) && (L.nd % 4)), MG_ERR_ARG,
+        GB_REQUIRE(!(prec_is16(L.prec) && (L.nd % 4)), MG_ERR_ARG,
                    "16-bit coarse links need an even number of null vectors");
       }
       L.vprec = vec_prec_of(L.prec);

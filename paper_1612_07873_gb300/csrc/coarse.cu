@@ -21,6 +21,7 @@
 #include <type_traits>
 
 #include "kernels.cuh"
+#include "tune.cuh"
 
 namespace gbmg {
 
@@ -65,6 +66,18 @@ struct Unpack<f16c> {
       float2 f = __half22float2(h);
       out[i] = cpx<float>(f.x, f.y);
     }
+  }
+};
+
+template <>
+struct Unpack<i16c> {
+  static constexpr int RPC = 4;
+  __device__ static __forceinline__ void get(uint4 v, cpx<float> out[4]) {
+    uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    const float s = 1.f / 32767.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      out[i] = cpx<float>(float(short(w[i] & 0xffffu)) * s, float(short(w[i] >> 16)) * s);
   }
 };
 
@@ -361,31 +374,76 @@ void launch_stream5(const Level& L, void* y, const void* x, const void* links, c
                                                      (const S*)links, L.scales.as<float>(), L.g);
 }
 
+// Column-group counts the autotuner chooses from: the middle one is the
+// default; a count is a candidate when it divides the kernel's K.
+template <typename S>
+struct CgSet {
+  static constexpr int RPC = Unpack<S>::RPC;
+  static constexpr int c0 = RPC == 1 ? 4 : (RPC == 2 ? 8 : 16);
+  static constexpr int c1 = c0 / 2;
+  static constexpr int c2 = c0 * 2;
+};
+
+template <typename S, int N, bool FIVE>
+void launch_cg(int cg, const Level& L, void* y, const void* x, const void* links, cudaStream_t st) {
+  using CS = CgSet<S>;
+  if constexpr (FIVE) {
+    if (cg == CS::c1) {
+      if constexpr (N % CS::c1 == 0) return launch_stream5<S, N, CS::c1>(L, y, x, links, st);
+    } else if (cg == CS::c2) {
+      if constexpr (N % CS::c2 == 0) return launch_stream5<S, N, CS::c2>(L, y, x, links, st);
+    }
+    return launch_stream5<S, N, CS::c0>(L, y, x, links, st);
+  } else {
+    if (cg == CS::c1) {
+      if constexpr ((9 * N) % CS::c1 == 0) return launch_stream<S, N, CS::c1>(L, y, x, links, st);
+    } else if (cg == CS::c2) {
+      if constexpr ((9 * N) % CS::c2 == 0) return launch_stream<S, N, CS::c2>(L, y, x, links, st);
+    }
+    return launch_stream<S, N, CS::c0>(L, y, x, links, st);
+  }
+}
+
+template <typename S, int N, bool FIVE>
+void tuned_stream(const Level& L, void* y, const void* x, const void* links, cudaStream_t st) {
+  using CS = CgSet<S>;
+  std::vector<int> cands{CS::c0};
+  // FP64 stores serve parity runs only: not tuned
+  if (!std::is_same<S, cpx<double>>::value) {
+    const int K = FIVE ? N : 9 * N;
+    if (K % CS::c1 == 0) cands.push_back(CS::c1);
+    if (K % CS::c2 == 0) cands.push_back(CS::c2);
+  }
+  const std::string key = std::string(FIVE ? "stream5" : "stream") + "/p" +
+                          std::to_string(int(L.prec)) + "/n" + std::to_string(N) + "/v" +
+                          std::to_string(L.g.vol);
+  const int cg = Tuner::get().choose(key, cands, st, [&](int c) {
+    launch_cg<S, N, FIVE>(c, L, y, x, links, st);
+  });
+  launch_cg<S, N, FIVE>(cg, L, y, x, links, st);
+}
+
 template <typename S>
 bool try_stream5(const Level& L, void* y, const void* x, cudaStream_t st) {
   // FP64 stores (parity runs) keep the nine-block kernel: the five-block
   // form's reduction buffer would not fit its static shared memory
   if (std::is_same<S, cpx<double>>::value) return false;
-  constexpr int RPC = Unpack<S>::RPC;
-  constexpr int CG = RPC == 1 ? 4 : (RPC == 2 ? 8 : 16);
   const void* links = L.links5.p;
   switch (L.nd) {
-    case 32: launch_stream5<S, 32, CG>(L, y, x, links, st); return true;
-    case 48: launch_stream5<S, 48, CG>(L, y, x, links, st); return true;
-    case 64: launch_stream5<S, 64, CG>(L, y, x, links, st); return true;
+    case 32: tuned_stream<S, 32, true>(L, y, x, links, st); return true;
+    case 48: tuned_stream<S, 48, true>(L, y, x, links, st); return true;
+    case 64: tuned_stream<S, 64, true>(L, y, x, links, st); return true;
     default: return false;
   }
 }
 
 template <typename S>
 bool try_stream(const Level& L, void* y, const void* x, const void* links, cudaStream_t st) {
-  constexpr int RPC = Unpack<S>::RPC;
-  constexpr int CG = RPC == 1 ? 4 : (RPC == 2 ? 8 : 16);
   switch (L.nd) {
-    case 16: launch_stream<S, 16, CG>(L, y, x, links, st); return true;
-    case 32: launch_stream<S, 32, CG>(L, y, x, links, st); return true;
-    case 48: launch_stream<S, 48, CG>(L, y, x, links, st); return true;
-    case 64: launch_stream<S, 64, CG>(L, y, x, links, st); return true;
+    case 16: tuned_stream<S, 16, false>(L, y, x, links, st); return true;
+    case 32: tuned_stream<S, 32, false>(L, y, x, links, st); return true;
+    case 48: tuned_stream<S, 48, false>(L, y, x, links, st); return true;
+    case 64: tuned_stream<S, 64, false>(L, y, x, links, st); return true;
     default: return false;
   }
 }
@@ -428,6 +486,7 @@ void coarse_apply(mg_ctx* c, int level, void* y, const void* x, int nrhs, cudaSt
     case MG_F32: dispatch_apply<cpx<float>>(L, y, x, L.links.p, nrhs, st); break;
     case MG_BF16: dispatch_apply<bf16c>(L, y, x, L.links16.p, nrhs, st); break;
     case MG_F16: dispatch_apply<f16c>(L, y, x, L.links16.p, nrhs, st); break;
+    case MG_I16: dispatch_apply<i16c>(L, y, x, L.links16.p, nrhs, st); break;
   }
   GB_LAUNCH_CHECK();
   c->launches++;
@@ -462,7 +521,7 @@ void links_pick5(mg_ctx* c, int level, cudaStream_t st) {
 
 void links_pack16(mg_ctx* c, int level, cudaStream_t st) {
   Level& L = c->L[level];
-  if (L.prec != MG_BF16 && L.prec != MG_F16) {
+  if (!prec_is16(L.prec)) {
     links_pick5(c, level, st);
     return;
   }
@@ -472,8 +531,11 @@ void links_pack16(mg_ctx* c, int level, cudaStream_t st) {
   if (L.prec == MG_BF16)
     k_links_pack16<bf16c><<<L.g.vol, 256, 0, st>>>(L.links16.as<bf16c>(), L.scales.as<float>(),
                                                    L.links.as<cpx<float>>(), L.nd);
-  else
+  else if (L.prec == MG_F16)
     k_links_pack16<f16c><<<L.g.vol, 256, 0, st>>>(L.links16.as<f16c>(), L.scales.as<float>(),
+                                                  L.links.as<cpx<float>>(), L.nd);
+  else
+    k_links_pack16<i16c><<<L.g.vol, 256, 0, st>>>(L.links16.as<i16c>(), L.scales.as<float>(),
                                                   L.links.as<cpx<float>>(), L.nd);
   GB_LAUNCH_CHECK();
   c->launches++;
@@ -519,6 +581,9 @@ void links_export(mg_ctx* c, int level, void* ext, cudaStream_t st) {
       break;
     case MG_F16:
       k_links_export<f16c><<<blocks, 256, 0, st>>>(o, L.links16.as<f16c>(), sc, L.g.vol, L.nd);
+      break;
+    case MG_I16:
+      k_links_export<i16c><<<blocks, 256, 0, st>>>(o, L.links16.as<i16c>(), sc, L.g.vol, L.nd);
       break;
   }
   GB_LAUNCH_CHECK();

@@ -19,6 +19,7 @@
 // Every mbarrier wait is bounded: on timeout the kernel records an error
 // word, waits (bounded) for its MMAs, frees its TMEM and returns.
 #include "kernels.cuh"
+#include "tune.cuh"
 
 namespace gbmg {
 
@@ -368,10 +369,19 @@ void launch_mma(mg_ctx* c, const Level& L, void* y, const void* x, int nrhs, cud
   if (by_regs < per_sm) per_sm = by_regs;
   if (per_sm > 8) per_sm = 8;
   if (per_sm < 1) per_sm = 1;
-  int grid = sms * per_sm;
-  if (grid > L.g.vol) grid = L.g.vol;
-  kern<<<grid, 128, smem, st>>>((cpx<float>*)y, (const cpx<float>*)x, L.links_mma.as<uint4>(),
-                                L.scales.as<float>(), L.g, nrhs, c->status.as<int>() + 1);
+  // autotuned: resident CTAs per SM (the largest that fits is the default)
+  std::vector<int> cands{per_sm};
+  for (int q = per_sm - 1; q >= 1 && cands.size() < 3; --q) cands.push_back(q);
+  auto launch = [&](int q) {
+    int grid = sms * q;
+    if (grid > L.g.vol) grid = L.g.vol;
+    kern<<<grid, 128, smem, st>>>((cpx<float>*)y, (const cpx<float>*)x, L.links_mma.as<uint4>(),
+                                  L.scales.as<float>(), L.g, nrhs, c->status.as<int>() + 1);
+  };
+  const std::string key = std::string("mma/") + (BF16 ? "bf16" : "f16") + "/n" +
+                          std::to_string(N) + "/r" + std::to_string(nrhs) + "/v" +
+                          std::to_string(L.g.vol);
+  launch(Tuner::get().choose(key, cands, st, launch));
 }
 
 }  // namespace

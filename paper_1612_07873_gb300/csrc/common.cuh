@@ -117,6 +117,11 @@ struct f16c {
   __half2 v;
 };
 
+// 16-bit fixed point: q = round(value / scale * 32767), |value| <= scale
+struct i16c {
+  short2 v;
+};
+
 template <typename S>
 struct StoreTraits;
 template <>
@@ -159,6 +164,23 @@ struct StoreTraits<f16c> {
     return r;
   }
 };
+
+template <>
+struct StoreTraits<i16c> {
+  using real = float;
+  static constexpr bool scaled = true;
+  __device__ static __forceinline__ cpx<float> load(i16c s) {
+    return cpx<float>(float(s.v.x) * (1.f / 32767.f), float(s.v.y) * (1.f / 32767.f));
+  }
+  __device__ static __forceinline__ i16c pack(cpx<float> c) {
+    i16c r;
+    r.v.x = short(__float2int_rn(fminf(fmaxf(c.re, -1.f), 1.f) * 32767.f));
+    r.v.y = short(__float2int_rn(fminf(fmaxf(c.im, -1.f), 1.f) * 32767.f));
+    return r;
+  }
+};
+
+inline bool prec_is16(mg_prec p) { return p == MG_BF16 || p == MG_F16 || p == MG_I16; }
 
 inline size_t prec_bytes_complex(mg_prec p) {
   switch (p) {

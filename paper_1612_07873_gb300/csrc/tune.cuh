@@ -1,0 +1,98 @@
+// Launch-policy autotuner: the first call for a key (kernel, precision,
+// shape) times every candidate policy with CUDA events on the caller's
+// stream and keeps the fastest, in memory and, when GBMG_TUNE_CACHE names a
+// file, on disk ("key value" lines, read on first use).  GBMG_TUNE=0 turns
+// tuning off (the first candidate is used).  A stream that is being
+// captured into a CUDA graph is never timed: the cached or first candidate
+// is used, so tune (make one call) before capturing.
+#pragma once
+
+#include <cstdio>
+#include <cstdlib>
+#include <fstream>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "common.cuh"
+
+namespace gbmg {
+
+class Tuner {
+ public:
+  static Tuner& get() {
+    static Tuner t;
+    return t;
+  }
+
+  // Returns the chosen candidate.  launch(c) must enqueue one launch with
+  // policy c on stream st; it is called repeatedly while timing.
+  template <typename F>
+  int choose(const std::string& key, const std::vector<int>& cands, cudaStream_t st, F&& launch) {
+    std::lock_guard<std::mutex> lk(mu_);
+    load();
+    auto it = best_.find(key);
+    if (it != best_.end()) return it->second;
+    if (!enabled_ || cands.size() == 1) return cands.front();
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+      return cands.front();
+    cudaEvent_t a, b;
+    GB_CHECK(cudaEventCreate(&a));
+    GB_CHECK(cudaEventCreate(&b));
+    int pick = cands.front();
+    float best_ms = 1e30f;
+    for (int c : cands) {
+      launch(c);  // warm-up
+      GB_CHECK(cudaEventRecord(a, st));
+      for (int r = 0; r < 3; ++r) launch(c);
+      GB_CHECK(cudaEventRecord(b, st));
+      GB_CHECK(cudaEventSynchronize(b));
+      float ms = 0.f;
+      GB_CHECK(cudaEventElapsedTime(&ms, a, b));
+      if (ms < best_ms) {
+        best_ms = ms;
+        pick = c;
+      }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    best_[key] = pick;
+    if (!path_.empty()) {
+      std::ofstream f(path_, std::ios::app);
+      if (f) f << key << " " << pick << "\n";
+    }
+    return pick;
+  }
+
+  // number of entries (tests)
+  size_t size() {
+    std::lock_guard<std::mutex> lk(mu_);
+    return best_.size();
+  }
+
+ private:
+  Tuner() {
+    const char* e = std::getenv("GBMG_TUNE");
+    enabled_ = !(e && std::string(e) == "0");
+    const char* p = std::getenv("GBMG_TUNE_CACHE");
+    if (p) path_ = p;
+  }
+  void load() {
+    if (loaded_) return;
+    loaded_ = true;
+    if (path_.empty()) return;
+    std::ifstream f(path_);
+    std::string k;
+    int v;
+    while (f >> k >> v) best_[k] = v;
+  }
+  std::mutex mu_;
+  std::unordered_map<std::string, int> best_;
+  bool loaded_ = false;
+  bool enabled_ = true;
+  std::string path_;
+};
+
+}  // namespace gbmg

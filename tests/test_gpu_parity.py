@@ -14,7 +14,7 @@ from gpu_helpers import make_ctx, oracle_fine, rel_l2, to_dev, to_np
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-12, 1: 1e-5, 2: 5e-3, 3: 5e-3}
+TOL = {0: 1e-12, 1: 1e-5, 2: 5e-3, 3: 5e-3, 4: 5e-3}
 
 
 # ------------------------------------------------------------------ Eq. (2)
@@ -56,7 +56,7 @@ def _random_links(vol, n, seed):
 
 @pytest.mark.parametrize("cdims,nv", [((2, 2, 2, 2), 8), ((4, 4, 4, 4), 24), ((2, 4, 2, 4), 32),
                                       ((3, 2, 2, 2), 3), ((2, 2, 2, 2), 5), ((4, 2, 2, 2), 16)])
-@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3, 4])
 def test_coarse_apply_random_links(gpu_lib, cdims, nv, prec):
     """Coarse links set from the host (random), y = sum_slot L x(nbr) against
     the oracle stencil apply.  Covers the streaming kernel (n = 16, 48, 64)
