@@ -179,6 +179,20 @@ def reference_main(args):
     return 0
 
 
+# ---------------------------------------------------------------- multi-rank
+def aggregate_ranks(ms_total, kernel_ms, kernel_bytes, device):
+    """Replicas: the step time and the kernel time of the job are the maxima
+    over ranks, the bytes moved are summed (whole-job throughput)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms_total, kernel_ms, kernel_bytes], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = t.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(mx[1]), float(sm[2])
+
+
 # ---------------------------------------------------------------- learned setup
 def run_learned(args, gb, torch, ev, stream, dev):
     """Train the null-vector proposer on the plain setup's vectors of
@@ -316,12 +330,7 @@ def gpu_main(args):
 
     # whole-job aggregation over ranks: bytes summed, time = max over ranks
     if world > 1:
-        t = torch.tensor([ms_total, ca_ms, ca_bytes], dtype=torch.float64, device=dev)
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = t.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        ms_total, ca_ms, ca_bytes = float(mx[0]), float(mx[1]), float(sm[2])
+        ms_total, ca_ms, ca_bytes = aggregate_ranks(ms_total, ca_ms, ca_bytes, dev)
     gbs = ca_bytes / (ca_ms * 1e-3) / 1e9 if ca_ms > 0 else 0.0
     per_launch_bytes = ca["bytes"] / max(ca["launches"], 1)
     per_launch_ms = ca["ms"] / max(ca["launches"], 1)

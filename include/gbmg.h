@@ -155,6 +155,17 @@ mg_status mg_build_coarse(mg_ctx* ctx, int level, void* stream);
 mg_status mg_coarse_apply(mg_ctx* ctx, int level, void* y_dev, const void* x_dev, int nrhs,
                           void* stream);
 
+/* Eq. (3) with nrhs right-hand sides on `count` (1..8) coarse operators of
+ * possibly different lattices -- level levels[i] of ctxs[i], all with the
+ * same n and 16-bit (BF16/FP16) links -- in ONE persistent tensor-core
+ * launch that walks the concatenated site lists.  y[i], x[i]: device arrays
+ * [V_i][n][nrhs] complex float, nrhs a multiple of 4 up to 64.  The call
+ * enqueues a single kernel with no host-side state, so it can be captured
+ * into a CUDA graph (make one uncaptured call first: it tunes the launch).
+ * Errors of the bounded device waits go to ctxs[0] (mg_device_status).     */
+mg_status mg_coarse_apply_multi(mg_ctx* const* ctxs, const int* levels, void* const* y_dev,
+                                const void* const* x_dev, int count, int nrhs, void* stream);
+
 /* The level-l operator on one vector: Eq. (2) for l = 0, Eq. (3) above.    */
 mg_status mg_apply(mg_ctx* ctx, int level, void* y_dev, const void* x_dev, void* stream);
 

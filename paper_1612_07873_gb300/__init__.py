@@ -96,6 +96,8 @@ def _load():
                                                 i, i, vp]),
         "mg_device_status": (i, [vp, vp]),
         "mg_set_setup_sweeps": (i, [vp, i]),
+        "mg_coarse_apply_multi": (i, [C.POINTER(vp), C.POINTER(C.c_int), C.POINTER(vp),
+                                      C.POINTER(vp), i, i, vp]),
         "mg_cnn_create": (i, [i, C.c_uint64, C.POINTER(vp)]),
         "mg_cnn_destroy": (i, [vp]),
         "mg_cnn_nparams": (i, [vp, C.POINTER(C.c_int)]),
@@ -273,6 +275,17 @@ def mg_block_orthonormalise_noalloc(vecs, out, dims, block, stream=None):
 
 def mg_device_status(ctx, stream=None):
     _ok(LIB.mg_device_status(ctx, _stream(stream)), ctx)
+
+
+def mg_coarse_apply_multi(ctxs, levels, ys, xs, nrhs, stream=None):
+    k = len(ctxs)
+    c_ctx = (C.c_void_p * k)(*[c.value if isinstance(c, C.c_void_p) else c for c in ctxs])
+    c_lev = (C.c_int * k)(*levels)
+    c_y = (C.c_void_p * k)(*[t.data_ptr() for t in ys])
+    c_x = (C.c_void_p * k)(*[t.data_ptr() for t in xs])
+    for t in list(ys) + list(xs):
+        assert t.is_cuda and t.is_contiguous()
+    _ok(LIB.mg_coarse_apply_multi(c_ctx, c_lev, c_y, c_x, k, nrhs, _stream(stream)), ctxs[0])
 
 
 def mg_set_setup_sweeps(ctx, sweeps):

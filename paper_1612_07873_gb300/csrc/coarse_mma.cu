@@ -141,12 +141,28 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
   }
 }
 
+// One lattice of a batched launch; the launch walks the concatenated site
+// list of all lattices (global site gs belongs to the last lattice whose
+// site0 <= gs).  Passed by value, so a launch carries no host-side state and
+// can be captured into a CUDA graph.
+constexpr int kMaxBatch = 8;
+struct MmaLattice {
+  const uint4* links;
+  const float* scales;
+  const cpx<float>* x;
+  cpx<float>* y;
+  Geom g;
+  int site0;
+};
+struct MmaBatch {
+  MmaLattice lat[kMaxBatch];
+  int count;
+  int total;
+};
+
 template <bool BF16, int N>
-__global__ void __launch_bounds__(128) k_coarse_mma(cpx<float>* __restrict__ y,
-                                                    const cpx<float>* __restrict__ x,
-                                                    const uint4* __restrict__ links,
-                                                    const float* __restrict__ scales, Geom g,
-                                                    int nrhs, int* __restrict__ err) {
+__global__ void __launch_bounds__(128) k_coarse_mma(const MmaBatch batch, int nrhs,
+                                                    int* __restrict__ err) {
   // a pipeline stage is half a stencil slot: N/2 complex link columns, i.e.
   // KS = N real K values; 18 stages per site
   constexpr int KS = N;                     // real K of one stage
@@ -193,6 +209,7 @@ __global__ void __launch_bounds__(128) k_coarse_mma(cpx<float>* __restrict__ y,
   // Operands of one slot are fetched into registers by fully unrolled,
   // independent loads (every load of the slot in flight at once); slot d+1
   // is fetched while slot d's barrier and MMAs run.
+  MmaLattice cur = batch.lat[0];  // lattice of the site being processed
   constexpr int XPT = ((N / 2) * 64 + 127) / 128;  // spinor elements per thread (nrhs <= 64)
   constexpr int BPT = (B_BYTES / 16 + 127) / 128;   // 16-byte link chunks per thread
   cpx<float> xr[XPT];
@@ -201,8 +218,8 @@ __global__ void __launch_bounds__(128) k_coarse_mma(cpx<float>* __restrict__ y,
   const int nxs = (N / 2) * nrhs;   // spinor elements of one stage
   auto fetch = [&](int site, int st) {
     const int d = st >> 1, h = st & 1;
-    const cpx<float>* xs = x + size_t(nb_sh[d]) * nx + size_t(h) * nxs;
-    const uint4* src = links + (size_t(site) * NST + st) * (B_BYTES / 16);
+    const cpx<float>* xs = cur.x + size_t(nb_sh[d]) * nx + size_t(h) * nxs;
+    const uint4* src = cur.links + (size_t(site) * NST + st) * (B_BYTES / 16);
 #pragma unroll
     for (int u = 0; u < BPT; ++u) {
       const int i = tid + 128 * u;
@@ -234,11 +251,17 @@ __global__ void __launch_bounds__(128) k_coarse_mma(cpx<float>* __restrict__ y,
     }
   };
 
-  for (int site = blockIdx.x; site < g.vol && ok; site += gridDim.x) {
+  for (int gs = blockIdx.x; gs < batch.total && ok; gs += gridDim.x) {
+    int li = 0;
+#pragma unroll
+    for (int q = 1; q < kMaxBatch; ++q)
+      if (q < batch.count && batch.lat[q].site0 <= gs) li = q;
+    cur = batch.lat[li];
+    const int site = gs - cur.site0;
     if (tid < 9) {
       int c[4];
-      site_coords(g, site, c);
-      nb_sh[tid] = neighbour(g, site, c, tid);
+      site_coords(cur.g, site, c);
+      nb_sh[tid] = neighbour(cur.g, site, c, tid);
     }
     __syncthreads();
     fetch(site, 0);
@@ -298,8 +321,8 @@ __global__ void __launch_bounds__(128) k_coarse_mma(cpx<float>* __restrict__ y,
     }
     tc_fence_before();
     __syncthreads();
-    const float sc = scales[site];
-    cpx<float>* ys = y + size_t(site) * nx;
+    const float sc = cur.scales[site];
+    cpx<float>* ys = cur.y + size_t(site) * nx;
     for (int e = tid; e < nx; e += 128) {
       const int m = e / nrhs, j = e - m * nrhs;
       ys[e] = cpx<float>(sc * Cs[j * N + m], sc * Cs[(nrhs + j) * N + m]);
@@ -349,7 +372,7 @@ __global__ void k_links_tile_mma(uint32_t* __restrict__ out, const cpx<float>* _
 }
 
 template <bool BF16, int N>
-void launch_mma(mg_ctx* c, const Level& L, void* y, const void* x, int nrhs, cudaStream_t st) {
+void launch_mma_batch(int* err, const MmaBatch& batch, int nrhs, cudaStream_t st, bool tune) {
   constexpr int KS = N;
   const int smem = 2 * (128 * KS * 2) + 2 * (N * KS * 2);
   auto kern = k_coarse_mma<BF16, N>;
@@ -374,14 +397,37 @@ void launch_mma(mg_ctx* c, const Level& L, void* y, const void* x, int nrhs, cud
   for (int q = per_sm - 1; q >= 1 && cands.size() < 3; --q) cands.push_back(q);
   auto launch = [&](int q) {
     int grid = sms * q;
-    if (grid > L.g.vol) grid = L.g.vol;
-    kern<<<grid, 128, smem, st>>>((cpx<float>*)y, (const cpx<float>*)x, L.links_mma.as<uint4>(),
-                                  L.scales.as<float>(), L.g, nrhs, c->status.as<int>() + 1);
+    if (grid > batch.total) grid = batch.total;
+    kern<<<grid, 128, smem, st>>>(batch, nrhs, err);
   };
+  if (!tune) {
+    launch(per_sm);
+    return;
+  }
   const std::string key = std::string("mma/") + (BF16 ? "bf16" : "f16") + "/n" +
                           std::to_string(N) + "/r" + std::to_string(nrhs) + "/v" +
-                          std::to_string(L.g.vol);
+                          std::to_string(batch.total) + "/b" + std::to_string(batch.count);
   launch(Tuner::get().choose(key, cands, st, launch));
+}
+
+MmaLattice lattice_of(const Level& L, void* y, const void* x) {
+  MmaLattice m;
+  m.links = L.links_mma.as<uint4>();
+  m.scales = L.scales.as<float>();
+  m.x = (const cpx<float>*)x;
+  m.y = (cpx<float>*)y;
+  m.g = L.g;
+  m.site0 = 0;
+  return m;
+}
+
+template <bool BF16, int N>
+void launch_mma(mg_ctx* c, const Level& L, void* y, const void* x, int nrhs, cudaStream_t st) {
+  MmaBatch b{};
+  b.lat[0] = lattice_of(L, y, x);
+  b.count = 1;
+  b.total = L.g.vol;
+  launch_mma_batch<BF16, N>(c->status.as<int>() + 1, b, nrhs, st, true);
 }
 
 }  // namespace
@@ -421,3 +467,49 @@ void links_tile_mma(mg_ctx* c, int level, cudaStream_t st) {
 }
 
 }  // namespace gbmg
+
+extern "C" mg_status mg_coarse_apply_multi(mg_ctx* const* ctxs, const int* levels,
+                                           void* const* y, const void* const* x, int count,
+                                           int nrhs, void* stream) {
+  using namespace gbmg;
+  try {
+    GB_REQUIRE(ctxs && levels && y && x && count >= 1 && count <= kMaxBatch, MG_ERR_ARG,
+               "coarse_apply_multi: 1..8 lattices with non-null arrays");
+    MmaBatch b{};
+    int n = 0;
+    mg_prec prec = MG_F64;
+    for (int i = 0; i < count; ++i) {
+      mg_ctx* c = ctxs[i];
+      GB_REQUIRE(c && levels[i] >= 1 && levels[i] < c->nlevels, MG_ERR_ARG,
+                 "coarse_apply_multi: bad context or level");
+      const Level& L = c->L[levels[i]];
+      GB_REQUIRE(L.have_op, MG_ERR_STATE, "coarse_apply_multi: coarse operator not built");
+      GB_REQUIRE(coarse_apply_mma_supported(L, nrhs), MG_ERR_ARG,
+                 "coarse_apply_multi: needs BF16/FP16 links, n in {32,48,64}, nrhs 4..64 (x4)");
+      GB_REQUIRE(i == 0 || (L.nd == n && L.prec == prec), MG_ERR_ARG,
+                 "coarse_apply_multi: all lattices need the same n and precision");
+      GB_REQUIRE(y[i] && x[i] && y[i] != x[i], MG_ERR_ARG, "coarse_apply_multi: bad vectors");
+      n = L.nd;
+      prec = L.prec;
+      b.lat[i] = lattice_of(L, y[i], x[i]);
+      b.lat[i].site0 = b.total;
+      b.total += L.g.vol;
+    }
+    b.count = count;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int* err = ctxs[0]->status.as<int>() + 1;
+    const bool bf16 = prec == MG_BF16;
+    switch (n) {
+      case 32: bf16 ? launch_mma_batch<true, 32>(err, b, nrhs, st, true) : launch_mma_batch<false, 32>(err, b, nrhs, st, true); break;
+      case 48: bf16 ? launch_mma_batch<true, 48>(err, b, nrhs, st, true) : launch_mma_batch<false, 48>(err, b, nrhs, st, true); break;
+      default: bf16 ? launch_mma_batch<true, 64>(err, b, nrhs, st, true) : launch_mma_batch<false, 64>(err, b, nrhs, st, true); break;
+    }
+    GB_LAUNCH_CHECK();
+    for (int i = 0; i < count; ++i) ctxs[i]->launches += (i == 0);
+    return MG_OK;
+  } catch (const Error& e) {
+    set_last_error(e.what());
+    if (ctxs && count >= 1 && ctxs[0]) ctxs[0]->err = e.what();
+    return e.code;
+  }
+}

@@ -32,3 +32,47 @@ def test_coarse_apply_tensor_cores(gpu_lib, prec, cdims, nv, nrhs):
     err = rel_l2(to_np(y), want)
     assert err < 5e-3, err
     mg.close()
+
+
+def test_uneven_lattices_one_launch_and_graph(gpu_lib):
+    """4^4, 6^4 and 8^3x16 coarse lattices (n = 48, BF16) in one persistent
+    tensor-core launch, then the same launch captured in a CUDA graph and
+    replayed with new inputs."""
+    gb = gpu_lib
+    cds = [(4, 4, 4, 4), (6, 6, 6, 6), (8, 8, 8, 16)]
+    nv, n, nrhs = 24, 48, 8
+    mgs, ys, xs, want = [], [], [], []
+    for k, cd in enumerate(cds):
+        mg, _ = make_ctx(gb, tuple(2 * c for c in cd), [(2, 2, 2, 2)], [nv], prec_fine=1,
+                         prec_coarse=2, eps=0.0)
+        vol = lat.volume(cd)
+        links = syn.gaussian_field((vol, 9, n, n), 60 + k) / np.sqrt(n)
+        gb.mg_set_coarse_links(mg.ctx, 1, to_dev(links))
+        mgs.append((mg, dirac.StencilOp(cd, links)))
+        xs.append(to_dev(syn.gaussian_field((vol, n, nrhs), 70 + k), torch.complex64))
+        ys.append(torch.zeros((vol, n, nrhs), dtype=torch.complex64, device="cuda"))
+    ctxs = [m.ctx for m, _ in mgs]
+    gb.mg_coarse_apply_multi(ctxs, [1, 1, 1], ys, xs, nrhs)
+    gb.mg_device_status(ctxs[0])
+    for (m, cop), y, x in zip(mgs, ys, xs):
+        xn = to_np(x)
+        ref = np.stack([cop.apply(xn[:, :, r]) for r in range(nrhs)], axis=-1)
+        assert rel_l2(to_np(y), ref) < 5e-3
+    # capture and replay
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        gb.mg_coarse_apply_multi(ctxs, [1, 1, 1], ys, xs, nrhs, stream=s)
+    for k, x in enumerate(xs):
+        x.copy_(to_dev(syn.gaussian_field(tuple(x.shape), 80 + k), torch.complex64))
+        ys[k].zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    gb.mg_device_status(ctxs[0])
+    for (m, cop), y, x in zip(mgs, ys, xs):
+        xn = to_np(x)
+        ref = np.stack([cop.apply(xn[:, :, r]) for r in range(nrhs)], axis=-1)
+        assert rel_l2(to_np(y), ref) < 5e-3
+    for m, _ in mgs:
+        m.close()
