@@ -323,7 +323,8 @@ def gpu_main(args):
     ms_total = t_start.elapsed_time(t_stop)
     ph = np.array([[es[i].elapsed_time(es[i + 1]) for i in range(5)] for es in phases])
     kern = {k: gb.mg_profile_query(ctx, k, -1) for k in
-            ("coarse_apply", "wilson_clover", "galerkin", "block_orth", "restrict", "prolong")}
+            ("coarse_apply", "coarse_apply_multi", "wilson_clover", "galerkin", "block_orth",
+             "restrict", "prolong")}
     ca = gb.mg_profile_query(ctx, "coarse_apply", 1)
     ca_ms = ca["ms"]
     ca_bytes = ca["bytes"]
@@ -470,7 +471,7 @@ def coarse_apply_main(args):
     for _ in range(args.steps):
         gb.mg_coarse_apply(mg.ctx, 1, y, x, nrhs=nrhs)
     gb.mg_device_status(mg.ctx)
-    q = gb.mg_profile_query(mg.ctx, "coarse_apply", 1)
+    q = gb.mg_profile_query(mg.ctx, "coarse_apply" if nrhs == 1 else "coarse_apply_multi", 1)
     peak, kind = peaks()
     gbs = q["bytes"] / (q["ms"] * 1e-3) / 1e9
     tflops = q["flops"] / (q["ms"] * 1e-3) / 1e12

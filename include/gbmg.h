@@ -202,8 +202,9 @@ mg_status mg_level_info(mg_ctx* ctx, int level, int dims[4], int* volume, int* n
                         int* vec_prec);
 
 /* Device-side timing of the library's own kernels.  When enabled, every
- * launch of kernel class `name` ("coarse_apply", "wilson_clover",
- * "galerkin", "restrict", "prolong", "block_orth", "blas") on level
+ * launch of kernel class `name` ("coarse_apply" for single right-hand
+ * sides, "coarse_apply_multi" for nrhs > 1, "wilson_clover", "galerkin",
+ * "restrict", "prolong", "block_orth") on level
  * `level` is bracketed by CUDA events on its stream.  query() sums the
  * durations (waiting for them) and the algorithmic bytes and flops the
  * launches moved; level -1 sums all levels.  reset() clears the record.   */

@@ -27,6 +27,14 @@ int ew_blocks(size_t n) {
   if (b < 1) b = 1;
   return int(b);
 }
+// batched element-wise grid: (blocks per vector, vector)
+dim3 ew_grid_b(size_t n, int nvec) {
+  long long b = (long long)((n + kThreads - 1) / kThreads);
+  long long cap = (152 * 64 + nvec - 1) / nvec;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return dim3(unsigned(b), unsigned(nvec));
+}
 
 __device__ __forceinline__ double2 block_sum(double2 v, double2* sh) {
   for (int o = 16; o > 0; o >>= 1) {
@@ -164,19 +172,27 @@ __global__ void k_scale_invnorm(cpx<Ra>* __restrict__ a, cpx<Rb>* __restrict__ b
   }
 }
 
-// x += a z ; r -= a w
+// x += a z ; r -= a w.  With FP32 directions z, w the products a z and a w
+// are formed in FP32 (they carry the precision of z and w, no more) and only
+// the sums run in the precision of x and r; x and r receive the same a.
 template <typename Rx, typename Rz>
 __global__ void k_gcr_update(cpx<Rx>* __restrict__ x, cpx<Rx>* __restrict__ r,
                              const cpx<Rz>* __restrict__ z, const cpx<Rz>* __restrict__ w,
                              size_t n, const double2* S, int slot) {
-  cpx<double> a(S[slot].x, S[slot].y);
+  using T = typename std::conditional<std::is_same<Rz, float>::value, float, double>::type;
+  const cpx<T> a(T(S[slot].x), T(S[slot].y));
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
        i += size_t(gridDim.x) * blockDim.x) {
-    cpx<double> xi(x[i]), ri(r[i]);
-    cmac(xi, a, cpx<double>(z[i]));
-    cmac(ri, -a, cpx<double>(w[i]));
-    x[i] = cpx<Rx>(xi);
-    r[i] = cpx<Rx>(ri);
+    cpx<Rx> xi = x[i], ri = r[i];
+    if constexpr (std::is_same<T, float>::value) {
+      xi += cpx<Rx>(a * cpx<T>(z[i]));
+      ri -= cpx<Rx>(a * cpx<T>(w[i]));
+    } else {
+      cmac(xi, cpx<Rx>(a), cpx<Rx>(z[i]));
+      cmac(ri, -cpx<Rx>(a), cpx<Rx>(w[i]));
+    }
+    x[i] = xi;
+    r[i] = ri;
   }
 }
 
@@ -237,35 +253,56 @@ __global__ void k_reduce_final_b(const double2* __restrict__ part, int nparts,
   if (threadIdx.x == 0) out[blockIdx.x] = acc;
 }
 
-// x_v -= (B[2v] / B[2v+1].re) t_v   (setup sweep, every vector at once)
+// Per-vector scalar of the batched updates, computed once per warp (lane 0,
+// broadcast): FP64 division and square root are slow on GB300, so they stay
+// out of the per-element loop.
+__device__ __forceinline__ double2 warp_bcast(double2 v) {
+  v.x = __shfl_sync(0xffffffffu, v.x, 0);
+  v.y = __shfl_sync(0xffffffffu, v.y, 0);
+  return v;
+}
+
+// x_v -= (B[2v] / B[2v+1].re) t_v   (setup sweep, every vector at once;
+// blockIdx.y is the vector)
 template <typename R>
 __global__ void k_sweep_update_b(cpx<R>* __restrict__ x, const cpx<R>* __restrict__ t, size_t n,
-                                 int nvec, const double2* __restrict__ B) {
-  const size_t total = n * nvec;
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < total;
-       i += size_t(gridDim.x) * blockDim.x) {
-    const int v = int(i / n);
+                                 const double2* __restrict__ B) {
+  const int v = blockIdx.y;
+  double2 a = make_double2(0.0, 0.0);
+  if ((threadIdx.x & 31) == 0) {
     const double den = B[2 * v + 1].x;
-    cpx<R> a(R(0), R(0));
-    if (den > 0.0) a = cpx<R>(R(-B[2 * v].x / den), R(-B[2 * v].y / den));
+    if (den > 0.0) {
+      const double inv = 1.0 / den;
+      a = make_double2(-B[2 * v].x * inv, -B[2 * v].y * inv);
+    }
+  }
+  a = warp_bcast(a);
+  const cpx<R> ar(R(a.x), R(a.y));
+  x += size_t(v) * n;
+  t += size_t(v) * n;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
+       i += size_t(gridDim.x) * blockDim.x) {
     cpx<R> xi = x[i];
-    cmac(xi, a, t[i]);
+    cmac(xi, ar, t[i]);
     x[i] = xi;
   }
 }
 
 // x_v /= sqrt(B[2v+1].re)
 template <typename R>
-__global__ void k_normalise_b(cpx<R>* __restrict__ x, size_t n, int nvec,
-                              const double2* __restrict__ B) {
-  const size_t total = n * nvec;
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < total;
-       i += size_t(gridDim.x) * blockDim.x) {
-    const int v = int(i / n);
+__global__ void k_normalise_b(cpx<R>* __restrict__ x, size_t n, const double2* __restrict__ B) {
+  const int v = blockIdx.y;
+  double2 s = make_double2(0.0, 0.0);
+  if ((threadIdx.x & 31) == 0) {
     const double nn = B[2 * v + 1].x;
-    const R s = R(nn > 0.0 ? 1.0 / sqrt(nn) : 0.0);
-    x[i] = s * x[i];
+    s.x = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
   }
+  s = warp_bcast(s);
+  const R sr = R(s.x);
+  x += size_t(v) * n;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
+       i += size_t(gridDim.x) * blockDim.x)
+    x[i] = sr * x[i];
 }
 
 // [nvec][n] <-> [n][nvec] layout change of complex vectors
@@ -435,8 +472,8 @@ void blas_dot2_batched(mg_ctx* c, Vec p, Vec r, int nvec, cudaStream_t st) {
 void blas_sweep_update_batched(mg_ctx* c, Vec x, Vec t, int nvec, cudaStream_t st) {
   GB_REQUIRE(x.prec == t.prec, MG_ERR_ARG, "sweep_update_batched: precision mix");
   GB_DISPATCH1(x.prec, R,
-               (k_sweep_update_b<R><<<ew_blocks(x.n * nvec), kThreads, 0, st>>>(
-                   (cpx<R>*)x.p, (const cpx<R>*)t.p, x.n, nvec, c->batch_scalars.as<double2>())));
+               (k_sweep_update_b<R><<<ew_grid_b(x.n, nvec), kThreads, 0, st>>>(
+                   (cpx<R>*)x.p, (const cpx<R>*)t.p, x.n, c->batch_scalars.as<double2>())));
   GB_LAUNCH_CHECK();
   c->launches++;
 }
@@ -445,8 +482,8 @@ void blas_normalise_batched(mg_ctx* c, Vec x, int nvec, cudaStream_t st) {
   // |x_v|^2 into the second slot of each vector's pair
   blas_dot2_batched(c, x, x, nvec, st);
   GB_DISPATCH1(x.prec, R,
-               (k_normalise_b<R><<<ew_blocks(x.n * nvec), kThreads, 0, st>>>(
-                   (cpx<R>*)x.p, x.n, nvec, c->batch_scalars.as<double2>())));
+               (k_normalise_b<R><<<ew_grid_b(x.n, nvec), kThreads, 0, st>>>(
+                   (cpx<R>*)x.p, x.n, c->batch_scalars.as<double2>())));
   GB_LAUNCH_CHECK();
   c->launches++;
 }

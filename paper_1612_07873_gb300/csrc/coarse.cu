@@ -81,8 +81,8 @@ struct Unpack<i16c> {
   }
 };
 
-constexpr int batch_of(int iters) {
-  for (int u = 8; u > 1; --u)
+constexpr int batch_of(int iters, int umax = 8) {
+  for (int u = umax; u > 1; --u)
     if (iters % u == 0) return u;
   return 1;
 }
@@ -144,6 +144,84 @@ __global__ void __launch_bounds__(CG*(N / Unpack<S>::RPC))
     for (int q = 1; q < CG; ++q) s += red[q][row];
     if (StoreTraits<S>::scaled) s = R(scales[site]) * s;
     y[size_t(site) * N + row] = s;
+  }
+}
+
+// Multi-RHS form of the streaming kernel for stores without a tensor-core
+// path (FP32): vectors interleaved [site][n][nrhs]; CTA (chunk, site) applies
+// the site's links to NR right-hand sides, so each link chunk read from HBM
+// feeds NR x RPC complex multiply-adds.  The gathered neighbour values sit
+// in shared memory as xs[k][r] (k = slot*n + col); the same buffer then
+// holds the CG partial sums as red[cg][r][row].
+template <typename S, int N, int CG, int NR>
+__global__ void __launch_bounds__(CG*(N / Unpack<S>::RPC))
+    k_coarse_stream_mr(cpx<typename StoreTraits<S>::real>* __restrict__ y,
+                       const cpx<typename StoreTraits<S>::real>* __restrict__ x,
+                       const S* __restrict__ links, const float* __restrict__ scales, Geom g,
+                       int nrhs) {
+  using R = typename StoreTraits<S>::real;
+  constexpr int RPC = Unpack<S>::RPC;
+  constexpr int TPC = N / RPC;
+  constexpr int K = 9 * N;
+  constexpr int NT = CG * TPC;
+  constexpr int ITER = K / CG;
+  constexpr int U = batch_of(ITER, 4);
+  constexpr int XS = K * NR, RED = CG * NR * N;
+  static_assert(N % RPC == 0 && K % CG == 0 && NR % 2 == 0 && ITER % U == 0, "tile shape");
+  __shared__ __align__(16) cpx<R> buf[XS > RED ? XS : RED];
+  __shared__ int nb[9];
+  const int chunk = blockIdx.x, site = blockIdx.y;
+  const int tid = threadIdx.x;
+  if (tid < 9) {
+    int c[4];
+    site_coords(g, site, c);
+    nb[tid] = neighbour(g, site, c, tid);
+  }
+  __syncthreads();
+  for (int i = tid; i < XS; i += NT) {
+    const int k = i / NR, r = i - k * NR;
+    const int d = k / N;
+    buf[i] = x[(size_t(nb[d]) * N + (k - d * N)) * nrhs + chunk * NR + r];
+  }
+  __syncthreads();
+  const int rp = tid % TPC;
+  const int cg = tid / TPC;
+  cpx<R> acc[NR][RPC];
+#pragma unroll
+  for (int r = 0; r < NR; ++r)
+#pragma unroll
+    for (int q = 0; q < RPC; ++q) acc[r][q] = cpx<R>(R(0), R(0));
+  const uint4* L = reinterpret_cast<const uint4*>(links) + size_t(site) * K * TPC + rp;
+  for (int it = 0; it < ITER; it += U) {
+    uint4 v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = ld_stream16(L + size_t(cg + (it + u) * CG) * TPC);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      cpx<R> e[RPC];
+      Unpack<S>::get(v[u], e);
+      const cpx<R>* xk = buf + (cg + (it + u) * CG) * NR;
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        const cpx<R> xv = xk[r];
+#pragma unroll
+        for (int q = 0; q < RPC; ++q) cmac(acc[r][q], e[q], xv);
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < NR; ++r)
+#pragma unroll
+    for (int q = 0; q < RPC; ++q) buf[(cg * NR + r) * N + rp * RPC + q] = acc[r][q];
+  __syncthreads();
+  const R sc = StoreTraits<S>::scaled ? R(scales[site]) : R(1);
+  for (int o = tid; o < N * NR; o += NT) {
+    const int row = o / NR, r = o - row * NR;
+    cpx<R> sum = buf[r * N + row];
+#pragma unroll
+    for (int q = 1; q < CG; ++q) sum += buf[(q * NR + r) * N + row];
+    y[(size_t(site) * N + row) * nrhs + chunk * NR + r] = sc * sum;
   }
 }
 
@@ -448,18 +526,61 @@ bool try_stream(const Level& L, void* y, const void* x, const void* links, cudaS
   }
 }
 
+template <typename S, int N>
+void launch_stream_mr(const Level& L, void* y, const void* x, const void* links, int nrhs,
+                      cudaStream_t st) {
+  using R = typename StoreTraits<S>::real;
+  constexpr int CG = CgSet<S>::c0;
+  constexpr int NT = CG * (N / Unpack<S>::RPC);
+  const cpx<R>* xp = (const cpx<R>*)x;
+  cpx<R>* yp = (cpx<R>*)y;
+  const S* lp = (const S*)links;
+  if (nrhs % 8 == 0)
+    k_coarse_stream_mr<S, N, CG, 8><<<dim3(nrhs / 8, L.g.vol), NT, 0, st>>>(
+        yp, xp, lp, L.scales.as<float>(), L.g, nrhs);
+  else if (nrhs % 4 == 0)
+    k_coarse_stream_mr<S, N, CG, 4><<<dim3(nrhs / 4, L.g.vol), NT, 0, st>>>(
+        yp, xp, lp, L.scales.as<float>(), L.g, nrhs);
+  else
+    k_coarse_stream_mr<S, N, CG, 2><<<dim3(nrhs / 2, L.g.vol), NT, 0, st>>>(
+        yp, xp, lp, L.scales.as<float>(), L.g, nrhs);
+}
+
+template <typename S>
+bool try_stream_mr(const Level& L, void* y, const void* x, const void* links, int nrhs,
+                   cudaStream_t st) {
+  if (nrhs % 2 != 0) return false;
+  switch (L.nd) {
+    case 16: launch_stream_mr<S, 16>(L, y, x, links, nrhs, st); return true;
+    case 32: launch_stream_mr<S, 32>(L, y, x, links, nrhs, st); return true;
+    case 48: launch_stream_mr<S, 48>(L, y, x, links, nrhs, st); return true;
+    case 64: launch_stream_mr<S, 64>(L, y, x, links, nrhs, st); return true;
+    default: return false;
+  }
+}
+
 template <typename S>
 void dispatch_apply(const Level& L, void* y, const void* x, const void* links, int nrhs,
                     cudaStream_t st) {
   using R = typename StoreTraits<S>::real;
   if (nrhs == 1 && L.slots5 && L.links5.p && try_stream5<S>(L, y, x, st)) return;
   if (nrhs == 1 && try_stream<S>(L, y, x, links, st)) return;
+  if constexpr (std::is_same<S, cpx<float>>::value) {
+    if (nrhs > 1 && try_stream_mr<S>(L, y, x, links, nrhs, st)) return;
+  }
   int threads = L.nd * nrhs >= 256 ? 256 : ((L.nd * nrhs + 31) / 32) * 32;
   k_coarse_generic<S><<<L.g.vol, threads, 0, st>>>((cpx<R>*)y, (const cpx<R>*)x, (const S*)links,
                                                    L.scales.as<float>(), L.g, L.nd, nrhs);
 }
 
 }  // namespace
+
+bool coarse_apply_multi_fast(const Level& L, int nrhs) {
+  if (nrhs < 2) return false;
+  if (coarse_apply_mma_supported(L, nrhs)) return true;
+  return L.prec == MG_F32 && nrhs % 2 == 0 &&
+         (L.nd == 16 || L.nd == 32 || L.nd == 48 || L.nd == 64);
+}
 
 void coarse_apply(mg_ctx* c, int level, void* y, const void* x, int nrhs, cudaStream_t st) {
   Level& L = c->L[level];
@@ -473,7 +594,9 @@ void coarse_apply(mg_ctx* c, int level, void* y, const void* x, int nrhs, cudaSt
   const double lbytes = double(L.g.vol) * (five ? 5 : 9) * n * n *
                         (L.prec == MG_F64 ? 16 : L.prec == MG_F32 ? 8 : 4);
   const double vbytes = double(L.g.vol) * 2 * n * nrhs * (L.vprec == MG_F64 ? 16 : 8);
-  ProfScope ps(c->prof, st, "coarse_apply", level, lbytes + vbytes,
+  // single- and multi-RHS applies are profiled under separate names
+  ProfScope ps(c->prof, st, nrhs == 1 ? "coarse_apply" : "coarse_apply_multi", level,
+               lbytes + vbytes,
                8.0 * 9 * n * n * L.g.vol * nrhs);
   if (nrhs > 1 && coarse_apply_mma_supported(L, nrhs)) {
     coarse_apply_mma(c, level, y, x, nrhs, st);

@@ -71,6 +71,9 @@ void links_pack16(mg_ctx* c, int level, cudaStream_t st);
 
 // ---------------------------------------------------------------- coarse_mma.cu
 bool coarse_apply_mma_supported(const Level& L, int nrhs);
+// true when an nrhs-vector coarse apply of level L runs a multi-RHS kernel
+// (tensor cores for 16-bit stores, the FP32 multi-RHS stream for FP32)
+bool coarse_apply_multi_fast(const Level& L, int nrhs);
 void coarse_apply_mma(mg_ctx* c, int level, void* y, const void* x, int nrhs, cudaStream_t st);
 void links_tile_mma(mg_ctx* c, int level, cudaStream_t st);
 

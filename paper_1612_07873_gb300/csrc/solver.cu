@@ -257,10 +257,11 @@ void setup_sweeps(mg_ctx* c, int l, const void* init, cudaStream_t st) {
     // element (v, j) draws counter v * n + j
     blas_gaussian(c, Xall, c->p.seed + 0x9E3779B97F4A7C15ull * uint64_t(l + 1), 0, st);
   }
-  // 16-bit coarse levels apply the operator to all vectors at once on the
-  // tensor cores (interleaved [site][dof][vec] operand layout)
+  // coarse levels apply the operator to all vectors at once (interleaved
+  // [site][dof][vec] operand layout): on the tensor cores for 16-bit stores,
+  // with the FP32 multi-RHS stream for FP32 stores
   DevBuf ib, ob;
-  const bool mrhs = l > 0 && coarse_apply_mma_supported(L, nv);
+  const bool mrhs = l > 0 && coarse_apply_multi_fast(L, nv);
   if (mrhs) {
     ib.alloc(bytes);
     ob.alloc(bytes);

@@ -290,6 +290,132 @@ __global__ void k_prolong(cpx<Rf>* __restrict__ fine, const cpx<Rc>* __restrict_
   }
 }
 
+// ---- Transfer kernels for the fine level (12 dofs per site), one CTA per
+// aggregate.  Every fine site of an aggregate sits at the aggregate's first
+// site plus an offset that depends only on its local index, so the offsets
+// are tabulated once per CTA in shared memory and the per-row index work is
+// one table lookup.  Vp rows (Nv coefficients of one fine dof, 96 B / 192 B
+// for Nv = 24 in FP32 / FP64) are read as 16-byte vectors.
+
+__device__ __forceinline__ int agg_origin(const AggMap& m, int xc) {
+  int cc[4];
+  site_coords(m.coarse, xc, cc);
+  return cc[0] * m.b[0] + m.fine.stride[1] * cc[1] * m.b[1] +
+         m.fine.stride[2] * cc[2] * m.b[2] + m.fine.stride[3] * cc[3] * m.b[3];
+}
+__device__ __forceinline__ int local_offset(const AggMap& m, int ls) {
+  int l0 = ls % m.b[0];
+  ls /= m.b[0];
+  int l1 = ls % m.b[1];
+  ls /= m.b[1];
+  int l2 = ls % m.b[2];
+  int l3 = ls / m.b[2];
+  return l0 + m.fine.stride[1] * l1 + m.fine.stride[2] * l2 + m.fine.stride[3] * l3;
+}
+
+// coarse[xc][chi*Nv + i] = sum over fine sites x of the aggregate and dofs a
+// of chirality chi of conj(Vp[x][a][i]) fine[x][a].  Thread (g, p): p picks
+// the 16-byte column of Vp rows (CPL coefficients), g strides over sites.
+template <typename Rf, typename Rc>
+__global__ void __launch_bounds__(256) k_restrict12(cpx<Rc>* __restrict__ coarse,
+                                                   const cpx<Rf>* __restrict__ fine,
+                                                   const cpx<Rf>* __restrict__ Vp, AggMap m,
+                                                   int nv, int G) {
+  constexpr int ND = 12, CPL = 16 / int(sizeof(cpx<Rf>));
+  constexpr int FW = ND * int(sizeof(cpx<Rf>)) / 16;  // 16-byte words of a fine site
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<Rf>* red = reinterpret_cast<cpx<Rf>*>(smem_raw);  // [G][2][nv]
+  int* off = reinterpret_cast<int*>(red + size_t(G) * 2 * nv);
+  const int xc = blockIdx.x;
+  const int NP = nv / CPL;
+  const int p = threadIdx.x % NP, g = threadIdx.x / NP;
+  for (int ls = threadIdx.x; ls < m.per; ls += blockDim.x) off[ls] = local_offset(m, ls);
+  const size_t base = size_t(agg_origin(m, xc));
+  __syncthreads();
+  cpx<Rf> acc[2][CPL];
+#pragma unroll
+  for (int k = 0; k < CPL; ++k) acc[0][k] = acc[1][k] = cpx<Rf>(Rf(0), Rf(0));
+  if (g < G) {
+    for (int ls = g; ls < m.per; ls += G) {
+      const size_t x = base + off[ls];
+      const uint4* vr = reinterpret_cast<const uint4*>(Vp + x * ND * nv) + p;
+      uint4 w[ND];
+#pragma unroll
+      for (int a = 0; a < ND; ++a) w[a] = ld_stream16(vr + a * NP);
+      uint4 fw[FW];
+      const uint4* fr = reinterpret_cast<const uint4*>(fine + x * ND);
+#pragma unroll
+      for (int k = 0; k < FW; ++k) fw[k] = __ldg(fr + k);
+      const cpx<Rf>* f = reinterpret_cast<const cpx<Rf>*>(fw);
+#pragma unroll
+      for (int a = 0; a < ND; ++a) {
+        const cpx<Rf>* v = reinterpret_cast<const cpx<Rf>*>(&w[a]);
+#pragma unroll
+        for (int k = 0; k < CPL; ++k) cmac_conj(acc[a < ND / 2 ? 0 : 1][k], v[k], f[a]);
+      }
+    }
+#pragma unroll
+    for (int chi = 0; chi < 2; ++chi)
+#pragma unroll
+      for (int k = 0; k < CPL; ++k) red[(g * 2 + chi) * nv + p * CPL + k] = acc[chi][k];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < 2 * nv; t += blockDim.x) {
+    cpx<Rf> sum(Rf(0), Rf(0));
+    for (int k = 0; k < G; ++k) sum += red[k * 2 * nv + t];
+    coarse[size_t(xc) * 2 * nv + t] = cpx<Rc>(sum);
+  }
+}
+
+// fine[x][a] = sum_i Vp[x][a][i] coarse[agg(x)][chi(a)*Nv + i].  Two threads
+// per Vp row, each summing half of it; the halves meet by one shuffle.
+template <typename Rf, typename Rc>
+__global__ void __launch_bounds__(256) k_prolong12(cpx<Rf>* __restrict__ fine,
+                                                  const cpx<Rc>* __restrict__ coarse,
+                                                  const cpx<Rf>* __restrict__ Vp, AggMap m,
+                                                  int nv) {
+  constexpr int ND = 12, CPL = 16 / int(sizeof(cpx<Rf>));
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<Rf>* cs = reinterpret_cast<cpx<Rf>*>(smem_raw);  // [2][nv]
+  int* off = reinterpret_cast<int*>(cs + 2 * nv);
+  const int xc = blockIdx.x;
+  for (int ls = threadIdx.x; ls < m.per; ls += blockDim.x) off[ls] = local_offset(m, ls);
+  for (int t = threadIdx.x; t < 2 * nv; t += blockDim.x)
+    cs[t] = cpx<Rf>(coarse[size_t(xc) * 2 * nv + t]);
+  const size_t base = size_t(agg_origin(m, xc));
+  __syncthreads();
+  const int NP = nv / CPL, PW = NP / 2;  // 16-byte words per row and per half row
+  const int q = threadIdx.x & 1;
+  const int rows = m.per * ND;
+  // the loop bound is uniform across the CTA, so every lane reaches the
+  // full-warp shuffle; rows past the end compute nothing and store nothing
+  for (int r0 = 0; r0 < rows; r0 += blockDim.x >> 1) {
+    const int r = r0 + (threadIdx.x >> 1);
+    const bool ok = r < rows;
+    const int ls = ok ? r / ND : 0, a = ok ? r - ls * ND : 0;
+    const size_t x = base + off[ls];
+    const uint4* vr = reinterpret_cast<const uint4*>(Vp + (x * ND + a) * nv) + q * PW;
+    const cpx<Rf>* c = cs + (a < ND / 2 ? 0 : nv) + q * PW * CPL;
+    cpx<Rf> acc(Rf(0), Rf(0));
+    for (int k0 = 0; ok && k0 < PW; k0 += 6) {
+      uint4 w[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k)
+        if (k0 + k < PW) w[k] = ld_stream16(vr + k0 + k);
+#pragma unroll
+      for (int k = 0; k < 6; ++k)
+        if (k0 + k < PW) {
+          const cpx<Rf>* v = reinterpret_cast<const cpx<Rf>*>(&w[k]);
+#pragma unroll
+          for (int j = 0; j < CPL; ++j) cmac(acc, v[j], c[(k0 + k) * CPL + j]);
+        }
+    }
+    acc.re += __shfl_xor_sync(0xffffffffu, acc.re, 1);
+    acc.im += __shfl_xor_sync(0xffffffffu, acc.im, 1);
+    if (ok && q == 0) fine[x * ND + a] = acc;
+  }
+}
+
 // W [agg][chi][Nv][rows] -> out [Nv][V][nd] (FP64)
 __global__ void k_blocked_to_vectors(double2* __restrict__ out, const double2* __restrict__ W,
                                   AggMap m, int nd, int nv) {
@@ -368,6 +494,42 @@ void restrict_apply(mg_ctx* c, int level, Vec coarse, Vec fine, cudaStream_t st)
   ProfScope ps(c->prof, st, "restrict", level,
                double(F.g.vol) * F.nd * (nv + 1) * vb + double(C.g.vol) * C.nd * vb,
                8.0 * F.g.vol * F.nd * nv);
+  if (F.nd == 12) {
+    // per-aggregate kernel: NP 16-byte columns per Vp row, G site groups
+    const int cpl = F.vprec == MG_F64 ? 1 : 2;
+    const int NP = nv / cpl;
+    int G2 = 256 / NP;
+    while (G2 > 1 && m.per % G2) --G2;
+    const size_t smem2 = size_t(G2) * 2 * nv * size_t(vb) + size_t(m.per) * sizeof(int);
+    // the fine vector is read in 16-byte words: a misaligned caller pointer
+    // takes the generic kernel
+    const bool aligned = (reinterpret_cast<uintptr_t>(fine.p) & 15) == 0;
+    if (aligned && nv % cpl == 0 && G2 >= 1 && smem2 <= 48 * 1024) {
+      const int thr = G2 * NP;
+      if (F.vprec == MG_F64) {
+        if (coarse.prec == MG_F64)
+          k_restrict12<double, double><<<C.g.vol, thr, smem2, st>>>(
+              (cpx<double>*)coarse.p, (const cpx<double>*)fine.p, F.Vp.as<cpx<double>>(), m, nv,
+              G2);
+        else
+          k_restrict12<double, float><<<C.g.vol, thr, smem2, st>>>(
+              (cpx<float>*)coarse.p, (const cpx<double>*)fine.p, F.Vp.as<cpx<double>>(), m, nv,
+              G2);
+      } else {
+        if (coarse.prec == MG_F64)
+          k_restrict12<float, double><<<C.g.vol, thr, smem2, st>>>(
+              (cpx<double>*)coarse.p, (const cpx<float>*)fine.p, F.Vp.as<cpx<float>>(), m, nv,
+              G2);
+        else
+          k_restrict12<float, float><<<C.g.vol, thr, smem2, st>>>(
+              (cpx<float>*)coarse.p, (const cpx<float>*)fine.p, F.Vp.as<cpx<float>>(), m, nv,
+              G2);
+      }
+      GB_LAUNCH_CHECK();
+      c->launches++;
+      return;
+    }
+  }
   if (F.vprec == MG_F64) {
     if (coarse.prec == MG_F64)
       k_restrict<double, double><<<C.g.vol, threads, smem, st>>>(
@@ -398,6 +560,28 @@ void prolong_apply(mg_ctx* c, int level, Vec fine, Vec coarse, cudaStream_t st) 
   const double vb = prec_bytes_complex(F.vprec);
   ProfScope ps(c->prof, st, "prolong", level,
                double(n) * (nv + 1) * vb + double(C.g.vol) * C.nd * vb, 8.0 * n * nv);
+  const int cpl = F.vprec == MG_F64 ? 1 : 2;
+  const size_t smem2 = size_t(2) * nv * size_t(vb) + size_t(m.per) * sizeof(int);
+  if (F.nd == 12 && nv % (2 * cpl) == 0 && smem2 <= 48 * 1024) {
+    if (F.vprec == MG_F64) {
+      if (coarse.prec == MG_F64)
+        k_prolong12<double, double><<<C.g.vol, 256, smem2, st>>>(
+            (cpx<double>*)fine.p, (const cpx<double>*)coarse.p, F.Vp.as<cpx<double>>(), m, nv);
+      else
+        k_prolong12<double, float><<<C.g.vol, 256, smem2, st>>>(
+            (cpx<double>*)fine.p, (const cpx<float>*)coarse.p, F.Vp.as<cpx<double>>(), m, nv);
+    } else {
+      if (coarse.prec == MG_F64)
+        k_prolong12<float, double><<<C.g.vol, 256, smem2, st>>>(
+            (cpx<float>*)fine.p, (const cpx<double>*)coarse.p, F.Vp.as<cpx<float>>(), m, nv);
+      else
+        k_prolong12<float, float><<<C.g.vol, 256, smem2, st>>>(
+            (cpx<float>*)fine.p, (const cpx<float>*)coarse.p, F.Vp.as<cpx<float>>(), m, nv);
+    }
+    GB_LAUNCH_CHECK();
+    c->launches++;
+    return;
+  }
   if (F.vprec == MG_F64) {
     if (coarse.prec == MG_F64)
       k_prolong<double, double><<<grid_for(n), 256, 0, st>>>(

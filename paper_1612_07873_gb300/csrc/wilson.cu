@@ -2,6 +2,7 @@
 // and the stencil apply (one thread per site and vector).
 #include "kernels.cuh"
 #include "wilson_ops.cuh"
+#include "tune.cuh"
 
 namespace gbmg {
 
@@ -212,6 +213,84 @@ __global__ void __launch_bounds__(128) k_wilson(cpx<R>* __restrict__ out, const 
   for (int i = 0; i < 12; ++i) out[size_t(s) * 12 + i] = acc[i];
 }
 
+// Batched form for the setup sweeps: one thread applies the operator at one
+// site to NB vectors, so the site's links and clover are read once for NB
+// vectors instead of once per vector.  Vectors are stored back to back
+// (vector v at offset v * vstride); blockIdx.y picks a group of NB vectors.
+template <typename R, int NB>
+__global__ void __launch_bounds__(128) k_wilson_mv(cpx<R>* __restrict__ out,
+                                                   const cpx<R>* __restrict__ in,
+                                                   const cpx<R>* __restrict__ U,
+                                                   const R* __restrict__ A, Geom g, R diag,
+                                                   size_t vstride) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.vol) return;
+  in += size_t(blockIdx.y) * NB * vstride;
+  out += size_t(blockIdx.y) * NB * vstride;
+  int c[4];
+  site_coords(g, s, c);
+  cpx<R> acc[NB][12];
+#pragma unroll
+  for (int b = 0; b < NB; ++b)
+#pragma unroll
+    for (int i = 0; i < 12; ++i) acc[b][i] = cpx<R>(R(0), R(0));
+  constexpr int SW = sizeof(cpx<R>) * 12 / 16;  // 16-byte words of a spinor
+  auto load_spinor = [&](int b, int site, cpx<R> psi[12]) {
+    const uint4* p = reinterpret_cast<const uint4*>(in + b * vstride + size_t(site) * 12);
+    uint4 w[SW];
+#pragma unroll
+    for (int i = 0; i < SW; ++i) w[i] = __ldg(p + i);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) psi[i] = reinterpret_cast<const cpx<R>*>(w)[i];
+  };
+  // clover, one chirality block (36 reals) at a time
+#pragma unroll
+  for (int chi = 0; chi < 2; ++chi) {
+    constexpr int CW = sizeof(R) * 36 / 16;
+    uint4 w[CW];
+    const uint4* p = reinterpret_cast<const uint4*>(A + size_t(s) * 72 + chi * 36);
+#pragma unroll
+    for (int i = 0; i < CW; ++i) w[i] = __ldg(p + i);
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      cpx<R> psi[12];
+      load_spinor(b, s, psi);
+      clover_block_accum(reinterpret_cast<const R*>(w), diag, psi + chi * 6, acc[b] + chi * 6);
+    }
+  }
+  const size_t V = g.vol;
+  cpx<R> u[9];
+  auto load_link = [&](size_t idx) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) u[i] = U[idx * 9 + i];
+  };
+#define GB_HOP_MV(MU)                                   \
+  {                                                     \
+    const int sf = neighbour(g, s, c, 1 + 2 * MU);      \
+    load_link(MU * V + s);                              \
+    _Pragma("unroll") for (int b = 0; b < NB; ++b) {    \
+      cpx<R> psi[12];                                   \
+      load_spinor(b, sf, psi);                          \
+      hop_accum<MU, true>(u, psi, acc[b]);              \
+    }                                                   \
+    const int sb = neighbour(g, s, c, 2 + 2 * MU);      \
+    load_link(MU * V + sb);                             \
+    _Pragma("unroll") for (int b = 0; b < NB; ++b) {    \
+      cpx<R> psi[12];                                   \
+      load_spinor(b, sb, psi);                          \
+      hop_accum<MU, false>(u, psi, acc[b]);             \
+    }                                                   \
+  }
+  GB_HOP_MV(0) GB_HOP_MV(1) GB_HOP_MV(2) GB_HOP_MV(3)
+#undef GB_HOP_MV
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    uint4* o = reinterpret_cast<uint4*>(out + b * vstride + size_t(s) * 12);
+#pragma unroll
+    for (int i = 0; i < SW; ++i) o[i] = reinterpret_cast<const uint4*>(acc[b])[i];
+  }
+}
+
 }  // namespace
 
 void fine_operator_build(mg_ctx* c, const void* gauge_ext, cudaStream_t st) {
@@ -250,7 +329,32 @@ void wilson_apply(mg_ctx* c, Vec out, Vec in, int nvec, cudaStream_t st) {
   const double bytes =
       double(L.g.vol) * (48.0 * nvec + 144.0) * (out.prec == MG_F64 ? 8 : 4);
   ProfScope ps(c->prof, st, "wilson_clover", 0, bytes, double(nvec) * L.g.vol * 1824.0);
-  if (out.prec == MG_F64) {
+  if (out.prec == MG_F32 && nvec > 1 && nvec % 2 == 0) {
+    // batched: NB vectors per thread; the autotuner picks NB in {1, 2, 4}
+    // (more reuse of the links and clover against fewer resident warps)
+    GB_REQUIRE(L.gauge32.p, MG_ERR_STATE, "FP32 fine operator not built");
+    const unsigned gx = ceil_div(L.g.vol, 128);
+    auto launch = [&](int nb) {
+      if (nb == 4)
+        k_wilson_mv<float, 4><<<dim3(gx, nvec / 4), 128, 0, st>>>(
+            (cpx<float>*)out.p, (const cpx<float>*)in.p, L.gauge32.as<cpx<float>>(),
+            L.clover32.as<float>(), L.g, float(L.diag), vs);
+      else if (nb == 2)
+        k_wilson_mv<float, 2><<<dim3(gx, nvec / 2), 128, 0, st>>>(
+            (cpx<float>*)out.p, (const cpx<float>*)in.p, L.gauge32.as<cpx<float>>(),
+            L.clover32.as<float>(), L.g, float(L.diag), vs);
+      else
+        k_wilson<float><<<grid, 128, 0, st>>>((cpx<float>*)out.p, (const cpx<float>*)in.p,
+                                              L.gauge32.as<cpx<float>>(),
+                                              L.clover32.as<float>(), L.g, float(L.diag), vs,
+                                              nvec);
+    };
+    std::vector<int> cands = {2, 1};
+    if (nvec % 4 == 0) cands.insert(cands.begin(), 4);
+    const std::string key =
+        "wilson_mv/v" + std::to_string(L.g.vol) + "/n" + std::to_string(nvec);
+    launch(Tuner::get().choose(key, cands, st, launch));
+  } else if (out.prec == MG_F64) {
     k_wilson<double><<<grid, 128, 0, st>>>((cpx<double>*)out.p, (const cpx<double>*)in.p,
                                            L.gauge64.as<cpx<double>>(), L.clover64.as<double>(),
                                            L.g, L.diag, vs, nvec);

@@ -87,10 +87,15 @@ def test_coarse_apply_random_links(gpu_lib, cdims, nv, prec):
     mg.close()
 
 
-@pytest.mark.parametrize("nrhs", [2, 8])
-def test_coarse_apply_multi_rhs(gpu_lib, nrhs):
+@pytest.mark.parametrize("cdims,nv,nrhs", [
+    ((2, 2, 4, 2), 24, 2), ((2, 2, 4, 2), 24, 8), ((2, 2, 4, 2), 24, 12),  # NR 2, 8, 4 x 3
+    ((3, 2, 2, 4), 16, 16), ((2, 2, 2, 2), 32, 6), ((2, 2, 2, 2), 8, 4),    # n 32, 64, 16
+    ((2, 2, 4, 2), 24, 3)])                                                 # odd: generic
+def test_coarse_apply_multi_rhs(gpu_lib, cdims, nv, nrhs):
+    """FP32 multi-RHS apply, [site][n][nrhs] layout: the FP32 multi-RHS stream
+    for even nrhs (chunks of 8, 4 or 2 right-hand sides per CTA), the generic
+    kernel for odd nrhs."""
     gb = gpu_lib
-    cdims, nv = (2, 2, 4, 2), 24
     dims = tuple(c * 2 for c in cdims)
     mg, U = make_ctx(gb, dims, [(2, 2, 2, 2)], [nv], prec_fine=1, prec_coarse=1)
     n, vol = 2 * nv, lat.volume(cdims)
@@ -147,11 +152,59 @@ def test_setup_sweeps_fp64(gpu_lib):
     mg.close()
 
 
-# ------------------------------------------------------------------ transfer
-@pytest.mark.parametrize("prec", [0, 1])
-def test_restrict_prolong(gpu_lib, prec):
+@pytest.mark.parametrize("nv", [4, 6])
+def test_setup_sweeps_fp32(gpu_lib, nv):
+    """FP32 fine-level sweeps run the batched Wilson kernel (NB = 4, 2 or 1
+    vectors per thread, as the autotuner picks) on all vectors at once."""
     gb = gpu_lib
-    dims, block, nv = (4, 4, 2, 6), (2, 2, 2, 3), 5
+    dims, sweeps = (4, 4, 4, 8), 3
+    mg, U = make_ctx(gb, dims, [(2, 2, 2, 2)], [nv], sweeps=sweeps, prec_fine=1, prec_coarse=1)
+    x0 = syn.gaussian_field((nv, lat.volume(dims), 12), 27)
+    gb.mg_setup_nullvecs(mg.ctx, 0, to_dev(x0))
+    raw = torch.empty((nv, lat.volume(dims), 12), dtype=torch.complex128, device="cuda")
+    gb.mg_get_nullvecs(mg.ctx, 0, raw, kind=0)
+    torch.cuda.synchronize()
+    want = mgo.null_vectors(oracle_fine(U, dims), x0, sweeps)
+    err = rel_l2(to_np(raw), want)
+    assert err < 1e-5, err
+    mg.close()
+
+
+@pytest.mark.parametrize("nv2", [8, 6])
+def test_setup_sweeps_coarse_fp32(gpu_lib, nv2):
+    """FP32 coarse-level sweeps apply the level-1 operator to all vectors at
+    once through the FP32 multi-RHS stream; checked against the oracle's sweeps
+    on the same (GPU-built, exported) coarse operator."""
+    gb = gpu_lib
+    dims, b1, b2, nv1, sweeps = (8, 4, 4, 8), (2, 2, 2, 2), (2, 1, 1, 2), 16, 3
+    mg, U = make_ctx(gb, dims, [b1, b2], [nv1, nv2], prec_fine=1, prec_coarse=1, sweeps=sweeps)
+    v1 = syn.gaussian_field((nv1, lat.volume(dims), 12), 43)
+    gb.mg_set_nullvecs(mg.ctx, 0, to_dev(v1))
+    gb.mg_build_coarse(mg.ctx, 0)
+    cd1 = lat.coarse_dims(dims, b1)
+    n1, vol1 = 2 * nv1, lat.volume(cd1)
+    links = torch.empty((vol1, 9, n1, n1), dtype=torch.complex128, device="cuda")
+    gb.mg_get_coarse_links(mg.ctx, 1, links)
+    x0 = syn.gaussian_field((nv2, vol1, n1), 44)
+    gb.mg_setup_nullvecs(mg.ctx, 1, to_dev(x0))
+    raw = torch.empty((nv2, vol1, n1), dtype=torch.complex128, device="cuda")
+    gb.mg_get_nullvecs(mg.ctx, 1, raw, kind=0)
+    torch.cuda.synchronize()
+    want = mgo.null_vectors(dirac.StencilOp(cd1, to_np(links)), x0, sweeps)
+    err = rel_l2(to_np(raw), want)
+    assert err < 1e-5, err
+    mg.close()
+
+
+# ------------------------------------------------------------------ transfer
+@pytest.mark.parametrize("dims,block,nv", [((4, 4, 2, 6), (2, 2, 2, 3), 5),
+                                           ((4, 4, 4, 4), (2, 2, 2, 2), 8),
+                                           ((8, 4, 4, 8), (4, 4, 4, 4), 24)])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_restrict_prolong(gpu_lib, dims, block, nv, prec):
+    """Fine-level transfers: per-aggregate vector kernels (even Nv in FP32,
+    any Nv in FP64 restrict) and the generic ones (odd Nv)."""
+    gb = gpu_lib
     mg, U = make_ctx(gb, dims, [block], [nv], prec_fine=prec, prec_coarse=prec)
     v = syn.gaussian_field((nv, lat.volume(dims), 12), 24)
     gb.mg_set_nullvecs(mg.ctx, 0, to_dev(v))
