@@ -367,8 +367,9 @@ def gpu_main(args):
     forms = {}
     if args.forms:
         mg.close()
-        for fname, pc, slots in (("bf16", 2, 9), ("fp16", 3, 9), ("int16", 4, 9),
-                                 ("fp32_5blocks", 1, 5), ("bf16_5blocks", 2, 5)):
+        for fname, pc, slots, nr in (("bf16", 2, 9, 1), ("fp16", 3, 9, 1), ("int16", 4, 9, 1),
+                                     ("fp32_5blocks", 1, 5, 1), ("bf16_5blocks", 2, 5, 1),
+                                     ("fp32_mrhs8", 1, 9, 8), ("bf16_mrhs8", 2, 9, 8)):
             if fname == form:
                 continue
             pf = gb.default_params(dims=dims, block=blocks, nvec=nvecs, mass=w["mass"],
@@ -384,14 +385,36 @@ def gpu_main(args):
             gb.mg_setup_nullvecs(mf.ctx, 1, None)
             gb.mg_build_coarse(mf.ctx, 1)
             t1.record(stream)
-            xs = torch.zeros_like(b)
-            gb.mg_gcr_solve(mf.ctx, xs, b, 1e-10, 500)  # warm-up
-            sts = [gb.mg_gcr_solve(mf.ctx, xs, b, 1e-10, 500) for _ in range(3)]
-            torch.cuda.synchronize()
-            forms[fname] = {"s_per_solve_median": statistics.median(st["seconds"] for st in sts),
-                            "outer_iters": [st["iters"] for st in sts],
-                            "true_residual": max(st["true_residual"] for st in sts),
-                            "setup_ms": t0.elapsed_time(t1)}
+            if nr == 1:
+                xs = torch.zeros_like(b)
+                gb.mg_gcr_solve(mf.ctx, xs, b, 1e-10, 500)  # warm-up
+                sts = [gb.mg_gcr_solve(mf.ctx, xs, b, 1e-10, 500) for _ in range(3)]
+                torch.cuda.synchronize()
+                forms[fname] = {
+                    "s_per_solve_median": statistics.median(st["seconds"] for st in sts),
+                    "outer_iters": [st["iters"] for st in sts],
+                    "true_residual": max(st["true_residual"] for st in sts),
+                    "setup_ms": t0.elapsed_time(t1)}
+            else:
+                # nr right-hand sides per call: the workload's b and nr - 1
+                # seeded Gaussian ones; s/solve = seconds per call / nr
+                g = torch.Generator(device=dev).manual_seed(w["seed"] + 77)
+                bm = torch.randn((nr,) + tuple(b.shape), dtype=torch.complex128, device=dev,
+                                 generator=g)
+                bm[0].copy_(b)
+                xm = torch.zeros_like(bm)
+                gb.mg_gcr_solve_multi(mf.ctx, xm, bm, nr, 1e-10, 500)  # warm-up
+                calls = [gb.mg_gcr_solve_multi(mf.ctx, xm, bm, nr, 1e-10, 500)
+                         for _ in range(2)]
+                torch.cuda.synchronize()
+                forms[fname] = {
+                    "s_per_solve_median": statistics.median(c[0]["seconds"] for c in calls) / nr,
+                    "nrhs": nr,
+                    "s_per_call_median": statistics.median(c[0]["seconds"] for c in calls),
+                    "outer_iters": [[st["iters"] for st in c] for c in calls],
+                    "true_residual": max(st["true_residual"] for c in calls for st in c),
+                    "setup_ms": t0.elapsed_time(t1)}
+                del bm, xm
             mf.close()
     learned_setup = run_learned(args, gb, torch, ev, stream, dev) if args.learned else None
     peak, peak_kind = peaks()

@@ -58,6 +58,7 @@ extern "C" {
 #endif
 
 #define MG_MAX_LEVELS 4
+#define MG_MAX_NRHS 32   /* right-hand sides of one mg_gcr_solve_multi call */
 
 typedef enum {
   MG_OK = 0,
@@ -186,6 +187,21 @@ mg_status mg_prolong(mg_ctx* ctx, int level, void* fine_dev, const void* coarse_
  * Returns MG_ERR_NOT_CONVERGED at maxiter (x holds the last iterate).      */
 mg_status mg_gcr_solve(mg_ctx* ctx, void* x_dev, const void* b_dev, double tol, int maxiter,
                        mg_solve_stats* stats, void* stream);
+
+/* The same solve for nrhs right-hand sides at once (1 <= nrhs <=
+ * MG_MAX_NRHS).  x_dev, b_dev: nrhs fine vectors back to back,
+ * [nrhs][site][12] complex double.  Every step of the method runs on all
+ * right-hand sides in one batched launch with per-RHS scalars, so the
+ * fine links, the prolongators and the coarse links are read once per step
+ * for all of them (the coarse applies of FP32 and 16-bit levels run
+ * multi-RHS kernels; the 16-bit ones on the tensor cores).  The iteration
+ * stops when every right-hand side meets tol.  stats: an array of nrhs
+ * records or NULL; record v holds the step at which right-hand side v met
+ * tol (iters), its true residual and history; level_iters and seconds are
+ * totals of the call.  The solver workspace grows with nrhs (about 30 fine
+ * vectors per right-hand side).                                            */
+mg_status mg_gcr_solve_multi(mg_ctx* ctx, void* x_dev, const void* b_dev, int nrhs, double tol,
+                             int maxiter, mg_solve_stats* stats, void* stream);
 
 /* Coarse links of level l >= 1 in the external layout (see top), complex
  * double, bytes = V_l * 9 * n_l^2 * 16.  set replaces the operator of the

@@ -84,6 +84,7 @@ def _load():
         "mg_restrict": (i, [vp, i, vp, vp, vp]),
         "mg_prolong": (i, [vp, i, vp, vp, vp]),
         "mg_gcr_solve": (i, [vp, vp, vp, d, i, C.POINTER(mg_solve_stats), vp]),
+        "mg_gcr_solve_multi": (i, [vp, vp, vp, i, d, i, C.POINTER(mg_solve_stats), vp]),
         "mg_get_coarse_links": (i, [vp, i, vp, sz, vp]),
         "mg_set_coarse_links": (i, [vp, i, vp, sz, vp]),
         "mg_level_info": (i, [vp, i, C.POINTER(C.c_int), C.POINTER(C.c_int),
@@ -222,6 +223,19 @@ def mg_gcr_solve(ctx, x, b, tol=1e-10, maxiter=200, stream=None, check=True):
     return dict(status=st, iters=s.iters, restarts=s.restarts,
                 level_iters=list(s.level_iters), true_residual=s.true_residual,
                 seconds=s.seconds, history=list(s.history[:s.history_len]))
+
+
+def mg_gcr_solve_multi(ctx, x, b, nrhs, tol=1e-10, maxiter=200, stream=None, check=True):
+    """x, b: [nrhs][V][12] complex128 on the device.  Returns one stats dict
+    per right-hand side."""
+    recs = (mg_solve_stats * nrhs)()
+    st = LIB.mg_gcr_solve_multi(ctx, _ptr(x), _ptr(b), nrhs, tol, maxiter, recs,
+                                _stream(stream))
+    if check:
+        _ok(st, ctx)
+    return [dict(status=st, iters=s.iters, restarts=s.restarts,
+                 level_iters=list(s.level_iters), true_residual=s.true_residual,
+                 seconds=s.seconds, history=list(s.history[:s.history_len])) for s in recs]
 
 
 def mg_get_coarse_links(ctx, level, out, stream=None):

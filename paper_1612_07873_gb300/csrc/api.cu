@@ -164,11 +164,11 @@ mg_status mg_create(const mg_params* p, const void* gauge_dev, mg_ctx** out) {
     }
     GB_REQUIRE(!(c->L[0].vprec == MG_F32 && c->L[1].vprec == MG_F64), MG_ERR_ARG,
                "FP64 coarse levels need an FP64 fine level");
-    c->red_partials.alloc(2 * 1024 * sizeof(double2));
-    c->scalars.alloc(SC_COUNT * sizeof(double2));
+    c->red_partials.alloc(size_t(2) * 1024 * kMaxNrhs * sizeof(double2));
+    c->scalars.alloc(size_t(SC_COUNT) * kMaxNrhs * sizeof(double2));
     c->status.alloc(64);
     c->batch_scalars.alloc(2 * 64 * sizeof(double2));
-    GB_CHECK(cudaMallocHost(&c->h_scalars, SC_COUNT * sizeof(double2)));
+    GB_CHECK(cudaMallocHost(&c->h_scalars, size_t(kMaxNrhs) * sizeof(double2)));
     GB_CHECK(cudaMemset(c->scalars.p, 0, c->scalars.bytes));
     GB_CHECK(cudaMemset(c->status.p, 0, c->status.bytes));
     fine_operator_build(c, gauge_dev, 0);
@@ -291,6 +291,16 @@ mg_status mg_gcr_solve(mg_ctx* c, void* x, const void* b, double tol, int maxite
     GB_REQUIRE(x && b && x != b, MG_ERR_ARG, "gcr_solve: bad vectors");
     GB_REQUIRE(tol > 0 && maxiter > 0, MG_ERR_ARG, "gcr_solve: bad tol/maxiter");
     gcr_solve(c, x, b, tol, maxiter, stats, S(stream));
+  });
+}
+
+mg_status mg_gcr_solve_multi(mg_ctx* c, void* x, const void* b, int nrhs, double tol,
+                             int maxiter, mg_solve_stats* stats, void* stream) {
+  return guarded(c, [&] {
+    GB_REQUIRE(x && b && x != b, MG_ERR_ARG, "gcr_solve_multi: bad vectors");
+    GB_REQUIRE(nrhs >= 1 && nrhs <= MG_MAX_NRHS, MG_ERR_ARG, "gcr_solve_multi: bad nrhs");
+    GB_REQUIRE(tol > 0 && maxiter > 0, MG_ERR_ARG, "gcr_solve_multi: bad tol/maxiter");
+    gcr_solve_multi(c, x, b, nrhs, tol, maxiter, stats, S(stream));
   });
 }
 

@@ -1,7 +1,8 @@
 // Level-1 vector kernels of the solvers (Sec. VI-A: GCR, MR, setup
-// iteration).  Scalars stay on the device: a reduction writes a complex
-// double into a slot of ctx->scalars and the following update kernel reads
-// it, so smoothers and orthogonalisation never wait on the host.
+// iteration).  Scalars stay on the device: a reduction writes one complex
+// double per right-hand side into a row of ctx->scalars and the following
+// update kernel reads it, so smoothers and orthogonalisation never wait on
+// the host.
 // Reductions are two-stage with a grid that depends only on the length,
 // so results are bitwise reproducible run to run.
 #include <type_traits>
@@ -63,157 +64,25 @@ using acc_t = typename std::conditional<std::is_same<Ra, float>::value &&
                                             std::is_same<Rb, float>::value,
                                         float, double>::type;
 
+// ---- Solver kernels.  Every vector argument holds nr right-hand sides back
+// to back (rhs v at offset v * n); blockIdx.y is the right-hand side and
+// per-RHS scalars are read from a row S[v] of the scalar table.
+
 template <typename Ra, typename Rb, typename T>
 __global__ void k_dot_partial(const cpx<Ra>* __restrict__ a, const cpx<Rb>* __restrict__ b,
                               size_t n, double2* __restrict__ part) {
   __shared__ double2 sh[32];
+  a += size_t(blockIdx.y) * n;
+  b += size_t(blockIdx.y) * n;
   cpx<T> acc(T(0), T(0));
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
        i += size_t(gridDim.x) * blockDim.x)
     cmac_conj(acc, cpx<T>(a[i]), cpx<T>(b[i]));
   double2 d = block_sum(make_double2(double(acc.re), double(acc.im)), sh);
-  if (threadIdx.x == 0) part[blockIdx.x] = d;
+  if (threadIdx.x == 0) part[size_t(blockIdx.y) * gridDim.x + blockIdx.x] = d;
 }
 
-template <typename Ra, typename Rb>
-__global__ void k_dot2_partial(const cpx<Ra>* __restrict__ p, const cpx<Rb>* __restrict__ r,
-                               size_t n, double2* __restrict__ part, int stride) {
-  using T = acc_t<Ra, Rb>;
-  __shared__ double2 sh[32];
-  cpx<T> a_pr(T(0), T(0));
-  T a_pp = T(0);
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
-       i += size_t(gridDim.x) * blockDim.x) {
-    cpx<T> x(p[i]), y(r[i]);
-    cmac_conj(a_pr, x, y);
-    a_pp = fma(x.re, x.re, fma(x.im, x.im, a_pp));
-  }
-  double2 pr = block_sum(make_double2(double(a_pr.re), double(a_pr.im)), sh);
-  __syncthreads();
-  double2 pp = block_sum(make_double2(double(a_pp), 0.0), sh);
-  if (threadIdx.x == 0) {
-    part[blockIdx.x] = pr;
-    part[stride + blockIdx.x] = pp;
-  }
-}
-
-__global__ void k_reduce_final(const double2* __restrict__ part, int nparts, double2* out) {
-  __shared__ double2 sh[32];
-  double2 acc = make_double2(0.0, 0.0);
-  for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
-    acc.x += part[i].x;
-    acc.y += part[i].y;
-  }
-  acc = block_sum(acc, sh);
-  if (threadIdx.x == 0) *out = acc;
-}
-
-template <typename Ry, typename Rx>
-__global__ void k_copy(cpx<Ry>* __restrict__ y, const cpx<Rx>* __restrict__ x, size_t n) {
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
-       i += size_t(gridDim.x) * blockDim.x)
-    y[i] = cpx<Ry>(x[i]);
-}
-
-template <typename Ry, typename Rx>
-__global__ void k_axpy(cpx<Ry>* __restrict__ y, const cpx<Rx>* __restrict__ x, size_t n,
-                       double are, double aim, const double2* __restrict__ S, int slot,
-                       double sign) {
-  using T = acc_t<Ry, Rx>;
-  cpx<double> a(are, aim);
-  if (S) a = cpx<double>(sign * S[slot].x, sign * S[slot].y);
-  const cpx<T> at(a);
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
-       i += size_t(gridDim.x) * blockDim.x) {
-    cpx<T> yy(y[i]);
-    cmac(yy, at, cpx<T>(x[i]));
-    y[i] = cpx<Ry>(yy);
-  }
-}
-
-template <typename Ro, typename Rb, typename Ra>
-__global__ void k_sub(cpx<Ro>* __restrict__ o, const cpx<Rb>* __restrict__ b,
-                      const cpx<Ra>* __restrict__ ax, size_t n) {
-  using T = acc_t<Ro, acc_t<Rb, Ra>>;
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
-       i += size_t(gridDim.x) * blockDim.x)
-    o[i] = cpx<Ro>(cpx<T>(b[i]) - cpx<T>(ax[i]));
-}
-
-// x += a r ; r -= a p  with a = omega S[spr] / S[spp].re
-template <typename R>
-__global__ void k_mr_update(cpx<R>* __restrict__ x, cpx<R>* __restrict__ r,
-                            const cpx<R>* __restrict__ p, size_t n, const double2* S, int spr,
-                            int spp, double omega) {
-  double den = S[spp].x;
-  cpx<double> a(0.0, 0.0);
-  if (den > 0.0) a = cpx<double>(omega * S[spr].x / den, omega * S[spr].y / den);
-  cpx<R> ar(R(a.re), R(a.im));
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
-       i += size_t(gridDim.x) * blockDim.x) {
-    cpx<R> ri = r[i], xi = x[i];
-    cmac(xi, ar, ri);
-    cmac(ri, -ar, p[i]);
-    x[i] = xi;
-    r[i] = ri;
-  }
-}
-
-template <typename Ra, typename Rb>
-__global__ void k_scale_invnorm(cpx<Ra>* __restrict__ a, cpx<Rb>* __restrict__ b, size_t n,
-                                const double2* S, int slot) {
-  const double s = S[slot].x > 0.0 ? 1.0 / sqrt(S[slot].x) : 0.0;
-  const Ra sa = Ra(s);
-  const Rb sb = Rb(s);
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
-       i += size_t(gridDim.x) * blockDim.x) {
-    a[i] = sa * a[i];
-    if (b) b[i] = sb * b[i];
-  }
-}
-
-// x += a z ; r -= a w.  With FP32 directions z, w the products a z and a w
-// are formed in FP32 (they carry the precision of z and w, no more) and only
-// the sums run in the precision of x and r; x and r receive the same a.
-template <typename Rx, typename Rz>
-__global__ void k_gcr_update(cpx<Rx>* __restrict__ x, cpx<Rx>* __restrict__ r,
-                             const cpx<Rz>* __restrict__ z, const cpx<Rz>* __restrict__ w,
-                             size_t n, const double2* S, int slot) {
-  using T = typename std::conditional<std::is_same<Rz, float>::value, float, double>::type;
-  const cpx<T> a(T(S[slot].x), T(S[slot].y));
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
-       i += size_t(gridDim.x) * blockDim.x) {
-    cpx<Rx> xi = x[i], ri = r[i];
-    if constexpr (std::is_same<T, float>::value) {
-      xi += cpx<Rx>(a * cpx<T>(z[i]));
-      ri -= cpx<Rx>(a * cpx<T>(w[i]));
-    } else {
-      cmac(xi, cpx<Rx>(a), cpx<Rx>(z[i]));
-      cmac(ri, -cpx<Rx>(a), cpx<Rx>(w[i]));
-    }
-    x[i] = xi;
-    r[i] = ri;
-  }
-}
-
-// x -= (S[qt] / S[qq].re) t
-template <typename R>
-__global__ void k_sweep_update(cpx<R>* __restrict__ x, const cpx<R>* __restrict__ t, size_t n,
-                               const double2* S, int sqt, int sqq) {
-  double den = S[sqq].x;
-  cpx<double> a(0.0, 0.0);
-  if (den > 0.0) a = cpx<double>(-S[sqt].x / den, -S[sqt].y / den);
-  cpx<R> ar(R(a.re), R(a.im));
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
-       i += size_t(gridDim.x) * blockDim.x) {
-    cpx<R> xi = x[i];
-    cmac(xi, ar, t[i]);
-    x[i] = xi;
-  }
-}
-
-// ---- batched forms over nvec vectors stored back to back (vector v at
-// offset v * n); blockIdx.y is the vector.
+// <p, r> and |p|^2 in one pass; partials at part[(2 v + k) * gridDim.x + block]
 template <typename Ra, typename Rb>
 __global__ void k_dot2_partial_b(const cpx<Ra>* __restrict__ p, const cpx<Rb>* __restrict__ r,
                                  size_t n, double2* __restrict__ part) {
@@ -239,7 +108,7 @@ __global__ void k_dot2_partial_b(const cpx<Ra>* __restrict__ p, const cpx<Rb>* _
   }
 }
 
-// out[2 v + k] = sum of the nparts partials of (vector v, quantity k)
+// out[b] = sum of the nparts partials of row b (one block per row)
 __global__ void k_reduce_final_b(const double2* __restrict__ part, int nparts,
                                  double2* __restrict__ out) {
   __shared__ double2 sh[32];
@@ -253,17 +122,157 @@ __global__ void k_reduce_final_b(const double2* __restrict__ part, int nparts,
   if (threadIdx.x == 0) out[blockIdx.x] = acc;
 }
 
-// Per-vector scalar of the batched updates, computed once per warp (lane 0,
-// broadcast): FP64 division and square root are slow on GB300, so they stay
-// out of the per-element loop.
+// rows (2 v, 2 v + 1) of the dot2 partials into A[v] and B[v]
+__global__ void k_reduce_final_pair(const double2* __restrict__ part, int nparts,
+                                    double2* __restrict__ A, double2* __restrict__ B) {
+  __shared__ double2 sh[32];
+  const double2* src = part + size_t(blockIdx.x) * nparts;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+    acc.x += src[i].x;
+    acc.y += src[i].y;
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) (blockIdx.x & 1 ? B : A)[blockIdx.x >> 1] = acc;
+}
+
+// Per-RHS scalar of an update, formed once per warp (lane 0, broadcast):
+// FP64 division and square root are slow on GB300, so they stay out of the
+// per-element work.
 __device__ __forceinline__ double2 warp_bcast(double2 v) {
   v.x = __shfl_sync(0xffffffffu, v.x, 0);
   v.y = __shfl_sync(0xffffffffu, v.y, 0);
   return v;
 }
 
-// x_v -= (B[2v] / B[2v+1].re) t_v   (setup sweep, every vector at once;
+template <typename Ry, typename Rx>
+__global__ void k_copy(cpx<Ry>* __restrict__ y, const cpx<Rx>* __restrict__ x, size_t n) {
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
+       i += size_t(gridDim.x) * blockDim.x)
+    y[i] = cpx<Ry>(x[i]);
+}
+
+// y += a x with a host constant
+template <typename Ry, typename Rx>
+__global__ void k_axpy(cpx<Ry>* __restrict__ y, const cpx<Rx>* __restrict__ x, size_t n,
+                       double are, double aim) {
+  using T = acc_t<Ry, Rx>;
+  const cpx<T> at(cpx<double>(are, aim));
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
+       i += size_t(gridDim.x) * blockDim.x) {
+    cpx<T> yy(y[i]);
+    cmac(yy, at, cpx<T>(x[i]));
+    y[i] = cpx<Ry>(yy);
+  }
+}
+
+// y_v += sign S[v] x_v
+template <typename Ry, typename Rx>
+__global__ void k_axpy_s(cpx<Ry>* __restrict__ y, const cpx<Rx>* __restrict__ x, size_t n,
+                         const double2* __restrict__ S, double sign) {
+  using T = acc_t<Ry, Rx>;
+  const int v = blockIdx.y;
+  const cpx<T> at(T(sign * S[v].x), T(sign * S[v].y));
+  y += size_t(v) * n;
+  x += size_t(v) * n;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
+       i += size_t(gridDim.x) * blockDim.x) {
+    cpx<T> yy(y[i]);
+    cmac(yy, at, cpx<T>(x[i]));
+    y[i] = cpx<Ry>(yy);
+  }
+}
+
+template <typename Ro, typename Rb, typename Ra>
+__global__ void k_sub(cpx<Ro>* __restrict__ o, const cpx<Rb>* __restrict__ b,
+                      const cpx<Ra>* __restrict__ ax, size_t n) {
+  using T = acc_t<Ro, acc_t<Rb, Ra>>;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
+       i += size_t(gridDim.x) * blockDim.x)
+    o[i] = cpx<Ro>(cpx<T>(b[i]) - cpx<T>(ax[i]));
+}
+
+// x_v += a_v r_v ; r_v -= a_v p_v  with a_v = omega PR[v] / PP[v].re
+template <typename R>
+__global__ void k_mr_update(cpx<R>* __restrict__ x, cpx<R>* __restrict__ r,
+                            const cpx<R>* __restrict__ p, size_t n,
+                            const double2* __restrict__ PR, const double2* __restrict__ PP,
+                            double omega) {
+  const int v = blockIdx.y;
+  double2 a = make_double2(0.0, 0.0);
+  if ((threadIdx.x & 31) == 0) {
+    const double den = PP[v].x;
+    if (den > 0.0) {
+      const double f = omega / den;
+      a = make_double2(f * PR[v].x, f * PR[v].y);
+    }
+  }
+  a = warp_bcast(a);
+  const cpx<R> ar(R(a.x), R(a.y));
+  x += size_t(v) * n;
+  r += size_t(v) * n;
+  p += size_t(v) * n;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
+       i += size_t(gridDim.x) * blockDim.x) {
+    cpx<R> ri = r[i], xi = x[i];
+    cmac(xi, ar, ri);
+    cmac(ri, -ar, p[i]);
+    x[i] = xi;
+    r[i] = ri;
+  }
+}
+
+// a_v, b_v *= 1 / sqrt(S[v].re)   (b may be null)
+template <typename Ra, typename Rb>
+__global__ void k_scale_invnorm(cpx<Ra>* __restrict__ a, cpx<Rb>* __restrict__ b, size_t n,
+                                const double2* __restrict__ S) {
+  const int v = blockIdx.y;
+  double2 sv = make_double2(0.0, 0.0);
+  if ((threadIdx.x & 31) == 0) sv.x = S[v].x > 0.0 ? 1.0 / sqrt(S[v].x) : 0.0;
+  sv = warp_bcast(sv);
+  const Ra sa = Ra(sv.x);
+  const Rb sb = Rb(sv.x);
+  a += size_t(v) * n;
+  if (b) b += size_t(v) * n;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
+       i += size_t(gridDim.x) * blockDim.x) {
+    a[i] = sa * a[i];
+    if (b) b[i] = sb * b[i];
+  }
+}
+
+// x_v += S[v] z_v ; r_v -= S[v] w_v.  With FP32 directions z, w the products
+// are formed in FP32 (they carry the precision of z and w, no more) and only
+// the sums run in the precision of x and r; x and r receive the same scalar.
+template <typename Rx, typename Rz>
+__global__ void k_gcr_update(cpx<Rx>* __restrict__ x, cpx<Rx>* __restrict__ r,
+                             const cpx<Rz>* __restrict__ z, const cpx<Rz>* __restrict__ w,
+                             size_t n, const double2* __restrict__ S) {
+  using T = typename std::conditional<std::is_same<Rz, float>::value, float, double>::type;
+  const int v = blockIdx.y;
+  const cpx<T> a(T(S[v].x), T(S[v].y));
+  x += size_t(v) * n;
+  r += size_t(v) * n;
+  z += size_t(v) * n;
+  w += size_t(v) * n;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
+       i += size_t(gridDim.x) * blockDim.x) {
+    cpx<Rx> xi = x[i], ri = r[i];
+    if constexpr (std::is_same<T, float>::value) {
+      xi += cpx<Rx>(a * cpx<T>(z[i]));
+      ri -= cpx<Rx>(a * cpx<T>(w[i]));
+    } else {
+      cmac(xi, cpx<Rx>(a), cpx<Rx>(z[i]));
+      cmac(ri, -cpx<Rx>(a), cpx<Rx>(w[i]));
+    }
+    x[i] = xi;
+    r[i] = ri;
+  }
+}
+
+// ---- batched forms for the setup sweeps (nvec vectors back to back;
 // blockIdx.y is the vector)
+// x_v -= (B[2v] / B[2v+1].re) t_v
 template <typename R>
 __global__ void k_sweep_update_b(cpx<R>* __restrict__ x, const cpx<R>* __restrict__ t, size_t n,
                                  const double2* __restrict__ B) {
@@ -356,20 +365,17 @@ __global__ void k_gaussian(cpx<R>* __restrict__ v, size_t n, uint64_t seed, uint
   }
 }
 
-template <typename R>
-__global__ void k_normalise(cpx<R>* __restrict__ x, size_t n, const double2* S, int slot) {
-  const R s = R(S[slot].x > 0.0 ? 1.0 / sqrt(S[slot].x) : 0.0);
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
-       i += size_t(gridDim.x) * blockDim.x)
-    x[i] = s * x[i];
+// row of slot `slot`: the nr per-RHS values S[slot][v]
+double2* srow(mg_ctx* c, int slot) { return c->scalars.as<double2>() + size_t(slot) * kMaxNrhs; }
+
+double2* partials(mg_ctx* c, size_t count) {
+  const size_t need = count * sizeof(double2);
+  if (c->red_partials.bytes < need) c->red_partials.alloc(need);
+  return c->red_partials.as<double2>();
 }
 
-double2* scal(mg_ctx* c) { return c->scalars.as<double2>(); }
-
-void finish_reduction(mg_ctx* c, int nb, int slot, const double2* part, cudaStream_t st) {
-  k_reduce_final<<<1, 256, 0, st>>>(part, nb, scal(c) + slot);
-  GB_LAUNCH_CHECK();
-  c->launches++;
+void check_nr(const Vec& v) {
+  GB_REQUIRE(v.nr >= 1 && v.nr <= kMaxNrhs, MG_ERR_ARG, "more right-hand sides than supported");
 }
 
 }  // namespace
@@ -389,68 +395,131 @@ void finish_reduction(mg_ctx* c, int nb, int slot, const double2* part, cudaStre
   GB_DISPATCH1(pa, Ra, GB_DISPATCH1(pb, Rb, __VA_ARGS__))
 
 void blas_zero(mg_ctx* c, Vec v, cudaStream_t st) {
-  GB_CHECK(cudaMemsetAsync(v.p, 0, v.n * prec_bytes_complex(v.prec), st));
+  GB_CHECK(cudaMemsetAsync(v.p, 0, v.total() * prec_bytes_complex(v.prec), st));
 }
 
 void blas_copy(mg_ctx* c, Vec d, Vec s, cudaStream_t st) {
-  GB_REQUIRE(d.n == s.n, MG_ERR_ARG, "copy: length mismatch");
+  GB_REQUIRE(d.total() == s.total(), MG_ERR_ARG, "copy: length mismatch");
   if (d.prec == s.prec) {
-    GB_CHECK(cudaMemcpyAsync(d.p, s.p, d.n * prec_bytes_complex(d.prec), cudaMemcpyDeviceToDevice,
-                             st));
+    GB_CHECK(cudaMemcpyAsync(d.p, s.p, d.total() * prec_bytes_complex(d.prec),
+                             cudaMemcpyDeviceToDevice, st));
     return;
   }
   GB_DISPATCH2(d.prec, Ry, s.prec, Rx,
-               (k_copy<Ry, Rx><<<ew_blocks(d.n), kThreads, 0, st>>>(
-                   (cpx<Ry>*)d.p, (const cpx<Rx>*)s.p, d.n)));
+               (k_copy<Ry, Rx><<<ew_blocks(d.total()), kThreads, 0, st>>>(
+                   (cpx<Ry>*)d.p, (const cpx<Rx>*)s.p, d.total())));
   GB_LAUNCH_CHECK();
   c->launches++;
 }
 
 void blas_axpy_host(mg_ctx* c, Vec y, Vec x, double are, double aim, cudaStream_t st) {
+  GB_REQUIRE(y.total() == x.total(), MG_ERR_ARG, "axpy: length mismatch");
   GB_DISPATCH2(y.prec, Ry, x.prec, Rx,
-               (k_axpy<Ry, Rx><<<ew_blocks(y.n), kThreads, 0, st>>>(
-                   (cpx<Ry>*)y.p, (const cpx<Rx>*)x.p, y.n, are, aim, nullptr, 0, 1.0)));
+               (k_axpy<Ry, Rx><<<ew_blocks(y.total()), kThreads, 0, st>>>(
+                   (cpx<Ry>*)y.p, (const cpx<Rx>*)x.p, y.total(), are, aim)));
   GB_LAUNCH_CHECK();
   c->launches++;
 }
 
 void blas_axpy_slot(mg_ctx* c, Vec y, Vec x, int slot, double sign, cudaStream_t st) {
+  check_nr(y);
+  GB_REQUIRE(y.n == x.n && y.nr == x.nr, MG_ERR_ARG, "axpy: shape mismatch");
   GB_DISPATCH2(y.prec, Ry, x.prec, Rx,
-               (k_axpy<Ry, Rx><<<ew_blocks(y.n), kThreads, 0, st>>>(
-                   (cpx<Ry>*)y.p, (const cpx<Rx>*)x.p, y.n, 0.0, 0.0, scal(c), slot, sign)));
+               (k_axpy_s<Ry, Rx><<<ew_grid_b(y.n, y.nr), kThreads, 0, st>>>(
+                   (cpx<Ry>*)y.p, (const cpx<Rx>*)x.p, y.n, srow(c, slot), sign)));
   GB_LAUNCH_CHECK();
   c->launches++;
 }
 
 void blas_sub(mg_ctx* c, Vec o, Vec b, Vec ax, cudaStream_t st) {
-  GB_REQUIRE(o.n == b.n && b.n == ax.n, MG_ERR_ARG, "sub: length mismatch");
+  GB_REQUIRE(o.total() == b.total() && b.total() == ax.total(), MG_ERR_ARG,
+             "sub: length mismatch");
   GB_DISPATCH1(o.prec, Ro,
                GB_DISPATCH2(b.prec, Rb, ax.prec, Ra,
-                            (k_sub<Ro, Rb, Ra><<<ew_blocks(o.n), kThreads, 0, st>>>(
-                                (cpx<Ro>*)o.p, (const cpx<Rb>*)b.p, (const cpx<Ra>*)ax.p, o.n))));
+                            (k_sub<Ro, Rb, Ra><<<ew_blocks(o.total()), kThreads, 0, st>>>(
+                                (cpx<Ro>*)o.p, (const cpx<Rb>*)b.p, (const cpx<Ra>*)ax.p,
+                                o.total()))));
   GB_LAUNCH_CHECK();
   c->launches++;
 }
 
 void blas_dot(mg_ctx* c, Vec a, Vec b, int slot, cudaStream_t st, bool fp64_partials) {
-  int nb = red_blocks(a.n);
-  double2* part = c->red_partials.as<double2>();
+  check_nr(a);
+  GB_REQUIRE(a.n == b.n && a.nr == b.nr, MG_ERR_ARG, "dot: shape mismatch");
+  const int nb = red_blocks(a.n);
+  double2* part = partials(c, size_t(nb) * a.nr);
+  const dim3 grid(nb, a.nr);
   if (fp64_partials) {
     GB_DISPATCH2(a.prec, Ra, b.prec, Rb,
-                 (k_dot_partial<Ra, Rb, double><<<nb, kThreads, 0, st>>>(
+                 (k_dot_partial<Ra, Rb, double><<<grid, kThreads, 0, st>>>(
                      (const cpx<Ra>*)a.p, (const cpx<Rb>*)b.p, a.n, part)));
   } else {
     GB_DISPATCH2(a.prec, Ra, b.prec, Rb,
-                 (k_dot_partial<Ra, Rb, acc_t<Ra, Rb>><<<nb, kThreads, 0, st>>>(
+                 (k_dot_partial<Ra, Rb, acc_t<Ra, Rb>><<<grid, kThreads, 0, st>>>(
                      (const cpx<Ra>*)a.p, (const cpx<Rb>*)b.p, a.n, part)));
   }
   GB_LAUNCH_CHECK();
-  c->launches++;
-  finish_reduction(c, nb, slot, part, st);
+  k_reduce_final_b<<<a.nr, 256, 0, st>>>(part, nb, srow(c, slot));
+  GB_LAUNCH_CHECK();
+  c->launches += 2;
 }
 
 void blas_norm2(mg_ctx* c, Vec a, int slot, cudaStream_t st, bool fp64_partials) {
   blas_dot(c, a, a, slot, st, fp64_partials);
+}
+
+void blas_dot2(mg_ctx* c, Vec p, Vec r, int s_pr, int s_pp, cudaStream_t st) {
+  check_nr(p);
+  GB_REQUIRE(p.n == r.n && p.nr == r.nr, MG_ERR_ARG, "dot2: shape mismatch");
+  const int nb = red_blocks(p.n);
+  double2* part = partials(c, size_t(nb) * 2 * p.nr);
+  GB_DISPATCH2(p.prec, Ra, r.prec, Rb,
+               (k_dot2_partial_b<Ra, Rb><<<dim3(nb, p.nr), kThreads, 0, st>>>(
+                   (const cpx<Ra>*)p.p, (const cpx<Rb>*)r.p, p.n, part)));
+  GB_LAUNCH_CHECK();
+  k_reduce_final_pair<<<2 * p.nr, 256, 0, st>>>(part, nb, srow(c, s_pr), srow(c, s_pp));
+  GB_LAUNCH_CHECK();
+  c->launches += 2;
+}
+
+void blas_mr_update(mg_ctx* c, Vec x, Vec r, Vec p, int s_pr, int s_pp, double omega,
+                    cudaStream_t st) {
+  check_nr(x);
+  GB_REQUIRE(x.prec == r.prec && r.prec == p.prec, MG_ERR_ARG, "mr_update: precision mix");
+  GB_DISPATCH1(x.prec, R,
+               (k_mr_update<R><<<ew_grid_b(x.n, x.nr), kThreads, 0, st>>>(
+                   (cpx<R>*)x.p, (cpx<R>*)r.p, (const cpx<R>*)p.p, x.n, srow(c, s_pr),
+                   srow(c, s_pp), omega)));
+  GB_LAUNCH_CHECK();
+  c->launches++;
+}
+
+void blas_scale_invnorm(mg_ctx* c, Vec a, Vec b, int slot, cudaStream_t st) {
+  check_nr(a);
+  GB_DISPATCH2(a.prec, Ra, b.prec, Rb,
+               (k_scale_invnorm<Ra, Rb><<<ew_grid_b(a.n, a.nr), kThreads, 0, st>>>(
+                   (cpx<Ra>*)a.p, (cpx<Rb>*)b.p, a.n, srow(c, slot))));
+  GB_LAUNCH_CHECK();
+  c->launches++;
+}
+
+void blas_gcr_update(mg_ctx* c, Vec x, Vec r, Vec z, Vec w, int slot, cudaStream_t st) {
+  check_nr(x);
+  GB_REQUIRE(x.prec == r.prec && z.prec == w.prec, MG_ERR_ARG, "gcr_update: precision mix");
+  GB_DISPATCH2(x.prec, Rx, z.prec, Rz,
+               (k_gcr_update<Rx, Rz><<<ew_grid_b(x.n, x.nr), kThreads, 0, st>>>(
+                   (cpx<Rx>*)x.p, (cpx<Rx>*)r.p, (const cpx<Rz>*)z.p, (const cpx<Rz>*)w.p, x.n,
+                   srow(c, slot))));
+  GB_LAUNCH_CHECK();
+  c->launches++;
+}
+
+void blas_read_slot(mg_ctx* c, int slot, int nr, double* out_re, cudaStream_t st) {
+  GB_REQUIRE(nr >= 1 && nr <= kMaxNrhs, MG_ERR_ARG, "read_slot: bad count");
+  GB_CHECK(cudaMemcpyAsync(c->h_scalars, srow(c, slot), sizeof(double2) * nr,
+                           cudaMemcpyDeviceToHost, st));
+  GB_CHECK(cudaStreamSynchronize(st));
+  for (int v = 0; v < nr; ++v) out_re[v] = c->h_scalars[2 * v];
 }
 
 void blas_dot2_batched(mg_ctx* c, Vec p, Vec r, int nvec, cudaStream_t st) {
@@ -488,63 +557,6 @@ void blas_normalise_batched(mg_ctx* c, Vec x, int nvec, cudaStream_t st) {
   c->launches++;
 }
 
-void blas_dot2(mg_ctx* c, Vec p, Vec r, int s_pr, int s_pp, cudaStream_t st) {
-  int nb = red_blocks(p.n);
-  double2* part = c->red_partials.as<double2>();
-  GB_DISPATCH2(p.prec, Ra, r.prec, Rb,
-               (k_dot2_partial<Ra, Rb><<<nb, kThreads, 0, st>>>(
-                   (const cpx<Ra>*)p.p, (const cpx<Rb>*)r.p, p.n, part, kMaxRedBlocks)));
-  GB_LAUNCH_CHECK();
-  c->launches++;
-  finish_reduction(c, nb, s_pr, part, st);
-  finish_reduction(c, nb, s_pp, part + kMaxRedBlocks, st);
-}
-
-void blas_mr_update(mg_ctx* c, Vec x, Vec r, Vec p, int s_pr, int s_pp, double omega,
-                    cudaStream_t st) {
-  GB_REQUIRE(x.prec == r.prec && r.prec == p.prec, MG_ERR_ARG, "mr_update: precision mix");
-  GB_DISPATCH1(x.prec, R,
-               (k_mr_update<R><<<ew_blocks(x.n), kThreads, 0, st>>>(
-                   (cpx<R>*)x.p, (cpx<R>*)r.p, (const cpx<R>*)p.p, x.n, scal(c), s_pr, s_pp,
-                   omega)));
-  GB_LAUNCH_CHECK();
-  c->launches++;
-}
-
-void blas_scale_invnorm(mg_ctx* c, Vec a, Vec b, int slot, cudaStream_t st) {
-  GB_DISPATCH2(a.prec, Ra, b.prec, Rb,
-               (k_scale_invnorm<Ra, Rb><<<ew_blocks(a.n), kThreads, 0, st>>>(
-                   (cpx<Ra>*)a.p, (cpx<Rb>*)b.p, a.n, scal(c), slot)));
-  GB_LAUNCH_CHECK();
-  c->launches++;
-}
-
-void blas_gcr_update(mg_ctx* c, Vec x, Vec r, Vec z, Vec w, int slot, cudaStream_t st) {
-  GB_REQUIRE(x.prec == r.prec && z.prec == w.prec, MG_ERR_ARG, "gcr_update: precision mix");
-  GB_DISPATCH2(x.prec, Rx, z.prec, Rz,
-               (k_gcr_update<Rx, Rz><<<ew_blocks(x.n), kThreads, 0, st>>>(
-                   (cpx<Rx>*)x.p, (cpx<Rx>*)r.p, (const cpx<Rz>*)z.p, (const cpx<Rz>*)w.p, x.n,
-                   scal(c), slot)));
-  GB_LAUNCH_CHECK();
-  c->launches++;
-}
-
-void blas_sweep_update(mg_ctx* c, Vec x, Vec t, int s_qt, int s_qq, cudaStream_t st) {
-  GB_REQUIRE(x.prec == t.prec, MG_ERR_ARG, "sweep_update: precision mix");
-  GB_DISPATCH1(x.prec, R,
-               (k_sweep_update<R><<<ew_blocks(x.n), kThreads, 0, st>>>(
-                   (cpx<R>*)x.p, (const cpx<R>*)t.p, x.n, scal(c), s_qt, s_qq)));
-  GB_LAUNCH_CHECK();
-  c->launches++;
-}
-
-void blas_read_scalars(mg_ctx* c, int first, int count, double* out, cudaStream_t st) {
-  GB_CHECK(cudaMemcpyAsync(c->h_scalars, scal(c) + first, sizeof(double2) * count,
-                           cudaMemcpyDeviceToHost, st));
-  GB_CHECK(cudaStreamSynchronize(st));
-  for (int i = 0; i < 2 * count; ++i) out[i] = c->h_scalars[i];
-}
-
 void blas_transpose(mg_ctx* c, Vec out, Vec in, int nvec, bool to_interleaved, cudaStream_t st) {
   GB_REQUIRE(out.prec == in.prec && out.n == in.n, MG_ERR_ARG, "transpose: mismatch");
   GB_DISPATCH1(out.prec, R,
@@ -558,14 +570,6 @@ void blas_gaussian(mg_ctx* c, Vec v, uint64_t seed, uint64_t offset, cudaStream_
   GB_DISPATCH1(v.prec, R,
                (k_gaussian<R><<<ew_blocks(v.n), kThreads, 0, st>>>((cpx<R>*)v.p, v.n, seed,
                                                                     offset)));
-  GB_LAUNCH_CHECK();
-  c->launches++;
-}
-
-void blas_normalise(mg_ctx* c, Vec x, int slot, cudaStream_t st) {
-  GB_DISPATCH1(x.prec, R,
-               (k_normalise<R><<<ew_blocks(x.n), kThreads, 0, st>>>((cpx<R>*)x.p, x.n, scal(c),
-                                                                     slot)));
   GB_LAUNCH_CHECK();
   c->launches++;
 }

@@ -148,17 +148,19 @@ __global__ void __launch_bounds__(CG*(N / Unpack<S>::RPC))
 }
 
 // Multi-RHS form of the streaming kernel for stores without a tensor-core
-// path (FP32): vectors interleaved [site][n][nrhs]; CTA (chunk, site) applies
-// the site's links to NR right-hand sides, so each link chunk read from HBM
-// feeds NR x RPC complex multiply-adds.  The gathered neighbour values sit
-// in shared memory as xs[k][r] (k = slot*n + col); the same buffer then
-// holds the CG partial sums as red[cg][r][row].
+// path (FP32).  Element (rhs, site, dof) sits at rhs * rs + (site * n + dof)
+// * ss: interleaved [site][n][nrhs] (rs = 1, ss = nrhs) or back to back
+// [nrhs][site][n] (rs = V n, ss = 1).  CTA (chunk, site) applies the site's
+// links to NR right-hand sides, so each link chunk read from HBM feeds
+// NR x RPC complex multiply-adds.  The gathered neighbour values sit in
+// shared memory as xs[k][r] (k = slot*n + col); the same buffer then holds
+// the CG partial sums as red[cg][r][row].
 template <typename S, int N, int CG, int NR>
 __global__ void __launch_bounds__(CG*(N / Unpack<S>::RPC))
     k_coarse_stream_mr(cpx<typename StoreTraits<S>::real>* __restrict__ y,
                        const cpx<typename StoreTraits<S>::real>* __restrict__ x,
                        const S* __restrict__ links, const float* __restrict__ scales, Geom g,
-                       int nrhs) {
+                       size_t rs, size_t ss) {
   using R = typename StoreTraits<S>::real;
   constexpr int RPC = Unpack<S>::RPC;
   constexpr int TPC = N / RPC;
@@ -178,10 +180,18 @@ __global__ void __launch_bounds__(CG*(N / Unpack<S>::RPC))
     nb[tid] = neighbour(g, site, c, tid);
   }
   __syncthreads();
-  for (int i = tid; i < XS; i += NT) {
-    const int k = i / NR, r = i - k * NR;
-    const int d = k / N;
-    buf[i] = x[(size_t(nb[d]) * N + (k - d * N)) * nrhs + chunk * NR + r];
+  if (ss == 1) {  // back to back: read each vector's neighbour values in order
+    for (int i = tid; i < XS; i += NT) {
+      const int r = i / K, k = i - r * K;
+      const int d = k / N;
+      buf[k * NR + r] = x[size_t(chunk * NR + r) * rs + size_t(nb[d]) * N + (k - d * N)];
+    }
+  } else {
+    for (int i = tid; i < XS; i += NT) {
+      const int k = i / NR, r = i - k * NR;
+      const int d = k / N;
+      buf[i] = x[size_t(chunk * NR + r) * rs + (size_t(nb[d]) * N + (k - d * N)) * ss];
+    }
   }
   __syncthreads();
   const int rp = tid % TPC;
@@ -217,11 +227,18 @@ __global__ void __launch_bounds__(CG*(N / Unpack<S>::RPC))
   __syncthreads();
   const R sc = StoreTraits<S>::scaled ? R(scales[site]) : R(1);
   for (int o = tid; o < N * NR; o += NT) {
-    const int row = o / NR, r = o - row * NR;
+    int row, r;
+    if (ss == 1) {
+      r = o / N;
+      row = o - r * N;
+    } else {
+      row = o / NR;
+      r = o - row * NR;
+    }
     cpx<R> sum = buf[r * N + row];
 #pragma unroll
     for (int q = 1; q < CG; ++q) sum += buf[(q * NR + r) * N + row];
-    y[(size_t(site) * N + row) * nrhs + chunk * NR + r] = sc * sum;
+    y[size_t(chunk * NR + r) * rs + (size_t(site) * N + row) * ss] = sc * sum;
   }
 }
 
@@ -528,33 +545,35 @@ bool try_stream(const Level& L, void* y, const void* x, const void* links, cudaS
 
 template <typename S, int N>
 void launch_stream_mr(const Level& L, void* y, const void* x, const void* links, int nrhs,
-                      cudaStream_t st) {
+                      bool blocked, cudaStream_t st) {
   using R = typename StoreTraits<S>::real;
   constexpr int CG = CgSet<S>::c0;
   constexpr int NT = CG * (N / Unpack<S>::RPC);
   const cpx<R>* xp = (const cpx<R>*)x;
   cpx<R>* yp = (cpx<R>*)y;
   const S* lp = (const S*)links;
+  const size_t rs = blocked ? size_t(L.g.vol) * N : 1;
+  const size_t ss = blocked ? 1 : size_t(nrhs);
   if (nrhs % 8 == 0)
     k_coarse_stream_mr<S, N, CG, 8><<<dim3(nrhs / 8, L.g.vol), NT, 0, st>>>(
-        yp, xp, lp, L.scales.as<float>(), L.g, nrhs);
+        yp, xp, lp, L.scales.as<float>(), L.g, rs, ss);
   else if (nrhs % 4 == 0)
     k_coarse_stream_mr<S, N, CG, 4><<<dim3(nrhs / 4, L.g.vol), NT, 0, st>>>(
-        yp, xp, lp, L.scales.as<float>(), L.g, nrhs);
+        yp, xp, lp, L.scales.as<float>(), L.g, rs, ss);
   else
     k_coarse_stream_mr<S, N, CG, 2><<<dim3(nrhs / 2, L.g.vol), NT, 0, st>>>(
-        yp, xp, lp, L.scales.as<float>(), L.g, nrhs);
+        yp, xp, lp, L.scales.as<float>(), L.g, rs, ss);
 }
 
 template <typename S>
 bool try_stream_mr(const Level& L, void* y, const void* x, const void* links, int nrhs,
-                   cudaStream_t st) {
+                   bool blocked, cudaStream_t st) {
   if (nrhs % 2 != 0) return false;
   switch (L.nd) {
-    case 16: launch_stream_mr<S, 16>(L, y, x, links, nrhs, st); return true;
-    case 32: launch_stream_mr<S, 32>(L, y, x, links, nrhs, st); return true;
-    case 48: launch_stream_mr<S, 48>(L, y, x, links, nrhs, st); return true;
-    case 64: launch_stream_mr<S, 64>(L, y, x, links, nrhs, st); return true;
+    case 16: launch_stream_mr<S, 16>(L, y, x, links, nrhs, blocked, st); return true;
+    case 32: launch_stream_mr<S, 32>(L, y, x, links, nrhs, blocked, st); return true;
+    case 48: launch_stream_mr<S, 48>(L, y, x, links, nrhs, blocked, st); return true;
+    case 64: launch_stream_mr<S, 64>(L, y, x, links, nrhs, blocked, st); return true;
     default: return false;
   }
 }
@@ -566,7 +585,7 @@ void dispatch_apply(const Level& L, void* y, const void* x, const void* links, i
   if (nrhs == 1 && L.slots5 && L.links5.p && try_stream5<S>(L, y, x, st)) return;
   if (nrhs == 1 && try_stream<S>(L, y, x, links, st)) return;
   if constexpr (std::is_same<S, cpx<float>>::value) {
-    if (nrhs > 1 && try_stream_mr<S>(L, y, x, links, nrhs, st)) return;
+    if (nrhs > 1 && try_stream_mr<S>(L, y, x, links, nrhs, false, st)) return;
   }
   int threads = L.nd * nrhs >= 256 ? 256 : ((L.nd * nrhs + 31) / 32) * 32;
   k_coarse_generic<S><<<L.g.vol, threads, 0, st>>>((cpx<R>*)y, (const cpx<R>*)x, (const S*)links,
@@ -613,6 +632,46 @@ void coarse_apply(mg_ctx* c, int level, void* y, const void* x, int nrhs, cudaSt
   }
   GB_LAUNCH_CHECK();
   c->launches++;
+}
+
+void coarse_apply_blocked(mg_ctx* c, int level, void* y, const void* x, int nr,
+                          cudaStream_t st) {
+  if (nr == 1) return coarse_apply(c, level, y, x, 1, st);
+  Level& L = c->L[level];
+  GB_REQUIRE(level >= 1 && level < c->nlevels, MG_ERR_ARG, "coarse_apply: bad level");
+  GB_REQUIRE(L.have_op, MG_ERR_STATE, "coarse_apply: coarse operator not built");
+  GB_REQUIRE(y != x, MG_ERR_ARG, "coarse_apply: output aliases input");
+  const size_t n = L.vec_elems();
+  const size_t vb = n * prec_bytes_complex(L.vprec);
+  if (L.prec == MG_F32 && !L.slots5 && nr % 2 == 0 &&
+      (L.nd == 16 || L.nd == 32 || L.nd == 48 || L.nd == 64)) {
+    const double nd = L.nd;
+    ProfScope ps(c->prof, st, "coarse_apply_multi", level,
+                 double(L.g.vol) * 9 * nd * nd * 8 + double(nr) * 2 * double(vb),
+                 8.0 * 9 * nd * nd * L.g.vol * nr);
+    try_stream_mr<cpx<float>>(L, y, x, L.links.p, nr, true, st);
+    GB_LAUNCH_CHECK();
+    c->launches++;
+    return;
+  }
+  if (coarse_apply_mma_supported(L, nr)) {
+    // the tensor-core kernel takes the interleaved layout
+    if (L.tr_in.bytes < vb * nr) L.tr_in.alloc(vb * nr);
+    if (L.tr_out.bytes < vb * nr) L.tr_out.alloc(vb * nr);
+    Vec vx, vi, vo, vy;
+    vx.p = const_cast<void*>(x);
+    vy.p = y;
+    vi.p = L.tr_in.p;
+    vo.p = L.tr_out.p;
+    vx.prec = vy.prec = vi.prec = vo.prec = L.vprec;
+    vx.n = vy.n = vi.n = vo.n = n;
+    blas_transpose(c, vi, vx, nr, true, st);
+    coarse_apply(c, level, vo.p, vi.p, nr, st);
+    blas_transpose(c, vy, vo, nr, false, st);
+    return;
+  }
+  for (int v = 0; v < nr; ++v)
+    coarse_apply(c, level, (char*)y + v * vb, (const char*)x + v * vb, 1, st);
 }
 
 void links_pick5(mg_ctx* c, int level, cudaStream_t st) {

@@ -82,6 +82,7 @@ struct Level {
   // 16-bit store + per-site scale when prec is BF16/F16.
   DevBuf links, links16, scales;
   DevBuf links_mma;            // 16-bit links tiled as the tensor-core operand
+  DevBuf tr_in, tr_out;        // interleaved copies for multi-RHS tensor-core applies
   bool slots5 = false;         // single-RHS apply from 5 stored blocks
   DevBuf links5;               // [V][5][col][row]: slots 0, 1, 3, 5, 7 in the store type
   bool have_op = false;
@@ -98,12 +99,12 @@ struct Level {
   size_t vec_bytes() const { return vec_elems() * prec_bytes_complex(vprec); }
 };
 
-// Scalars that solver kernels exchange through device memory.
+// Scalars that solver kernels exchange through device memory: SC_COUNT
+// slots, each with one complex double per right-hand side.
 enum ScalarSlot {
-  SC_DOT0 = 0,    // complex dot results ...
-  SC_NRM0 = 32,   // real norms ...
   SC_COUNT = 64
 };
+constexpr int kMaxNrhs = MG_MAX_NRHS;
 
 }  // namespace gbmg
 
@@ -115,8 +116,8 @@ struct mg_ctx {
   gbmg::Profiler prof;
   long long launches = 0;
   // reductions: per-block partials and final scalars (complex double)
-  gbmg::DevBuf red_partials;   // [slots][max_blocks] double2
-  gbmg::DevBuf scalars;        // [SC_COUNT] double2
+  gbmg::DevBuf red_partials;   // [2][nrhs][max_blocks] double2
+  gbmg::DevBuf scalars;        // [SC_COUNT][kMaxNrhs] double2
   gbmg::DevBuf status;         // device status words (int)
   gbmg::DevBuf batch_partials; // batched reductions: [nvec][2][blocks] double2
   gbmg::DevBuf batch_scalars;  // batched reductions: [2 * 64] double2

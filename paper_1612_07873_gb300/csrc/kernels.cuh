@@ -6,53 +6,55 @@
 
 namespace gbmg {
 
-// A device vector of n complex numbers in precision prec (F64 or F32).
+// nr device vectors of n complex numbers each, stored back to back (vector
+// v at offset v * n), in precision prec (F64 or F32).  Element-wise kernels
+// treat them as one vector of n * nr numbers; reductions and scalar updates
+// act per vector, with per-vector scalars.
 struct Vec {
   void* p = nullptr;
   mg_prec prec = MG_F64;
   size_t n = 0;
+  int nr = 1;
+  size_t total() const { return n * size_t(nr); }
 };
 
 // ---------------------------------------------------------------- blas.cu
-// Device scalars live in ctx->scalars as complex doubles, indexed by slot.
+// Device scalars live in ctx->scalars as complex doubles: slot s holds one
+// value per right-hand side, S[s][v] (kMaxNrhs per slot).
 void blas_zero(mg_ctx* c, Vec v, cudaStream_t st);
 void blas_copy(mg_ctx* c, Vec dst, Vec src, cudaStream_t st);        // converts precision
 void blas_axpy_host(mg_ctx* c, Vec y, Vec x, double are, double aim, cudaStream_t st);
-// y += sign * S[slot] * x
+// y_v += sign * S[slot][v] * x_v
 void blas_axpy_slot(mg_ctx* c, Vec y, Vec x, int slot, double sign, cudaStream_t st);
 // out = b - ax
 void blas_sub(mg_ctx* c, Vec out, Vec b, Vec ax, cudaStream_t st);
-// S[slot] = <a, b> = sum conj(a) b ; S[slot].re = |a|^2
+// S[slot][v] = <a_v, b_v> = sum conj(a_v) b_v
 // fp64_partials: per-thread partial sums in FP64 even for FP32 data (the
 // outer GCR's orthogonalisation); otherwise FP32 data sums per thread in FP32
 void blas_dot(mg_ctx* c, Vec a, Vec b, int slot, cudaStream_t st, bool fp64_partials = false);
 void blas_norm2(mg_ctx* c, Vec a, int slot, cudaStream_t st, bool fp64_partials = false);
-// nvec vectors of length p.n back to back: B[2v] = <p_v, r_v>, B[2v+1] = |p_v|^2
-// with B = ctx->batch_scalars
+// S[s_pr][v] = <p_v, r_v>, S[s_pp][v] = <p_v, p_v> in one pass
+void blas_dot2(mg_ctx* c, Vec p, Vec r, int s_pr, int s_pp, cudaStream_t st);
+// MR step per vector: a = omega S[s_pr]/S[s_pp].re ; x += a r ; r -= a p
+void blas_mr_update(mg_ctx* c, Vec x, Vec r, Vec p, int s_pr, int s_pp, double omega,
+                    cudaStream_t st);
+// a_v *= 1/sqrt(S[slot][v].re), b_v likewise
+void blas_scale_invnorm(mg_ctx* c, Vec a, Vec b, int slot, cudaStream_t st);
+// x_v += S[slot][v] z_v ; r_v -= S[slot][v] w_v
+void blas_gcr_update(mg_ctx* c, Vec x, Vec r, Vec z, Vec w, int slot, cudaStream_t st);
+// real parts of S[slot][0..nr) to the host (synchronises st)
+void blas_read_slot(mg_ctx* c, int slot, int nr, double* out_re, cudaStream_t st);
+// Setup sweeps: nvec vectors of length p.n back to back, scalars in
+// ctx->batch_scalars: B[2v] = <p_v, r_v>, B[2v+1] = |p_v|^2
 void blas_dot2_batched(mg_ctx* c, Vec p, Vec r, int nvec, cudaStream_t st);
 // x_v -= (B[2v] / B[2v+1]) t_v
 void blas_sweep_update_batched(mg_ctx* c, Vec x, Vec t, int nvec, cudaStream_t st);
 // x_v /= |x_v|
 void blas_normalise_batched(mg_ctx* c, Vec x, int nvec, cudaStream_t st);
-// S[s_pr] = <p, r>, S[s_pp] = <p, p> in one pass
-void blas_dot2(mg_ctx* c, Vec p, Vec r, int s_pr, int s_pp, cudaStream_t st);
-// MR step: a = omega S[s_pr]/S[s_pp].re ; x += a r ; r -= a p
-void blas_mr_update(mg_ctx* c, Vec x, Vec r, Vec p, int s_pr, int s_pp, double omega,
-                    cudaStream_t st);
-// a *= 1/sqrt(S[slot].re), b likewise
-void blas_scale_invnorm(mg_ctx* c, Vec a, Vec b, int slot, cudaStream_t st);
-// x += S[slot] z ; r -= S[slot] w
-void blas_gcr_update(mg_ctx* c, Vec x, Vec r, Vec z, Vec w, int slot, cudaStream_t st);
-// setup sweep update: x -= (S[s_qt] / S[s_qq].re) t
-void blas_sweep_update(mg_ctx* c, Vec x, Vec t, int s_qt, int s_qq, cudaStream_t st);
-// copy slot values to the host (synchronises st)
-void blas_read_scalars(mg_ctx* c, int first, int count, double* out_re_im, cudaStream_t st);
 // nvec vectors of out.n elements: [nvec][n] -> [n][nvec] (to_interleaved) or back
 void blas_transpose(mg_ctx* c, Vec out, Vec in, int nvec, bool to_interleaved, cudaStream_t st);
 // complex Gaussian (Re, Im iid N(0,1)) from a counter-based Philox4x32-10
 void blas_gaussian(mg_ctx* c, Vec v, uint64_t seed, uint64_t offset, cudaStream_t st);
-// x /= sqrt(S[slot].re)
-void blas_normalise(mg_ctx* c, Vec x, int slot, cudaStream_t st);
 // a device status word check (host reads it; synchronises)
 int read_status(mg_ctx* c, cudaStream_t st);
 void clear_status(mg_ctx* c, cudaStream_t st);
@@ -64,7 +66,11 @@ void fine_operator_build(mg_ctx* c, const void* gauge_ext, cudaStream_t st);
 void wilson_apply(mg_ctx* c, Vec out, Vec in, int nvec, cudaStream_t st);
 
 // ---------------------------------------------------------------- coarse.cu
+// nrhs > 1: vectors interleaved [site][n][nrhs] (the public layout)
 void coarse_apply(mg_ctx* c, int level, void* y, const void* x, int nrhs, cudaStream_t st);
+// nr vectors back to back [nr][site][n] (the solver's layout)
+void coarse_apply_blocked(mg_ctx* c, int level, void* y, const void* x, int nr,
+                          cudaStream_t st);
 void links_import(mg_ctx* c, int level, const void* ext, cudaStream_t st);
 void links_export(mg_ctx* c, int level, void* ext, cudaStream_t st);
 void links_pack16(mg_ctx* c, int level, cudaStream_t st);
@@ -92,6 +98,9 @@ void level_apply(mg_ctx* c, int level, Vec out, Vec in, cudaStream_t st);
 void setup_sweeps(mg_ctx* c, int level, const void* init, cudaStream_t st);
 void gcr_solve(mg_ctx* c, void* x, const void* b, double tol, int maxiter, mg_solve_stats* stats,
                cudaStream_t st);
+// nr right-hand sides back to back; stats: nr records or null
+void gcr_solve_multi(mg_ctx* c, void* x, const void* b, int nr, double tol, int maxiter,
+                     mg_solve_stats* stats, cudaStream_t st);
 
 // message returned by mg_last_error(NULL) for calls without a context
 void set_last_error(const char* msg);

@@ -8,7 +8,13 @@
 // vectors, the K-cycle and all coarse levels run in each level's vector
 // precision.  Inner products accumulate in FP64.  Scalars (MR and GCR
 // coefficients) stay on the device; the host reads one residual norm per
-// GCR step to decide convergence.
+// right-hand side per GCR step to decide convergence.
+//
+// Several right-hand sides: every vector of the solver holds nr right-hand
+// sides back to back and every step acts on all of them at once (one
+// batched kernel per step, per-RHS scalars), so the fine operator's links,
+// the prolongator and the coarse links are read once per step for all nr.
+// A GCR loop ends when every right-hand side meets its tolerance.
 #include <chrono>
 #include <cmath>
 
@@ -22,6 +28,7 @@ struct mg_ctx::SolverWS {
   };
   LevelWS lv[MG_MAX_LEVELS];
   int nk = 0;
+  int nr = 0;  // right-hand sides the buffers hold
 };
 
 mg_ctx::mg_ctx() = default;
@@ -39,11 +46,12 @@ namespace {
 inline int slot(int level, int k) { return level * 8 + k; }
 enum { S_BETA = 0, S_NRM = 1, S_ALPHA = 2, S_R = 3, S_PR = 4, S_PP = 5 };
 
-Vec vbuf(DevBuf& b, mg_prec p, size_t n) {
+Vec vbuf(DevBuf& b, mg_prec p, size_t n, int nr = 1) {
   Vec v;
   v.p = b.p;
   v.prec = p;
   v.n = n;
+  v.nr = nr;
   return v;
 }
 
@@ -51,14 +59,15 @@ void ensure(DevBuf& b, size_t bytes) {
   if (b.bytes != bytes) b.alloc(bytes);
 }
 
-void ensure_ws(mg_ctx* c) {
+// solver buffers for nr right-hand sides (reallocated when nr changes)
+void ensure_ws(mg_ctx* c, int nr) {
   if (!c->ws) c->ws.reset(new mg_ctx::SolverWS());
   auto& ws = *c->ws;
   const int nk = c->p.gcr_nkrylov;
   for (int l = 0; l < c->nlevels; ++l) {
     Level& L = c->L[l];
     auto& w = ws.lv[l];
-    const size_t vb = L.vec_bytes();
+    const size_t vb = L.vec_bytes() * nr;
     if (int(w.Z.size()) != nk) {
       w.Z.clear();
       w.W.clear();
@@ -80,25 +89,27 @@ void ensure_ws(mg_ctx* c) {
     ensure(w.mrr, vb);
     ensure(w.mrp, vb);
     if (l == 0) {
-      ensure(w.r64, L.vec_elems() * 16);
-      ensure(w.tmp64, L.vec_elems() * 16);
+      ensure(w.r64, L.vec_elems() * 16 * nr);
+      ensure(w.tmp64, L.vec_elems() * 16 * nr);
     }
   }
   ws.nk = nk;
+  ws.nr = nr;
 }
 
-double read_norm2(mg_ctx* c, int s, cudaStream_t st) {
-  double v[2];
-  blas_read_scalars(c, s, 1, v, st);
-  return v[0];
+// real parts of slot s for the nr right-hand sides
+std::vector<double> read_slot(mg_ctx* c, int s, int nr, cudaStream_t st) {
+  std::vector<double> v(nr);
+  blas_read_slot(c, s, nr, v.data(), st);
+  return v;
 }
 
 // x = MR_k(b) from a zero guess
 void mr_smooth(mg_ctx* c, int l, Vec x, Vec b, cudaStream_t st) {
   auto& w = c->ws->lv[l];
   Level& L = c->L[l];
-  Vec r = vbuf(w.mrr, L.vprec, L.vec_elems());
-  Vec p = vbuf(w.mrp, L.vprec, L.vec_elems());
+  Vec r = vbuf(w.mrr, L.vprec, L.vec_elems(), x.nr);
+  Vec p = vbuf(w.mrp, L.vprec, L.vec_elems(), x.nr);
   blas_zero(c, x, st);
   blas_copy(c, r, b, st);
   for (int k = 0; k < c->p.mr_iters; ++k) {
@@ -111,38 +122,65 @@ void mr_smooth(mg_ctx* c, int l, Vec x, Vec b, cudaStream_t st) {
 struct GcrOut {
   int iters = 0;
   int restarts = 0;
-  double rel = 0.0;
   bool converged = false;
+  std::vector<double> rel;     // final relative residual per right-hand side
+  std::vector<int> conv_iter;  // step at which each right-hand side met tol
 };
 
 void kcycle(mg_ctx* c, int l, Vec z, Vec r, cudaStream_t st, mg_solve_stats* stats);
 
-// Flexible GCR at level l.  x, b: level-0 -> FP64; inner levels -> vprec.
+// Flexible GCR at level l on x.nr right-hand sides.  x, b: level-0 -> FP64;
+// inner levels -> vprec.  stats: one record per right-hand side (or null);
+// level totals go to stats[0].
 GcrOut gcr(mg_ctx* c, int l, Vec x, Vec b, bool precond, double tol, int maxiter,
            cudaStream_t st, mg_solve_stats* stats, bool record) {
   auto& w = c->ws->lv[l];
   Level& L = c->L[l];
   const size_t n = L.vec_elems();
+  const int nr = x.nr;
   const bool outer = (l == 0);
-  Vec r = outer ? vbuf(w.r64, MG_F64, n) : vbuf(w.r, L.vprec, n);
-  Vec rK = vbuf(w.r, L.vprec, n);  // residual in level precision (outer level)
-  Vec tmp = outer ? vbuf(w.tmp64, MG_F64, n) : vbuf(w.tmp, L.vprec, n);
+  Vec r = outer ? vbuf(w.r64, MG_F64, n, nr) : vbuf(w.r, L.vprec, n, nr);
+  Vec rK = vbuf(w.r, L.vprec, n, nr);  // residual in level precision (outer level)
+  Vec tmp = outer ? vbuf(w.tmp64, MG_F64, n, nr) : vbuf(w.tmp, L.vprec, n, nr);
   GcrOut out;
+  out.rel.assign(nr, 0.0);
+  out.conv_iter.assign(nr, -1);
   blas_norm2(c, b, slot(l, S_R), st);
-  const double b2 = read_norm2(c, slot(l, S_R), st);
+  const std::vector<double> b2 = read_slot(c, slot(l, S_R), nr, st);
   blas_zero(c, x, st);
-  if (!(b2 > 0.0)) {
-    GB_REQUIRE(std::isfinite(b2), MG_ERR_NUMERICAL, "gcr: non-finite right-hand side");
+  std::vector<double> tol2(nr);
+  bool any = false;
+  for (int v = 0; v < nr; ++v) {
+    GB_REQUIRE(std::isfinite(b2[v]), MG_ERR_NUMERICAL, "gcr: non-finite right-hand side");
+    tol2[v] = tol * tol * b2[v];
+    any = any || b2[v] > 0.0;
+    if (!(b2[v] > 0.0)) out.conv_iter[v] = 0;
+  }
+  if (!any) {
     out.converged = true;
     return out;
   }
   blas_copy(c, r, b, st);
-  const double tol2 = tol * tol * b2;
   const int nk = c->ws->nk;
+  // true when every right-hand side meets its tolerance; records the step
+  // at which each first did
+  auto check = [&](const std::vector<double>& r2) {
+    bool all = true;
+    for (int v = 0; v < nr; ++v) {
+      GB_REQUIRE(std::isfinite(r2[v]), MG_ERR_NUMERICAL, "gcr: non-finite residual");
+      out.rel[v] = b2[v] > 0.0 ? std::sqrt(r2[v] / b2[v]) : 0.0;
+      if (r2[v] <= tol2[v]) {
+        if (out.conv_iter[v] < 0) out.conv_iter[v] = out.iters;
+      } else {
+        all = false;
+      }
+    }
+    return all;
+  };
   while (true) {
-    double r2 = 0.0;
+    bool done = false;
     for (int k = 0; k < nk; ++k) {
-      Vec Zk = vbuf(*w.Z[k], L.vprec, n), Wk = vbuf(*w.W[k], L.vprec, n);
+      Vec Zk = vbuf(*w.Z[k], L.vprec, n, nr), Wk = vbuf(*w.W[k], L.vprec, n, nr);
       if (precond) {
         if (outer && r.prec != L.vprec) {
           blas_copy(c, rK, r, st);
@@ -155,7 +193,7 @@ GcrOut gcr(mg_ctx* c, int l, Vec x, Vec b, bool precond, double tol, int maxiter
       }
       level_apply(c, l, Wk, Zk, st);
       for (int j = 0; j < k; ++j) {
-        Vec Zj = vbuf(*w.Z[j], L.vprec, n), Wj = vbuf(*w.W[j], L.vprec, n);
+        Vec Zj = vbuf(*w.Z[j], L.vprec, n, nr), Wj = vbuf(*w.W[j], L.vprec, n, nr);
         blas_dot(c, Wj, Wk, slot(l, S_BETA), st, outer);
         blas_axpy_slot(c, Wk, Wj, slot(l, S_BETA), -1.0, st);
         blas_axpy_slot(c, Zk, Zj, slot(l, S_BETA), -1.0, st);
@@ -165,16 +203,16 @@ GcrOut gcr(mg_ctx* c, int l, Vec x, Vec b, bool precond, double tol, int maxiter
       blas_dot(c, Wk, r, slot(l, S_ALPHA), st);
       blas_gcr_update(c, x, r, Zk, Wk, slot(l, S_ALPHA), st);
       blas_norm2(c, r, slot(l, S_R), st);
-      r2 = read_norm2(c, slot(l, S_R), st);
-      GB_REQUIRE(std::isfinite(r2), MG_ERR_NUMERICAL, "gcr: non-finite residual");
+      const std::vector<double> r2 = read_slot(c, slot(l, S_R), nr, st);
       out.iters++;
-      if (record && stats && stats->history_len < 512)
-        stats->history[stats->history_len++] = std::sqrt(r2 / b2);
-      if (r2 <= tol2 || out.iters >= maxiter) break;
+      done = check(r2);
+      if (record && stats)
+        for (int v = 0; v < nr; ++v)
+          if (stats[v].history_len < 512) stats[v].history[stats[v].history_len++] = out.rel[v];
+      if (done || out.iters >= maxiter) break;
     }
-    if (out.iters >= maxiter) {
-      out.rel = std::sqrt(r2 / b2);
-      out.converged = r2 <= tol2;
+    if (done || out.iters >= maxiter) {
+      out.converged = done;
       break;
     }
     // restart: true residual
@@ -182,15 +220,12 @@ GcrOut gcr(mg_ctx* c, int l, Vec x, Vec b, bool precond, double tol, int maxiter
     blas_sub(c, r, b, tmp, st);
     out.restarts++;
     blas_norm2(c, r, slot(l, S_R), st);
-    r2 = read_norm2(c, slot(l, S_R), st);
-    GB_REQUIRE(std::isfinite(r2), MG_ERR_NUMERICAL, "gcr: non-finite true residual");
-    if (r2 <= tol2) {
-      out.rel = std::sqrt(r2 / b2);
+    if (check(read_slot(c, slot(l, S_R), nr, st))) {
       out.converged = true;
       break;
     }
   }
-  if (stats) stats->level_iters[l] += out.iters;
+  if (stats) stats[0].level_iters[l] += out.iters;
   return out;
 }
 
@@ -198,12 +233,13 @@ void kcycle(mg_ctx* c, int l, Vec z, Vec r, cudaStream_t st, mg_solve_stats* sta
   auto& w = c->ws->lv[l];
   Level& L = c->L[l];
   const size_t n = L.vec_elems();
-  Vec tmp = vbuf(w.tmp, L.vprec, n), kres = vbuf(w.kres, L.vprec, n);
-  Vec mrx = vbuf(w.mrx, L.vprec, n);
+  const int nr = z.nr;
+  Vec tmp = vbuf(w.tmp, L.vprec, n, nr), kres = vbuf(w.kres, L.vprec, n, nr);
+  Vec mrx = vbuf(w.mrx, L.vprec, n, nr);
   const int nl = l + 1;
   Level& C = c->L[nl];
   auto& wc = c->ws->lv[nl];
-  Vec rc = vbuf(wc.rhs, C.vprec, C.vec_elems()), ec = vbuf(wc.x, C.vprec, C.vec_elems());
+  Vec rc = vbuf(wc.rhs, C.vprec, C.vec_elems(), nr), ec = vbuf(wc.x, C.vprec, C.vec_elems(), nr);
   // pre-smooth
   mr_smooth(c, l, z, r, st);
   level_apply(c, l, tmp, z, st);
@@ -226,10 +262,11 @@ void kcycle(mg_ctx* c, int l, Vec z, Vec r, cudaStream_t st, mg_solve_stats* sta
 }  // namespace
 
 void level_apply(mg_ctx* c, int level, Vec out, Vec in, cudaStream_t st) {
+  GB_REQUIRE(out.nr == in.nr, MG_ERR_ARG, "level_apply: shape mismatch");
   if (level == 0)
-    wilson_apply(c, out, in, 1, st);
+    wilson_apply(c, out, in, in.nr, st);
   else
-    coarse_apply(c, level, out.p, in.p, 1, st);
+    coarse_apply_blocked(c, level, out.p, in.p, in.nr, st);
 }
 
 void setup_sweeps(mg_ctx* c, int l, const void* init, cudaStream_t st) {
@@ -295,41 +332,55 @@ void setup_sweeps(mg_ctx* c, int l, const void* init, cudaStream_t st) {
   GB_CHECK(cudaStreamSynchronize(st));
 }
 
-void gcr_solve(mg_ctx* c, void* xp, const void* bp, double tol, int maxiter,
-               mg_solve_stats* stats, cudaStream_t st) {
+void gcr_solve_multi(mg_ctx* c, void* xp, const void* bp, int nr, double tol, int maxiter,
+                     mg_solve_stats* stats, cudaStream_t st) {
+  GB_REQUIRE(nr >= 1 && nr <= kMaxNrhs, MG_ERR_ARG, "solve: nrhs out of range");
   for (int l = 0; l + 1 < c->nlevels; ++l) {
     GB_REQUIRE(c->L[l].have_V, MG_ERR_STATE, "solve: null vectors of a level missing");
     GB_REQUIRE(c->L[l + 1].have_op, MG_ERR_STATE, "solve: coarse operator missing");
   }
-  ensure_ws(c);
+  ensure_ws(c, nr);
   auto t0 = std::chrono::steady_clock::now();
-  mg_solve_stats local{};
-  mg_solve_stats* s = stats ? stats : &local;
-  *s = mg_solve_stats{};
+  std::vector<mg_solve_stats> local(nr);
+  mg_solve_stats* s = stats ? stats : local.data();
+  for (int v = 0; v < nr; ++v) s[v] = mg_solve_stats{};
   Level& L = c->L[0];
   const size_t n = L.vec_elems();
   Vec x, b;
   x.p = xp;
   x.prec = MG_F64;
   x.n = n;
+  x.nr = nr;
   b.p = const_cast<void*>(bp);
   b.prec = MG_F64;
   b.n = n;
+  b.nr = nr;
   GcrOut o = gcr(c, 0, x, b, true, tol, maxiter, st, s, true);
   // true residual of the returned x, in FP64
   auto& w = c->ws->lv[0];
-  Vec tmp = vbuf(w.tmp64, MG_F64, n), r = vbuf(w.r64, MG_F64, n);
+  Vec tmp = vbuf(w.tmp64, MG_F64, n, nr), r = vbuf(w.r64, MG_F64, n, nr);
   level_apply(c, 0, tmp, x, st);
   blas_sub(c, r, b, tmp, st);
   blas_norm2(c, r, slot(0, S_R), st);
-  double r2 = read_norm2(c, slot(0, S_R), st);
+  const std::vector<double> r2 = read_slot(c, slot(0, S_R), nr, st);
   blas_norm2(c, b, slot(0, S_R), st);
-  double b2 = read_norm2(c, slot(0, S_R), st);
-  s->iters = o.iters;
-  s->restarts = o.restarts;
-  s->true_residual = b2 > 0 ? std::sqrt(r2 / b2) : 0.0;
-  s->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  const std::vector<double> b2 = read_slot(c, slot(0, S_R), nr, st);
+  const double secs =
+      std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  for (int v = 0; v < nr; ++v) {
+    s[v].iters = o.conv_iter[v] >= 0 ? o.conv_iter[v] : o.iters;
+    s[v].restarts = o.restarts;
+    if (v > 0)
+      for (int l = 0; l < MG_MAX_LEVELS; ++l) s[v].level_iters[l] = s[0].level_iters[l];
+    s[v].true_residual = b2[v] > 0 ? std::sqrt(r2[v] / b2[v]) : 0.0;
+    s[v].seconds = secs;
+  }
   if (!o.converged) throw Error(MG_ERR_NOT_CONVERGED, "gcr: maxiter reached before tolerance");
+}
+
+void gcr_solve(mg_ctx* c, void* xp, const void* bp, double tol, int maxiter,
+               mg_solve_stats* stats, cudaStream_t st) {
+  gcr_solve_multi(c, xp, bp, 1, tol, maxiter, stats, st);
 }
 
 }  // namespace gbmg

@@ -234,13 +234,18 @@ __global__ void k_mgs_scatter(cpx<R>* __restrict__ Vp, const double2* __restrict
   }
 }
 
-// coarse[xc][chi*Nv + i] = sum_{x in A(xc), a in chi} conj(Vp[x][a][i]) fine[x][a]
+// coarse_v[xc][chi*Nv + i] = sum_{x in A(xc), a in chi} conj(Vp[x][a][i])
+// fine_v[x][a].  CTA b: aggregate b / nr, right-hand side b % nr (the nr
+// CTAs of one aggregate run side by side and share its Vp rows through L2).
 template <typename Rf, typename Rc>
 __global__ void k_restrict(cpx<Rc>* __restrict__ coarse, const cpx<Rf>* __restrict__ fine,
-                           const cpx<Rf>* __restrict__ Vp, AggMap m, int nd, int nv) {
+                           const cpx<Rf>* __restrict__ Vp, AggMap m, int nd, int nv, int nr,
+                           size_t fstride, size_t cstride) {
   extern __shared__ unsigned char smem_raw[];
   cpx<Rf>* red = reinterpret_cast<cpx<Rf>*>(smem_raw);  // [G][2][nv]
-  const int xc = blockIdx.x;
+  const int xc = blockIdx.x / nr, rhs = blockIdx.x - xc * nr;
+  fine += rhs * fstride;
+  coarse += rhs * cstride;
   const int G = blockDim.x / nv;
   const int i = threadIdx.x % nv, g = threadIdx.x / nv;
   const int half = nd / 2;
@@ -269,14 +274,19 @@ __global__ void k_restrict(cpx<Rc>* __restrict__ coarse, const cpx<Rf>* __restri
   }
 }
 
-// fine[x][a] = sum_i Vp[x][a][i] coarse[agg(x)][chi(a)*Nv + i]
+// fine_v[x][a] = sum_i Vp[x][a][i] coarse_v[agg(x)][chi(a)*Nv + i].  CTA b
+// works on right-hand side b % nr, element chunk b / nr.
 template <typename Rf, typename Rc>
 __global__ void k_prolong(cpx<Rf>* __restrict__ fine, const cpx<Rc>* __restrict__ coarse,
-                          const cpx<Rf>* __restrict__ Vp, AggMap m, int nd, int nv) {
+                          const cpx<Rf>* __restrict__ Vp, AggMap m, int nd, int nv, int nr,
+                          size_t fstride, size_t cstride) {
+  const int rhs = blockIdx.x % nr;
+  const size_t blk = blockIdx.x / nr, nblk = gridDim.x / nr;
+  fine += rhs * fstride;
+  coarse += rhs * cstride;
   size_t total = size_t(m.fine.vol) * nd;
   const int half = nd / 2;
-  for (size_t idx = blockIdx.x * size_t(blockDim.x) + threadIdx.x; idx < total;
-       idx += size_t(gridDim.x) * blockDim.x) {
+  for (size_t idx = blk * blockDim.x + threadIdx.x; idx < total; idx += nblk * blockDim.x) {
     int a = int(idx % nd);
     int s = int(idx / nd);
     int c[4];
@@ -313,28 +323,37 @@ __device__ __forceinline__ int local_offset(const AggMap& m, int ls) {
   return l0 + m.fine.stride[1] * l1 + m.fine.stride[2] * l2 + m.fine.stride[3] * l3;
 }
 
-// coarse[xc][chi*Nv + i] = sum over fine sites x of the aggregate and dofs a
-// of chirality chi of conj(Vp[x][a][i]) fine[x][a].  Thread (g, p): p picks
-// the 16-byte column of Vp rows (CPL coefficients), g strides over sites.
-template <typename Rf, typename Rc>
+// coarse_v[xc][chi*Nv + i] = sum over fine sites x of the aggregate and dofs
+// a of chirality chi of conj(Vp[x][a][i]) fine_v[x][a], for NRB right-hand
+// sides v per CTA.  Thread (g, p): p picks the 16-byte column of Vp rows (CPL
+// coefficients), g strides over sites; each Vp word read serves NRB
+// right-hand sides.  CTA b: aggregate b / nchunk, right-hand-side chunk
+// b % nchunk (chunks of one aggregate run side by side and share its Vp
+// rows through L2).
+template <typename Rf, typename Rc, int NRB>
 __global__ void __launch_bounds__(256) k_restrict12(cpx<Rc>* __restrict__ coarse,
                                                    const cpx<Rf>* __restrict__ fine,
                                                    const cpx<Rf>* __restrict__ Vp, AggMap m,
-                                                   int nv, int G) {
+                                                   int nv, int G, int nchunk, size_t fstride,
+                                                   size_t cstride) {
   constexpr int ND = 12, CPL = 16 / int(sizeof(cpx<Rf>));
   constexpr int FW = ND * int(sizeof(cpx<Rf>)) / 16;  // 16-byte words of a fine site
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<Rf>* red = reinterpret_cast<cpx<Rf>*>(smem_raw);  // [G][2][nv]
   int* off = reinterpret_cast<int*>(red + size_t(G) * 2 * nv);
-  const int xc = blockIdx.x;
+  const int xc = blockIdx.x / nchunk, chunk = blockIdx.x - xc * nchunk;
+  fine += size_t(chunk) * NRB * fstride;
+  coarse += size_t(chunk) * NRB * cstride;
   const int NP = nv / CPL;
   const int p = threadIdx.x % NP, g = threadIdx.x / NP;
   for (int ls = threadIdx.x; ls < m.per; ls += blockDim.x) off[ls] = local_offset(m, ls);
   const size_t base = size_t(agg_origin(m, xc));
   __syncthreads();
-  cpx<Rf> acc[2][CPL];
+  cpx<Rf> acc[NRB][2][CPL];
 #pragma unroll
-  for (int k = 0; k < CPL; ++k) acc[0][k] = acc[1][k] = cpx<Rf>(Rf(0), Rf(0));
+  for (int b = 0; b < NRB; ++b)
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) acc[b][0][k] = acc[b][1][k] = cpx<Rf>(Rf(0), Rf(0));
   if (g < G) {
     for (int ls = g; ls < m.per; ls += G) {
       const size_t x = base + off[ls];
@@ -342,46 +361,60 @@ __global__ void __launch_bounds__(256) k_restrict12(cpx<Rc>* __restrict__ coarse
       uint4 w[ND];
 #pragma unroll
       for (int a = 0; a < ND; ++a) w[a] = ld_stream16(vr + a * NP);
-      uint4 fw[FW];
-      const uint4* fr = reinterpret_cast<const uint4*>(fine + x * ND);
 #pragma unroll
-      for (int k = 0; k < FW; ++k) fw[k] = __ldg(fr + k);
-      const cpx<Rf>* f = reinterpret_cast<const cpx<Rf>*>(fw);
+      for (int b = 0; b < NRB; ++b) {
+        uint4 fw[FW];
+        const uint4* fr = reinterpret_cast<const uint4*>(fine + b * fstride + x * ND);
 #pragma unroll
-      for (int a = 0; a < ND; ++a) {
-        const cpx<Rf>* v = reinterpret_cast<const cpx<Rf>*>(&w[a]);
+        for (int k = 0; k < FW; ++k) fw[k] = __ldg(fr + k);
+        const cpx<Rf>* f = reinterpret_cast<const cpx<Rf>*>(fw);
 #pragma unroll
-        for (int k = 0; k < CPL; ++k) cmac_conj(acc[a < ND / 2 ? 0 : 1][k], v[k], f[a]);
+        for (int a = 0; a < ND; ++a) {
+          const cpx<Rf>* v = reinterpret_cast<const cpx<Rf>*>(&w[a]);
+#pragma unroll
+          for (int k = 0; k < CPL; ++k) cmac_conj(acc[b][a < ND / 2 ? 0 : 1][k], v[k], f[a]);
+        }
       }
     }
-#pragma unroll
-    for (int chi = 0; chi < 2; ++chi)
-#pragma unroll
-      for (int k = 0; k < CPL; ++k) red[(g * 2 + chi) * nv + p * CPL + k] = acc[chi][k];
   }
-  __syncthreads();
-  for (int t = threadIdx.x; t < 2 * nv; t += blockDim.x) {
-    cpx<Rf> sum(Rf(0), Rf(0));
-    for (int k = 0; k < G; ++k) sum += red[k * 2 * nv + t];
-    coarse[size_t(xc) * 2 * nv + t] = cpx<Rc>(sum);
+#pragma unroll
+  for (int b = 0; b < NRB; ++b) {
+    if (g < G) {
+#pragma unroll
+      for (int chi = 0; chi < 2; ++chi)
+#pragma unroll
+        for (int k = 0; k < CPL; ++k) red[(g * 2 + chi) * nv + p * CPL + k] = acc[b][chi][k];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 2 * nv; t += blockDim.x) {
+      cpx<Rf> sum(Rf(0), Rf(0));
+      for (int k = 0; k < G; ++k) sum += red[k * 2 * nv + t];
+      coarse[b * cstride + size_t(xc) * 2 * nv + t] = cpx<Rc>(sum);
+    }
+    __syncthreads();
   }
 }
 
-// fine[x][a] = sum_i Vp[x][a][i] coarse[agg(x)][chi(a)*Nv + i].  Two threads
-// per Vp row, each summing half of it; the halves meet by one shuffle.
+// fine_v[x][a] = sum_i Vp[x][a][i] coarse_v[agg(x)][chi(a)*Nv + i] for all nr
+// right-hand sides.  Two threads per Vp row, each holding half of it in
+// registers for every right-hand side; the halves meet by one shuffle.
 template <typename Rf, typename Rc>
 __global__ void __launch_bounds__(256) k_prolong12(cpx<Rf>* __restrict__ fine,
                                                   const cpx<Rc>* __restrict__ coarse,
                                                   const cpx<Rf>* __restrict__ Vp, AggMap m,
-                                                  int nv) {
+                                                  int nv, int nr, size_t fstride,
+                                                  size_t cstride) {
   constexpr int ND = 12, CPL = 16 / int(sizeof(cpx<Rf>));
+  constexpr int MAXPW = 12;  // Nv <= 48 (FP32) / 24 (FP64)
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cpx<Rf>* cs = reinterpret_cast<cpx<Rf>*>(smem_raw);  // [2][nv]
-  int* off = reinterpret_cast<int*>(cs + 2 * nv);
+  cpx<Rf>* cs = reinterpret_cast<cpx<Rf>*>(smem_raw);  // [nr][2][nv]
+  int* off = reinterpret_cast<int*>(cs + size_t(nr) * 2 * nv);
   const int xc = blockIdx.x;
   for (int ls = threadIdx.x; ls < m.per; ls += blockDim.x) off[ls] = local_offset(m, ls);
-  for (int t = threadIdx.x; t < 2 * nv; t += blockDim.x)
-    cs[t] = cpx<Rf>(coarse[size_t(xc) * 2 * nv + t]);
+  for (int t = threadIdx.x; t < nr * 2 * nv; t += blockDim.x) {
+    const int b = t / (2 * nv), e = t - b * 2 * nv;
+    cs[t] = cpx<Rf>(coarse[b * cstride + size_t(xc) * 2 * nv + e]);
+  }
   const size_t base = size_t(agg_origin(m, xc));
   __syncthreads();
   const int NP = nv / CPL, PW = NP / 2;  // 16-byte words per row and per half row
@@ -395,24 +428,25 @@ __global__ void __launch_bounds__(256) k_prolong12(cpx<Rf>* __restrict__ fine,
     const int ls = ok ? r / ND : 0, a = ok ? r - ls * ND : 0;
     const size_t x = base + off[ls];
     const uint4* vr = reinterpret_cast<const uint4*>(Vp + (x * ND + a) * nv) + q * PW;
-    const cpx<Rf>* c = cs + (a < ND / 2 ? 0 : nv) + q * PW * CPL;
-    cpx<Rf> acc(Rf(0), Rf(0));
-    for (int k0 = 0; ok && k0 < PW; k0 += 6) {
-      uint4 w[6];
+    uint4 w[MAXPW];
 #pragma unroll
-      for (int k = 0; k < 6; ++k)
-        if (k0 + k < PW) w[k] = ld_stream16(vr + k0 + k);
+    for (int k = 0; k < MAXPW; ++k)
+      if (ok && k < PW) w[k] = ld_stream16(vr + k);
+    const int coff = (a < ND / 2 ? 0 : nv) + q * PW * CPL;
+    for (int b = 0; b < nr; ++b) {
+      const cpx<Rf>* c = cs + b * 2 * nv + coff;
+      cpx<Rf> acc(Rf(0), Rf(0));
 #pragma unroll
-      for (int k = 0; k < 6; ++k)
-        if (k0 + k < PW) {
+      for (int k = 0; k < MAXPW; ++k)
+        if (ok && k < PW) {
           const cpx<Rf>* v = reinterpret_cast<const cpx<Rf>*>(&w[k]);
 #pragma unroll
-          for (int j = 0; j < CPL; ++j) cmac(acc, v[j], c[(k0 + k) * CPL + j]);
+          for (int j = 0; j < CPL; ++j) cmac(acc, v[j], c[k * CPL + j]);
         }
+      acc.re += __shfl_xor_sync(0xffffffffu, acc.re, 1);
+      acc.im += __shfl_xor_sync(0xffffffffu, acc.im, 1);
+      if (ok && q == 0) fine[b * fstride + x * ND + a] = acc;
     }
-    acc.re += __shfl_xor_sync(0xffffffffu, acc.re, 1);
-    acc.im += __shfl_xor_sync(0xffffffffu, acc.im, 1);
-    if (ok && q == 0) fine[x * ND + a] = acc;
   }
 }
 
@@ -479,72 +513,104 @@ void block_orthonormalise(mg_ctx* c, int level, cudaStream_t st) {
   F.have_V = true;
 }
 
+namespace {
+
+template <typename Rf, typename Rc>
+void launch_restrict12(int nrb, dim3 grid, int thr, size_t smem, cudaStream_t st, Vec coarse,
+                       Vec fine, const void* Vp, const AggMap& m, int nv, int G, int nchunk) {
+  auto* cp = (cpx<Rc>*)coarse.p;
+  auto* fp = (const cpx<Rf>*)fine.p;
+  auto* vp = (const cpx<Rf>*)Vp;
+  switch (nrb) {
+    case 8:
+      k_restrict12<Rf, Rc, 8><<<grid, thr, smem, st>>>(cp, fp, vp, m, nv, G, nchunk, fine.n,
+                                                        coarse.n);
+      break;
+    case 4:
+      k_restrict12<Rf, Rc, 4><<<grid, thr, smem, st>>>(cp, fp, vp, m, nv, G, nchunk, fine.n,
+                                                        coarse.n);
+      break;
+    case 2:
+      k_restrict12<Rf, Rc, 2><<<grid, thr, smem, st>>>(cp, fp, vp, m, nv, G, nchunk, fine.n,
+                                                        coarse.n);
+      break;
+    default:
+      k_restrict12<Rf, Rc, 1><<<grid, thr, smem, st>>>(cp, fp, vp, m, nv, G, nchunk, fine.n,
+                                                        coarse.n);
+      break;
+  }
+}
+
+#define GB_TRANSFER_DISPATCH(fprec, cprec, Rf, Rc, ...)      \
+  do {                                                       \
+    if ((fprec) == MG_F64) {                                 \
+      using Rf = double;                                     \
+      if ((cprec) == MG_F64) {                               \
+        using Rc = double;                                   \
+        __VA_ARGS__;                                         \
+      } else {                                               \
+        using Rc = float;                                    \
+        __VA_ARGS__;                                         \
+      }                                                      \
+    } else {                                                 \
+      using Rf = float;                                      \
+      if ((cprec) == MG_F64) {                               \
+        using Rc = double;                                   \
+        __VA_ARGS__;                                         \
+      } else {                                               \
+        using Rc = float;                                    \
+        __VA_ARGS__;                                         \
+      }                                                      \
+    }                                                        \
+  } while (0)
+
+}  // namespace
+
 void restrict_apply(mg_ctx* c, int level, Vec coarse, Vec fine, cudaStream_t st) {
   Level& F = c->L[level];
   Level& C = c->L[level + 1];
   GB_REQUIRE(F.have_V, MG_ERR_STATE, "restrict: null vectors not set");
   GB_REQUIRE(fine.prec == F.vprec, MG_ERR_ARG, "restrict: fine vector precision");
+  GB_REQUIRE(fine.nr == coarse.nr && fine.n == F.vec_elems() && coarse.n == C.vec_elems(),
+             MG_ERR_ARG, "restrict: vector shapes");
   AggMap m = make_map(F, C);
-  const int nv = F.nvec;
-  int G = 256 / nv;
-  if (G < 1) G = 1;
-  const int threads = G * nv;
-  const size_t smem = size_t(G) * 2 * nv * prec_bytes_complex(F.vprec);
+  const int nv = F.nvec, nr = fine.nr;
   const double vb = prec_bytes_complex(F.vprec);
   ProfScope ps(c->prof, st, "restrict", level,
-               double(F.g.vol) * F.nd * (nv + 1) * vb + double(C.g.vol) * C.nd * vb,
-               8.0 * F.g.vol * F.nd * nv);
+               double(F.g.vol) * F.nd * (nv + nr) * vb + double(C.g.vol) * C.nd * nr * vb,
+               8.0 * F.g.vol * F.nd * nv * nr);
   if (F.nd == 12) {
-    // per-aggregate kernel: NP 16-byte columns per Vp row, G site groups
+    // per-aggregate kernel: NP 16-byte columns per Vp row, G site groups,
+    // NRB right-hand sides per CTA
     const int cpl = F.vprec == MG_F64 ? 1 : 2;
     const int NP = nv / cpl;
     int G2 = 256 / NP;
     while (G2 > 1 && m.per % G2) --G2;
     const size_t smem2 = size_t(G2) * 2 * nv * size_t(vb) + size_t(m.per) * sizeof(int);
-    // the fine vector is read in 16-byte words: a misaligned caller pointer
+    // the fine vectors are read in 16-byte words: a misaligned caller pointer
     // takes the generic kernel
     const bool aligned = (reinterpret_cast<uintptr_t>(fine.p) & 15) == 0;
     if (aligned && nv % cpl == 0 && G2 >= 1 && smem2 <= 48 * 1024) {
-      const int thr = G2 * NP;
-      if (F.vprec == MG_F64) {
-        if (coarse.prec == MG_F64)
-          k_restrict12<double, double><<<C.g.vol, thr, smem2, st>>>(
-              (cpx<double>*)coarse.p, (const cpx<double>*)fine.p, F.Vp.as<cpx<double>>(), m, nv,
-              G2);
-        else
-          k_restrict12<double, float><<<C.g.vol, thr, smem2, st>>>(
-              (cpx<float>*)coarse.p, (const cpx<double>*)fine.p, F.Vp.as<cpx<double>>(), m, nv,
-              G2);
-      } else {
-        if (coarse.prec == MG_F64)
-          k_restrict12<float, double><<<C.g.vol, thr, smem2, st>>>(
-              (cpx<double>*)coarse.p, (const cpx<float>*)fine.p, F.Vp.as<cpx<float>>(), m, nv,
-              G2);
-        else
-          k_restrict12<float, float><<<C.g.vol, thr, smem2, st>>>(
-              (cpx<float>*)coarse.p, (const cpx<float>*)fine.p, F.Vp.as<cpx<float>>(), m, nv,
-              G2);
-      }
+      const int nrb = nr % 8 == 0 ? 8 : nr % 4 == 0 ? 4 : nr % 2 == 0 ? 2 : 1;
+      const int nchunk = nr / nrb;
+      const dim3 grid(unsigned(C.g.vol) * nchunk);
+      GB_TRANSFER_DISPATCH(F.vprec, coarse.prec, Rf, Rc,
+                           (launch_restrict12<Rf, Rc>(nrb, grid, G2 * NP, smem2, st, coarse, fine,
+                                                      F.Vp.p, m, nv, G2, nchunk)));
       GB_LAUNCH_CHECK();
       c->launches++;
       return;
     }
   }
-  if (F.vprec == MG_F64) {
-    if (coarse.prec == MG_F64)
-      k_restrict<double, double><<<C.g.vol, threads, smem, st>>>(
-          (cpx<double>*)coarse.p, (const cpx<double>*)fine.p, F.Vp.as<cpx<double>>(), m, F.nd, nv);
-    else
-      k_restrict<double, float><<<C.g.vol, threads, smem, st>>>(
-          (cpx<float>*)coarse.p, (const cpx<double>*)fine.p, F.Vp.as<cpx<double>>(), m, F.nd, nv);
-  } else {
-    if (coarse.prec == MG_F64)
-      k_restrict<float, double><<<C.g.vol, threads, smem, st>>>(
-          (cpx<double>*)coarse.p, (const cpx<float>*)fine.p, F.Vp.as<cpx<float>>(), m, F.nd, nv);
-    else
-      k_restrict<float, float><<<C.g.vol, threads, smem, st>>>(
-          (cpx<float>*)coarse.p, (const cpx<float>*)fine.p, F.Vp.as<cpx<float>>(), m, F.nd, nv);
-  }
+  int G = 256 / nv;
+  if (G < 1) G = 1;
+  const int threads = G * nv;
+  const size_t smem = size_t(G) * 2 * nv * prec_bytes_complex(F.vprec);
+  const dim3 grid(unsigned(C.g.vol) * nr);
+  GB_TRANSFER_DISPATCH(F.vprec, coarse.prec, Rf, Rc,
+                       (k_restrict<Rf, Rc><<<grid, threads, smem, st>>>(
+                           (cpx<Rc>*)coarse.p, (const cpx<Rf>*)fine.p, F.Vp.as<cpx<Rf>>(), m,
+                           F.nd, nv, nr, fine.n, coarse.n)));
   GB_LAUNCH_CHECK();
   c->launches++;
 }
@@ -554,49 +620,31 @@ void prolong_apply(mg_ctx* c, int level, Vec fine, Vec coarse, cudaStream_t st) 
   Level& C = c->L[level + 1];
   GB_REQUIRE(F.have_V, MG_ERR_STATE, "prolong: null vectors not set");
   GB_REQUIRE(fine.prec == F.vprec, MG_ERR_ARG, "prolong: fine vector precision");
+  GB_REQUIRE(fine.nr == coarse.nr && fine.n == F.vec_elems() && coarse.n == C.vec_elems(),
+             MG_ERR_ARG, "prolong: vector shapes");
   AggMap m = make_map(F, C);
-  const int nv = F.nvec;
+  const int nv = F.nvec, nr = fine.nr;
   const size_t n = size_t(F.g.vol) * F.nd;
   const double vb = prec_bytes_complex(F.vprec);
   ProfScope ps(c->prof, st, "prolong", level,
-               double(n) * (nv + 1) * vb + double(C.g.vol) * C.nd * vb, 8.0 * n * nv);
+               double(n) * (nv + nr) * vb + double(C.g.vol) * C.nd * nr * vb, 8.0 * n * nv * nr);
   const int cpl = F.vprec == MG_F64 ? 1 : 2;
-  const size_t smem2 = size_t(2) * nv * size_t(vb) + size_t(m.per) * sizeof(int);
-  if (F.nd == 12 && nv % (2 * cpl) == 0 && smem2 <= 48 * 1024) {
-    if (F.vprec == MG_F64) {
-      if (coarse.prec == MG_F64)
-        k_prolong12<double, double><<<C.g.vol, 256, smem2, st>>>(
-            (cpx<double>*)fine.p, (const cpx<double>*)coarse.p, F.Vp.as<cpx<double>>(), m, nv);
-      else
-        k_prolong12<double, float><<<C.g.vol, 256, smem2, st>>>(
-            (cpx<double>*)fine.p, (const cpx<float>*)coarse.p, F.Vp.as<cpx<double>>(), m, nv);
-    } else {
-      if (coarse.prec == MG_F64)
-        k_prolong12<float, double><<<C.g.vol, 256, smem2, st>>>(
-            (cpx<float>*)fine.p, (const cpx<double>*)coarse.p, F.Vp.as<cpx<float>>(), m, nv);
-      else
-        k_prolong12<float, float><<<C.g.vol, 256, smem2, st>>>(
-            (cpx<float>*)fine.p, (const cpx<float>*)coarse.p, F.Vp.as<cpx<float>>(), m, nv);
-    }
+  const size_t smem2 = size_t(nr) * 2 * nv * size_t(vb) + size_t(m.per) * sizeof(int);
+  if (F.nd == 12 && nv % (2 * cpl) == 0 && nv / (2 * cpl) <= 12 && smem2 <= 48 * 1024) {
+    GB_TRANSFER_DISPATCH(F.vprec, coarse.prec, Rf, Rc,
+                         (k_prolong12<Rf, Rc><<<C.g.vol, 256, smem2, st>>>(
+                             (cpx<Rf>*)fine.p, (const cpx<Rc>*)coarse.p, F.Vp.as<cpx<Rf>>(), m,
+                             nv, nr, fine.n, coarse.n)));
     GB_LAUNCH_CHECK();
     c->launches++;
     return;
   }
-  if (F.vprec == MG_F64) {
-    if (coarse.prec == MG_F64)
-      k_prolong<double, double><<<grid_for(n), 256, 0, st>>>(
-          (cpx<double>*)fine.p, (const cpx<double>*)coarse.p, F.Vp.as<cpx<double>>(), m, F.nd, nv);
-    else
-      k_prolong<double, float><<<grid_for(n), 256, 0, st>>>(
-          (cpx<double>*)fine.p, (const cpx<float>*)coarse.p, F.Vp.as<cpx<double>>(), m, F.nd, nv);
-  } else {
-    if (coarse.prec == MG_F64)
-      k_prolong<float, double><<<grid_for(n), 256, 0, st>>>(
-          (cpx<float>*)fine.p, (const cpx<double>*)coarse.p, F.Vp.as<cpx<float>>(), m, F.nd, nv);
-    else
-      k_prolong<float, float><<<grid_for(n), 256, 0, st>>>(
-          (cpx<float>*)fine.p, (const cpx<float>*)coarse.p, F.Vp.as<cpx<float>>(), m, F.nd, nv);
-  }
+  int blocks = grid_for(n);
+  if (blocks * size_t(nr) > (1u << 30)) blocks = int((1u << 30) / nr);
+  GB_TRANSFER_DISPATCH(F.vprec, coarse.prec, Rf, Rc,
+                       (k_prolong<Rf, Rc><<<unsigned(blocks) * nr, 256, 0, st>>>(
+                           (cpx<Rf>*)fine.p, (const cpx<Rc>*)coarse.p, F.Vp.as<cpx<Rf>>(), m,
+                           F.nd, nv, nr, fine.n, coarse.n)));
   GB_LAUNCH_CHECK();
   c->launches++;
 }
