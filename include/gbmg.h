@@ -229,6 +229,18 @@ mg_status mg_profile_reset(mg_ctx* ctx);
 mg_status mg_profile_query(mg_ctx* ctx, const char* name, int level, int* launches,
                            double* total_ms, double* bytes, double* flops);
 
+/* Launch-policy autotuner (process-wide).  The first call of a tuned kernel
+ * for a shape times its candidate policies and keeps the fastest; keys name
+ * the kernel and shape, e.g. "wilson/v<volume>/n<vectors>/c<0|1>".
+ * mg_tune_set pins `choice` for `key` (a choice that is not a candidate of
+ * a later call is ignored there; choice < 0 removes the entry so the next
+ * call tunes again); mg_tune_get returns the entry or -1.  The environment
+ * variable GBMG_TUNE=0 turns timing off (first candidate) and
+ * GBMG_TUNE_CACHE=<file> keeps choices across processes.  The paper's
+ * autotuning of launch parameters (Sec. IV) is the model.                  */
+mg_status mg_tune_set(const char* key, int choice);
+int mg_tune_get(const char* key);
+
 /* Block orthonormalisation that allocates no device memory.  The paper has
  * no counterpart: this entry point exists for callers that cannot let a
  * library call cudaMalloc -- programs whose device memory belongs to another

@@ -85,6 +85,8 @@ def _load():
         "mg_prolong": (i, [vp, i, vp, vp, vp]),
         "mg_gcr_solve": (i, [vp, vp, vp, d, i, C.POINTER(mg_solve_stats), vp]),
         "mg_gcr_solve_multi": (i, [vp, vp, vp, i, d, i, C.POINTER(mg_solve_stats), vp]),
+        "mg_tune_set": (i, [C.c_char_p, i]),
+        "mg_tune_get": (i, [C.c_char_p]),
         "mg_get_coarse_links": (i, [vp, i, vp, sz, vp]),
         "mg_set_coarse_links": (i, [vp, i, vp, sz, vp]),
         "mg_level_info": (i, [vp, i, C.POINTER(C.c_int), C.POINTER(C.c_int),
@@ -236,6 +238,15 @@ def mg_gcr_solve_multi(ctx, x, b, nrhs, tol=1e-10, maxiter=200, stream=None, che
     return [dict(status=st, iters=s.iters, restarts=s.restarts,
                  level_iters=list(s.level_iters), true_residual=s.true_residual,
                  seconds=s.seconds, history=list(s.history[:s.history_len])) for s in recs]
+
+
+def mg_tune_set(key, choice):
+    """Pin the autotuner's choice for `key` (choice < 0: forget it)."""
+    _ok(LIB.mg_tune_set(key.encode(), int(choice)), None)
+
+
+def mg_tune_get(key):
+    return LIB.mg_tune_get(key.encode())
 
 
 def mg_get_coarse_links(ctx, level, out, stream=None):

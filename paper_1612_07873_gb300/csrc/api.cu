@@ -4,6 +4,7 @@
 #include <string>
 
 #include "kernels.cuh"
+#include "tune.cuh"
 
 using namespace gbmg;
 
@@ -303,6 +304,17 @@ mg_status mg_gcr_solve_multi(mg_ctx* c, void* x, const void* b, int nrhs, double
     gcr_solve_multi(c, x, b, nrhs, tol, maxiter, stats, S(stream));
   });
 }
+
+mg_status mg_tune_set(const char* key, int choice) {
+  if (!key) {
+    set_last_error("tune_set: null key");
+    return MG_ERR_ARG;
+  }
+  gbmg::Tuner::get().set(key, choice);
+  return MG_OK;
+}
+
+int mg_tune_get(const char* key) { return key ? gbmg::Tuner::get().get(key) : -1; }
 
 mg_status mg_get_coarse_links(mg_ctx* c, int level, void* dst, size_t bytes, void* stream) {
   return guarded(c, [&] {

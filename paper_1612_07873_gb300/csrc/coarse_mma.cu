@@ -210,12 +210,25 @@ __global__ void __launch_bounds__(128) k_coarse_mma(const MmaBatch batch, int nr
   // independent loads (every load of the slot in flight at once); slot d+1
   // is fetched while slot d's barrier and MMAs run.
   MmaLattice cur = batch.lat[0];  // lattice of the site being processed
-  constexpr int XPT = ((N / 2) * 64 + 127) / 128;  // spinor elements per thread (nrhs <= 64)
+  // Spinor staging: the (N/2) x nrhs complex values of a stage are cut into
+  // tiles of 4 columns k x 8 right-hand sides j; warp w stages tiles w, w+4,
+  // ...  Lane l takes j = 8 jt + (l & 7), k = 4 kt + (l >> 3), so the 32
+  // 4-byte stores of a warp fill one 8-row x 16-byte core matrix: 32
+  // different banks.  The right-hand-side tile count is rounded up to a
+  // power of two (tiles past nrhs stage nothing) so the mapping is shifts.
+  constexpr int XPT = N / 4;                        // tiles per warp (nrhs <= 64)
   constexpr int BPT = (B_BYTES / 16 + 127) / 128;   // 16-byte link chunks per thread
   cpx<float> xr[XPT];
   uint4 br[BPT];
   const int nx = N * nrhs;          // spinor elements of one site
   const int nxs = (N / 2) * nrhs;   // spinor elements of one stage
+  const int jsh = nrhs <= 8 ? 0 : nrhs <= 16 ? 1 : nrhs <= 32 ? 2 : 3;  // log2 of the tile count
+  auto tile_jk = [&](int u, int& j, int& k) {
+    const int t = warp + 4 * u;
+    j = 8 * (t & ((1 << jsh) - 1)) + (lane & 7);
+    k = 4 * (t >> jsh) + (lane >> 3);
+    return k < N / 2 && j < nrhs;
+  };
   auto fetch = [&](int site, int st) {
     const int d = st >> 1, h = st & 1;
     const cpx<float>* xs = cur.x + size_t(nb_sh[d]) * nx + size_t(h) * nxs;
@@ -227,8 +240,8 @@ __global__ void __launch_bounds__(128) k_coarse_mma(const MmaBatch batch, int nr
     }
 #pragma unroll
     for (int u = 0; u < XPT; ++u) {
-      const int e = tid + 128 * u;
-      if (e < nxs) xr[u] = xs[e];
+      int j, k;
+      if (tile_jk(u, j, k)) xr[u] = xs[k * nrhs + j];
     }
   };
   auto stage = [&](int b) {
@@ -241,9 +254,8 @@ __global__ void __launch_bounds__(128) k_coarse_mma(const MmaBatch batch, int nr
     unsigned char* A = ABUF(b);
 #pragma unroll
     for (int u = 0; u < XPT; ++u) {
-      const int e = tid + 128 * u;
-      if (e < nxs) {
-        const int k = e / nrhs, j = e - k * nrhs;  // k: complex column within the stage
+      int j, k;  // k: complex column within the stage, j: right-hand side
+      if (tile_jk(u, j, k)) {
         const cpx<float> v = xr[u];
         *reinterpret_cast<uint32_t*>(A + core_off(j, 2 * k, KS)) = pack2<BF16>(v.re, -v.im);
         *reinterpret_cast<uint32_t*>(A + core_off(nrhs + j, 2 * k, KS)) = pack2<BF16>(v.im, v.re);
@@ -306,8 +318,13 @@ __global__ void __launch_bounds__(128) k_coarse_mma(const MmaBatch batch, int nr
       }
     if (!ok) break;
     tc_fence_after();
-    // TMEM lanes 32w..32w+31 = rows of D, staged as FP32 [row][N] over the two
-    // spinor buffers (2 nrhs * 4N <= 512 N bytes = both buffers)
+    // TMEM lanes 32w..32w+31 = rows of D, staged as FP32 [row][N + 1] (the
+    // odd row stride keeps both the row-per-lane stores and the column reads
+    // below free of bank conflicts) over the spinor buffers and, for 2 nrhs
+    // = 128, the first 512 bytes of the idle link buffer: 128 (N + 1) 4 <=
+    // 2 A_BYTES + B_BYTES for N = 32, 48, 64
+    constexpr int CS = N + 1;
+    static_assert(128 * CS * 4 <= 2 * A_BYTES + B_BYTES, "epilogue staging fits");
     float* Cs = reinterpret_cast<float*>(smem);
     const int row = 32 * warp + lane;
 #pragma unroll
@@ -316,7 +333,7 @@ __global__ void __launch_bounds__(128) k_coarse_mma(const MmaBatch batch, int nr
       tmem_ld16(tmem + (uint32_t(32 * warp) << 16) + uint32_t(c0), v);
       if (row < 2 * nrhs) {
 #pragma unroll
-        for (int q = 0; q < 16; ++q) Cs[row * N + c0 + q] = v[q];
+        for (int q = 0; q < 16; ++q) Cs[row * CS + c0 + q] = v[q];
       }
     }
     tc_fence_before();
@@ -325,7 +342,7 @@ __global__ void __launch_bounds__(128) k_coarse_mma(const MmaBatch batch, int nr
     cpx<float>* ys = cur.y + size_t(site) * nx;
     for (int e = tid; e < nx; e += 128) {
       const int m = e / nrhs, j = e - m * nrhs;
-      ys[e] = cpx<float>(sc * Cs[j * N + m], sc * Cs[(nrhs + j) * N + m]);
+      ys[e] = cpx<float>(sc * Cs[j * CS + m], sc * Cs[(nrhs + j) * CS + m]);
     }
     __syncthreads();
     // restore the zero rows >= 2 nrhs of both spinor buffers

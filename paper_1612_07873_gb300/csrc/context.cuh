@@ -76,6 +76,12 @@ struct Level {
   // fine operator (level 0): gauge [4][V][9] complex with the t boundary
   // sign folded into the last slice; clover [V][2][36] packed Hermitian.
   DevBuf gauge64, gauge32, clover64, clover32;
+  // FP32 links compressed to their first two rows [mu][V][6] complex; the
+  // third row is rebuilt as conj(row0 x row1) (times the boundary sign),
+  // valid when the field is special unitary to FP32 precision (checked at
+  // import: gauge12_ok)
+  DevBuf gauge12;
+  bool gauge12_ok = false;
   double diag = 0.0;           // 4 + m
 
   // coarse operator (level >= 1): internal layout [V][9][col][row] in vprec;

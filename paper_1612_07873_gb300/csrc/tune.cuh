@@ -7,6 +7,7 @@
 // is used, so tune (make one call) before capturing.
 #pragma once
 
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <fstream>
@@ -33,7 +34,10 @@ class Tuner {
     std::lock_guard<std::mutex> lk(mu_);
     load();
     auto it = best_.find(key);
-    if (it != best_.end()) return it->second;
+    // a cached or pinned choice is used only if it is a candidate of this call
+    if (it != best_.end() &&
+        std::find(cands.begin(), cands.end(), it->second) != cands.end())
+      return it->second;
     if (!enabled_ || cands.size() == 1) return cands.front();
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
@@ -70,6 +74,23 @@ class Tuner {
   size_t size() {
     std::lock_guard<std::mutex> lk(mu_);
     return best_.size();
+  }
+
+  // pin a choice for key (choice < 0 removes the entry, so the next call
+  // tunes again); the pin is not written to the cache file
+  void set(const std::string& key, int choice) {
+    std::lock_guard<std::mutex> lk(mu_);
+    load();
+    if (choice < 0)
+      best_.erase(key);
+    else
+      best_[key] = choice;
+  }
+  int get(const std::string& key) {
+    std::lock_guard<std::mutex> lk(mu_);
+    load();
+    auto it = best_.find(key);
+    return it == best_.end() ? -1 : it->second;
   }
 
  private:

@@ -1,5 +1,7 @@
 // Fine Wilson-clover operator of Eq. (2): gauge import, clover term A_x
 // and the stencil apply (one thread per site and vector).
+#include <cstring>
+
 #include "kernels.cuh"
 #include "wilson_ops.cuh"
 #include "tune.cuh"
@@ -24,6 +26,36 @@ __global__ void k_gauge_import(cpx<R>* __restrict__ out, const cpx<double>* __re
     if (antiperiodic && mu == 3 && s / g.stride[3] == g.L[3] - 1) sgn = -1.0;
     out[i] = cpx<R>(sgn * in[i]);
   }
+}
+
+// First two rows of every (sign-folded) link in FP32, [mu][V][6] complex,
+// and the largest deviation, over all links, of the rebuilt third row
+// sgn * conj(row0 x row1) from the stored one (FP64, as float bits into
+// *maxdev; non-negative floats order like their bit patterns).
+__global__ void k_gauge_compress12(cpx<float>* __restrict__ out, unsigned* __restrict__ maxdev,
+                                   const cpx<double>* __restrict__ in, Geom g, int antiperiodic) {
+  const size_t n = size_t(4) * g.vol;
+  float dev = 0.f;
+  for (size_t link = blockIdx.x * size_t(blockDim.x) + threadIdx.x; link < n;
+       link += size_t(gridDim.x) * blockDim.x) {
+    const int mu = int(link / g.vol);
+    const int s = int(link % g.vol);
+    const double sgn = (antiperiodic && mu == 3 && s / g.stride[3] == g.L[3] - 1) ? -1.0 : 1.0;
+    cpx<double> u[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) u[i] = sgn * in[link * 9 + i];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) out[link * 6 + i] = cpx<float>(u[i]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int b = (a + 1) % 3, c = (a + 2) % 3;
+      const cpx<double> r = sgn * conj(u[b] * u[3 + c] - u[c] * u[3 + b]);
+      const cpx<double> d = r - u[6 + a];
+      dev = fmaxf(dev, float(sqrt(d.re * d.re + d.im * d.im)));
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) dev = fmaxf(dev, __shfl_xor_sync(0xffffffffu, dev, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(maxdev, __float_as_uint(dev));
 }
 
 struct M3 {
@@ -154,10 +186,14 @@ __global__ void k_clover(const cpx<double>* __restrict__ U, Geom g, double csw,
   }
 }
 
-template <typename R>
-__global__ void __launch_bounds__(128) k_wilson(cpx<R>* __restrict__ out, const cpx<R>* __restrict__ in,
+// C12: links in the two-row form (16-byte loads, 48 B per FP32 link) with
+// the third row rebuilt in registers; the rebuilt row carries the boundary
+// sign of the link (t-links leaving the last time slice).
+template <typename R, bool C12, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_wilson(cpx<R>* __restrict__ out, const cpx<R>* __restrict__ in,
                                                 const cpx<R>* __restrict__ U, const R* __restrict__ A,
-                                                Geom g, R diag, size_t vstride, int nvec) {
+                                                Geom g, R diag, size_t vstride, int nvec,
+                                                int antiperiodic) {
   // CTAs are ordered vector-fastest: the nvec CTAs of one site chunk run
   // close together, so the chunk's links and clover come from DRAM once and
   // from L2 for the other vectors.
@@ -180,10 +216,27 @@ __global__ void __launch_bounds__(128) k_wilson(cpx<R>* __restrict__ out, const 
 #pragma unroll
     for (int i = 0; i < 12; ++i) psi[i] = reinterpret_cast<const cpx<R>*>(w)[i];
   };
-  auto load_link = [&](size_t idx) {
+  auto load_link = [&](size_t idx, bool neg) {
+    if constexpr (C12) {
+      const uint4* p = reinterpret_cast<const uint4*>(U + idx * 6);
+      uint4 w[3];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) u[i] = U[idx * 9 + i];
+      for (int i = 0; i < 3; ++i) w[i] = __ldg(p + i);
+#pragma unroll
+      for (int i = 0; i < 6; ++i) u[i] = reinterpret_cast<const cpx<R>*>(w)[i];
+      const R sg = neg ? R(-1) : R(1);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int b = (a + 1) % 3, c = (a + 2) % 3;
+        u[6 + a] = sg * conj(u[b] * u[3 + c] - u[c] * u[3 + b]);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) u[i] = U[idx * 9 + i];
+    }
   };
+  // boundary sign of the t-links that wrap (only the rebuilt row needs it)
+  const bool tlast = antiperiodic && c[3] == g.L[3] - 1, tfirst = antiperiodic && c[3] == 0;
   load_spinor(s);
 #pragma unroll
   for (int i = 0; i < 12; ++i) acc[i] = cpx<R>(R(0), R(0));
@@ -200,11 +253,11 @@ __global__ void __launch_bounds__(128) k_wilson(cpx<R>* __restrict__ out, const 
   {                                                      \
     int sf = neighbour(g, s, c, 1 + 2 * MU);             \
     load_spinor(sf);                                     \
-    load_link(MU * V + s);                               \
+    load_link(MU * V + s, MU == 3 && tlast);             \
     hop_accum<MU, true>(u, psi, acc);                    \
     int sb = neighbour(g, s, c, 2 + 2 * MU);             \
     load_spinor(sb);                                     \
-    load_link(MU * V + sb);                              \
+    load_link(MU * V + sb, MU == 3 && tfirst);           \
     hop_accum<MU, false>(u, psi, acc);                   \
   }
   GB_HOP(0) GB_HOP(1) GB_HOP(2) GB_HOP(3)
@@ -309,6 +362,24 @@ void fine_operator_build(mg_ctx* c, const void* gauge_ext, cudaStream_t st) {
     GB_LAUNCH_CHECK();
     L.clover32.alloc(size_t(L.g.vol) * 72 * sizeof(float));
     c32 = L.clover32.as<float>();
+    // two-row link form, used only if every link rebuilds to FP32 precision
+    L.gauge12.alloc(size_t(4) * L.g.vol * 6 * sizeof(cpx<float>));
+    DevBuf dev;
+    dev.alloc(sizeof(unsigned));
+    GB_CHECK(cudaMemsetAsync(dev.p, 0, sizeof(unsigned), st));
+    int blocks = ceil_div(size_t(4) * L.g.vol, 256);
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    k_gauge_compress12<<<blocks, 256, 0, st>>>(L.gauge12.as<cpx<float>>(), dev.as<unsigned>(),
+                                                (const cpx<double>*)gauge_ext, L.g,
+                                                c->p.t_antiperiodic);
+    GB_LAUNCH_CHECK();
+    unsigned h = 0;
+    GB_CHECK(cudaMemcpyAsync(&h, dev.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    GB_CHECK(cudaStreamSynchronize(st));
+    float maxdev;
+    std::memcpy(&maxdev, &h, sizeof(float));
+    L.gauge12_ok = maxdev < 1e-5f;
+    c->launches++;
   }
   k_clover<<<ceil_div(L.g.vol, 128), 128, 0, st>>>(L.gauge64.as<cpx<double>>(), L.g, c->p.csw,
                                                     L.clover64.as<double>(), c32);
@@ -329,40 +400,44 @@ void wilson_apply(mg_ctx* c, Vec out, Vec in, int nvec, cudaStream_t st) {
   const double bytes =
       double(L.g.vol) * (48.0 * nvec + 144.0) * (out.prec == MG_F64 ? 8 : 4);
   ProfScope ps(c->prof, st, "wilson_clover", 0, bytes, double(nvec) * L.g.vol * 1824.0);
-  if (out.prec == MG_F32 && nvec > 1 && nvec % 2 == 0) {
-    // batched: NB vectors per thread; the autotuner picks NB in {1, 2, 4}
-    // (more reuse of the links and clover against fewer resident warps)
+  if (out.prec == MG_F32) {
+    // FP32: the autotuner picks one launch policy from kPolicies: vectors
+    // per thread (1, 2, 4: more reuse of the links and clover against fewer
+    // resident warps), link form (two-row links rebuilt in registers, when
+    // the field allows it) and register budget (minimum CTAs per SM given
+    // to the compiler; 0 = its default).
     GB_REQUIRE(L.gauge32.p, MG_ERR_STATE, "FP32 fine operator not built");
     const unsigned gx = ceil_div(L.g.vol, 128);
-    auto launch = [&](int nb) {
-      if (nb == 4)
-        k_wilson_mv<float, 4><<<dim3(gx, nvec / 4), 128, 0, st>>>(
-            (cpx<float>*)out.p, (const cpx<float>*)in.p, L.gauge32.as<cpx<float>>(),
-            L.clover32.as<float>(), L.g, float(L.diag), vs);
-      else if (nb == 2)
-        k_wilson_mv<float, 2><<<dim3(gx, nvec / 2), 128, 0, st>>>(
-            (cpx<float>*)out.p, (const cpx<float>*)in.p, L.gauge32.as<cpx<float>>(),
-            L.clover32.as<float>(), L.g, float(L.diag), vs);
-      else
-        k_wilson<float><<<grid, 128, 0, st>>>((cpx<float>*)out.p, (const cpx<float>*)in.p,
-                                              L.gauge32.as<cpx<float>>(),
-                                              L.clover32.as<float>(), L.g, float(L.diag), vs,
-                                              nvec);
+    const int ap = c->p.t_antiperiodic;
+    const cpx<float>* U18 = L.gauge32.as<cpx<float>>();
+    const cpx<float>* U12 = L.gauge12.as<cpx<float>>();
+    const float* A = L.clover32.as<float>();
+    auto* o = (cpx<float>*)out.p;
+    auto* i = (const cpx<float>*)in.p;
+    const float dg = float(L.diag);
+    auto launch = [&](int q) {
+      switch (q) {
+        case 1: k_wilson<float, true, 0><<<grid, 128, 0, st>>>(o, i, U12, A, L.g, dg, vs, nvec, ap); break;
+        case 2: k_wilson<float, false, 2><<<grid, 128, 0, st>>>(o, i, U18, A, L.g, dg, vs, nvec, ap); break;
+        case 3: k_wilson<float, true, 2><<<grid, 128, 0, st>>>(o, i, U12, A, L.g, dg, vs, nvec, ap); break;
+        case 4: k_wilson<float, true, 4><<<grid, 128, 0, st>>>(o, i, U12, A, L.g, dg, vs, nvec, ap); break;
+        case 5: k_wilson<float, true, 6><<<grid, 128, 0, st>>>(o, i, U12, A, L.g, dg, vs, nvec, ap); break;
+        case 6: k_wilson_mv<float, 2><<<dim3(gx, nvec / 2), 128, 0, st>>>(o, i, U18, A, L.g, dg, vs); break;
+        case 7: k_wilson_mv<float, 4><<<dim3(gx, nvec / 4), 128, 0, st>>>(o, i, U18, A, L.g, dg, vs); break;
+        default: k_wilson<float, false, 0><<<grid, 128, 0, st>>>(o, i, U18, A, L.g, dg, vs, nvec, ap); break;
+      }
     };
-    std::vector<int> cands = {2, 1};
-    if (nvec % 4 == 0) cands.insert(cands.begin(), 4);
-    const std::string key =
-        "wilson_mv/v" + std::to_string(L.g.vol) + "/n" + std::to_string(nvec);
+    std::vector<int> cands = {0, 2};
+    if (L.gauge12_ok) cands.insert(cands.end(), {1, 3, 4, 5});
+    if (nvec % 2 == 0) cands.push_back(6);
+    if (nvec % 4 == 0) cands.push_back(7);
+    const std::string key = "wilson/v" + std::to_string(L.g.vol) + "/n" + std::to_string(nvec) +
+                            "/c" + std::to_string(int(L.gauge12_ok));
     launch(Tuner::get().choose(key, cands, st, launch));
-  } else if (out.prec == MG_F64) {
-    k_wilson<double><<<grid, 128, 0, st>>>((cpx<double>*)out.p, (const cpx<double>*)in.p,
-                                           L.gauge64.as<cpx<double>>(), L.clover64.as<double>(),
-                                           L.g, L.diag, vs, nvec);
   } else {
-    GB_REQUIRE(L.gauge32.p, MG_ERR_STATE, "FP32 fine operator not built");
-    k_wilson<float><<<grid, 128, 0, st>>>((cpx<float>*)out.p, (const cpx<float>*)in.p,
-                                          L.gauge32.as<cpx<float>>(), L.clover32.as<float>(),
-                                          L.g, float(L.diag), vs, nvec);
+    k_wilson<double, false, 0><<<grid, 128, 0, st>>>(
+        (cpx<double>*)out.p, (const cpx<double>*)in.p, L.gauge64.as<cpx<double>>(),
+        L.clover64.as<double>(), L.g, L.diag, vs, nvec, c->p.t_antiperiodic);
   }
   GB_LAUNCH_CHECK();
   c->launches++;

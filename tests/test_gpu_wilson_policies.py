@@ -1,0 +1,82 @@
+"""Every launch policy of the FP32 fine operator against the FP64 oracle.
+
+The autotuner picks one policy per shape; here each policy is pinned in turn
+through mg_tune_set: stored 18-real links or two-row links rebuilt in
+registers (third row = conj(row0 x row1) times the boundary sign), four
+register budgets, and 2 or 4 vectors per thread in the batched form used by
+the setup sweeps.  A field that is not special unitary must never take the
+two-row form.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synthetic as syn
+from oracle import dirac, lattice as lat, multigrid as mgo
+from gpu_helpers import make_ctx, oracle_fine, rel_l2, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+SINGLE = [0, 1, 2, 3, 4, 5]   # 1 vector per thread: (link form, register budget)
+BATCHED = [6, 7]              # 2 or 4 vectors per thread
+
+
+@pytest.mark.parametrize("antiperiodic", [1, 0])
+@pytest.mark.parametrize("policy", SINGLE)
+def test_single_vector_policy(gpu_lib, policy, antiperiodic):
+    gb = gpu_lib
+    dims = (4, 6, 4, 8)
+    vol = lat.volume(dims)
+    gb.mg_tune_set(f"wilson/v{vol}/n1/c1", policy)
+    mg, U = make_ctx(gb, dims, [(2, 2, 2, 2)], [2], prec_fine=1, prec_coarse=1,
+                     antiperiodic=antiperiodic, eps=0.5)
+    psi = syn.gaussian_field((vol, 12), 71)
+    out = torch.empty((vol, 12), dtype=torch.complex64, device="cuda")
+    gb.mg_wilson_clover_apply(mg.ctx, out, to_dev(psi, torch.complex64))
+    torch.cuda.synchronize()
+    assert gb.mg_tune_get(f"wilson/v{vol}/n1/c1") == policy
+    op = dirac.wilson_clover_op(U, dims, -0.2, 1.0, antiperiodic=bool(antiperiodic))
+    err = rel_l2(to_np(out), op.apply(psi))
+    assert err < 1e-5, (policy, err)
+    gb.mg_tune_set(f"wilson/v{vol}/n1/c1", -1)
+    mg.close()
+
+
+@pytest.mark.parametrize("policy", BATCHED + [1])
+def test_batched_policy_in_setup(gpu_lib, policy):
+    gb = gpu_lib
+    dims, nv, sweeps = (4, 4, 4, 8), 4, 3
+    vol = lat.volume(dims)
+    gb.mg_tune_set(f"wilson/v{vol}/n{nv}/c1", policy)
+    mg, U = make_ctx(gb, dims, [(2, 2, 2, 2)], [nv], sweeps=sweeps, prec_fine=1,
+                     prec_coarse=1)
+    x0 = syn.gaussian_field((nv, vol, 12), 72)
+    gb.mg_setup_nullvecs(mg.ctx, 0, to_dev(x0))
+    raw = torch.empty((nv, vol, 12), dtype=torch.complex128, device="cuda")
+    gb.mg_get_nullvecs(mg.ctx, 0, raw, kind=0)
+    torch.cuda.synchronize()
+    assert gb.mg_tune_get(f"wilson/v{vol}/n{nv}/c1") == policy
+    err = rel_l2(to_np(raw), mgo.null_vectors(oracle_fine(U, dims), x0, sweeps))
+    assert err < 1e-5, (policy, err)
+    gb.mg_tune_set(f"wilson/v{vol}/n{nv}/c1", -1)
+    mg.close()
+
+
+def test_non_unitary_field_keeps_stored_links(gpu_lib):
+    """Links scaled off SU(3): the two-row form is not eligible (key suffix
+    c0) and a pinned two-row policy is ignored."""
+    gb = gpu_lib
+    dims = (4, 4, 6, 4)
+    vol = lat.volume(dims)
+    U = syn.gauge_field(dims, 0.4, 5) * 1.05
+    gb.mg_tune_set(f"wilson/v{vol}/n1/c0", 3)  # a two-row policy: not a candidate here
+    mg, _ = make_ctx(gb, dims, [(2, 2, 2, 2)], [2], prec_fine=1, prec_coarse=1, U=U)
+    psi = syn.gaussian_field((vol, 12), 73)
+    out = torch.empty((vol, 12), dtype=torch.complex64, device="cuda")
+    gb.mg_wilson_clover_apply(mg.ctx, out, to_dev(psi, torch.complex64))
+    torch.cuda.synchronize()
+    assert gb.mg_tune_get(f"wilson/v{vol}/n1/c0") in (0, 2)
+    err = rel_l2(to_np(out), oracle_fine(U, dims).apply(psi))
+    assert err < 1e-5, err
+    gb.mg_tune_set(f"wilson/v{vol}/n1/c0", -1)
+    mg.close()
