@@ -5,10 +5,10 @@
  *
  * Method: Clark et al., "Accelerating Lattice QCD Multigrid on GPUs Using
  * Fine-Grained Parallelization" (SC16).  Eq. (1) is the linear system
- * M x = b, Eq. (2) the fine Wilson-clover matrix, Sec. II-D the adaptive
+ * M x = b, Eq. (2) the fine Wilson-clover matrix, Sec. 3.4 the adaptive
  * setup (null vectors, aggregates, chiral split, block QR, Galerkin
- * product), Eq. (3) the coarse operator, Sec. IV the coarse stencil
- * kernel, Sec. IV-F the transfer operators, Sec. VI-A the K-cycle solver.
+ * product), Eq. (3) the coarse operator, Sec. 6 the coarse stencil
+ * kernel, Sec. 6.6 the transfer operators, Sec. 7.1 the K-cycle solver.
  *
  * Conventions shared by every call
  * --------------------------------
@@ -19,7 +19,7 @@
  *                     in the DeGrand-Rossi chiral basis, gamma_5 =
  *                     diag(1, 1, -1, -1): spins {0,1} = chirality 0.
  * Coarse spinor       [site][dof] complex, dof = s*Nv + c, s the chirality
- *                     (Sec. IV-B), 2*Nv dofs per site.
+ *                     (Sec. 6.2), 2*Nv dofs per site.
  * Multi-RHS spinor    [site][dof][rhs] complex.
  * Complex numbers     interleaved (re, im).
  * Gauge field         [mu][site][3][3] complex double (row-major SU(3)).
@@ -73,14 +73,14 @@ typedef enum {
 } mg_status;
 
 /* MG_I16: 16-bit fixed point (re, im) pairs, value = site scale * q / 32767,
- * the paper's "half" storage (Sec. III).                                 */
+ * the paper's "half" storage (Sec. 4).                                 */
 typedef enum { MG_F64 = 0, MG_F32 = 1, MG_BF16 = 2, MG_F16 = 3, MG_I16 = 4 } mg_prec;
 
 typedef struct mg_ctx mg_ctx;
 
 /* Problem and solver parameters.  Eq. (2): dims, mass m, csw, boundary;
- * Sec. II-D: blocks (aggregate extents), nvec (null vectors), setup
- * sweeps; Sec. VI-A: GCR Krylov size, MR smoother, inner tolerances.      */
+ * Sec. 3.4: blocks (aggregate extents), nvec (null vectors), setup
+ * sweeps; Sec. 7.1: GCR Krylov size, MR smoother, inner tolerances.      */
 typedef struct {
   int dims[4];                      /* fine lattice extents Lx, Ly, Lz, Lt          */
   int t_antiperiodic;               /* 1: antiperiodic fermion boundary in t        */
@@ -126,7 +126,7 @@ void mg_default_params(mg_params* p);
 mg_status mg_create(const mg_params* params, const void* gauge_dev, mg_ctx** out);
 mg_status mg_destroy(mg_ctx* ctx);
 
-/* Sec. II-D steps 1-3 for the coarsening level -> level+1: starting from
+/* Sec. 3.4 steps 1-3 for the coarsening level -> level+1: starting from
  * init_dev ([nvec][V_l][nd_l] complex double; NULL draws Gaussian x0 on the
  * device from params.seed) run setup_sweeps minimal-residual steps on
  * A_l x = 0 in the level's vector precision, normalise every vector, then
@@ -144,7 +144,7 @@ mg_status mg_set_nullvecs(mg_ctx* ctx, int level, const void* vecs_dev, void* st
 mg_status mg_get_nullvecs(mg_ctx* ctx, int level, int kind, void* dst_dev, size_t bytes,
                           void* stream);
 
-/* Sec. II-D step 4: Galerkin product P^dag A_l P of level l, stored as the
+/* Sec. 3.4 step 4: Galerkin product P^dag A_l P of level l, stored as the
  * nine blocks of Eq. (3) per coarse site of level l+1 (X and Y_{+-mu}),
  * in prec_coarse.  Requires the null vectors of level l.                   */
 mg_status mg_build_coarse(mg_ctx* ctx, int level, void* stream);
@@ -174,14 +174,14 @@ mg_status mg_apply(mg_ctx* ctx, int level, void* y_dev, const void* x_dev, void*
  * precision.                                                               */
 mg_status mg_wilson_clover_apply(mg_ctx* ctx, void* out_dev, const void* in_dev, void* stream);
 
-/* Sec. IV-F transfer operators between level l and l+1 (vector precision of
+/* Sec. 6.6 transfer operators between level l and l+1 (vector precision of
  * each level):  coarse = P^dag fine  (restrict),  fine = P coarse (prolong). */
 mg_status mg_restrict(mg_ctx* ctx, int level, void* coarse_dev, const void* fine_dev,
                       void* stream);
 mg_status mg_prolong(mg_ctx* ctx, int level, void* fine_dev, const void* coarse_dev,
                      void* stream);
 
-/* Sec. VI-A: flexible GCR on the fine level, preconditioned by the K-cycle,
+/* Sec. 7.1: flexible GCR on the fine level, preconditioned by the K-cycle,
  * to |b - M x| <= tol |b| (true residual, FP64).  x_dev, b_dev: fine
  * vectors, complex double.  Synchronises `stream` for convergence checks.
  * Returns MG_ERR_NOT_CONVERGED at maxiter (x holds the last iterate).      */
@@ -237,7 +237,7 @@ mg_status mg_profile_query(mg_ctx* ctx, const char* name, int level, int* launch
  * call tunes again); mg_tune_get returns the entry or -1.  The environment
  * variable GBMG_TUNE=0 turns timing off (first candidate) and
  * GBMG_TUNE_CACHE=<file> keeps choices across processes.  The paper's
- * autotuning of launch parameters (Sec. IV) is the model.                  */
+ * autotuning of launch parameters (Secs. 4 and 6) is the model.                  */
 mg_status mg_tune_set(const char* key, int choice);
 int mg_tune_get(const char* key);
 
@@ -269,7 +269,7 @@ mg_status mg_block_orthonormalise_noalloc(const void* vecs_dev, void* out_dev, c
 mg_status mg_set_setup_sweeps(mg_ctx* ctx, int sweeps);
 
 /* ---- Learned null-vector proposer.  The paper draws the setup's starting
- * vectors x0 at random (Sec. II-D step 1); this addition proposes them with
+ * vectors x0 at random (Sec. 3.4 step 1); this addition proposes them with
  * a three-layer network whose layers are nearest-neighbour stencils on the
  * lattice: 72 link features (Re, Im of U_mu(x)) -> 32 -> 32 (tanh) ->
  * 24 * nvec outputs = nvec complex 12-component vectors per site.  FP32

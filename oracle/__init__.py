@@ -13,12 +13,12 @@ reordering beyond what the definitions state:
 * ``dirac``     -- gamma matrices, clover term A_x, Wilson-clover operator
                    M of Eq. (2) as nine dense 12x12 blocks per site, and the
                    generic nearest-neighbour stencil apply (Eq. 2 / Eq. 3).
-* ``multigrid`` -- adaptive setup (Sec. II-D steps 1-3): null vectors by
+* ``multigrid`` -- adaptive setup (Sec. 3.4 steps 1-3): null vectors by
                    iterating M x = 0, chiral split, per-aggregate QR by
                    twice-repeated modified Gram-Schmidt; prolongator P,
                    restrictor R = P^dag; Galerkin coarse operator
                    P^dag M P (step 4) in the stencil form of Eq. (3).
-* ``solvers``   -- MR smoother, flexible GCR, K-cycle (Sec. VI-A).
+* ``solvers``   -- MR smoother, flexible GCR, K-cycle (Sec. 7.1).
 
 Every function names the passage it follows.  Where the paper is silent
 the reading used is stated in the docstring (gamma basis, projector

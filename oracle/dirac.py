@@ -4,10 +4,10 @@ Readings of passages where the paper is silent:
 
 * Gamma basis: DeGrand-Rossi chiral basis, gamma_5 = g1 g2 g3 g4 =
   diag(1, 1, -1, -1), so spins {0, 1} and {2, 3} are the two chiralities
-  that the footnote of Sec. II-D aggregates separately.
-* Projectors: P^{+-mu} = 1 +- gamma_mu ("projectors" in Sec. II-B up to the
+  that the footnote of Sec. 3.4 aggregates separately.
+* Projectors: P^{+-mu} = 1 +- gamma_mu ("projectors" in Sec. 3.2 up to the
   factor 2 that the -1/2 and the 4 + m diagonal of Eq. (2) require).
-* Clover term A_x (Sec. II-B names it, gives no formula): the
+* Clover term A_x (Sec. 3.2 names it, gives no formula): the
   Sheikholeslami-Wohlert form
       A_x = c_sw * (i/4) * sum_{mu != nu} sigma_{mu nu} (x) Fhat_{mu nu}(x),
       sigma_{mu nu} = (i/2) [gamma_mu, gamma_nu],

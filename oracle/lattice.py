@@ -1,4 +1,4 @@
-"""Lattice geometry for the oracle (Sec. IV-A: site index <-> coordinates).
+"""Lattice geometry for the oracle (Sec. 6.1: site index <-> coordinates).
 
 Site index s = x + Lx*(y + Ly*(z + Lz*t)); direction mu = 0..3 is x, y, z, t.
 Stencil slot d: 0 = the site itself, 1 + 2*mu = forward neighbour x + mu,

@@ -1,5 +1,5 @@
 """Learned null-vector proposer (oracle, FP64).  Not in the paper: an
-addition that proposes the random starting vectors x0 of Sec. II-D step 1.
+addition that proposes the random starting vectors x0 of Sec. 3.4 step 1.
 
 Network (every layer a nearest-neighbour stencil on the lattice, the
 "4D convolution" of this build):

@@ -1,6 +1,6 @@
 """Adaptive geometric multigrid setup and Galerkin coarse operator (oracle).
 
-Follows Sec. II-D, setup steps 1-4, and Eq. (3).
+Follows Sec. 3.4, setup steps 1-4, and Eq. (3).
 
 Readings of passages where the paper is silent or garbled:
 
@@ -36,7 +36,7 @@ class RankError(ValueError):
 
 # ------------------------------------------------------------- step 1, 2
 def null_vectors(op: StencilOp, x0: np.ndarray, sweeps: int) -> np.ndarray:
-    """Sec. II-D steps 1-2: from each random x0[i] run `sweeps` minimal-
+    """Sec. 3.4 steps 1-2: from each random x0[i] run `sweeps` minimal-
     residual steps on M x = 0, then normalise.  x0: [Nv][V][nd]."""
     out = []
     for x in np.asarray(x0, dtype=np.complex128):
@@ -84,7 +84,7 @@ def aggregate_blocks(vecs, dims, block, s):
 
 
 def block_orthonormalise(vecs: np.ndarray, dims, block) -> np.ndarray:
-    """Sec. II-D step 3 with the chiral split: returns Q [Nv][V][nd]; the
+    """Sec. 3.4 step 3 with the chiral split: returns Q [Nv][V][nd]; the
     prolongator column (s, i) is Q[i] restricted to chirality s."""
     vecs = np.asarray(vecs, dtype=np.complex128)
     nv, vol, nd = vecs.shape
@@ -156,7 +156,7 @@ def crosses_face(dims, block, d) -> np.ndarray:
 
 
 def galerkin(op: StencilOp, Q: np.ndarray, block) -> StencilOp:
-    """Sec. II-D step 4: M_hat = P^dag M P, as the nine blocks of Eq. (3).
+    """Sec. 3.4 step 4: M_hat = P^dag M P, as the nine blocks of Eq. (3).
 
     For every fine site x and slot d the term P(x)^dag B[x, d] P(x + d)
     is added to slot d of agg(x) if the hop crosses the aggregate face in

@@ -1,6 +1,6 @@
 """Krylov solvers and the K-cycle multigrid preconditioner (oracle).
 
-Sec. VI-A: three-level K-cycle; flexible GCR with a Krylov space of 10
+Sec. 7.1: three-level K-cycle; flexible GCR with a Krylov space of 10
 vectors on the fine and intermediate levels, preconditioned by the next
 level; 4 pre- and 4 post-smoothing steps of minimal residual (MR); GCR as
 the coarsest-grid solver.  Residual norms are L2 norms.

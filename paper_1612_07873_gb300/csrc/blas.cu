@@ -1,4 +1,4 @@
-// Level-1 vector kernels of the solvers (Sec. VI-A: GCR, MR, setup
+// Level-1 vector kernels of the solvers (Sec. 7.1: GCR, MR, setup
 // iteration).  Scalars stay on the device: a reduction writes one complex
 // double per right-hand side into a row of ctx->scalars and the following
 // update kernel reads it, so smoothers and orthogonalisation never wait on

@@ -1,6 +1,6 @@
 // Learned null-vector proposer: a three-layer nearest-neighbour-stencil
 // network (the "4D convolution" of this library) that maps the links around
-// a site to Nv starting vectors for the adaptive setup (Sec. II-D step 1
+// a site to Nv starting vectors for the adaptive setup (Sec. 3.4 step 1
 // draws them at random; the paper has no learned part).
 //
 //   f(x)  = (Re, Im) of U_mu(x)[a][b]                            72 channels

@@ -7,7 +7,7 @@
 // site: [slot][col][row] -- a column of n rows is contiguous -- so the 9n
 // "columns" of a site form one contiguous run of 9n*n complex numbers.
 //
-// Thread mapping of the streaming kernel (Sec. IV-B..E exposed differently):
+// Thread mapping of the streaming kernel (Secs. 6.1-6.4 exposed differently):
 //  * one CTA per coarse site;
 //  * a thread owns one 16-byte chunk of rows (RPC = 16 / sizeof(element)
 //    rows: 1 in FP64, 2 in FP32, 4 in 16-bit) -> TPC = n / RPC threads span a

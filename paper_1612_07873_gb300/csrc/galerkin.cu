@@ -1,4 +1,4 @@
-// Galerkin coarse operator, Sec. II-D step 4:  M_hat = P^dag M P, stored as
+// Galerkin coarse operator, Sec. 3.4 step 4:  M_hat = P^dag M P, stored as
 // the nine blocks of Eq. (3) per coarse site.
 //
 // For coarse site xc and slot d:

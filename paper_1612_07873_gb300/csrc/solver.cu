@@ -1,5 +1,5 @@
-// Adaptive setup iteration (Sec. II-D step 1) and the K-cycle multigrid
-// solver of Sec. VI-A: flexible GCR(nkrylov) on the fine and intermediate
+// Adaptive setup iteration (Sec. 3.4 step 1) and the K-cycle multigrid
+// solver of Sec. 7.1: flexible GCR(nkrylov) on the fine and intermediate
 // levels, preconditioned by the next level; MR pre/post smoothing; GCR on
 // the coarsest level.
 //

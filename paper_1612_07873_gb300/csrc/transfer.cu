@@ -1,5 +1,5 @@
-// Null-vector block orthonormalisation (Sec. II-D step 3 with the chiral
-// split of its footnote) and the transfer operators of Sec. IV-F.
+// Null-vector block orthonormalisation (Sec. 3.4 step 3 with the chiral
+// split of its footnote) and the transfer operators of Sec. 6.6.
 //
 // For aggregate A and chirality s the (|A| * nd/2) x Nv block of chirality-s
 // components is orthonormalised by modified Gram-Schmidt with every

@@ -10,7 +10,7 @@ numbers and shapes them into inputs.
   for them with the lattice shapes of the paper's workloads.
 * ``gaussian_field`` -- complex Gaussian fields (Re, Im iid N(0, 1)), used
   as the random initial null-vector guesses x0 of the adaptive setup
-  (Sec. II-D, step 1) and as right-hand sides.
+  (Sec. 3.4, step 1) and as right-hand sides.
 * ``WORKLOADS`` -- lattice sizes and solver parameters of the five
   workloads (small 2-level FP64, production-shaped 3-level FP32, 16-bit
   storage, multi-RHS, learned setup).
