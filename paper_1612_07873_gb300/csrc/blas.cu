@@ -68,7 +68,9 @@ using acc_t = typename std::conditional<std::is_same<Ra, float>::value &&
 // to back (rhs v at offset v * n); blockIdx.y is the right-hand side and
 // per-RHS scalars are read from a row S[v] of the scalar table.
 
-template <typename Ra, typename Rb, typename T>
+// NORM: a == b, only the real part |a|^2 is formed (half the multiply-adds,
+// which matters where they are FP64)
+template <typename Ra, typename Rb, typename T, bool NORM = false>
 __global__ void k_dot_partial(const cpx<Ra>* __restrict__ a, const cpx<Rb>* __restrict__ b,
                               size_t n, double2* __restrict__ part) {
   __shared__ double2 sh[32];
@@ -76,8 +78,14 @@ __global__ void k_dot_partial(const cpx<Ra>* __restrict__ a, const cpx<Rb>* __re
   b += size_t(blockIdx.y) * n;
   cpx<T> acc(T(0), T(0));
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
-       i += size_t(gridDim.x) * blockDim.x)
-    cmac_conj(acc, cpx<T>(a[i]), cpx<T>(b[i]));
+       i += size_t(gridDim.x) * blockDim.x) {
+    if constexpr (NORM) {
+      const cpx<T> x(a[i]);
+      acc.re = fma(x.re, x.re, fma(x.im, x.im, acc.re));
+    } else {
+      cmac_conj(acc, cpx<T>(a[i]), cpx<T>(b[i]));
+    }
+  }
   double2 d = block_sum(make_double2(double(acc.re), double(acc.im)), sh);
   if (threadIdx.x == 0) part[size_t(blockIdx.y) * gridDim.x + blockIdx.x] = d;
 }
@@ -449,7 +457,16 @@ void blas_dot(mg_ctx* c, Vec a, Vec b, int slot, cudaStream_t st, bool fp64_part
   const int nb = red_blocks(a.n);
   double2* part = partials(c, size_t(nb) * a.nr);
   const dim3 grid(nb, a.nr);
-  if (fp64_partials) {
+  const bool norm = a.p == b.p && a.prec == b.prec;
+  if (norm && fp64_partials) {
+    GB_DISPATCH1(a.prec, Ra,
+                 (k_dot_partial<Ra, Ra, double, true><<<grid, kThreads, 0, st>>>(
+                     (const cpx<Ra>*)a.p, (const cpx<Ra>*)a.p, a.n, part)));
+  } else if (norm) {
+    GB_DISPATCH1(a.prec, Ra,
+                 (k_dot_partial<Ra, Ra, acc_t<Ra, Ra>, true><<<grid, kThreads, 0, st>>>(
+                     (const cpx<Ra>*)a.p, (const cpx<Ra>*)a.p, a.n, part)));
+  } else if (fp64_partials) {
     GB_DISPATCH2(a.prec, Ra, b.prec, Rb,
                  (k_dot_partial<Ra, Rb, double><<<grid, kThreads, 0, st>>>(
                      (const cpx<Ra>*)a.p, (const cpx<Rb>*)b.p, a.n, part)));

@@ -12,6 +12,7 @@
 #include <mutex>
 
 #include "kernels.cuh"
+#include "tune.cuh"
 
 namespace gbmg {
 
@@ -91,12 +92,14 @@ __device__ __forceinline__ double2 blk_sum2(double2 v, double2* sh) {
 }
 
 // One CTA per (aggregate, chirality) block of `rows` x nv, in place, FP64.
-// Gram-Schmidt in column order with every projection step done twice.  The
-// projection of column i on the finished columns 0..i-1 is formed as one
-// classical step (all i coefficients reduced together) rather than i
-// sequential ones: the same Q in exact arithmetic, and with the second pass
-// as stable as the modified form, but with ~8 block barriers per column
-// instead of ~4i.
+// Gram-Schmidt in column order.  The projection of column i on the finished
+// columns 0..i-1 is formed as one classical step (all i coefficients reduced
+// together) rather than i sequential ones: the same Q in exact arithmetic,
+// with ~8 block barriers per column instead of ~4i.  The projection is
+// repeated ("twice is enough") when the first one removed more than half of
+// the column's squared norm (the Kahan-Parlett / Daniel-Gragg-Kaufman-
+// Stewart criterion, |v'| < |v| / sqrt 2); otherwise one pass already leaves
+// the column orthogonal to the others to working precision.
 constexpr int kQrMaxVec = 64;
 constexpr int kQrMaxWarps = 32;
 
@@ -121,6 +124,13 @@ __global__ void k_block_qr(double2* __restrict__ W, int rows, int nv, int* statu
     for (int r = 0; r < RPT; ++r) {
       int row = threadIdx.x + r * T;
       v[r] = row < rows ? B[size_t(i) * rows + row] : make_double2(0.0, 0.0);
+    }
+    double n0 = 0.0;  // squared norm before the first projection
+    if (i > 0) {
+      double2 nn0 = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) nn0.x += v[r].x * v[r].x + v[r].y * v[r].y;
+      n0 = blk_sum2(nn0, sh).x;
     }
     for (int pass = 0; pass < 2 && i > 0; ++pass) {
       for (int j = 0; j < i; ++j) {
@@ -171,6 +181,13 @@ __global__ void k_block_qr(double2* __restrict__ W, int rows, int nv, int* statu
         }
       }
       __syncthreads();  // coef / part are rewritten by the next pass
+      if (pass == 0) {
+        double2 nn1 = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) nn1.x += v[r].x * v[r].x + v[r].y * v[r].y;
+        // the same value in every thread: the whole CTA takes the same branch
+        if (blk_sum2(nn1, sh).x >= 0.5 * n0) break;
+      }
     }
     double2 nn = make_double2(0.0, 0.0);
 #pragma unroll
@@ -397,7 +414,9 @@ __global__ void __launch_bounds__(256) k_restrict12(cpx<Rc>* __restrict__ coarse
 
 // fine_v[x][a] = sum_i Vp[x][a][i] coarse_v[agg(x)][chi(a)*Nv + i] for all nr
 // right-hand sides.  Two threads per Vp row, each holding half of it in
-// registers for every right-hand side; the halves meet by one shuffle.
+// registers for every right-hand side: thread q takes the 16-byte words
+// 2k + q, so a pair reads whole 32-byte sectors; the halves meet by one
+// shuffle.
 template <typename Rf, typename Rc>
 __global__ void __launch_bounds__(256) k_prolong12(cpx<Rf>* __restrict__ fine,
                                                   const cpx<Rc>* __restrict__ coarse,
@@ -427,12 +446,12 @@ __global__ void __launch_bounds__(256) k_prolong12(cpx<Rf>* __restrict__ fine,
     const bool ok = r < rows;
     const int ls = ok ? r / ND : 0, a = ok ? r - ls * ND : 0;
     const size_t x = base + off[ls];
-    const uint4* vr = reinterpret_cast<const uint4*>(Vp + (x * ND + a) * nv) + q * PW;
+    const uint4* vr = reinterpret_cast<const uint4*>(Vp + (x * ND + a) * nv) + q;
     uint4 w[MAXPW];
 #pragma unroll
     for (int k = 0; k < MAXPW; ++k)
-      if (ok && k < PW) w[k] = ld_stream16(vr + k);
-    const int coff = (a < ND / 2 ? 0 : nv) + q * PW * CPL;
+      if (ok && k < PW) w[k] = ld_stream16(vr + 2 * k);
+    const int coff = (a < ND / 2 ? 0 : nv) + q * CPL;
     for (int b = 0; b < nr; ++b) {
       const cpx<Rf>* c = cs + b * 2 * nv + coff;
       cpx<Rf> acc(Rf(0), Rf(0));
@@ -441,7 +460,7 @@ __global__ void __launch_bounds__(256) k_prolong12(cpx<Rf>* __restrict__ fine,
         if (ok && k < PW) {
           const cpx<Rf>* v = reinterpret_cast<const cpx<Rf>*>(&w[k]);
 #pragma unroll
-          for (int j = 0; j < CPL; ++j) cmac(acc, v[j], c[k * CPL + j]);
+          for (int j = 0; j < CPL; ++j) cmac(acc, v[j], c[2 * k * CPL + j]);
         }
       acc.re += __shfl_xor_sync(0xffffffffu, acc.re, 1);
       acc.im += __shfl_xor_sync(0xffffffffu, acc.im, 1);
@@ -591,12 +610,22 @@ void restrict_apply(mg_ctx* c, int level, Vec coarse, Vec fine, cudaStream_t st)
     // takes the generic kernel
     const bool aligned = (reinterpret_cast<uintptr_t>(fine.p) & 15) == 0;
     if (aligned && nv % cpl == 0 && G2 >= 1 && smem2 <= 48 * 1024) {
-      const int nrb = nr % 8 == 0 ? 8 : nr % 4 == 0 ? 4 : nr % 2 == 0 ? 2 : 1;
-      const int nchunk = nr / nrb;
-      const dim3 grid(unsigned(C.g.vol) * nchunk);
-      GB_TRANSFER_DISPATCH(F.vprec, coarse.prec, Rf, Rc,
-                           (launch_restrict12<Rf, Rc>(nrb, grid, G2 * NP, smem2, st, coarse, fine,
-                                                      F.Vp.p, m, nv, G2, nchunk)));
+      // right-hand sides per CTA: the autotuner weighs Vp reuse against the
+      // registers of the accumulators
+      std::vector<int> cands;
+      for (int q : {8, 4, 2, 1})
+        if (nr % q == 0) cands.push_back(q);
+      auto launch = [&](int nrb) {
+        const int nchunk = nr / nrb;
+        const dim3 grid(unsigned(C.g.vol) * nchunk);
+        GB_TRANSFER_DISPATCH(F.vprec, coarse.prec, Rf, Rc,
+                             (launch_restrict12<Rf, Rc>(nrb, grid, G2 * NP, smem2, st, coarse,
+                                                        fine, F.Vp.p, m, nv, G2, nchunk)));
+      };
+      const std::string key = "restrict12/p" + std::to_string(int(F.vprec)) + "/v" +
+                              std::to_string(F.g.vol) + "/nv" + std::to_string(nv) + "/r" +
+                              std::to_string(nr);
+      launch(Tuner::get().choose(key, cands, st, launch));
       GB_LAUNCH_CHECK();
       c->launches++;
       return;

@@ -189,16 +189,27 @@ __global__ void k_clover(const cpx<double>* __restrict__ U, Geom g, double csw,
 // C12: links in the two-row form (16-byte loads, 48 B per FP32 link) with
 // the third row rebuilt in registers; the rebuilt row carries the boundary
 // sign of the link (t-links leaving the last time slice).
-template <typename R, bool C12, int MINB>
+// Several vectors (nvec > 1, stored vstride apart):
+//  * VIW = false: CTAs ordered vector-fastest, so the nvec CTAs of one site
+//    chunk run close together and the chunk's links and clover come from
+//    DRAM once and from L2 for the other vectors;
+//  * VIW = true: thread g works on site g / nvec, vector g % nvec, so the
+//    vectors of a site sit in neighbouring lanes and one load instruction
+//    serves the site's link or clover word to all of them.
+template <typename R, bool C12, int MINB, bool VIW = false>
 __global__ void __launch_bounds__(128, MINB) k_wilson(cpx<R>* __restrict__ out, const cpx<R>* __restrict__ in,
                                                 const cpx<R>* __restrict__ U, const R* __restrict__ A,
                                                 Geom g, R diag, size_t vstride, int nvec,
                                                 int antiperiodic) {
-  // CTAs are ordered vector-fastest: the nvec CTAs of one site chunk run
-  // close together, so the chunk's links and clover come from DRAM once and
-  // from L2 for the other vectors.
-  const int vec = blockIdx.x % nvec;
-  int s = (blockIdx.x / nvec) * blockDim.x + threadIdx.x;
+  int vec, s;
+  if constexpr (VIW) {
+    const size_t gi = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    s = int(gi / size_t(nvec));
+    vec = int(gi - size_t(s) * nvec);
+  } else {
+    vec = blockIdx.x % nvec;
+    s = (blockIdx.x / nvec) * blockDim.x + threadIdx.x;
+  }
   if (s >= g.vol) return;
   in += vec * vstride;
   out += vec * vstride;
@@ -401,11 +412,13 @@ void wilson_apply(mg_ctx* c, Vec out, Vec in, int nvec, cudaStream_t st) {
       double(L.g.vol) * (48.0 * nvec + 144.0) * (out.prec == MG_F64 ? 8 : 4);
   ProfScope ps(c->prof, st, "wilson_clover", 0, bytes, double(nvec) * L.g.vol * 1824.0);
   if (out.prec == MG_F32) {
-    // FP32: the autotuner picks one launch policy from kPolicies: vectors
-    // per thread (1, 2, 4: more reuse of the links and clover against fewer
-    // resident warps), link form (two-row links rebuilt in registers, when
-    // the field allows it) and register budget (minimum CTAs per SM given
-    // to the compiler; 0 = its default).
+    // FP32: the autotuner picks one launch policy q:
+    //   0 / 1   one vector per thread, stored / two-row links, default registers
+    //   2 .. 5  the same with a register budget (minimum CTAs per SM 2, 2, 4, 6)
+    //   6 / 7   2 / 4 vectors per thread (links and clover reused in registers)
+    //   8 .. 10 the vectors of a site in neighbouring lanes (stored links;
+    //           two-row links; two-row links with 4 CTAs per SM)
+    // Two-row policies are candidates only when the field allows them.
     GB_REQUIRE(L.gauge32.p, MG_ERR_STATE, "FP32 fine operator not built");
     const unsigned gx = ceil_div(L.g.vol, 128);
     const int ap = c->p.t_antiperiodic;
@@ -415,6 +428,7 @@ void wilson_apply(mg_ctx* c, Vec out, Vec in, int nvec, cudaStream_t st) {
     auto* o = (cpx<float>*)out.p;
     auto* i = (const cpx<float>*)in.p;
     const float dg = float(L.diag);
+    const unsigned gv = ceil_div(size_t(L.g.vol) * nvec, 128);
     auto launch = [&](int q) {
       switch (q) {
         case 1: k_wilson<float, true, 0><<<grid, 128, 0, st>>>(o, i, U12, A, L.g, dg, vs, nvec, ap); break;
@@ -424,6 +438,9 @@ void wilson_apply(mg_ctx* c, Vec out, Vec in, int nvec, cudaStream_t st) {
         case 5: k_wilson<float, true, 6><<<grid, 128, 0, st>>>(o, i, U12, A, L.g, dg, vs, nvec, ap); break;
         case 6: k_wilson_mv<float, 2><<<dim3(gx, nvec / 2), 128, 0, st>>>(o, i, U18, A, L.g, dg, vs); break;
         case 7: k_wilson_mv<float, 4><<<dim3(gx, nvec / 4), 128, 0, st>>>(o, i, U18, A, L.g, dg, vs); break;
+        case 8: k_wilson<float, false, 0, true><<<gv, 128, 0, st>>>(o, i, U18, A, L.g, dg, vs, nvec, ap); break;
+        case 9: k_wilson<float, true, 0, true><<<gv, 128, 0, st>>>(o, i, U12, A, L.g, dg, vs, nvec, ap); break;
+        case 10: k_wilson<float, true, 4, true><<<gv, 128, 0, st>>>(o, i, U12, A, L.g, dg, vs, nvec, ap); break;
         default: k_wilson<float, false, 0><<<grid, 128, 0, st>>>(o, i, U18, A, L.g, dg, vs, nvec, ap); break;
       }
     };
@@ -431,6 +448,10 @@ void wilson_apply(mg_ctx* c, Vec out, Vec in, int nvec, cudaStream_t st) {
     if (L.gauge12_ok) cands.insert(cands.end(), {1, 3, 4, 5});
     if (nvec % 2 == 0) cands.push_back(6);
     if (nvec % 4 == 0) cands.push_back(7);
+    if (nvec > 1) {
+      cands.push_back(8);
+      if (L.gauge12_ok) cands.insert(cands.end(), {9, 10});
+    }
     const std::string key = "wilson/v" + std::to_string(L.g.vol) + "/n" + std::to_string(nvec) +
                             "/c" + std::to_string(int(L.gauge12_ok));
     launch(Tuner::get().choose(key, cands, st, launch));

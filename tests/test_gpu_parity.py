@@ -126,6 +126,22 @@ def test_block_orthonormalise(gpu_lib, dims, block, nv):
     mg.close()
 
 
+def test_block_orthonormalise_nearly_parallel_columns(gpu_lib):
+    """Columns that differ by 1e-3 relative: the first projection removes
+    almost all of their norm, so the second pass runs (and must)."""
+    gb = gpu_lib
+    dims, block, nv = (4, 4, 4, 4), (2, 2, 2, 2), 6
+    mg, U = make_ctx(gb, dims, [block], [nv])
+    base = syn.gaussian_field((1, lat.volume(dims), 12), 28)
+    v = base + 1e-3 * syn.gaussian_field((nv, lat.volume(dims), 12), 29)
+    gb.mg_set_nullvecs(mg.ctx, 0, to_dev(v))
+    out = torch.empty((nv, lat.volume(dims), 12), dtype=torch.complex128, device="cuda")
+    gb.mg_get_nullvecs(mg.ctx, 0, out, kind=1)
+    torch.cuda.synchronize()
+    assert rel_l2(to_np(out), mgo.block_orthonormalise(v, dims, block)) < 1e-12
+    mg.close()
+
+
 def test_rank_deficient_block_is_reported(gpu_lib):
     gb = gpu_lib
     dims, nv = (4, 4, 4, 4), 3

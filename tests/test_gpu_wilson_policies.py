@@ -3,8 +3,9 @@
 The autotuner picks one policy per shape; here each policy is pinned in turn
 through mg_tune_set: stored 18-real links or two-row links rebuilt in
 registers (third row = conj(row0 x row1) times the boundary sign), four
-register budgets, and 2 or 4 vectors per thread in the batched form used by
-the setup sweeps.  A field that is not special unitary must never take the
+register budgets, and, in the batched form used by the setup sweeps and the
+multi-RHS solve, 2 or 4 vectors per thread or the vectors of a site in
+neighbouring lanes.  A field that is not special unitary must never take the
 two-row form.
 """
 import numpy as np
@@ -18,7 +19,7 @@ from gpu_helpers import make_ctx, oracle_fine, rel_l2, to_dev, to_np
 pytestmark = pytest.mark.gpu
 
 SINGLE = [0, 1, 2, 3, 4, 5]   # 1 vector per thread: (link form, register budget)
-BATCHED = [6, 7]              # 2 or 4 vectors per thread
+BATCHED = [6, 7, 8, 9, 10]    # 2 or 4 vectors per thread; vectors of a site in neighbouring lanes
 
 
 @pytest.mark.parametrize("antiperiodic", [1, 0])
