@@ -19,10 +19,14 @@ reordering beyond what the definitions state:
                    restrictor R = P^dag; Galerkin coarse operator
                    P^dag M P (step 4) in the stencil form of Eq. (3).
 * ``solvers``   -- MR smoother, flexible GCR, K-cycle (Sec. 7.1).
+* ``schur``     -- red-black (Schur complement) preconditioning of any
+                   level's operator (Secs. 3.3, 7.1).
+* ``learned``   -- the learned null-vector proposer (an addition, not in
+                   the paper).
 
 Every function names the passage it follows.  Where the paper is silent
 the reading used is stated in the docstring (gamma basis, projector
 normalisation, clover formula, the setup iteration, the coarse diagonal
 and the solver tolerances).
 """
-from . import lattice, dirac, multigrid, solvers  # noqa: F401
+from . import lattice, dirac, multigrid, solvers, schur  # noqa: F401

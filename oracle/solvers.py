@@ -13,6 +13,10 @@ Readings of what the paper does not state:
   normalised directions with modified Gram-Schmidt; after every cycle of
   nkrylov steps (or on meeting the tolerance) the true residual b - A x is
   recomputed and the cycle restarts, unless maxiter is reached.
+* Red-black preconditioning (MGParams.schur): the smoother of every level
+  runs MR on the Schur complement and reconstructs, and the coarsest GCR
+  solves the Schur system (see ``schur``); the outer GCR keeps the full
+  fine operator.
 """
 from __future__ import annotations
 
@@ -21,6 +25,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import multigrid as mgo
+from . import schur as rb
 from .dirac import StencilOp
 
 
@@ -100,6 +105,7 @@ class MGParams:
     inner_maxiter: int = 10
     coarse_tol: float = 0.1
     coarse_maxiter: int = 100
+    schur: bool = False
 
 
 class MultigridHierarchy:
@@ -113,6 +119,8 @@ class MultigridHierarchy:
         self.blocks = [tuple(b) for b in blocks]
         self.p = params or MGParams()
         self.inner_iters = [0] * len(self.ops)
+        self.S = [rb.SchurOp(op) if self.p.schur and rb.supported(op.dims) else None
+                  for op in self.ops]
 
     @classmethod
     def build(cls, fine: StencilOp, x0s, sweeps, blocks, params=None):
@@ -133,17 +141,32 @@ class MultigridHierarchy:
         p = self.p
         A = self.ops[level].apply
         dims, blk, Q = self.ops[level].dims, self.blocks[level], self.Qs[level]
-        x = mr(A, r, p.mr_iters, p.mr_omega)
+        S = self.S[level]
+        if S is None:
+            smooth = lambda v: mr(A, v, p.mr_iters, p.mr_omega)  # noqa: E731
+        else:
+            smooth = lambda v: S.reconstruct(v, mr(S.apply, S.source(v), p.mr_iters,  # noqa: E731
+                                                   p.mr_omega))
+        x = smooth(r)
         rc = mgo.restrict(Q, r - A(x), dims, blk)
         nxt = level + 1
         if nxt == len(self.ops) - 1:
-            res = fgcr(self.ops[nxt].apply, rc, None, p.coarse_tol, p.coarse_maxiter, p.nkrylov)
+            Sc = self.S[nxt]
+            if Sc is None:
+                res = fgcr(self.ops[nxt].apply, rc, None, p.coarse_tol, p.coarse_maxiter,
+                           p.nkrylov)
+                xc = res.x
+            else:
+                res = fgcr(Sc.apply, Sc.source(rc), None, p.coarse_tol, p.coarse_maxiter,
+                           p.nkrylov)
+                xc = Sc.reconstruct(rc, res.x)
         else:
             res = fgcr(self.ops[nxt].apply, rc, lambda v: self.kcycle(nxt, v),
                        p.inner_tol, p.inner_maxiter, p.nkrylov)
+            xc = res.x
         self.inner_iters[nxt] += res.iters
-        x = x + mgo.prolong(Q, res.x, dims, blk)
-        x = x + mr(A, r - A(x), p.mr_iters, p.mr_omega)
+        x = x + mgo.prolong(Q, xc, dims, blk)
+        x = x + smooth(r - A(x))
         return x
 
     def solve(self, b, tol: float = 1e-10, maxiter: int = 200) -> GCRResult:

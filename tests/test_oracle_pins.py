@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import synthetic as syn
-from oracle import dirac, lattice as lat, multigrid as mgo, solvers
+from oracle import dirac, lattice as lat, multigrid as mgo, schur as rb, solvers
 
 RNG = np.random.default_rng(1234)
 
@@ -285,6 +285,74 @@ def test_three_level_mg_converges():
     b = syn.gaussian_field((vol, 12), 64)
     res = mg.solve(b, 1e-10, 100)
     assert res.true_residual <= 1e-10
+
+
+# ------------------------------------------------------------ red-black (Schur)
+def test_schur_solve_reconstructs_the_full_solution():
+    """S x_o = b^ plus x_e = A_e^-1 (b_e - H_eo x_o) solves M x = b: compared
+    with a dense direct solve of the full system (Secs. 3.3, 7.1)."""
+    dims = (4, 2, 2, 4)
+    U = syn.gauge_field(dims, 0.4, 81)
+    op = dirac.wilson_clover_op(U, dims, -0.2, 1.0, True)
+    S = rb.SchurOp(op)
+    b = syn.gaussian_field((lat.volume(dims), 12), 82)
+    x_o = np.linalg.solve(S.dense(), S.source(b).ravel()).reshape(-1, 12)
+    x = S.reconstruct(b, x_o)
+    want = np.linalg.solve(op.dense(), b.ravel()).reshape(x.shape)
+    assert np.abs(x - want).max() < 1e-12 * np.abs(want).max()
+
+
+def test_schur_determinant_identity():
+    """det M = det A_e * det S (block elimination), on a coarse operator."""
+    dims, block = (4, 4, 4, 4), (2, 2, 2, 2)
+    U, op, Q, cop = _hierarchy(dims, block, 2)
+    S = rb.SchurOp(cop)
+    s_full, l_full = np.linalg.slogdet(cop.dense())
+    s_s, l_s = np.linalg.slogdet(S.dense())
+    s_a, l_a = np.linalg.slogdet(cop.blocks[S.e, 0])
+    assert abs(l_full - (l_s + l_a.sum())) < 1e-9 * abs(l_full)
+    assert abs(s_full - s_s * np.prod(s_a)) < 1e-9
+
+
+def test_schur_gamma5_hermiticity_coarse():
+    """The coarse Schur operator inherits g5hat-hermiticity from Eq. (3)."""
+    dims, block = (4, 4, 4, 4), (2, 2, 2, 2)
+    U, op, Q, cop = _hierarchy(dims, block, 3)
+    S = rb.SchurOp(cop)
+    g5c = mgo.gamma5_hat(cop.nd)
+    u, v = _rand((len(S.o), cop.nd)), _rand((len(S.o), cop.nd))
+    lhs = np.vdot(g5c * S.apply(g5c * u), v)
+    assert abs(lhs - np.vdot(u, S.apply(v))) < 1e-12 * abs(lhs)
+
+
+def test_compact_parity_index():
+    """Compact parity order: site x of parity p at h = x >> 1, each pair of
+    sites (2h, 2h + 1) holding one site of each parity."""
+    dims = (4, 2, 6, 2)
+    par = rb.parity(dims)
+    for p in (0, 1):
+        sites = rb.half_sites(dims, p)
+        assert np.array_equal(sites >> 1, np.arange(lat.volume(dims) // 2))
+        assert np.all(par[sites] == p)
+    # every hop joins the two parities
+    assert np.all(par[lat.neighbours(dims)[:, 1:]] != par[:, None])
+
+
+def test_three_level_mg_with_red_black_smoothing_converges():
+    dims = (8, 4, 4, 8)
+    U = syn.gauge_field(dims, 0.3, 61)
+    op = dirac.wilson_clover_op(U, dims, -0.2, 1.0, True)
+    vol = lat.volume(dims)
+    x0a = syn.gaussian_field((6, vol, 12), 62)
+    x0b = syn.gaussian_field((8, vol // 16, 12), 63)
+    plain = solvers.MultigridHierarchy.build(op, [x0a, x0b], 6, [(2, 2, 2, 2), (2, 1, 1, 2)])
+    rbp = solvers.MultigridHierarchy(plain.ops, plain.Qs, plain.blocks,
+                                     solvers.MGParams(schur=True))
+    assert all(S is not None for S in rbp.S)
+    b = syn.gaussian_field((vol, 12), 64)
+    res = rbp.solve(b, 1e-10, 100)
+    assert res.true_residual <= 1e-10
+    assert res.iters <= plain.solve(b, 1e-10, 100).iters
 
 
 # ------------------------------------------------------------ learned proposer
