@@ -377,15 +377,19 @@ def gpu_main(args):
     forms = {}
     if args.forms:
         mg.close()
-        for fname, pc, slots, nr in (("bf16", 2, 9, 1), ("fp16", 3, 9, 1), ("int16", 4, 9, 1),
-                                     ("fp32_5blocks", 1, 5, 1), ("bf16_5blocks", 2, 5, 1),
-                                     ("fp32_mrhs8", 1, 9, 8), ("bf16_mrhs8", 2, 9, 8)):
+        for fname, pc, slots, nr, rbp in (
+                ("bf16", 2, 9, 1, 0), ("fp16", 3, 9, 1, 0), ("int16", 4, 9, 1, 0),
+                ("fp32_5blocks", 1, 5, 1, 0), ("bf16_5blocks", 2, 5, 1, 0),
+                ("fp32_mrhs8", 1, 9, 8, 0), ("bf16_mrhs8", 2, 9, 8, 0),
+                ("fp32_redblack", 1, 9, 1, 1), ("bf16_redblack", 2, 9, 1, 1),
+                ("bf16_redblack_mrhs8", 2, 9, 8, 1)):
             if fname == form:
                 continue
             pf = gb.default_params(dims=dims, block=blocks, nvec=nvecs, mass=w["mass"],
                                    csw=w["csw"], nlevels=3, prec_fine=1, prec_coarse=pc,
                                    setup_sweeps=w["sweeps"], t_antiperiodic=w["antiperiodic"],
-                                   seed=w["seed"] + 1000 * rank, link_slots=slots)
+                                   seed=w["seed"] + 1000 * rank, link_slots=slots,
+                                   red_black=rbp)
             mf = gb.Multigrid(pf, gauge_dev)
             t0 = ev()
             t1 = ev()
@@ -403,6 +407,7 @@ def gpu_main(args):
                 forms[fname] = {
                     "s_per_solve_median": statistics.median(st["seconds"] for st in sts),
                     "outer_iters": [st["iters"] for st in sts],
+                    "level_iters": sts[-1]["level_iters"],
                     "true_residual": max(st["true_residual"] for st in sts),
                     "setup_ms": t0.elapsed_time(t1)}
             else:

@@ -103,6 +103,11 @@ typedef struct {
   int link_slots;                   /* coarse link store: 9 (all blocks of Eq. 3) or
                                        5 (X and Y_{+mu}; Y_{-mu}(x) is rebuilt as
                                        g5 Y_{+mu}(x-mu)^dag g5 inside the apply) */
+  int red_black;                    /* 1: red-black (Schur complement) preconditioning
+                                       on every level with all extents even (Secs.
+                                       3.3, 7.1): MR smoothing on the Schur system
+                                       S = A_o - H_oe A_e^-1 H_eo and the coarsest
+                                       GCR on S; 0: off (default)                  */
 } mg_params;
 
 typedef struct {
@@ -202,6 +207,14 @@ mg_status mg_gcr_solve(mg_ctx* ctx, void* x_dev, const void* b_dev, double tol, 
  * vectors per right-hand side).                                            */
 mg_status mg_gcr_solve_multi(mg_ctx* ctx, void* x_dev, const void* b_dev, int nrhs, double tol,
                              int maxiter, mg_solve_stats* stats, void* stream);
+
+/* Red-black preconditioning (Secs. 3.3, 7.1; params.red_black = 1, every
+ * extent of the level even): y_o = S x_o with S = A_o - H_oe A_e^-1 H_eo the
+ * Schur complement of level l's operator on the odd sites.  Compact parity
+ * vectors: the odd site s is entry s >> 1, [nrhs][V/2][ndof] in the level's
+ * vector precision.  MG_ERR_STATE if the level has no red-black form.      */
+mg_status mg_schur_apply(mg_ctx* ctx, int level, void* y_dev, const void* x_dev, int nrhs,
+                         void* stream);
 
 /* Coarse links of level l >= 1 in the external layout (see top), complex
  * double, bytes = V_l * 9 * n_l^2 * 16.  set replaces the operator of the

@@ -48,6 +48,7 @@ class mg_params(C.Structure):
         ("coarse_tol", C.c_double),
         ("coarse_maxiter", C.c_int),
         ("link_slots", C.c_int),
+        ("red_black", C.c_int),
     ]
 
 
@@ -86,6 +87,7 @@ def _load():
         "mg_gcr_solve": (i, [vp, vp, vp, d, i, C.POINTER(mg_solve_stats), vp]),
         "mg_gcr_solve_multi": (i, [vp, vp, vp, i, d, i, C.POINTER(mg_solve_stats), vp]),
         "mg_tune_set": (i, [C.c_char_p, i]),
+        "mg_schur_apply": (i, [vp, i, vp, vp, i, vp]),
         "mg_tune_get": (i, [C.c_char_p]),
         "mg_get_coarse_links": (i, [vp, i, vp, sz, vp]),
         "mg_set_coarse_links": (i, [vp, i, vp, sz, vp]),
@@ -238,6 +240,11 @@ def mg_gcr_solve_multi(ctx, x, b, nrhs, tol=1e-10, maxiter=200, stream=None, che
     return [dict(status=st, iters=s.iters, restarts=s.restarts,
                  level_iters=list(s.level_iters), true_residual=s.true_residual,
                  seconds=s.seconds, history=list(s.history[:s.history_len])) for s in recs]
+
+
+def mg_schur_apply(ctx, level, y, x, nrhs=1, stream=None):
+    """y_o = S x_o on compact odd-parity vectors [nrhs][V/2][ndof]."""
+    _ok(LIB.mg_schur_apply(ctx, level, _ptr(y), _ptr(x), nrhs, _stream(stream)), ctx)
 
 
 def mg_tune_set(key, choice):

@@ -105,6 +105,7 @@ void mg_default_params(mg_params* p) {
   p->coarse_tol = 0.1;
   p->coarse_maxiter = 100;
   p->link_slots = 9;
+  p->red_black = 0;
 }
 
 mg_status mg_create(const mg_params* p, const void* gauge_dev, mg_ctx** out) {
@@ -173,6 +174,7 @@ mg_status mg_create(const mg_params* p, const void* gauge_dev, mg_ctx** out) {
     GB_CHECK(cudaMemset(c->scalars.p, 0, c->scalars.bytes));
     GB_CHECK(cudaMemset(c->status.p, 0, c->status.bytes));
     fine_operator_build(c, gauge_dev, 0);
+    if (p->red_black) schur_prepare(c, 0, 0);
     GB_CHECK(cudaDeviceSynchronize());
   } catch (const Error& e) {
     delete c;
@@ -235,6 +237,7 @@ mg_status mg_build_coarse(mg_ctx* c, int level, void* stream) {
   return guarded(c, [&] {
     check_level(c, level, 0, c->nlevels - 2);
     galerkin_build(c, level, S(stream));
+    if (c->p.red_black) schur_prepare(c, level + 1, S(stream));
   });
 }
 
@@ -316,6 +319,28 @@ mg_status mg_tune_set(const char* key, int choice) {
 
 int mg_tune_get(const char* key) { return key ? gbmg::Tuner::get().get(key) : -1; }
 
+mg_status mg_schur_apply(mg_ctx* c, int level, void* y, const void* x, int nrhs, void* stream) {
+  return guarded(c, [&] {
+    check_level(c, level, 0, c->nlevels - 1);
+    Level& L = c->L[level];
+    GB_REQUIRE(x && y && x != y, MG_ERR_ARG, "schur_apply: bad vectors");
+    GB_REQUIRE(nrhs >= 1 && nrhs <= MG_MAX_NRHS, MG_ERR_ARG, "schur_apply: bad nrhs");
+    GB_REQUIRE(L.have_schur, MG_ERR_STATE, "schur_apply: level has no red-black form");
+    Vec vx, vy, vt;
+    vx.p = const_cast<void*>(x);
+    vy.p = y;
+    vx.prec = vy.prec = vt.prec = L.vprec;
+    vx.n = vy.n = vt.n = L.vec_elems() / 2;
+    vx.nr = vy.nr = vt.nr = nrhs;
+    DevBuf tmp;
+    tmp.alloc(L.vec_bytes() / 2 * nrhs);
+    vt.p = tmp.p;
+    eo_apply(c, level, EO_AINV_HOP, vt, vx, nullptr, 0, S(stream));
+    eo_apply(c, level, EO_A_XC_MINUS_HOP, vy, vt, x, 1, S(stream));
+    GB_CHECK(cudaStreamSynchronize(S(stream)));
+  });
+}
+
 mg_status mg_get_coarse_links(mg_ctx* c, int level, void* dst, size_t bytes, void* stream) {
   return guarded(c, [&] {
     check_level(c, level, 1, c->nlevels - 1);
@@ -333,6 +358,7 @@ mg_status mg_set_coarse_links(mg_ctx* c, int level, const void* src, size_t byte
     GB_REQUIRE(src && bytes == size_t(L.g.vol) * 9 * L.nd * L.nd * 16, MG_ERR_ARG,
                "set_coarse_links: size mismatch");
     links_import(c, level, src, S(stream));
+    if (c->p.red_black) schur_prepare(c, level, S(stream));
   });
 }
 

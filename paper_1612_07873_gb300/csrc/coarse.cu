@@ -20,72 +20,13 @@
 // arithmetic accumulates in FP32.
 #include <type_traits>
 
+#include "coarse_ops.cuh"
 #include "kernels.cuh"
 #include "tune.cuh"
 
 namespace gbmg {
 
 namespace {
-
-template <typename S>
-struct Unpack;
-template <>
-struct Unpack<cpx<double>> {
-  static constexpr int RPC = 1;
-  __device__ static __forceinline__ void get(uint4 v, cpx<double> out[1]) {
-    out[0] = cpx<double>(__hiloint2double(int(v.y), int(v.x)), __hiloint2double(int(v.w), int(v.z)));
-  }
-};
-template <>
-struct Unpack<cpx<float>> {
-  static constexpr int RPC = 2;
-  __device__ static __forceinline__ void get(uint4 v, cpx<float> out[2]) {
-    out[0] = cpx<float>(__uint_as_float(v.x), __uint_as_float(v.y));
-    out[1] = cpx<float>(__uint_as_float(v.z), __uint_as_float(v.w));
-  }
-};
-template <>
-struct Unpack<bf16c> {
-  static constexpr int RPC = 4;
-  __device__ static __forceinline__ void get(uint4 v, cpx<float> out[4]) {
-    uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      out[i] = cpx<float>(__uint_as_float(w[i] << 16), __uint_as_float(w[i] & 0xffff0000u));
-    }
-  }
-};
-template <>
-struct Unpack<f16c> {
-  static constexpr int RPC = 4;
-  __device__ static __forceinline__ void get(uint4 v, cpx<float> out[4]) {
-    uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      __half2 h = *reinterpret_cast<__half2*>(&w[i]);
-      float2 f = __half22float2(h);
-      out[i] = cpx<float>(f.x, f.y);
-    }
-  }
-};
-
-template <>
-struct Unpack<i16c> {
-  static constexpr int RPC = 4;
-  __device__ static __forceinline__ void get(uint4 v, cpx<float> out[4]) {
-    uint32_t w[4] = {v.x, v.y, v.z, v.w};
-    const float s = 1.f / 32767.f;
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-      out[i] = cpx<float>(float(short(w[i] & 0xffffu)) * s, float(short(w[i] >> 16)) * s);
-  }
-};
-
-constexpr int batch_of(int iters, int umax = 8) {
-  for (int u = umax; u > 1; --u)
-    if (iters % u == 0) return u;
-  return 1;
-}
 
 template <typename S, int N, int CG>
 __global__ void __launch_bounds__(CG*(N / Unpack<S>::RPC))

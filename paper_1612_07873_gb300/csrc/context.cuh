@@ -99,6 +99,12 @@ struct Level {
   DevBuf raw;                  // FP64 [Nv][V][nd] raw null vectors
   DevBuf orth64;               // FP64 block-orthonormalised, [agg][chi][Nv][rows]
   DevBuf Vp;                   // vprec [V][nd][Nv] (transfer operator layout)
+
+  // red-black preconditioning: A_e^-1 on the even sites (fine: packed
+  // Hermitian 6x6 chirality blocks, [V/2][72] reals; coarse: [V/2][col][row]
+  // complex), both in the vector precision
+  DevBuf ainv, xinv;
+  bool have_schur = false;
   bool have_raw = false, have_V = false;
 
   size_t vec_elems() const { return size_t(g.vol) * nd; }

@@ -90,6 +90,28 @@ void nullvecs_export(mg_ctx* c, int level, void* dst, cudaStream_t st);
 void restrict_apply(mg_ctx* c, int level, Vec coarse, Vec fine, cudaStream_t st);
 void prolong_apply(mg_ctx* c, int level, Vec fine, Vec coarse, cudaStream_t st);
 
+// ---------------------------------------------------------------- schur.cu
+// Red-black preconditioning (compact parity vectors: site s at s >> 1).
+// Hops of one parity with a fused epilogue; out and xc on parity p, in on
+// the other parity:
+enum EoMode {
+  EO_HOP = 0,                // out = H in
+  EO_AINV_HOP = 1,           // out = A^-1 H in            (p even)
+  EO_A_XC_MINUS_HOP = 2,     // out = A xc - H in
+  EO_XC_MINUS_HOP = 3,       // out = xc - H in
+  EO_AINV_XC_MINUS_HOP = 4,  // out = A^-1 (xc - H in)     (p even)
+};
+bool schur_supported(const mg_ctx* c, int level);
+// A_e^-1 of the level's operator (FP64 inversion); throws on a singular block
+void schur_prepare(mg_ctx* c, int level, cudaStream_t st);
+void eo_apply(mg_ctx* c, int level, int mode, Vec out, Vec in, const void* xc, int p,
+              cudaStream_t st);
+// full [nr][V][nd] <-> compact halves [nr][V/2][nd]
+void eo_split(mg_ctx* c, int level, Vec he, Vec ho, Vec full, cudaStream_t st);
+void eo_merge(mg_ctx* c, int level, Vec full, Vec he, Vec ho, cudaStream_t st);
+// out_e = A_e^-1 in_e
+void eo_ainv(mg_ctx* c, int level, Vec out, Vec in, cudaStream_t st);
+
 // ---------------------------------------------------------------- galerkin.cu
 void galerkin_build(mg_ctx* c, int level, cudaStream_t st);
 

@@ -24,7 +24,8 @@ struct mg_ctx::SolverWS {
   struct LevelWS {
     std::vector<std::unique_ptr<gbmg::DevBuf>> Z, W;
     gbmg::DevBuf r, x, rhs, tmp, kres, mrx, mrr, mrp;
-    gbmg::DevBuf r64, tmp64;  // level 0 only
+    gbmg::DevBuf eo1, eo2, eo3;  // red-black: each holds two compact parity halves
+    gbmg::DevBuf r64, tmp64;     // level 0 only
   };
   LevelWS lv[MG_MAX_LEVELS];
   int nk = 0;
@@ -88,6 +89,11 @@ void ensure_ws(mg_ctx* c, int nr) {
     ensure(w.mrx, vb);
     ensure(w.mrr, vb);
     ensure(w.mrp, vb);
+    if (c->p.red_black && L.have_schur) {
+      ensure(w.eo1, vb);
+      ensure(w.eo2, vb);
+      ensure(w.eo3, vb);
+    }
     if (l == 0) {
       ensure(w.r64, L.vec_elems() * 16 * nr);
       ensure(w.tmp64, L.vec_elems() * 16 * nr);
@@ -119,6 +125,45 @@ void mr_smooth(mg_ctx* c, int l, Vec x, Vec b, cudaStream_t st) {
   }
 }
 
+// compact parity half k (0 or 1) of a full-size buffer holding nr vectors:
+// [nr][V/2][nd] at byte offset k * (buffer bytes / 2)
+Vec half(DevBuf& b, const Level& L, int k, int nr) {
+  Vec v;
+  v.prec = L.vprec;
+  v.n = L.vec_elems() / 2;
+  v.nr = nr;
+  v.p = static_cast<char*>(b.p) + size_t(k) * (L.vec_bytes() / 2) * nr;
+  return v;
+}
+
+// out_o = S in_o = A_o in_o - H_oe A_e^-1 H_eo in_o; tmp_e: a compact even vector
+void schur_apply(mg_ctx* c, int l, Vec out, Vec in, Vec tmp, cudaStream_t st) {
+  eo_apply(c, l, EO_AINV_HOP, tmp, in, nullptr, 0, st);
+  eo_apply(c, l, EO_A_XC_MINUS_HOP, out, tmp, in.p, 1, st);
+}
+
+// z = approximate M^-1 r through the Schur system (Secs. 3.3, 7.1):
+// b^ = r_o - H_oe A_e^-1 r_e, x_o = MR_k(S, b^), z_e = A_e^-1 (r_e - H_eo x_o)
+void schur_smooth(mg_ctx* c, int l, Vec z, Vec r, cudaStream_t st) {
+  auto& w = c->ws->lv[l];
+  Level& L = c->L[l];
+  const int nr = z.nr;
+  Vec he = half(w.eo1, L, 0, nr), ho = half(w.eo1, L, 1, nr);
+  Vec ht = half(w.eo2, L, 0, nr), hx = half(w.eo2, L, 1, nr);
+  Vec hr = half(w.mrr, L, 0, nr), hp = half(w.mrp, L, 0, nr);
+  eo_split(c, l, he, ho, r, st);
+  eo_ainv(c, l, ht, he, st);
+  eo_apply(c, l, EO_XC_MINUS_HOP, hr, ht, ho.p, 1, st);  // MR residual starts at b^
+  blas_zero(c, hx, st);
+  for (int k = 0; k < c->p.mr_iters; ++k) {
+    schur_apply(c, l, hp, hr, ht, st);
+    blas_dot2(c, hp, hr, slot(l, S_PR), slot(l, S_PP), st);
+    blas_mr_update(c, hx, hr, hp, slot(l, S_PR), slot(l, S_PP), c->p.mr_omega, st);
+  }
+  eo_apply(c, l, EO_AINV_XC_MINUS_HOP, ht, hx, he.p, 0, st);
+  eo_merge(c, l, z, ht, hx, st);
+}
+
 struct GcrOut {
   int iters = 0;
   int restarts = 0;
@@ -132,16 +177,25 @@ void kcycle(mg_ctx* c, int l, Vec z, Vec r, cudaStream_t st, mg_solve_stats* sta
 // Flexible GCR at level l on x.nr right-hand sides.  x, b: level-0 -> FP64;
 // inner levels -> vprec.  stats: one record per right-hand side (or null);
 // level totals go to stats[0].
+// schur: solve S x_o = b^ on compact odd vectors (no preconditioner).
 GcrOut gcr(mg_ctx* c, int l, Vec x, Vec b, bool precond, double tol, int maxiter,
-           cudaStream_t st, mg_solve_stats* stats, bool record) {
+           cudaStream_t st, mg_solve_stats* stats, bool record, bool schur = false) {
   auto& w = c->ws->lv[l];
   Level& L = c->L[l];
-  const size_t n = L.vec_elems();
+  const size_t n = schur ? L.vec_elems() / 2 : L.vec_elems();
   const int nr = x.nr;
   const bool outer = (l == 0);
   Vec r = outer ? vbuf(w.r64, MG_F64, n, nr) : vbuf(w.r, L.vprec, n, nr);
   Vec rK = vbuf(w.r, L.vprec, n, nr);  // residual in level precision (outer level)
   Vec tmp = outer ? vbuf(w.tmp64, MG_F64, n, nr) : vbuf(w.tmp, L.vprec, n, nr);
+  Vec etmp;
+  if (schur) etmp = half(w.eo3, L, 0, nr);
+  auto op = [&](Vec o, Vec i) {
+    if (schur)
+      schur_apply(c, l, o, i, etmp, st);
+    else
+      level_apply(c, l, o, i, st);
+  };
   GcrOut out;
   out.rel.assign(nr, 0.0);
   out.conv_iter.assign(nr, -1);
@@ -191,7 +245,7 @@ GcrOut gcr(mg_ctx* c, int l, Vec x, Vec b, bool precond, double tol, int maxiter
       } else {
         blas_copy(c, Zk, r, st);
       }
-      level_apply(c, l, Wk, Zk, st);
+      op(Wk, Zk);
       for (int j = 0; j < k; ++j) {
         Vec Zj = vbuf(*w.Z[j], L.vprec, n, nr), Wj = vbuf(*w.W[j], L.vprec, n, nr);
         blas_dot(c, Wj, Wk, slot(l, S_BETA), st, outer);
@@ -216,7 +270,7 @@ GcrOut gcr(mg_ctx* c, int l, Vec x, Vec b, bool precond, double tol, int maxiter
       break;
     }
     // restart: true residual
-    level_apply(c, l, tmp, x, st);
+    op(tmp, x);
     blas_sub(c, r, b, tmp, st);
     out.restarts++;
     blas_norm2(c, r, slot(l, S_R), st);
@@ -240,22 +294,42 @@ void kcycle(mg_ctx* c, int l, Vec z, Vec r, cudaStream_t st, mg_solve_stats* sta
   Level& C = c->L[nl];
   auto& wc = c->ws->lv[nl];
   Vec rc = vbuf(wc.rhs, C.vprec, C.vec_elems(), nr), ec = vbuf(wc.x, C.vprec, C.vec_elems(), nr);
+  const bool rb = c->p.red_black && L.have_schur;
+  auto smooth = [&](Vec out, Vec in) {
+    if (rb)
+      schur_smooth(c, l, out, in, st);
+    else
+      mr_smooth(c, l, out, in, st);
+  };
   // pre-smooth
-  mr_smooth(c, l, z, r, st);
+  smooth(z, r);
   level_apply(c, l, tmp, z, st);
   blas_sub(c, kres, r, tmp, st);
   // coarse-grid correction
   restrict_apply(c, l, rc, kres, st);
-  if (nl == c->nlevels - 1)
-    gcr(c, nl, ec, rc, false, c->p.coarse_tol, c->p.coarse_maxiter, st, stats, false);
-  else
+  if (nl == c->nlevels - 1) {
+    if (c->p.red_black && C.have_schur) {
+      // coarsest solve on the Schur system, then the even sites
+      Vec he = half(wc.eo1, C, 0, nr), hb = half(wc.eo1, C, 1, nr);
+      Vec ht = half(wc.eo2, C, 0, nr), hx = half(wc.eo2, C, 1, nr);
+      eo_split(c, nl, he, hx, rc, st);
+      eo_ainv(c, nl, ht, he, st);
+      eo_apply(c, nl, EO_XC_MINUS_HOP, hb, ht, hx.p, 1, st);
+      gcr(c, nl, hx, hb, false, c->p.coarse_tol, c->p.coarse_maxiter, st, stats, false, true);
+      eo_apply(c, nl, EO_AINV_XC_MINUS_HOP, ht, hx, he.p, 0, st);
+      eo_merge(c, nl, ec, ht, hx, st);
+    } else {
+      gcr(c, nl, ec, rc, false, c->p.coarse_tol, c->p.coarse_maxiter, st, stats, false);
+    }
+  } else {
     gcr(c, nl, ec, rc, true, c->p.inner_tol, c->p.inner_maxiter, st, stats, false);
+  }
   prolong_apply(c, l, tmp, ec, st);
   blas_axpy_host(c, z, tmp, 1.0, 0.0, st);
   // post-smooth
   level_apply(c, l, tmp, z, st);
   blas_sub(c, kres, r, tmp, st);
-  mr_smooth(c, l, mrx, kres, st);
+  smooth(mrx, kres);
   blas_axpy_host(c, z, mrx, 1.0, 0.0, st);
 }
 

@@ -22,12 +22,12 @@ def to_np(t):
 
 
 def make_ctx(gb, dims, blocks, nvecs, mass=-0.2, csw=1.0, eps=0.3, seed=1, prec_fine=0,
-             prec_coarse=0, sweeps=4, antiperiodic=1, U=None):
+             prec_coarse=0, sweeps=4, antiperiodic=1, U=None, red_black=0):
     if U is None:
         U = syn.gauge_field(dims, eps, seed)
     p = gb.default_params(dims=dims, block=blocks, nvec=nvecs, mass=mass, csw=csw,
                           nlevels=len(blocks) + 1, prec_fine=prec_fine, prec_coarse=prec_coarse,
-                          setup_sweeps=sweeps, t_antiperiodic=antiperiodic)
+                          setup_sweeps=sweeps, t_antiperiodic=antiperiodic, red_black=red_black)
     mg = gb.Multigrid(p, to_dev(U))
     return mg, U
 
