@@ -241,13 +241,22 @@ def run_learned(args, gb, torch, ev, stream, dev):
         rows.append({"sweeps": k, "outer_iters": st["iters"], "s_per_solve": st["seconds"],
                      "true_residual": st["true_residual"]})
     saved = [10 - r["sweeps"] for r in rows if r["outer_iters"] <= plain["iters"]]
+    # red-black smoothing at the same near-critical mass (plain and learned starts)
+    p3rb = gb.default_params(dims=dims, block=w["block"], nvec=w["nvec"], mass=mass, csw=1.0,
+                             nlevels=3, prec_fine=1, prec_coarse=1, seed=9000, red_black=1)
+    rb_plain = learned.mg_iterations(p3rb, Ue, None, 10, b)
+    rb_learned = learned.mg_iterations(p3rb, Ue, prop, 2, b)
     P.close()
     return {"mass": mass, "train_fields": args.learned_ntrain, "train_lattice": list(tdims),
             "epochs": args.learned_epochs, "targets_s": t_targets, "train_s": t_train,
             "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1],
             "eval_lattice": list(dims),
             "plain": {"sweeps": 10, "outer_iters": plain["iters"], "s_per_solve": plain["seconds"]},
-            "learned": rows, "setup_sweeps_saved": max(saved) if saved else 0}
+            "learned": rows, "setup_sweeps_saved": max(saved) if saved else 0,
+            "red_black": {"plain_10_sweeps": {"outer_iters": rb_plain["iters"],
+                                              "s_per_solve": rb_plain["seconds"]},
+                          "learned_2_sweeps": {"outer_iters": rb_learned["iters"],
+                                               "s_per_solve": rb_learned["seconds"]}}}
 
 
 # ---------------------------------------------------------------- GPU leg

@@ -42,14 +42,16 @@ __device__ __forceinline__ int parity_of(const int c[4]) { return (c[0] + c[1] +
 __device__ __forceinline__ cpx<double> crecip(cpx<double> z) { return (1.0 / norm2(z)) * conj(z); }
 
 // ------------------------------------------------------------ fine level
-template <typename R, int MODE>
+// C12: links in the two-row form, third row rebuilt in registers with the
+// boundary sign of the link (as in the full-lattice kernel).
+template <typename R, int MODE, bool C12>
 __global__ void __launch_bounds__(128) k_wilson_eo(cpx<R>* __restrict__ out,
                                                    const cpx<R>* __restrict__ in,
                                                    const cpx<R>* __restrict__ xc,
                                                    const cpx<R>* __restrict__ U,
                                                    const R* __restrict__ A,
                                                    const R* __restrict__ Ainv, Geom g, R diag,
-                                                   int p, size_t hstride) {
+                                                   int p, size_t hstride, int antiperiodic) {
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
   if (h >= (g.vol >> 1)) return;
   const size_t off = size_t(blockIdx.y) * hstride;
@@ -70,20 +72,36 @@ __global__ void __launch_bounds__(128) k_wilson_eo(cpx<R>* __restrict__ out,
 #pragma unroll
     for (int i = 0; i < 12; ++i) psi[i] = reinterpret_cast<const cpx<R>*>(w)[i];
   };
-  auto load_link = [&](size_t idx) {
+  auto load_link = [&](size_t idx, bool neg) {
+    if constexpr (C12) {
+      const uint4* q = reinterpret_cast<const uint4*>(U + idx * 6);
+      uint4 w[3];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) u[i] = U[idx * 9 + i];
+      for (int i = 0; i < 3; ++i) w[i] = __ldg(q + i);
+#pragma unroll
+      for (int i = 0; i < 6; ++i) u[i] = reinterpret_cast<const cpx<R>*>(w)[i];
+      const R sg = neg ? R(-1) : R(1);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int b = (a + 1) % 3, cc = (a + 2) % 3;
+        u[6 + a] = sg * conj(u[b] * u[3 + cc] - u[cc] * u[3 + b]);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) u[i] = U[idx * 9 + i];
+    }
   };
+  const bool tlast = antiperiodic && c[3] == g.L[3] - 1, tfirst = antiperiodic && c[3] == 0;
   const size_t V = g.vol;
 #define GB_EO_HOP(MU)                                    \
   {                                                      \
     const int sf = neighbour(g, s, c, 1 + 2 * MU);       \
     load_spinor(in, sf >> 1);                            \
-    load_link(MU * V + s);                               \
+    load_link(MU * V + s, MU == 3 && tlast);             \
     hop_accum<MU, true>(u, psi, acc);                    \
     const int sb = neighbour(g, s, c, 2 + 2 * MU);       \
     load_spinor(in, sb >> 1);                            \
-    load_link(MU * V + sb);                              \
+    load_link(MU * V + sb, MU == 3 && tfirst);           \
     hop_accum<MU, false>(u, psi, acc);                   \
   }
   GB_EO_HOP(0) GB_EO_HOP(1) GB_EO_HOP(2) GB_EO_HOP(3)
@@ -500,16 +518,22 @@ template <int MODE>
 void fine_eo(mg_ctx* c, Vec out, Vec in, const void* xc, int p, cudaStream_t st) {
   Level& L = c->L[0];
   const dim3 grid(ceil_div(L.g.vol / 2, 128), unsigned(in.nr));
+  const int ap = c->p.t_antiperiodic;
   if (L.vprec == MG_F64)
-    k_wilson_eo<double, MODE><<<grid, 128, 0, st>>>(
+    k_wilson_eo<double, MODE, false><<<grid, 128, 0, st>>>(
         (cpx<double>*)out.p, (const cpx<double>*)in.p, (const cpx<double>*)xc,
         L.gauge64.as<cpx<double>>(), L.clover64.as<double>(), L.ainv.as<double>(), L.g, L.diag,
-        p, in.n);
+        p, in.n, ap);
+  else if (L.gauge12_ok)  // two-row links: a third fewer link bytes, read twice per S
+    k_wilson_eo<float, MODE, true><<<grid, 128, 0, st>>>(
+        (cpx<float>*)out.p, (const cpx<float>*)in.p, (const cpx<float>*)xc,
+        L.gauge12.as<cpx<float>>(), L.clover32.as<float>(), L.ainv.as<float>(), L.g,
+        float(L.diag), p, in.n, ap);
   else
-    k_wilson_eo<float, MODE><<<grid, 128, 0, st>>>(
+    k_wilson_eo<float, MODE, false><<<grid, 128, 0, st>>>(
         (cpx<float>*)out.p, (const cpx<float>*)in.p, (const cpx<float>*)xc,
         L.gauge32.as<cpx<float>>(), L.clover32.as<float>(), L.ainv.as<float>(), L.g,
-        float(L.diag), p, in.n);
+        float(L.diag), p, in.n, ap);
 }
 
 }  // namespace
