@@ -179,6 +179,12 @@ mg_status mg_apply(mg_ctx* ctx, int level, void* y_dev, const void* x_dev, void*
  * precision.                                                               */
 mg_status mg_wilson_clover_apply(mg_ctx* ctx, void* out_dev, const void* in_dev, void* stream);
 
+/* The same on nrhs vectors at once, [nrhs][site][12] back to back
+ * (1 <= nrhs <= 64); out must not overlap in.  One launch: the links and
+ * clover of a site serve all nrhs vectors (the launch policy is autotuned). */
+mg_status mg_wilson_clover_apply_multi(mg_ctx* ctx, void* out_dev, const void* in_dev, int nrhs,
+                                       void* stream);
+
 /* Sec. 6.6 transfer operators between level l and l+1 (vector precision of
  * each level):  coarse = P^dag fine  (restrict),  fine = P coarse (prolong). */
 mg_status mg_restrict(mg_ctx* ctx, int level, void* coarse_dev, const void* fine_dev,

@@ -87,6 +87,7 @@ def _load():
         "mg_gcr_solve": (i, [vp, vp, vp, d, i, C.POINTER(mg_solve_stats), vp]),
         "mg_gcr_solve_multi": (i, [vp, vp, vp, i, d, i, C.POINTER(mg_solve_stats), vp]),
         "mg_tune_set": (i, [C.c_char_p, i]),
+        "mg_wilson_clover_apply_multi": (i, [vp, vp, vp, i, vp]),
         "mg_schur_apply": (i, [vp, i, vp, vp, i, vp]),
         "mg_tune_get": (i, [C.c_char_p]),
         "mg_get_coarse_links": (i, [vp, i, vp, sz, vp]),
@@ -209,6 +210,11 @@ def mg_apply(ctx, level, y, x, stream=None):
 
 def mg_wilson_clover_apply(ctx, out, inp, stream=None):
     _ok(LIB.mg_wilson_clover_apply(ctx, _ptr(out), _ptr(inp), _stream(stream)), ctx)
+
+
+def mg_wilson_clover_apply_multi(ctx, out, inp, nrhs, stream=None):
+    """out[v] = M inp[v] for nrhs fine vectors stored back to back."""
+    _ok(LIB.mg_wilson_clover_apply_multi(ctx, _ptr(out), _ptr(inp), nrhs, _stream(stream)), ctx)
 
 
 def mg_restrict(ctx, level, coarse, fine, stream=None):

@@ -271,6 +271,21 @@ mg_status mg_wilson_clover_apply(mg_ctx* c, void* out, const void* in, void* str
   });
 }
 
+mg_status mg_wilson_clover_apply_multi(mg_ctx* c, void* out, const void* in, int nrhs,
+                                       void* stream) {
+  return guarded(c, [&] {
+    GB_REQUIRE(in && out, MG_ERR_ARG, "wilson_clover_apply_multi: null vector");
+    GB_REQUIRE(nrhs >= 1 && nrhs <= 64, MG_ERR_ARG, "wilson_clover_apply_multi: bad nrhs");
+    Level& L = c->L[0];
+    const size_t bytes = L.vec_bytes() * size_t(nrhs);
+    const char* a = (const char*)in;
+    const char* b = (const char*)out;
+    GB_REQUIRE(a + bytes <= b || b + bytes <= a, MG_ERR_ARG,
+               "wilson_clover_apply_multi: output overlaps input");
+    wilson_apply(c, level_vec(L, out), level_vec(L, const_cast<void*>(in)), nrhs, S(stream));
+  });
+}
+
 mg_status mg_restrict(mg_ctx* c, int level, void* coarse, const void* fine, void* stream) {
   return guarded(c, [&] {
     check_level(c, level, 0, c->nlevels - 2);

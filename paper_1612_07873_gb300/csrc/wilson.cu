@@ -189,27 +189,17 @@ __global__ void k_clover(const cpx<double>* __restrict__ U, Geom g, double csw,
 // C12: links in the two-row form (16-byte loads, 48 B per FP32 link) with
 // the third row rebuilt in registers; the rebuilt row carries the boundary
 // sign of the link (t-links leaving the last time slice).
-// Several vectors (nvec > 1, stored vstride apart):
-//  * VIW = false: CTAs ordered vector-fastest, so the nvec CTAs of one site
-//    chunk run close together and the chunk's links and clover come from
-//    DRAM once and from L2 for the other vectors;
-//  * VIW = true: thread g works on site g / nvec, vector g % nvec, so the
-//    vectors of a site sit in neighbouring lanes and one load instruction
-//    serves the site's link or clover word to all of them.
-template <typename R, bool C12, int MINB, bool VIW = false>
+// Several vectors (nvec > 1, stored vstride apart): CTAs are ordered
+// vector-fastest, so the nvec CTAs of one site chunk run close together and
+// the chunk's links and clover come from DRAM once and from L2 for the
+// other vectors.
+template <typename R, bool C12, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_wilson(cpx<R>* __restrict__ out, const cpx<R>* __restrict__ in,
                                                 const cpx<R>* __restrict__ U, const R* __restrict__ A,
                                                 Geom g, R diag, size_t vstride, int nvec,
                                                 int antiperiodic) {
-  int vec, s;
-  if constexpr (VIW) {
-    const size_t gi = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    s = int(gi / size_t(nvec));
-    vec = int(gi - size_t(s) * nvec);
-  } else {
-    vec = blockIdx.x % nvec;
-    s = (blockIdx.x / nvec) * blockDim.x + threadIdx.x;
-  }
+  const int vec = blockIdx.x % nvec;
+  const int s = (blockIdx.x / nvec) * blockDim.x + threadIdx.x;
   if (s >= g.vol) return;
   in += vec * vstride;
   out += vec * vstride;
@@ -355,6 +345,107 @@ __global__ void __launch_bounds__(128) k_wilson_mv(cpx<R>* __restrict__ out,
   }
 }
 
+// Batched form with the operator staged in shared memory: CTA b holds the
+// eight hop links (two-row form when C12) and the clover of the 32 sites
+// [32 b, 32 b + 32), stored transposed ([element][site]) so that the 32
+// lanes of a warp (32 consecutive sites) read consecutive words.  Warp w
+// then applies the operator to vectors w, w + 4, ...: per vector the same
+// work and registers as the one-vector kernel, while links and clover come
+// from HBM once for all nvec vectors.
+template <bool C12>
+__global__ void __launch_bounds__(128) k_wilson_tile(cpx<float>* __restrict__ out,
+                                                     const cpx<float>* __restrict__ in,
+                                                     const cpx<float>* __restrict__ U,
+                                                     const float* __restrict__ A, Geom g,
+                                                     float diag, size_t vstride, int nvec,
+                                                     int antiperiodic) {
+  constexpr int TS = 32;               // sites per CTA
+  constexpr int LC = C12 ? 6 : 9;      // stored complex numbers per link
+  __shared__ cpx<float> lk[8 * LC * TS];   // [hop][element][site]
+  __shared__ float cl[72 * TS];             // [element][site]
+  __shared__ int nbb[4 * TS];               // backward neighbour of each site, per mu
+  const int tid = threadIdx.x;
+  const int s0 = blockIdx.x * TS;
+  const size_t V = g.vol;
+  {
+    const int sl = tid & (TS - 1), mu = tid >> 5;
+    const int s = s0 + sl;
+    if (s < g.vol) {
+      int c[4];
+      site_coords(g, s, c);
+      nbb[mu * TS + sl] = neighbour(g, s, c, 2 + 2 * mu);
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < 8 * LC * TS; i += 128) {
+    const int sl = i & (TS - 1), e = (i / TS) % LC, h = i / (TS * LC);
+    const int s = s0 + sl;
+    if (s < g.vol) {
+      const int mu = h >> 1;
+      const size_t link = size_t(mu) * V + ((h & 1) ? nbb[mu * TS + sl] : s);
+      const float2 f = __ldg(reinterpret_cast<const float2*>(U + link * LC + e));
+      lk[i] = cpx<float>(f.x, f.y);
+    }
+  }
+  for (int i = tid; i < 72 * TS; i += 128) {
+    const int sl = i & (TS - 1), k = i / TS;
+    const int s = s0 + sl;
+    if (s < g.vol) cl[i] = __ldg(A + size_t(s) * 72 + k);
+  }
+  __syncthreads();
+  const int sl = tid & (TS - 1), w = tid >> 5;
+  const int s = s0 + sl;
+  if (s >= g.vol) return;
+  int c[4];
+  site_coords(g, s, c);
+  int nbr[8];
+#pragma unroll
+  for (int d = 0; d < 8; ++d) nbr[d] = neighbour(g, s, c, 1 + d);
+  const bool tlast = antiperiodic && c[3] == g.L[3] - 1, tfirst = antiperiodic && c[3] == 0;
+  for (int v = w; v < nvec; v += 4) {
+    const cpx<float>* x = in + size_t(v) * vstride;
+    cpx<float> psi[12], acc[12], u[9];
+    auto load_spinor = [&](int site) {
+      const uint4* q = reinterpret_cast<const uint4*>(x + size_t(site) * 12);
+      uint4 wv[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) wv[i] = __ldg(q + i);
+#pragma unroll
+      for (int i = 0; i < 12; ++i) psi[i] = reinterpret_cast<const cpx<float>*>(wv)[i];
+    };
+    auto load_link = [&](int h, bool neg) {
+#pragma unroll
+      for (int e = 0; e < LC; ++e) u[e] = lk[(h * LC + e) * TS + sl];
+      if constexpr (C12) {
+        const float sg = neg ? -1.f : 1.f;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          const int b = (r + 1) % 3, cc = (r + 2) % 3;
+          u[6 + r] = sg * conj(u[b] * u[3 + cc] - u[cc] * u[3 + b]);
+        }
+      }
+    };
+    load_spinor(s);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) acc[i] = cpx<float>(0.f, 0.f);
+    clover_accum_strided(cl + sl, TS, diag, psi, acc);
+#define GB_TILE_HOP(MU)                                  \
+  {                                                      \
+    load_spinor(nbr[2 * MU]);                            \
+    load_link(2 * MU, MU == 3 && tlast);                 \
+    hop_accum<MU, true>(u, psi, acc);                    \
+    load_spinor(nbr[2 * MU + 1]);                        \
+    load_link(2 * MU + 1, MU == 3 && tfirst);            \
+    hop_accum<MU, false>(u, psi, acc);                   \
+  }
+    GB_TILE_HOP(0) GB_TILE_HOP(1) GB_TILE_HOP(2) GB_TILE_HOP(3)
+#undef GB_TILE_HOP
+    uint4* o = reinterpret_cast<uint4*>(out + size_t(v) * vstride + size_t(s) * 12);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) o[i] = reinterpret_cast<const uint4*>(acc)[i];
+  }
+}
+
 }  // namespace
 
 void fine_operator_build(mg_ctx* c, const void* gauge_ext, cudaStream_t st) {
@@ -416,8 +507,8 @@ void wilson_apply(mg_ctx* c, Vec out, Vec in, int nvec, cudaStream_t st) {
     //   0 / 1   one vector per thread, stored / two-row links, default registers
     //   2 .. 5  the same with a register budget (minimum CTAs per SM 2, 2, 4, 6)
     //   6 / 7   2 / 4 vectors per thread (links and clover reused in registers)
-    //   8 .. 10 the vectors of a site in neighbouring lanes (stored links;
-    //           two-row links; two-row links with 4 CTAs per SM)
+    //   8 / 9   links (stored / two-row) and clover of 32 sites staged in
+    //           shared memory, warps looping over the vectors (nvec >= 4)
     // Two-row policies are candidates only when the field allows them.
     GB_REQUIRE(L.gauge32.p, MG_ERR_STATE, "FP32 fine operator not built");
     const unsigned gx = ceil_div(L.g.vol, 128);
@@ -428,7 +519,7 @@ void wilson_apply(mg_ctx* c, Vec out, Vec in, int nvec, cudaStream_t st) {
     auto* o = (cpx<float>*)out.p;
     auto* i = (const cpx<float>*)in.p;
     const float dg = float(L.diag);
-    const unsigned gv = ceil_div(size_t(L.g.vol) * nvec, 128);
+    const unsigned gt = ceil_div(L.g.vol, 32);
     auto launch = [&](int q) {
       switch (q) {
         case 1: k_wilson<float, true, 0><<<grid, 128, 0, st>>>(o, i, U12, A, L.g, dg, vs, nvec, ap); break;
@@ -438,9 +529,8 @@ void wilson_apply(mg_ctx* c, Vec out, Vec in, int nvec, cudaStream_t st) {
         case 5: k_wilson<float, true, 6><<<grid, 128, 0, st>>>(o, i, U12, A, L.g, dg, vs, nvec, ap); break;
         case 6: k_wilson_mv<float, 2><<<dim3(gx, nvec / 2), 128, 0, st>>>(o, i, U18, A, L.g, dg, vs); break;
         case 7: k_wilson_mv<float, 4><<<dim3(gx, nvec / 4), 128, 0, st>>>(o, i, U18, A, L.g, dg, vs); break;
-        case 8: k_wilson<float, false, 0, true><<<gv, 128, 0, st>>>(o, i, U18, A, L.g, dg, vs, nvec, ap); break;
-        case 9: k_wilson<float, true, 0, true><<<gv, 128, 0, st>>>(o, i, U12, A, L.g, dg, vs, nvec, ap); break;
-        case 10: k_wilson<float, true, 4, true><<<gv, 128, 0, st>>>(o, i, U12, A, L.g, dg, vs, nvec, ap); break;
+        case 8: k_wilson_tile<false><<<gt, 128, 0, st>>>(o, i, U18, A, L.g, dg, vs, nvec, ap); break;
+        case 9: k_wilson_tile<true><<<gt, 128, 0, st>>>(o, i, U12, A, L.g, dg, vs, nvec, ap); break;
         default: k_wilson<float, false, 0><<<grid, 128, 0, st>>>(o, i, U18, A, L.g, dg, vs, nvec, ap); break;
       }
     };
@@ -448,9 +538,9 @@ void wilson_apply(mg_ctx* c, Vec out, Vec in, int nvec, cudaStream_t st) {
     if (L.gauge12_ok) cands.insert(cands.end(), {1, 3, 4, 5});
     if (nvec % 2 == 0) cands.push_back(6);
     if (nvec % 4 == 0) cands.push_back(7);
-    if (nvec > 1) {
+    if (nvec >= 4) {
       cands.push_back(8);
-      if (L.gauge12_ok) cands.insert(cands.end(), {9, 10});
+      if (L.gauge12_ok) cands.push_back(9);
     }
     const std::string key = "wilson/v" + std::to_string(L.g.vol) + "/n" + std::to_string(nvec) +
                             "/c" + std::to_string(int(L.gauge12_ok));

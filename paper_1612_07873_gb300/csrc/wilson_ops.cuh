@@ -140,6 +140,30 @@ __device__ __forceinline__ void clover_accum(const R* __restrict__ A, R diag, co
   }
 }
 
+// clover_accum with element k of the packed clover at A[k * stride] (a
+// transposed shared-memory tile).
+template <typename R>
+__device__ __forceinline__ void clover_accum_strided(const R* __restrict__ A, int stride, R diag,
+                                                     const cpx<R> psi[12], cpx<R> acc[12]) {
+#pragma unroll
+  for (int chi = 0; chi < 2; ++chi) {
+    const R* a = A + chi * 36 * stride;
+    const cpx<R>* in = psi + chi * 6;
+    cpx<R>* out = acc + chi * 6;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) out[i] += (diag + a[i * stride]) * in[i];
+#pragma unroll
+    for (int i = 1; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j < i; ++j) {
+        int k = i * (i - 1) / 2 + j;
+        cpx<R> l(a[(6 + 2 * k) * stride], a[(7 + 2 * k) * stride]);
+        cmac(out[i], l, in[j]);
+        cmac_conj(out[j], l, in[i]);
+      }
+  }
+}
+
 // acc6 += (diag + A_chi) psi6 for one packed 6x6 Hermitian chirality block.
 template <typename R>
 __device__ __forceinline__ void clover_block_accum(const R* __restrict__ a, R diag,

@@ -4,8 +4,8 @@ The autotuner picks one policy per shape; here each policy is pinned in turn
 through mg_tune_set: stored 18-real links or two-row links rebuilt in
 registers (third row = conj(row0 x row1) times the boundary sign), four
 register budgets, and, in the batched form used by the setup sweeps and the
-multi-RHS solve, 2 or 4 vectors per thread or the vectors of a site in
-neighbouring lanes.  A field that is not special unitary must never take the
+multi-RHS solve, 2 or 4 vectors per thread or the operator of 32 sites staged
+in shared memory for all vectors.  A field that is not special unitary must never take the
 two-row form.
 """
 import numpy as np
@@ -19,7 +19,7 @@ from gpu_helpers import make_ctx, oracle_fine, rel_l2, to_dev, to_np
 pytestmark = pytest.mark.gpu
 
 SINGLE = [0, 1, 2, 3, 4, 5]   # 1 vector per thread: (link form, register budget)
-BATCHED = [6, 7, 8, 9, 10]    # 2 or 4 vectors per thread; vectors of a site in neighbouring lanes
+BATCHED = [6, 7, 8, 9]        # 2 or 4 vectors per thread; shared-memory operator tile
 
 
 @pytest.mark.parametrize("antiperiodic", [1, 0])
@@ -80,4 +80,22 @@ def test_non_unitary_field_keeps_stored_links(gpu_lib):
     err = rel_l2(to_np(out), oracle_fine(U, dims).apply(psi))
     assert err < 1e-5, err
     gb.mg_tune_set(f"wilson/v{vol}/n1/c0", -1)
+    mg.close()
+
+
+@pytest.mark.parametrize("nrhs", [3, 8])
+def test_apply_multi(gpu_lib, nrhs):
+    """mg_wilson_clover_apply_multi: nrhs vectors back to back, one launch."""
+    gb = gpu_lib
+    dims = (4, 4, 6, 4)
+    mg, U = make_ctx(gb, dims, [(2, 2, 2, 2)], [2], prec_fine=1, prec_coarse=1, eps=0.5)
+    psi = syn.gaussian_field((nrhs, lat.volume(dims), 12), 74)
+    out = torch.empty(psi.shape, dtype=torch.complex64, device="cuda")
+    gb.mg_wilson_clover_apply_multi(mg.ctx, out, to_dev(psi, torch.complex64), nrhs)
+    torch.cuda.synchronize()
+    op = oracle_fine(U, dims)
+    err = rel_l2(to_np(out), np.stack([op.apply(p) for p in psi]))
+    assert err < 1e-5, err
+    with pytest.raises(gb.MGError):
+        gb.mg_wilson_clover_apply_multi(mg.ctx, out, out, nrhs)
     mg.close()
