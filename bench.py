@@ -325,6 +325,8 @@ def gpu_main(args):
         dist.barrier()
     torch.cuda.synchronize()
     launches0 = gb.mg_launch_count(ctx)
+    if args.profile_range:  # only the timed steps are seen by a profiler started off
+        torch.cuda.cudart().cudaProfilerStart()
     t_start, t_stop = ev(), ev()
     t_start.record(stream)
     phases, stats = [], []
@@ -334,6 +336,8 @@ def gpu_main(args):
         stats.append(st)
     t_stop.record(stream)
     torch.cuda.synchronize()
+    if args.profile_range:
+        torch.cuda.cudart().cudaProfilerStop()
     if world > 1:
         dist.barrier()
     launches = gb.mg_launch_count(ctx) - launches0
@@ -544,6 +548,9 @@ def main():
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides (coarse-apply mode)")
     ap.add_argument("--slots", type=int, default=9, choices=[5, 9],
                     help="coarse link blocks stored (coarse-apply mode)")
+    ap.add_argument("--profile-range", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop (for ncu "
+                         "--profile-from-start off)")
     ap.add_argument("--no-learned", dest="learned", action="store_false",
                     help="skip training / evaluating the learned setup")
     ap.add_argument("--learned-ntrain", type=int, default=24)
