@@ -536,6 +536,54 @@ def coarse_apply_main(args):
     return 0
 
 
+def wilson_policies_main(args):
+    """Every launch policy of the FP32 fine operator, pinned in turn through
+    mg_tune_set, on the 32^3x64 workload lattice for 1, 8 and 24 vectors
+    (mg_wilson_clover_apply_multi); microseconds per vector by CUDA events."""
+    import torch
+
+    import paper_1612_07873_gb300 as gb
+    w = syn.WORKLOADS[WORKLOAD]
+    dims = w["dims"]
+    vol = syn.volume(dims)
+    U = torch.from_numpy(syn.gauge_field(dims, w["eps"], w["seed"])).cuda()
+    p = gb.default_params(dims=dims, block=w["block"], nvec=w["nvec"], mass=w["mass"],
+                          csw=w["csw"], nlevels=3, prec_fine=1, prec_coarse=1)
+    mg = gb.Multigrid(p, U)
+    rows = []
+    for nvec in (1, 8, 24):
+        g = torch.Generator(device="cuda").manual_seed(nvec)
+        x = torch.randn((nvec, vol, 12), dtype=torch.complex64, device="cuda", generator=g)
+        y = torch.empty_like(x)
+        key = f"wilson/v{vol}/n{nvec}/c1"
+        gb.mg_tune_set(key, -1)
+        gb.mg_wilson_clover_apply_multi(mg.ctx, y, x, nvec)
+        torch.cuda.synchronize()
+        pick = gb.mg_tune_get(key)
+        for pol in range(10):
+            if (pol >= 6 and nvec == 1) or (pol == 6 and nvec % 2) or (pol == 7 and nvec % 4) \
+                    or (pol >= 8 and nvec < 4):
+                continue
+            gb.mg_tune_set(key, pol)
+            for _ in range(args.warmup):
+                gb.mg_wilson_clover_apply_multi(mg.ctx, y, x, nvec)
+            torch.cuda.synchronize()
+            gb.mg_profile_reset(mg.ctx)
+            gb.mg_profile_enable(mg.ctx, True)
+            for _ in range(args.steps):
+                gb.mg_wilson_clover_apply_multi(mg.ctx, y, x, nvec)
+            q = gb.mg_profile_query(mg.ctx, "wilson_clover", 0)
+            gb.mg_profile_enable(mg.ctx, False)
+            us = 1e3 * q["ms"] / q["launches"]
+            rows.append({"nvec": nvec, "policy": pol, "us_per_vector": us / nvec,
+                         "tuner_pick": pol == pick,
+                         "gbs_algorithmic": q["bytes"] / q["launches"] / (us * 1e-6) / 1e9})
+        gb.mg_tune_set(key, -1)
+    mg.close()
+    print(json.dumps({"mode": "wilson-policies", "lattice": list(dims), "rows": rows}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -543,7 +591,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gbmg", choices=["gbmg", "reference"])
     ap.add_argument("--form", default="fp32", choices=["fp32", "bf16", "fp16", "int16"])
-    ap.add_argument("--mode", default="pipeline", choices=["pipeline", "coarse-apply"])
+    ap.add_argument("--mode", default="pipeline",
+                    choices=["pipeline", "coarse-apply", "wilson-policies"])
     ap.add_argument("--fine", default="", help="override the fine extents, e.g. 16,16,16,32")
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides (coarse-apply mode)")
     ap.add_argument("--slots", type=int, default=9, choices=[5, 9],
@@ -562,6 +611,8 @@ def main():
         return reference_main(args)
     if args.mode == "coarse-apply":
         return coarse_apply_main(args)
+    if args.mode == "wilson-policies":
+        return wilson_policies_main(args)
     return gpu_main(args)
 
 
