@@ -390,19 +390,22 @@ def gpu_main(args):
     forms = {}
     if args.forms:
         mg.close()
-        for fname, pc, slots, nr, rbp in (
-                ("bf16", 2, 9, 1, 0), ("fp16", 3, 9, 1, 0), ("int16", 4, 9, 1, 0),
-                ("fp32_5blocks", 1, 5, 1, 0), ("bf16_5blocks", 2, 5, 1, 0),
-                ("fp32_mrhs8", 1, 9, 8, 0), ("bf16_mrhs8", 2, 9, 8, 0),
-                ("fp32_redblack", 1, 9, 1, 1), ("bf16_redblack", 2, 9, 1, 1),
-                ("bf16_redblack_mrhs8", 2, 9, 8, 1)):
+        # (name, coarse link store, link slots, RHS per call, red-black, fine smoother)
+        for fname, pc, slots, nr, rbp, ps in (
+                ("bf16", 2, 9, 1, 0, 1), ("fp16", 3, 9, 1, 0, 1), ("int16", 4, 9, 1, 0, 1),
+                ("fp32_5blocks", 1, 5, 1, 0, 1), ("bf16_5blocks", 2, 5, 1, 0, 1),
+                ("fp32_mrhs8", 1, 9, 8, 0, 1), ("bf16_mrhs8", 2, 9, 8, 0, 1),
+                ("fp32_redblack", 1, 9, 1, 1, 1), ("bf16_redblack", 2, 9, 1, 1, 1),
+                ("bf16_redblack_mrhs8", 2, 9, 8, 1, 1),
+                ("fp32_smoother16", 1, 9, 1, 0, 2), ("bf16_smoother16", 2, 9, 1, 0, 2),
+                ("bf16_smoother16_mrhs8", 2, 9, 8, 0, 2)):
             if fname == form:
                 continue
             pf = gb.default_params(dims=dims, block=blocks, nvec=nvecs, mass=w["mass"],
                                    csw=w["csw"], nlevels=3, prec_fine=1, prec_coarse=pc,
                                    setup_sweeps=w["sweeps"], t_antiperiodic=w["antiperiodic"],
                                    seed=w["seed"] + 1000 * rank, link_slots=slots,
-                                   red_black=rbp)
+                                   red_black=rbp, prec_smoother=ps)
             mf = gb.Multigrid(pf, gauge_dev)
             t0 = ev()
             t1 = ev()

@@ -108,6 +108,11 @@ typedef struct {
                                        3.3, 7.1): MR smoothing on the Schur system
                                        S = A_o - H_oe A_e^-1 H_eo and the coarsest
                                        GCR on S; 0: off (default)                  */
+  mg_prec prec_smoother;            /* fine-level MR smoother storage: MG_F32 (the
+                                       fine level's own) or MG_BF16 (Sec. 7.1: the
+                                       finest smoother in 16 bits; vectors and a copy
+                                       of the operator in BF16, FP32 arithmetic;
+                                       needs an FP32 fine level)                   */
 } mg_params;
 
 typedef struct {
@@ -184,6 +189,13 @@ mg_status mg_wilson_clover_apply(mg_ctx* ctx, void* out_dev, const void* in_dev,
  * clover of a site serve all nrhs vectors (the launch policy is autotuned). */
 mg_status mg_wilson_clover_apply_multi(mg_ctx* ctx, void* out_dev, const void* in_dev, int nrhs,
                                        void* stream);
+
+/* The operator of the 16-bit fine-level smoother (params.prec_smoother =
+ * MG_BF16): out = M in on BF16 complex vectors ([nrhs][site][12] pairs of
+ * bfloat16 (re, im)), with the BF16 copy of the links and clover and FP32
+ * arithmetic.  MG_ERR_STATE when the context has no 16-bit smoother.      */
+mg_status mg_wilson_clover_apply_bf16(mg_ctx* ctx, void* out_dev, const void* in_dev, int nrhs,
+                                      void* stream);
 
 /* Sec. 6.6 transfer operators between level l and l+1 (vector precision of
  * each level):  coarse = P^dag fine  (restrict),  fine = P coarse (prolong). */

@@ -49,6 +49,7 @@ class mg_params(C.Structure):
         ("coarse_maxiter", C.c_int),
         ("link_slots", C.c_int),
         ("red_black", C.c_int),
+        ("prec_smoother", C.c_int),
     ]
 
 
@@ -88,6 +89,7 @@ def _load():
         "mg_gcr_solve_multi": (i, [vp, vp, vp, i, d, i, C.POINTER(mg_solve_stats), vp]),
         "mg_tune_set": (i, [C.c_char_p, i]),
         "mg_wilson_clover_apply_multi": (i, [vp, vp, vp, i, vp]),
+        "mg_wilson_clover_apply_bf16": (i, [vp, vp, vp, i, vp]),
         "mg_schur_apply": (i, [vp, i, vp, vp, i, vp]),
         "mg_tune_get": (i, [C.c_char_p]),
         "mg_get_coarse_links": (i, [vp, i, vp, sz, vp]),
@@ -215,6 +217,11 @@ def mg_wilson_clover_apply(ctx, out, inp, stream=None):
 def mg_wilson_clover_apply_multi(ctx, out, inp, nrhs, stream=None):
     """out[v] = M inp[v] for nrhs fine vectors stored back to back."""
     _ok(LIB.mg_wilson_clover_apply_multi(ctx, _ptr(out), _ptr(inp), nrhs, _stream(stream)), ctx)
+
+
+def mg_wilson_clover_apply_bf16(ctx, out, inp, nrhs=1, stream=None):
+    """The 16-bit smoother's operator; out, inp: bfloat16 tensors [nrhs][V][12][2]."""
+    _ok(LIB.mg_wilson_clover_apply_bf16(ctx, _ptr(out), _ptr(inp), nrhs, _stream(stream)), ctx)
 
 
 def mg_restrict(ctx, level, coarse, fine, stream=None):

@@ -106,6 +106,7 @@ void mg_default_params(mg_params* p) {
   p->coarse_maxiter = 100;
   p->link_slots = 9;
   p->red_black = 0;
+  p->prec_smoother = MG_F32;
 }
 
 mg_status mg_create(const mg_params* p, const void* gauge_dev, mg_ctx** out) {
@@ -173,8 +174,12 @@ mg_status mg_create(const mg_params* p, const void* gauge_dev, mg_ctx** out) {
     GB_CHECK(cudaMallocHost(&c->h_scalars, size_t(kMaxNrhs) * sizeof(double2)));
     GB_CHECK(cudaMemset(c->scalars.p, 0, c->scalars.bytes));
     GB_CHECK(cudaMemset(c->status.p, 0, c->status.bytes));
+    GB_REQUIRE(p->prec_smoother == MG_F32 || p->prec_smoother == MG_F64 ||
+                   (p->prec_smoother == MG_BF16 && p->prec_fine == MG_F32),
+               MG_ERR_ARG, "prec_smoother: MG_F32, or MG_BF16 with an FP32 fine level");
     fine_operator_build(c, gauge_dev, 0);
     if (p->red_black) schur_prepare(c, 0, 0);
+    smoother16_prepare(c, 0);
     GB_CHECK(cudaDeviceSynchronize());
   } catch (const Error& e) {
     delete c;
@@ -283,6 +288,23 @@ mg_status mg_wilson_clover_apply_multi(mg_ctx* c, void* out, const void* in, int
     GB_REQUIRE(a + bytes <= b || b + bytes <= a, MG_ERR_ARG,
                "wilson_clover_apply_multi: output overlaps input");
     wilson_apply(c, level_vec(L, out), level_vec(L, const_cast<void*>(in)), nrhs, S(stream));
+  });
+}
+
+mg_status mg_wilson_clover_apply_bf16(mg_ctx* c, void* out, const void* in, int nrhs,
+                                      void* stream) {
+  return guarded(c, [&] {
+    GB_REQUIRE(in && out && in != out, MG_ERR_ARG, "wilson_clover_apply_bf16: bad vectors");
+    GB_REQUIRE(nrhs >= 1 && nrhs <= 64, MG_ERR_ARG, "wilson_clover_apply_bf16: bad nrhs");
+    GB_REQUIRE(smoother16_enabled(c), MG_ERR_STATE, "wilson_clover_apply_bf16: no 16-bit smoother");
+    Level& L = c->L[0];
+    Vec vo, vi;
+    vo.p = out;
+    vi.p = const_cast<void*>(in);
+    vo.prec = vi.prec = MG_BF16;
+    vo.n = vi.n = L.vec_elems();
+    vo.nr = vi.nr = nrhs;
+    wilson16_apply(c, vo, vi, S(stream));
   });
 }
 

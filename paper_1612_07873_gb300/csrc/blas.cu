@@ -278,6 +278,72 @@ __global__ void k_gcr_update(cpx<Rx>* __restrict__ x, cpx<Rx>* __restrict__ r,
   }
 }
 
+// ---- BF16 vectors (the 16-bit fine-level smoother): storage BF16, all
+// arithmetic FP32, per-thread sums FP32 and cross-thread sums FP64
+__device__ __forceinline__ cpx<float> h2f(bf16c v) { return StoreTraits<bf16c>::load(v); }
+
+__global__ void k_copy_to16(bf16c* __restrict__ y, const cpx<float>* __restrict__ x, size_t n) {
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
+       i += size_t(gridDim.x) * blockDim.x)
+    y[i] = StoreTraits<bf16c>::pack(x[i]);
+}
+__global__ void k_copy_from16(cpx<float>* __restrict__ y, const bf16c* __restrict__ x, size_t n) {
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
+       i += size_t(gridDim.x) * blockDim.x)
+    y[i] = h2f(x[i]);
+}
+
+__global__ void k_dot2_partial_h(const bf16c* __restrict__ p, const bf16c* __restrict__ r,
+                                 size_t n, double2* __restrict__ part) {
+  __shared__ double2 sh[32];
+  p += blockIdx.y * n;
+  r += blockIdx.y * n;
+  cpx<float> a_pr(0.f, 0.f);
+  float a_pp = 0.f;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
+       i += size_t(gridDim.x) * blockDim.x) {
+    const cpx<float> x = h2f(p[i]), y = h2f(r[i]);
+    cmac_conj(a_pr, x, y);
+    a_pp = fmaf(x.re, x.re, fmaf(x.im, x.im, a_pp));
+  }
+  double2 pr = block_sum(make_double2(double(a_pr.re), double(a_pr.im)), sh);
+  __syncthreads();
+  double2 pp = block_sum(make_double2(double(a_pp), 0.0), sh);
+  if (threadIdx.x == 0) {
+    const size_t base = size_t(blockIdx.y) * 2 * gridDim.x;
+    part[base + blockIdx.x] = pr;
+    part[base + gridDim.x + blockIdx.x] = pp;
+  }
+}
+
+__global__ void k_mr_update_h(bf16c* __restrict__ x, bf16c* __restrict__ r,
+                              const bf16c* __restrict__ p, size_t n,
+                              const double2* __restrict__ PR, const double2* __restrict__ PP,
+                              double omega) {
+  const int v = blockIdx.y;
+  double2 a = make_double2(0.0, 0.0);
+  if ((threadIdx.x & 31) == 0) {
+    const double den = PP[v].x;
+    if (den > 0.0) {
+      const double f = omega / den;
+      a = make_double2(f * PR[v].x, f * PR[v].y);
+    }
+  }
+  a = warp_bcast(a);
+  const cpx<float> ar(float(a.x), float(a.y));
+  x += size_t(v) * n;
+  r += size_t(v) * n;
+  p += size_t(v) * n;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
+       i += size_t(gridDim.x) * blockDim.x) {
+    cpx<float> ri = h2f(r[i]), xi = h2f(x[i]);
+    cmac(xi, ar, ri);
+    cmac(ri, -ar, h2f(p[i]));
+    x[i] = StoreTraits<bf16c>::pack(xi);
+    r[i] = StoreTraits<bf16c>::pack(ri);
+  }
+}
+
 // ---- batched forms for the setup sweeps (nvec vectors back to back;
 // blockIdx.y is the vector)
 // x_v -= (B[2v] / B[2v+1].re) t_v
@@ -408,6 +474,18 @@ void blas_zero(mg_ctx* c, Vec v, cudaStream_t st) {
 
 void blas_copy(mg_ctx* c, Vec d, Vec s, cudaStream_t st) {
   GB_REQUIRE(d.total() == s.total(), MG_ERR_ARG, "copy: length mismatch");
+  if (d.prec != s.prec && (d.prec == MG_BF16 || s.prec == MG_BF16)) {
+    GB_REQUIRE(d.prec == MG_F32 || s.prec == MG_F32, MG_ERR_ARG, "copy: BF16 <-> FP32 only");
+    if (d.prec == MG_BF16)
+      k_copy_to16<<<ew_blocks(d.total()), kThreads, 0, st>>>((bf16c*)d.p,
+                                                             (const cpx<float>*)s.p, d.total());
+    else
+      k_copy_from16<<<ew_blocks(d.total()), kThreads, 0, st>>>((cpx<float>*)d.p,
+                                                               (const bf16c*)s.p, d.total());
+    GB_LAUNCH_CHECK();
+    c->launches++;
+    return;
+  }
   if (d.prec == s.prec) {
     GB_CHECK(cudaMemcpyAsync(d.p, s.p, d.total() * prec_bytes_complex(d.prec),
                              cudaMemcpyDeviceToDevice, st));
@@ -490,9 +568,15 @@ void blas_dot2(mg_ctx* c, Vec p, Vec r, int s_pr, int s_pp, cudaStream_t st) {
   GB_REQUIRE(p.n == r.n && p.nr == r.nr, MG_ERR_ARG, "dot2: shape mismatch");
   const int nb = red_blocks(p.n);
   double2* part = partials(c, size_t(nb) * 2 * p.nr);
-  GB_DISPATCH2(p.prec, Ra, r.prec, Rb,
-               (k_dot2_partial_b<Ra, Rb><<<dim3(nb, p.nr), kThreads, 0, st>>>(
-                   (const cpx<Ra>*)p.p, (const cpx<Rb>*)r.p, p.n, part)));
+  if (p.prec == MG_BF16 || r.prec == MG_BF16) {
+    GB_REQUIRE(p.prec == MG_BF16 && r.prec == MG_BF16, MG_ERR_ARG, "dot2: precision mix");
+    k_dot2_partial_h<<<dim3(nb, p.nr), kThreads, 0, st>>>((const bf16c*)p.p,
+                                                          (const bf16c*)r.p, p.n, part);
+  } else {
+    GB_DISPATCH2(p.prec, Ra, r.prec, Rb,
+                 (k_dot2_partial_b<Ra, Rb><<<dim3(nb, p.nr), kThreads, 0, st>>>(
+                     (const cpx<Ra>*)p.p, (const cpx<Rb>*)r.p, p.n, part)));
+  }
   GB_LAUNCH_CHECK();
   k_reduce_final_pair<<<2 * p.nr, 256, 0, st>>>(part, nb, srow(c, s_pr), srow(c, s_pp));
   GB_LAUNCH_CHECK();
@@ -503,6 +587,13 @@ void blas_mr_update(mg_ctx* c, Vec x, Vec r, Vec p, int s_pr, int s_pp, double o
                     cudaStream_t st) {
   check_nr(x);
   GB_REQUIRE(x.prec == r.prec && r.prec == p.prec, MG_ERR_ARG, "mr_update: precision mix");
+  if (x.prec == MG_BF16) {
+    k_mr_update_h<<<ew_grid_b(x.n, x.nr), kThreads, 0, st>>>(
+        (bf16c*)x.p, (bf16c*)r.p, (const bf16c*)p.p, x.n, srow(c, s_pr), srow(c, s_pp), omega);
+    GB_LAUNCH_CHECK();
+    c->launches++;
+    return;
+  }
   GB_DISPATCH1(x.prec, R,
                (k_mr_update<R><<<ew_grid_b(x.n, x.nr), kThreads, 0, st>>>(
                    (cpx<R>*)x.p, (cpx<R>*)r.p, (const cpx<R>*)p.p, x.n, srow(c, s_pr),

@@ -82,6 +82,9 @@ struct Level {
   // import: gauge12_ok)
   DevBuf gauge12;
   bool gauge12_ok = false;
+  // BF16 copy of the operator for a 16-bit fine-level smoother: links
+  // ([mu][V][6] two-row when gauge12_ok, else [mu][V][9]) and clover [V][72]
+  DevBuf gauge16, clover16;
   double diag = 0.0;           // 4 + m
 
   // coarse operator (level >= 1): internal layout [V][9][col][row] in vprec;

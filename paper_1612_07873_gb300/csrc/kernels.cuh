@@ -112,6 +112,13 @@ void eo_merge(mg_ctx* c, int level, Vec full, Vec he, Vec ho, cudaStream_t st);
 // out_e = A_e^-1 in_e
 void eo_ainv(mg_ctx* c, int level, Vec out, Vec in, cudaStream_t st);
 
+// ---------------------------------------------------------------- smoother16.cu
+// 16-bit fine-level smoother (params.prec_smoother = MG_BF16, FP32 fine level)
+bool smoother16_enabled(const mg_ctx* c);
+void smoother16_prepare(mg_ctx* c, cudaStream_t st);
+// out = M in on BF16 vectors (in.nr vectors back to back)
+void wilson16_apply(mg_ctx* c, Vec out, Vec in, cudaStream_t st);
+
 // ---------------------------------------------------------------- galerkin.cu
 void galerkin_build(mg_ctx* c, int level, cudaStream_t st);
 

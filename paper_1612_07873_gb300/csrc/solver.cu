@@ -25,6 +25,7 @@ struct mg_ctx::SolverWS {
     std::vector<std::unique_ptr<gbmg::DevBuf>> Z, W;
     gbmg::DevBuf r, x, rhs, tmp, kres, mrx, mrr, mrp;
     gbmg::DevBuf eo1, eo2, eo3;  // red-black: each holds two compact parity halves
+    gbmg::DevBuf s16x, s16r, s16p;  // 16-bit fine-level smoother (BF16 vectors)
     gbmg::DevBuf r64, tmp64;     // level 0 only
   };
   LevelWS lv[MG_MAX_LEVELS];
@@ -97,6 +98,11 @@ void ensure_ws(mg_ctx* c, int nr) {
     if (l == 0) {
       ensure(w.r64, L.vec_elems() * 16 * nr);
       ensure(w.tmp64, L.vec_elems() * 16 * nr);
+      if (smoother16_enabled(c)) {
+        ensure(w.s16x, L.vec_elems() * 4 * nr);
+        ensure(w.s16r, L.vec_elems() * 4 * nr);
+        ensure(w.s16p, L.vec_elems() * 4 * nr);
+      }
     }
   }
   ws.nk = nk;
@@ -114,6 +120,21 @@ std::vector<double> read_slot(mg_ctx* c, int s, int nr, cudaStream_t st) {
 void mr_smooth(mg_ctx* c, int l, Vec x, Vec b, cudaStream_t st) {
   auto& w = c->ws->lv[l];
   Level& L = c->L[l];
+  if (l == 0 && smoother16_enabled(c)) {
+    // the same MR steps on BF16 vectors with the BF16 copy of the operator
+    Vec x16 = vbuf(w.s16x, MG_BF16, L.vec_elems(), x.nr);
+    Vec r16 = vbuf(w.s16r, MG_BF16, L.vec_elems(), x.nr);
+    Vec p16 = vbuf(w.s16p, MG_BF16, L.vec_elems(), x.nr);
+    blas_zero(c, x16, st);
+    blas_copy(c, r16, b, st);
+    for (int k = 0; k < c->p.mr_iters; ++k) {
+      wilson16_apply(c, p16, r16, st);
+      blas_dot2(c, p16, r16, slot(l, S_PR), slot(l, S_PP), st);
+      blas_mr_update(c, x16, r16, p16, slot(l, S_PR), slot(l, S_PP), c->p.mr_omega, st);
+    }
+    blas_copy(c, x, x16, st);
+    return;
+  }
   Vec r = vbuf(w.mrr, L.vprec, L.vec_elems(), x.nr);
   Vec p = vbuf(w.mrp, L.vprec, L.vec_elems(), x.nr);
   blas_zero(c, x, st);
