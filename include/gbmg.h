@@ -20,7 +20,9 @@
  *                     diag(1, 1, -1, -1): spins {0,1} = chirality 0.
  * Coarse spinor       [site][dof] complex, dof = s*Nv + c, s the chirality
  *                     (Sec. 6.2), 2*Nv dofs per site.
- * Multi-RHS spinor    [site][dof][rhs] complex.
+ * Multi-RHS spinor    [site][dof][rhs] complex (mg_coarse_apply, nrhs > 1);
+ *                     the multi-RHS solve and fine apply take the vectors
+ *                     back to back instead, [rhs][site][dof].
  * Complex numbers     interleaved (re, im).
  * Gauge field         [mu][site][3][3] complex double (row-major SU(3)).
  * Coarse links        [site][slot 0..8][row][col] complex double, the

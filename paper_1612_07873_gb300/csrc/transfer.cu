@@ -2,8 +2,9 @@
 // split of its footnote) and the transfer operators of Sec. 6.6.
 //
 // For aggregate A and chirality s the (|A| * nd/2) x Nv block of chirality-s
-// components is orthonormalised by modified Gram-Schmidt with every
-// projection done twice, in FP64.  Rows are ordered (site of A in
+// components is orthonormalised column by column by Gram-Schmidt in FP64
+// (projection repeated when the first one cancels more than half of the
+// column's squared norm; see k_block_qr).  Rows are ordered (site of A in
 // lexicographic order, dof of chirality s).  The prolongator column (s, i)
 // is vector i of the result restricted to chirality s; coarse dof = s*Nv + i.
 //
