@@ -102,6 +102,7 @@ struct Level {
   DevBuf raw;                  // FP64 [Nv][V][nd] raw null vectors
   DevBuf orth64;               // FP64 block-orthonormalised, [agg][chi][Nv][rows]
   DevBuf Vp;                   // vprec [V][nd][Nv] (transfer operator layout)
+  DevBuf Vp16;                 // BF16 copy of Vp for the fine-level transfers (16-bit smoother)
 
   // red-black preconditioning: A_e^-1 on the even sites (fine: packed
   // Hermitian 6x6 chirality blocks, [V/2][72] reals; coarse: [V/2][col][row]

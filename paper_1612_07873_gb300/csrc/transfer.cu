@@ -341,6 +341,24 @@ __device__ __forceinline__ int local_offset(const AggMap& m, int ls) {
   return l0 + m.fine.stride[1] * l1 + m.fine.stride[2] * l2 + m.fine.stride[3] * l3;
 }
 
+// A 16-byte word of Vp as CPL complex numbers in the fine vector precision:
+// Vp stored in the vector precision, or in BF16 (the fine-level copy used
+// when the fine smoother runs in 16 bits).
+template <typename VT, typename Rf>
+struct VUnpack {
+  static constexpr int CPL = 16 / int(sizeof(VT));
+  __device__ static __forceinline__ void get(const uint4& w, cpx<Rf> out[CPL]) {
+    if constexpr (std::is_same<VT, bf16c>::value) {
+#pragma unroll
+      for (int k = 0; k < CPL; ++k)
+        out[k] = cpx<Rf>(StoreTraits<bf16c>::load(reinterpret_cast<const bf16c*>(&w)[k]));
+    } else {
+#pragma unroll
+      for (int k = 0; k < CPL; ++k) out[k] = reinterpret_cast<const cpx<Rf>*>(&w)[k];
+    }
+  }
+};
+
 // coarse_v[xc][chi*Nv + i] = sum over fine sites x of the aggregate and dofs
 // a of chirality chi of conj(Vp[x][a][i]) fine_v[x][a], for NRB right-hand
 // sides v per CTA.  Thread (g, p): p picks the 16-byte column of Vp rows (CPL
@@ -348,13 +366,13 @@ __device__ __forceinline__ int local_offset(const AggMap& m, int ls) {
 // right-hand sides.  CTA b: aggregate b / nchunk, right-hand-side chunk
 // b % nchunk (chunks of one aggregate run side by side and share its Vp
 // rows through L2).
-template <typename Rf, typename Rc, int NRB>
+template <typename Rf, typename Rc, int NRB, typename VT>
 __global__ void __launch_bounds__(256) k_restrict12(cpx<Rc>* __restrict__ coarse,
                                                    const cpx<Rf>* __restrict__ fine,
-                                                   const cpx<Rf>* __restrict__ Vp, AggMap m,
+                                                   const VT* __restrict__ Vp, AggMap m,
                                                    int nv, int G, int nchunk, size_t fstride,
                                                    size_t cstride) {
-  constexpr int ND = 12, CPL = 16 / int(sizeof(cpx<Rf>));
+  constexpr int ND = 12, CPL = VUnpack<VT, Rf>::CPL;
   constexpr int FW = ND * int(sizeof(cpx<Rf>)) / 16;  // 16-byte words of a fine site
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<Rf>* red = reinterpret_cast<cpx<Rf>*>(smem_raw);  // [G][2][nv]
@@ -388,7 +406,8 @@ __global__ void __launch_bounds__(256) k_restrict12(cpx<Rc>* __restrict__ coarse
         const cpx<Rf>* f = reinterpret_cast<const cpx<Rf>*>(fw);
 #pragma unroll
         for (int a = 0; a < ND; ++a) {
-          const cpx<Rf>* v = reinterpret_cast<const cpx<Rf>*>(&w[a]);
+          cpx<Rf> v[CPL];
+          VUnpack<VT, Rf>::get(w[a], v);
 #pragma unroll
           for (int k = 0; k < CPL; ++k) cmac_conj(acc[b][a < ND / 2 ? 0 : 1][k], v[k], f[a]);
         }
@@ -418,13 +437,13 @@ __global__ void __launch_bounds__(256) k_restrict12(cpx<Rc>* __restrict__ coarse
 // registers for every right-hand side: thread q takes the 16-byte words
 // 2k + q, so a pair reads whole 32-byte sectors; the halves meet by one
 // shuffle.
-template <typename Rf, typename Rc>
+template <typename Rf, typename Rc, typename VT>
 __global__ void __launch_bounds__(256) k_prolong12(cpx<Rf>* __restrict__ fine,
                                                   const cpx<Rc>* __restrict__ coarse,
-                                                  const cpx<Rf>* __restrict__ Vp, AggMap m,
+                                                  const VT* __restrict__ Vp, AggMap m,
                                                   int nv, int nr, size_t fstride,
                                                   size_t cstride) {
-  constexpr int ND = 12, CPL = 16 / int(sizeof(cpx<Rf>));
+  constexpr int ND = 12, CPL = VUnpack<VT, Rf>::CPL;
   constexpr int MAXPW = 12;  // Nv <= 48 (FP32) / 24 (FP64)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<Rf>* cs = reinterpret_cast<cpx<Rf>*>(smem_raw);  // [nr][2][nv]
@@ -459,7 +478,8 @@ __global__ void __launch_bounds__(256) k_prolong12(cpx<Rf>* __restrict__ fine,
 #pragma unroll
       for (int k = 0; k < MAXPW; ++k)
         if (ok && k < PW) {
-          const cpx<Rf>* v = reinterpret_cast<const cpx<Rf>*>(&w[k]);
+          cpx<Rf> v[CPL];
+          VUnpack<VT, Rf>::get(w[k], v);
 #pragma unroll
           for (int j = 0; j < CPL; ++j) cmac(acc, v[j], c[2 * k * CPL + j]);
         }
@@ -526,6 +546,19 @@ void block_orthonormalise(mg_ctx* c, int level, cudaStream_t st) {
     k_mgs_scatter<float><<<grid_for(elems), 256, 0, st>>>(F.Vp.as<cpx<float>>(), W, m, nd, nv);
   GB_LAUNCH_CHECK();
   c->launches += 3;
+  if (level == 0 && F.vprec == MG_F32 && smoother16_enabled(c)) {
+    // the fine-level transfers read a BF16 copy (the Galerkin build keeps Vp)
+    F.Vp16.alloc(elems * 4);
+    Vec src, dst;
+    src.p = F.Vp.p;
+    src.prec = MG_F32;
+    dst.p = F.Vp16.p;
+    dst.prec = MG_BF16;
+    src.n = dst.n = elems;
+    blas_copy(c, dst, src, st);
+  } else {
+    F.Vp16.release();
+  }
   if (read_status(c, st) & 1) {
     F.have_V = false;
     throw Error(MG_ERR_RANK, "rank-deficient null-vector aggregate block");
@@ -535,27 +568,27 @@ void block_orthonormalise(mg_ctx* c, int level, cudaStream_t st) {
 
 namespace {
 
-template <typename Rf, typename Rc>
+template <typename Rf, typename Rc, typename VT = cpx<Rf>>
 void launch_restrict12(int nrb, dim3 grid, int thr, size_t smem, cudaStream_t st, Vec coarse,
                        Vec fine, const void* Vp, const AggMap& m, int nv, int G, int nchunk) {
   auto* cp = (cpx<Rc>*)coarse.p;
   auto* fp = (const cpx<Rf>*)fine.p;
-  auto* vp = (const cpx<Rf>*)Vp;
+  auto* vp = (const VT*)Vp;
   switch (nrb) {
     case 8:
-      k_restrict12<Rf, Rc, 8><<<grid, thr, smem, st>>>(cp, fp, vp, m, nv, G, nchunk, fine.n,
+      k_restrict12<Rf, Rc, 8, VT><<<grid, thr, smem, st>>>(cp, fp, vp, m, nv, G, nchunk, fine.n,
                                                         coarse.n);
       break;
     case 4:
-      k_restrict12<Rf, Rc, 4><<<grid, thr, smem, st>>>(cp, fp, vp, m, nv, G, nchunk, fine.n,
+      k_restrict12<Rf, Rc, 4, VT><<<grid, thr, smem, st>>>(cp, fp, vp, m, nv, G, nchunk, fine.n,
                                                         coarse.n);
       break;
     case 2:
-      k_restrict12<Rf, Rc, 2><<<grid, thr, smem, st>>>(cp, fp, vp, m, nv, G, nchunk, fine.n,
+      k_restrict12<Rf, Rc, 2, VT><<<grid, thr, smem, st>>>(cp, fp, vp, m, nv, G, nchunk, fine.n,
                                                         coarse.n);
       break;
     default:
-      k_restrict12<Rf, Rc, 1><<<grid, thr, smem, st>>>(cp, fp, vp, m, nv, G, nchunk, fine.n,
+      k_restrict12<Rf, Rc, 1, VT><<<grid, thr, smem, st>>>(cp, fp, vp, m, nv, G, nchunk, fine.n,
                                                         coarse.n);
       break;
   }
@@ -596,13 +629,15 @@ void restrict_apply(mg_ctx* c, int level, Vec coarse, Vec fine, cudaStream_t st)
   AggMap m = make_map(F, C);
   const int nv = F.nvec, nr = fine.nr;
   const double vb = prec_bytes_complex(F.vprec);
+  const bool h16 = F.Vp16.p && F.vprec == MG_F32 && F.nd == 12 && nv % 4 == 0;
   ProfScope ps(c->prof, st, "restrict", level,
-               double(F.g.vol) * F.nd * (nv + nr) * vb + double(C.g.vol) * C.nd * nr * vb,
+               double(F.g.vol) * F.nd * (nv * (h16 ? 4.0 : vb) + nr * vb) +
+                   double(C.g.vol) * C.nd * nr * vb,
                8.0 * F.g.vol * F.nd * nv * nr);
   if (F.nd == 12) {
     // per-aggregate kernel: NP 16-byte columns per Vp row, G site groups,
     // NRB right-hand sides per CTA
-    const int cpl = F.vprec == MG_F64 ? 1 : 2;
+    const int cpl = h16 ? 4 : F.vprec == MG_F64 ? 1 : 2;
     const int NP = nv / cpl;
     int G2 = 256 / NP;
     while (G2 > 1 && m.per % G2) --G2;
@@ -619,13 +654,22 @@ void restrict_apply(mg_ctx* c, int level, Vec coarse, Vec fine, cudaStream_t st)
       auto launch = [&](int nrb) {
         const int nchunk = nr / nrb;
         const dim3 grid(unsigned(C.g.vol) * nchunk);
-        GB_TRANSFER_DISPATCH(F.vprec, coarse.prec, Rf, Rc,
-                             (launch_restrict12<Rf, Rc>(nrb, grid, G2 * NP, smem2, st, coarse,
-                                                        fine, F.Vp.p, m, nv, G2, nchunk)));
+        if (h16) {
+          if (coarse.prec == MG_F64)
+            launch_restrict12<float, double, bf16c>(nrb, grid, G2 * NP, smem2, st, coarse, fine,
+                                                    F.Vp16.p, m, nv, G2, nchunk);
+          else
+            launch_restrict12<float, float, bf16c>(nrb, grid, G2 * NP, smem2, st, coarse, fine,
+                                                   F.Vp16.p, m, nv, G2, nchunk);
+        } else {
+          GB_TRANSFER_DISPATCH(F.vprec, coarse.prec, Rf, Rc,
+                               (launch_restrict12<Rf, Rc>(nrb, grid, G2 * NP, smem2, st, coarse,
+                                                          fine, F.Vp.p, m, nv, G2, nchunk)));
+        }
       };
-      const std::string key = "restrict12/p" + std::to_string(int(F.vprec)) + "/v" +
-                              std::to_string(F.g.vol) + "/nv" + std::to_string(nv) + "/r" +
-                              std::to_string(nr);
+      const std::string key = "restrict12/p" + std::to_string(int(F.vprec)) + "/h" +
+                              std::to_string(int(h16)) + "/v" + std::to_string(F.g.vol) +
+                              "/nv" + std::to_string(nv) + "/r" + std::to_string(nr);
       launch(Tuner::get().choose(key, cands, st, launch));
       GB_LAUNCH_CHECK();
       c->launches++;
@@ -656,15 +700,28 @@ void prolong_apply(mg_ctx* c, int level, Vec fine, Vec coarse, cudaStream_t st) 
   const int nv = F.nvec, nr = fine.nr;
   const size_t n = size_t(F.g.vol) * F.nd;
   const double vb = prec_bytes_complex(F.vprec);
+  const bool h16 = F.Vp16.p && F.vprec == MG_F32 && F.nd == 12 && nv % 8 == 0;
   ProfScope ps(c->prof, st, "prolong", level,
-               double(n) * (nv + nr) * vb + double(C.g.vol) * C.nd * nr * vb, 8.0 * n * nv * nr);
-  const int cpl = F.vprec == MG_F64 ? 1 : 2;
+               double(n) * (nv * (h16 ? 4.0 : vb) + nr * vb) + double(C.g.vol) * C.nd * nr * vb,
+               8.0 * n * nv * nr);
+  const int cpl = h16 ? 4 : F.vprec == MG_F64 ? 1 : 2;
   const size_t smem2 = size_t(nr) * 2 * nv * size_t(vb) + size_t(m.per) * sizeof(int);
   if (F.nd == 12 && nv % (2 * cpl) == 0 && nv / (2 * cpl) <= 12 && smem2 <= 48 * 1024) {
-    GB_TRANSFER_DISPATCH(F.vprec, coarse.prec, Rf, Rc,
-                         (k_prolong12<Rf, Rc><<<C.g.vol, 256, smem2, st>>>(
-                             (cpx<Rf>*)fine.p, (const cpx<Rc>*)coarse.p, F.Vp.as<cpx<Rf>>(), m,
-                             nv, nr, fine.n, coarse.n)));
+    if (h16) {
+      if (coarse.prec == MG_F64)
+        k_prolong12<float, double, bf16c><<<C.g.vol, 256, smem2, st>>>(
+            (cpx<float>*)fine.p, (const cpx<double>*)coarse.p, F.Vp16.as<bf16c>(), m, nv, nr,
+            fine.n, coarse.n);
+      else
+        k_prolong12<float, float, bf16c><<<C.g.vol, 256, smem2, st>>>(
+            (cpx<float>*)fine.p, (const cpx<float>*)coarse.p, F.Vp16.as<bf16c>(), m, nv, nr,
+            fine.n, coarse.n);
+    } else {
+      GB_TRANSFER_DISPATCH(F.vprec, coarse.prec, Rf, Rc,
+                           (k_prolong12<Rf, Rc, cpx<Rf>><<<C.g.vol, 256, smem2, st>>>(
+                               (cpx<Rf>*)fine.p, (const cpx<Rc>*)coarse.p, F.Vp.as<cpx<Rf>>(),
+                               m, nv, nr, fine.n, coarse.n)));
+    }
     GB_LAUNCH_CHECK();
     c->launches++;
     return;

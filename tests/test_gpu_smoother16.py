@@ -76,3 +76,29 @@ def test_bf16_smoother_needs_fp32_fine_level(gpu_lib):
     with pytest.raises(gb.MGError) as e:
         gb.Multigrid(p, to_dev(U))
     assert e.value.status == gb.MG_ERR_ARG
+
+
+@pytest.mark.parametrize("nv", [24, 8])
+def test_bf16_prolongator_transfers(gpu_lib, nv):
+    """With the 16-bit smoother the fine-level restrict / prolong read a BF16
+    copy of the prolongator (the Galerkin build keeps FP32)."""
+    from oracle import multigrid as mgo
+    gb = gpu_lib
+    dims, block = (8, 4, 4, 8), (4, 4, 4, 4)
+    U = syn.gauge_field(dims, 0.4, 6)
+    mg, _ = _ctx(gb, dims, [block], [nv], U=U)
+    vol = lat.volume(dims)
+    v = syn.gaussian_field((nv, vol, 12), 113)
+    gb.mg_set_nullvecs(mg.ctx, 0, to_dev(v))
+    Q = mgo.block_orthonormalise(v, dims, block)
+    cd = lat.coarse_dims(dims, block)
+    r = syn.gaussian_field((vol, 12), 114)
+    rc = torch.empty((lat.volume(cd), 2 * nv), dtype=torch.complex64, device="cuda")
+    gb.mg_restrict(mg.ctx, 0, rc, to_dev(r, torch.complex64))
+    ec = syn.gaussian_field((lat.volume(cd), 2 * nv), 115)
+    e = torch.empty((vol, 12), dtype=torch.complex64, device="cuda")
+    gb.mg_prolong(mg.ctx, 0, e, to_dev(ec, torch.complex64))
+    torch.cuda.synchronize()
+    assert rel_l2(to_np(rc), mgo.restrict(Q, r, dims, block)) < 5e-3
+    assert rel_l2(to_np(e), mgo.prolong(Q, ec, dims, block)) < 5e-3
+    mg.close()
