@@ -262,6 +262,20 @@ mg_status mg_profile_reset(mg_ctx* ctx);
 mg_status mg_profile_query(mg_ctx* ctx, const char* name, int level, int* launches,
                            double* total_ms, double* bytes, double* flops);
 
+/* Checkpoint of the setup (the setup is amortised over many solves, Sec.
+ * 7.1): mg_save writes the block-orthonormal null vectors of every
+ * coarsening and the links of every coarse level to `path` (one JSON
+ * header line with lattice, blocks, nvec, precisions, seed, record sizes
+ * and an FNV-1a 64 checksum, then raw little-endian complex doubles);
+ * MG_ERR_STATE unless every level is set up.  mg_load restores them into a
+ * context created with the same lattice, blocks, nvec and precisions
+ * (MG_ERR_ARG on a mismatch, a short file or a bad checksum): the
+ * prolongators are rebuilt from the vectors and the coarse operators taken
+ * from the file, so a solve can follow without setup sweeps or Galerkin
+ * builds.                                                                  */
+mg_status mg_save(mg_ctx* ctx, const char* path);
+mg_status mg_load(mg_ctx* ctx, const char* path);
+
 /* Launch-policy autotuner (process-wide).  The first call of a tuned kernel
  * for a shape times its candidate policies and keeps the fastest; keys name
  * the kernel and shape, e.g. "wilson/v<volume>/n<vectors>/c<0|1>".

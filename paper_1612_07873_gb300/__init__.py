@@ -21,10 +21,14 @@ F64, F32, BF16, F16, I16 = 0, 1, 2, 3, 4
 STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "out of device memory",
           -4: "call out of order", -5: "solver did not converge", -6: "numerical breakdown",
           -7: "device wait timed out", -8: "rank-deficient null-vector block"}
-MG_ERR_NOT_CONVERGED = -5
-MG_ERR_RANK = -8
 MG_ERR_ARG = -1
+MG_ERR_CUDA = -2
+MG_ERR_OOM = -3
 MG_ERR_STATE = -4
+MG_ERR_NOT_CONVERGED = -5
+MG_ERR_NUMERICAL = -6
+MG_ERR_TIMEOUT = -7
+MG_ERR_RANK = -8
 
 
 class mg_params(C.Structure):
@@ -88,6 +92,8 @@ def _load():
         "mg_gcr_solve": (i, [vp, vp, vp, d, i, C.POINTER(mg_solve_stats), vp]),
         "mg_gcr_solve_multi": (i, [vp, vp, vp, i, d, i, C.POINTER(mg_solve_stats), vp]),
         "mg_tune_set": (i, [C.c_char_p, i]),
+        "mg_save": (i, [vp, C.c_char_p]),
+        "mg_load": (i, [vp, C.c_char_p]),
         "mg_wilson_clover_apply_multi": (i, [vp, vp, vp, i, vp]),
         "mg_wilson_clover_apply_bf16": (i, [vp, vp, vp, i, vp]),
         "mg_schur_apply": (i, [vp, i, vp, vp, i, vp]),
@@ -258,6 +264,16 @@ def mg_gcr_solve_multi(ctx, x, b, nrhs, tol=1e-10, maxiter=200, stream=None, che
 def mg_schur_apply(ctx, level, y, x, nrhs=1, stream=None):
     """y_o = S x_o on compact odd-parity vectors [nrhs][V/2][ndof]."""
     _ok(LIB.mg_schur_apply(ctx, level, _ptr(y), _ptr(x), nrhs, _stream(stream)), ctx)
+
+
+def mg_save(ctx, path):
+    """Write the setup (null vectors, coarse links) of every level to path."""
+    _ok(LIB.mg_save(ctx, str(path).encode()), ctx)
+
+
+def mg_load(ctx, path):
+    """Restore a setup written by mg_save into a matching context."""
+    _ok(LIB.mg_load(ctx, str(path).encode()), ctx)
 
 
 def mg_tune_set(key, choice):

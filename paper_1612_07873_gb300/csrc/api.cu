@@ -1,7 +1,12 @@
 // extern "C" entry points of libgbmg.so (declared in include/gbmg.h):
 // argument checks, context lifecycle, error reporting, kernel timing.
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
+#include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "kernels.cuh"
 #include "tune.cuh"
@@ -64,9 +69,14 @@ Profiler::~Profiler() {
   clear();
   for (auto e : pool) cudaEventDestroy(e);
 }
+// Every scope is also an NVTX range ("<kernel class> L<level>"), visible to
+// Nsight tools whether or not the event timing is enabled.
 ProfScope::ProfScope(Profiler& p, cudaStream_t s, const char* name, int level, double bytes,
                      double flops)
     : prof(&p), st(s), active(p.on) {
+  char label[64];
+  std::snprintf(label, sizeof(label), "%s L%d", name, level);
+  nvtxRangePushA(label);
   if (!active) return;
   rec.name = name;
   rec.level = level;
@@ -77,6 +87,7 @@ ProfScope::ProfScope(Profiler& p, cudaStream_t s, const char* name, int level, d
   cudaEventRecord(rec.start, st);
 }
 ProfScope::~ProfScope() {
+  nvtxRangePop();
   if (!active) return;
   cudaEventRecord(rec.stop, st);
   prof->recs.push_back(rec);
@@ -375,6 +386,141 @@ mg_status mg_schur_apply(mg_ctx* c, int level, void* y, const void* x, int nrhs,
     eo_apply(c, level, EO_AINV_HOP, vt, vx, nullptr, 0, S(stream));
     eo_apply(c, level, EO_A_XC_MINUS_HOP, vy, vt, x, 1, S(stream));
     GB_CHECK(cudaStreamSynchronize(S(stream)));
+  });
+}
+
+// ---- checkpoint of the setup: the block-orthonormal null vectors of every
+// coarsening and the coarse links of every coarse level.  File: one JSON
+// header line (format, lattice, blocks, nvec, precisions, seed, the byte
+// count of every record, FNV-1a 64 checksum of the payload), then the raw
+// little-endian records: for l = 0 .. nlevels-2 the null vectors
+// [Nv][V][nd] complex double of level l, then the links [V][9][n][n]
+// complex double of level l + 1.
+namespace {
+
+uint64_t fnv1a(const unsigned char* p, size_t n, uint64_t h) {
+  for (size_t i = 0; i < n; ++i) {
+    h ^= p[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+std::string header_json(const mg_ctx* c, const std::vector<size_t>& sizes, uint64_t sum) {
+  std::string j = "{\"format\": \"gbmg-setup-1\", \"dims\": [";
+  for (int m = 0; m < 4; ++m) j += std::to_string(c->p.dims[m]) + (m < 3 ? ", " : "]");
+  j += ", \"nlevels\": " + std::to_string(c->nlevels) + ", \"blocks\": [";
+  for (int l = 0; l + 1 < c->nlevels; ++l) {
+    j += "[";
+    for (int m = 0; m < 4; ++m) j += std::to_string(c->p.block[l][m]) + (m < 3 ? ", " : "]");
+    j += l + 2 < c->nlevels ? ", " : "";
+  }
+  j += "], \"nvec\": [";
+  for (int l = 0; l + 1 < c->nlevels; ++l)
+    j += std::to_string(c->p.nvec[l]) + (l + 2 < c->nlevels ? ", " : "");
+  j += "], \"prec_fine\": " + std::to_string(int(c->p.prec_fine)) +
+       ", \"prec_coarse\": " + std::to_string(int(c->p.prec_coarse)) +
+       ", \"seed\": " + std::to_string(c->p.seed) + ", \"records\": [";
+  for (size_t i = 0; i < sizes.size(); ++i)
+    j += std::to_string(sizes[i]) + (i + 1 < sizes.size() ? ", " : "");
+  j += "], \"fnv1a64\": \"" + std::to_string(sum) + "\"}\n";
+  return j;
+}
+
+}  // namespace
+
+mg_status mg_save(mg_ctx* c, const char* path) {
+  return guarded(c, [&] {
+    GB_REQUIRE(path, MG_ERR_ARG, "save: null path");
+    std::vector<std::vector<unsigned char>> recs;
+    for (int l = 0; l + 1 < c->nlevels; ++l) {
+      Level& F = c->L[l];
+      Level& C = c->L[l + 1];
+      GB_REQUIRE(F.have_V && C.have_op, MG_ERR_STATE, "save: setup of every level required");
+      const size_t nb = size_t(F.nvec) * F.vec_elems() * 16;
+      const size_t lb = size_t(C.g.vol) * 9 * C.nd * C.nd * 16;
+      DevBuf tmp;
+      tmp.alloc(nb > lb ? nb : lb);
+      recs.emplace_back(nb);
+      nullvecs_export(c, l, tmp.p, 0);
+      GB_CHECK(cudaMemcpy(recs.back().data(), tmp.p, nb, cudaMemcpyDeviceToHost));
+      recs.emplace_back(lb);
+      links_export(c, l + 1, tmp.p, 0);
+      GB_CHECK(cudaMemcpy(recs.back().data(), tmp.p, lb, cudaMemcpyDeviceToHost));
+    }
+    uint64_t sum = 1469598103934665603ull;
+    std::vector<size_t> sizes;
+    for (auto& r : recs) {
+      sum = fnv1a(r.data(), r.size(), sum);
+      sizes.push_back(r.size());
+    }
+    FILE* f = std::fopen(path, "wb");
+    GB_REQUIRE(f, MG_ERR_ARG, "save: cannot open the file");
+    const std::string h = header_json(c, sizes, sum);
+    bool ok = std::fwrite(h.data(), 1, h.size(), f) == h.size();
+    for (auto& r : recs) ok = ok && std::fwrite(r.data(), 1, r.size(), f) == r.size();
+    ok = (std::fclose(f) == 0) && ok;
+    GB_REQUIRE(ok, MG_ERR_ARG, "save: write failed");
+  });
+}
+
+mg_status mg_load(mg_ctx* c, const char* path) {
+  return guarded(c, [&] {
+    GB_REQUIRE(path, MG_ERR_ARG, "load: null path");
+    FILE* f = std::fopen(path, "rb");
+    GB_REQUIRE(f, MG_ERR_ARG, "load: cannot open the file");
+    std::string h;
+    for (int ch; (ch = std::fgetc(f)) != EOF && ch != '\n';) h.push_back(char(ch));
+    std::vector<size_t> want;
+    for (int l = 0; l + 1 < c->nlevels; ++l) {
+      want.push_back(size_t(c->L[l].nvec) * c->L[l].vec_elems() * 16);
+      const Level& C = c->L[l + 1];
+      want.push_back(size_t(C.g.vol) * 9 * C.nd * C.nd * 16);
+    }
+    // the header must describe this context (lattice, levels, blocks, nvec,
+    // precisions; the seed may differ): compare with the one it would write
+    const std::string key_seed = ", \"seed\": ", key_sum = ", \"fnv1a64\": \"";
+    const std::string key_rec = "\"records\": [";
+    const std::string mine = header_json(c, want, 0);
+    const size_t cut = mine.find(key_seed), at = h.find(key_sum);
+    const size_t r0 = mine.find(key_rec) + key_rec.size();
+    const std::string records = key_rec + mine.substr(r0, mine.find(']', r0) + 1 - r0);
+    bool match = at != std::string::npos && h.size() > at + key_sum.size() + 2 &&
+                 h.compare(0, cut, mine, 0, cut) == 0 && h.find(records) != std::string::npos;
+    uint64_t sum_file = 0;
+    if (match) {
+      const std::string digits = h.substr(at + key_sum.size(), h.size() - at - key_sum.size() - 2);
+      match = !digits.empty() && digits.find_first_not_of("0123456789") == std::string::npos;
+      if (match) sum_file = std::strtoull(digits.c_str(), nullptr, 10);
+    }
+    if (!match) std::fclose(f);
+    GB_REQUIRE(match, MG_ERR_ARG, "load: file does not match the context's lattice and setup");
+    std::vector<std::vector<unsigned char>> recs;
+    uint64_t sum = 1469598103934665603ull;
+    bool ok = true;
+    for (size_t n : want) {
+      recs.emplace_back(n);
+      ok = ok && std::fread(recs.back().data(), 1, n, f) == n;
+      if (ok) sum = fnv1a(recs.back().data(), n, sum);
+    }
+    std::fclose(f);
+    GB_REQUIRE(ok, MG_ERR_ARG, "load: file truncated");
+    GB_REQUIRE(sum == sum_file, MG_ERR_ARG, "load: checksum mismatch");
+    for (int l = 0; l + 1 < c->nlevels; ++l) {
+      Level& F = c->L[l];
+      const auto& nvr = recs[2 * l];
+      F.raw.alloc(nvr.size());
+      GB_CHECK(cudaMemcpy(F.raw.p, nvr.data(), nvr.size(), cudaMemcpyHostToDevice));
+      F.have_raw = true;
+      block_orthonormalise(c, l, 0);
+      const auto& lr = recs[2 * l + 1];
+      DevBuf tmp;
+      tmp.alloc(lr.size());
+      GB_CHECK(cudaMemcpy(tmp.p, lr.data(), lr.size(), cudaMemcpyHostToDevice));
+      links_import(c, l + 1, tmp.p, 0);
+      if (c->p.red_black) schur_prepare(c, l + 1, 0);
+      GB_CHECK(cudaDeviceSynchronize());
+    }
   });
 }
 
