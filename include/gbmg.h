@@ -350,6 +350,16 @@ mg_status mg_cnn_adam_step(mg_cnn* net, float lr, void* stream);
  * is cleared.                                                              */
 mg_status mg_device_status(mg_ctx* ctx, void* stream);
 
+/* Host-side fault injection for tests of the error paths (no fault of the
+ * GPU is made).  what = "coarse_mma_wait": the next `count` tensor-core
+ * multi-RHS launches of this context (mg_coarse_apply with nrhs > 1 on
+ * 16-bit links, or mg_coarse_apply_multi with ctx first) wait, before any
+ * MMA, on an mbarrier that nothing arrives at; the wait gives up after its
+ * one-second budget, the launch writes no output, and the next
+ * mg_device_status returns MG_ERR_TIMEOUT.  MG_ERR_ARG for another name or
+ * count outside 0..1000; count = 0 cancels.                               */
+mg_status mg_inject_fault(mg_ctx* ctx, const char* what, int count);
+
 /* Number of kernels the library has launched since creation.              */
 long long mg_launch_count(mg_ctx* ctx);
 

@@ -94,6 +94,7 @@ def _load():
         "mg_tune_set": (i, [C.c_char_p, i]),
         "mg_save": (i, [vp, C.c_char_p]),
         "mg_load": (i, [vp, C.c_char_p]),
+        "mg_inject_fault": (i, [vp, C.c_char_p, i]),
         "mg_wilson_clover_apply_multi": (i, [vp, vp, vp, i, vp]),
         "mg_wilson_clover_apply_bf16": (i, [vp, vp, vp, i, vp]),
         "mg_schur_apply": (i, [vp, i, vp, vp, i, vp]),
@@ -336,6 +337,11 @@ def mg_block_orthonormalise_noalloc(vecs, out, dims, block, stream=None):
 
 def mg_device_status(ctx, stream=None):
     _ok(LIB.mg_device_status(ctx, _stream(stream)), ctx)
+
+
+def mg_inject_fault(ctx, what, count=1):
+    """Host-side fault injection for error-path tests ("coarse_mma_wait")."""
+    _ok(LIB.mg_inject_fault(ctx, what.encode(), count), ctx)
 
 
 def mg_coarse_apply_multi(ctxs, levels, ys, xs, nrhs, stream=None):

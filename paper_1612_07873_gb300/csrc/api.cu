@@ -611,6 +611,15 @@ mg_status mg_device_status(mg_ctx* c, void* stream) {
   });
 }
 
+mg_status mg_inject_fault(mg_ctx* c, const char* what, int count) {
+  return guarded(c, [&] {
+    GB_REQUIRE(what && count >= 0 && count <= 1000, MG_ERR_ARG, "inject_fault: bad arguments");
+    GB_REQUIRE(std::string(what) == "coarse_mma_wait", MG_ERR_ARG,
+               "inject_fault: unknown fault (known: coarse_mma_wait)");
+    c->inject_mma_stall = count;
+  });
+}
+
 long long mg_launch_count(mg_ctx* c) { return c ? c->launches : 0; }
 
 const char* mg_status_string(mg_status s) {

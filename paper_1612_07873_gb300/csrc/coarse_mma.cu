@@ -57,10 +57,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait; false on timeout
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// bounded wait: false once one second has passed on the global timer (or
+// after 2^24 polls, whichever comes first)
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (uint32_t it = 0; it < (1u << 24); ++it)
+  constexpr uint64_t kBudgetNs = 1000000000ull;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 0; it < (1u << 24); ++it) {
     if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 255u && global_ns() - t0 > kBudgetNs) return false;
+  }
   return false;
 }
 __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
@@ -158,6 +168,9 @@ struct MmaBatch {
   MmaLattice lat[kMaxBatch];
   int count;
   int total;
+  // fault injection (host-set, for tests of the timeout path): every CTA
+  // first waits on a barrier that nothing arrives at, before any MMA
+  int stall;
 };
 
 template <bool BF16, int N>
@@ -174,7 +187,7 @@ __global__ void __launch_bounds__(128) k_coarse_mma(const MmaBatch batch, int nr
   constexpr uint32_t IDESC = mma_idesc(128, N, BF16);
   constexpr uint32_t TMEM_COLS = N <= 32 ? 32 : (N <= 64 ? 64 : 128);
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ uint64_t mbar[2];
+  __shared__ uint64_t mbar[3];
   __shared__ uint32_t tmem_base_sh;
   __shared__ int nb_sh[9];
   __shared__ int abort_sh;
@@ -191,6 +204,7 @@ __global__ void __launch_bounds__(128) k_coarse_mma(const MmaBatch batch, int nr
   if (tid == 0) {
     mbar_init(&mbar[0], 1);
     mbar_init(&mbar[1], 1);
+    mbar_init(&mbar[2], 1);  // the injected stall's barrier; never arrived at
     fence_mbar_init();
     abort_sh = 0;
   }
@@ -205,6 +219,11 @@ __global__ void __launch_bounds__(128) k_coarse_mma(const MmaBatch batch, int nr
   // `pending` = MMAs committed on that buffer not yet waited for
   uint32_t parity = 0u, pending = 0u;
   bool ok = true;
+  if (batch.stall) {
+    if (tid == 0 && !mbar_wait(&mbar[2], 0u)) abort_sh = 1;
+    __syncthreads();
+    ok = !abort_sh;
+  }
 
   // Operands of one slot are fetched into registers by fully unrolled,
   // independent loads (every load of the slot in flight at once); slot d+1
@@ -417,7 +436,7 @@ void launch_mma_batch(int* err, const MmaBatch& batch, int nrhs, cudaStream_t st
     if (grid > batch.total) grid = batch.total;
     kern<<<grid, 128, smem, st>>>(batch, nrhs, err);
   };
-  if (!tune) {
+  if (!tune || batch.stall) {
     launch(per_sm);
     return;
   }
@@ -425,6 +444,12 @@ void launch_mma_batch(int* err, const MmaBatch& batch, int nrhs, cudaStream_t st
                           std::to_string(N) + "/r" + std::to_string(nrhs) + "/v" +
                           std::to_string(batch.total) + "/b" + std::to_string(batch.count);
   launch(Tuner::get().choose(key, cands, st, launch));
+}
+
+int take_injected_stall(mg_ctx* c) {
+  if (c->inject_mma_stall <= 0) return 0;
+  --c->inject_mma_stall;
+  return 1;
 }
 
 MmaLattice lattice_of(const Level& L, void* y, const void* x) {
@@ -444,6 +469,7 @@ void launch_mma(mg_ctx* c, const Level& L, void* y, const void* x, int nrhs, cud
   b.lat[0] = lattice_of(L, y, x);
   b.count = 1;
   b.total = L.g.vol;
+  b.stall = take_injected_stall(c);
   launch_mma_batch<BF16, N>(c->status.as<int>() + 1, b, nrhs, st, true);
 }
 
@@ -513,6 +539,7 @@ extern "C" mg_status mg_coarse_apply_multi(mg_ctx* const* ctxs, const int* level
       b.total += L.g.vol;
     }
     b.count = count;
+    b.stall = take_injected_stall(ctxs[0]);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int* err = ctxs[0]->status.as<int>() + 1;
     const bool bf16 = prec == MG_BF16;

@@ -131,6 +131,7 @@ struct mg_ctx {
   std::string err;
   gbmg::Profiler prof;
   long long launches = 0;
+  int inject_mma_stall = 0;     // fault injection: stalled tensor-core launches to come
   // reductions: per-block partials and final scalars (complex double)
   gbmg::DevBuf red_partials;   // [2][nrhs][max_blocks] double2
   gbmg::DevBuf scalars;        // [SC_COUNT][kMaxNrhs] double2

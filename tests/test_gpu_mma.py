@@ -1,5 +1,7 @@
 """Multi-RHS coarse apply on the tcgen05 tensor cores (16-bit links and
 operands, FP32 accumulation) against the FP64 oracle stencil apply."""
+import time
+
 import numpy as np
 import pytest
 import torch
@@ -76,3 +78,39 @@ def test_uneven_lattices_one_launch_and_graph(gpu_lib):
         assert rel_l2(to_np(y), ref) < 5e-3
     for m, _ in mgs:
         m.close()
+
+
+def test_injected_wait_times_out_and_context_stays_usable(gpu_lib):
+    """The tensor-core launch's mbarrier waits are bounded by a one-second
+    budget: an injected wait on a barrier that nothing arrives at gives up,
+    the launch writes nothing, mg_device_status reports MG_ERR_TIMEOUT once,
+    and the next launch on the same context is correct."""
+    gb = gpu_lib
+    cdims, nv, nrhs = (2, 2, 4, 2), 24, 8
+    mg, _ = make_ctx(gb, tuple(2 * c for c in cdims), [(2, 2, 2, 2)], [nv], prec_fine=1,
+                     prec_coarse=2)
+    n, vol = 2 * nv, lat.volume(cdims)
+    links = syn.gaussian_field((vol, 9, n, n), 53) / np.sqrt(n)
+    gb.mg_set_coarse_links(mg.ctx, 1, to_dev(links))
+    x = to_dev(syn.gaussian_field((vol, n, nrhs), 54), torch.complex64)
+    y = torch.zeros((vol, n, nrhs), dtype=torch.complex64, device="cuda")
+    with pytest.raises(gb.MGError) as e:
+        gb.mg_inject_fault(mg.ctx, "no_such_fault", 1)
+    assert e.value.status == gb.MG_ERR_ARG
+    gb.mg_inject_fault(mg.ctx, "coarse_mma_wait", 1)
+    t0 = time.monotonic()
+    gb.mg_coarse_apply(mg.ctx, 1, y, x, nrhs=nrhs)
+    with pytest.raises(gb.MGError) as e:
+        gb.mg_device_status(mg.ctx)
+    waited = time.monotonic() - t0
+    assert e.value.status == gb.MG_ERR_TIMEOUT
+    assert 0.9 < waited < 30.0, waited
+    assert not torch.any(y != 0)  # the stalled launch wrote nothing
+    gb.mg_device_status(mg.ctx)  # the record was cleared
+    gb.mg_coarse_apply(mg.ctx, 1, y, x, nrhs=nrhs)
+    gb.mg_device_status(mg.ctx)
+    cop = dirac.StencilOp(cdims, links)
+    xn = to_np(x)
+    want = np.stack([cop.apply(xn[:, :, k]) for k in range(nrhs)], axis=-1)
+    assert rel_l2(to_np(y), want) < 5e-3
+    mg.close()
