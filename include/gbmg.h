@@ -350,6 +350,17 @@ mg_status mg_cnn_adam_step(mg_cnn* net, float lr, void* stream);
  * is cleared.                                                              */
 mg_status mg_device_status(mg_ctx* ctx, void* stream);
 
+/* out[0] + i out[1] = sum_k conj(a_k) b_k over one vector of `level`
+ * (level_volume x level_dof complex numbers in `prec`, MG_F32 or MG_F64,
+ * device memory, caller-owned), with the accumulation the solvers use
+ * (Sec. 7.1): fp64 != 0 is the outer GCR's orthogonalisation form, FP64
+ * accurate (FP32 operands: exact products summed in float-float pairs, the
+ * pairs combined in FP64); fp64 = 0 the inner levels' form (FP32 operands:
+ * FP32 partial sums combined in FP64).  a == b gives |a|^2.  Synchronises
+ * `stream`; not concurrent with other calls on the same context.          */
+mg_status mg_inner_product(mg_ctx* ctx, int level, const void* a, const void* b, mg_prec prec,
+                           int fp64, double* out, void* stream);
+
 /* Host-side fault injection for tests of the error paths (no fault of the
  * GPU is made).  what = "coarse_mma_wait": the next `count` tensor-core
  * multi-RHS launches of this context (mg_coarse_apply with nrhs > 1 on

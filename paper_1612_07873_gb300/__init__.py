@@ -95,6 +95,7 @@ def _load():
         "mg_save": (i, [vp, C.c_char_p]),
         "mg_load": (i, [vp, C.c_char_p]),
         "mg_inject_fault": (i, [vp, C.c_char_p, i]),
+        "mg_inner_product": (i, [vp, i, vp, vp, i, i, C.POINTER(C.c_double), vp]),
         "mg_wilson_clover_apply_multi": (i, [vp, vp, vp, i, vp]),
         "mg_wilson_clover_apply_bf16": (i, [vp, vp, vp, i, vp]),
         "mg_schur_apply": (i, [vp, i, vp, vp, i, vp]),
@@ -337,6 +338,17 @@ def mg_block_orthonormalise_noalloc(vecs, out, dims, block, stream=None):
 
 def mg_device_status(ctx, stream=None):
     _ok(LIB.mg_device_status(ctx, _stream(stream)), ctx)
+
+
+def mg_inner_product(ctx, level, a, b, fp64=True, stream=None):
+    """sum conj(a) b over one level vector (complex64 or complex128 tensors)
+    with the solvers' accumulation; returns a Python complex."""
+    prec = {torch.complex64: 1, torch.complex128: 0}[a.dtype]
+    assert b.dtype == a.dtype and a.is_contiguous() and b.is_contiguous()
+    out = (C.c_double * 2)()
+    _ok(LIB.mg_inner_product(ctx, level, C.c_void_p(a.data_ptr()), C.c_void_p(b.data_ptr()),
+                             prec, int(bool(fp64)), out, _stream(stream)), ctx)
+    return complex(out[0], out[1])
 
 
 def mg_inject_fault(ctx, what, count=1):

@@ -611,6 +611,21 @@ mg_status mg_device_status(mg_ctx* c, void* stream) {
   });
 }
 
+mg_status mg_inner_product(mg_ctx* c, int level, const void* a, const void* b, mg_prec prec,
+                           int fp64, double* out, void* stream) {
+  return guarded(c, [&] {
+    check_level(c, level, 0, c->nlevels - 1);
+    GB_REQUIRE(a && b && out, MG_ERR_ARG, "inner_product: null pointer");
+    GB_REQUIRE(prec == MG_F32 || prec == MG_F64, MG_ERR_ARG,
+               "inner_product: FP32 or FP64 vectors");
+    const size_t n = c->L[level].vec_elems();
+    Vec va{const_cast<void*>(a), prec, n, 1}, vb{const_cast<void*>(b), prec, n, 1};
+    const int slot = level * 8 + 7;  // the solvers use slots 0..5 of each level
+    blas_dot(c, va, vb, slot, S(stream), fp64 != 0);
+    blas_read_slot_c(c, slot, out, S(stream));
+  });
+}
+
 mg_status mg_inject_fault(mg_ctx* c, const char* what, int count) {
   return guarded(c, [&] {
     GB_REQUIRE(what && count >= 0 && count <= 1000, MG_ERR_ARG, "inject_fault: bad arguments");

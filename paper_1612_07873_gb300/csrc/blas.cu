@@ -68,6 +68,23 @@ using acc_t = typename std::conditional<std::is_same<Ra, float>::value &&
 // to back (rhs v at offset v * n); blockIdx.y is the right-hand side and
 // per-RHS scalars are read from a row S[v] of the scalar table.
 
+// Grid-stride loop over [0, n) that hands each thread's elements to
+// body(i, k) round-robin over kAcc independent accumulators k (a fixed
+// assignment, so sums stay bitwise reproducible): a single accumulator
+// chains every multiply-add on the previous one, and an FP64 chain of that
+// kind runs far below GB300's FP64 issue rate.
+constexpr int kAcc = 4;
+template <typename F>
+__device__ __forceinline__ void grid_loop_acc(size_t n, F&& body) {
+  const size_t stride = size_t(gridDim.x) * blockDim.x;
+  size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x;
+  for (; i + (kAcc - 1) * stride < n; i += kAcc * stride) {
+#pragma unroll
+    for (int k = 0; k < kAcc; ++k) body(i + k * stride, k);
+  }
+  for (; i < n; i += stride) body(i, 0);
+}
+
 // NORM: a == b, only the real part |a|^2 is formed (half the multiply-adds,
 // which matters where they are FP64)
 template <typename Ra, typename Rb, typename T, bool NORM = false>
@@ -76,17 +93,77 @@ __global__ void k_dot_partial(const cpx<Ra>* __restrict__ a, const cpx<Rb>* __re
   __shared__ double2 sh[32];
   a += size_t(blockIdx.y) * n;
   b += size_t(blockIdx.y) * n;
-  cpx<T> acc(T(0), T(0));
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
-       i += size_t(gridDim.x) * blockDim.x) {
+  cpx<T> acc[kAcc];
+#pragma unroll
+  for (int k = 0; k < kAcc; ++k) acc[k] = cpx<T>(T(0), T(0));
+  grid_loop_acc(n, [&](size_t i, int k) {
     if constexpr (NORM) {
       const cpx<T> x(a[i]);
-      acc.re = fma(x.re, x.re, fma(x.im, x.im, acc.re));
+      acc[k].re = fma(x.re, x.re, fma(x.im, x.im, acc[k].re));
     } else {
-      cmac_conj(acc, cpx<T>(a[i]), cpx<T>(b[i]));
+      cmac_conj(acc[k], cpx<T>(a[i]), cpx<T>(b[i]));
     }
+  });
+  const cpx<T> t = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+  double2 d = block_sum(make_double2(double(t.re), double(t.im)), sh);
+  if (threadIdx.x == 0) part[size_t(blockIdx.y) * gridDim.x + blockIdx.x] = d;
+}
+
+// FP64-accurate inner products of FP32 vectors without the FP64 pipe, whose
+// issue rate on GB300 would make them several times slower than reading
+// the vectors.  Each product is split exactly, a b = p + e (p rounded,
+// e = fma(a, b, -p)); the running sum is an unevaluated pair hi + lo of
+// floats (about 48 significant bits), updated with Knuth's TwoSum, which
+// returns the rounding error of a float addition exactly, and renormalised
+// (Dekker's Fast2Sum) after every element.  The rounding-explicit
+// intrinsics keep the compiler from contracting these sums into FMAs, which
+// would break the exact error terms.  Per-thread pairs are combined in FP64.
+__device__ __forceinline__ void ff_mac(float& hi, float& lo, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float e = __fmaf_rn(a, b, -p);
+  const float s = __fadd_rn(hi, p);
+  const float v = __fsub_rn(s, hi);
+  const float t = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, v)), __fsub_rn(p, v));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(t, e));
+}
+__device__ __forceinline__ void ff_renorm(float& hi, float& lo) {
+  const float s = __fadd_rn(hi, lo);
+  lo = __fsub_rn(lo, __fsub_rn(s, hi));
+  hi = s;
+}
+
+template <bool NORM>
+__global__ void k_dot_partial_ff(const cpx<float>* __restrict__ a, const cpx<float>* __restrict__ b,
+                                 size_t n, double2* __restrict__ part) {
+  __shared__ double2 sh[32];
+  a += size_t(blockIdx.y) * n;
+  b += size_t(blockIdx.y) * n;
+  float rh[kAcc], rl[kAcc], ih[kAcc], il[kAcc];
+#pragma unroll
+  for (int k = 0; k < kAcc; ++k) rh[k] = rl[k] = ih[k] = il[k] = 0.f;
+  grid_loop_acc(n, [&](size_t i, int k) {
+    const cpx<float> x = a[i];
+    if constexpr (NORM) {
+      ff_mac(rh[k], rl[k], x.re, x.re);
+      ff_mac(rh[k], rl[k], x.im, x.im);
+    } else {
+      const cpx<float> y = b[i];
+      ff_mac(rh[k], rl[k], x.re, y.re);  // conj(x) y
+      ff_mac(rh[k], rl[k], x.im, y.im);
+      ff_mac(ih[k], il[k], x.re, y.im);
+      ff_mac(ih[k], il[k], -x.im, y.re);
+      ff_renorm(ih[k], il[k]);
+    }
+    ff_renorm(rh[k], rl[k]);
+  });
+  double re = 0.0, im = 0.0;
+#pragma unroll
+  for (int k = 0; k < kAcc; ++k) {
+    re += double(rh[k]) + double(rl[k]);
+    im += double(ih[k]) + double(il[k]);
   }
-  double2 d = block_sum(make_double2(double(acc.re), double(acc.im)), sh);
+  double2 d = block_sum(make_double2(re, im), sh);
   if (threadIdx.x == 0) part[size_t(blockIdx.y) * gridDim.x + blockIdx.x] = d;
 }
 
@@ -98,14 +175,20 @@ __global__ void k_dot2_partial_b(const cpx<Ra>* __restrict__ p, const cpx<Rb>* _
   __shared__ double2 sh[32];
   p += blockIdx.y * n;
   r += blockIdx.y * n;
-  cpx<T> a_pr(T(0), T(0));
-  T a_pp = T(0);
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
-       i += size_t(gridDim.x) * blockDim.x) {
-    cpx<T> x(p[i]), y(r[i]);
-    cmac_conj(a_pr, x, y);
-    a_pp = fma(x.re, x.re, fma(x.im, x.im, a_pp));
+  cpx<T> pr_k[kAcc];
+  T pp_k[kAcc];
+#pragma unroll
+  for (int k = 0; k < kAcc; ++k) {
+    pr_k[k] = cpx<T>(T(0), T(0));
+    pp_k[k] = T(0);
   }
+  grid_loop_acc(n, [&](size_t i, int k) {
+    cpx<T> x(p[i]), y(r[i]);
+    cmac_conj(pr_k[k], x, y);
+    pp_k[k] = fma(x.re, x.re, fma(x.im, x.im, pp_k[k]));
+  });
+  const cpx<T> a_pr = (pr_k[0] + pr_k[1]) + (pr_k[2] + pr_k[3]);
+  const T a_pp = (pp_k[0] + pp_k[1]) + (pp_k[2] + pp_k[3]);
   double2 pr = block_sum(make_double2(double(a_pr.re), double(a_pr.im)), sh);
   __syncthreads();
   double2 pp = block_sum(make_double2(double(a_pp), 0.0), sh);
@@ -298,14 +381,20 @@ __global__ void k_dot2_partial_h(const bf16c* __restrict__ p, const bf16c* __res
   __shared__ double2 sh[32];
   p += blockIdx.y * n;
   r += blockIdx.y * n;
-  cpx<float> a_pr(0.f, 0.f);
-  float a_pp = 0.f;
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
-       i += size_t(gridDim.x) * blockDim.x) {
-    const cpx<float> x = h2f(p[i]), y = h2f(r[i]);
-    cmac_conj(a_pr, x, y);
-    a_pp = fmaf(x.re, x.re, fmaf(x.im, x.im, a_pp));
+  cpx<float> pr_k[kAcc];
+  float pp_k[kAcc];
+#pragma unroll
+  for (int k = 0; k < kAcc; ++k) {
+    pr_k[k] = cpx<float>(0.f, 0.f);
+    pp_k[k] = 0.f;
   }
+  grid_loop_acc(n, [&](size_t i, int k) {
+    const cpx<float> x = h2f(p[i]), y = h2f(r[i]);
+    cmac_conj(pr_k[k], x, y);
+    pp_k[k] = fmaf(x.re, x.re, fmaf(x.im, x.im, pp_k[k]));
+  });
+  const cpx<float> a_pr = (pr_k[0] + pr_k[1]) + (pr_k[2] + pr_k[3]);
+  const float a_pp = (pp_k[0] + pp_k[1]) + (pp_k[2] + pp_k[3]);
   double2 pr = block_sum(make_double2(double(a_pr.re), double(a_pr.im)), sh);
   __syncthreads();
   double2 pp = block_sum(make_double2(double(a_pp), 0.0), sh);
@@ -536,7 +625,14 @@ void blas_dot(mg_ctx* c, Vec a, Vec b, int slot, cudaStream_t st, bool fp64_part
   double2* part = partials(c, size_t(nb) * a.nr);
   const dim3 grid(nb, a.nr);
   const bool norm = a.p == b.p && a.prec == b.prec;
-  if (norm && fp64_partials) {
+  const bool ff = fp64_partials && a.prec == MG_F32 && b.prec == MG_F32;
+  if (ff && norm) {
+    k_dot_partial_ff<true><<<grid, kThreads, 0, st>>>((const cpx<float>*)a.p,
+                                                      (const cpx<float>*)a.p, a.n, part);
+  } else if (ff) {
+    k_dot_partial_ff<false><<<grid, kThreads, 0, st>>>((const cpx<float>*)a.p,
+                                                       (const cpx<float>*)b.p, a.n, part);
+  } else if (norm && fp64_partials) {
     GB_DISPATCH1(a.prec, Ra,
                  (k_dot_partial<Ra, Ra, double, true><<<grid, kThreads, 0, st>>>(
                      (const cpx<Ra>*)a.p, (const cpx<Ra>*)a.p, a.n, part)));
@@ -628,6 +724,14 @@ void blas_read_slot(mg_ctx* c, int slot, int nr, double* out_re, cudaStream_t st
                            cudaMemcpyDeviceToHost, st));
   GB_CHECK(cudaStreamSynchronize(st));
   for (int v = 0; v < nr; ++v) out_re[v] = c->h_scalars[2 * v];
+}
+
+void blas_read_slot_c(mg_ctx* c, int slot, double out[2], cudaStream_t st) {
+  GB_CHECK(cudaMemcpyAsync(c->h_scalars, srow(c, slot), sizeof(double2),
+                           cudaMemcpyDeviceToHost, st));
+  GB_CHECK(cudaStreamSynchronize(st));
+  out[0] = c->h_scalars[0];
+  out[1] = c->h_scalars[1];
 }
 
 void blas_dot2_batched(mg_ctx* c, Vec p, Vec r, int nvec, cudaStream_t st) {

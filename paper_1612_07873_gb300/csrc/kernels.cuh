@@ -44,6 +44,8 @@ void blas_scale_invnorm(mg_ctx* c, Vec a, Vec b, int slot, cudaStream_t st);
 void blas_gcr_update(mg_ctx* c, Vec x, Vec r, Vec z, Vec w, int slot, cudaStream_t st);
 // real parts of S[slot][0..nr) to the host (synchronises st)
 void blas_read_slot(mg_ctx* c, int slot, int nr, double* out_re, cudaStream_t st);
+// both parts of right-hand side 0's value in `slot` (synchronises)
+void blas_read_slot_c(mg_ctx* c, int slot, double out[2], cudaStream_t st);
 // Setup sweeps: nvec vectors of length p.n back to back, scalars in
 // ctx->batch_scalars: B[2v] = <p_v, r_v>, B[2v+1] = |p_v|^2
 void blas_dot2_batched(mg_ctx* c, Vec p, Vec r, int nvec, cudaStream_t st);

@@ -12,6 +12,8 @@
 // so the Nv coefficients of one fine dof are contiguous.
 #include <mutex>
 
+#include <type_traits>
+
 #include "kernels.cuh"
 #include "tune.cuh"
 
@@ -434,17 +436,18 @@ __global__ void __launch_bounds__(256) k_restrict12(cpx<Rc>* __restrict__ coarse
 
 // fine_v[x][a] = sum_i Vp[x][a][i] coarse_v[agg(x)][chi(a)*Nv + i] for all nr
 // right-hand sides.  Two threads per Vp row, each holding half of it in
-// registers for every right-hand side: thread q takes the 16-byte words
-// 2k + q, so a pair reads whole 32-byte sectors; the halves meet by one
-// shuffle.
-template <typename Rf, typename Rc, typename VT>
+// registers: thread q takes the 16-byte words 2k + q (PW words), so a pair
+// reads whole 32-byte sectors; the halves meet by one shuffle.  A pair
+// loads RPI rows (RPI * PW <= 12 words) before any arithmetic, so short
+// rows (16-bit Vp, small Nv) still keep several loads per thread in flight.
+template <typename Rf, typename Rc, typename VT, int PW>
 __global__ void __launch_bounds__(256) k_prolong12(cpx<Rf>* __restrict__ fine,
                                                   const cpx<Rc>* __restrict__ coarse,
                                                   const VT* __restrict__ Vp, AggMap m,
                                                   int nv, int nr, size_t fstride,
                                                   size_t cstride) {
   constexpr int ND = 12, CPL = VUnpack<VT, Rf>::CPL;
-  constexpr int MAXPW = 12;  // Nv <= 48 (FP32) / 24 (FP64)
+  constexpr int RPI = PW >= 12 ? 1 : (12 / PW > 6 ? 6 : 12 / PW);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<Rf>* cs = reinterpret_cast<cpx<Rf>*>(smem_raw);  // [nr][2][nv]
   int* off = reinterpret_cast<int*>(cs + size_t(nr) * 2 * nv);
@@ -456,36 +459,45 @@ __global__ void __launch_bounds__(256) k_prolong12(cpx<Rf>* __restrict__ fine,
   }
   const size_t base = size_t(agg_origin(m, xc));
   __syncthreads();
-  const int NP = nv / CPL, PW = NP / 2;  // 16-byte words per row and per half row
-  const int q = threadIdx.x & 1;
+  const int q = threadIdx.x & 1, pair = threadIdx.x >> 1, npairs = blockDim.x >> 1;
   const int rows = m.per * ND;
   // the loop bound is uniform across the CTA, so every lane reaches the
-  // full-warp shuffle; rows past the end compute nothing and store nothing
-  for (int r0 = 0; r0 < rows; r0 += blockDim.x >> 1) {
-    const int r = r0 + (threadIdx.x >> 1);
-    const bool ok = r < rows;
-    const int ls = ok ? r / ND : 0, a = ok ? r - ls * ND : 0;
-    const size_t x = base + off[ls];
-    const uint4* vr = reinterpret_cast<const uint4*>(Vp + (x * ND + a) * nv) + q;
-    uint4 w[MAXPW];
+  // full-warp shuffles; rows past the end compute nothing and store nothing
+  for (int r0 = 0; r0 < rows; r0 += npairs * RPI) {
+    uint4 w[RPI][PW];
+    size_t frow[RPI];  // fine element x * ND + a of each row
+    int coff[RPI];     // its chirality's offset into the coarse vector
+    bool ok[RPI];
 #pragma unroll
-    for (int k = 0; k < MAXPW; ++k)
-      if (ok && k < PW) w[k] = ld_stream16(vr + 2 * k);
-    const int coff = (a < ND / 2 ? 0 : nv) + q * CPL;
+    for (int j = 0; j < RPI; ++j) {
+      const int r = r0 + j * npairs + pair;
+      ok[j] = r < rows;
+      const int ls = ok[j] ? r / ND : 0, a = ok[j] ? r - ls * ND : 0;
+      frow[j] = (base + off[ls]) * ND + a;
+      coff[j] = (a < ND / 2 ? 0 : nv) + q * CPL;
+      const uint4* vr = reinterpret_cast<const uint4*>(Vp + frow[j] * nv) + q;
+#pragma unroll
+      for (int k = 0; k < PW; ++k)
+        if (ok[j]) w[j][k] = ld_stream16(vr + 2 * k);
+    }
     for (int b = 0; b < nr; ++b) {
-      const cpx<Rf>* c = cs + b * 2 * nv + coff;
-      cpx<Rf> acc(Rf(0), Rf(0));
 #pragma unroll
-      for (int k = 0; k < MAXPW; ++k)
-        if (ok && k < PW) {
-          cpx<Rf> v[CPL];
-          VUnpack<VT, Rf>::get(w[k], v);
+      for (int j = 0; j < RPI; ++j) {
+        const cpx<Rf>* c = cs + b * 2 * nv + coff[j];
+        cpx<Rf> acc(Rf(0), Rf(0));
+        if (ok[j]) {
 #pragma unroll
-          for (int j = 0; j < CPL; ++j) cmac(acc, v[j], c[2 * k * CPL + j]);
+          for (int k = 0; k < PW; ++k) {
+            cpx<Rf> v[CPL];
+            VUnpack<VT, Rf>::get(w[j][k], v);
+#pragma unroll
+            for (int i = 0; i < CPL; ++i) cmac(acc, v[i], c[2 * k * CPL + i]);
+          }
         }
-      acc.re += __shfl_xor_sync(0xffffffffu, acc.re, 1);
-      acc.im += __shfl_xor_sync(0xffffffffu, acc.im, 1);
-      if (ok && q == 0) fine[b * fstride + x * ND + a] = acc;
+        acc.re += __shfl_xor_sync(0xffffffffu, acc.re, 1);
+        acc.im += __shfl_xor_sync(0xffffffffu, acc.im, 1);
+        if (ok[j] && q == 0) fine[b * fstride + frow[j]] = acc;
+      }
     }
   }
 }
@@ -706,21 +718,35 @@ void prolong_apply(mg_ctx* c, int level, Vec fine, Vec coarse, cudaStream_t st) 
                8.0 * n * nv * nr);
   const int cpl = h16 ? 4 : F.vprec == MG_F64 ? 1 : 2;
   const size_t smem2 = size_t(nr) * 2 * nv * size_t(vb) + size_t(m.per) * sizeof(int);
-  if (F.nd == 12 && nv % (2 * cpl) == 0 && nv / (2 * cpl) <= 12 && smem2 <= 48 * 1024) {
-    if (h16) {
-      if (coarse.prec == MG_F64)
-        k_prolong12<float, double, bf16c><<<C.g.vol, 256, smem2, st>>>(
-            (cpx<float>*)fine.p, (const cpx<double>*)coarse.p, F.Vp16.as<bf16c>(), m, nv, nr,
-            fine.n, coarse.n);
-      else
-        k_prolong12<float, float, bf16c><<<C.g.vol, 256, smem2, st>>>(
-            (cpx<float>*)fine.p, (const cpx<float>*)coarse.p, F.Vp16.as<bf16c>(), m, nv, nr,
-            fine.n, coarse.n);
-    } else {
-      GB_TRANSFER_DISPATCH(F.vprec, coarse.prec, Rf, Rc,
-                           (k_prolong12<Rf, Rc, cpx<Rf>><<<C.g.vol, 256, smem2, st>>>(
-                               (cpx<Rf>*)fine.p, (const cpx<Rc>*)coarse.p, F.Vp.as<cpx<Rf>>(),
-                               m, nv, nr, fine.n, coarse.n)));
+  const int pw = nv % (2 * cpl) == 0 ? nv / (2 * cpl) : 0;  // 16-byte words per half row
+  if (F.nd == 12 && (pw == 1 || pw == 2 || pw == 3 || pw == 4 || pw == 6 || pw == 8 || pw == 12) &&
+      smem2 <= 48 * 1024) {
+    auto go = [&](auto pwc) {
+      constexpr int PW = decltype(pwc)::value;
+      if (h16) {
+        if (coarse.prec == MG_F64)
+          k_prolong12<float, double, bf16c, PW><<<C.g.vol, 256, smem2, st>>>(
+              (cpx<float>*)fine.p, (const cpx<double>*)coarse.p, F.Vp16.as<bf16c>(), m, nv, nr,
+              fine.n, coarse.n);
+        else
+          k_prolong12<float, float, bf16c, PW><<<C.g.vol, 256, smem2, st>>>(
+              (cpx<float>*)fine.p, (const cpx<float>*)coarse.p, F.Vp16.as<bf16c>(), m, nv, nr,
+              fine.n, coarse.n);
+      } else {
+        GB_TRANSFER_DISPATCH(F.vprec, coarse.prec, Rf, Rc,
+                             (k_prolong12<Rf, Rc, cpx<Rf>, PW><<<C.g.vol, 256, smem2, st>>>(
+                                 (cpx<Rf>*)fine.p, (const cpx<Rc>*)coarse.p,
+                                 F.Vp.as<cpx<Rf>>(), m, nv, nr, fine.n, coarse.n)));
+      }
+    };
+    switch (pw) {
+      case 1: go(std::integral_constant<int, 1>{}); break;
+      case 2: go(std::integral_constant<int, 2>{}); break;
+      case 3: go(std::integral_constant<int, 3>{}); break;
+      case 4: go(std::integral_constant<int, 4>{}); break;
+      case 6: go(std::integral_constant<int, 6>{}); break;
+      case 8: go(std::integral_constant<int, 8>{}); break;
+      default: go(std::integral_constant<int, 12>{}); break;
     }
     GB_LAUNCH_CHECK();
     c->launches++;

@@ -105,3 +105,51 @@ def test_solve_residual_sampled(hierarchy):
                                         sites=sites)
     r = b[sites] - dirac.apply_at(blocks, xs, DIMS, sites)
     assert np.linalg.norm(r) / np.linalg.norm(b[sites]) < 1e-9
+
+
+def _exact_dot(a, b):
+    """sum conj(a) b for vectors whose parts are FP32 values: every product
+    is exact in float64, and numpy's pairwise float64 sum adds an error of
+    about log2(N) 2^-53 of sum |terms|.  Returns the value and, per part,
+    sum |terms| (the scale any summation error is measured against)."""
+    ar, ai = a.real.astype(np.float64).ravel(), a.imag.astype(np.float64).ravel()
+    br, bi = b.real.astype(np.float64).ravel(), b.imag.astype(np.float64).ravel()
+    re = np.concatenate([ar * br, ai * bi])
+    im = np.concatenate([ar * bi, -(ai * br)])
+    return complex(np.sum(re), np.sum(im)), np.sum(np.abs(re)), np.sum(np.abs(im))
+
+
+def test_outer_inner_products_are_fp64_accurate(hierarchy):
+    """The outer GCR's inner products (Sec. 7.1) on FP32 vectors of the full
+    fine lattice (25.2 M complex numbers, the bench's launch configuration):
+    within 1e-12 of sum |terms| of the exact value, a bound that products
+    rounded to FP32 (about 2^-24 / sqrt(N) of it) would miss; b is x's
+    complement so that the result cancels to ~1e-4 of the scale.  The same
+    holds for FP64 vectors with FP32-representable parts, and the inner
+    levels' FP32 form stays within 1e-5."""
+    gb, mg, U = hierarchy
+    vol = lat.volume(DIMS)
+    rng = np.random.default_rng(106)
+    x = (rng.standard_normal((vol, 12)) + 1j * rng.standard_normal((vol, 12))).astype(np.complex64)
+    z = (rng.standard_normal((vol, 12)) + 1j * rng.standard_normal((vol, 12))).astype(np.complex64)
+    xd = x.astype(np.complex128)
+    zd = z.astype(np.complex128)
+    y = (zd - (np.vdot(xd, zd) / np.vdot(xd, xd)) * xd).astype(np.complex64)
+    del xd, zd, z
+    want, s_re, s_im = _exact_dot(x, y)
+    assert abs(want) < 1e-3 * (s_re + s_im)  # the sum really cancels
+    nrm, s_nrm, _ = _exact_dot(x, x)
+    xg, yg = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    for dt in (torch.complex64, torch.complex128):
+        a, b = xg.to(dt), yg.to(dt)
+        got = gb.mg_inner_product(mg.ctx, 0, a, b, fp64=True)
+        assert abs(got.real - want.real) <= 1e-12 * s_re, (dt, got, want)
+        assert abs(got.imag - want.imag) <= 1e-12 * s_im, (dt, got, want)
+        got = gb.mg_inner_product(mg.ctx, 0, a, a, fp64=True)
+        assert abs(got.real - nrm.real) <= 1e-12 * s_nrm and got.imag == 0.0, (dt, got, nrm)
+    got = gb.mg_inner_product(mg.ctx, 0, xg, yg, fp64=False)
+    assert abs(got.real - want.real) <= 1e-5 * s_re and abs(got.imag - want.imag) <= 1e-5 * s_im
+    # a NaN anywhere reaches the result (the solvers' breakdown check)
+    xg[vol // 3, 5] = complex("nan")
+    got = gb.mg_inner_product(mg.ctx, 0, xg, yg, fp64=True)
+    assert not np.isfinite(got.real)
