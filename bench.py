@@ -587,6 +587,71 @@ def wilson_policies_main(args):
     return 0
 
 
+def solve_breakdown_main(args):
+    """Per-kernel device time of one MG-GCR solve on the 32^3x64 workload
+    (setup untimed), for the plain FP32 form and the 16-bit fine smoother
+    form: every kernel launch of the solve recorded by the CUDA activity
+    tracer (torch.profiler, not serialised, warm caches), summed per kernel.
+    Prints one JSON line per form: wall time of the solve, summed kernel
+    time, the span from first to last launch, and the kernels by share."""
+    import torch
+    from torch.profiler import ProfilerActivity, profile
+
+    import paper_1612_07873_gb300 as gb
+    w = syn.WORKLOADS[WORKLOAD]
+    dims = tuple(w["dims"])
+    vol = syn.volume(dims)
+    U = torch.from_numpy(syn.gauge_field(dims, w["eps"], w["seed"])).cuda()
+    b = torch.from_numpy(syn.gaussian_field((vol, 12), w["seed"], stream=99)).cuda()
+    with profile(activities=[ProfilerActivity.CUDA]):  # the tracer's first session
+        torch.zeros(1, device="cuda").add_(1)           # can come back empty
+        torch.cuda.synchronize()
+    for name, pc, ps in (("fp32", 1, 1), ("bf16_smoother16", 2, 2)):
+        p = gb.default_params(dims=dims, block=w["block"], nvec=w["nvec"], mass=w["mass"],
+                              csw=w["csw"], nlevels=3, prec_fine=1, prec_coarse=pc,
+                              setup_sweeps=w["sweeps"], t_antiperiodic=w["antiperiodic"],
+                              seed=w["seed"], prec_smoother=ps)
+        mg = gb.Multigrid(p, U)
+        for lv in range(2):
+            gb.mg_setup_nullvecs(mg.ctx, lv, None)
+            gb.mg_build_coarse(mg.ctx, lv)
+        x = torch.zeros_like(b)
+        for _ in range(max(args.warmup, 1)):
+            gb.mg_gcr_solve(mg.ctx, x, b, 1e-10, 500)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = gb.mg_gcr_solve(mg.ctx, x, b, 1e-10, 500)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            gb.mg_gcr_solve(mg.ctx, x, b, 1e-10, 500)
+            torch.cuda.synchronize()
+        agg, busy, t_lo, t_hi = {}, 0.0, None, None
+        for e in prof.events():
+            if e.device_type != torch.autograd.DeviceType.CUDA:
+                continue
+            d = getattr(e, "device_time", None)
+            d = e.cuda_time if d is None else d
+            key = e.name.replace("(anonymous namespace)::", "")
+            key = key.split("(")[0].replace("void ", "")
+            a = agg.setdefault(key, [0, 0.0])
+            a[0] += 1
+            a[1] += d
+            busy += d
+            t_lo = e.time_range.start if t_lo is None else min(t_lo, e.time_range.start)
+            t_hi = e.time_range.end if t_hi is None else max(t_hi, e.time_range.end)
+        rows = [{"kernel": k, "launches": n, "ms": t / 1e3, "us_per_launch": t / n,
+                 "share": t / busy if busy else 0.0}
+                for k, (n, t) in sorted(agg.items(), key=lambda kv: -kv[1][1])]
+        print(json.dumps({"mode": "solve-breakdown", "form": name, "lattice": list(dims),
+                          "iters": st["iters"], "wall_ms": wall * 1e3,
+                          "kernel_ms": busy / 1e3,
+                          "span_ms": (t_hi - t_lo) / 1e3 if rows else 0.0,
+                          "kernels": rows}), flush=True)
+        mg.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -595,7 +660,7 @@ def main():
     ap.add_argument("--impl", default="gbmg", choices=["gbmg", "reference"])
     ap.add_argument("--form", default="fp32", choices=["fp32", "bf16", "fp16", "int16"])
     ap.add_argument("--mode", default="pipeline",
-                    choices=["pipeline", "coarse-apply", "wilson-policies"])
+                    choices=["pipeline", "coarse-apply", "wilson-policies", "solve-breakdown"])
     ap.add_argument("--fine", default="", help="override the fine extents, e.g. 16,16,16,32")
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides (coarse-apply mode)")
     ap.add_argument("--slots", type=int, default=9, choices=[5, 9],
@@ -616,6 +681,8 @@ def main():
         return coarse_apply_main(args)
     if args.mode == "wilson-policies":
         return wilson_policies_main(args)
+    if args.mode == "solve-breakdown":
+        return solve_breakdown_main(args)
     return gpu_main(args)
 
 

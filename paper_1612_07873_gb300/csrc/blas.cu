@@ -16,10 +16,24 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kMaxRedBlocks = 1024;
 
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Reduction grid: one block per 4096 elements, at most one full wave of
+// the reduction kernels (<= 64 registers a thread, so 4 blocks of 256
+// threads per SM); a second, partly filled wave would leave SMs idle at
+// the end.  The grid depends only on the length and the device.
 int red_blocks(size_t n) {
+  static const int cap = [] {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms < 1)
+      return kMaxRedBlocks;
+    return 4 * sms < kMaxRedBlocks ? 4 * sms : kMaxRedBlocks;
+  }();
   long long b = (long long)((n + 4095) / 4096);
   if (b < 1) b = 1;
-  if (b > kMaxRedBlocks) b = kMaxRedBlocks;
+  if (b > cap) b = cap;
   return int(b);
 }
 int ew_blocks(size_t n) {
@@ -133,7 +147,9 @@ __device__ __forceinline__ void ff_renorm(float& hi, float& lo) {
   hi = s;
 }
 
-template <bool NORM>
+// W = 1: one complex number per access; W = 2: 16-byte loads of two (the
+// vectors 16-byte aligned, n even)
+template <bool NORM, int W>
 __global__ void k_dot_partial_ff(const cpx<float>* __restrict__ a, const cpx<float>* __restrict__ b,
                                  size_t n, double2* __restrict__ part) {
   __shared__ double2 sh[32];
@@ -142,13 +158,11 @@ __global__ void k_dot_partial_ff(const cpx<float>* __restrict__ a, const cpx<flo
   float rh[kAcc], rl[kAcc], ih[kAcc], il[kAcc];
 #pragma unroll
   for (int k = 0; k < kAcc; ++k) rh[k] = rl[k] = ih[k] = il[k] = 0.f;
-  grid_loop_acc(n, [&](size_t i, int k) {
-    const cpx<float> x = a[i];
+  auto term = [&](cpx<float> x, cpx<float> y, int k) {
     if constexpr (NORM) {
       ff_mac(rh[k], rl[k], x.re, x.re);
       ff_mac(rh[k], rl[k], x.im, x.im);
     } else {
-      const cpx<float> y = b[i];
       ff_mac(rh[k], rl[k], x.re, y.re);  // conj(x) y
       ff_mac(rh[k], rl[k], x.im, y.im);
       ff_mac(ih[k], il[k], x.re, y.im);
@@ -156,7 +170,19 @@ __global__ void k_dot_partial_ff(const cpx<float>* __restrict__ a, const cpx<flo
       ff_renorm(ih[k], il[k]);
     }
     ff_renorm(rh[k], rl[k]);
-  });
+  };
+  if constexpr (W == 2) {
+    const float4* a4 = reinterpret_cast<const float4*>(a);
+    const float4* b4 = reinterpret_cast<const float4*>(b);
+    grid_loop_acc(n / 2, [&](size_t i, int k) {
+      const float4 x = a4[i];
+      const float4 y = NORM ? x : b4[i];
+      term(cpx<float>(x.x, x.y), cpx<float>(y.x, y.y), k);
+      term(cpx<float>(x.z, x.w), cpx<float>(y.z, y.w), k);
+    });
+  } else {
+    grid_loop_acc(n, [&](size_t i, int k) { term(a[i], NORM ? a[i] : b[i], k); });
+  }
   double re = 0.0, im = 0.0;
 #pragma unroll
   for (int k = 0; k < kAcc; ++k) {
@@ -376,6 +402,9 @@ __global__ void k_copy_from16(cpx<float>* __restrict__ y, const bf16c* __restric
     y[i] = h2f(x[i]);
 }
 
+// W = 1: one complex number per access; W = 4: 16-byte loads of four (the
+// vectors 16-byte aligned, n a multiple of 4)
+template <int W>
 __global__ void k_dot2_partial_h(const bf16c* __restrict__ p, const bf16c* __restrict__ r,
                                  size_t n, double2* __restrict__ part) {
   __shared__ double2 sh[32];
@@ -388,11 +417,23 @@ __global__ void k_dot2_partial_h(const bf16c* __restrict__ p, const bf16c* __res
     pr_k[k] = cpx<float>(0.f, 0.f);
     pp_k[k] = 0.f;
   }
-  grid_loop_acc(n, [&](size_t i, int k) {
-    const cpx<float> x = h2f(p[i]), y = h2f(r[i]);
+  auto term = [&](bf16c xp, bf16c yr, int k) {
+    const cpx<float> x = h2f(xp), y = h2f(yr);
     cmac_conj(pr_k[k], x, y);
     pp_k[k] = fmaf(x.re, x.re, fmaf(x.im, x.im, pp_k[k]));
-  });
+  };
+  if constexpr (W == 4) {
+    const uint4* p4 = reinterpret_cast<const uint4*>(p);
+    const uint4* r4 = reinterpret_cast<const uint4*>(r);
+    grid_loop_acc(n / 4, [&](size_t i, int k) {
+      const uint4 wp = p4[i], wr = r4[i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        term(reinterpret_cast<const bf16c*>(&wp)[j], reinterpret_cast<const bf16c*>(&wr)[j], k);
+    });
+  } else {
+    grid_loop_acc(n, [&](size_t i, int k) { term(p[i], r[i], k); });
+  }
   const cpx<float> a_pr = (pr_k[0] + pr_k[1]) + (pr_k[2] + pr_k[3]);
   const float a_pp = (pp_k[0] + pp_k[1]) + (pp_k[2] + pp_k[3]);
   double2 pr = block_sum(make_double2(double(a_pr.re), double(a_pr.im)), sh);
@@ -405,6 +446,7 @@ __global__ void k_dot2_partial_h(const bf16c* __restrict__ p, const bf16c* __res
   }
 }
 
+template <int W>
 __global__ void k_mr_update_h(bf16c* __restrict__ x, bf16c* __restrict__ r,
                               const bf16c* __restrict__ p, size_t n,
                               const double2* __restrict__ PR, const double2* __restrict__ PP,
@@ -423,13 +465,32 @@ __global__ void k_mr_update_h(bf16c* __restrict__ x, bf16c* __restrict__ r,
   x += size_t(v) * n;
   r += size_t(v) * n;
   p += size_t(v) * n;
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
-       i += size_t(gridDim.x) * blockDim.x) {
-    cpx<float> ri = h2f(r[i]), xi = h2f(x[i]);
+  auto upd = [&](bf16c& xs, bf16c& rs, bf16c ps) {
+    cpx<float> ri = h2f(rs), xi = h2f(xs);
     cmac(xi, ar, ri);
-    cmac(ri, -ar, h2f(p[i]));
-    x[i] = StoreTraits<bf16c>::pack(xi);
-    r[i] = StoreTraits<bf16c>::pack(ri);
+    cmac(ri, -ar, h2f(ps));
+    xs = StoreTraits<bf16c>::pack(xi);
+    rs = StoreTraits<bf16c>::pack(ri);
+  };
+  if constexpr (W == 4) {
+    uint4* x4 = reinterpret_cast<uint4*>(x);
+    uint4* r4 = reinterpret_cast<uint4*>(r);
+    const uint4* p4 = reinterpret_cast<const uint4*>(p);
+    for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n / 4;
+         i += size_t(gridDim.x) * blockDim.x) {
+      uint4 wx = x4[i], wr = r4[i];
+      const uint4 wp = p4[i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        upd(reinterpret_cast<bf16c*>(&wx)[j], reinterpret_cast<bf16c*>(&wr)[j],
+            reinterpret_cast<const bf16c*>(&wp)[j]);
+      x4[i] = wx;
+      r4[i] = wr;
+    }
+  } else {
+    for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
+         i += size_t(gridDim.x) * blockDim.x)
+      upd(x[i], r[i], p[i]);
   }
 }
 
@@ -626,12 +687,18 @@ void blas_dot(mg_ctx* c, Vec a, Vec b, int slot, cudaStream_t st, bool fp64_part
   const dim3 grid(nb, a.nr);
   const bool norm = a.p == b.p && a.prec == b.prec;
   const bool ff = fp64_partials && a.prec == MG_F32 && b.prec == MG_F32;
-  if (ff && norm) {
-    k_dot_partial_ff<true><<<grid, kThreads, 0, st>>>((const cpx<float>*)a.p,
-                                                      (const cpx<float>*)a.p, a.n, part);
-  } else if (ff) {
-    k_dot_partial_ff<false><<<grid, kThreads, 0, st>>>((const cpx<float>*)a.p,
-                                                       (const cpx<float>*)b.p, a.n, part);
+  const bool w2 = a.n % 2 == 0 && aligned16(a.p) && aligned16(b.p);
+  if (ff) {
+    const auto* pa = (const cpx<float>*)a.p;
+    const auto* pb = (const cpx<float>*)b.p;
+    if (norm && w2)
+      k_dot_partial_ff<true, 2><<<grid, kThreads, 0, st>>>(pa, pa, a.n, part);
+    else if (norm)
+      k_dot_partial_ff<true, 1><<<grid, kThreads, 0, st>>>(pa, pa, a.n, part);
+    else if (w2)
+      k_dot_partial_ff<false, 2><<<grid, kThreads, 0, st>>>(pa, pb, a.n, part);
+    else
+      k_dot_partial_ff<false, 1><<<grid, kThreads, 0, st>>>(pa, pb, a.n, part);
   } else if (norm && fp64_partials) {
     GB_DISPATCH1(a.prec, Ra,
                  (k_dot_partial<Ra, Ra, double, true><<<grid, kThreads, 0, st>>>(
@@ -666,8 +733,12 @@ void blas_dot2(mg_ctx* c, Vec p, Vec r, int s_pr, int s_pp, cudaStream_t st) {
   double2* part = partials(c, size_t(nb) * 2 * p.nr);
   if (p.prec == MG_BF16 || r.prec == MG_BF16) {
     GB_REQUIRE(p.prec == MG_BF16 && r.prec == MG_BF16, MG_ERR_ARG, "dot2: precision mix");
-    k_dot2_partial_h<<<dim3(nb, p.nr), kThreads, 0, st>>>((const bf16c*)p.p,
-                                                          (const bf16c*)r.p, p.n, part);
+    if (p.n % 4 == 0 && aligned16(p.p) && aligned16(r.p))
+      k_dot2_partial_h<4><<<dim3(nb, p.nr), kThreads, 0, st>>>((const bf16c*)p.p,
+                                                               (const bf16c*)r.p, p.n, part);
+    else
+      k_dot2_partial_h<1><<<dim3(nb, p.nr), kThreads, 0, st>>>((const bf16c*)p.p,
+                                                               (const bf16c*)r.p, p.n, part);
   } else {
     GB_DISPATCH2(p.prec, Ra, r.prec, Rb,
                  (k_dot2_partial_b<Ra, Rb><<<dim3(nb, p.nr), kThreads, 0, st>>>(
@@ -684,8 +755,12 @@ void blas_mr_update(mg_ctx* c, Vec x, Vec r, Vec p, int s_pr, int s_pp, double o
   check_nr(x);
   GB_REQUIRE(x.prec == r.prec && r.prec == p.prec, MG_ERR_ARG, "mr_update: precision mix");
   if (x.prec == MG_BF16) {
-    k_mr_update_h<<<ew_grid_b(x.n, x.nr), kThreads, 0, st>>>(
-        (bf16c*)x.p, (bf16c*)r.p, (const bf16c*)p.p, x.n, srow(c, s_pr), srow(c, s_pp), omega);
+    if (x.n % 4 == 0 && aligned16(x.p) && aligned16(r.p) && aligned16(p.p))
+      k_mr_update_h<4><<<ew_grid_b(x.n / 4, x.nr), kThreads, 0, st>>>(
+          (bf16c*)x.p, (bf16c*)r.p, (const bf16c*)p.p, x.n, srow(c, s_pr), srow(c, s_pp), omega);
+    else
+      k_mr_update_h<1><<<ew_grid_b(x.n, x.nr), kThreads, 0, st>>>(
+          (bf16c*)x.p, (bf16c*)r.p, (const bf16c*)p.p, x.n, srow(c, s_pr), srow(c, s_pp), omega);
     GB_LAUNCH_CHECK();
     c->launches++;
     return;

@@ -5,6 +5,7 @@
 // outer iterations need no rescaling); all arithmetic runs in FP32.  The
 // outer FP64 GCR and the rest of the K-cycle are unchanged.
 #include "kernels.cuh"
+#include "tune.cuh"
 #include "wilson_ops.cuh"
 
 namespace gbmg {
@@ -31,9 +32,11 @@ __global__ void k_clover_to16(__nv_bfloat16* __restrict__ out, const float* __re
 
 // out = M in on 16-bit vectors; one thread per site, CTAs vector-fastest
 // (as the FP32 kernel).  LC = 6: two-row links, third row rebuilt with the
-// boundary sign of the link.
-template <int LC>
-__global__ void __launch_bounds__(128) k_wilson16(bf16c* __restrict__ out,
+// boundary sign of the link.  MINB: minimum resident CTAs per SM promised
+// to the compiler (0: none), which sets its register budget and with it how
+// far ahead of the arithmetic it can issue the neighbour loads.
+template <int LC, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_wilson16(bf16c* __restrict__ out,
                                                   const bf16c* __restrict__ in,
                                                   const bf16c* __restrict__ U,
                                                   const __nv_bfloat16* __restrict__ A, Geom g,
@@ -165,16 +168,33 @@ void wilson16_apply(mg_ctx* c, Vec out, Vec in, cudaStream_t st) {
   const double bytes = double(L.g.vol) * (96.0 * nvec + (L.gauge12_ok ? 4 * 24.0 : 4 * 36.0) +
                                           144.0);
   ProfScope ps(c->prof, st, "wilson_clover16", 0, bytes, double(nvec) * L.g.vol * 1824.0);
-  if (L.gauge12_ok)
-    k_wilson16<6><<<grid, 128, 0, st>>>((bf16c*)out.p, (const bf16c*)in.p,
-                                        L.gauge16.as<bf16c>(),
-                                        L.clover16.as<__nv_bfloat16>(), L.g, float(L.diag), vs,
-                                        nvec, c->p.t_antiperiodic);
-  else
-    k_wilson16<9><<<grid, 128, 0, st>>>((bf16c*)out.p, (const bf16c*)in.p,
-                                        L.gauge16.as<bf16c>(),
-                                        L.clover16.as<__nv_bfloat16>(), L.g, float(L.diag), vs,
-                                        nvec, c->p.t_antiperiodic);
+  auto* o = (bf16c*)out.p;
+  auto* i = (const bf16c*)in.p;
+  const bf16c* U = L.gauge16.as<bf16c>();
+  const __nv_bfloat16* A = L.clover16.as<__nv_bfloat16>();
+  const float dg = float(L.diag);
+  const int ap = c->p.t_antiperiodic;
+  // autotuned register budget: minimum CTAs per SM 0 (none), 3, 4 or 6
+  auto launch = [&](int q) {
+    if (L.gauge12_ok) {
+      switch (q) {
+        case 3: k_wilson16<6, 3><<<grid, 128, 0, st>>>(o, i, U, A, L.g, dg, vs, nvec, ap); break;
+        case 4: k_wilson16<6, 4><<<grid, 128, 0, st>>>(o, i, U, A, L.g, dg, vs, nvec, ap); break;
+        case 6: k_wilson16<6, 6><<<grid, 128, 0, st>>>(o, i, U, A, L.g, dg, vs, nvec, ap); break;
+        default: k_wilson16<6, 0><<<grid, 128, 0, st>>>(o, i, U, A, L.g, dg, vs, nvec, ap); break;
+      }
+    } else {
+      switch (q) {
+        case 3: k_wilson16<9, 3><<<grid, 128, 0, st>>>(o, i, U, A, L.g, dg, vs, nvec, ap); break;
+        case 4: k_wilson16<9, 4><<<grid, 128, 0, st>>>(o, i, U, A, L.g, dg, vs, nvec, ap); break;
+        case 6: k_wilson16<9, 6><<<grid, 128, 0, st>>>(o, i, U, A, L.g, dg, vs, nvec, ap); break;
+        default: k_wilson16<9, 0><<<grid, 128, 0, st>>>(o, i, U, A, L.g, dg, vs, nvec, ap); break;
+      }
+    }
+  };
+  const std::string key = "wilson16/v" + std::to_string(L.g.vol) + "/n" + std::to_string(nvec) +
+                          "/c" + std::to_string(int(L.gauge12_ok));
+  launch(Tuner::get().choose(key, {0, 3, 4, 6}, st, launch));
   GB_LAUNCH_CHECK();
   c->launches++;
 }

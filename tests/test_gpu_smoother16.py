@@ -26,9 +26,12 @@ def _ctx(gb, dims, blocks, nvecs, U=None, **kw):
     return gb.Multigrid(p, to_dev(U)), U
 
 
+@pytest.mark.parametrize("policy", [0, 3, 4, 6])
 @pytest.mark.parametrize("unitary", [True, False])
-def test_bf16_operator(gpu_lib, unitary):
-    """Two-row links for an SU(3) field, all nine entries otherwise."""
+def test_bf16_operator(gpu_lib, unitary, policy):
+    """Two-row links for an SU(3) field, all nine entries otherwise; every
+    register-budget policy of the kernel pinned in turn (minimum CTAs per
+    SM 0, 3, 4, 6)."""
     gb = gpu_lib
     dims = (4, 4, 4, 6)
     U = syn.gauge_field(dims, 0.5, 5) * (1.0 if unitary else 1.05)
@@ -37,7 +40,13 @@ def test_bf16_operator(gpu_lib, unitary):
     psi = syn.gaussian_field((nr, lat.volume(dims), 12), 111)
     xin = torch.from_numpy(np.stack([psi.real, psi.imag], -1)).to("cuda", torch.bfloat16)
     out = torch.empty_like(xin)
-    gb.mg_wilson_clover_apply_bf16(mg.ctx, out, xin, nr)
+    key = f"wilson16/v{lat.volume(dims)}/n{nr}/c{int(unitary)}"
+    gb.mg_tune_set(key, policy)
+    try:
+        gb.mg_wilson_clover_apply_bf16(mg.ctx, out, xin, nr)
+        assert gb.mg_tune_get(key) == policy
+    finally:
+        gb.mg_tune_set(key, -1)
     o = out.float().cpu().numpy()
     got = o[..., 0] + 1j * o[..., 1]
     op = oracle_fine(U, dims)
