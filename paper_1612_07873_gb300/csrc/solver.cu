@@ -116,8 +116,9 @@ std::vector<double> read_slot(mg_ctx* c, int s, int nr, cudaStream_t st) {
   return v;
 }
 
-// x = MR_k(b) from a zero guess
-void mr_smooth(mg_ctx* c, int l, Vec x, Vec b, cudaStream_t st) {
+// x = MR_k(b) from a zero guess.  res (optional, level precision, not b):
+// receives the smoother's own residual b - A x, which MR keeps up to date.
+void mr_smooth(mg_ctx* c, int l, Vec x, Vec b, cudaStream_t st, const Vec* res = nullptr) {
   auto& w = c->ws->lv[l];
   Level& L = c->L[l];
   if (l == 0 && smoother16_enabled(c)) {
@@ -133,9 +134,10 @@ void mr_smooth(mg_ctx* c, int l, Vec x, Vec b, cudaStream_t st) {
       blas_mr_update(c, x16, r16, p16, slot(l, S_PR), slot(l, S_PP), c->p.mr_omega, st);
     }
     blas_copy(c, x, x16, st);
+    if (res) blas_copy(c, *res, r16, st);
     return;
   }
-  Vec r = vbuf(w.mrr, L.vprec, L.vec_elems(), x.nr);
+  Vec r = res ? *res : vbuf(w.mrr, L.vprec, L.vec_elems(), x.nr);
   Vec p = vbuf(w.mrp, L.vprec, L.vec_elems(), x.nr);
   blas_zero(c, x, st);
   blas_copy(c, r, b, st);
@@ -164,8 +166,11 @@ void schur_apply(mg_ctx* c, int l, Vec out, Vec in, Vec tmp, cudaStream_t st) {
 }
 
 // z = approximate M^-1 r through the Schur system (Secs. 3.3, 7.1):
-// b^ = r_o - H_oe A_e^-1 r_e, x_o = MR_k(S, b^), z_e = A_e^-1 (r_e - H_eo x_o)
-void schur_smooth(mg_ctx* c, int l, Vec z, Vec r, cudaStream_t st) {
+// b^ = r_o - H_oe A_e^-1 r_e, x_o = MR_k(S, b^), z_e = A_e^-1 (r_e - H_eo x_o).
+// res (optional): the full residual r - M z, which is zero on the even
+// sites (z_e solves the even rows exactly) and b^ - S x_o, the MR
+// residual, on the odd ones.
+void schur_smooth(mg_ctx* c, int l, Vec z, Vec r, cudaStream_t st, const Vec* res = nullptr) {
   auto& w = c->ws->lv[l];
   Level& L = c->L[l];
   const int nr = z.nr;
@@ -183,6 +188,10 @@ void schur_smooth(mg_ctx* c, int l, Vec z, Vec r, cudaStream_t st) {
   }
   eo_apply(c, l, EO_AINV_XC_MINUS_HOP, ht, hx, he.p, 0, st);
   eo_merge(c, l, z, ht, hx, st);
+  if (res) {
+    blas_zero(c, he, st);
+    eo_merge(c, l, *res, he, hr, st);
+  }
 }
 
 struct GcrOut {
@@ -316,16 +325,16 @@ void kcycle(mg_ctx* c, int l, Vec z, Vec r, cudaStream_t st, mg_solve_stats* sta
   auto& wc = c->ws->lv[nl];
   Vec rc = vbuf(wc.rhs, C.vprec, C.vec_elems(), nr), ec = vbuf(wc.x, C.vprec, C.vec_elems(), nr);
   const bool rb = c->p.red_black && L.have_schur;
-  auto smooth = [&](Vec out, Vec in) {
+  auto smooth = [&](Vec out, Vec in, const Vec* res) {
     if (rb)
-      schur_smooth(c, l, out, in, st);
+      schur_smooth(c, l, out, in, st, res);
     else
-      mr_smooth(c, l, out, in, st);
+      mr_smooth(c, l, out, in, st, res);
   };
-  // pre-smooth
-  smooth(z, r);
-  level_apply(c, l, tmp, z, st);
-  blas_sub(c, kres, r, tmp, st);
+  // pre-smooth; the smoother hands back kres = r - A z from its own
+  // residual recurrence (equal to the recomputed residual in exact
+  // arithmetic), which saves an operator apply per cycle
+  smooth(z, r, &kres);
   // coarse-grid correction
   restrict_apply(c, l, rc, kres, st);
   if (nl == c->nlevels - 1) {
@@ -350,7 +359,7 @@ void kcycle(mg_ctx* c, int l, Vec z, Vec r, cudaStream_t st, mg_solve_stats* sta
   // post-smooth
   level_apply(c, l, tmp, z, st);
   blas_sub(c, kres, r, tmp, st);
-  smooth(mrx, kres);
+  smooth(mrx, kres, nullptr);
   blas_axpy_host(c, z, mrx, 1.0, 0.0, st);
 }
 
