@@ -353,7 +353,8 @@ mg_status mg_device_status(mg_ctx* ctx, void* stream);
 /* out[0] + i out[1] = sum_k conj(a_k) b_k over one vector of `level`
  * (level_volume x level_dof complex numbers in `prec`, MG_F32 or MG_F64,
  * device memory, caller-owned), with the accumulation the solvers use
- * (Sec. 7.1): fp64 != 0 is the outer GCR's orthogonalisation form, FP64
+ * (Sec. 7.1; the same kernels as GCR's norms and Gram-Schmidt
+ * coefficients): fp64 != 0 is the outer GCR's orthogonalisation form, FP64
  * accurate (FP32 operands: exact products summed in float-float pairs, the
  * pairs combined in FP64); fp64 = 0 the inner levels' form (FP32 operands:
  * FP32 partial sums combined in FP64).  a == b gives |a|^2.  Synchronises

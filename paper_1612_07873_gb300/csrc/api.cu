@@ -621,7 +621,12 @@ mg_status mg_inner_product(mg_ctx* c, int level, const void* a, const void* b, m
     const size_t n = c->L[level].vec_elems();
     Vec va{const_cast<void*>(a), prec, n, 1}, vb{const_cast<void*>(b), prec, n, 1};
     const int slot = level * 8 + 7;  // the solvers use slots 0..5 of each level
-    blas_dot(c, va, vb, slot, S(stream), fp64 != 0);
+    // the kernels GCR uses: norms by blas_dot, products of two vectors by
+    // the block Gram-Schmidt reduction
+    if (a == b)
+      blas_dot(c, va, va, slot, S(stream), fp64 != 0);
+    else
+      blas_dot_multi(c, &va, 1, vb, slot, S(stream), fp64 != 0);
     blas_read_slot_c(c, slot, out, S(stream));
   });
 }

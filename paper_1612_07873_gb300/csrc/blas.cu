@@ -19,18 +19,19 @@ constexpr int kMaxRedBlocks = 1024;
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 // Reduction grid: one block per 4096 elements, at most one full wave of
-// the reduction kernels (<= 64 registers a thread, so 4 blocks of 256
-// threads per SM); a second, partly filled wave would leave SMs idle at
-// the end.  The grid depends only on the length and the device.
-int red_blocks(size_t n) {
-  static const int cap = [] {
-    int dev = 0, sms = 0;
+// the reduction kernel (per_sm resident blocks of 256 threads: 4 for the
+// kernels of <= 64 registers a thread); a second, partly filled wave would
+// leave SMs idle at the end.  The grid depends only on the length and the
+// device.
+int red_blocks(size_t n, int per_sm = 4) {
+  static const int sms = [] {
+    int dev = 0, v = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        sms < 1)
-      return kMaxRedBlocks;
-    return 4 * sms < kMaxRedBlocks ? 4 * sms : kMaxRedBlocks;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1)
+      return kMaxRedBlocks / 4;
+    return v;
   }();
+  const int cap = per_sm * sms < kMaxRedBlocks ? per_sm * sms : kMaxRedBlocks;
   long long b = (long long)((n + 4095) / 4096);
   if (b < 1) b = 1;
   if (b > cap) b = cap;
@@ -191,6 +192,145 @@ __global__ void k_dot_partial_ff(const cpx<float>* __restrict__ a, const cpx<flo
   }
   double2 d = block_sum(make_double2(re, im), sh);
   if (threadIdx.x == 0) part[size_t(blockIdx.y) * gridDim.x + blockIdx.x] = d;
+}
+
+// ---- block Gram-Schmidt: m <= kCgs vectors X[j] (nr right-hand sides each,
+// back to back) against y in one pass.
+struct VecList {
+  const void* p[kCgs];
+};
+
+// partial <X[j], y> per block at part[(v m + j) * gridDim.x + block].  FF:
+// float-float sums of exact products (FP32 operands, FP64-accurate);
+// otherwise sums in acc_t<R, R>.  Each j is its own accumulation chain.
+template <typename R, bool FF>
+__global__ void __launch_bounds__(256, 2) k_dot_multi(VecList X, const cpx<R>* __restrict__ y, int m, size_t n,
+                            double2* __restrict__ part) {
+  using T = acc_t<R, R>;
+  __shared__ double2 sh[32];
+  const int v = blockIdx.y;
+  const size_t off = size_t(v) * n;
+  y += off;
+  cpx<T> acc[kCgs];
+  float rh[kCgs], rl[kCgs], ih[kCgs], il[kCgs];
+#pragma unroll
+  for (int j = 0; j < kCgs; ++j) {
+    acc[j] = cpx<T>(T(0), T(0));
+    rh[j] = rl[j] = ih[j] = il[j] = 0.f;
+  }
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
+       i += size_t(gridDim.x) * blockDim.x) {
+    const cpx<R> yi = y[i];
+#pragma unroll
+    for (int j = 0; j < kCgs; ++j)
+      if (j < m) {
+        const cpx<R> xj = static_cast<const cpx<R>*>(X.p[j])[off + i];
+        if constexpr (FF) {
+          ff_mac(rh[j], rl[j], xj.re, yi.re);  // conj(x) y
+          ff_mac(rh[j], rl[j], xj.im, yi.im);
+          ff_mac(ih[j], il[j], xj.re, yi.im);
+          ff_mac(ih[j], il[j], -xj.im, yi.re);
+          ff_renorm(rh[j], rl[j]);
+          ff_renorm(ih[j], il[j]);
+        } else {
+          cmac_conj(acc[j], cpx<T>(xj), cpx<T>(yi));
+        }
+      }
+  }
+#pragma unroll
+  for (int j = 0; j < kCgs; ++j)
+    if (j < m) {  // m is uniform: every thread takes the same branches
+      double2 d;
+      if constexpr (FF)
+        d = make_double2(double(rh[j]) + double(rl[j]), double(ih[j]) + double(il[j]));
+      else
+        d = make_double2(double(acc[j].re), double(acc[j].im));
+      d = block_sum(d, sh);
+      if (threadIdx.x == 0) part[(size_t(v) * m + j) * gridDim.x + blockIdx.x] = d;
+      __syncthreads();
+    }
+}
+
+// The float-float form of k_dot_multi for a compile-time count M of
+// vectors, 16-byte loads of two complex numbers (16-byte aligned vectors, n
+// even): registers grow with M only, so small blocks keep many warps and
+// loads in flight.
+template <int M>
+__global__ void __launch_bounds__(256) k_dot_multi_ff(VecList X, const cpx<float>* __restrict__ y,
+                                                      size_t n, double2* __restrict__ part) {
+  __shared__ double2 sh[32];
+  const int v = blockIdx.y;
+  const size_t off2 = size_t(v) * (n / 2);
+  const float4* y4 = reinterpret_cast<const float4*>(y) + off2;
+  float rh[M], rl[M], ih[M], il[M];
+#pragma unroll
+  for (int j = 0; j < M; ++j) rh[j] = rl[j] = ih[j] = il[j] = 0.f;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n / 2;
+       i += size_t(gridDim.x) * blockDim.x) {
+    const float4 yv = y4[i];
+    float4 xv[M];
+#pragma unroll
+    for (int j = 0; j < M; ++j) xv[j] = (reinterpret_cast<const float4*>(X.p[j]) + off2)[i];
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+      ff_mac(rh[j], rl[j], xv[j].x, yv.x);  // conj(x) y, first complex number
+      ff_mac(rh[j], rl[j], xv[j].y, yv.y);
+      ff_mac(ih[j], il[j], xv[j].x, yv.y);
+      ff_mac(ih[j], il[j], -xv[j].y, yv.x);
+      ff_mac(rh[j], rl[j], xv[j].z, yv.z);  // second
+      ff_mac(rh[j], rl[j], xv[j].w, yv.w);
+      ff_mac(ih[j], il[j], xv[j].z, yv.w);
+      ff_mac(ih[j], il[j], -xv[j].w, yv.z);
+      ff_renorm(rh[j], rl[j]);
+      ff_renorm(ih[j], il[j]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    double2 d = make_double2(double(rh[j]) + double(rl[j]), double(ih[j]) + double(il[j]));
+    d = block_sum(d, sh);
+    if (threadIdx.x == 0) part[(size_t(v) * M + j) * gridDim.x + blockIdx.x] = d;
+    __syncthreads();
+  }
+}
+
+// row r = v m + j of the partials -> S[j][v] (slot stride kMaxNrhs)
+__global__ void k_reduce_final_multi(const double2* __restrict__ part, int nparts, int m,
+                                     double2* __restrict__ S) {
+  __shared__ double2 sh[32];
+  const double2* src = part + size_t(blockIdx.x) * nparts;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+    acc.x += src[i].x;
+    acc.y += src[i].y;
+  }
+  acc = block_sum(acc, sh);
+  const int v = blockIdx.x / m, j = blockIdx.x - v * m;
+  if (threadIdx.x == 0) S[size_t(j) * kMaxNrhs + v] = acc;
+}
+
+// y += sign sum_j S[j][v] X[j]
+template <typename R>
+__global__ void k_axpy_multi(cpx<R>* __restrict__ y, VecList X, int m, size_t n,
+                             const double2* __restrict__ S, double sign) {
+  using T = acc_t<R, R>;
+  const int v = blockIdx.y;
+  const size_t off = size_t(v) * n;
+  cpx<T> a[kCgs];
+#pragma unroll
+  for (int j = 0; j < kCgs; ++j) {
+    const double2 s = j < m ? S[size_t(j) * kMaxNrhs + v] : make_double2(0.0, 0.0);
+    a[j] = cpx<T>(T(sign * s.x), T(sign * s.y));
+  }
+  y += off;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
+       i += size_t(gridDim.x) * blockDim.x) {
+    cpx<T> yy(y[i]);
+#pragma unroll
+    for (int j = 0; j < kCgs; ++j)
+      if (j < m) cmac(yy, a[j], cpx<T>(static_cast<const cpx<R>*>(X.p[j])[off + i]));
+    y[i] = cpx<R>(yy);
+  }
 }
 
 // <p, r> and |p|^2 in one pass; partials at part[(2 v + k) * gridDim.x + block]
@@ -799,6 +939,66 @@ void blas_read_slot(mg_ctx* c, int slot, int nr, double* out_re, cudaStream_t st
                            cudaMemcpyDeviceToHost, st));
   GB_CHECK(cudaStreamSynchronize(st));
   for (int v = 0; v < nr; ++v) out_re[v] = c->h_scalars[2 * v];
+}
+
+void blas_dot_multi(mg_ctx* c, const Vec* X, int m, Vec y, int slot, cudaStream_t st,
+                    bool fp64_partials) {
+  check_nr(y);
+  GB_REQUIRE(m >= 1 && m <= kCgs && slot + m <= SC_COUNT, MG_ERR_ARG, "dot_multi: bad count");
+  VecList L{};
+  for (int j = 0; j < m; ++j) {
+    GB_REQUIRE(X[j].n == y.n && X[j].nr == y.nr && X[j].prec == y.prec, MG_ERR_ARG,
+               "dot_multi: shape mismatch");
+    L.p[j] = X[j].p;
+  }
+  bool w2 = y.prec == MG_F32 && fp64_partials && y.n % 2 == 0 && aligned16(y.p);
+  for (int j = 0; j < m; ++j) w2 = w2 && aligned16(X[j].p);
+  // resident blocks per SM from the registers a thread: k_dot_multi <= 128;
+  // k_dot_multi_ff<M> <= 64 up to M = 6, <= 80 up to M = 8, <= 128 beyond
+  const int nb = red_blocks(y.n, !w2 ? 2 : m <= 6 ? 4 : m <= 8 ? 3 : 2);
+  double2* part = partials(c, size_t(nb) * m * y.nr);
+  const dim3 grid(nb, y.nr);
+  const auto* yp = (const cpx<float>*)y.p;
+  if (w2) {
+    switch (m) {
+      case 1: k_dot_multi_ff<1><<<grid, kThreads, 0, st>>>(L, yp, y.n, part); break;
+      case 2: k_dot_multi_ff<2><<<grid, kThreads, 0, st>>>(L, yp, y.n, part); break;
+      case 3: k_dot_multi_ff<3><<<grid, kThreads, 0, st>>>(L, yp, y.n, part); break;
+      case 4: k_dot_multi_ff<4><<<grid, kThreads, 0, st>>>(L, yp, y.n, part); break;
+      case 5: k_dot_multi_ff<5><<<grid, kThreads, 0, st>>>(L, yp, y.n, part); break;
+      case 6: k_dot_multi_ff<6><<<grid, kThreads, 0, st>>>(L, yp, y.n, part); break;
+      case 7: k_dot_multi_ff<7><<<grid, kThreads, 0, st>>>(L, yp, y.n, part); break;
+      case 8: k_dot_multi_ff<8><<<grid, kThreads, 0, st>>>(L, yp, y.n, part); break;
+      case 9: k_dot_multi_ff<9><<<grid, kThreads, 0, st>>>(L, yp, y.n, part); break;
+      default: k_dot_multi_ff<10><<<grid, kThreads, 0, st>>>(L, yp, y.n, part); break;
+    }
+  } else if (y.prec == MG_F32 && fp64_partials)
+    k_dot_multi<float, true><<<grid, kThreads, 0, st>>>(L, yp, m, y.n, part);
+  else
+    GB_DISPATCH1(y.prec, R,
+                 (k_dot_multi<R, false><<<grid, kThreads, 0, st>>>(L, (const cpx<R>*)y.p, m,
+                                                                  y.n, part)));
+  GB_LAUNCH_CHECK();
+  k_reduce_final_multi<<<m * y.nr, 256, 0, st>>>(part, nb, m, srow(c, slot));
+  GB_LAUNCH_CHECK();
+  c->launches += 2;
+}
+
+void blas_axpy_multi(mg_ctx* c, Vec y, const Vec* X, int m, int slot, double sign,
+                     cudaStream_t st) {
+  check_nr(y);
+  GB_REQUIRE(m >= 1 && m <= kCgs && slot + m <= SC_COUNT, MG_ERR_ARG, "axpy_multi: bad count");
+  VecList L{};
+  for (int j = 0; j < m; ++j) {
+    GB_REQUIRE(X[j].n == y.n && X[j].nr == y.nr && X[j].prec == y.prec, MG_ERR_ARG,
+               "axpy_multi: shape mismatch");
+    L.p[j] = X[j].p;
+  }
+  GB_DISPATCH1(y.prec, R,
+               (k_axpy_multi<R><<<ew_grid_b(y.n, y.nr), kThreads, 0, st>>>(
+                   (cpx<R>*)y.p, L, m, y.n, srow(c, slot), sign)));
+  GB_LAUNCH_CHECK();
+  c->launches++;
 }
 
 void blas_read_slot_c(mg_ctx* c, int slot, double out[2], cudaStream_t st) {

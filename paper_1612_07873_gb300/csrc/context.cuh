@@ -118,7 +118,8 @@ struct Level {
 // Scalars that solver kernels exchange through device memory: SC_COUNT
 // slots, each with one complex double per right-hand side.
 enum ScalarSlot {
-  SC_COUNT = 64
+  SC_CGS = 32,  // first slot of the block Gram-Schmidt coefficients (10 per level)
+  SC_COUNT = 96
 };
 constexpr int kMaxNrhs = MG_MAX_NRHS;
 

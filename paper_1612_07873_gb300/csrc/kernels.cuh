@@ -43,6 +43,14 @@ void blas_scale_invnorm(mg_ctx* c, Vec a, Vec b, int slot, cudaStream_t st);
 // x_v += S[slot][v] z_v ; r_v -= S[slot][v] w_v
 void blas_gcr_update(mg_ctx* c, Vec x, Vec r, Vec z, Vec w, int slot, cudaStream_t st);
 // real parts of S[slot][0..nr) to the host (synchronises st)
+// Block (classical) Gram-Schmidt against m <= kCgs vectors X[j] in one
+// pass each: S[slot + j] = <X[j], y> (FP64-accurate when fp64_partials;
+// see blas_dot), then y += sign sum_j S[slot + j] X[j].
+constexpr int kCgs = 10;  // GCR(10) needs at most 9
+void blas_dot_multi(mg_ctx* c, const Vec* X, int m, Vec y, int slot, cudaStream_t st,
+                    bool fp64_partials);
+void blas_axpy_multi(mg_ctx* c, Vec y, const Vec* X, int m, int slot, double sign,
+                     cudaStream_t st);
 void blas_read_slot(mg_ctx* c, int slot, int nr, double* out_re, cudaStream_t st);
 // both parts of right-hand side 0's value in `slot` (synchronises)
 void blas_read_slot_c(mg_ctx* c, int slot, double out[2], cudaStream_t st);

@@ -15,6 +15,7 @@
 // batched kernel per step, per-RHS scalars), so the fine operator's links,
 // the prolongator and the coarse links are read once per step for all nr.
 // A GCR loop ends when every right-hand side meets its tolerance.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 
@@ -276,11 +277,20 @@ GcrOut gcr(mg_ctx* c, int l, Vec x, Vec b, bool precond, double tol, int maxiter
         blas_copy(c, Zk, r, st);
       }
       op(Wk, Zk);
-      for (int j = 0; j < k; ++j) {
-        Vec Zj = vbuf(*w.Z[j], L.vprec, n, nr), Wj = vbuf(*w.W[j], L.vprec, n, nr);
-        blas_dot(c, Wj, Wk, slot(l, S_BETA), st, outer);
-        blas_axpy_slot(c, Wk, Wj, slot(l, S_BETA), -1.0, st);
-        blas_axpy_slot(c, Zk, Zj, slot(l, S_BETA), -1.0, st);
+      // block (classical) Gram-Schmidt against the previous W_j, up to kCgs
+      // per pass: all beta_j = <W_j, W_k> in one pass over the vectors,
+      // then one update of W_k and one of Z_k
+      for (int j0 = 0; j0 < k; j0 += kCgs) {
+        const int m = std::min(kCgs, k - j0);
+        Vec Ws[kCgs], Zs[kCgs];
+        for (int j = 0; j < m; ++j) {
+          Ws[j] = vbuf(*w.W[j0 + j], L.vprec, n, nr);
+          Zs[j] = vbuf(*w.Z[j0 + j], L.vprec, n, nr);
+        }
+        const int cs = SC_CGS + kCgs * l;
+        blas_dot_multi(c, Ws, m, Wk, cs, st, outer);
+        blas_axpy_multi(c, Wk, Ws, m, cs, -1.0, st);
+        blas_axpy_multi(c, Zk, Zs, m, cs, -1.0, st);
       }
       blas_norm2(c, Wk, slot(l, S_NRM), st, outer);
       blas_scale_invnorm(c, Wk, Zk, slot(l, S_NRM), st);
