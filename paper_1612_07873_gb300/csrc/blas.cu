@@ -333,6 +333,39 @@ __global__ void k_axpy_multi(cpx<R>* __restrict__ y, VecList X, int m, size_t n,
   }
 }
 
+// k_axpy_multi for FP32 vectors with a compile-time count M, 16-byte loads
+// of two complex numbers (16-byte aligned vectors, n even)
+template <int M>
+__global__ void __launch_bounds__(256) k_axpy_multi_w2(cpx<float>* __restrict__ y, VecList X,
+                                                       size_t n, const double2* __restrict__ S,
+                                                       double sign) {
+  const int v = blockIdx.y;
+  const size_t off2 = size_t(v) * (n / 2);
+  float ar[M], ai[M];
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    const double2 s = S[size_t(j) * kMaxNrhs + v];
+    ar[j] = float(sign * s.x);
+    ai[j] = float(sign * s.y);
+  }
+  float4* y4 = reinterpret_cast<float4*>(y) + off2;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n / 2;
+       i += size_t(gridDim.x) * blockDim.x) {
+    float4 yy = y4[i];
+    float4 xv[M];
+#pragma unroll
+    for (int j = 0; j < M; ++j) xv[j] = (reinterpret_cast<const float4*>(X.p[j]) + off2)[i];
+#pragma unroll
+    for (int j = 0; j < M; ++j) {  // yy += a_j x_j, two complex numbers
+      yy.x = fmaf(ar[j], xv[j].x, fmaf(-ai[j], xv[j].y, yy.x));
+      yy.y = fmaf(ar[j], xv[j].y, fmaf(ai[j], xv[j].x, yy.y));
+      yy.z = fmaf(ar[j], xv[j].z, fmaf(-ai[j], xv[j].w, yy.z));
+      yy.w = fmaf(ar[j], xv[j].w, fmaf(ai[j], xv[j].z, yy.w));
+    }
+    y4[i] = yy;
+  }
+}
+
 // <p, r> and |p|^2 in one pass; partials at part[(2 v + k) * gridDim.x + block]
 template <typename Ra, typename Rb>
 __global__ void k_dot2_partial_b(const cpx<Ra>* __restrict__ p, const cpx<Rb>* __restrict__ r,
@@ -531,15 +564,42 @@ __global__ void k_gcr_update(cpx<Rx>* __restrict__ x, cpx<Rx>* __restrict__ r,
 // arithmetic FP32, per-thread sums FP32 and cross-thread sums FP64
 __device__ __forceinline__ cpx<float> h2f(bf16c v) { return StoreTraits<bf16c>::load(v); }
 
+// W = 1: one complex number per access; W = 4: 16-byte words of four BF16
+// complex numbers (both vectors 16-byte aligned, n a multiple of 4)
+template <int W>
 __global__ void k_copy_to16(bf16c* __restrict__ y, const cpx<float>* __restrict__ x, size_t n) {
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
-       i += size_t(gridDim.x) * blockDim.x)
-    y[i] = StoreTraits<bf16c>::pack(x[i]);
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n / W;
+       i += size_t(gridDim.x) * blockDim.x) {
+    if constexpr (W == 4) {
+      const float4* x4 = reinterpret_cast<const float4*>(x) + 2 * i;
+      const float4 a = x4[0], b = x4[1];
+      uint4 o;
+      bf16c* oc = reinterpret_cast<bf16c*>(&o);
+      oc[0] = StoreTraits<bf16c>::pack(cpx<float>(a.x, a.y));
+      oc[1] = StoreTraits<bf16c>::pack(cpx<float>(a.z, a.w));
+      oc[2] = StoreTraits<bf16c>::pack(cpx<float>(b.x, b.y));
+      oc[3] = StoreTraits<bf16c>::pack(cpx<float>(b.z, b.w));
+      reinterpret_cast<uint4*>(y)[i] = o;
+    } else {
+      y[i] = StoreTraits<bf16c>::pack(x[i]);
+    }
+  }
 }
+template <int W>
 __global__ void k_copy_from16(cpx<float>* __restrict__ y, const bf16c* __restrict__ x, size_t n) {
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
-       i += size_t(gridDim.x) * blockDim.x)
-    y[i] = h2f(x[i]);
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n / W;
+       i += size_t(gridDim.x) * blockDim.x) {
+    if constexpr (W == 4) {
+      const uint4 w = reinterpret_cast<const uint4*>(x)[i];
+      const bf16c* wc = reinterpret_cast<const bf16c*>(&w);
+      const cpx<float> c0 = h2f(wc[0]), c1 = h2f(wc[1]), c2 = h2f(wc[2]), c3 = h2f(wc[3]);
+      float4* y4 = reinterpret_cast<float4*>(y) + 2 * i;
+      y4[0] = make_float4(c0.re, c0.im, c1.re, c1.im);
+      y4[1] = make_float4(c2.re, c2.im, c3.re, c3.im);
+    } else {
+      y[i] = h2f(x[i]);
+    }
+  }
 }
 
 // W = 1: one complex number per access; W = 4: 16-byte loads of four (the
@@ -766,12 +826,23 @@ void blas_copy(mg_ctx* c, Vec d, Vec s, cudaStream_t st) {
   GB_REQUIRE(d.total() == s.total(), MG_ERR_ARG, "copy: length mismatch");
   if (d.prec != s.prec && (d.prec == MG_BF16 || s.prec == MG_BF16)) {
     GB_REQUIRE(d.prec == MG_F32 || s.prec == MG_F32, MG_ERR_ARG, "copy: BF16 <-> FP32 only");
-    if (d.prec == MG_BF16)
-      k_copy_to16<<<ew_blocks(d.total()), kThreads, 0, st>>>((bf16c*)d.p,
-                                                             (const cpx<float>*)s.p, d.total());
-    else
-      k_copy_from16<<<ew_blocks(d.total()), kThreads, 0, st>>>((cpx<float>*)d.p,
-                                                               (const bf16c*)s.p, d.total());
+    const size_t n = d.total();
+    const bool w4 = n % 4 == 0 && aligned16(d.p) && aligned16(s.p);
+    if (d.prec == MG_BF16) {
+      if (w4)
+        k_copy_to16<4><<<ew_blocks(n / 4), kThreads, 0, st>>>((bf16c*)d.p,
+                                                              (const cpx<float>*)s.p, n);
+      else
+        k_copy_to16<1><<<ew_blocks(n), kThreads, 0, st>>>((bf16c*)d.p, (const cpx<float>*)s.p,
+                                                          n);
+    } else {
+      if (w4)
+        k_copy_from16<4><<<ew_blocks(n / 4), kThreads, 0, st>>>((cpx<float>*)d.p,
+                                                                (const bf16c*)s.p, n);
+      else
+        k_copy_from16<1><<<ew_blocks(n), kThreads, 0, st>>>((cpx<float>*)d.p,
+                                                            (const bf16c*)s.p, n);
+    }
     GB_LAUNCH_CHECK();
     c->launches++;
     return;
@@ -994,9 +1065,29 @@ void blas_axpy_multi(mg_ctx* c, Vec y, const Vec* X, int m, int slot, double sig
                "axpy_multi: shape mismatch");
     L.p[j] = X[j].p;
   }
-  GB_DISPATCH1(y.prec, R,
-               (k_axpy_multi<R><<<ew_grid_b(y.n, y.nr), kThreads, 0, st>>>(
-                   (cpx<R>*)y.p, L, m, y.n, srow(c, slot), sign)));
+  bool w2 = y.prec == MG_F32 && y.n % 2 == 0 && aligned16(y.p);
+  for (int j = 0; j < m; ++j) w2 = w2 && aligned16(X[j].p);
+  if (w2) {
+    const dim3 grid = ew_grid_b(y.n / 2, y.nr);
+    auto* yp = (cpx<float>*)y.p;
+    const double2* S = srow(c, slot);
+    switch (m) {
+      case 1: k_axpy_multi_w2<1><<<grid, kThreads, 0, st>>>(yp, L, y.n, S, sign); break;
+      case 2: k_axpy_multi_w2<2><<<grid, kThreads, 0, st>>>(yp, L, y.n, S, sign); break;
+      case 3: k_axpy_multi_w2<3><<<grid, kThreads, 0, st>>>(yp, L, y.n, S, sign); break;
+      case 4: k_axpy_multi_w2<4><<<grid, kThreads, 0, st>>>(yp, L, y.n, S, sign); break;
+      case 5: k_axpy_multi_w2<5><<<grid, kThreads, 0, st>>>(yp, L, y.n, S, sign); break;
+      case 6: k_axpy_multi_w2<6><<<grid, kThreads, 0, st>>>(yp, L, y.n, S, sign); break;
+      case 7: k_axpy_multi_w2<7><<<grid, kThreads, 0, st>>>(yp, L, y.n, S, sign); break;
+      case 8: k_axpy_multi_w2<8><<<grid, kThreads, 0, st>>>(yp, L, y.n, S, sign); break;
+      case 9: k_axpy_multi_w2<9><<<grid, kThreads, 0, st>>>(yp, L, y.n, S, sign); break;
+      default: k_axpy_multi_w2<10><<<grid, kThreads, 0, st>>>(yp, L, y.n, S, sign); break;
+    }
+  } else {
+    GB_DISPATCH1(y.prec, R,
+                 (k_axpy_multi<R><<<ew_grid_b(y.n, y.nr), kThreads, 0, st>>>(
+                     (cpx<R>*)y.p, L, m, y.n, srow(c, slot), sign)));
+  }
   GB_LAUNCH_CHECK();
   c->launches++;
 }
