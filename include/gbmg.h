@@ -301,11 +301,13 @@ int mg_tune_get(const char* key);
  * overlap vecs_dev).  No context is needed; dims and block are host arrays.
  * Workspace: a file-scope device array of 2^21 complex doubles (32 MiB) that
  * every GPU loading the library holds until exit; calls with
- * nvec * V * ndof > 2^21 fail with MG_ERR_ARG.  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  All
- * calls share the workspace and it keeps the last call's contents: calls
- * that overlap on the GPU (other streams, other host threads) race.  The
+ * nvec * V * ndof > 2^21, nvec > 64 or an aggregate of more than 24576
+ * rows per chirality fail with MG_ERR_ARG before any device work.  The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the workspace and it keeps
+ * the last call's contents: calls that overlap on the GPU (other streams,
+ * other host threads) race.  The
  * call synchronises `stream` to read the rank test; MG_ERR_RANK as for
  * mg_set_nullvecs.  Error text: mg_last_error(NULL).                       */
 mg_status mg_block_orthonormalise_noalloc(const void* vecs_dev, void* out_dev, const int dims[4],

@@ -818,6 +818,7 @@ extern "C" mg_status mg_block_orthonormalise_noalloc(const void* vecs_dev, void*
   if (!vecs_dev || !out_dev || !dims || !block) return fail(MG_ERR_ARG, "noalloc: null argument");
   if (vecs_dev == out_dev) return fail(MG_ERR_ARG, "noalloc: output aliases input");
   if (nvec < 1 || ndof < 2 || (ndof & 1)) return fail(MG_ERR_ARG, "noalloc: bad nvec or ndof");
+  if (nvec > kQrMaxVec) return fail(MG_ERR_ARG, "noalloc: nvec exceeds 64");
   int cd[4];
   long long vol = 1;
   for (int m = 0; m < 4; ++m) {
@@ -867,7 +868,8 @@ extern "C" mg_status mg_block_orthonormalise_noalloc(const void* vecs_dev, void*
   k_mgs_gather<<<grid_for(elems), 256, 0, st>>>(slot.scratch, (const double2*)vecs_dev, m, ndof,
                                                 nvec);
   const int nblk = m.coarse.vol * 2;
-  launch_block_qr(slot.scratch, rows, nvec, nblk, slot.status, st);
+  if (!launch_block_qr(slot.scratch, rows, nvec, nblk, slot.status, st))
+    return fail(MG_ERR_ARG, "noalloc: aggregate block too large for the block QR");
   k_blocked_to_vectors<<<grid_for(elems), 256, 0, st>>>((double2*)out_dev, slot.scratch, m, ndof,
                                                      nvec);
   if (cudaGetLastError() != cudaSuccess) return fail(MG_ERR_CUDA, "noalloc: kernel launch failed");

@@ -83,3 +83,26 @@ def test_create_rejects_bad_arguments_without_a_gpu(lib):
     p.nlevels = 9
     assert gb.LIB.mg_create(C.byref(p), C.c_void_p(16), C.byref(h)) == gb.MG_ERR_ARG
     assert b"nlevels" in gb.LIB.mg_last_error(None)
+
+
+def test_noalloc_rejects_bad_arguments_without_a_gpu(lib):
+    """The allocation-free block orthonormalisation checks its arguments
+    before any device call: the pointers below are never dereferenced."""
+    import paper_1612_07873_gb300 as gb
+    f = gb.LIB.mg_block_orthonormalise_noalloc
+    a, b = C.c_void_p(256), C.c_void_p(512)
+
+    def call(dims, block, ndof, nvec, x=a, y=b):
+        return f(x, y, (C.c_int * 4)(*dims), (C.c_int * 4)(*block), ndof, nvec, None)
+
+    cases = [
+        (((4, 4, 4, 4), (2, 2, 2, 2), 12, 4, None, b), b"null"),
+        (((4, 4, 4, 4), (2, 2, 2, 2), 12, 4, a, a), b"aliases"),
+        (((4, 4, 4, 4), (2, 2, 2, 2), 11, 4), b"ndof"),
+        (((4, 4, 4, 4), (2, 2, 2, 2), 12, 65), b"exceeds 64"),
+        (((4, 4, 4, 6), (2, 2, 2, 4), 12, 4), b"divisible"),
+        (((8, 8, 8, 8), (2, 2, 2, 2), 24, 24), b"2^21"),
+    ]
+    for args, text in cases:
+        assert call(*args) == gb.MG_ERR_ARG, args
+        assert text in gb.LIB.mg_last_error(None), (args, gb.LIB.mg_last_error(None))
