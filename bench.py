@@ -136,7 +136,9 @@ class ClockSampler:
 def oracle_coarse_apply_sample(n=48, cdims=(8, 8, 8, 16), sites=1024, budget_s=12.0):
     """The FP64 oracle stencil apply (Eq. 3) on a bounded sample of the
     level-1 lattice: `sites` output sites per repetition, repeated for
-    about budget_s seconds.  Returns GB/s of FP64 algorithmic bytes."""
+    about budget_s seconds.  Returns GB/s of FP64 algorithmic bytes.
+    One core: the oracle's einsum (no `optimize`) runs numpy's own loops,
+    not a threaded BLAS, so the thread cap below is a guard, not a need."""
     from oracle import dirac, lattice as lat
     try:
         from threadpoolctl import threadpool_limits
