@@ -1,0 +1,53 @@
+"""The reference arm of bench.py (the FP64 oracle's Eq. (3) apply timed on
+host cores) prints one JSON line with the keys the benchmark contract
+fixes; checked on the CPU with a shortened sample."""
+import json
+import types
+
+
+def test_reference_line_keys(monkeypatch, capsys):
+    import bench
+    full = bench.oracle_coarse_apply_sample
+
+    def short(**kw):
+        return full(sites=32, budget_s=0.05)
+
+    monkeypatch.setattr(bench, "oracle_coarse_apply_sample", short)
+    monkeypatch.delenv("RANK", raising=False)
+    args = types.SimpleNamespace(steps=2, warmup=1, gpus=1)
+    assert bench.reference_main(args) == 0
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC
+    assert d["unit"] == "GB/s" and d["higher_is_better"] is True
+    assert d["n_gpus"] == 1 and d["steps"] == 2 and d["warmup"] == 1
+    assert d["value"] > 0 and d["ms_per_step"] > 0
+    assert d["config"]["workload"] == bench.WORKLOAD
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["sample"]
+    assert cb["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "GB/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_other_ranks_do_no_work(monkeypatch, capsys):
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setattr(bench, "oracle_coarse_apply_sample",
+                        lambda **kw: (_ for _ in ()).throw(AssertionError("ran on rank 1")))
+    assert bench.reference_main(types.SimpleNamespace(steps=1, warmup=0, gpus=2)) == 0
+    assert capsys.readouterr().out == ""
+
+
+def test_oracle_sample_counts_fp64_algorithmic_bytes(monkeypatch):
+    """GB/s = sites x (9 n^2 links + 2 n spinor) x 16 B x repetitions / s,
+    with a clock that advances one second per reading (one repetition)."""
+    import itertools
+
+    import bench
+    clock = itertools.count()
+    monkeypatch.setattr(bench.time, "perf_counter", lambda: float(next(clock)))
+    r = bench.oracle_coarse_apply_sample(n=8, cdims=(2, 2, 2, 4), sites=8, budget_s=0.5)
+    assert r["value"] == 8 * (9 * 64 * 16 + 2 * 8 * 16) / 1e9
+    assert r["unit"] == "GB/s" and r["cores"] == 1 and "1 repetitions" in r["sample"]
