@@ -392,3 +392,24 @@ def test_learned_gradient_matches_finite_differences():
         Lm, _ = ol.loss_and_grad(th - e, U, dims, nv, T, block)
         fd = (Lp - Lm) / 2e-6
         assert abs(fd - g[i]) <= 1e-5 * max(abs(fd), 1e-3), (i, fd, g[i])
+
+
+def test_galerkin_coarse_to_coarser_equals_dense_product():
+    """Level 2 from the level-1 stencil operator: 8^4 -> 4^4 (n = 8) -> 2^4
+    (n = 6).  The coarse level's chirality split is the first / second half
+    of its dofs; explicit P2^dag A1 P2 equals the assembled level-2 stencil,
+    and the level-2 operator is g5hat-hermitian."""
+    dims, block = (8, 8, 8, 8), (2, 2, 2, 2)
+    U, op, Q, cop = _hierarchy(dims, block, 4, sweeps=3)
+    x1 = syn.gaussian_field((3, cop.vol, cop.nd), 41)
+    Q2 = mgo.block_orthonormalise(mgo.null_vectors(cop, x1, 3), cop.dims, block)
+    cop2 = mgo.galerkin(cop, Q2, block)
+    assert cop2.nd == 6 and tuple(cop2.dims) == (2, 2, 2, 2)
+    P2 = mgo.dense_prolongator(Q2, cop.dims, block)
+    assert np.abs(P2.conj().T @ P2 - np.eye(P2.shape[1])).max() < 1e-14
+    want = P2.conj().T @ cop.dense() @ P2
+    assert np.abs(want - cop2.dense()).max() < 1e-13 * np.abs(want).max()
+    g5 = mgo.gamma5_hat(cop2.nd)
+    u, v = _rand((cop2.vol, cop2.nd)), _rand((cop2.vol, cop2.nd))
+    lhs = np.vdot(g5 * cop2.apply(g5 * u), v)
+    assert abs(lhs - np.vdot(u, cop2.apply(v))) < 1e-12 * abs(lhs)
