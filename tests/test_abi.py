@@ -106,3 +106,29 @@ def test_noalloc_rejects_bad_arguments_without_a_gpu(lib):
     for args, text in cases:
         assert call(*args) == gb.MG_ERR_ARG, args
         assert text in gb.LIB.mg_last_error(None), (args, gb.LIB.mg_last_error(None))
+
+
+def test_tuner_cache_file_and_pins_without_a_gpu(lib, tmp_path):
+    """The launch-policy cache (GBMG_TUNE_CACHE, "key value" lines) is read
+    on first use; mg_tune_set pins or (choice < 0) clears a key.  Run in a
+    fresh process, where the tuner reads its environment."""
+    import sys
+    cache = tmp_path / "tune.txt"
+    cache.write_text("wilson/v4096/n1/c1 4\ncoarse/v256/n48 2\n")
+    code = (
+        "import ctypes as C, sys\n"
+        "sys.path.insert(0, %r)\n"
+        "import paper_1612_07873_gb300 as gb\n"
+        "L = gb.LIB\n"
+        "g = lambda k: L.mg_tune_get(k.encode())\n"
+        "assert g('wilson/v4096/n1/c1') == 4 and g('coarse/v256/n48') == 2\n"
+        "assert g('absent') == -1\n"
+        "assert L.mg_tune_set(b'wilson/v4096/n1/c1', 7) == 0 and g('wilson/v4096/n1/c1') == 7\n"
+        "assert L.mg_tune_set(b'coarse/v256/n48', -1) == 0 and g('coarse/v256/n48') == -1\n"
+        "assert L.mg_tune_set(None, 1) == gb.MG_ERR_ARG and L.mg_tune_get(None) == -1\n"
+        "print('ok')\n" % ROOT)
+    env = dict(os.environ, GBMG_TUNE_CACHE=str(cache))
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stderr
+    # pins are not written back to the cache file
+    assert cache.read_text() == "wilson/v4096/n1/c1 4\ncoarse/v256/n48 2\n"
