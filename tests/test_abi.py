@@ -132,3 +132,29 @@ def test_tuner_cache_file_and_pins_without_a_gpu(lib, tmp_path):
     assert r.returncode == 0 and r.stdout.strip() == "ok", r.stderr
     # pins are not written back to the cache file
     assert cache.read_text() == "wilson/v4096/n1/c1 4\ncoarse/v256/n48 2\n"
+
+
+@pytest.mark.parametrize("change,text", [
+    (dict(dims=(4, 4, 4, 0)), b"extent < 1"),
+    (dict(dims=(2048, 2048, 512, 1)), b"too large"),
+    (dict(prec_fine=2), b"prec_fine"),
+    (dict(prec_coarse=7), b"prec_coarse"),
+    (dict(gcr_nkrylov=0), b"solver parameters"),
+    (dict(block=[(3, 2, 2, 2)]), b"not divisible by block 3"),
+    (dict(nvec=[0]), b"nvec"),
+    (dict(nvec=[49]), b"nvec"),
+    (dict(link_slots=7), b"link_slots"),
+    (dict(prec_fine=1, prec_coarse=2, nvec=[3]), b"even number of null vectors"),
+    (dict(prec_fine=1, prec_coarse=0), b"FP64 coarse levels need an FP64 fine level"),
+])
+def test_create_checks_parameters_before_device_work(lib, change, text):
+    """Inconsistent parameters are rejected with MG_ERR_ARG and a message
+    before mg_create touches the device (the gauge pointer is never read)."""
+    import paper_1612_07873_gb300 as gb
+    kw = dict(dims=(4, 4, 4, 4), block=[(2, 2, 2, 2)], nvec=[4])
+    kw.update(change)
+    p = gb.default_params(**kw)
+    h = C.c_void_p()
+    assert gb.LIB.mg_create(C.byref(p), C.c_void_p(256), C.byref(h)) == gb.MG_ERR_ARG
+    assert text in gb.LIB.mg_last_error(None), gb.LIB.mg_last_error(None)
+    assert not h.value
