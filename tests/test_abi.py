@@ -158,3 +158,25 @@ def test_create_checks_parameters_before_device_work(lib, change, text):
     assert gb.LIB.mg_create(C.byref(p), C.c_void_p(256), C.byref(h)) == gb.MG_ERR_ARG
     assert text in gb.LIB.mg_last_error(None), gb.LIB.mg_last_error(None)
     assert not h.value
+
+
+def test_import_without_built_library_raises(tmp_path):
+    """No fallback: a copy of the package without its compiled library
+    refuses to import."""
+    import shutil
+    import sys
+    pkg = os.path.join(ROOT, "paper_1612_07873_gb300")
+    dst = tmp_path / "paper_1612_07873_gb300"
+    dst.mkdir()
+    for f in os.listdir(pkg):
+        if f.endswith(".py"):
+            shutil.copy(os.path.join(pkg, f), dst / f)
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "try:\n"
+            "    import paper_1612_07873_gb300\n"
+            "except ImportError as e:\n"
+            "    print('refused:', e)\n"
+            "else:\n"
+            "    print('imported')\n" % str(tmp_path))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=tmp_path)
+    assert r.stdout.startswith("refused:") and "not built" in r.stdout, (r.stdout, r.stderr)
