@@ -96,6 +96,24 @@ def test_clover_hermitian_chiral_and_covariant():
     assert np.abs(Ag - Gs @ A @ np.conj(np.swapaxes(Gs, 1, 2))).max() < 1e-13
 
 
+def test_wilson_operator_gauge_covariance():
+    """Eq. (2) under U_mu(x) -> G(x) U_mu(x) G(x+mu)^dag: M[U^G] (G psi) =
+    G (M[U] psi), with the antiperiodic t boundary and the clover term.  A
+    backward hop through U_mu(x) instead of U_mu(x-mu)^dag, or a forward
+    hop through U^dag, breaks it."""
+    dims = (4, 2, 3, 4)
+    U = syn.gauge_field(dims, 0.5, 13)
+    G = syn.gauge_transform(dims, 14)
+    nb = lat.neighbours(dims)
+    Ug = np.stack([G @ U[m] @ np.conj(np.swapaxes(G[nb[:, 1 + 2 * m]], 1, 2)) for m in range(4)])
+    Gs = np.einsum("ab,xij->xaibj", np.eye(4), G).reshape(-1, 12, 12)
+    psi = _rand((lat.volume(dims), 12))
+    Mpsi = dirac.wilson_clover_op(U, dims, -0.3, 1.0, True).apply(psi)
+    got = dirac.wilson_clover_op(Ug, dims, -0.3, 1.0, True).apply(np.einsum("xab,xb->xa", Gs, psi))
+    want = np.einsum("xab,xb->xa", Gs, Mpsi)
+    assert np.abs(got - want).max() < 1e-13 * np.abs(want).max()
+
+
 # ------------------------------------------------------------ gamma5-hermiticity
 def _hierarchy(dims, block, nv, eps=0.3, mass=-0.2, seed=7, sweeps=4):
     U = syn.gauge_field(dims, eps, seed)
