@@ -88,14 +88,16 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, path: str = ""):
+        import tempfile
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.path = path or os.path.join(tempfile.gettempdir(), f"gbmg_clocks_rank{index}.csv")
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            if os.path.dirname(self.path):
+                os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
@@ -321,7 +323,7 @@ def gpu_main(args):
     torch.cuda.synchronize()
     gb.mg_profile_reset(ctx)
     gb.mg_profile_enable(ctx, True)
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(local, args.clocks_csv.replace("{rank}", str(rank)))
     clocks.start()
     if world > 1:
         dist.barrier()
@@ -676,6 +678,9 @@ def main():
     ap.add_argument("--learned-epochs", type=int, default=10)
     ap.add_argument("--no-forms", dest="forms", action="store_false",
                     help="skip the 16-bit storage forms' s/solve")
+    ap.add_argument("--clocks-csv", default="",
+                    help="where the nvidia-smi clock samples of the timed region go "
+                         "('{rank}' is replaced; default: the temp directory)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_main(args)
