@@ -51,3 +51,28 @@ def test_oracle_sample_counts_fp64_algorithmic_bytes(monkeypatch):
     r = bench.oracle_coarse_apply_sample(n=8, cdims=(2, 2, 2, 4), sites=8, budget_s=0.5)
     assert r["value"] == 8 * (9 * 64 * 16 + 2 * 8 * 16) / 1e9
     assert r["unit"] == "GB/s" and r["cores"] == 1 and "1 repetitions" in r["sample"]
+
+
+def test_clock_sampler_summary(tmp_path):
+    """Median SM clock, maximum clock and the throttle reasons seen, from
+    nvidia-smi's csv,noheader,nounits lines of the query the bench issues."""
+    import bench
+
+    class Done:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    path = tmp_path / "clocks.csv"
+    path.write_text(
+        "0, 2070, 2070, 950.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n"
+        "0, 1965, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active\n"
+        "0, 2010, 2070, 1200.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n"
+        "garbage line\n")
+    s = bench.ClockSampler(0, str(path))
+    s.proc, s.fh = Done(), open(path, "a")
+    out = s.stop()
+    assert out == {"sm_mhz": 2010.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"],
+                   "samples": 3}
