@@ -180,3 +180,29 @@ def test_import_without_built_library_raises(tmp_path):
             "    print('imported')\n" % str(tmp_path))
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=tmp_path)
     assert r.stdout.startswith("refused:") and "not built" in r.stdout, (r.stdout, r.stderr)
+
+
+def test_plain_c_program_links_and_calls_the_abi(lib, tmp_path):
+    """The library is usable from C without Python: a C99 program compiled
+    against include/gbmg.h links libgbmg.so, reads the default parameters
+    and gets MG_ERR_ARG with its message for a bad level count (no device
+    work happens before that check)."""
+    import paper_1612_07873_gb300 as gb
+    libdir = os.path.dirname(gb.LIB_PATH)
+    src = tmp_path / "abi.c"
+    src.write_text(
+        '#include <stdio.h>\n#include "gbmg.h"\n'
+        "int main(void) {\n"
+        "  mg_params p; mg_ctx* ctx = 0; mg_default_params(&p);\n"
+        "  p.dims[0] = p.dims[1] = p.dims[2] = p.dims[3] = 4; p.nlevels = 9;\n"
+        "  mg_status s = mg_create(&p, (const void*)256, &ctx);\n"
+        '  printf("%d %d %s|%s|%s\\n", p.gcr_nkrylov, (int)s, mg_status_string(s),\n'
+        '         mg_last_error(0), ctx ? "ctx" : "null");\n'
+        "  return s == MG_ERR_ARG ? 0 : 1;\n}\n")
+    exe = tmp_path / "abi"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                    "-I", os.path.join(ROOT, "include"), str(src), "-L", libdir, "-lgbmg",
+                    f"-Wl,-rpath,{libdir}", "-o", str(exe)], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == "10 -1 invalid argument|mg_create: nlevels must be 2..4|null"
