@@ -16,6 +16,39 @@ def _rand(shape):
     return RNG.standard_normal(shape) + 1j * RNG.standard_normal(shape)
 
 
+# ------------------------------------------------------------ lattice indexing
+def test_site_index_neighbours_and_aggregates_by_brute_force():
+    """Site order x fastest (s = x + Lx (y + Ly (z + Lz t))), stencil slot
+    1 + 2 mu = x + mu and 2 + 2 mu = x - mu with periodic wrap, aggregate =
+    floor(coordinate / block) in the same order; checked site by site on a
+    lattice with four different extents."""
+    dims, block = (4, 2, 6, 3), (2, 1, 3, 3)
+    c = lat.coords(dims)
+    s = 0
+    for t in range(3):
+        for z in range(6):
+            for y in range(2):
+                for x in range(4):
+                    assert tuple(c[s]) == (x, y, z, t) and lat.index(dims, (x, y, z, t)) == s
+                    s += 1
+    nb = lat.neighbours(dims)
+    agg = lat.aggregate_of(dims, block)
+    cd = lat.coarse_dims(dims, block)
+    assert cd == (2, 2, 2, 1)
+    for s in range(lat.volume(dims)):
+        assert nb[s, 0] == s
+        for mu in range(4):
+            up, dn = list(c[s]), list(c[s])
+            up[mu] = (up[mu] + 1) % dims[mu]
+            dn[mu] = (dn[mu] - 1) % dims[mu]
+            assert nb[s, 1 + 2 * mu] == lat.index(dims, up)
+            assert nb[s, 2 + 2 * mu] == lat.index(dims, dn)
+        a = [c[s][m] // block[m] for m in range(4)]
+        assert agg[s] == a[0] + cd[0] * (a[1] + cd[1] * (a[2] + cd[2] * a[3]))
+    # every aggregate holds prod(block) sites
+    assert np.all(np.bincount(agg) == np.prod(block))
+
+
 # ------------------------------------------------------------ gamma algebra
 def test_gamma_clifford_and_chiral_basis():
     G = dirac.GAMMA
