@@ -49,14 +49,17 @@ I4 = np.eye(4, dtype=np.complex128)
 
 
 def sigma(mu: int, nu: int) -> np.ndarray:
-    """sigma_{mu nu} = (i/2)[gamma_mu, gamma_nu]."""
+    """sigma_{mu nu} = (i/2)[gamma_mu, gamma_nu], the spin matrices of the
+    clover term A_x (Sec. 3.2; the paper names A_x without a formula)."""
     return 0.5j * (GAMMA[mu] @ GAMMA[nu] - GAMMA[nu] @ GAMMA[mu])
 
 
 def chirality_of_dof(nd: int) -> np.ndarray:
     """Chirality (0 upper, 1 lower) of each of the nd dofs of a site: the
     first half of the dofs is chirality 0 on every level (fine: spins 0, 1;
-    coarse: dof = s*Nv + c with s the chirality)."""
+    coarse: dof = s*Nv + c with s the chirality).  The split that the
+    footnote of Sec. 3.4 applies to the null vectors; the coarse dof order
+    is the one of Sec. 6.2."""
     return (np.arange(nd) >= nd // 2).astype(np.int64)
 
 
@@ -67,7 +70,8 @@ def _dag(a):
 
 def clover_leaves(U, dims, sites, mu, nu):
     """Q_{mu nu}(x) at the given sites: the four plaquette leaves touching x,
-    each a closed loop from x with the orientation (+mu, +nu, -mu, -nu)."""
+    each a closed loop from x with the orientation (+mu, +nu, -mu, -nu)
+    (field strength of the clover term, Sec. 3.2 reading)."""
     c = lat.coords(dims)[sites]
     e_mu = np.eye(4, dtype=np.int64)[mu]
     e_nu = np.eye(4, dtype=np.int64)[nu]
@@ -81,7 +85,9 @@ def clover_leaves(U, dims, sites, mu, nu):
 
 
 def clover(U, dims, csw, sites=None) -> np.ndarray:
-    """A_x (12x12, dof = spin*3 + color) at the given sites (all by default)."""
+    """A_x (12x12, dof = spin*3 + color) at the given sites (all by default):
+    the clover term of Eq. (2), Sec. 3.2, in the Sheikholeslami-Wohlert
+    form c_sw (i/4) sum_{mu != nu} sigma_{mu nu} (x) Fhat_{mu nu}."""
     if sites is None:
         sites = np.arange(lat.volume(dims))
     sites = np.asarray(sites)
@@ -149,7 +155,8 @@ class StencilOp:
         self.nbr = lat.neighbours(self.dims)
 
     def apply(self, psi):
-        """psi: [V][nd] (or [k][V][nd] for k vectors)."""
+        """(A psi)(x) = sum_d B[x, d] psi(x + shift(d)): Eq. (2) for the fine
+        operator, Eq. (3) for a coarse one.  psi: [V][nd] (or [k][V][nd])."""
         psi = np.asarray(psi)
         if psi.ndim == 3:
             return np.stack([self.apply(p) for p in psi])
@@ -159,7 +166,8 @@ class StencilOp:
         return out
 
     def dense(self):
-        """The full (V*nd) x (V*nd) matrix (tiny lattices only)."""
+        """The full (V*nd) x (V*nd) matrix of Eq. (2) / Eq. (3), blocks of
+        partners that coincide (extent 1 or 2) summed (tiny lattices only)."""
         n = self.vol * self.nd
         D = np.zeros((n, n), dtype=np.complex128)
         for x in range(self.vol):
@@ -170,12 +178,14 @@ class StencilOp:
 
 
 def wilson_clover_op(U, dims, mass, csw, antiperiodic=True) -> StencilOp:
+    """The Wilson-clover matrix M of Eq. (2) (Sec. 3.2) as a stencil."""
     return StencilOp(dims, wilson_clover_blocks(U, dims, mass, csw, antiperiodic))
 
 
 def apply_at(blocks_at_sites, psi, dims, sites):
-    """(A psi)(x) at the given sites only, with B the blocks at those sites;
-    used to sample outputs of a full-size lattice one by one."""
+    """Eq. (3) (or Eq. (2)) at the given sites only: (A psi)(x) with B the
+    blocks at those sites; used to sample outputs of a full-size lattice one
+    by one."""
     c = lat.coords(dims)[np.asarray(sites)]
     out = np.zeros((len(sites), psi.shape[-1]), dtype=np.complex128)
     for d in range(lat.NDIR):

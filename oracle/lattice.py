@@ -12,11 +12,12 @@ NDIR = 9  # diagonal + 8 hops
 
 
 def volume(dims) -> int:
+    """Number of sites of a 4D lattice (Sec. 3.1)."""
     return int(np.prod(dims))
 
 
 def coords(dims) -> np.ndarray:
-    """[V][4] integer coordinates of every site."""
+    """[V][4] integer coordinates of every site (site order of Sec. 6.1)."""
     lx, ly, lz, lt = dims
     s = np.arange(volume(dims))
     x = s % lx
@@ -27,7 +28,8 @@ def coords(dims) -> np.ndarray:
 
 
 def index(dims, c) -> np.ndarray:
-    """Site index of coordinates c ([..., 4]), wrapped periodically."""
+    """Site index of coordinates c ([..., 4]), wrapped periodically (x
+    fastest, the site order of Sec. 6.1)."""
     c = np.asarray(c)
     lx, ly, lz, lt = dims
     x = c[..., 0] % lx
@@ -38,7 +40,8 @@ def index(dims, c) -> np.ndarray:
 
 
 def shift(d: int) -> np.ndarray:
-    """Coordinate offset of stencil slot d."""
+    """Coordinate offset of stencil slot d: 0 for the site term, +-e_mu for
+    the hops of Eq. (2) / Eq. (3)."""
     off = np.zeros(4, dtype=np.int64)
     if d > 0:
         mu = (d - 1) // 2
@@ -47,12 +50,15 @@ def shift(d: int) -> np.ndarray:
 
 
 def neighbours(dims) -> np.ndarray:
-    """[V][9] site index of the stencil partner in every slot."""
+    """[V][9] site index of the stencil partner in every slot: the site and
+    its eight nearest neighbours, the partners of Eq. (2) and Eq. (3)."""
     c = coords(dims)
     return np.stack([index(dims, c + shift(d)) for d in range(NDIR)], axis=1)
 
 
 def coarse_dims(dims, block):
+    """Extents of the coarse lattice: one site per aggregate of `block`
+    fine sites (the geometric blocking of Sec. 3.4)."""
     for L, b in zip(dims, block):
         if L % b:
             raise ValueError(f"lattice extent {L} not divisible by block {b}")
@@ -60,7 +66,8 @@ def coarse_dims(dims, block):
 
 
 def aggregate_of(dims, block) -> np.ndarray:
-    """[V] coarse site (aggregate) index of every fine site: floor(x / block)."""
+    """[V] coarse site (aggregate) index of every fine site: floor(x / block),
+    the hypercubic aggregates of Sec. 3.4."""
     c = coords(dims)
     cd = coarse_dims(dims, block)
     return index(cd, c // np.asarray(block))

@@ -31,11 +31,15 @@ NFEAT, NHID = 72, 32
 
 
 def param_shapes(nvec: int):
+    """Parameter names and shapes of the three stencil layers (an addition,
+    not in the paper; it proposes the x0 of Sec. 3.4 step 1)."""
     return [("W1", (9, NHID, NFEAT)), ("b1", (NHID,)), ("W2", (9, NHID, NHID)),
             ("b2", (NHID,)), ("W3", (24 * nvec, NHID)), ("b3", (24 * nvec,))]
 
 
 def unflatten(theta, nvec):
+    """Flat parameter vector -> named arrays, in param_shapes order (the
+    learned addition; no paper passage)."""
     out, k = {}, 0
     for name, shp in param_shapes(nvec):
         n = int(np.prod(shp))
@@ -45,18 +49,21 @@ def unflatten(theta, nvec):
 
 
 def flatten(p, nvec):
+    """Named arrays -> flat parameter vector (inverse of unflatten)."""
     return np.concatenate([p[name].ravel() for name, _ in param_shapes(nvec)])
 
 
 def features(U):
-    """[V][72]: (Re, Im) of U_mu(x)[a][b], ordered (mu, a, b, re/im)."""
+    """[V][72]: (Re, Im) of U_mu(x)[a][b], ordered (mu, a, b, re/im): the
+    links of Eq. (2) at x as the network's input channels (addition)."""
     vol = U.shape[1]
     u = np.transpose(U, (1, 0, 2, 3)).reshape(vol, 36)
     return np.stack([u.real, u.imag], axis=-1).reshape(vol, 72)
 
 
 def conv9(inp, W, b, nbr):
-    """out(x) = b + sum_d W[d] in(x + shift(d))."""
+    """out(x) = b + sum_d W[d] in(x + shift(d)): one layer, a stencil over
+    the nine partners of Eq. (2) (the "4D convolution" of the addition)."""
     out = np.broadcast_to(b, (inp.shape[0], W.shape[1])).copy()
     for d in range(9):
         out += inp[nbr[:, d]] @ W[d].T
@@ -64,6 +71,8 @@ def conv9(inp, W, b, nbr):
 
 
 def forward(theta, U, dims, nvec):
+    """The three layers of the proposer on one gauge field (addition),
+    keeping every activation for the backward pass."""
     p = unflatten(theta, nvec)
     nbr = lat.neighbours(dims)
     f = features(U)
@@ -74,7 +83,8 @@ def forward(theta, U, dims, nvec):
 
 
 def vectors(o, nvec):
-    """[Nv][V][12] complex from the output channels."""
+    """[Nv][V][12] complex from the output channels: the proposed starting
+    vectors x0 of Sec. 3.4 step 1."""
     vol = o.shape[0]
     z = o.reshape(vol, nvec, 12, 2)
     return np.transpose(z[..., 0] + 1j * z[..., 1], (1, 0, 2))
@@ -82,7 +92,9 @@ def vectors(o, nvec):
 
 def subspace_loss(V, T, dims, block):
     """Mean over (aggregate, chirality) blocks of 1 - tr(C^H G^{-1} C)/Nv and its
-    gradient dL/dV* (same layout as V)."""
+    gradient dL/dV* (same layout as V).  The blocks are those of the
+    per-aggregate QR of Sec. 3.4 step 3 (addition: the paper trains
+    nothing)."""
     nv, vol, nd = V.shape
     grad = np.zeros_like(V)
     total, nblocks = 0.0, 0
@@ -108,7 +120,8 @@ def subspace_loss(V, T, dims, block):
 
 
 def loss_and_grad(theta, U, dims, nvec, T, block):
-    """Loss and its gradient with respect to the flat parameter vector."""
+    """Loss and its gradient with respect to the flat parameter vector, by
+    the chain rule through the three layers (addition, not in the paper)."""
     fw = forward(theta, U, dims, nvec)
     p, nbr = fw["p"], fw["nbr"]
     V = vectors(fw["o"], nvec)
@@ -132,6 +145,8 @@ def loss_and_grad(theta, U, dims, nvec, T, block):
 
 
 def init_params(nvec: int, seed: int):
+    """Seeded initial parameters: zero biases, weights N(0, 1/fan_in)
+    (addition, not in the paper)."""
     rng = np.random.default_rng(seed)
     p = {}
     for name, shp in param_shapes(nvec):

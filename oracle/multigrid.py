@@ -31,7 +31,8 @@ from .dirac import StencilOp, chirality_of_dof
 
 
 class RankError(ValueError):
-    """An aggregate block of null vectors is rank deficient."""
+    """An aggregate block of null vectors is rank deficient: the QR of
+    Sec. 3.4 step 3 has no positive-definite R."""
 
 
 # ------------------------------------------------------------- step 1, 2
@@ -53,7 +54,8 @@ def null_vectors(op: StencilOp, x0: np.ndarray, sweeps: int) -> np.ndarray:
 # ------------------------------------------------------------- step 3
 def mgs2(B: np.ndarray) -> np.ndarray:
     """Modified Gram-Schmidt, each projection done twice, on the columns of
-    every matrix in the batch B [..., rows, Nv]."""
+    every matrix in the batch B [..., rows, Nv]: the per-aggregate QR of
+    Sec. 3.4 step 3."""
     Q = np.array(B, dtype=np.complex128, copy=True)
     scale = np.linalg.norm(Q, axis=(-2, -1))
     nv = Q.shape[-1]
@@ -72,7 +74,9 @@ def mgs2(B: np.ndarray) -> np.ndarray:
 
 def aggregate_blocks(vecs, dims, block, s):
     """[nagg][rows][Nv] matrices of the chirality-s components of the vectors,
-    rows ordered (site inside the aggregate in lexicographic order, dof)."""
+    rows ordered (site inside the aggregate in lexicographic order, dof): the
+    blocks that Sec. 3.4 step 3 orthonormalises, split by chirality as its
+    footnote asks."""
     nv, vol, nd = vecs.shape
     agg = lat.aggregate_of(dims, block)
     nagg = lat.volume(lat.coarse_dims(dims, block))
@@ -102,7 +106,8 @@ def block_orthonormalise(vecs: np.ndarray, dims, block) -> np.ndarray:
 
 # ------------------------------------------------------------- P and R
 def local_prolongator(Q: np.ndarray) -> np.ndarray:
-    """P(x): [V][nd][2Nv]; column (s, i) is Q[i](x) on chirality-s dofs, 0 else."""
+    """P(x): [V][nd][2Nv]; column (s, i) is Q[i](x) on chirality-s dofs, 0 else
+    (the prolongator of Sec. 3.4 step 3, chirally split)."""
     nv, vol, nd = Q.shape
     chi = chirality_of_dof(nd)
     P = np.zeros((vol, nd, 2 * nv), dtype=np.complex128)
@@ -113,13 +118,15 @@ def local_prolongator(Q: np.ndarray) -> np.ndarray:
 
 
 def prolong(Q, ec, dims, block):
-    """e = P e_c:  e(x) = P(x) e_c(agg(x))."""
+    """e = P e_c:  e(x) = P(x) e_c(agg(x))  (prolongation, Sec. 3.4 and
+    Sec. 6.6)."""
     agg = lat.aggregate_of(dims, block)
     return np.einsum("xaj,xj->xa", local_prolongator(Q), np.asarray(ec)[agg])
 
 
 def restrict(Q, r, dims, block):
-    """r_c = R r with R = P^dag:  r_c(xc) = sum_{x in A(xc)} P(x)^dag r(x)."""
+    """r_c = R r with R = P^dag:  r_c(xc) = sum_{x in A(xc)} P(x)^dag r(x)
+    (restriction, Sec. 3.4 and Sec. 6.6)."""
     nv, vol, nd = Q.shape
     agg = lat.aggregate_of(dims, block)
     nagg = lat.volume(lat.coarse_dims(dims, block))
@@ -130,7 +137,8 @@ def restrict(Q, r, dims, block):
 
 
 def dense_prolongator(Q, dims, block) -> np.ndarray:
-    """The explicit (V*nd) x (Vc*2Nv) matrix P (tiny lattices only)."""
+    """The explicit (V*nd) x (Vc*2Nv) matrix P of Sec. 3.4 (tiny lattices
+    only)."""
     nv, vol, nd = Q.shape
     agg = lat.aggregate_of(dims, block)
     nagg = lat.volume(lat.coarse_dims(dims, block))
@@ -144,7 +152,8 @@ def dense_prolongator(Q, dims, block) -> np.ndarray:
 
 # ------------------------------------------------------------- step 4
 def crosses_face(dims, block, d) -> np.ndarray:
-    """[V] bool: does the hop in stencil slot d leave the aggregate?"""
+    """[V] bool: does the hop in stencil slot d leave the aggregate?  Such
+    hops make the links Y_{+-mu} of Eq. (3); the others fall into X."""
     if d == 0:
         return np.zeros(lat.volume(dims), dtype=bool)
     c = lat.coords(dims)
@@ -177,5 +186,7 @@ def galerkin(op: StencilOp, Q: np.ndarray, block) -> StencilOp:
 
 
 def gamma5_hat(n: int) -> np.ndarray:
-    """Coarse gamma_5: +1 on chirality-0 dofs, -1 on chirality-1 dofs."""
+    """Coarse gamma_5: +1 on chirality-0 dofs, -1 on chirality-1 dofs.  The
+    chiral split of Sec. 3.4 keeps the coarse operator gamma_5-hermitian with
+    it, which gives the backward links of Eq. (3) from the forward ones."""
     return np.where(chirality_of_dof(n) == 0, 1.0, -1.0)

@@ -36,22 +36,27 @@ from .dirac import StencilOp
 
 
 def parity(dims) -> np.ndarray:
+    """Site parity (x + y + z + t) mod 2: the red-black colouring of Sec. 3.3."""
     return (lat.coords(dims).sum(axis=1) % 2).astype(np.int64)
 
 
 def half_sites(dims, p: int) -> np.ndarray:
-    """Sites of parity p in compact order (entry h is the site with x >> 1 == h)."""
+    """Sites of parity p in compact order (entry h is the site with x >> 1 == h),
+    the checkerboard of Sec. 3.3."""
     sites = np.nonzero(parity(dims) == p)[0]
     assert np.array_equal(sites >> 1, np.arange(len(sites)))
     return sites
 
 
 def supported(dims) -> bool:
+    """Every extent even: only then is the periodic lattice two-coloured, so
+    that the hops of Eq. (2) / Eq. (3) couple opposite parities (Sec. 3.3)."""
     return all(int(L) % 2 == 0 for L in dims)
 
 
 class SchurOp:
-    """The Schur complement of a StencilOp on the odd sites."""
+    """The Schur complement of a StencilOp on the odd sites: the red-black
+    preconditioning of Sec. 3.3, used on all levels in Sec. 7.1."""
 
     def __init__(self, op: StencilOp):
         assert supported(op.dims), "red-black needs every extent even"
@@ -70,26 +75,28 @@ class SchurOp:
         return full
 
     def apply(self, x_o):
-        """S x_o = A_o x_o - H_oe A_e^-1 H_eo x_o."""
+        """S x_o = A_o x_o - H_oe A_e^-1 H_eo x_o (Sec. 3.3)."""
         t_e = self.H.apply(self._embed(x_o, self.o))[self.e]
         u_e = np.einsum("hij,hj->hi", self.Ae_inv, t_e)
         v_o = self.H.apply(self._embed(u_e, self.e))[self.o]
         return np.einsum("hij,hj->hi", self.A[self.o], x_o) - v_o
 
     def source(self, b):
-        """b^ = b_o - H_oe A_e^-1 b_e."""
+        """b^ = b_o - H_oe A_e^-1 b_e, the right-hand side of the odd-site
+        system (Sec. 3.3)."""
         u_e = np.einsum("hij,hj->hi", self.Ae_inv, b[self.e])
         return b[self.o] - self.H.apply(self._embed(u_e, self.e))[self.o]
 
     def reconstruct(self, b, x_o):
-        """Full x from x_o: x_e = A_e^-1 (b_e - H_eo x_o)."""
+        """Full x from x_o: x_e = A_e^-1 (b_e - H_eo x_o) (Sec. 3.3)."""
         t_e = b[self.e] - self.H.apply(self._embed(x_o, self.o))[self.e]
         x = self._embed(x_o, self.o)
         x[self.e] = np.einsum("hij,hj->hi", self.Ae_inv, t_e)
         return x
 
     def dense(self):
-        """S as a dense matrix (tiny lattices only), column by column."""
+        """S of Sec. 3.3 as a dense matrix (tiny lattices only), column by
+        column."""
         n = len(self.o) * self.op.nd
         D = np.zeros((n, n), dtype=np.complex128)
         for k in range(n):

@@ -30,7 +30,8 @@ from .dirac import StencilOp
 
 
 def mr(apply, b, iters: int, omega: float = 1.0):
-    """MR smoother from a zero guess: r = b; per step p = A r,
+    """MR smoother from a zero guess (Sec. 7.1: 4 pre- and 4 post-smoothing
+    MR steps; Sec. 3.3 for the Krylov background): r = b; per step p = A r,
     alpha = omega <p, r>/<p, p>, x += alpha r, r -= alpha p."""
     x = np.zeros_like(b)
     r = b.copy()
@@ -44,6 +45,8 @@ def mr(apply, b, iters: int, omega: float = 1.0):
 
 @dataclass
 class GCRResult:
+    """Solution, step count, residual history and final true residual of
+    one GCR solve (Sec. 7.1 measures convergence in the L2 norm)."""
     x: np.ndarray
     iters: int
     history: list = field(default_factory=list)   # |r_k| / |b| per step
@@ -51,7 +54,8 @@ class GCRResult:
 
 
 def fgcr(apply, b, precond, tol: float, maxiter: int, nkrylov: int) -> GCRResult:
-    """Flexible GCR(nkrylov) with right preconditioner `precond` (or None).
+    """Flexible GCR(nkrylov) with right preconditioner `precond` (or None):
+    the outer and intermediate solvers of Sec. 7.1 (Krylov space of 10).
 
     Step k: z = K r, w = A z; for j < k: beta = <w_j, w>, w -= beta w_j,
     z -= beta z_j; scale z, w by 1/|w|; alpha = <w, r>; x += alpha z;
@@ -98,6 +102,8 @@ def fgcr(apply, b, precond, tol: float, maxiter: int, nkrylov: int) -> GCRResult
 
 @dataclass
 class MGParams:
+    """Solver parameters of Sec. 7.1 and the readings where it is silent
+    (omega, the inner and coarsest tolerances and iteration limits)."""
     nkrylov: int = 10
     mr_iters: int = 4
     mr_omega: float = 1.0
@@ -109,7 +115,8 @@ class MGParams:
 
 
 class MultigridHierarchy:
-    """ops[l] is the level-l operator (ops[0] the fine Wilson-clover matrix),
+    """The multigrid hierarchy of Sec. 3.4 with the K-cycle of Sec. 7.1.
+    ops[l] is the level-l operator (ops[0] the fine Wilson-clover matrix),
     Qs[l] / blocks[l] the block-orthonormal null vectors and aggregate
     extents of the transfer from level l to l + 1."""
 
@@ -124,7 +131,8 @@ class MultigridHierarchy:
 
     @classmethod
     def build(cls, fine: StencilOp, x0s, sweeps, blocks, params=None):
-        """Full setup: for each level, null vectors from x0s[l], block QR,
+        """Full setup (Sec. 3.4 steps 1-4, then recursively on the coarse
+        operator): for each level, null vectors from x0s[l], block QR,
         Galerkin coarse operator."""
         ops, Qs = [fine], []
         for l, (x0, blk) in enumerate(zip(x0s, blocks)):
@@ -135,9 +143,10 @@ class MultigridHierarchy:
         return cls(ops, Qs, blocks, params)
 
     def kcycle(self, level: int, r):
-        """One K-cycle at `level`: MR pre-smooth, restrict the residual, solve
-        on level + 1 with GCR (preconditioned by the next K-cycle unless
-        level + 1 is the coarsest), prolong and add, MR post-smooth."""
+        """One K-cycle at `level` (Sec. 7.1): MR pre-smooth, restrict the
+        residual (Sec. 6.6), solve on level + 1 with GCR (preconditioned by
+        the next K-cycle unless level + 1 is the coarsest), prolong and add,
+        MR post-smooth."""
         p = self.p
         A = self.ops[level].apply
         dims, blk, Q = self.ops[level].dims, self.blocks[level], self.Qs[level]
@@ -170,6 +179,8 @@ class MultigridHierarchy:
         return x
 
     def solve(self, b, tol: float = 1e-10, maxiter: int = 200) -> GCRResult:
+        """Outer flexible GCR on the fine operator preconditioned by the
+        K-cycle, to |b - M x| <= tol |b| (Sec. 7.1)."""
         self.inner_iters = [0] * len(self.ops)
         return fgcr(self.ops[0].apply, b, lambda v: self.kcycle(0, v), tol, maxiter,
                     self.p.nkrylov)
