@@ -28,6 +28,7 @@ namespace gbmg {
 
 namespace {
 
+// Eq. (3), one right-hand side: y = X x + sum_{+-mu} Y_{+-mu} x(. +- mu).
 template <typename S, int N, int CG>
 __global__ void __launch_bounds__(CG*(N / Unpack<S>::RPC))
     k_coarse_stream(cpx<typename StoreTraits<S>::real>* __restrict__ y,
@@ -96,6 +97,7 @@ __global__ void __launch_bounds__(CG*(N / Unpack<S>::RPC))
 // NR x RPC complex multiply-adds.  The gathered neighbour values sit in
 // shared memory as xs[k][r] (k = slot*n + col); the same buffer then holds
 // the CG partial sums as red[cg][r][row].
+// Eq. (3) on NR right-hand sides per link read.
 template <typename S, int N, int CG, int NR>
 __global__ void __launch_bounds__(CG*(N / Unpack<S>::RPC))
     k_coarse_stream_mr(cpx<typename StoreTraits<S>::real>* __restrict__ y,
@@ -195,6 +197,7 @@ __global__ void __launch_bounds__(CG*(N / Unpack<S>::RPC))
 // neighbour's own CTA, so most of these reads hit L2: HBM traffic is 5 of
 // the 9 blocks.  16-bit forms: each backward input is pre-scaled by the
 // neighbour's per-site scale.
+// Eq. (3) from five stored blocks, Y_{-mu}(x) = g5hat Y_{+mu}(x - mu)^dag g5hat.
 template <typename S, int N, int CG>
 __global__ void __launch_bounds__(CG*(N / Unpack<S>::RPC))
     k_coarse_stream5(cpx<typename StoreTraits<S>::real>* __restrict__ y,
@@ -293,6 +296,7 @@ __global__ void __launch_bounds__(CG*(N / Unpack<S>::RPC))
 }
 
 // [V][9][n][n] (any store type) -> [V][5][n][n]: slots 0, 1, 3, 5, 7
+// Five-block store of the Eq. (3) links (X and the four Y_{+mu}).
 template <typename S>
 __global__ void k_links_pick5(S* __restrict__ out, const S* __restrict__ in, int vol, int n) {
   const size_t per = size_t(n) * n;
@@ -309,6 +313,7 @@ __global__ void k_links_pick5(S* __restrict__ out, const S* __restrict__ in, int
 
 // Any n, any number of right-hand sides: one CTA per site, threads over
 // (row, rhs); links are read column-wise (coalesced over rows).
+// Eq. (3) for any n and any number of right-hand sides.
 template <typename S>
 __global__ void k_coarse_generic(cpx<typename StoreTraits<S>::real>* __restrict__ y,
                                  const cpx<typename StoreTraits<S>::real>* __restrict__ x,
@@ -339,6 +344,7 @@ __global__ void k_coarse_generic(cpx<typename StoreTraits<S>::real>* __restrict_
 }
 
 // ext [V][9][row][col] complex double -> internal [V][9][col][row] in R
+// Eq. (3) link store: ABI layout [slot][row][col] -> internal [slot][col][row].
 template <typename R>
 __global__ void k_links_import(cpx<R>* __restrict__ out, const cpx<double>* __restrict__ in,
                                int vol, int n) {
@@ -352,6 +358,7 @@ __global__ void k_links_import(cpx<R>* __restrict__ out, const cpx<double>* __re
   }
 }
 
+// Eq. (3) link store: internal layout -> ABI layout.
 template <typename S>
 __global__ void k_links_export(cpx<double>* __restrict__ out, const S* __restrict__ in,
                                const float* __restrict__ scales, int vol, int n) {
@@ -369,6 +376,7 @@ __global__ void k_links_export(cpx<double>* __restrict__ out, const S* __restric
 }
 
 // per-site scale = max |component| over the nine blocks; stored = value/scale
+// Eq. (3) links in 16-bit storage with one scale per site (Sec. 4 half precision).
 template <typename S>
 __global__ void k_links_pack16(S* __restrict__ out, float* __restrict__ scales,
                                const cpx<float>* __restrict__ in, int n) {

@@ -173,6 +173,7 @@ struct MmaBatch {
   int stall;
 };
 
+// Eq. (3) on nrhs right-hand sides: a complex GEMM per coarse site.
 template <bool BF16, int N>
 __global__ void __launch_bounds__(128) k_coarse_mma(const MmaBatch batch, int nrhs,
                                                     int* __restrict__ err) {
@@ -387,6 +388,7 @@ __global__ void __launch_bounds__(128) k_coarse_mma(const MmaBatch batch, int nr
 
 // FP32 internal links [V][9][col k][row m] (unscaled) -> tiled 16-bit MMA
 // operand [V][9][core(m, 2k)] scaled by the per-site scale.
+// Eq. (3) links tiled as the tensor-core B operand.
 template <bool BF16>
 __global__ void k_links_tile_mma(uint32_t* __restrict__ out, const cpx<float>* __restrict__ in,
                                  const float* __restrict__ scales, int vol, int n) {

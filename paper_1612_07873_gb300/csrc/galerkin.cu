@@ -65,6 +65,7 @@ struct CoarseOp {
 // 256 threads form a 16 x 16 grid, thread (ty, tx) owning output rows
 // ty*TILE.. and columns tx*TILE.. (2Nv = 16 TILE, MAXO = TILE^2), so that a
 // shared-memory load of P(x) or T feeds TILE complex MACs.
+// Sec. 3.4 step 4: P^dag M P into the nine blocks of Eq. (3).
 template <typename R, typename Rout, typename Op, int MAXO, int TILE>
 __global__ void __launch_bounds__(256) k_galerkin(Op op, const cpx<R>* __restrict__ Vp, AggGeom m,
                                                   int nf, int nv, cpx<Rout>* __restrict__ out) {

@@ -44,6 +44,7 @@ __device__ __forceinline__ cpx<double> crecip(cpx<double> z) { return (1.0 / nor
 // ------------------------------------------------------------ fine level
 // C12: links in the two-row form, third row rebuilt in registers with the
 // boundary sign of the link (as in the full-lattice kernel).
+// Sec. 3.3: the hops of Eq. (2) between parities, fused epilogue.
 template <typename R, int MODE, bool C12>
 __global__ void __launch_bounds__(128) k_wilson_eo(cpx<R>* __restrict__ out,
                                                    const cpx<R>* __restrict__ in,
@@ -140,6 +141,7 @@ __global__ void __launch_bounds__(128) k_wilson_eo(cpx<R>* __restrict__ out,
 // (4 + m + A_x)^-1 for the even sites: two 6x6 Hermitian chirality blocks,
 // inverted in FP64 by Gauss-Jordan with partial pivoting, stored packed as
 // the clover (6 real diagonal entries, then the 15 entries below it).
+// Sec. 3.3: A_e^-1 of the fine level, per even site.
 template <typename Rout>
 __global__ void k_clover_inverse(Rout* __restrict__ out, const double* __restrict__ clover,
                                  Geom g, double diag, int* __restrict__ status) {
@@ -207,6 +209,7 @@ __global__ void k_clover_inverse(Rout* __restrict__ out, const double* __restric
 }
 
 // full [V][nd] <-> compact halves [V/2][nd] (even, odd)
+// Sec. 3.3: full vector -> compact parity halves.
 template <typename R>
 __global__ void k_eo_split(cpx<R>* __restrict__ he, cpx<R>* __restrict__ ho,
                            const cpx<R>* __restrict__ full, Geom g, int nd, size_t fstride,
@@ -224,6 +227,7 @@ __global__ void k_eo_split(cpx<R>* __restrict__ he, cpx<R>* __restrict__ ho,
   }
 }
 
+// Sec. 3.3: compact parity halves -> full vector.
 template <typename R>
 __global__ void k_eo_merge(cpx<R>* __restrict__ full, const cpx<R>* __restrict__ he,
                            const cpx<R>* __restrict__ ho, Geom g, int nd, size_t fstride,
@@ -242,6 +246,7 @@ __global__ void k_eo_merge(cpx<R>* __restrict__ full, const cpx<R>* __restrict__
 }
 
 // A_e^-1 applied site by site to a compact even vector (fine level)
+// Sec. 3.3: A_e^-1 applied on the even sites.
 template <typename R>
 __global__ void k_clover_inv_apply(cpx<R>* __restrict__ out, const cpx<R>* __restrict__ in,
                                    const R* __restrict__ Ainv, int vh, size_t hstride) {
@@ -316,6 +321,7 @@ __device__ __forceinline__ void stream_cols(const S* __restrict__ cols,
 // h (blockIdx.x) and right-hand side (blockIdx.y).  S: the level's link
 // store (with per-site scales for 16-bit stores); Xinv: A_e^-1 = X_e^-1 as
 // [V/2][col][row] in the vector precision.
+// Sec. 3.3: the hops of Eq. (3) between parities, fused epilogue.
 template <typename S, int N, int CG, int MODE>
 __global__ void __launch_bounds__(CG*(N / Unpack<S>::RPC))
     k_coarse_eo(cpx<typename StoreTraits<S>::real>* __restrict__ out,
@@ -375,6 +381,7 @@ __global__ void __launch_bounds__(CG*(N / Unpack<S>::RPC))
 // X_e^-1 per even site: the dense site block (slot 0, internal [col][row],
 // vector precision) inverted in FP64 by Gauss-Jordan with partial pivoting
 // in shared memory; written as [V/2][col][row].  status bit 2: singular.
+// Sec. 3.3: X_e^-1 of a coarse level, per even site.
 template <typename R>
 __global__ void k_site_inverse(cpx<R>* __restrict__ out, const cpx<R>* __restrict__ links,
                                Geom g, int n, int* __restrict__ status) {
@@ -454,6 +461,7 @@ __global__ void k_site_inverse(cpx<R>* __restrict__ out, const cpx<R>* __restric
 }
 
 // out_h = X_e^-1 in_h on a compact even vector (CTA per site and RHS)
+// Sec. 3.3: X_e^-1 applied on the even sites.
 template <typename R, int N, int CG>
 __global__ void __launch_bounds__(CG*(N / Unpack<cpx<R>>::RPC))
     k_coarse_xinv(cpx<R>* __restrict__ out, const cpx<R>* __restrict__ in,

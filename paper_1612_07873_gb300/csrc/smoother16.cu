@@ -16,6 +16,7 @@ __device__ __forceinline__ cpx<float> ld16(bf16c v) { return StoreTraits<bf16c>:
 __device__ __forceinline__ bf16c st16(cpx<float> v) { return StoreTraits<bf16c>::pack(v); }
 
 // two-row (LC = 6) or full (LC = 9) FP32 links -> BF16; FP32 clover -> BF16
+// Eq. (2) links in BF16 for the 16-bit fine smoother (Sec. 7.1).
 template <int LC>
 __global__ void k_links_to16(bf16c* __restrict__ out, const cpx<float>* __restrict__ in,
                              size_t n) {
@@ -23,6 +24,7 @@ __global__ void k_links_to16(bf16c* __restrict__ out, const cpx<float>* __restri
        i += size_t(gridDim.x) * blockDim.x)
     out[i] = st16(in[i]);
 }
+// Eq. (2) clover in BF16 for the 16-bit fine smoother (Sec. 7.1).
 __global__ void k_clover_to16(__nv_bfloat16* __restrict__ out, const float* __restrict__ in,
                               size_t n) {
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
@@ -35,6 +37,7 @@ __global__ void k_clover_to16(__nv_bfloat16* __restrict__ out, const float* __re
 // boundary sign of the link.  MINB: minimum resident CTAs per SM promised
 // to the compiler (0: none), which sets its register budget and with it how
 // far ahead of the arithmetic it can issue the neighbour loads.
+// Eq. (2) on BF16 vectors: the fine smoother of Sec. 7.1.
 template <int LC, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_wilson16(bf16c* __restrict__ out,
                                                   const bf16c* __restrict__ in,

@@ -58,6 +58,7 @@ AggMap make_map(const Level& f, const Level& c) {
 }
 
 // raw [Nv][V][nd] -> W [agg][chi][Nv][rows]
+// Sec. 3.4 step 3: chirality-split aggregate blocks of the null vectors.
 __global__ void k_mgs_gather(double2* __restrict__ W, const double2* __restrict__ raw, AggMap m,
                              int nd, int nv) {
   const int half = nd / 2;
@@ -106,6 +107,7 @@ __device__ __forceinline__ double2 blk_sum2(double2 v, double2* sh) {
 constexpr int kQrMaxVec = 64;
 constexpr int kQrMaxWarps = 32;
 
+// Sec. 3.4 step 3: QR of every (aggregate, chirality) block.
 template <int RPT>
 __global__ void k_block_qr(double2* __restrict__ W, int rows, int nv, int* status) {
   __shared__ double2 sh[32];
@@ -232,6 +234,7 @@ bool launch_block_qr(double2* W, int rows, int nv, int nblk, int* status, cudaSt
 }
 
 // W -> Vp [V][nd][Nv] (R)
+// Sec. 3.4 step 3: the orthonormal blocks as prolongator rows.
 template <typename R>
 __global__ void k_mgs_scatter(cpx<R>* __restrict__ Vp, const double2* __restrict__ W, AggMap m,
                               int nd, int nv) {
@@ -257,6 +260,7 @@ __global__ void k_mgs_scatter(cpx<R>* __restrict__ Vp, const double2* __restrict
 // coarse_v[xc][chi*Nv + i] = sum_{x in A(xc), a in chi} conj(Vp[x][a][i])
 // fine_v[x][a].  CTA b: aggregate b / nr, right-hand side b % nr (the nr
 // CTAs of one aggregate run side by side and share its Vp rows through L2).
+// Restriction R = P^dag (Secs. 3.4 and 6.6).
 template <typename Rf, typename Rc>
 __global__ void k_restrict(cpx<Rc>* __restrict__ coarse, const cpx<Rf>* __restrict__ fine,
                            const cpx<Rf>* __restrict__ Vp, AggMap m, int nd, int nv, int nr,
@@ -296,6 +300,7 @@ __global__ void k_restrict(cpx<Rc>* __restrict__ coarse, const cpx<Rf>* __restri
 
 // fine_v[x][a] = sum_i Vp[x][a][i] coarse_v[agg(x)][chi(a)*Nv + i].  CTA b
 // works on right-hand side b % nr, element chunk b / nr.
+// Prolongation P (Secs. 3.4 and 6.6).
 template <typename Rf, typename Rc>
 __global__ void k_prolong(cpx<Rf>* __restrict__ fine, const cpx<Rc>* __restrict__ coarse,
                           const cpx<Rf>* __restrict__ Vp, AggMap m, int nd, int nv, int nr,
@@ -368,6 +373,7 @@ struct VUnpack {
 // right-hand sides.  CTA b: aggregate b / nchunk, right-hand-side chunk
 // b % nchunk (chunks of one aggregate run side by side and share its Vp
 // rows through L2).
+// Restriction R = P^dag from the 12-dof fine level (Sec. 6.6).
 template <typename Rf, typename Rc, int NRB, typename VT>
 __global__ void __launch_bounds__(256) k_restrict12(cpx<Rc>* __restrict__ coarse,
                                                    const cpx<Rf>* __restrict__ fine,
@@ -440,6 +446,7 @@ __global__ void __launch_bounds__(256) k_restrict12(cpx<Rc>* __restrict__ coarse
 // reads whole 32-byte sectors; the halves meet by one shuffle.  A pair
 // loads RPI rows (RPI * PW <= 12 words) before any arithmetic, so short
 // rows (16-bit Vp, small Nv) still keep several loads per thread in flight.
+// Prolongation P onto the 12-dof fine level (Sec. 6.6).
 template <typename Rf, typename Rc, typename VT, int PW>
 __global__ void __launch_bounds__(256) k_prolong12(cpx<Rf>* __restrict__ fine,
                                                   const cpx<Rc>* __restrict__ coarse,
@@ -503,6 +510,7 @@ __global__ void __launch_bounds__(256) k_prolong12(cpx<Rf>* __restrict__ fine,
 }
 
 // W [agg][chi][Nv][rows] -> out [Nv][V][nd] (FP64)
+// Sec. 3.4 step 3: orthonormal blocks back to the null-vector layout.
 __global__ void k_blocked_to_vectors(double2* __restrict__ out, const double2* __restrict__ W,
                                   AggMap m, int nd, int nv) {
   const int half = nd / 2;

@@ -13,6 +13,7 @@ namespace {
 // gauge_int[mu][s] = gauge_ext[mu][s] * (t antiperiodic and mu = t and
 // t(s) = Lt - 1 ? -1 : 1): the fermion boundary sign lives on the link
 // that wraps, so hops need no special case.
+// Links of Eq. (2) with the fermion boundary sign folded in.
 template <typename R>
 __global__ void k_gauge_import(cpx<R>* __restrict__ out, const cpx<double>* __restrict__ in,
                                Geom g, int antiperiodic) {
@@ -32,6 +33,7 @@ __global__ void k_gauge_import(cpx<R>* __restrict__ out, const cpx<double>* __re
 // and the largest deviation, over all links, of the rebuilt third row
 // sgn * conj(row0 x row1) from the stored one (FP64, as float bits into
 // *maxdev; non-negative floats order like their bit patterns).
+// Two-row link form (gauge compression, Sec. 4).
 __global__ void k_gauge_compress12(cpx<float>* __restrict__ out, unsigned* __restrict__ maxdev,
                                    const cpx<double>* __restrict__ in, Geom g, int antiperiodic) {
   const size_t n = size_t(4) * g.vol;
@@ -137,6 +139,7 @@ __device__ M3 field_strength(const cpx<double>* __restrict__ U, const Geom& g, i
 //   (01): s3, s3   (02): s2, s2   (03): -s1, s1
 //   (12): s1, s1   (13): s2, -s2  (23): -s3, s3
 // so per chirality A = c_sw (i/2) [s1 (x) G1 + s2 (x) G2 + s3 (x) G3].
+// Clover term A_x of Eq. (2) (Sec. 3.2).
 __global__ void k_clover(const cpx<double>* __restrict__ U, Geom g, double csw,
                          double* __restrict__ out64, float* __restrict__ out32) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -193,6 +196,7 @@ __global__ void k_clover(const cpx<double>* __restrict__ U, Geom g, double csw,
 // vector-fastest, so the nvec CTAs of one site chunk run close together and
 // the chunk's links and clover come from DRAM once and from L2 for the
 // other vectors.
+// Eq. (2): the Wilson-clover matrix on one or several vectors.
 template <typename R, bool C12, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_wilson(cpx<R>* __restrict__ out, const cpx<R>* __restrict__ in,
                                                 const cpx<R>* __restrict__ U, const R* __restrict__ A,
@@ -271,6 +275,7 @@ __global__ void __launch_bounds__(128, MINB) k_wilson(cpx<R>* __restrict__ out, 
 // site to NB vectors, so the site's links and clover are read once for NB
 // vectors instead of once per vector.  Vectors are stored back to back
 // (vector v at offset v * vstride); blockIdx.y picks a group of NB vectors.
+// Eq. (2) on NB vectors per thread (setup sweeps, Sec. 3.4 step 1).
 template <typename R, int NB>
 __global__ void __launch_bounds__(128) k_wilson_mv(cpx<R>* __restrict__ out,
                                                    const cpx<R>* __restrict__ in,
@@ -352,6 +357,7 @@ __global__ void __launch_bounds__(128) k_wilson_mv(cpx<R>* __restrict__ out,
 // then applies the operator to vectors w, w + 4, ...: per vector the same
 // work and registers as the one-vector kernel, while links and clover come
 // from HBM once for all nvec vectors.
+// Eq. (2) with a tile of links and clover in shared memory.
 template <bool C12>
 __global__ void __launch_bounds__(128) k_wilson_tile(cpx<float>* __restrict__ out,
                                                      const cpx<float>* __restrict__ in,
