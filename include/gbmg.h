@@ -298,20 +298,24 @@ int mg_tune_get(const char* key);
  * vecs_dev [nvec][V][ndof] complex double (V = dims[0]*..*dims[3], ndof even,
  * first half of the dofs = chirality 0) is orthonormalised per aggregate
  * (extents `block`) and chirality into out_dev (same layout, must not
- * overlap vecs_dev).  No context is needed; dims and block are host arrays.
+ * overlap vecs_dev).  `bytes` is the size of each of the two arrays and must
+ * equal nvec * V * ndof * 16 (MG_ERR_ARG otherwise).  No context is needed;
+ * dims and block are host arrays.
  * Workspace: a file-scope device array of 2^21 complex doubles (32 MiB) that
  * every GPU loading the library holds until exit; calls with
  * nvec * V * ndof > 2^21, nvec > 64 or an aggregate of more than 24576
  * rows per chirality fail with MG_ERR_ARG before any device work.  The
  * first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the workspace and it keeps
- * the last call's contents: calls that overlap on the GPU (other streams,
- * other host threads) race.  The
- * call synchronises `stream` to read the rank test; MG_ERR_RANK as for
- * mg_set_nullvecs.  Error text: mg_last_error(NULL).                       */
-mg_status mg_block_orthonormalise_noalloc(const void* vecs_dev, void* out_dev, const int dims[4],
-                                          const int block[4], int ndof, int nvec, void* stream);
+ * (cudaGetSymbolAddress) with that device current and keeps it for the
+ * life of the process; make that first call before any stream capture.  A
+ * device reset (cudaDeviceReset) invalidates the kept address: calls after
+ * one are not supported.  All calls share the workspace and it keeps the
+ * last call's contents: calls that overlap on the GPU (other streams, other
+ * host threads) race.  The call synchronises `stream` to read the rank
+ * test; MG_ERR_RANK as for mg_set_nullvecs.  Error text: mg_last_error(NULL). */
+mg_status mg_block_orthonormalise_noalloc(const void* vecs_dev, void* out_dev, size_t bytes,
+                                          const int dims[4], const int block[4], int ndof,
+                                          int nvec, void* stream);
 
 /* Number of minimal-residual sweeps the next mg_setup_nullvecs runs (the
  * learned setup starts from proposed vectors and needs fewer).             */

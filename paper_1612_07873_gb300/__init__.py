@@ -108,8 +108,8 @@ def _load():
         "mg_profile_reset": (i, [vp]),
         "mg_profile_query": (i, [vp, C.c_char_p, i, C.POINTER(C.c_int), C.POINTER(d),
                                  C.POINTER(d), C.POINTER(d)]),
-        "mg_block_orthonormalise_noalloc": (i, [vp, vp, C.POINTER(C.c_int), C.POINTER(C.c_int),
-                                                i, i, vp]),
+        "mg_block_orthonormalise_noalloc": (i, [vp, vp, sz, C.POINTER(C.c_int),
+                                                C.POINTER(C.c_int), i, i, vp]),
         "mg_device_status": (i, [vp, vp]),
         "mg_set_setup_sweeps": (i, [vp, i]),
         "mg_coarse_apply_multi": (i, [C.POINTER(vp), C.POINTER(C.c_int), C.POINTER(vp),
@@ -325,12 +325,18 @@ def mg_profile_query(ctx, name, level=-1):
 def mg_block_orthonormalise_noalloc(vecs, out, dims, block, stream=None):
     """Context-free block orthonormalisation that allocates no device memory
     (for callers that cannot let the library allocate); vecs, out:
-    [nvec][V][ndof] complex128 CUDA tensors."""
+    [nvec][V][ndof] complex128 CUDA tensors of the same shape on the current
+    device."""
     assert vecs.dtype == torch.complex128 and out.dtype == torch.complex128
+    assert vecs.dim() == 3 and out.shape == vecs.shape, "out must have the shape of vecs"
+    dev = torch.cuda.current_device()
+    assert vecs.device == out.device and vecs.device.index == dev, \
+        "vecs and out must be on the current CUDA device"
     nvec, vol, ndof = vecs.shape
     d = (C.c_int * 4)(*dims)
     b = (C.c_int * 4)(*block)
-    st = LIB.mg_block_orthonormalise_noalloc(_ptr(vecs), _ptr(out), d, b, ndof, nvec,
+    st = LIB.mg_block_orthonormalise_noalloc(_ptr(vecs), _ptr(out),
+                                             out.numel() * out.element_size(), d, b, ndof, nvec,
                                              _stream(stream))
     _ok(st, None)
     return out

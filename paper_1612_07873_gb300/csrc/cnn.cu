@@ -14,10 +14,11 @@
 //   l = 1 - tr(C^H G^{-1} C) / Nv,  G = B^H B + kappa |B|_F^2 I,  C = B^H T,
 // kappa = 1e-5 / Nv, averaged over blocks;
 //   dl/dB* = -(T A^H - B A A^H - kappa |A|_F^2 B) / Nv,  A = G^{-1} C.
-// Parameters are FP32 (flat: W1, b1, W2, b2, W3, b3); Gram and cross
-// products accumulate in FP32 per thread, the small factorisations run in
-// FP64.  Weight gradients are per-weight sums over sites in a fixed order
-// (deterministic).
+// Parameters and activations are FP32 (flat: W1, b1, W2, b2, W3, b3); the
+// loss and its gradient with respect to the network output are formed in
+// FP64 (Gram and cross products, factorisation, gradient rows).  Weight
+// gradients are per-weight sums over sites in a fixed order
+// (deterministic): FP32 over 32 sites, FP64 beyond.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -145,45 +146,52 @@ __device__ __forceinline__ int agg_site(const AggInfo& m, int xc, int ls) {
          m.fine.stride[2] * (cc[2] * m.b[2] + l2) + m.fine.stride[3] * (cc[3] * m.b[3] + l3);
 }
 
-constexpr int KCH = 64;  // rows per shared-memory chunk
+constexpr int KCH = 32;  // rows per shared-memory chunk
 constexpr int NVMAX = 32;
 
-// One CTA per (aggregate, chirality) block; see the file comment.
+// One CTA per (aggregate, chirality) block; see the file comment.  Every
+// quantity of the loss and of dl/dB is formed in FP64: B (the FP32 network
+// output, exact in FP64), T (FP64), the Gram matrix G, the cross products C,
+// the factorisation and the gradient rows.  Only the gradient rows written
+// for the backward pass are rounded to FP32.
 __global__ void __launch_bounds__(256) k_subspace_loss(
     float* __restrict__ go, float* __restrict__ blk_loss, const float* __restrict__ o,
     const cpx<double>* __restrict__ tgt, AggInfo m, int nvec, float gscale) {
   extern __shared__ unsigned char smem_raw[];
-  cpx<float>* Bs = reinterpret_cast<cpx<float>*>(smem_raw);       // [KCH][nvec]
-  cpx<float>* Ts = Bs + KCH * nvec;                               // [KCH][nvec]
-  cpx<double>* G = reinterpret_cast<cpx<double>*>(Ts + KCH * nvec);  // [nvec][nvec]
-  cpx<double>* C = G + nvec * nvec;
-  cpx<float>* AH = reinterpret_cast<cpx<float>*>(C + nvec * nvec);  // A^H [nvec][nvec]
-  cpx<float>* M2 = AH + nvec * nvec;                                // A A^H
+  cpx<double>* Bs = reinterpret_cast<cpx<double>*>(smem_raw);  // [KCH][nvec]
+  cpx<double>* Ts = Bs + KCH * nvec;                           // [KCH][nvec]
+  cpx<double>* G = Ts + KCH * nvec;                            // [nvec][nvec]
+  cpx<double>* C = G + nvec * nvec;                            // [nvec][nvec]
+  cpx<double>* AH = C + nvec * nvec;                           // A^H
+  cpx<double>* M2 = AH + nvec * nvec;                          // A A^H
   const int blk = blockIdx.x;
   const int xc = blk >> 1, chi = blk & 1;
   const int rows = m.per * 6;
   const int nv2 = nvec * nvec;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nout = 24 * nvec;
-  // ---- G = B^H B, C = B^H T (FP32 per thread)
-  constexpr int EPT = (2 * NVMAX * NVMAX + 255) / 256;
-  cpx<float> acc[EPT];
-#pragma unroll
-  for (int e = 0; e < EPT; ++e) acc[e] = cpx<float>(0.f, 0.f);
-  for (int r0 = 0; r0 < rows; r0 += KCH) {
+  auto load_chunk = [&](int r0) {
     for (int k = tid; k < KCH * nvec; k += 256) {
       const int rr = k / nvec, i = k - rr * nvec, row = r0 + rr;
-      cpx<float> bv(0.f, 0.f), tv(0.f, 0.f);
+      cpx<double> bv(0.0, 0.0), tv(0.0, 0.0);
       if (row < rows) {
         const int ls = row / 6, a = row - ls * 6, dof = chi * 6 + a;
         const int x = agg_site(m, xc, ls);
         const float* src = o + size_t(x) * nout + 24 * i + 2 * dof;
-        bv = cpx<float>(src[0], src[1]);
-        tv = cpx<float>(tgt[(size_t(i) * m.fine.vol + x) * 12 + dof]);
+        bv = cpx<double>(double(src[0]), double(src[1]));
+        tv = tgt[(size_t(i) * m.fine.vol + x) * 12 + dof];
       }
       Bs[k] = bv;
       Ts[k] = tv;
     }
+  };
+  // ---- G = B^H B, C = B^H T
+  constexpr int EPT = (2 * NVMAX * NVMAX + 255) / 256;
+  cpx<double> acc[EPT];
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) acc[e] = cpx<double>(0.0, 0.0);
+  for (int r0 = 0; r0 < rows; r0 += KCH) {
+    load_chunk(r0);
     __syncthreads();
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
@@ -191,8 +199,8 @@ __global__ void __launch_bounds__(256) k_subspace_loss(
       if (q < 2 * nv2) {
         const int which = q / nv2, ij = q - which * nv2;
         const int i = ij / nvec, j = ij - i * nvec;
-        const cpx<float>* R = which ? Ts : Bs;
-        cpx<float> a_ = acc[e];
+        const cpx<double>* R = which ? Ts : Bs;
+        cpx<double> a_ = acc[e];
         for (int rr = 0; rr < KCH; ++rr) cmac_conj(a_, Bs[rr * nvec + i], R[rr * nvec + j]);
         acc[e] = a_;
       }
@@ -204,29 +212,36 @@ __global__ void __launch_bounds__(256) k_subspace_loss(
     const int q = tid + 256 * e;
     if (q < 2 * nv2) {
       const int which = q / nv2, ij = q - which * nv2;
-      (which ? C : G)[ij] = cpx<double>(acc[e]);
+      (which ? C : G)[ij] = acc[e];
     }
   }
   __syncthreads();
-  // ---- thread 0: G += 1e-8 rows I, Cholesky G = L L^H, A = G^{-1} C (FP64)
+  // ---- warp 0: G += kappa tr(G) I, Cholesky G = L L^H (lane i owns row i),
+  // then A = G^{-1} C in place of C (lane c owns column c)
   __shared__ double a2_sh;
-  if (tid == 0) {
-    double trG = 0.0;
-    for (int i = 0; i < nvec; ++i) trG += G[i * nvec + i].re;
-    const double ridge = 1e-5 / nvec * trG;
-    for (int i = 0; i < nvec; ++i) G[i * nvec + i].re += ridge;
+  if (warp == 0) {
+    double trG = lane < nvec ? G[lane * nvec + lane].re : 0.0;
+    for (int off = 16; off > 0; off >>= 1) trG += __shfl_xor_sync(0xffffffffu, trG, off);
+    if (lane < nvec) G[lane * nvec + lane].re += 1e-5 / nvec * trG;
+    __syncwarp();
     for (int j = 0; j < nvec; ++j) {  // lower triangle of G becomes L
-      double dsum = G[j * nvec + j].re;
-      for (int k = 0; k < j; ++k) dsum -= norm2(G[j * nvec + k]);
-      const double ljj = sqrt(fmax(dsum, 1e-300));
-      G[j * nvec + j] = cpx<double>(ljj, 0.0);
-      for (int i = j + 1; i < nvec; ++i) {
-        cpx<double> s = G[i * nvec + j];
-        for (int k = 0; k < j; ++k) s -= G[i * nvec + k] * conj(G[j * nvec + k]);
-        G[i * nvec + j] = (1.0 / ljj) * s;
+      if (lane == j) {
+        double dsum = G[j * nvec + j].re;
+        for (int k = 0; k < j; ++k) dsum -= norm2(G[j * nvec + k]);
+        G[j * nvec + j] = cpx<double>(sqrt(fmax(dsum, 1e-300)), 0.0);
       }
+      __syncwarp();
+      if (lane > j && lane < nvec) {
+        const double ljj = G[j * nvec + j].re;
+        cpx<double> s = G[lane * nvec + j];
+        for (int k = 0; k < j; ++k) s -= G[lane * nvec + k] * conj(G[j * nvec + k]);
+        G[lane * nvec + j] = (1.0 / ljj) * s;
+      }
+      __syncwarp();
     }
-    for (int c = 0; c < nvec; ++c) {  // solve L L^H a = C[:, c] in place in C
+    double a2 = 0.0;
+    if (lane < nvec) {  // solve L L^H a = C[:, c], c = lane
+      const int c = lane;
       for (int i = 0; i < nvec; ++i) {
         cpx<double> s = C[i * nvec + c];
         for (int k = 0; k < i; ++k) s -= G[i * nvec + k] * C[k * nvec + c];
@@ -236,64 +251,52 @@ __global__ void __launch_bounds__(256) k_subspace_loss(
         cpx<double> s = C[i * nvec + c];
         for (int k = i + 1; k < nvec; ++k) s -= conj(G[k * nvec + i]) * C[k * nvec + c];
         C[i * nvec + c] = (1.0 / G[i * nvec + i].re) * s;
+        a2 += norm2(C[i * nvec + c]);
       }
     }
-    double a2 = 0.0;
-    for (int q = 0; q < nv2; ++q) a2 += norm2(C[q]);
-    a2_sh = a2;
+    for (int off = 16; off > 0; off >>= 1) a2 += __shfl_xor_sync(0xffffffffu, a2, off);
+    if (lane == 0) a2_sh = a2;
   }
   __syncthreads();
-  const float ka2 = float(1e-5 / nvec * a2_sh);
-  // C now holds A.  f = Re tr(C0^H A) needs the original C: recompute from the
-  // accumulators of this thread's entries.
+  const double ka2 = 1e-5 / nvec * a2_sh;
+  // C now holds A.  f = Re tr(C0^H A) needs the original C: it is still in
+  // the accumulators of this thread's entries.
   double fpart = 0.0;
 #pragma unroll
   for (int e = 0; e < EPT; ++e) {
     const int q = tid + 256 * e;
     if (q >= nv2 && q < 2 * nv2) {
       const int ij = q - nv2;
-      const cpx<double> c0(acc[e]);
-      fpart += c0.re * C[ij].re + c0.im * C[ij].im;
+      fpart += acc[e].re * C[ij].re + acc[e].im * C[ij].im;
     }
   }
-  // A^H and A A^H (FP32 for the gradient pass)
+  // A^H and A A^H
   for (int q = tid; q < nv2; q += 256) {
     const int i = q / nvec, j = q - i * nvec;
-    AH[q] = cpx<float>(conj(C[j * nvec + i]));
+    AH[q] = conj(C[j * nvec + i]);
     cpx<double> s(0.0, 0.0);
     for (int k = 0; k < nvec; ++k) s += C[i * nvec + k] * conj(C[j * nvec + k]);
-    M2[q] = cpx<float>(s);
+    M2[q] = s;
   }
   // block sum of fpart
   __shared__ double red[8];
   for (int off = 16; off > 0; off >>= 1) fpart += __shfl_xor_sync(0xffffffffu, fpart, off);
-  if ((tid & 31) == 0) red[tid >> 5] = fpart;
+  if (lane == 0) red[warp] = fpart;
   __syncthreads();
   if (tid == 0) {
     double f = 0.0;
     for (int w = 0; w < 8; ++w) f += red[w];
-    blk_loss[blk] = 1.0f - float(f / nvec);
+    blk_loss[blk] = float(1.0 - f / nvec);
   }
-  // ---- gradient rows: Gamma = T A^H - B (A A^H);  dO = -2 gscale (Re, Im) Gamma
+  // ---- gradient rows: Gamma = T A^H - B (A A^H) - kappa |A|_F^2 B;
+  // dO = -2 gscale (Re, Im) Gamma
   for (int r0 = 0; r0 < rows; r0 += KCH) {
-    for (int k = tid; k < KCH * nvec; k += 256) {
-      const int rr = k / nvec, i = k - rr * nvec, row = r0 + rr;
-      cpx<float> bv(0.f, 0.f), tv(0.f, 0.f);
-      if (row < rows) {
-        const int ls = row / 6, a = row - ls * 6, dof = chi * 6 + a;
-        const int x = agg_site(m, xc, ls);
-        const float* src = o + size_t(x) * nout + 24 * i + 2 * dof;
-        bv = cpx<float>(src[0], src[1]);
-        tv = cpx<float>(tgt[(size_t(i) * m.fine.vol + x) * 12 + dof]);
-      }
-      Bs[k] = bv;
-      Ts[k] = tv;
-    }
+    load_chunk(r0);
     __syncthreads();
     for (int k = tid; k < KCH * nvec; k += 256) {
       const int rr = k / nvec, i = k - rr * nvec, row = r0 + rr;
       if (row >= rows) continue;
-      cpx<float> gam = -ka2 * Bs[rr * nvec + i];
+      cpx<double> gam = -ka2 * Bs[rr * nvec + i];
       for (int j = 0; j < nvec; ++j) {
         cmac(gam, Ts[rr * nvec + j], AH[j * nvec + i]);
         cmac(gam, -Bs[rr * nvec + j], M2[j * nvec + i]);
@@ -301,8 +304,8 @@ __global__ void __launch_bounds__(256) k_subspace_loss(
       const int ls = row / 6, a = row - ls * 6, dof = chi * 6 + a;
       const int x = agg_site(m, xc, ls);
       float* dst = go + size_t(x) * nout + 24 * i + 2 * dof;
-      dst[0] = -2.f * gscale * gam.re;
-      dst[1] = -2.f * gscale * gam.im;
+      dst[0] = float(-2.0 * gscale * gam.re);
+      dst[1] = float(-2.0 * gscale * gam.im);
     }
     __syncthreads();
   }
@@ -327,10 +330,11 @@ __global__ void k_dense_back_in(float* __restrict__ g2, const float* __restrict_
 // Segmented weight gradient  P[seg][d][co][k] = sum_{x in seg} gp(x)[co] in(src_d(x))[k]
 // with src_d(x) = x + shift(d) (conv layers, d < 9) or x (dense layer, d = 0
 // with ndir = 1).  Grid (segment, d, 32-row chunk of co); sites staged in
-// shared memory 32 at a time; a second kernel sums the segments in order.
+// shared memory 32 at a time, the 32-site partial sum formed in FP32 and
+// added to an FP64 accumulator; a second kernel sums the segments in order.
 constexpr int WSEG = 1024;  // sites per segment
 template <int CI>
-__global__ void __launch_bounds__(256) k_wgrad_seg(float* __restrict__ part,
+__global__ void __launch_bounds__(256) k_wgrad_seg(double* __restrict__ part,
                                                    const float* __restrict__ gp, int co_total,
                                                    const float* __restrict__ in, Geom g, int ndir) {
   __shared__ float sg[32][33];
@@ -338,9 +342,9 @@ __global__ void __launch_bounds__(256) k_wgrad_seg(float* __restrict__ part,
   const int seg = blockIdx.x, d = blockIdx.y, co0 = blockIdx.z * 32;
   const int tid = threadIdx.x;
   constexpr int OPT = (32 * CI + 255) / 256;
-  float acc[OPT];
+  double acc[OPT];
 #pragma unroll
-  for (int e = 0; e < OPT; ++e) acc[e] = 0.f;
+  for (int e = 0; e < OPT; ++e) acc[e] = 0.0;
   const int x0 = seg * WSEG, x1 = min(g.vol, x0 + WSEG);
   for (int xb = x0; xb < x1; xb += 32) {
     for (int q = tid; q < 32 * 32; q += 256) {
@@ -367,10 +371,10 @@ __global__ void __launch_bounds__(256) k_wgrad_seg(float* __restrict__ part,
       const int o = tid + 256 * e;
       if (o < 32 * CI) {
         const int c = o / CI, k = o - c * CI;
-        float a = acc[e];
+        float a = 0.f;
 #pragma unroll 8
         for (int r = 0; r < 32; ++r) a = fmaf(sg[r][c], si[r][k], a);
-        acc[e] = a;
+        acc[e] += double(a);
       }
     }
     __syncthreads();
@@ -387,29 +391,29 @@ __global__ void __launch_bounds__(256) k_wgrad_seg(float* __restrict__ part,
   }
 }
 
-// W[i] = sum_seg part[i][seg];  bias[co] = sum_x gp(x)[co]
-__global__ void k_wgrad_sum(float* __restrict__ W, const float* __restrict__ part, int n,
+// W[i] = sum_seg part[i][seg] (FP64, rounded once);  bias[co] = sum_x gp(x)[co]
+__global__ void k_wgrad_sum(float* __restrict__ W, const double* __restrict__ part, int n,
                             int nseg) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    float s = 0.f;
+    double s = 0.0;
     for (int q = 0; q < nseg; ++q) s += part[size_t(i) * nseg + q];
-    W[i] = s;
+    W[i] = float(s);
   }
 }
 __global__ void k_bias_grad(float* __restrict__ gb, const float* __restrict__ gp, int vol,
                             int co_total) {
-  // one CTA per output channel, fixed-order tree over sites
-  __shared__ float sh[256];
+  // one CTA per output channel, fixed-order FP64 tree over sites
+  __shared__ double sh[256];
   const int c = blockIdx.x;
-  float s = 0.f;
-  for (int x = threadIdx.x; x < vol; x += 256) s += gp[size_t(x) * co_total + c];
+  double s = 0.0;
+  for (int x = threadIdx.x; x < vol; x += 256) s += double(gp[size_t(x) * co_total + c]);
   sh[threadIdx.x] = s;
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
     if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0) gb[c] = sh[0];
+  if (threadIdx.x == 0) gb[c] = float(sh[0]);
 }
 
 // slot d' whose partner is the site that uses y in slot d: y = x + shift(d)  <=>  x = y - shift(d)
@@ -629,7 +633,7 @@ mg_status mg_cnn_loss_grad(mg_cnn* n, const int dims[4], const int block[4], con
     const int nblk = 2 * m.coarse.vol;
     n->blk_loss.alloc(size_t(nblk) * 4);
     const int nv = n->nvec;
-    const size_t smem = size_t(2) * KCH * nv * 8 + size_t(2) * nv * nv * 16 + size_t(2) * nv * nv * 8;
+    const size_t smem = size_t(2) * KCH * nv * 16 + size_t(4) * nv * nv * 16;
     GB_CHECK(cudaFuncSetAttribute(k_subspace_loss, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   int(smem)));
     k_subspace_loss<<<nblk, 256, smem, st>>>(n->go.as<float>(), n->blk_loss.as<float>(),
@@ -641,8 +645,8 @@ mg_status mg_cnn_loss_grad(mg_cnn* n, const int dims[4], const int block[4], con
     const float* th = n->theta.as<float>();
     const int nseg = (g.vol + WSEG - 1) / WSEG;
     const size_t part_elems = size_t(nseg) * std::max(9 * NH * NF, n->nout * NH);
-    if (n->part.bytes < part_elems * 4) n->part.alloc(part_elems * 4);
-    float* part = n->part.as<float>();
+    if (n->part.bytes < part_elems * 8) n->part.alloc(part_elems * 8);
+    double* part = n->part.as<double>();
     // dense layer
     k_wgrad_seg<NH><<<dim3(nseg, 1, (n->nout + 31) / 32), 256, 0, st>>>(
         part, n->go.as<float>(), n->nout, n->h2.as<float>(), g, 1);

@@ -800,6 +800,10 @@ constexpr size_t kNoAllocMaxElems = size_t(1) << 21;  // complex doubles: 32 MiB
 static __device__ __align__(256) double2 g_noalloc_scratch[kNoAllocMaxElems];
 static __device__ __align__(256) int g_noalloc_status[64];
 
+// The device address of the workspace, looked up once per device and kept
+// for the life of the process.  A reset of the device (cudaDeviceReset, or a
+// framework that tears down and recreates the primary context) makes the
+// kept address stale; calls after such a reset are not supported.
 struct NoAllocSlot {
   bool ready = false;
   double2* scratch = nullptr;
@@ -809,14 +813,14 @@ constexpr int kNoAllocMaxDevices = 64;
 NoAllocSlot g_noalloc_slots[kNoAllocMaxDevices];
 std::mutex g_noalloc_mutex;
 
-
 }  // namespace
 
 }  // namespace gbmg
 
 extern "C" mg_status mg_block_orthonormalise_noalloc(const void* vecs_dev, void* out_dev,
-                                                     const int dims[4], const int block[4],
-                                                     int ndof, int nvec, void* stream) {
+                                                     size_t bytes, const int dims[4],
+                                                     const int block[4], int ndof, int nvec,
+                                                     void* stream) {
   using namespace gbmg;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   auto fail = [](mg_status s, const char* msg) {
@@ -828,17 +832,21 @@ extern "C" mg_status mg_block_orthonormalise_noalloc(const void* vecs_dev, void*
   if (nvec < 1 || ndof < 2 || (ndof & 1)) return fail(MG_ERR_ARG, "noalloc: bad nvec or ndof");
   if (nvec > kQrMaxVec) return fail(MG_ERR_ARG, "noalloc: nvec exceeds 64");
   int cd[4];
-  long long vol = 1;
+  unsigned long long vol = 1;
   for (int m = 0; m < 4; ++m) {
     if (dims[m] < 1 || block[m] < 1 || dims[m] % block[m])
       return fail(MG_ERR_ARG, "noalloc: lattice extent not divisible by block");
     cd[m] = dims[m] / block[m];
-    vol *= dims[m];
+    // the running product stays below 2^21 or the call is refused: no wrap
+    vol *= (unsigned long long)dims[m];
+    if (vol * (unsigned long long)ndof * (unsigned long long)nvec > kNoAllocMaxElems)
+      return fail(MG_ERR_ARG,
+                  "noalloc: nvec * volume * ndof exceeds the 2^21 complex-double workspace "
+                  "(32 MiB)");
   }
   const unsigned long long elems = (unsigned long long)nvec * vol * ndof;
-  if (elems > kNoAllocMaxElems)
-    return fail(MG_ERR_ARG,
-                "noalloc: nvec * volume * ndof exceeds the 2^21 complex-double workspace (32 MiB)");
+  if (bytes != elems * 16ull)
+    return fail(MG_ERR_ARG, "noalloc: bytes differs from nvec * volume * ndof * 16");
   AggMap m;
   m.fine = make_geom(dims);
   m.coarse = make_geom(cd);
@@ -848,6 +856,8 @@ extern "C" mg_status mg_block_orthonormalise_noalloc(const void* vecs_dev, void*
   const int threads = rows <= 256 * 16 ? 256 : 1024;
   const int rpt = (rows + threads - 1) / threads;
   if (rpt > 24) return fail(MG_ERR_ARG, "noalloc: aggregate block too large (rows > 24576)");
+  // an error left pending by earlier, unrelated work is not this call's
+  cudaGetLastError();
   // once per device, with that device current: device address of the workspace
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices)
@@ -875,12 +885,17 @@ extern "C" mg_status mg_block_orthonormalise_noalloc(const void* vecs_dev, void*
     return fail(MG_ERR_CUDA, "noalloc: cudaMemsetAsync failed");
   k_mgs_gather<<<grid_for(elems), 256, 0, st>>>(slot.scratch, (const double2*)vecs_dev, m, ndof,
                                                 nvec);
+  if (cudaGetLastError() != cudaSuccess)
+    return fail(MG_ERR_CUDA, "noalloc: gather launch failed");
   const int nblk = m.coarse.vol * 2;
   if (!launch_block_qr(slot.scratch, rows, nvec, nblk, slot.status, st))
     return fail(MG_ERR_ARG, "noalloc: aggregate block too large for the block QR");
+  if (cudaGetLastError() != cudaSuccess)
+    return fail(MG_ERR_CUDA, "noalloc: block QR launch failed");
   k_blocked_to_vectors<<<grid_for(elems), 256, 0, st>>>((double2*)out_dev, slot.scratch, m, ndof,
                                                      nvec);
-  if (cudaGetLastError() != cudaSuccess) return fail(MG_ERR_CUDA, "noalloc: kernel launch failed");
+  if (cudaGetLastError() != cudaSuccess)
+    return fail(MG_ERR_CUDA, "noalloc: scatter launch failed");
   int h = 0;
   if (cudaMemcpyAsync(&h, slot.status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)

@@ -11,6 +11,8 @@ numbers and shapes them into inputs.
 * ``gaussian_field`` -- complex Gaussian fields (Re, Im iid N(0, 1)), used
   as the random initial null-vector guesses x0 of the adaptive setup
   (Sec. 3.4, step 1) and as right-hand sides.
+* ``free_field_starts`` -- deterministic plane-wave start vectors (the low
+  modes of the free Wilson operator), a control for the learned setup.
 * ``WORKLOADS`` -- lattice sizes and solver parameters of the five
   workloads (small 2-level FP64, production-shaped 3-level FP32, 16-bit
   storage, multi-RHS, learned setup).
@@ -25,7 +27,8 @@ import os
 
 import numpy as np
 
-__all__ = ["gauge_field", "gaussian_field", "gauge_transform", "WORKLOADS", "volume"]
+__all__ = ["gauge_field", "gaussian_field", "gauge_transform", "free_field_starts", "WORKLOADS",
+           "volume"]
 
 
 def volume(dims) -> int:
@@ -129,6 +132,34 @@ def gaussian_field(shape, seed: int, stream: int = 1) -> np.ndarray:
     rng = _rng(seed, 0x9A55 + int(stream))
     g = rng.standard_normal(tuple(shape) + (2,))
     return g[..., 0] + 1j * g[..., 1]
+
+
+def free_field_starts(dims, nvec: int, antiperiodic: bool = True) -> np.ndarray:
+    """nvec plane-wave vectors [nvec][V][12] complex128: vector i carries
+    the unit spin-colour components a = i mod 6 (chirality 0) and a + 6
+    (chirality 1), times exp(i p.x) with p the lowest momentum of the
+    boundary conditions (p_t = pi / Lt when antiperiodic, else 0) plus
+    2 pi / L_mu in direction mu = (i div 6) - 1 for i >= 6 (mu cycling over
+    x, y, z, t).  These are low modes of the free (unit-gauge) operator and
+    have rank nvec on every aggregate whose extents exceed 1; they carry no
+    information about the gauge field."""
+    vol = volume(dims)
+    L = np.array(dims)
+    idx = np.arange(vol)
+    coords = np.stack([idx % L[0], (idx // L[0]) % L[1], (idx // (L[0] * L[1])) % L[2],
+                       idx // (L[0] * L[1] * L[2])], axis=-1).astype(np.float64)
+    p0 = np.array([0.0, 0.0, 0.0, np.pi / L[3] if antiperiodic else 0.0])
+    out = np.zeros((nvec, vol, 12), dtype=np.complex128)
+    for i in range(nvec):
+        a, k = i % 6, i // 6
+        p = p0.copy()
+        if k >= 1:
+            mu = (k - 1) % 4
+            p[mu] += 2.0 * np.pi * (1 + (k - 1) // 4) / L[mu]
+        phase = np.exp(1j * coords @ p)
+        out[i, :, a] = phase
+        out[i, :, a + 6] = phase
+    return out
 
 
 # Workload definitions.  Extents are (Lx, Ly, Lz, Lt); "block" lists the

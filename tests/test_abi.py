@@ -92,9 +92,15 @@ def test_noalloc_rejects_bad_arguments_without_a_gpu(lib):
     f = gb.LIB.mg_block_orthonormalise_noalloc
     a, b = C.c_void_p(256), C.c_void_p(512)
 
-    def call(dims, block, ndof, nvec, x=a, y=b):
-        return f(x, y, (C.c_int * 4)(*dims), (C.c_int * 4)(*block), ndof, nvec, None)
+    def call(dims, block, ndof, nvec, x=a, y=b, nbytes=None):
+        if nbytes is None:
+            vol = 1
+            for v in dims:
+                vol *= v
+            nbytes = nvec * vol * ndof * 16
+        return f(x, y, nbytes, (C.c_int * 4)(*dims), (C.c_int * 4)(*block), ndof, nvec, None)
 
+    big = 1 << 16   # 2^64 sites: the running volume product must not wrap
     cases = [
         (((4, 4, 4, 4), (2, 2, 2, 2), 12, 4, None, b), b"null"),
         (((4, 4, 4, 4), (2, 2, 2, 2), 12, 4, a, a), b"aliases"),
@@ -102,6 +108,9 @@ def test_noalloc_rejects_bad_arguments_without_a_gpu(lib):
         (((4, 4, 4, 4), (2, 2, 2, 2), 12, 65), b"exceeds 64"),
         (((4, 4, 4, 6), (2, 2, 2, 4), 12, 4), b"divisible"),
         (((8, 8, 8, 8), (2, 2, 2, 2), 24, 24), b"2^21"),
+        (((big, big, big, big), (1, 1, 1, 1), 12, 1, a, b, 16), b"2^21"),
+        (((4, 4, 4, 4), (2, 2, 2, 2), 12, 4, a, b, 4 * 256 * 12 * 16 - 16), b"bytes"),
+        (((4, 4, 4, 4), (2, 2, 2, 2), 12, 4, a, b, 0), b"bytes"),
     ]
     for args, text in cases:
         assert call(*args) == gb.MG_ERR_ARG, args

@@ -17,7 +17,7 @@ import torch
 
 import synthetic as syn
 from gpu_helpers import make_ctx, rel_l2, to_dev, to_np
-from oracle import lattice as lat
+from oracle import lattice as lat, multigrid as mgo
 
 pytestmark = pytest.mark.gpu
 
@@ -43,6 +43,24 @@ def test_noalloc_matches_context_path_twice(gpu_lib, dims, block, nv):
         v = syn.gaussian_field((nv, vol, 12), seed)
         want = _context_path(gb, dims, block, v)
         out = torch.full((nv, vol, 12), float("nan"), dtype=torch.complex128, device="cuda")
+        gb.mg_block_orthonormalise_noalloc(to_dev(v), out, dims, block)
+        torch.cuda.synchronize()
+        err = rel_l2(to_np(out), want)
+        assert err < 1e-12, (call, err)
+
+
+@pytest.mark.parametrize("dims,block,ndof,nv", [((4, 4, 2, 2), (2, 2, 2, 2), 48, 8),
+                                                ((2, 2, 2, 4), (1, 2, 2, 2), 64, 12)])
+def test_noalloc_coarse_level_vectors_match_oracle_twice(gpu_lib, dims, block, ndof, nv):
+    """Coarse-level vectors (ndof = 2 Nv of the level above: 48 and 64
+    dofs, chirality = first / second half of the dofs) against the oracle's
+    block orthonormalisation, on two calls in a row."""
+    gb = gpu_lib
+    vol = lat.volume(dims)
+    for call, seed in enumerate((401, 402)):
+        v = syn.gaussian_field((nv, vol, ndof), seed)
+        want = mgo.block_orthonormalise(v, dims, block)
+        out = torch.full((nv, vol, ndof), float("nan"), dtype=torch.complex128, device="cuda")
         gb.mg_block_orthonormalise_noalloc(to_dev(v), out, dims, block)
         torch.cuda.synchronize()
         err = rel_l2(to_np(out), want)
