@@ -350,6 +350,64 @@ mg_status mg_cnn_loss_grad(mg_cnn* net, const int dims[4], const int block[4],
 /* one Adam step (beta 0.9 / 0.999) with the last gradient                 */
 mg_status mg_cnn_adam_step(mg_cnn* net, float lr, void* stream);
 
+/* ---- Domain decomposition of a coarse level with a one-site halo (Sec.
+ * 6.5: a coarse spinor halo one site deep on every face, one pack kernel
+ * for all dimensions, then the exchange).  The level's lattice is cut into
+ * procs[0] x .. x procs[3] equal sub-domains, "ranks" numbered
+ * lexicographically (x fastest); rank r owns the sites whose coordinates
+ * lie in its block.  Every rank lives on the calling GPU (the exchange is
+ * a device-to-device copy into the receiver's own halo buffer), so the
+ * multi-GPU data path can be checked on one GPU.
+ * Faces: f = 2 mu + s for each mu with procs[mu] > 1.  Send face 2mu holds
+ * the rank's sites at local x_mu = 0 and goes to rank r - mu; send face
+ * 2mu+1 the sites at x_mu = l_mu - 1, to rank r + mu; recv face f of a
+ * rank receives send face f of its neighbour (recv 2mu from r + mu: the
+ * +mu partners of the sites at x_mu = l_mu - 1; recv 2mu+1 from r - mu).
+ * Face sites are ordered lexicographically over the other three local
+ * coordinates; face f starts at site face_offset[f] of the rank's send and
+ * recv buffers ([halo_sites][n] complex in the level's vector precision).*/
+typedef struct mg_halo mg_halo;
+
+/* Host-only plan of rank `rank` (no GPU is touched): for every face f the
+ * rank it sends to and receives from (-1 for an inactive face), its first
+ * site and its number of sites.  MG_ERR_ARG if an extent is not a multiple
+ * of its rank count or rank is out of range.                               */
+mg_status mg_halo_plan(const int dims[4], const int procs[4], int rank, int send_to[8],
+                       int recv_from[8], int face_offset[8], int face_sites[8]);
+/* Host-only: the local site index of every face site of direction mu,
+ * side 0 (x_mu = 0) or 1 (x_mu = l_mu - 1), in face order; `sites` holds
+ * vol(local_dims) / local_dims[mu] ints.                                   */
+mg_status mg_halo_face_sites(const int local_dims[4], int mu, int side, int* sites);
+/* Split the built coarse operator of `level` (1 <= level, n in 16, 32, 48,
+ * 64, any link store) into the ranks' link stores and allocate every
+ * rank's send and recv buffers (owned by the handle).  Synchronises.      */
+mg_status mg_halo_create(mg_ctx* ctx, int level, const int procs[4], mg_halo** out,
+                         void* stream);
+mg_status mg_halo_destroy(mg_halo* h);
+/* Number of ranks, local extents, sites and bytes of one rank's halo.     */
+mg_status mg_halo_info(mg_halo* h, int* nranks, int local_dims[4], int* halo_sites,
+                       size_t* halo_bytes);
+/* to_global = 0: rank r's local vector [V_local][n] from a global one
+ * [V][n]; to_global = 1: the reverse (rank r's sites of the global vector
+ * are overwritten).  Vector precision of the level.                        */
+mg_status mg_halo_scatter(mg_halo* h, int rank, void* local_dev, const void* global_dev,
+                          int to_global, void* stream);
+/* One kernel: every send face of rank r from its local vector.            */
+mg_status mg_halo_pack(mg_halo* h, int rank, const void* local_dev, void* stream);
+/* Every rank's send faces into the receivers' recv buffers (one
+ * stream-ordered device-to-device copy per face); call after every rank's
+ * pack and before any rank's apply.                                        */
+mg_status mg_halo_exchange(mg_halo* h, void* stream);
+/* Eq. (3) on the sites of rank r: y_local = (A x)_r, hops that leave the
+ * sub-domain read the recv buffer.  y_local must not overlap x_local.     */
+mg_status mg_halo_apply(mg_halo* h, int rank, void* y_local, const void* x_local,
+                        void* stream);
+/* Device addresses of rank r's send and recv buffers (for an exchange made
+ * by the caller, e.g. between processes).                                 */
+mg_status mg_halo_buffers(mg_halo* h, int rank, void** send_dev, void** recv_dev);
+/* Kernels the handle has launched.                                         */
+long long mg_halo_launch_count(mg_halo* h);
+
 /* Synchronise `stream` and report errors that kernels recorded on the
  * device: MG_ERR_TIMEOUT if a bounded wait inside a kernel (the tensor-core
  * multi-RHS apply's mbarrier waits) gave up since the last call; the record

@@ -124,6 +124,19 @@ def _load():
                                  C.POINTER(d), vp]),
         "mg_cnn_adam_step": (i, [vp, C.c_float, vp]),
         "mg_launch_count": (C.c_longlong, [vp]),
+        "mg_halo_plan": (i, [C.POINTER(C.c_int), C.POINTER(C.c_int), i, C.POINTER(C.c_int),
+                             C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "mg_halo_face_sites": (i, [C.POINTER(C.c_int), i, i, C.POINTER(C.c_int)]),
+        "mg_halo_create": (i, [vp, i, C.POINTER(C.c_int), C.POINTER(vp), vp]),
+        "mg_halo_destroy": (i, [vp]),
+        "mg_halo_info": (i, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                             C.POINTER(sz)]),
+        "mg_halo_scatter": (i, [vp, i, vp, vp, i, vp]),
+        "mg_halo_pack": (i, [vp, i, vp, vp]),
+        "mg_halo_exchange": (i, [vp, vp]),
+        "mg_halo_apply": (i, [vp, i, vp, vp, vp]),
+        "mg_halo_buffers": (i, [vp, i, C.POINTER(vp), C.POINTER(vp)]),
+        "mg_halo_launch_count": (C.c_longlong, [vp]),
         "mg_status_string": (C.c_char_p, [i]),
         "mg_last_error": (C.c_char_p, [vp]),
     }
@@ -425,6 +438,112 @@ def mg_cnn_adam_step(net, lr, stream=None):
 
 def mg_launch_count(ctx) -> int:
     return int(LIB.mg_launch_count(ctx))
+
+
+def mg_halo_plan(dims, procs, rank):
+    """Host-only exchange plan of one rank: dict of per-face lists
+    send_to, recv_from, face_offset, face_sites (8 faces, f = 2 mu + s)."""
+    arrs = [(C.c_int * 8)() for _ in range(4)]
+    _ok(LIB.mg_halo_plan(_dims(dims), _dims(procs), int(rank), *arrs), None)
+    names = ("send_to", "recv_from", "face_offset", "face_sites")
+    return {k: list(a) for k, a in zip(names, arrs)}
+
+
+def mg_halo_face_sites(local_dims, mu, side):
+    """Host-only: local site indices of one face, in face order."""
+    n = 1
+    for m, v in enumerate(local_dims):
+        if m != mu:
+            n *= int(v)
+    out = (C.c_int * n)()
+    _ok(LIB.mg_halo_face_sites(_dims(local_dims), int(mu), int(side), out), None)
+    return list(out)
+
+
+def mg_halo_create(ctx, level, procs, stream=None):
+    h = C.c_void_p()
+    _ok(LIB.mg_halo_create(ctx, level, _dims(procs), C.byref(h), _stream(stream)), None)
+    return h
+
+
+def mg_halo_destroy(h):
+    _ok(LIB.mg_halo_destroy(h), None)
+
+
+def mg_halo_info(h):
+    nr, ld, hs, hb = C.c_int(), (C.c_int * 4)(), C.c_int(), C.c_size_t()
+    _ok(LIB.mg_halo_info(h, C.byref(nr), ld, C.byref(hs), C.byref(hb)), None)
+    return dict(nranks=nr.value, local_dims=tuple(ld), halo_sites=hs.value,
+                halo_bytes=hb.value)
+
+
+def mg_halo_scatter(h, rank, local, glob, to_global=False, stream=None):
+    _ok(LIB.mg_halo_scatter(h, rank, _ptr(local), _ptr(glob), int(bool(to_global)),
+                            _stream(stream)), None)
+
+
+def mg_halo_pack(h, rank, local, stream=None):
+    _ok(LIB.mg_halo_pack(h, rank, _ptr(local), _stream(stream)), None)
+
+
+def mg_halo_exchange(h, stream=None):
+    _ok(LIB.mg_halo_exchange(h, _stream(stream)), None)
+
+
+def mg_halo_apply(h, rank, y, x, stream=None):
+    _ok(LIB.mg_halo_apply(h, rank, _ptr(y), _ptr(x), _stream(stream)), None)
+
+
+def mg_halo_buffers(h, rank):
+    s, r = C.c_void_p(), C.c_void_p()
+    _ok(LIB.mg_halo_buffers(h, rank, C.byref(s), C.byref(r)), None)
+    return s.value, r.value
+
+
+def mg_halo_launch_count(h) -> int:
+    return int(LIB.mg_halo_launch_count(h))
+
+
+class Halo:
+    """Owner of an mg_halo: coarse level `level` of ctx cut into sub-domains."""
+
+    def __init__(self, ctx, level, procs, stream=None):
+        self.h = mg_halo_create(ctx, level, procs, stream)
+        info = mg_halo_info(self.h)
+        self.nranks, self.local_dims = info["nranks"], info["local_dims"]
+        self.halo_sites, self.halo_bytes = info["halo_sites"], info["halo_bytes"]
+
+    def close(self):
+        if self.h is not None:
+            mg_halo_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def scatter(self, rank, local, glob, stream=None):
+        mg_halo_scatter(self.h, rank, local, glob, False, stream)
+
+    def gather(self, rank, glob, local, stream=None):
+        mg_halo_scatter(self.h, rank, local, glob, True, stream)
+
+    def pack(self, rank, local, stream=None):
+        mg_halo_pack(self.h, rank, local, stream)
+
+    def exchange(self, stream=None):
+        mg_halo_exchange(self.h, stream)
+
+    def apply(self, rank, y, x, stream=None):
+        mg_halo_apply(self.h, rank, y, x, stream)
+
+    def buffers(self, rank):
+        return mg_halo_buffers(self.h, rank)
+
+    def launch_count(self):
+        return mg_halo_launch_count(self.h)
 
 
 class Multigrid:
