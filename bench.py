@@ -208,59 +208,121 @@ def aggregate_ranks(ms_total, kernel_ms, kernel_bytes, device):
 
 
 # ---------------------------------------------------------------- learned setup
-def run_learned(args, gb, torch, ev, stream, dev):
-    """Train the null-vector proposer on the plain setup's vectors of
-    `ntrain` 16^4 fields (eps uniform in [0.5, 0.6]) and compare, on a
-    held-out field of the production shape (32^3x64, eps 0.55), the 3-level
-    MG after the plain setup (Gaussian starts, 10 sweeps) with the MG after
-    learned starts and k sweeps.  Mass -0.90: near critical for these fields
-    (at -0.40 the MG iteration count does not depend on the setup)."""
+LEARNED_EVAL_SEEDS = (2000, 2001, 2002)
+
+
+def _stats(vals):
+    return {"per_field": vals, "mean": float(np.mean(vals)), "min": min(vals), "max": max(vals)}
+
+
+def run_learned(args, gb, torch, dev):
+    """The learned setup (an addition; the paper draws x0 at random) against
+    its controls.  Training: the plain setup's block-orthonormal null
+    vectors (Gaussian starts, 10 MR sweeps, m = -0.90) of `ntrain` seeded
+    16^4 fields with eps ~ U[0.3, 0.6] (seeds 1000 + i), `epochs` passes of
+    Adam, one step per field; held-out loss on four more 16^4 fields (eps
+    0.45) after 0, 25, 50, 100, 200 fields of the first pass.  Evaluation:
+    three held-out fields of the production shape (32^3x64, eps 0.55, seeds
+    2000..2002) at m = -0.90 (near critical for these fields), 3-level MG to
+    1e-10 after a setup of k sweeps from
+      trained    -- the network's proposals (k = 0, 2, 5),
+      untrained  -- the same network with its initial parameters (same seed),
+      free_field -- low-momentum plane waves (synthetic.free_field_starts),
+      gaussian   -- the plain setup's Gaussian starts (k = 0, 2, 5, 10).
+    Outer iterations and s/solve are reported per field with mean, min, max."""
     from paper_1612_07873_gb300 import learned
     mass, nv, tdims, tblock = -0.90, 24, (16, 16, 16, 16), (4, 4, 4, 4)
+    ntrain, epochs, lr = args.learned_ntrain, args.learned_epochs, 2e-3
     t0 = time.perf_counter()
-    samples = []
-    for s in range(args.learned_ntrain):
-        eps = 0.5 + 0.1 * np.random.default_rng(1000 + s).random()
-        U = torch.from_numpy(syn.gauge_field(tdims, eps, 1000 + s)).to(dev)
-        samples.append((tdims, U, learned.plain_vectors(U, tdims, tblock, nv, mass, 1.0, 10,
-                                                        5000 + s)))
-    t_targets = time.perf_counter() - t0
-    P = learned.Proposer(nv, seed=3)
+    seeds = [1000 + i for i in range(ntrain)]
+    eps = [0.3 + 0.3 * np.random.default_rng(sd).random() for sd in seeds]
+    fields = syn.gauge_fields(tdims, eps, seeds)
+    hseeds = [1900 + i for i in range(4)]
+    hfields = syn.gauge_fields(tdims, [0.45] * len(hseeds), hseeds)
+    t_gen = time.perf_counter() - t0
     t0 = time.perf_counter()
-    hist = P.train(samples, tblock, epochs=args.learned_epochs, lr=2e-3)
+
+    def target(U, sd):
+        Ud = torch.from_numpy(U).to(dev)
+        return (tdims, Ud, learned.plain_vectors(Ud, tdims, tblock, nv, mass, 1.0, 10, sd + 4000))
+    samples = [target(U, sd) for U, sd in zip(fields, seeds)]
+    held = [target(U, sd) for U, sd in zip(hfields, hseeds)]
+    del fields, hfields
     torch.cuda.synchronize()
-    t_train = time.perf_counter() - t0
-    del samples
+    t_targets = time.perf_counter() - t0
+
+    P = learned.Proposer(nv, seed=3)
+    P0 = learned.Proposer(nv, seed=3)  # the untrained control: the same initial parameters
+
+    def heldout(net):
+        return float(np.mean([net.loss(d, tblock, U, T) for d, U, T in held]))
+    loss_untrained = heldout(P0)
+    curve = [{"fields_seen": 0, "heldout_loss": loss_untrained}]
+    marks = {25, 50, 100, 200, ntrain}
+    hist, t_train, steps = [], 0.0, 0
+    for ep in range(epochs):
+        tot = 0.0
+        for k, (d, U, T) in enumerate(samples):
+            ts = time.perf_counter()
+            tot += P.step(d, tblock, U, T, lr)
+            t_train += time.perf_counter() - ts
+            steps += 1
+            if ep == 0 and (k + 1) in marks:
+                curve.append({"fields_seen": k + 1, "heldout_loss": heldout(P)})
+        hist.append(tot / len(samples))
+    loss_trained = heldout(P)
+    del samples, held
+
     w = syn.WORKLOADS[WORKLOAD]
     dims = w["dims"]
-    Ue = torch.from_numpy(syn.gauge_field(dims, 0.55, 2000)).to(dev)
-    prop = P.propose(dims, Ue)
-    b = torch.from_numpy(syn.gaussian_field((syn.volume(dims), 12), 5, stream=99)).to(dev)
+    vol = syn.volume(dims)
+    b = torch.from_numpy(syn.gaussian_field((vol, 12), 5, stream=99)).to(dev)
     p3 = gb.default_params(dims=dims, block=w["block"], nvec=w["nvec"], mass=mass, csw=1.0,
                            nlevels=3, prec_fine=1, prec_coarse=1, seed=9000)
-    plain = learned.mg_iterations(p3, Ue, None, 10, b)
-    rows = []
-    for k in (0, 2, 5):
-        st = learned.mg_iterations(p3, Ue, prop, k, b)
-        rows.append({"sweeps": k, "outer_iters": st["iters"], "s_per_solve": st["seconds"],
-                     "true_residual": st["true_residual"]})
-    saved = [10 - r["sweeps"] for r in rows if r["outer_iters"] <= plain["iters"]]
-    # red-black smoothing at the same near-critical mass (plain and learned starts)
-    p3rb = gb.default_params(dims=dims, block=w["block"], nvec=w["nvec"], mass=mass, csw=1.0,
-                             nlevels=3, prec_fine=1, prec_coarse=1, seed=9000, red_black=1)
-    rb_plain = learned.mg_iterations(p3rb, Ue, None, 10, b)
-    rb_learned = learned.mg_iterations(p3rb, Ue, prop, 2, b)
+    ff = torch.from_numpy(syn.free_field_starts(dims, nv)).to(dev)
+    plan = {"trained": (0, 2, 5), "untrained": (0, 2, 5), "free_field": (0, 2, 5),
+            "gaussian": (0, 2, 5, 10)}
+    res = {name: {k: {"iters": [], "s": [], "res": []} for k in ks} for name, ks in plan.items()}
+    for fs in LEARNED_EVAL_SEEDS:
+        Ue = torch.from_numpy(syn.gauge_field(dims, 0.55, fs)).to(dev)
+        starts = {"trained": P.propose(dims, Ue), "untrained": P0.propose(dims, Ue),
+                  "free_field": ff, "gaussian": None}
+        for name, ks in plan.items():
+            for k in ks:
+                st = learned.mg_iterations(p3, Ue, starts[name], k, b)
+                r = res[name][k]
+                r["iters"].append(st["iters"] if st["status"] == 0 else -1)
+                r["s"].append(st["seconds"])
+                r["res"].append(st["true_residual"])
+        del starts, Ue
     P.close()
-    return {"mass": mass, "train_fields": args.learned_ntrain, "train_lattice": list(tdims),
-            "epochs": args.learned_epochs, "targets_s": t_targets, "train_s": t_train,
-            "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1],
-            "eval_lattice": list(dims),
-            "plain": {"sweeps": 10, "outer_iters": plain["iters"], "s_per_solve": plain["seconds"]},
-            "learned": rows, "setup_sweeps_saved": max(saved) if saved else 0,
-            "red_black": {"plain_10_sweeps": {"outer_iters": rb_plain["iters"],
-                                              "s_per_solve": rb_plain["seconds"]},
-                          "learned_2_sweeps": {"outer_iters": rb_learned["iters"],
-                                               "s_per_solve": rb_learned["seconds"]}}}
+    P0.close()
+    rows = {name: {str(k): {"outer_iters": _stats(r["iters"]),
+                            "s_per_solve": _stats([round(v, 4) for v in r["s"]]),
+                            "max_true_residual": max(r["res"])}
+                   for k, r in ks.items()} for name, ks in res.items()}
+    plain = np.mean(res["gaussian"][10]["iters"])
+    saved = [10 - k for k in plan["trained"] if np.mean(res["trained"][k]["iters"]) <= plain]
+    return {"mass": mass, "train_fields": ntrain, "train_eps": [0.3, 0.6],
+            "train_lattice": list(tdims), "epochs": epochs, "adam_lr": lr,
+            "targets": "plain setup: Gaussian starts, 10 MR sweeps, block-orthonormalised",
+            "fields_gen_s": t_gen, "targets_s": t_targets, "train_s": t_train,
+            "train_ms_per_step": 1e3 * t_train / max(steps, 1),
+            "loss_per_epoch": hist,
+            "heldout_loss": {"untrained": loss_untrained, "trained": loss_trained},
+            "heldout_loss_vs_fields_seen": curve,
+            "eval_lattice": list(dims), "eval_eps": 0.55, "eval_seeds": list(LEARNED_EVAL_SEEDS),
+            "rows": rows, "setup_sweeps_saved": max(saved) if saved else 0}
+
+
+def learned_main(args):
+    """Only the learned-setup study (see run_learned); one JSON line."""
+    import torch
+
+    import paper_1612_07873_gb300 as gb
+    out = run_learned(args, gb, torch, torch.device("cuda"))
+    print(json.dumps({"mode": "learned", "learned_setup": out}), flush=True)
+    return 0
 
 
 # ---------------------------------------------------------------- GPU leg
@@ -451,7 +513,7 @@ def gpu_main(args):
                     "setup_ms": t0.elapsed_time(t1)}
                 del bm, xm
             mf.close()
-    learned_setup = run_learned(args, gb, torch, ev, stream, dev) if args.learned else None
+    learned_setup = run_learned(args, gb, torch, dev) if args.learned else None
     peak, peak_kind = peaks()
     solve_s = [s["seconds"] for s in stats]
     line = {
@@ -546,7 +608,9 @@ def coarse_apply_main(args):
 def wilson_policies_main(args):
     """Every launch policy of the FP32 fine operator, pinned in turn through
     mg_tune_set, on the 32^3x64 workload lattice for 1, 8 and 24 vectors
-    (mg_wilson_clover_apply_multi); microseconds per vector by CUDA events."""
+    (mg_wilson_clover_apply_multi); microseconds per vector by CUDA events.
+    Policies 10 and 11 read 8-real links; the line carries the 8-real
+    form's reconstruction error on this field."""
     import torch
 
     import paper_1612_07873_gb300 as gb
@@ -557,6 +621,7 @@ def wilson_policies_main(args):
     p = gb.default_params(dims=dims, block=w["block"], nvec=w["nvec"], mass=w["mass"],
                           csw=w["csw"], nlevels=3, prec_fine=1, prec_coarse=1)
     mg = gb.Multigrid(p, U)
+    comp = gb.mg_gauge_compression(mg.ctx)
     rows = []
     for nvec in (1, 8, 24):
         g = torch.Generator(device="cuda").manual_seed(nvec)
@@ -567,9 +632,9 @@ def wilson_policies_main(args):
         gb.mg_wilson_clover_apply_multi(mg.ctx, y, x, nvec)
         torch.cuda.synchronize()
         pick = gb.mg_tune_get(key)
-        for pol in range(10):
-            if (pol >= 6 and nvec == 1) or (pol == 6 and nvec % 2) or (pol == 7 and nvec % 4) \
-                    or (pol >= 8 and nvec < 4):
+        for pol in range(12):
+            if (6 <= pol < 10 and nvec == 1) or (pol == 6 and nvec % 2) or (pol == 7 and nvec % 4) \
+                    or (pol in (8, 9) and nvec < 4) or (pol >= 10 and not comp["eight_real"]):
                 continue
             gb.mg_tune_set(key, pol)
             for _ in range(args.warmup):
@@ -587,7 +652,8 @@ def wilson_policies_main(args):
                          "gbs_algorithmic": q["bytes"] / q["launches"] / (us * 1e-6) / 1e9})
         gb.mg_tune_set(key, -1)
     mg.close()
-    print(json.dumps({"mode": "wilson-policies", "lattice": list(dims), "rows": rows}), flush=True)
+    print(json.dumps({"mode": "wilson-policies", "lattice": list(dims), "compression": comp,
+                      "rows": rows}), flush=True)
     return 0
 
 
@@ -664,7 +730,8 @@ def main():
     ap.add_argument("--impl", default="gbmg", choices=["gbmg", "reference"])
     ap.add_argument("--form", default="fp32", choices=["fp32", "bf16", "fp16", "int16"])
     ap.add_argument("--mode", default="pipeline",
-                    choices=["pipeline", "coarse-apply", "wilson-policies", "solve-breakdown"])
+                    choices=["pipeline", "coarse-apply", "wilson-policies", "solve-breakdown",
+                             "learned"])
     ap.add_argument("--fine", default="", help="override the fine extents, e.g. 16,16,16,32")
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides (coarse-apply mode)")
     ap.add_argument("--slots", type=int, default=9, choices=[5, 9],
@@ -674,8 +741,8 @@ def main():
                          "--profile-from-start off)")
     ap.add_argument("--no-learned", dest="learned", action="store_false",
                     help="skip training / evaluating the learned setup")
-    ap.add_argument("--learned-ntrain", type=int, default=24)
-    ap.add_argument("--learned-epochs", type=int, default=10)
+    ap.add_argument("--learned-ntrain", type=int, default=200)
+    ap.add_argument("--learned-epochs", type=int, default=4)
     ap.add_argument("--no-forms", dest="forms", action="store_false",
                     help="skip the 16-bit storage forms' s/solve")
     ap.add_argument("--clocks-csv", default="",
@@ -690,6 +757,8 @@ def main():
         return wilson_policies_main(args)
     if args.mode == "solve-breakdown":
         return solve_breakdown_main(args)
+    if args.mode == "learned":
+        return learned_main(args)
     return gpu_main(args)
 
 

@@ -250,6 +250,17 @@ mg_status mg_set_coarse_links(mg_ctx* ctx, int level, const void* src_dev, size_
 mg_status mg_level_info(mg_ctx* ctx, int level, int dims[4], int* volume, int* ndof,
                         int* vec_prec);
 
+/* Compressed link forms of the FP32 fine operator (Sec. 4): bit 0 of
+ * *forms = the two-row (12-real) form is eligible, bit 1 = the 8-real form
+ * (a2, a3, b1 and the phases of a1, c1; the other entries rebuilt from
+ * unit rows and columns and det U = 1) is eligible.  *max_dev8 and
+ * *rms_dev8: the largest and the root-mean-square |U_rebuilt - U| over the
+ * entries of every link, FP32 rebuild against the FP64 field.  The 8-real
+ * form is eligible when the largest is below 1e-4; both forms are launch
+ * policies of mg_wilson_clover_apply that the autotuner may pick.  Zeros
+ * for an FP64 fine level.                                                  */
+mg_status mg_gauge_compression(mg_ctx* ctx, int* forms, double* max_dev8, double* rms_dev8);
+
 /* Device-side timing of the library's own kernels.  When enabled, every
  * launch of kernel class `name` ("coarse_apply" for single right-hand
  * sides, "coarse_apply_multi" for nrhs > 1, "wilson_clover", "galerkin",
@@ -324,14 +335,17 @@ mg_status mg_set_setup_sweeps(mg_ctx* ctx, int sweeps);
 /* ---- Learned null-vector proposer.  The paper draws the setup's starting
  * vectors x0 at random (Sec. 3.4 step 1); this addition proposes them with
  * a three-layer network whose layers are nearest-neighbour stencils on the
- * lattice: 72 link features (Re, Im of U_mu(x)) -> 32 -> 32 (tanh) ->
- * 24 * nvec outputs = nvec complex 12-component vectors per site.  FP32
- * parameters, flat order W1[9][32][72], b1[32], W2[9][32][32], b2[32],
- * W3[24 nvec][32], b3[24 nvec].  Training minimises, per aggregate and
- * chirality, 1 - |Q_pred^H Q_target|_F^2 / nvec (the share of the target
- * null space outside the span of the proposed vectors), averaged over
- * blocks, with Adam.  Vectors use the null-vector layout [vec][V][12]
- * complex double; the gauge field the mg_create layout.                    */
+ * lattice: 72 link features (Re, Im of U_mu(x)) and 8 position features
+ * (cos, sin of 2 pi x_mu / L_mu) -> 32 -> 32 (tanh) -> with the 8 position
+ * features again -> 24 * nvec outputs = nvec complex 12-component vectors
+ * per site.  FP32 parameters, flat order W1[9][32][80], b1[32],
+ * W2[9][32][32], b2[32], W3[24 nvec][40], b3[24 nvec].  Training
+ * minimises, per aggregate and chirality, 1 - |Q_pred^H Q_target|_F^2 /
+ * nvec (the share of the target null space outside the span of the
+ * proposed vectors, with a relative ridge), averaged over blocks, with
+ * Adam; the loss and its gradient with respect to the outputs are formed in
+ * FP64.  Vectors use the null-vector layout [vec][V][12] complex double;
+ * the gauge field the mg_create layout.                                    */
 typedef struct mg_cnn mg_cnn;
 mg_status mg_cnn_create(int nvec, uint64_t seed, mg_cnn** out);
 mg_status mg_cnn_destroy(mg_cnn* net);

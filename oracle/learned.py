@@ -3,11 +3,15 @@ addition that proposes the random starting vectors x0 of Sec. 3.4 step 1.
 
 Network (every layer a nearest-neighbour stencil on the lattice, the
 "4D convolution" of this build):
-  features  f(x)  = (Re, Im) of the four links U_mu(x)       72 channels
-  layer 1   h1(x) = tanh(b1 + sum_{d=0..8} W1[d] f(x + shift(d)))   72 -> 32
+  position  p(x)  = cos, sin (2 pi x_mu / L_mu), mu = 0..3      8 channels
+  features  f(x)  = (Re, Im) of the four links U_mu(x), then p(x)    72 + 8
+  layer 1   h1(x) = tanh(b1 + sum_{d=0..8} W1[d] f(x + shift(d)))   80 -> 32
   layer 2   h2(x) = tanh(b2 + sum_{d=0..8} W2[d] h1(x + shift(d)))  32 -> 32
-  layer 3   o(x)  = b3 + W3 h2(x)                                    32 -> 24 Nv
+  layer 3   o(x)  = b3 + W3 [h2(x); p(x)]                            40 -> 24 Nv
   vector i at site x, dof a: o[x][24 i + 2a] + i o[x][24 i + 2a + 1].
+The links carry no position; p gives the network the phases of the lowest
+lattice momenta, so it can produce the slowly varying low modes the setup
+looks for and correct them from the local links.
 
 Loss (proposed reading; raw null vectors are not unique): for every
 aggregate A and chirality s, with B the (|A| nd/2) x Nv block of the
@@ -27,14 +31,15 @@ from . import lattice as lat
 from .dirac import chirality_of_dof
 from .multigrid import aggregate_blocks
 
-NFEAT, NHID = 72, 32
+NLINK, NPOS, NHID = 72, 8, 32
+NFEAT = NLINK + NPOS
 
 
 def param_shapes(nvec: int):
     """Parameter names and shapes of the three stencil layers (an addition,
     not in the paper; it proposes the x0 of Sec. 3.4 step 1)."""
     return [("W1", (9, NHID, NFEAT)), ("b1", (NHID,)), ("W2", (9, NHID, NHID)),
-            ("b2", (NHID,)), ("W3", (24 * nvec, NHID)), ("b3", (24 * nvec,))]
+            ("b2", (NHID,)), ("W3", (24 * nvec, NHID + NPOS)), ("b3", (24 * nvec,))]
 
 
 def unflatten(theta, nvec):
@@ -53,12 +58,20 @@ def flatten(p, nvec):
     return np.concatenate([p[name].ravel() for name, _ in param_shapes(nvec)])
 
 
-def features(U):
-    """[V][72]: (Re, Im) of U_mu(x)[a][b], ordered (mu, a, b, re/im): the
-    links of Eq. (2) at x as the network's input channels (addition)."""
+def positions(dims):
+    """[V][8]: cos and sin of 2 pi x_mu / L_mu for mu = 0..3 (addition)."""
+    c = lat.coords(dims).astype(np.float64)
+    ph = 2.0 * np.pi * c / np.asarray(dims, dtype=np.float64)
+    return np.stack([np.cos(ph), np.sin(ph)], axis=-1).reshape(-1, 8)
+
+
+def features(U, dims):
+    """[V][80]: (Re, Im) of U_mu(x)[a][b], ordered (mu, a, b, re/im) -- the
+    links of Eq. (2) at x -- then the 8 position channels (addition)."""
     vol = U.shape[1]
     u = np.transpose(U, (1, 0, 2, 3)).reshape(vol, 36)
-    return np.stack([u.real, u.imag], axis=-1).reshape(vol, 72)
+    links = np.stack([u.real, u.imag], axis=-1).reshape(vol, 72)
+    return np.concatenate([links, positions(dims)], axis=1)
 
 
 def conv9(inp, W, b, nbr):
@@ -75,11 +88,12 @@ def forward(theta, U, dims, nvec):
     keeping every activation for the backward pass."""
     p = unflatten(theta, nvec)
     nbr = lat.neighbours(dims)
-    f = features(U)
+    f = features(U, dims)
     h1 = np.tanh(conv9(f, p["W1"], p["b1"], nbr))
     h2 = np.tanh(conv9(h1, p["W2"], p["b2"], nbr))
-    o = h2 @ p["W3"].T + p["b3"]
-    return dict(f=f, h1=h1, h2=h2, o=o, nbr=nbr, p=p)
+    hp = np.concatenate([h2, f[:, NLINK:]], axis=1)
+    o = hp @ p["W3"].T + p["b3"]
+    return dict(f=f, h1=h1, h2=h2, hp=hp, o=o, nbr=nbr, p=p)
 
 
 def vectors(o, nvec):
@@ -130,8 +144,8 @@ def loss_and_grad(theta, U, dims, nvec, T, block):
     # real-parameter gradient: dL/dRe z = 2 Re(dL/dz*), dL/dIm z = 2 Im(dL/dz*)
     gz = np.transpose(gV, (1, 0, 2))                     # [V][Nv][12]
     go = np.stack([2 * gz.real, 2 * gz.imag], axis=-1).reshape(vol, 24 * nvec)
-    g = {"W3": go.T @ fw["h2"], "b3": go.sum(0)}
-    gh2 = go @ p["W3"]
+    g = {"W3": go.T @ fw["hp"], "b3": go.sum(0)}
+    gh2 = go @ p["W3"][:, :NHID]
     gp2 = gh2 * (1.0 - fw["h2"] ** 2)
     g["b2"] = gp2.sum(0)
     g["W2"] = np.stack([gp2.T @ fw["h1"][nbr[:, d]] for d in range(9)])

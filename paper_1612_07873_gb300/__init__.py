@@ -104,6 +104,7 @@ def _load():
         "mg_set_coarse_links": (i, [vp, i, vp, sz, vp]),
         "mg_level_info": (i, [vp, i, C.POINTER(C.c_int), C.POINTER(C.c_int),
                               C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "mg_gauge_compression": (i, [vp, C.POINTER(C.c_int), C.POINTER(d), C.POINTER(d)]),
         "mg_profile_enable": (i, [vp, i]),
         "mg_profile_reset": (i, [vp]),
         "mg_profile_query": (i, [vp, C.c_char_p, i, C.POINTER(C.c_int), C.POINTER(d),
@@ -318,6 +319,15 @@ def mg_level_info(ctx, level):
     _ok(LIB.mg_level_info(ctx, level, dims, C.byref(vol), C.byref(nd), C.byref(vp)), ctx)
     return dict(dims=tuple(dims), volume=vol.value, ndof=nd.value,
                 dtype=torch.complex128 if vp.value == F64 else torch.complex64)
+
+
+def mg_gauge_compression(ctx):
+    """Eligible compressed link forms of the FP32 fine operator and the
+    8-real form's reconstruction error (largest, root-mean-square)."""
+    f, mx, rms = C.c_int(), C.c_double(), C.c_double()
+    _ok(LIB.mg_gauge_compression(ctx, C.byref(f), C.byref(mx), C.byref(rms)), ctx)
+    return dict(two_row=bool(f.value & 1), eight_real=bool(f.value & 2), max_dev8=mx.value,
+                rms_dev8=rms.value)
 
 
 def mg_profile_enable(ctx, on=True):

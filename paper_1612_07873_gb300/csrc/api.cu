@@ -557,6 +557,15 @@ mg_status mg_level_info(mg_ctx* c, int level, int dims[4], int* volume, int* ndo
   });
 }
 
+mg_status mg_gauge_compression(mg_ctx* c, int* forms, double* max_dev8, double* rms_dev8) {
+  return guarded(c, [&] {
+    const Level& L = c->L[0];
+    if (forms) *forms = (L.gauge12_ok ? 1 : 0) | (L.gauge8_ok ? 2 : 0);
+    if (max_dev8) *max_dev8 = L.gauge8_maxdev;
+    if (rms_dev8) *rms_dev8 = L.gauge8_rmsdev;
+  });
+}
+
 mg_status mg_profile_enable(mg_ctx* c, int on) {
   return guarded(c, [&] { c->prof.on = on != 0; });
 }

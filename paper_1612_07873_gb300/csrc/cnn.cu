@@ -3,10 +3,15 @@
 // a site to Nv starting vectors for the adaptive setup (Sec. 3.4 step 1
 // draws them at random; the paper has no learned part).
 //
-//   f(x)  = (Re, Im) of U_mu(x)[a][b]                            72 channels
+//   p(x)  = cos, sin (2 pi x_mu / L_mu), mu = 0..3                  8 channels
+//   f(x)  = (Re, Im) of U_mu(x)[a][b], then p(x)                 72 + 8 channels
 //   h1(x) = tanh(b1 + sum_{d=0..8} W1[d] f(x + shift(d)))         -> 32
 //   h2(x) = tanh(b2 + sum_{d=0..8} W2[d] h1(x + shift(d)))        -> 32
-//   o(x)  = b3 + W3 h2(x)                                         -> 24 Nv
+//   o(x)  = b3 + W3 [h2(x); p(x)]                                 -> 24 Nv
+// The links carry no position, and the smooth low modes the setup looks for
+// vary slowly across the lattice; the phases p(x) of the lowest lattice
+// momenta give the network that position (as inputs of the first layer and
+// directly to the output layer).
 //   vector i, dof a at x: o[x][24 i + 2 a] + i o[x][24 i + 2 a + 1]
 //
 // Training loss, per aggregate A and chirality s with B the block of the
@@ -40,7 +45,9 @@ namespace gbmg {
 
 namespace {
 
-constexpr int NF = 72, NH = 32;
+constexpr int NL = 72, NP = 8;       // link and position channels
+constexpr int NF = NL + NP, NH = 32;  // first-layer inputs, hidden channels
+constexpr int ND = NH + NP;           // output-layer inputs [h2; p]
 
 struct Offsets {
   int W1, b1, W2, b2, W3, b3, total;
@@ -52,7 +59,7 @@ Offsets offsets(int nout) {
   o.W2 = o.b1 + NH;
   o.b2 = o.W2 + 9 * NH * NH;
   o.W3 = o.b2 + NH;
-  o.b3 = o.W3 + nout * NH;
+  o.b3 = o.W3 + nout * ND;
   o.total = o.b3 + nout;
   return o;
 }
@@ -63,20 +70,37 @@ int blocks_for(size_t n) {
   return int(b < 1 ? 1 : b);
 }
 
-__global__ void k_features(float* __restrict__ f, const cpx<double>* __restrict__ U, int vol) {
-  const size_t total = size_t(vol) * 36;
+// f [V][NF] (links, then positions) and the position channels of the
+// output-layer input hp [V][ND]
+__global__ void k_features(float* __restrict__ f, float* __restrict__ hp,
+                           const cpx<double>* __restrict__ U, Geom g) {
+  const int vol = g.vol;
+  const size_t total = size_t(vol) * 40;
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < total;
        i += size_t(gridDim.x) * blockDim.x) {
-    const int x = int(i / 36), k = int(i - size_t(x) * 36);
-    const int mu = k / 9, ab = k - mu * 9;
-    const cpx<double> u = U[(size_t(mu) * vol + x) * 9 + ab];
-    f[size_t(x) * NF + 2 * k] = float(u.re);
-    f[size_t(x) * NF + 2 * k + 1] = float(u.im);
+    const int x = int(i / 40), k = int(i - size_t(x) * 40);
+    if (k < 36) {
+      const int mu = k / 9, ab = k - mu * 9;
+      const cpx<double> u = U[(size_t(mu) * vol + x) * 9 + ab];
+      f[size_t(x) * NF + 2 * k] = float(u.re);
+      f[size_t(x) * NF + 2 * k + 1] = float(u.im);
+    } else {
+      const int mu = k - 36;
+      int c[4];
+      site_coords(g, x, c);
+      float sn, cs;
+      sincospif(2.f * float(c[mu]) / float(g.L[mu]), &sn, &cs);
+      f[size_t(x) * NF + NL + 2 * mu] = cs;
+      f[size_t(x) * NF + NL + 2 * mu + 1] = sn;
+      hp[size_t(x) * ND + NH + 2 * mu] = cs;
+      hp[size_t(x) * ND + NH + 2 * mu + 1] = sn;
+    }
   }
 }
 
-// out(x)[c] = tanh(b[c] + sum_d sum_k W[d][c][k] in(x + shift(d))[k]); thread (x, c)
-template <int CIN>
+// out(x)[c] = tanh(b[c] + sum_d sum_k W[d][c][k] in(x + shift(d))[k]); thread (x, c);
+// output rows OS floats apart
+template <int CIN, int OS>
 __global__ void k_conv9_tanh(float* __restrict__ out, const float* __restrict__ in,
                              const float* __restrict__ W, const float* __restrict__ b, Geom g) {
   const size_t total = size_t(g.vol) * NH;
@@ -92,11 +116,11 @@ __global__ void k_conv9_tanh(float* __restrict__ out, const float* __restrict__ 
 #pragma unroll 8
       for (int k = 0; k < CIN; ++k) acc = fmaf(__ldg(w + k), src[k], acc);
     }
-    out[i] = tanhf(acc);
+    out[size_t(x) * OS + c] = tanhf(acc);
   }
 }
 
-// o(x)[j] = b3[j] + sum_c W3[j][c] h2(x)[c]
+// o(x)[j] = b3[j] + sum_c W3[j][c] hp(x)[c],  hp = [h2; p]
 __global__ void k_dense(float* __restrict__ o, const float* __restrict__ h2,
                         const float* __restrict__ W3, const float* __restrict__ b3, int vol,
                         int nout) {
@@ -104,11 +128,11 @@ __global__ void k_dense(float* __restrict__ o, const float* __restrict__ h2,
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < total;
        i += size_t(gridDim.x) * blockDim.x) {
     const int x = int(i / nout), j = int(i - size_t(x) * nout);
-    const float* h = h2 + size_t(x) * NH;
-    const float* w = W3 + size_t(j) * NH;
+    const float* h = h2 + size_t(x) * ND;
+    const float* w = W3 + size_t(j) * ND;
     float acc = b3[j];
 #pragma unroll
-    for (int c = 0; c < NH; ++c) acc = fmaf(__ldg(w + c), h[c], acc);
+    for (int c = 0; c < ND; ++c) acc = fmaf(__ldg(w + c), h[c], acc);
     o[i] = acc;
   }
 }
@@ -321,8 +345,8 @@ __global__ void k_dense_back_in(float* __restrict__ g2, const float* __restrict_
     const int x = int(i / NH), c = int(i - size_t(x) * NH);
     const float* gx = go + size_t(x) * nout;
     float acc = 0.f;
-    for (int j = 0; j < nout; ++j) acc = fmaf(__ldg(W3 + size_t(j) * NH + c), gx[j], acc);
-    const float h = h2[i];
+    for (int j = 0; j < nout; ++j) acc = fmaf(__ldg(W3 + size_t(j) * ND + c), gx[j], acc);
+    const float h = h2[size_t(x) * ND + c];
     g2[i] = acc * (1.f - h * h);
   }
 }
@@ -462,7 +486,7 @@ __global__ void k_init_params(float* th, int n, Offsets o, uint64_t seed) {
     else if (i < o.W2) scale = 0.f;
     else if (i < o.b2) scale = rsqrtf(9.f * NH);
     else if (i < o.W3) scale = 0.f;
-    else if (i < o.b3) scale = rsqrtf(float(NH));
+    else if (i < o.b3) scale = rsqrtf(float(ND));
     else scale = 0.f;
     // splitmix64 hash -> two uniforms -> Box-Muller
     uint64_t z = seed + 0x9E3779B97F4A7C15ull * uint64_t(i + 1);
@@ -479,7 +503,7 @@ void ensure_ws(mg_cnn* n, int vol) {
   if (n->vol == vol) return;
   n->f.alloc(size_t(vol) * NF * 4);
   n->h1.alloc(size_t(vol) * NH * 4);
-  n->h2.alloc(size_t(vol) * NH * 4);
+  n->h2.alloc(size_t(vol) * ND * 4);
   n->o.alloc(size_t(vol) * n->nout * 4);
   n->go.alloc(size_t(vol) * n->nout * 4);
   n->g2.alloc(size_t(vol) * NH * 4);
@@ -491,14 +515,12 @@ void forward(mg_cnn* n, const Geom& g, const void* gauge, cudaStream_t st) {
   ensure_ws(n, g.vol);
   const Offsets o = offsets(n->nout);
   const float* th = n->theta.as<float>();
-  k_features<<<blocks_for(size_t(g.vol) * 36), 256, 0, st>>>(n->f.as<float>(),
-                                                             (const cpx<double>*)gauge, g.vol);
-  k_conv9_tanh<NF><<<blocks_for(size_t(g.vol) * NH), 256, 0, st>>>(n->h1.as<float>(),
-                                                                   n->f.as<float>(), th + o.W1,
-                                                                   th + o.b1, g);
-  k_conv9_tanh<NH><<<blocks_for(size_t(g.vol) * NH), 256, 0, st>>>(n->h2.as<float>(),
-                                                                   n->h1.as<float>(), th + o.W2,
-                                                                   th + o.b2, g);
+  k_features<<<blocks_for(size_t(g.vol) * 40), 256, 0, st>>>(n->f.as<float>(), n->h2.as<float>(),
+                                                             (const cpx<double>*)gauge, g);
+  k_conv9_tanh<NF, NH><<<blocks_for(size_t(g.vol) * NH), 256, 0, st>>>(
+      n->h1.as<float>(), n->f.as<float>(), th + o.W1, th + o.b1, g);
+  k_conv9_tanh<NH, ND><<<blocks_for(size_t(g.vol) * NH), 256, 0, st>>>(
+      n->h2.as<float>(), n->h1.as<float>(), th + o.W2, th + o.b2, g);
   k_dense<<<blocks_for(size_t(g.vol) * n->nout), 256, 0, st>>>(n->o.as<float>(), n->h2.as<float>(),
                                                                th + o.W3, th + o.b3, g.vol,
                                                                n->nout);
@@ -644,14 +666,14 @@ mg_status mg_cnn_loss_grad(mg_cnn* n, const int dims[4], const int block[4], con
     float* gr = n->grad.as<float>();
     const float* th = n->theta.as<float>();
     const int nseg = (g.vol + WSEG - 1) / WSEG;
-    const size_t part_elems = size_t(nseg) * std::max(9 * NH * NF, n->nout * NH);
+    const size_t part_elems = size_t(nseg) * std::max(9 * NH * NF, n->nout * ND);
     if (n->part.bytes < part_elems * 8) n->part.alloc(part_elems * 8);
     double* part = n->part.as<double>();
     // dense layer
-    k_wgrad_seg<NH><<<dim3(nseg, 1, (n->nout + 31) / 32), 256, 0, st>>>(
+    k_wgrad_seg<ND><<<dim3(nseg, 1, (n->nout + 31) / 32), 256, 0, st>>>(
         part, n->go.as<float>(), n->nout, n->h2.as<float>(), g, 1);
-    k_wgrad_sum<<<blocks_for(size_t(n->nout) * NH), 256, 0, st>>>(gr + o.W3, part,
-                                                                  n->nout * NH, nseg);
+    k_wgrad_sum<<<blocks_for(size_t(n->nout) * ND), 256, 0, st>>>(gr + o.W3, part,
+                                                                  n->nout * ND, nseg);
     k_bias_grad<<<n->nout, 256, 0, st>>>(gr + o.b3, n->go.as<float>(), g.vol, n->nout);
     k_dense_back_in<<<blocks_for(size_t(g.vol) * NH), 256, 0, st>>>(
         n->g2.as<float>(), n->go.as<float>(), th + o.W3, n->h2.as<float>(), g.vol, n->nout);

@@ -82,6 +82,14 @@ struct Level {
   // import: gauge12_ok)
   DevBuf gauge12;
   bool gauge12_ok = false;
+  // FP32 links in the 8-real form [mu][V][8] (Sec. 4 gauge compression):
+  // a2, a3, b1 of U = [[a1 a2 a3][b1 b2 b3][c1 c2 c3]] and the phases of a1,
+  // c1, without the boundary sign (the kernel applies it); eligible when
+  // every link rebuilds to within 1e-4 (gauge8_ok); the rebuilt links'
+  // largest and root-mean-square deviation from the FP64 field
+  DevBuf gauge8;
+  bool gauge8_ok = false;
+  double gauge8_maxdev = 0.0, gauge8_rmsdev = 0.0;
   // BF16 copy of the operator for a 16-bit fine-level smoother: links
   // ([mu][V][6] two-row when gauge12_ok, else [mu][V][9]) and clover [V][72]
   DevBuf gauge16, clover16;

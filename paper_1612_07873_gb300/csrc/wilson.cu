@@ -1,5 +1,6 @@
 // Fine Wilson-clover operator of Eq. (2): gauge import, clover term A_x
 // and the stencil apply (one thread per site and vector).
+#include <cmath>
 #include <cstring>
 
 #include "kernels.cuh"
@@ -58,6 +59,86 @@ __global__ void k_gauge_compress12(cpx<float>* __restrict__ out, unsigned* __res
   }
   for (int o = 16; o > 0; o >>= 1) dev = fmaxf(dev, __shfl_xor_sync(0xffffffffu, dev, o));
   if ((threadIdx.x & 31) == 0) atomicMax(maxdev, __float_as_uint(dev));
+}
+
+// 8-real form of an SU(3) link (Sec. 4): U = [[a1 a2 a3][b1 b2 b3][c1 c2 c3]]
+// is stored as a2, a3, b1 and the phases of a1 and c1.  Unit rows and
+// columns give |a1|^2 = 1 - |a2|^2 - |a3|^2 =: n and |c1|^2 = n - |b1|^2;
+// orthogonality of rows 0 and 1 and c1 = conj(a2 b3 - a3 b2) (row 2 =
+// conj(row 0 x row 1), det U = 1) are two linear equations for b2, b3 with
+// determinant -n:
+//   b2 = -(conj(a3) conj(c1) + conj(a1) a2 b1) / n
+//   b3 =  (conj(a2) conj(c1) - conj(a1) a3 b1) / n
+// and then c2 = conj(a3 b1 - a1 b3), c3 = conj(a1 b2 - a2 b1).
+__device__ __forceinline__ void rebuild8(const float w[8], cpx<float> u[9]) {
+  const cpx<float> a2(w[0], w[1]), a3(w[2], w[3]), b1(w[4], w[5]);
+  const float n = norm2(a2) + norm2(a3);
+  const float ra1 = sqrtf(fmaxf(1.f - n, 0.f));
+  const float rc1 = sqrtf(fmaxf(n - norm2(b1), 0.f));
+  float sa, ca, sc, cc;
+  sincosf(w[6], &sa, &ca);
+  sincosf(w[7], &sc, &cc);
+  const cpx<float> a1(ra1 * ca, ra1 * sa), c1(rc1 * cc, rc1 * sc);
+  const float inv = 1.f / n;
+  const cpx<float> ab = conj(a1) * b1;
+  const cpx<float> cc1 = conj(c1);
+  const cpx<float> b2 = -inv * (conj(a3) * cc1 + a2 * ab);
+  const cpx<float> b3 = inv * (conj(a2) * cc1 - a3 * ab);
+  u[0] = a1;
+  u[1] = a2;
+  u[2] = a3;
+  u[3] = b1;
+  u[4] = b2;
+  u[5] = b3;
+  u[6] = c1;
+  u[7] = conj(a3 * b1 - a1 * b3);
+  u[8] = conj(a1 * b2 - a2 * b1);
+}
+
+// FP64 links (no boundary sign) -> the 8-real form, with the rebuilt
+// link's largest deviation (atomicMax on the float bits) and, per block,
+// the sum of squared deviations (summed on the host in block order)
+__global__ void __launch_bounds__(256) k_gauge_compress8(float* __restrict__ out,
+                                                         unsigned* __restrict__ maxdev,
+                                                         double* __restrict__ sq_part,
+                                                         const cpx<double>* __restrict__ in,
+                                                         Geom g) {
+  const size_t n = size_t(4) * g.vol;
+  float dev = 0.f;
+  double sq = 0.0;
+  for (size_t link = blockIdx.x * size_t(blockDim.x) + threadIdx.x; link < n;
+       link += size_t(gridDim.x) * blockDim.x) {
+    const cpx<double>* u = in + link * 9;
+    float w[8] = {float(u[1].re), float(u[1].im), float(u[2].re), float(u[2].im),
+                  float(u[3].re), float(u[3].im), float(atan2(u[0].im, u[0].re)),
+                  float(atan2(u[6].im, u[6].re))};
+#pragma unroll
+    for (int i = 0; i < 8; ++i) out[link * 8 + i] = w[i];
+    cpx<float> r[9];
+    rebuild8(w, r);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const double dr = double(r[i].re) - u[i].re, di = double(r[i].im) - u[i].im;
+      const double d2 = dr * dr + di * di;
+      sq += d2;
+      dev = fmaxf(dev, float(sqrt(d2)));
+    }
+  }
+  __shared__ double sh[8];
+  for (int o = 16; o > 0; o >>= 1) {
+    dev = fmaxf(dev, __shfl_xor_sync(0xffffffffu, dev, o));
+    sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(maxdev, __float_as_uint(dev));
+    sh[threadIdx.x >> 5] = sq;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (blockDim.x >> 5); ++w) t += sh[w];
+    sq_part[blockIdx.x] = t;
+  }
 }
 
 struct M3 {
@@ -189,15 +270,17 @@ __global__ void k_clover(const cpx<double>* __restrict__ U, Geom g, double csw,
   }
 }
 
-// C12: links in the two-row form (16-byte loads, 48 B per FP32 link) with
-// the third row rebuilt in registers; the rebuilt row carries the boundary
-// sign of the link (t-links leaving the last time slice).
+// LF = 18: links stored in full; LF = 12: the two-row form (16-byte loads,
+// 48 B per FP32 link) with the third row rebuilt in registers, the rebuilt
+// row carrying the boundary sign of the link (t-links leaving the last time
+// slice); LF = 8 (FP32 only): the 8-real form (two 16-byte loads, 32 B per
+// link) rebuilt by rebuild8, the boundary sign applied to the whole link.
 // Several vectors (nvec > 1, stored vstride apart): CTAs are ordered
 // vector-fastest, so the nvec CTAs of one site chunk run close together and
 // the chunk's links and clover come from DRAM once and from L2 for the
 // other vectors.
 // Eq. (2): the Wilson-clover matrix on one or several vectors.
-template <typename R, bool C12, int MINB>
+template <typename R, int LF, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_wilson(cpx<R>* __restrict__ out, const cpx<R>* __restrict__ in,
                                                 const cpx<R>* __restrict__ U, const R* __restrict__ A,
                                                 Geom g, R diag, size_t vstride, int nvec,
@@ -222,7 +305,18 @@ __global__ void __launch_bounds__(128, MINB) k_wilson(cpx<R>* __restrict__ out, 
     for (int i = 0; i < 12; ++i) psi[i] = reinterpret_cast<const cpx<R>*>(w)[i];
   };
   auto load_link = [&](size_t idx, bool neg) {
-    if constexpr (C12) {
+    if constexpr (LF == 8) {
+      const uint4* p = reinterpret_cast<const uint4*>(U) + idx * 2;
+      const uint4 w0 = __ldg(p), w1 = __ldg(p + 1);
+      const float w[8] = {__uint_as_float(w0.x), __uint_as_float(w0.y), __uint_as_float(w0.z),
+                          __uint_as_float(w0.w), __uint_as_float(w1.x), __uint_as_float(w1.y),
+                          __uint_as_float(w1.z), __uint_as_float(w1.w)};
+      rebuild8(w, u);
+      if (neg) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) u[i] = -u[i];
+      }
+    } else if constexpr (LF == 12) {
       const uint4* p = reinterpret_cast<const uint4*>(U + idx * 6);
       uint4 w[3];
 #pragma unroll
@@ -488,6 +582,27 @@ void fine_operator_build(mg_ctx* c, const void* gauge_ext, cudaStream_t st) {
     std::memcpy(&maxdev, &h, sizeof(float));
     L.gauge12_ok = maxdev < 1e-5f;
     c->launches++;
+    // 8-real link form (from the FP64 field, boundary sign applied in the kernel)
+    L.gauge8.alloc(size_t(4) * L.g.vol * 8 * sizeof(float));
+    DevBuf part;
+    part.alloc(size_t(blocks) * sizeof(double));
+    GB_CHECK(cudaMemsetAsync(dev.p, 0, sizeof(unsigned), st));
+    k_gauge_compress8<<<blocks, 256, 0, st>>>(L.gauge8.as<float>(), dev.as<unsigned>(),
+                                               part.as<double>(), (const cpx<double>*)gauge_ext,
+                                               L.g);
+    GB_LAUNCH_CHECK();
+    std::vector<double> hp(blocks);
+    GB_CHECK(cudaMemcpyAsync(&h, dev.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    GB_CHECK(cudaMemcpyAsync(hp.data(), part.p, size_t(blocks) * sizeof(double),
+                             cudaMemcpyDeviceToHost, st));
+    GB_CHECK(cudaStreamSynchronize(st));
+    std::memcpy(&maxdev, &h, sizeof(float));
+    double sq = 0.0;
+    for (double v : hp) sq += v;
+    L.gauge8_maxdev = maxdev;
+    L.gauge8_rmsdev = std::sqrt(sq / (double(n) * 2.0));
+    L.gauge8_ok = maxdev < 1e-4f;
+    c->launches++;
   }
   k_clover<<<ceil_div(L.g.vol, 128), 128, 0, st>>>(L.gauge64.as<cpx<double>>(), L.g, c->p.csw,
                                                     L.clover64.as<double>(), c32);
@@ -515,12 +630,15 @@ void wilson_apply(mg_ctx* c, Vec out, Vec in, int nvec, cudaStream_t st) {
     //   6 / 7   2 / 4 vectors per thread (links and clover reused in registers)
     //   8 / 9   links (stored / two-row) and clover of 32 sites staged in
     //           shared memory, warps looping over the vectors (nvec >= 4)
-    // Two-row policies are candidates only when the field allows them.
+    //   10 / 11 8-real links, default registers / at least 4 CTAs per SM
+    // Two-row and 8-real policies are candidates only when the field allows
+    // them.
     GB_REQUIRE(L.gauge32.p, MG_ERR_STATE, "FP32 fine operator not built");
     const unsigned gx = ceil_div(L.g.vol, 128);
     const int ap = c->p.t_antiperiodic;
     const cpx<float>* U18 = L.gauge32.as<cpx<float>>();
     const cpx<float>* U12 = L.gauge12.as<cpx<float>>();
+    const cpx<float>* U8 = L.gauge8.as<cpx<float>>();
     const float* A = L.clover32.as<float>();
     auto* o = (cpx<float>*)out.p;
     auto* i = (const cpx<float>*)in.p;
@@ -528,20 +646,23 @@ void wilson_apply(mg_ctx* c, Vec out, Vec in, int nvec, cudaStream_t st) {
     const unsigned gt = ceil_div(L.g.vol, 32);
     auto launch = [&](int q) {
       switch (q) {
-        case 1: k_wilson<float, true, 0><<<grid, 128, 0, st>>>(o, i, U12, A, L.g, dg, vs, nvec, ap); break;
-        case 2: k_wilson<float, false, 2><<<grid, 128, 0, st>>>(o, i, U18, A, L.g, dg, vs, nvec, ap); break;
-        case 3: k_wilson<float, true, 2><<<grid, 128, 0, st>>>(o, i, U12, A, L.g, dg, vs, nvec, ap); break;
-        case 4: k_wilson<float, true, 4><<<grid, 128, 0, st>>>(o, i, U12, A, L.g, dg, vs, nvec, ap); break;
-        case 5: k_wilson<float, true, 6><<<grid, 128, 0, st>>>(o, i, U12, A, L.g, dg, vs, nvec, ap); break;
+        case 1: k_wilson<float, 12, 0><<<grid, 128, 0, st>>>(o, i, U12, A, L.g, dg, vs, nvec, ap); break;
+        case 2: k_wilson<float, 18, 2><<<grid, 128, 0, st>>>(o, i, U18, A, L.g, dg, vs, nvec, ap); break;
+        case 3: k_wilson<float, 12, 2><<<grid, 128, 0, st>>>(o, i, U12, A, L.g, dg, vs, nvec, ap); break;
+        case 4: k_wilson<float, 12, 4><<<grid, 128, 0, st>>>(o, i, U12, A, L.g, dg, vs, nvec, ap); break;
+        case 5: k_wilson<float, 12, 6><<<grid, 128, 0, st>>>(o, i, U12, A, L.g, dg, vs, nvec, ap); break;
         case 6: k_wilson_mv<float, 2><<<dim3(gx, nvec / 2), 128, 0, st>>>(o, i, U18, A, L.g, dg, vs); break;
         case 7: k_wilson_mv<float, 4><<<dim3(gx, nvec / 4), 128, 0, st>>>(o, i, U18, A, L.g, dg, vs); break;
         case 8: k_wilson_tile<false><<<gt, 128, 0, st>>>(o, i, U18, A, L.g, dg, vs, nvec, ap); break;
         case 9: k_wilson_tile<true><<<gt, 128, 0, st>>>(o, i, U12, A, L.g, dg, vs, nvec, ap); break;
-        default: k_wilson<float, false, 0><<<grid, 128, 0, st>>>(o, i, U18, A, L.g, dg, vs, nvec, ap); break;
+        case 10: k_wilson<float, 8, 0><<<grid, 128, 0, st>>>(o, i, U8, A, L.g, dg, vs, nvec, ap); break;
+        case 11: k_wilson<float, 8, 4><<<grid, 128, 0, st>>>(o, i, U8, A, L.g, dg, vs, nvec, ap); break;
+        default: k_wilson<float, 18, 0><<<grid, 128, 0, st>>>(o, i, U18, A, L.g, dg, vs, nvec, ap); break;
       }
     };
     std::vector<int> cands = {0, 2};
     if (L.gauge12_ok) cands.insert(cands.end(), {1, 3, 4, 5});
+    if (L.gauge8_ok) cands.insert(cands.end(), {10, 11});
     if (nvec % 2 == 0) cands.push_back(6);
     if (nvec % 4 == 0) cands.push_back(7);
     if (nvec >= 4) {
@@ -552,7 +673,7 @@ void wilson_apply(mg_ctx* c, Vec out, Vec in, int nvec, cudaStream_t st) {
                             "/c" + std::to_string(int(L.gauge12_ok));
     launch(Tuner::get().choose(key, cands, st, launch));
   } else {
-    k_wilson<double, false, 0><<<grid, 128, 0, st>>>(
+    k_wilson<double, 18, 0><<<grid, 128, 0, st>>>(
         (cpx<double>*)out.p, (const cpx<double>*)in.p, L.gauge64.as<cpx<double>>(),
         L.clover64.as<double>(), L.g, L.diag, vs, nvec, c->p.t_antiperiodic);
   }

@@ -61,6 +61,12 @@ class Proposer:
                 log(ep, hist[-1])
         return hist
 
+    def step(self, dims, block, gauge, target, lr):
+        """One training step (loss, gradient, Adam); returns the loss."""
+        loss = mg_cnn_loss_grad(self.net, dims, block, gauge, target)
+        mg_cnn_adam_step(self.net, lr)
+        return loss
+
     def loss(self, dims, block, gauge, target):
         return mg_cnn_loss_grad(self.net, dims, block, gauge, target)
 

@@ -27,8 +27,8 @@ import os
 
 import numpy as np
 
-__all__ = ["gauge_field", "gaussian_field", "gauge_transform", "free_field_starts", "WORKLOADS",
-           "volume"]
+__all__ = ["gauge_field", "gauge_fields", "gaussian_field", "gauge_transform",
+           "free_field_starts", "WORKLOADS", "volume"]
 
 
 def volume(dims) -> int:
@@ -107,6 +107,26 @@ def gauge_field(dims, eps: float, seed: int, workers: int | None = None) -> np.n
     else:
         parts = [_gauge_chunk(j) for j in jobs]
     return np.concatenate(parts).reshape(4, vol, 3, 3)
+
+
+def _one_field(args):
+    dims, eps, seed = args
+    return gauge_field(dims, eps, seed, workers=1)
+
+
+def gauge_fields(dims, eps_list, seeds, workers: int | None = None) -> list:
+    """gauge_field(dims, eps_list[i], seeds[i]) for every i, the fields
+    drawn in parallel by `workers` spawned processes (each field is
+    identical to its serial draw)."""
+    jobs = [(tuple(dims), float(e), int(s)) for e, s in zip(eps_list, seeds)]
+    if workers is None:
+        workers = min(len(jobs), os.cpu_count() or 1, 16)
+    if workers <= 1 or len(jobs) <= 1:
+        return [_one_field(j) for j in jobs]
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_one_field, jobs))
 
 
 def random_su3(n: int, seed: int) -> np.ndarray:

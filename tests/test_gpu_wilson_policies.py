@@ -2,8 +2,9 @@
 
 The autotuner picks one policy per shape; here each policy is pinned in turn
 through mg_tune_set: stored 18-real links or two-row links rebuilt in
-registers (third row = conj(row0 x row1) times the boundary sign), four
-register budgets, and, in the batched form used by the setup sweeps and the
+registers (third row = conj(row0 x row1) times the boundary sign), 8-real
+links (a2, a3, b1 and two phases, the rest rebuilt from unitarity and
+det U = 1, the boundary sign applied to the whole link), register budgets, and, in the batched form used by the setup sweeps and the
 multi-RHS solve, 2 or 4 vectors per thread or the operator of 32 sites staged
 in shared memory for all vectors.  A field that is not special unitary must never take the
 two-row form.
@@ -18,7 +19,7 @@ from gpu_helpers import make_ctx, oracle_fine, rel_l2, to_dev, to_np
 
 pytestmark = pytest.mark.gpu
 
-SINGLE = [0, 1, 2, 3, 4, 5]   # 1 vector per thread: (link form, register budget)
+SINGLE = [0, 1, 2, 3, 4, 5, 10, 11]   # 1 vector per thread: (link form, register budget)
 BATCHED = [6, 7, 8, 9]        # 2 or 4 vectors per thread; shared-memory operator tile
 
 
@@ -63,15 +64,43 @@ def test_batched_policy_in_setup(gpu_lib, policy):
     mg.close()
 
 
+@pytest.mark.parametrize("eps", [0.3, 0.5, 0.9])
+def test_eight_real_reconstruction_error_is_stated(gpu_lib, eps):
+    """The 8-real form is eligible on these fields and its FP32 rebuild
+    deviates from the FP64 links by at most 1e-4 (largest entry) and by a
+    root-mean-square of FP32 rounding size; the operator built from it meets
+    the FP32 tier against the oracle."""
+    gb = gpu_lib
+    dims = (8, 4, 6, 8)
+    vol = lat.volume(dims)
+    key = f"wilson/v{vol}/n1/c1"
+    gb.mg_tune_set(key, 10)
+    mg, U = make_ctx(gb, dims, [(2, 2, 2, 2)], [2], prec_fine=1, prec_coarse=1, eps=eps)
+    info = gb.mg_gauge_compression(mg.ctx)
+    assert info["two_row"] and info["eight_real"], info
+    assert info["max_dev8"] < 1e-4 and info["rms_dev8"] < 1e-6, info
+    psi = syn.gaussian_field((vol, 12), 75)
+    out = torch.empty((vol, 12), dtype=torch.complex64, device="cuda")
+    gb.mg_wilson_clover_apply(mg.ctx, out, to_dev(psi, torch.complex64))
+    torch.cuda.synchronize()
+    assert gb.mg_tune_get(key) == 10
+    err = rel_l2(to_np(out), oracle_fine(U, dims).apply(psi))
+    assert err < 1e-5, err
+    gb.mg_tune_set(key, -1)
+    mg.close()
+
+
 def test_non_unitary_field_keeps_stored_links(gpu_lib):
-    """Links scaled off SU(3): the two-row form is not eligible (key suffix
-    c0) and a pinned two-row policy is ignored."""
+    """Links scaled off SU(3): neither the two-row nor the 8-real form is
+    eligible (key suffix c0) and a pinned two-row policy is ignored."""
     gb = gpu_lib
     dims = (4, 4, 6, 4)
     vol = lat.volume(dims)
     U = syn.gauge_field(dims, 0.4, 5) * 1.05
     gb.mg_tune_set(f"wilson/v{vol}/n1/c0", 3)  # a two-row policy: not a candidate here
     mg, _ = make_ctx(gb, dims, [(2, 2, 2, 2)], [2], prec_fine=1, prec_coarse=1, U=U)
+    info = gb.mg_gauge_compression(mg.ctx)
+    assert not info["two_row"] and not info["eight_real"], info
     psi = syn.gaussian_field((vol, 12), 73)
     out = torch.empty((vol, 12), dtype=torch.complex64, device="cuda")
     gb.mg_wilson_clover_apply(mg.ctx, out, to_dev(psi, torch.complex64))

@@ -436,7 +436,21 @@ def test_learned_gradient_matches_finite_differences():
     th = ol.init_params(nv, 75)
     L, g = ol.loss_and_grad(th, U, dims, nv, T, block)
     rng = np.random.default_rng(76)
-    for i in rng.choice(th.size, 12, replace=False):
+    # parameters of every block, the position channels of the first layer
+    # (W1[d][c][72..79]) and of the output layer (W3[j][32..39]) included
+    off, picks = 0, []
+    for name, shp in ol.param_shapes(nv):
+        blk = np.arange(int(np.prod(shp))).reshape(shp) + off
+        off += blk.size
+        if name == "W1":
+            picks += list(rng.choice(blk[..., :72].ravel(), 2, replace=False))
+            picks += list(rng.choice(blk[..., 72:].ravel(), 3, replace=False))
+        elif name == "W3":
+            picks += list(rng.choice(blk[:, :32].ravel(), 2, replace=False))
+            picks += list(rng.choice(blk[:, 32:].ravel(), 3, replace=False))
+        else:
+            picks += list(rng.choice(blk.ravel(), 1, replace=False))
+    for i in picks:
         e = np.zeros_like(th)
         e[i] = 1e-6
         Lp, _ = ol.loss_and_grad(th + e, U, dims, nv, T, block)

@@ -73,3 +73,35 @@ def test_random_su3_is_special_unitary():
     uu = np.einsum("nji,njk->nik", G.conj(), G)
     assert np.abs(uu - np.eye(3)).max() < 1e-14
     assert np.abs(np.linalg.det(G) - 1.0).max() < 1e-14
+
+
+def test_many_fields_equal_their_serial_draws():
+    dims = (2, 2, 4, 4)
+    eps, seeds = [0.3, 0.45, 0.6], [1000, 1001, 1002]
+    par = syn.gauge_fields(dims, eps, seeds, workers=2)
+    for e, s, u in zip(eps, seeds, par):
+        assert np.array_equal(u, syn.gauge_field(dims, e, s, workers=1))
+
+
+def test_free_field_starts_are_low_momentum_plane_waves():
+    """Vector i: unit components i mod 6 and i mod 6 + 6 (one per
+    chirality) times exp(i p.x), p_t = pi / Lt plus 2 pi / L_mu along mu =
+    i div 6 - 1; every vector has unit modulus on its two components, and
+    the translation by one site along mu multiplies it by exp(i p_mu)."""
+    dims = (4, 6, 4, 8)
+    v = syn.free_field_starts(dims, 24)
+    vol = syn.volume(dims)
+    assert v.shape == (24, vol, 12)
+    for i in range(24):
+        a, k = i % 6, i // 6
+        nz = np.nonzero(np.abs(v[i]).sum(axis=0))[0]
+        assert list(nz) == [a, a + 6]
+        assert np.allclose(np.abs(v[i][:, [a, a + 6]]), 1.0)
+        p = np.array([0.0, 0.0, 0.0, np.pi / dims[3]])
+        if k >= 1:
+            p[k - 1] += 2 * np.pi / dims[k - 1]
+        # x -> x + 1 (away from the x wrap): phase exp(i p_x)
+        s = 1 + dims[0] * (2 + dims[1] * (1 + dims[2] * 3))
+        assert np.isclose(v[i][s + 1, a] / v[i][s, a], np.exp(1j * p[0]))
+        st = dims[0] * dims[1] * dims[2]
+        assert np.isclose(v[i][s + st, a] / v[i][s, a], np.exp(1j * p[3]))
