@@ -605,6 +605,69 @@ def coarse_apply_main(args):
     return 0
 
 
+def mma_sweep_main(args):
+    """Config-4 sweep of the multi-RHS coarse apply (BF16 links, FP32
+    accumulation) on the two coarse lattices of the production workload,
+    8^3x16 (n = 48) and 4^3x8 (n = 64), with Gaussian links: nrhs = 1 (the
+    single-RHS stream) and 8, 16, 32, 64 (tensor cores, autotuned launch
+    shape).  Every timed apply follows a write of 512 MB (L2 flushed), timed
+    alone by the library's CUDA events; the same applies back to back give
+    the L2-warm figure.  GB/s of algorithmic bytes (links + x read + y
+    written) and the fraction of the measured HBM copy peak."""
+    import torch
+
+    import paper_1612_07873_gb300 as gb
+    peak, kind = peaks()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    rows = []
+    for cdims, nv in (((8, 8, 8, 16), 24), ((4, 4, 4, 8), 32)):
+        fine = tuple(2 * c for c in cdims)
+        U = torch.from_numpy(syn.gauge_field(fine, 0.0, 1)).cuda()
+        p = gb.default_params(dims=fine, block=[(2, 2, 2, 2)], nvec=[nv], nlevels=2,
+                              prec_fine=1, prec_coarse=2)
+        mg = gb.Multigrid(p, U)
+        l1 = mg.levels[1]
+        vol, n = l1["volume"], l1["ndof"]
+        g = torch.Generator(device="cuda").manual_seed(3)
+        links = torch.randn((vol, 9, n, n), dtype=torch.complex128, device="cuda", generator=g)
+        gb.mg_set_coarse_links(mg.ctx, 1, links)
+        del links
+        for nrhs in (1, 8, 16, 32, 64):
+            shape = (vol, n) if nrhs == 1 else (vol, n, nrhs)
+            x = torch.randn(shape, dtype=torch.complex64, device="cuda", generator=g)
+            y = torch.empty_like(x)
+            for _ in range(max(args.warmup, 2)):
+                gb.mg_coarse_apply(mg.ctx, 1, y, x, nrhs=nrhs)
+            name = "coarse_apply" if nrhs == 1 else "coarse_apply_multi"
+            out = {"lattice": list(cdims), "ndof": n, "nrhs": nrhs}
+            for mode in ("flushed", "warm"):
+                torch.cuda.synchronize()
+                gb.mg_profile_reset(mg.ctx)
+                gb.mg_profile_enable(mg.ctx, True)
+                for _ in range(args.steps):
+                    if mode == "flushed":
+                        flush.fill_(1)
+                    gb.mg_coarse_apply(mg.ctx, 1, y, x, nrhs=nrhs)
+                gb.mg_device_status(mg.ctx)
+                q = gb.mg_profile_query(mg.ctx, name, 1)
+                gb.mg_profile_enable(mg.ctx, False)
+                us = 1e3 * q["ms"] / q["launches"]
+                gbs = q["bytes"] / q["launches"] / (us * 1e-6) / 1e9
+                out[mode] = {"us": us, "gbs": gbs, "frac": gbs / peak,
+                             "tflops": q["flops"] / q["launches"] / (us * 1e-6) / 1e12}
+                out["bytes"] = q["bytes"] / q["launches"]
+            if nrhs > 1:
+                out["launch_choice"] = gb.mg_tune_get(f"mma2/bf16/n{n}/r{nrhs}/v{vol}/b1")
+            rows.append(out)
+            del x, y
+        mg.close()
+    print(json.dumps({"mode": "mma-sweep", "peak_gbs": peak, "peak_kind": kind,
+                      "choice_code": "100 + S: pipelined kernel, S-stage ring; q <= 8: "
+                                     "register-staged kernel, q CTAs per SM",
+                      "rows": rows}), flush=True)
+    return 0
+
+
 def wilson_policies_main(args):
     """Every launch policy of the FP32 fine operator, pinned in turn through
     mg_tune_set, on the 32^3x64 workload lattice for 1, 8 and 24 vectors
@@ -731,7 +794,7 @@ def main():
     ap.add_argument("--form", default="fp32", choices=["fp32", "bf16", "fp16", "int16"])
     ap.add_argument("--mode", default="pipeline",
                     choices=["pipeline", "coarse-apply", "wilson-policies", "solve-breakdown",
-                             "learned"])
+                             "learned", "mma-sweep"])
     ap.add_argument("--fine", default="", help="override the fine extents, e.g. 16,16,16,32")
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides (coarse-apply mode)")
     ap.add_argument("--slots", type=int, default=9, choices=[5, 9],
@@ -759,6 +822,8 @@ def main():
         return solve_breakdown_main(args)
     if args.mode == "learned":
         return learned_main(args)
+    if args.mode == "mma-sweep":
+        return mma_sweep_main(args)
     return gpu_main(args)
 
 

@@ -256,7 +256,9 @@ mg_status mg_level_info(mg_ctx* ctx, int level, int dims[4], int* volume, int* n
  * unit rows and columns and det U = 1) is eligible.  *max_dev8 and
  * *rms_dev8: the largest and the root-mean-square |U_rebuilt - U| over the
  * entries of every link, FP32 rebuild against the FP64 field.  The 8-real
- * form is eligible when the largest is below 1e-4; both forms are launch
+ * form is eligible when the root-mean-square is below 1e-6 and the largest
+ * below 1e-3 (the rebuild divides by 1 - |a1|^2, which is small on the
+ * rare links close to a diagonal matrix); both forms are launch
  * policies of mg_wilson_clover_apply that the autotuner may pick.  Zeros
  * for an FP64 fine level.                                                  */
 mg_status mg_gauge_compression(mg_ctx* ctx, int* forms, double* max_dev8, double* rms_dev8);

@@ -18,6 +18,12 @@
 // exchange real/imaginary rows through shared memory and store Y coalesced.
 // Every mbarrier wait is bounded: on timeout the kernel records an error
 // word, waits (bounded) for its MMAs, frees its TMEM and returns.
+//
+// Two kernels do this: k_coarse_mma (register-staged operands, two
+// buffers, the whole CTA in step) and k_coarse_mma_ws (warp-specialised:
+// bulk copies of the link operand into an S-stage ring, separate staging,
+// MMA and epilogue warps).  The autotuner picks the kernel and the ring
+// depth (or the CTAs per SM) per shape.
 #include "kernels.cuh"
 #include "tune.cuh"
 
@@ -100,6 +106,32 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// L2 policy for data read exactly once (the link stream): evicted first, so
+// the spinors that nine sites share stay resident
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+// bulk copy global -> this CTA's shared memory, completing `bytes` of
+// transaction on the mbarrier (16-byte aligned addresses, bytes % 16 == 0)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar, uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+      "[%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+      : "memory");
+}
+
 // 32 lanes x 16 consecutive FP32 columns
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   uint32_t r[16];
@@ -386,6 +418,254 @@ __global__ void __launch_bounds__(128) k_coarse_mma(const MmaBatch batch, int nr
 #undef BBUF
 }
 
+// ---------------------------------------------------------------------------
+// Warp-specialised, pipelined form of the same GEMM (persistent, one CTA per
+// SM, 320 threads).  A pipeline stage is one stencil slot (K = 2n): the
+// slot's links, one contiguous 4 n^2-byte run of the tiled store, arrive by
+// one bulk copy (cp.async.bulk, L2 evict-first) and the neighbour's spinor is
+// converted into the BF16/FP16 operand by four warps, into an S-deep ring.
+//   warps 0-3  spinor operand of each slot (x(nbr) -> rows j, nrhs + j)
+//   warps 4-7  epilogue: their TMEM lane quarter -> shared memory -> y
+//   warp 8     lane 0 issues the link copies
+//   warp 9     lane 0 issues the MMAs of each stage and commits them
+// Barriers per ring slot: full_l (copy bytes), full_x (128 staging
+// threads), empty (the slot's MMAs done); per accumulator (two TMEM buffers
+// of n columns, so the epilogue of one site overlaps the MMAs of the next):
+// acc_full (MMAs of the site done), acc_empty (128 epilogue threads done).
+// The spinor operand keeps only its 2 nrhs used rows; the MMA's rows beyond
+// them (M = 128) read whatever follows in shared memory and produce
+// accumulator rows that are never read.  Every wait is bounded; on a
+// timeout (or the injected stall) every role stops, the copy issuer waits
+// for its copies in flight, the MMA issuer for its MMAs, and TMEM is freed.
+constexpr int kWsThreads = 320;
+constexpr int kWsMaxStages = 8;
+
+__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity,
+                                              volatile int* abort_flag, int* err) {
+  constexpr uint64_t kBudgetNs = 1000000000ull;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 0;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if ((it & 255u) == 255u && global_ns() - t0 > kBudgetNs) {
+      *abort_flag = 1;
+      atomicOr(err, 1);
+      return false;
+    }
+  }
+}
+
+template <bool BF16, int N>
+__global__ void __launch_bounds__(kWsThreads, 1)
+    k_coarse_mma_ws(const MmaBatch batch, int nrhs, int S, int* __restrict__ err) {
+  constexpr int HB = 2 * N * N;                        // link bytes of a half slot
+  constexpr int LB = 2 * HB;                           // link bytes of a slot
+  constexpr uint32_t LBO = 128, SBO = (N / 8) * 128;  // K extent N per half, both operands
+  constexpr uint32_t IDESC = mma_idesc(128, N, BF16);
+  constexpr uint32_t TMEM_COLS = 128;                  // accumulators at columns 0 and 64
+  constexpr int CS = N + 1;
+  constexpr int XPT = (N / 4) * 8 / 4;                 // spinor tiles per staging warp, nrhs <= 64
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ uint64_t full_l[kWsMaxStages], full_x[kWsMaxStages], empty[kWsMaxStages];
+  __shared__ uint64_t acc_full[2], acc_empty[2], fin, stall_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ volatile int abort_sh;
+  __shared__ int epi_ok;
+  const int XH = 4 * nrhs * N;  // spinor bytes of a half slot: 2 nrhs rows x N K values
+  const int XB = 2 * XH;
+  unsigned char* xring = smem;
+  unsigned char* lring = smem + size_t(S) * XB;
+  float* Cs = reinterpret_cast<float*>(lring + size_t(S) * LB);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (warp == 0) {
+    tmem_alloc(&tmem_base_sh, TMEM_COLS);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    for (int q = 0; q < S; ++q) {
+      mbar_init(&full_l[q], 1);
+      mbar_init(&full_x[q], 128);
+      mbar_init(&empty[q], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 128);
+    }
+    mbar_init(&fin, 1);
+    mbar_init(&stall_bar, 1);  // the injected stall's barrier; never arrived at
+    fence_mbar_init();
+    abort_sh = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_sh;
+  if (batch.stall) {
+    if (tid == 0 && !mbar_wait(&stall_bar, 0u)) {
+      abort_sh = 1;
+      atomicOr(err, 1);
+    }
+    __syncthreads();
+  }
+  auto lattice_of_site = [&](int gs) {
+    int li = 0;
+#pragma unroll
+    for (int q = 1; q < kMaxBatch; ++q)
+      if (q < batch.count && batch.lat[q].site0 <= gs) li = q;
+    return li;
+  };
+
+  if (warp < 4) {
+    // ---- spinor operand: tiles of 4 complex columns k x 8 right-hand
+    // sides j; lane l takes j = 8 jt + (l & 7), k = 4 kt + (l >> 3), so a
+    // warp's 32 four-byte stores fill one 8-row x 16-byte core matrix
+    const int jt_n = (nrhs + 7) >> 3;
+    const int ntiles = (N / 4) * jt_n;
+    uint32_t q = 0;
+    for (int gs = blockIdx.x; gs < batch.total && !abort_sh; gs += gridDim.x) {
+      const MmaLattice& cur = batch.lat[lattice_of_site(gs)];
+      const int site = gs - cur.site0;
+      int c[4];
+      site_coords(cur.g, site, c);
+      for (int d = 0; d < 9; ++d, ++q) {
+        const uint32_t sl = q % uint32_t(S), ph = (q / uint32_t(S)) & 1u;
+        if (!wait_or_abort(&empty[sl], ph ^ 1u, &abort_sh, err)) break;
+        const cpx<float>* xs = cur.x + size_t(neighbour(cur.g, site, c, d)) * N * nrhs;
+        unsigned char* A = xring + size_t(sl) * XB;
+        // loads in batches of 16 independent 8-byte loads per thread
+#pragma unroll
+        for (int u0 = 0; u0 < XPT; u0 += 16) {
+          cpx<float> v[16];
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            const int t = warp + 4 * (u0 + u);
+            const int j = 8 * (t % jt_n) + (lane & 7), k = 4 * (t / jt_n) + (lane >> 3);
+            if (u0 + u < XPT && t < ntiles && j < nrhs) v[u] = xs[k * nrhs + j];
+          }
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            const int t = warp + 4 * (u0 + u);
+            const int j = 8 * (t % jt_n) + (lane & 7), k = 4 * (t / jt_n) + (lane >> 3);
+            if (u0 + u < XPT && t < ntiles && j < nrhs) {
+              const int h = k / (N / 2), kl = k - h * (N / 2);
+              unsigned char* Ah = A + h * XH;
+              *reinterpret_cast<uint32_t*>(Ah + core_off(j, 2 * kl, N)) =
+                  pack2<BF16>(v[u].re, -v[u].im);
+              *reinterpret_cast<uint32_t*>(Ah + core_off(nrhs + j, 2 * kl, N)) =
+                  pack2<BF16>(v[u].im, v[u].re);
+            }
+          }
+        }
+        fence_proxy_async_smem();
+        mbar_arrive(&full_x[sl]);
+      }
+    }
+  } else if (warp < 8) {
+    // ---- epilogue
+    const int e = tid - 128, ew = e >> 5;
+    uint32_t it = 0;
+    for (int gs = blockIdx.x; gs < batch.total; gs += gridDim.x, ++it) {
+      const uint32_t b = it & 1u, ph = (it >> 1) & 1u;
+      if (e == 0) epi_ok = wait_or_abort(&acc_full[b], ph, &abort_sh, err) ? 1 : 0;
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (!epi_ok) break;
+      tc_fence_after();
+      const MmaLattice& cur = batch.lat[lattice_of_site(gs)];
+      const int site = gs - cur.site0;
+      const int row = 32 * ew + lane;
+      if (32 * ew < 2 * nrhs) {
+#pragma unroll
+        for (int c0 = 0; c0 < N; c0 += 16) {
+          float v[16];
+          tmem_ld16(tmem + (uint32_t(32 * ew) << 16) + b * 64u + uint32_t(c0), v);
+          if (row < 2 * nrhs) {
+#pragma unroll
+            for (int q2 = 0; q2 < 16; ++q2) Cs[row * CS + c0 + q2] = v[q2];
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&acc_empty[b]);
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      const float sc = cur.scales[site];
+      cpx<float>* ys = cur.y + size_t(site) * N * nrhs;
+      for (int q2 = e; q2 < N * nrhs; q2 += 128) {
+        const int m = q2 / nrhs, j = q2 - m * nrhs;
+        ys[q2] = cpx<float>(sc * Cs[j * CS + m], sc * Cs[(nrhs + j) * CS + m]);
+      }
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+    }
+  } else if (warp == 8) {
+    // ---- link copies
+    if (lane == 0) {
+      const uint64_t pol = policy_evict_first();
+      uint32_t q = 0;
+      bool go = true;
+      for (int gs = blockIdx.x; gs < batch.total && go && !abort_sh; gs += gridDim.x) {
+        const MmaLattice& cur = batch.lat[lattice_of_site(gs)];
+        const unsigned char* src =
+            reinterpret_cast<const unsigned char*>(cur.links) + size_t(gs - cur.site0) * 9 * LB;
+        for (int d = 0; d < 9; ++d) {
+          const uint32_t sl = q % uint32_t(S), ph = (q / uint32_t(S)) & 1u;
+          if (!wait_or_abort(&empty[sl], ph ^ 1u, &abort_sh, err)) {
+            go = false;
+            break;
+          }
+          mbar_arrive_expect_tx(&full_l[sl], LB);
+          bulk_g2s(lring + size_t(sl) * LB, src + size_t(d) * LB, LB, &full_l[sl], pol);
+          ++q;
+        }
+      }
+      // copies still in flight land before the CTA's shared memory goes away
+      const uint32_t first = q > uint32_t(S) ? q - uint32_t(S) : 0u;
+      for (uint32_t r = first; r < q; ++r)
+        mbar_wait(&full_l[r % uint32_t(S)], (r / uint32_t(S)) & 1u);
+    }
+  } else {
+    // ---- MMA issue
+    if (lane == 0) {
+      uint32_t q = 0, it = 0;
+      bool issued = false, go = true;
+      for (int gs = blockIdx.x; gs < batch.total && go && !abort_sh; gs += gridDim.x, ++it) {
+        const uint32_t b = it & 1u, ph = (it >> 1) & 1u;
+        if (!wait_or_abort(&acc_empty[b], ph ^ 1u, &abort_sh, err)) break;
+        tc_fence_after();
+        const uint32_t dt = tmem + b * 64u;
+        for (int d = 0; d < 9; ++d, ++q) {
+          const uint32_t sl = q % uint32_t(S), sp = (q / uint32_t(S)) & 1u;
+          if (!wait_or_abort(&full_l[sl], sp, &abort_sh, err) ||
+              !wait_or_abort(&full_x[sl], sp, &abort_sh, err)) {
+            go = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(xring + size_t(sl) * XB);
+          const uint32_t b0 = smem_u32(lring + size_t(sl) * LB);
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int kk = 0; kk < N / 16; ++kk)
+              mma_f16(dt, smem_desc(a0 + h * XH + kk * 256, LBO, SBO),
+                      smem_desc(b0 + h * HB + kk * 256, LBO, SBO), IDESC,
+                      (d > 0 || h > 0 || kk > 0) ? 1u : 0u);
+          mma_commit(&empty[sl]);
+          issued = true;
+        }
+        if (!go) break;
+        mma_commit(&acc_full[b]);
+      }
+      if (issued) {  // every MMA issued has completed before TMEM is freed
+        mma_commit(&fin);
+        mbar_wait(&fin, 0u);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+}
+
 // FP32 internal links [V][9][col k][row m] (unscaled) -> tiled 16-bit MMA
 // operand [V][9][core(m, 2k)] scaled by the per-site scale.
 // Eq. (3) links tiled as the tensor-core B operand.
@@ -409,20 +689,36 @@ __global__ void k_links_tile_mma(uint32_t* __restrict__ out, const cpx<float>* _
   }
 }
 
+// Dynamic shared memory of the pipelined kernel with S stages; 0 if the
+// footprint exceeds `limit`.  The spinor ring comes first: the MMA rows
+// beyond 2 nrhs of its last half slot read up to 256 n bytes past that half,
+// which stays inside the link ring that follows.
+template <int N>
+size_t ws_smem(int nrhs, int S, size_t limit) {
+  const size_t XB = size_t(8) * nrhs * N, LB = size_t(4) * N * N;
+  const size_t cs = ((size_t(2) * nrhs * (N + 1) * 4) + 15) / 16 * 16;
+  const size_t total = size_t(S) * (XB + LB) + cs;
+  const size_t reach = size_t(S - 1) * XB + XB / 2 + size_t(256) * N;
+  if (reach > total || total > limit) return 0;
+  return total;
+}
+
 template <bool BF16, int N>
 void launch_mma_batch(int* err, const MmaBatch& batch, int nrhs, cudaStream_t st, bool tune) {
   constexpr int KS = N;
   const int smem = 2 * (128 * KS * 2) + 2 * (N * KS * 2);
   auto kern = k_coarse_mma<BF16, N>;
+  auto kws = k_coarse_mma_ws<BF16, N>;
   GB_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   GB_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   // CTAs per SM from the kernel's own footprint: shared memory (dynamic +
   // static + 1 KB reserved per CTA) and registers; TMEM allows 8 x 64 columns
-  int sms = 0, dev = 0, smem_sm = 0, regs_sm = 0;
+  int sms = 0, dev = 0, smem_sm = 0, regs_sm = 0, optin = 0;
   GB_CHECK(cudaGetDevice(&dev));
   GB_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   GB_CHECK(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
   GB_CHECK(cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev));
+  GB_CHECK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   cudaFuncAttributes fa;
   GB_CHECK(cudaFuncGetAttributes(&fa, kern));
   int per_sm = smem_sm / int(smem + fa.sharedSizeBytes + 1024);
@@ -430,19 +726,39 @@ void launch_mma_batch(int* err, const MmaBatch& batch, int nrhs, cudaStream_t st
   if (by_regs < per_sm) per_sm = by_regs;
   if (per_sm > 8) per_sm = 8;
   if (per_sm < 1) per_sm = 1;
-  // autotuned: resident CTAs per SM (the largest that fits is the default)
-  std::vector<int> cands{per_sm};
-  for (int q = per_sm - 1; q >= 1 && cands.size() < 3; --q) cands.push_back(q);
+  cudaFuncAttributes fw;
+  GB_CHECK(cudaFuncGetAttributes(&fw, kws));
+  const size_t ws_limit = size_t(optin) - fw.sharedSizeBytes;
+  // pipelined kernel: the deepest ring that fits (up to 8 stages)
+  int smax = 0;
+  for (int S = kWsMaxStages; S >= 2 && !smax; --S)
+    if (ws_smem<N>(nrhs, S, ws_limit)) smax = S;
+  // Autotuned launch shape.  Choice 100 + S: the pipelined kernel with an
+  // S-stage ring (one persistent CTA per SM); choice q <= 8: the
+  // register-staged kernel with q resident CTAs per SM.
+  std::vector<int> cands;
+  for (int S = smax; S >= 2; --S) cands.push_back(100 + S);
+  cands.push_back(per_sm);
+  if (per_sm > 1) cands.push_back(1);
   auto launch = [&](int q) {
+    if (q > 100) {
+      const int S = q - 100;
+      const size_t sm = ws_smem<N>(nrhs, S, ws_limit);
+      GB_CHECK(cudaFuncSetAttribute(kws, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
+      int grid = sms;
+      if (grid > batch.total) grid = batch.total;
+      kws<<<grid, kWsThreads, sm, st>>>(batch, nrhs, S, err);
+      return;
+    }
     int grid = sms * q;
     if (grid > batch.total) grid = batch.total;
     kern<<<grid, 128, smem, st>>>(batch, nrhs, err);
   };
   if (!tune || batch.stall) {
-    launch(per_sm);
+    launch(cands.front());
     return;
   }
-  const std::string key = std::string("mma/") + (BF16 ? "bf16" : "f16") + "/n" +
+  const std::string key = std::string("mma2/") + (BF16 ? "bf16" : "f16") + "/n" +
                           std::to_string(N) + "/r" + std::to_string(nrhs) + "/v" +
                           std::to_string(batch.total) + "/b" + std::to_string(batch.count);
   launch(Tuner::get().choose(key, cands, st, launch));

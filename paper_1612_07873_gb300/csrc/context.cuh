@@ -85,8 +85,8 @@ struct Level {
   // FP32 links in the 8-real form [mu][V][8] (Sec. 4 gauge compression):
   // a2, a3, b1 of U = [[a1 a2 a3][b1 b2 b3][c1 c2 c3]] and the phases of a1,
   // c1, without the boundary sign (the kernel applies it); eligible when
-  // every link rebuilds to within 1e-4 (gauge8_ok); the rebuilt links'
-  // largest and root-mean-square deviation from the FP64 field
+  // the rebuilt links deviate from the FP64 field by less than 1e-6 root-
+  // mean-square and 1e-3 at most (gauge8_ok); both deviations are kept
   DevBuf gauge8;
   bool gauge8_ok = false;
   double gauge8_maxdev = 0.0, gauge8_rmsdev = 0.0;

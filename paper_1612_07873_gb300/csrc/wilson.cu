@@ -601,7 +601,10 @@ void fine_operator_build(mg_ctx* c, const void* gauge_ext, cudaStream_t st) {
     for (double v : hp) sq += v;
     L.gauge8_maxdev = maxdev;
     L.gauge8_rmsdev = std::sqrt(sq / (double(n) * 2.0));
-    L.gauge8_ok = maxdev < 1e-4f;
+    // the rebuild's error grows like 1 / (1 - |a1|^2) on the rare links
+    // close to a diagonal matrix: the form is eligible when the deviation is
+    // at FP32 rounding size on average and bounded everywhere
+    L.gauge8_ok = L.gauge8_rmsdev < 1e-6 && maxdev < 1e-3f;
     c->launches++;
   }
   k_clover<<<ceil_div(L.g.vol, 128), 128, 0, st>>>(L.gauge64.as<cpx<double>>(), L.g, c->p.csw,

@@ -63,6 +63,37 @@ def test_fine_apply_sampled(hierarchy):
     assert err < 1e-5, err
 
 
+@pytest.mark.parametrize("policy", [4, 10])
+def test_fine_apply_compressed_links_sampled(hierarchy, policy):
+    """Two-row (policy 4) and 8-real (policy 10) links at full size; the
+    sample includes the 16 sites whose forward links are closest to a
+    diagonal matrix (smallest 1 - |U_00|^2, where the 8-real rebuild divides)
+    and their backward partners."""
+    gb, mg, U = hierarchy
+    vol = lat.volume(DIMS)
+    info = gb.mg_gauge_compression(mg.ctx)
+    assert info["two_row"] and info["eight_real"], info
+    key = f"wilson/v{vol}/n1/c1"
+    gb.mg_tune_set(key, policy)
+    psi = syn.gaussian_field((vol, 12), 105)
+    out = torch.empty((vol, 12), dtype=torch.complex64, device="cuda")
+    gb.mg_wilson_clover_apply(mg.ctx, out, torch.from_numpy(psi).to("cuda", torch.complex64))
+    got = out.cpu().numpy().astype(np.complex128)
+    assert gb.mg_tune_get(key) == policy
+    gb.mg_tune_set(key, -1)
+    nrm = 1.0 - np.abs(U[:, :, 0, 0]) ** 2            # [mu][site]
+    worst = np.argsort(nrm.ravel())[:16]
+    mu, site = np.unravel_index(worst, nrm.shape)
+    c = lat.coords(DIMS)[site]
+    partner = lat.index(DIMS, c + np.eye(4, dtype=np.int64)[mu])
+    sites = np.unique(np.concatenate([_sample_sites(DIMS, 100, 106), site, partner]))
+    blocks = dirac.wilson_clover_blocks(U, DIMS, W["mass"], W["csw"], bool(W["antiperiodic"]),
+                                        sites=sites)
+    want = dirac.apply_at(blocks, psi, DIMS, sites)
+    err = np.linalg.norm(got[sites] - want) / np.linalg.norm(want)
+    assert err < 1e-5, (policy, err, info)
+
+
 def test_level1_apply_and_backward_links_sampled(hierarchy):
     gb, mg, U = hierarchy
     lv = mg.levels[1]

@@ -36,6 +36,40 @@ def test_coarse_apply_tensor_cores(gpu_lib, prec, cdims, nv, nrhs):
     mg.close()
 
 
+@pytest.mark.parametrize("cdims,nv,nrhs,choices", [
+    ((4, 4, 4, 8), 24, 8, (102, 105, 108, 1)),     # 512 sites: several per CTA
+    ((6, 4, 4, 6), 24, 64, (102, 104, 106)),
+    ((4, 4, 4, 8), 32, 32, (102, 106, 1)),
+    ((4, 4, 4, 8), 16, 4, (102, 108)),
+])
+def test_every_launch_shape_on_many_sites(gpu_lib, cdims, nv, nrhs, choices):
+    """Each launch shape pinned in turn: the pipelined kernel with an S-deep
+    ring (choice 100 + S, S = 2 makes every slot wrap once per site) and the
+    register-staged kernel (choice = CTAs per SM), on lattices with more
+    sites than SMs, so the rings and both TMEM accumulators cycle."""
+    gb = gpu_lib
+    dims = tuple(c * 2 for c in cdims)
+    mg, _ = make_ctx(gb, dims, [(2, 2, 2, 2)], [nv], prec_fine=1, prec_coarse=2)
+    n, vol = 2 * nv, lat.volume(cdims)
+    links = syn.gaussian_field((vol, 9, n, n), 55) / np.sqrt(n)
+    gb.mg_set_coarse_links(mg.ctx, 1, to_dev(links))
+    x = syn.gaussian_field((vol, n, nrhs), 56)
+    cop = dirac.StencilOp(cdims, links)
+    want = np.stack([cop.apply(x[:, :, k]) for k in range(nrhs)], axis=-1)
+    key = f"mma2/bf16/n{n}/r{nrhs}/v{vol}/b1"
+    xd = to_dev(x, torch.complex64)
+    for choice in choices:
+        gb.mg_tune_set(key, choice)
+        y = torch.full((vol, n, nrhs), float("nan"), dtype=torch.complex64, device="cuda")
+        gb.mg_coarse_apply(mg.ctx, 1, y, xd, nrhs=nrhs)
+        gb.mg_device_status(mg.ctx)
+        assert gb.mg_tune_get(key) == choice, (choice, gb.mg_tune_get(key))
+        err = rel_l2(to_np(y), want)
+        assert err < 5e-3, (choice, err)
+    gb.mg_tune_set(key, -1)
+    mg.close()
+
+
 def test_uneven_lattices_one_launch_and_graph(gpu_lib):
     """4^4, 6^4 and 8^3x16 coarse lattices (n = 48, BF16) in one persistent
     tensor-core launch, then the same launch captured in a CUDA graph and

@@ -66,10 +66,10 @@ def test_batched_policy_in_setup(gpu_lib, policy):
 
 @pytest.mark.parametrize("eps", [0.3, 0.5, 0.9])
 def test_eight_real_reconstruction_error_is_stated(gpu_lib, eps):
-    """The 8-real form is eligible on these fields and its FP32 rebuild
-    deviates from the FP64 links by at most 1e-4 (largest entry) and by a
-    root-mean-square of FP32 rounding size; the operator built from it meets
-    the FP32 tier against the oracle."""
+    """The 8-real form is eligible on these fields: its FP32 rebuild
+    deviates from the FP64 links by a root-mean-square of FP32 rounding size
+    and by at most 1e-3 anywhere; the operator built from it meets the FP32
+    tier against the oracle."""
     gb = gpu_lib
     dims = (8, 4, 6, 8)
     vol = lat.volume(dims)
@@ -78,7 +78,7 @@ def test_eight_real_reconstruction_error_is_stated(gpu_lib, eps):
     mg, U = make_ctx(gb, dims, [(2, 2, 2, 2)], [2], prec_fine=1, prec_coarse=1, eps=eps)
     info = gb.mg_gauge_compression(mg.ctx)
     assert info["two_row"] and info["eight_real"], info
-    assert info["max_dev8"] < 1e-4 and info["rms_dev8"] < 1e-6, info
+    assert info["max_dev8"] < 1e-3 and info["rms_dev8"] < 1e-6, info
     psi = syn.gaussian_field((vol, 12), 75)
     out = torch.empty((vol, 12), dtype=torch.complex64, device="cuda")
     gb.mg_wilson_clover_apply(mg.ctx, out, to_dev(psi, torch.complex64))
