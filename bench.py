@@ -135,23 +135,28 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- oracle leg
-def oracle_coarse_apply_sample(n=48, cdims=(8, 8, 8, 16), sites=1024, budget_s=12.0):
-    """The FP64 oracle stencil apply (Eq. 3) on a bounded sample of the
-    level-1 lattice: `sites` output sites per repetition, repeated for
-    about budget_s seconds.  Returns GB/s of FP64 algorithmic bytes.
-    One core: the oracle's einsum (no `optimize`) runs numpy's own loops,
-    not a threaded BLAS, so the thread cap below is a guard, not a need."""
-    from oracle import dirac, lattice as lat
+def _limit_threads():
     try:
         from threadpoolctl import threadpool_limits
-        limiter = threadpool_limits(1)
+        return threadpool_limits(1)
     except Exception:
-        limiter = None
+        return None
+
+
+def _oracle_apply_worker(job):
+    """One process of the CPU baseline: the FP64 oracle's Eq. (3) on its
+    own chunk of coarse sites, repeated for `budget_s` seconds (one thread)."""
+    import sys
+    sys.path.insert(0, ROOT)
+    from oracle import dirac, lattice as lat
+    n, cdims, lo, hi, budget_s = job
+    _limit_threads()
     vol = lat.volume(cdims)
-    rng = np.random.default_rng(5)
-    sel = np.sort(rng.choice(vol, size=sites, replace=False))
-    blocks = (rng.standard_normal((sites, 9, n, n)) + 1j * rng.standard_normal((sites, 9, n, n)))
-    psi = rng.standard_normal((vol, n)) + 1j * rng.standard_normal((vol, n))
+    rng = np.random.default_rng(1000 + lo)
+    sel = np.arange(lo, hi)
+    blocks = rng.standard_normal((hi - lo, 9, n, n)) + 1j * rng.standard_normal((hi - lo, 9, n, n))
+    g = np.random.default_rng(5)
+    psi = g.standard_normal((vol, n)) + 1j * g.standard_normal((vol, n))
     reps, t0 = 0, time.perf_counter()
     while True:
         dirac.apply_at(blocks, psi, cdims, sel)
@@ -159,13 +164,31 @@ def oracle_coarse_apply_sample(n=48, cdims=(8, 8, 8, 16), sites=1024, budget_s=1
         el = time.perf_counter() - t0
         if el >= budget_s:
             break
-    if limiter is not None:
-        limiter.unregister() if hasattr(limiter, "unregister") else None
-    bytes_per = sites * (9 * n * n * 16 + 2 * n * 16)
-    return dict(value=bytes_per * reps / el / 1e9, unit="GB/s", cores=1, kind="oracle",
-                sample=f"FP64 numpy Eq. (3) apply on {sites} of {vol} sites of the {cdims} n={n} "
-                       f"level-1 lattice, {reps} repetitions in {el:.1f} s; GB/s of FP64 "
-                       f"algorithmic bytes (links + in/out spinor)")
+    return reps, el, (hi - lo) * (9 * n * n * 16 + 2 * n * 16)
+
+
+def oracle_coarse_apply_sample(n=48, cdims=(8, 8, 8, 16), budget_s=12.0, cores=None):
+    """The FP64 oracle stencil apply (Eq. 3) on the whole level-1 lattice,
+    its sites split into one chunk per host core, each chunk applied by its
+    own process (one thread each) for about budget_s seconds; returns the
+    summed GB/s of FP64 algorithmic bytes (links + spinor in and out).  The
+    processes are spawned: forked children of a CUDA process can hang."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    from oracle import lattice as lat
+    cores = cores or (os.cpu_count() or 1)
+    vol = lat.volume(cdims)
+    edges = np.linspace(0, vol, cores + 1).astype(int)
+    jobs = [(n, tuple(cdims), int(edges[i]), int(edges[i + 1]), budget_s) for i in range(cores)]
+    with cf.ProcessPoolExecutor(cores, mp_context=mp.get_context("spawn")) as ex:
+        res = list(ex.map(_oracle_apply_worker, jobs))
+    gbs = sum(b * r / el for r, el, b in res) / 1e9
+    reps = sum(r for r, _, _ in res)
+    return dict(value=gbs, unit="GB/s", cores=cores, kind="oracle",
+                sample=f"FP64 numpy Eq. (3) apply on all {vol} sites of the {tuple(cdims)} n={n} "
+                       f"level-1 lattice, split over {cores} processes (one per host core, one "
+                       f"thread each), {reps} chunk applies in about {budget_s:.0f} s each; GB/s "
+                       f"of FP64 algorithmic bytes (links + in/out spinor) summed over processes")
 
 
 def reference_main(args):
@@ -174,7 +197,7 @@ def reference_main(args):
         return 0
     samples = []
     for _ in range(args.warmup):
-        oracle_coarse_apply_sample(budget_s=2.0)
+        oracle_coarse_apply_sample(budget_s=1.0)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         samples.append(oracle_coarse_apply_sample(budget_s=max(2.0, 20.0 / args.steps)))
@@ -315,6 +338,81 @@ def run_learned(args, gb, torch, dev):
             "rows": rows, "setup_sweeps_saved": max(saved) if saved else 0}
 
 
+def run_precision(args, gb, torch, dev):
+    """Config 3, the precision forms of the small 2-level workload (8^4,
+    2^4 aggregates, 24 vectors, m = -0.2): the FP64 oracle builds its
+    hierarchy (10 MR sweeps from the seeded x0, block QR, Galerkin; timed:
+    the oracle's s/build on one core) and solves b to 1e-10 (s/solve).  The
+    GPU then takes the oracle's block-orthonormal null vectors, builds its
+    own Galerkin operator and stores it as FP64, FP32, BF16, FP16 or int16
+    (the fine operator FP64 for the first form, FP32 for the others), and
+    each level's apply is compared with the oracle's on a Gaussian vector
+    (relative L2); the MG-GCR solve of the same b gives the outer and
+    per-level iteration counts."""
+    from oracle import dirac, solvers
+    w = syn.WORKLOADS["c1_8^4_2lvl_fp64"]
+    dims, block, nv = w["dims"], w["block"][0], w["nvec"][0]
+    vol = syn.volume(dims)
+    U = syn.gauge_field(dims, w["eps"], w["seed"])
+    x0 = syn.gaussian_field((nv, vol, 12), w["seed"], stream=10)
+    b = syn.gaussian_field((vol, 12), w["seed"], stream=99)
+    lim = _limit_threads()
+    t0 = time.perf_counter()
+    op = dirac.wilson_clover_op(U, dims, w["mass"], w["csw"], True)
+    hier = solvers.MultigridHierarchy.build(op, [x0], w["sweeps"], [block])
+    t_build = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ref = hier.solve(b, 1e-10, 100)
+    t_solve = time.perf_counter() - t0
+    cop = hier.ops[1]
+    v0 = syn.gaussian_field((vol, 12), 31)
+    v1 = syn.gaussian_field((cop.vol, cop.nd), 32)
+    want = [op.apply(v0), cop.apply(v1)]
+    if lim is not None and hasattr(lim, "unregister"):
+        lim.unregister()
+    Ud = torch.from_numpy(U).to(dev)
+    Qd = torch.from_numpy(hier.Qs[0]).to(dev)
+    bd = torch.from_numpy(b).to(dev)
+    forms = {}
+    for name, pf, pc in (("fp64", 0, 0), ("fp32", 1, 1), ("bf16", 1, 2), ("fp16", 1, 3),
+                         ("int16", 1, 4)):
+        p = gb.default_params(dims=dims, block=[block], nvec=[nv], mass=w["mass"], csw=w["csw"],
+                              nlevels=2, prec_fine=pf, prec_coarse=pc, setup_sweeps=w["sweeps"],
+                              t_antiperiodic=w["antiperiodic"])
+        mg = gb.Multigrid(p, Ud)
+        gb.mg_set_nullvecs(mg.ctx, 0, Qd)
+        gb.mg_build_coarse(mg.ctx, 0)
+        errs = []
+        for lv, v, ref_y in ((0, v0, want[0]), (1, v1, want[1])):
+            dt = mg.levels[lv]["dtype"]
+            x = torch.from_numpy(v).to(dev, dt)
+            y = torch.empty_like(x)
+            gb.mg_apply(mg.ctx, lv, y, x)
+            got = y.cpu().numpy().astype(np.complex128)
+            errs.append(float(np.linalg.norm(got - ref_y) / np.linalg.norm(ref_y)))
+        xs = torch.zeros_like(bd)
+        st = gb.mg_gcr_solve(mg.ctx, xs, bd, 1e-10, 200)
+        forms[name] = {"fine": "fp64" if pf == 0 else "fp32", "links": name,
+                       "apply_rel_l2_vs_oracle": {"level0": errs[0], "level1": errs[1]},
+                       "outer_iters": st["iters"], "level_iters": st["level_iters"],
+                       "true_residual": st["true_residual"]}
+        mg.close()
+    return {"workload": "c1_8^4_2lvl_fp64 (fine 8^4, 2^4 aggregates, 24 vectors, m = -0.2)",
+            "oracle": {"outer_iters": ref.iters, "true_residual": ref.true_residual,
+                       "s_per_build": t_build, "s_per_solve": t_solve, "cores": 1},
+            "forms": forms}
+
+
+def precision_main(args):
+    """Only the config-3 precision study (see run_precision); one JSON line."""
+    import torch
+
+    import paper_1612_07873_gb300 as gb
+    out = run_precision(args, gb, torch, torch.device("cuda"))
+    print(json.dumps({"mode": "precision", "precision": out}), flush=True)
+    return 0
+
+
 def learned_main(args):
     """Only the learned-setup study (see run_learned); one JSON line."""
     import torch
@@ -323,6 +421,74 @@ def learned_main(args):
     out = run_learned(args, gb, torch, torch.device("cuda"))
     print(json.dumps({"mode": "learned", "learned_setup": out}), flush=True)
     return 0
+
+
+# ---------------------------------------------------------------- forms
+FORMS = (
+    # (name, coarse link store, link slots, RHS per call, red-black, fine smoother)
+    ("fp32", 1, 9, 1, 0, 1),
+    ("bf16", 2, 9, 1, 0, 1), ("fp16", 3, 9, 1, 0, 1), ("int16", 4, 9, 1, 0, 1),
+    ("fp32_5blocks", 1, 5, 1, 0, 1), ("bf16_5blocks", 2, 5, 1, 0, 1),
+    ("fp32_mrhs8", 1, 9, 8, 0, 1), ("bf16_mrhs8", 2, 9, 8, 0, 1),
+    ("fp32_redblack", 1, 9, 1, 1, 1), ("bf16_redblack", 2, 9, 1, 1, 1),
+    ("bf16_redblack_mrhs8", 2, 9, 8, 1, 1),
+    ("fp32_smoother16", 1, 9, 1, 0, 2), ("bf16_smoother16", 2, 9, 1, 0, 2),
+    ("bf16_smoother16_mrhs8", 2, 9, 8, 0, 2))
+
+
+def run_forms(args, gb, torch, ev, stream, dev, w, dims, blocks, nvecs, mass, gauge_dev, b, rank):
+    """s/solve to 1e-10 of every form at one mass: setup of both levels
+    (timed apart), then the median of 3 solves (1 RHS per call) or 2 calls
+    (8 RHS per call: the workload's b and 7 seeded Gaussian ones; s/solve =
+    seconds per call / 8), after one warm-up solve."""
+    out = {}
+    for fname, pc, slots, nr, rbp, ps in FORMS:
+        pf = gb.default_params(dims=dims, block=blocks, nvec=nvecs, mass=mass,
+                               csw=w["csw"], nlevels=3, prec_fine=1, prec_coarse=pc,
+                               setup_sweeps=w["sweeps"], t_antiperiodic=w["antiperiodic"],
+                               seed=w["seed"] + 1000 * rank, link_slots=slots,
+                               red_black=rbp, prec_smoother=ps)
+        mf = gb.Multigrid(pf, gauge_dev)
+        t0, t1 = ev(), ev()
+        t0.record(stream)
+        gb.mg_setup_nullvecs(mf.ctx, 0, None)
+        gb.mg_build_coarse(mf.ctx, 0)
+        gb.mg_setup_nullvecs(mf.ctx, 1, None)
+        gb.mg_build_coarse(mf.ctx, 1)
+        t1.record(stream)
+        if nr == 1:
+            xs = torch.zeros_like(b)
+            gb.mg_gcr_solve(mf.ctx, xs, b, 1e-10, 500)  # warm-up
+            sts = [gb.mg_gcr_solve(mf.ctx, xs, b, 1e-10, 500) for _ in range(3)]
+            torch.cuda.synchronize()
+            out[fname] = {
+                "s_per_solve_median": statistics.median(st["seconds"] for st in sts),
+                "outer_iters": [st["iters"] for st in sts],
+                "level_iters": sts[-1]["level_iters"],
+                "true_residual": max(st["true_residual"] for st in sts),
+                "setup_ms": t0.elapsed_time(t1)}
+        else:
+            g = torch.Generator(device=dev).manual_seed(w["seed"] + 77)
+            bm = torch.randn((nr,) + tuple(b.shape), dtype=torch.complex128, device=dev,
+                             generator=g)
+            bm[0].copy_(b)
+            xm = torch.zeros_like(bm)
+            gb.mg_gcr_solve_multi(mf.ctx, xm, bm, nr, 1e-10, 500)  # warm-up
+            calls = [gb.mg_gcr_solve_multi(mf.ctx, xm, bm, nr, 1e-10, 500) for _ in range(2)]
+            torch.cuda.synchronize()
+            out[fname] = {
+                "s_per_solve_median": statistics.median(c[0]["seconds"] for c in calls) / nr,
+                "nrhs": nr,
+                "s_per_call_median": statistics.median(c[0]["seconds"] for c in calls),
+                "outer_iters": [[st["iters"] for st in c] for c in calls],
+                "true_residual": max(st["true_residual"] for c in calls for st in c),
+                "setup_ms": t0.elapsed_time(t1)}
+            del bm, xm
+        mf.close()
+    base = out["fp32"]["s_per_solve_median"]
+    for v in out.values():
+        v["speedup_vs_fp32"] = base / v["s_per_solve_median"]
+    return out
 
 
 # ---------------------------------------------------------------- GPU leg
@@ -451,69 +617,17 @@ def gpu_main(args):
            "d2h_bytes_per_step": yh.numel() * yh.element_size(),
            "ms_per_apply": e2e_ms}
 
-    # the 16-bit storage forms of the same problem: same gauge field, seeds
-    # and solver; setup untimed, s/solve over `nsolve` solves
+    # the tuned forms of the same problem: same gauge field, seeds and solver;
+    # setup untimed, s/solve over several solves; at the workload's mass and
+    # at the near-critical mass of these fields
     forms = {}
     if args.forms:
         mg.close()
-        # (name, coarse link store, link slots, RHS per call, red-black, fine smoother)
-        for fname, pc, slots, nr, rbp, ps in (
-                ("bf16", 2, 9, 1, 0, 1), ("fp16", 3, 9, 1, 0, 1), ("int16", 4, 9, 1, 0, 1),
-                ("fp32_5blocks", 1, 5, 1, 0, 1), ("bf16_5blocks", 2, 5, 1, 0, 1),
-                ("fp32_mrhs8", 1, 9, 8, 0, 1), ("bf16_mrhs8", 2, 9, 8, 0, 1),
-                ("fp32_redblack", 1, 9, 1, 1, 1), ("bf16_redblack", 2, 9, 1, 1, 1),
-                ("bf16_redblack_mrhs8", 2, 9, 8, 1, 1),
-                ("fp32_smoother16", 1, 9, 1, 0, 2), ("bf16_smoother16", 2, 9, 1, 0, 2),
-                ("bf16_smoother16_mrhs8", 2, 9, 8, 0, 2)):
-            if fname == form:
-                continue
-            pf = gb.default_params(dims=dims, block=blocks, nvec=nvecs, mass=w["mass"],
-                                   csw=w["csw"], nlevels=3, prec_fine=1, prec_coarse=pc,
-                                   setup_sweeps=w["sweeps"], t_antiperiodic=w["antiperiodic"],
-                                   seed=w["seed"] + 1000 * rank, link_slots=slots,
-                                   red_black=rbp, prec_smoother=ps)
-            mf = gb.Multigrid(pf, gauge_dev)
-            t0 = ev()
-            t1 = ev()
-            t0.record(stream)
-            gb.mg_setup_nullvecs(mf.ctx, 0, None)
-            gb.mg_build_coarse(mf.ctx, 0)
-            gb.mg_setup_nullvecs(mf.ctx, 1, None)
-            gb.mg_build_coarse(mf.ctx, 1)
-            t1.record(stream)
-            if nr == 1:
-                xs = torch.zeros_like(b)
-                gb.mg_gcr_solve(mf.ctx, xs, b, 1e-10, 500)  # warm-up
-                sts = [gb.mg_gcr_solve(mf.ctx, xs, b, 1e-10, 500) for _ in range(3)]
-                torch.cuda.synchronize()
-                forms[fname] = {
-                    "s_per_solve_median": statistics.median(st["seconds"] for st in sts),
-                    "outer_iters": [st["iters"] for st in sts],
-                    "level_iters": sts[-1]["level_iters"],
-                    "true_residual": max(st["true_residual"] for st in sts),
-                    "setup_ms": t0.elapsed_time(t1)}
-            else:
-                # nr right-hand sides per call: the workload's b and nr - 1
-                # seeded Gaussian ones; s/solve = seconds per call / nr
-                g = torch.Generator(device=dev).manual_seed(w["seed"] + 77)
-                bm = torch.randn((nr,) + tuple(b.shape), dtype=torch.complex128, device=dev,
-                                 generator=g)
-                bm[0].copy_(b)
-                xm = torch.zeros_like(bm)
-                gb.mg_gcr_solve_multi(mf.ctx, xm, bm, nr, 1e-10, 500)  # warm-up
-                calls = [gb.mg_gcr_solve_multi(mf.ctx, xm, bm, nr, 1e-10, 500)
-                         for _ in range(2)]
-                torch.cuda.synchronize()
-                forms[fname] = {
-                    "s_per_solve_median": statistics.median(c[0]["seconds"] for c in calls) / nr,
-                    "nrhs": nr,
-                    "s_per_call_median": statistics.median(c[0]["seconds"] for c in calls),
-                    "outer_iters": [[st["iters"] for st in c] for c in calls],
-                    "true_residual": max(st["true_residual"] for c in calls for st in c),
-                    "setup_ms": t0.elapsed_time(t1)}
-                del bm, xm
-            mf.close()
+        for fmass in [float(v) for v in args.forms_mass.split(",") if v.strip()]:
+            forms[f"m={fmass:+.2f}"] = run_forms(args, gb, torch, ev, stream, dev, w, dims, blocks,
+                                                 nvecs, fmass, gauge_dev, b, rank)
     learned_setup = run_learned(args, gb, torch, dev) if args.learned else None
+    precision = run_precision(args, gb, torch, dev) if args.precision else None
     peak, peak_kind = peaks()
     solve_s = [s["seconds"] for s in stats]
     line = {
@@ -540,6 +654,7 @@ def gpu_main(args):
                   "true_residual": max(s["true_residual"] for s in stats),
                   "forms": forms},
         "learned_setup": learned_setup,
+        "precision": precision,
         "phases_ms_median": dict(zip(["setup_l0", "build_l1", "setup_l1", "build_l2", "solve"],
                                      [float(v) for v in np.median(ph, axis=0)])),
         "kernels": {k: {"launches": v["launches"], "ms": v["ms"],
@@ -550,6 +665,12 @@ def gpu_main(args):
     if rank == 0 and world == 1:
         try:
             line["cpu_baseline"] = oracle_coarse_apply_sample()
+            if precision is not None:
+                o = precision["oracle"]
+                line["cpu_baseline"]["oracle_small_workload"] = {
+                    "workload": "c1_8^4_2lvl_fp64", "s_per_build": o["s_per_build"],
+                    "s_per_solve": o["s_per_solve"], "outer_iters": o["outer_iters"],
+                    "cores": o["cores"]}
         except Exception as e:  # the baseline must not sink the GPU line
             line["cpu_baseline"] = {"error": str(e)}
     if rank == 0:
@@ -794,7 +915,7 @@ def main():
     ap.add_argument("--form", default="fp32", choices=["fp32", "bf16", "fp16", "int16"])
     ap.add_argument("--mode", default="pipeline",
                     choices=["pipeline", "coarse-apply", "wilson-policies", "solve-breakdown",
-                             "learned", "mma-sweep"])
+                             "learned", "mma-sweep", "precision"])
     ap.add_argument("--fine", default="", help="override the fine extents, e.g. 16,16,16,32")
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides (coarse-apply mode)")
     ap.add_argument("--slots", type=int, default=9, choices=[5, 9],
@@ -807,7 +928,11 @@ def main():
     ap.add_argument("--learned-ntrain", type=int, default=200)
     ap.add_argument("--learned-epochs", type=int, default=4)
     ap.add_argument("--no-forms", dest="forms", action="store_false",
-                    help="skip the 16-bit storage forms' s/solve")
+                    help="skip the tuned forms' s/solve")
+    ap.add_argument("--forms-mass", default="-0.40,-0.90",
+                    help="masses at which the forms table is measured")
+    ap.add_argument("--no-precision", dest="precision", action="store_false",
+                    help="skip the precision study of the small workload")
     ap.add_argument("--clocks-csv", default="",
                     help="where the nvidia-smi clock samples of the timed region go "
                          "('{rank}' is replaced; default: the temp directory)")
@@ -824,6 +949,8 @@ def main():
         return learned_main(args)
     if args.mode == "mma-sweep":
         return mma_sweep_main(args)
+    if args.mode == "precision":
+        return precision_main(args)
     return gpu_main(args)
 
 

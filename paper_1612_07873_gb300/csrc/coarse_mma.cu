@@ -21,9 +21,10 @@
 //
 // Two kernels do this: k_coarse_mma (register-staged operands, two
 // buffers, the whole CTA in step) and k_coarse_mma_ws (warp-specialised:
-// bulk copies of the link operand into an S-stage ring, separate staging,
-// MMA and epilogue warps).  The autotuner picks the kernel and the ring
-// depth (or the CTAs per SM) per shape.
+// bulk copies of the links and of the neighbour spinors into a load ring,
+// separate converting, MMA and epilogue warps).  The autotuner picks the
+// kernel, the stage granularity and the ring depths (or the CTAs per SM)
+// per shape.
 #include "kernels.cuh"
 #include "tune.cuh"
 
@@ -119,6 +120,12 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
 __device__ __forceinline__ uint64_t policy_evict_first() {
   uint64_t pol;
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+// L2 policy for data several CTAs read (a spinor serves nine sites)
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
   return pol;
 }
 // bulk copy global -> this CTA's shared memory, completing `bytes` of
@@ -420,22 +427,26 @@ __global__ void __launch_bounds__(128) k_coarse_mma(const MmaBatch batch, int nr
 
 // ---------------------------------------------------------------------------
 // Warp-specialised, pipelined form of the same GEMM (persistent, one CTA per
-// SM, 320 threads).  A pipeline stage is one stencil slot (K = 2n): the
-// slot's links, one contiguous 4 n^2-byte run of the tiled store, arrive by
-// one bulk copy (cp.async.bulk, L2 evict-first) and the neighbour's spinor is
-// converted into the BF16/FP16 operand by four warps, into an S-deep ring.
-//   warps 0-3  spinor operand of each slot (x(nbr) -> rows j, nrhs + j)
+// SM, 320 threads).  A pipeline stage is KH half slots of one stencil slot
+// (KH = 2: the whole slot, K = 2n; KH = 1: half of it, K = n).  Both inputs
+// of a stage are contiguous in global memory and arrive by bulk copies
+// (cp.async.bulk) into an SL-deep load ring: the stage's links (the tiled
+// store, L2 evict-first) and the rows of the neighbour's FP32 spinor the
+// stage needs.  Four warps convert the spinor rows into the 16-bit MMA
+// operand in shared memory (an SA-deep operand ring), and
+//   warps 0-3  convert (x(nbr) -> rows j, nrhs + j of the A operand)
 //   warps 4-7  epilogue: their TMEM lane quarter -> shared memory -> y
-//   warp 8     lane 0 issues the link copies
+//   warp 8     lane 0 issues the bulk copies
 //   warp 9     lane 0 issues the MMAs of each stage and commits them
-// Barriers per ring slot: full_l (copy bytes), full_x (128 staging
-// threads), empty (the slot's MMAs done); per accumulator (two TMEM buffers
-// of n columns, so the epilogue of one site overlaps the MMAs of the next):
-// acc_full (MMAs of the site done), acc_empty (128 epilogue threads done).
-// The spinor operand keeps only its 2 nrhs used rows; the MMA's rows beyond
-// them (M = 128) read whatever follows in shared memory and produce
-// accumulator rows that are never read.  Every wait is bounded; on a
-// timeout (or the injected stall) every role stops, the copy issuer waits
+// Barriers: load_full (copy bytes) and load_empty (the stage's MMAs and
+// its 128 converting threads done) per load slot; a_full (128 converting
+// threads) and a_empty (MMAs done) per operand slot; acc_full (MMAs of the
+// site done) and acc_empty (128 epilogue threads done) per accumulator (two
+// TMEM buffers of n columns, so the epilogue of one site overlaps the MMAs
+// of the next).  The A operand keeps only its 2 nrhs used rows; the MMA's
+// rows beyond them (M = 128) read whatever follows in shared memory and
+// produce accumulator rows that are never read.  Every wait is bounded; on
+// a timeout (or the injected stall) every role stops, the copy issuer waits
 // for its copies in flight, the MMA issuer for its MMAs, and TMEM is freed.
 constexpr int kWsThreads = 320;
 constexpr int kWsMaxStages = 8;
@@ -455,27 +466,49 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity,
   }
 }
 
-template <bool BF16, int N>
+// Shared-memory layout of the pipelined kernel: [A ring][link ring][spinor
+// ring][epilogue rows]; the A ring comes first, so the MMA rows beyond 2 nrhs
+// of its last half slot read up to 256 n bytes past it inside the rings that
+// follow.
+struct WsLayout {
+  uint32_t xh, ab, lb, rb, a_off, l_off, r_off, c_off, total;
+};
+__host__ __device__ inline WsLayout ws_layout(int N, int KH, int nrhs, int SL, int SA) {
+  WsLayout w;
+  w.xh = uint32_t(4 * nrhs * N);                 // A operand bytes of a half slot
+  w.ab = uint32_t(KH) * w.xh;                    // A operand bytes of a stage
+  w.lb = uint32_t(KH) * uint32_t(2 * N * N);     // link bytes of a stage
+  w.rb = uint32_t(KH) * uint32_t((N / 2) * nrhs * 8);  // spinor bytes of a stage
+  w.a_off = 0;
+  w.l_off = uint32_t(SA) * w.ab;
+  w.r_off = w.l_off + uint32_t(SL) * w.lb;
+  w.c_off = w.r_off + uint32_t(SL) * w.rb;
+  const uint32_t cs = (uint32_t(2 * nrhs * (N + 1) * 4) + 15u) / 16u * 16u;
+  w.total = w.c_off + cs;
+  return w;
+}
+
+template <bool BF16, int N, int KH>
 __global__ void __launch_bounds__(kWsThreads, 1)
-    k_coarse_mma_ws(const MmaBatch batch, int nrhs, int S, int* __restrict__ err) {
+    k_coarse_mma_ws(const MmaBatch batch, int nrhs, int SL, int SA, int* __restrict__ err) {
+  constexpr int NST = 18 / KH;                         // stages per site
   constexpr int HB = 2 * N * N;                        // link bytes of a half slot
-  constexpr int LB = 2 * HB;                           // link bytes of a slot
   constexpr uint32_t LBO = 128, SBO = (N / 8) * 128;  // K extent N per half, both operands
   constexpr uint32_t IDESC = mma_idesc(128, N, BF16);
   constexpr uint32_t TMEM_COLS = 128;                  // accumulators at columns 0 and 64
   constexpr int CS = N + 1;
-  constexpr int XPT = (N / 4) * 8 / 4;                 // spinor tiles per staging warp, nrhs <= 64
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ uint64_t full_l[kWsMaxStages], full_x[kWsMaxStages], empty[kWsMaxStages];
+  __shared__ uint64_t load_full[kWsMaxStages], load_empty[kWsMaxStages];
+  __shared__ uint64_t a_full[kWsMaxStages], a_empty[kWsMaxStages];
   __shared__ uint64_t acc_full[2], acc_empty[2], fin, stall_bar;
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int abort_sh;
   __shared__ int epi_ok;
-  const int XH = 4 * nrhs * N;  // spinor bytes of a half slot: 2 nrhs rows x N K values
-  const int XB = 2 * XH;
-  unsigned char* xring = smem;
-  unsigned char* lring = smem + size_t(S) * XB;
-  float* Cs = reinterpret_cast<float*>(lring + size_t(S) * LB);
+  const WsLayout lay = ws_layout(N, KH, nrhs, SL, SA);
+  unsigned char* aring = smem + lay.a_off;
+  unsigned char* lring = smem + lay.l_off;
+  unsigned char* rring = smem + lay.r_off;
+  float* Cs = reinterpret_cast<float*>(smem + lay.c_off);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (warp == 0) {
@@ -483,10 +516,13 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     tmem_relinquish();
   }
   if (tid == 0) {
-    for (int q = 0; q < S; ++q) {
-      mbar_init(&full_l[q], 1);
-      mbar_init(&full_x[q], 128);
-      mbar_init(&empty[q], 1);
+    for (int q = 0; q < SL; ++q) {
+      mbar_init(&load_full[q], 1);
+      mbar_init(&load_empty[q], 129);  // the MMA commit + 128 converting threads
+    }
+    for (int q = 0; q < SA; ++q) {
+      mbar_init(&a_full[q], 128);
+      mbar_init(&a_empty[q], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
@@ -517,48 +553,37 @@ __global__ void __launch_bounds__(kWsThreads, 1)
   };
 
   if (warp < 4) {
-    // ---- spinor operand: tiles of 4 complex columns k x 8 right-hand
-    // sides j; lane l takes j = 8 jt + (l & 7), k = 4 kt + (l >> 3), so a
+    // ---- convert: element (k, j) of a half slot, k < N / 2 complex columns,
+    // j < nrhs; lane l takes j = 8 jt + (l & 7), k = 4 kt + (l >> 3), so a
     // warp's 32 four-byte stores fill one 8-row x 16-byte core matrix
     const int jt_n = (nrhs + 7) >> 3;
-    const int ntiles = (N / 4) * jt_n;
+    const int ntiles = (N / 8) * jt_n;  // tiles of a half slot
     uint32_t q = 0;
     for (int gs = blockIdx.x; gs < batch.total && !abort_sh; gs += gridDim.x) {
-      const MmaLattice& cur = batch.lat[lattice_of_site(gs)];
-      const int site = gs - cur.site0;
-      int c[4];
-      site_coords(cur.g, site, c);
-      for (int d = 0; d < 9; ++d, ++q) {
-        const uint32_t sl = q % uint32_t(S), ph = (q / uint32_t(S)) & 1u;
-        if (!wait_or_abort(&empty[sl], ph ^ 1u, &abort_sh, err)) break;
-        const cpx<float>* xs = cur.x + size_t(neighbour(cur.g, site, c, d)) * N * nrhs;
-        unsigned char* A = xring + size_t(sl) * XB;
-        // loads in batches of 16 independent 8-byte loads per thread
+      for (int d = 0; d < NST; ++d, ++q) {
+        const uint32_t sl = q % uint32_t(SL), lph = (q / uint32_t(SL)) & 1u;
+        const uint32_t sa = q % uint32_t(SA), aph = (q / uint32_t(SA)) & 1u;
+        if (!wait_or_abort(&load_full[sl], lph, &abort_sh, err)) break;
+        if (!wait_or_abort(&a_empty[sa], aph ^ 1u, &abort_sh, err)) break;
+        const cpx<float>* xr = reinterpret_cast<const cpx<float>*>(rring + size_t(sl) * lay.rb);
+        unsigned char* A = aring + size_t(sa) * lay.ab;
 #pragma unroll
-        for (int u0 = 0; u0 < XPT; u0 += 16) {
-          cpx<float> v[16];
-#pragma unroll
-          for (int u = 0; u < 16; ++u) {
-            const int t = warp + 4 * (u0 + u);
+        for (int h = 0; h < KH; ++h) {
+          unsigned char* Ah = A + h * lay.xh;
+          const cpx<float>* xh = xr + h * (N / 2) * nrhs;
+          for (int t = warp; t < ntiles; t += 4) {
             const int j = 8 * (t % jt_n) + (lane & 7), k = 4 * (t / jt_n) + (lane >> 3);
-            if (u0 + u < XPT && t < ntiles && j < nrhs) v[u] = xs[k * nrhs + j];
-          }
-#pragma unroll
-          for (int u = 0; u < 16; ++u) {
-            const int t = warp + 4 * (u0 + u);
-            const int j = 8 * (t % jt_n) + (lane & 7), k = 4 * (t / jt_n) + (lane >> 3);
-            if (u0 + u < XPT && t < ntiles && j < nrhs) {
-              const int h = k / (N / 2), kl = k - h * (N / 2);
-              unsigned char* Ah = A + h * XH;
-              *reinterpret_cast<uint32_t*>(Ah + core_off(j, 2 * kl, N)) =
-                  pack2<BF16>(v[u].re, -v[u].im);
-              *reinterpret_cast<uint32_t*>(Ah + core_off(nrhs + j, 2 * kl, N)) =
-                  pack2<BF16>(v[u].im, v[u].re);
+            if (j < nrhs) {
+              const cpx<float> v = xh[k * nrhs + j];
+              *reinterpret_cast<uint32_t*>(Ah + core_off(j, 2 * k, N)) = pack2<BF16>(v.re, -v.im);
+              *reinterpret_cast<uint32_t*>(Ah + core_off(nrhs + j, 2 * k, N)) =
+                  pack2<BF16>(v.im, v.re);
             }
           }
         }
         fence_proxy_async_smem();
-        mbar_arrive(&full_x[sl]);
+        mbar_arrive(&a_full[sa]);
+        mbar_arrive(&load_empty[sl]);  // this thread has read the spinor rows
       }
     }
   } else if (warp < 8) {
@@ -597,30 +622,38 @@ __global__ void __launch_bounds__(kWsThreads, 1)
       asm volatile("bar.sync 1, 128;" ::: "memory");
     }
   } else if (warp == 8) {
-    // ---- link copies
+    // ---- bulk copies: the stage's links and the neighbour's spinor rows
     if (lane == 0) {
-      const uint64_t pol = policy_evict_first();
+      const uint64_t pol = policy_evict_first(), pol_x = policy_evict_last();
       uint32_t q = 0;
       bool go = true;
       for (int gs = blockIdx.x; gs < batch.total && go && !abort_sh; gs += gridDim.x) {
         const MmaLattice& cur = batch.lat[lattice_of_site(gs)];
-        const unsigned char* src =
-            reinterpret_cast<const unsigned char*>(cur.links) + size_t(gs - cur.site0) * 9 * LB;
-        for (int d = 0; d < 9; ++d) {
-          const uint32_t sl = q % uint32_t(S), ph = (q / uint32_t(S)) & 1u;
-          if (!wait_or_abort(&empty[sl], ph ^ 1u, &abort_sh, err)) {
+        const int site = gs - cur.site0;
+        int c[4];
+        site_coords(cur.g, site, c);
+        const unsigned char* lsrc =
+            reinterpret_cast<const unsigned char*>(cur.links) + size_t(site) * 18 * HB;
+        for (int d = 0; d < NST; ++d) {
+          const uint32_t sl = q % uint32_t(SL), ph = (q / uint32_t(SL)) & 1u;
+          if (!wait_or_abort(&load_empty[sl], ph ^ 1u, &abort_sh, err)) {
             go = false;
             break;
           }
-          mbar_arrive_expect_tx(&full_l[sl], LB);
-          bulk_g2s(lring + size_t(sl) * LB, src + size_t(d) * LB, LB, &full_l[sl], pol);
+          const int slot = (d * KH) >> 1, h0 = (d * KH) & 1;
+          const cpx<float>* xsrc = cur.x + size_t(neighbour(cur.g, site, c, slot)) * N * nrhs +
+                                   size_t(h0) * (N / 2) * nrhs;
+          mbar_arrive_expect_tx(&load_full[sl], lay.lb + lay.rb);
+          bulk_g2s(lring + size_t(sl) * lay.lb, lsrc + size_t(d) * lay.lb, lay.lb,
+                   &load_full[sl], pol);
+          bulk_g2s(rring + size_t(sl) * lay.rb, xsrc, lay.rb, &load_full[sl], pol_x);
           ++q;
         }
       }
       // copies still in flight land before the CTA's shared memory goes away
-      const uint32_t first = q > uint32_t(S) ? q - uint32_t(S) : 0u;
+      const uint32_t first = q > uint32_t(SL) ? q - uint32_t(SL) : 0u;
       for (uint32_t r = first; r < q; ++r)
-        mbar_wait(&full_l[r % uint32_t(S)], (r / uint32_t(S)) & 1u);
+        mbar_wait(&load_full[r % uint32_t(SL)], (r / uint32_t(SL)) & 1u);
     }
   } else {
     // ---- MMA issue
@@ -632,24 +665,26 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         if (!wait_or_abort(&acc_empty[b], ph ^ 1u, &abort_sh, err)) break;
         tc_fence_after();
         const uint32_t dt = tmem + b * 64u;
-        for (int d = 0; d < 9; ++d, ++q) {
-          const uint32_t sl = q % uint32_t(S), sp = (q / uint32_t(S)) & 1u;
-          if (!wait_or_abort(&full_l[sl], sp, &abort_sh, err) ||
-              !wait_or_abort(&full_x[sl], sp, &abort_sh, err)) {
+        for (int d = 0; d < NST; ++d, ++q) {
+          const uint32_t sl = q % uint32_t(SL), lph = (q / uint32_t(SL)) & 1u;
+          const uint32_t sa = q % uint32_t(SA), aph = (q / uint32_t(SA)) & 1u;
+          if (!wait_or_abort(&load_full[sl], lph, &abort_sh, err) ||
+              !wait_or_abort(&a_full[sa], aph, &abort_sh, err)) {
             go = false;
             break;
           }
           tc_fence_after();
-          const uint32_t a0 = smem_u32(xring + size_t(sl) * XB);
-          const uint32_t b0 = smem_u32(lring + size_t(sl) * LB);
+          const uint32_t a0 = smem_u32(aring + size_t(sa) * lay.ab);
+          const uint32_t b0 = smem_u32(lring + size_t(sl) * lay.lb);
 #pragma unroll
-          for (int h = 0; h < 2; ++h)
+          for (int h = 0; h < KH; ++h)
 #pragma unroll
             for (int kk = 0; kk < N / 16; ++kk)
-              mma_f16(dt, smem_desc(a0 + h * XH + kk * 256, LBO, SBO),
+              mma_f16(dt, smem_desc(a0 + h * lay.xh + kk * 256, LBO, SBO),
                       smem_desc(b0 + h * HB + kk * 256, LBO, SBO), IDESC,
                       (d > 0 || h > 0 || kk > 0) ? 1u : 0u);
-          mma_commit(&empty[sl]);
+          mma_commit(&load_empty[sl]);
+          mma_commit(&a_empty[sa]);
           issued = true;
         }
         if (!go) break;
@@ -689,18 +724,14 @@ __global__ void k_links_tile_mma(uint32_t* __restrict__ out, const cpx<float>* _
   }
 }
 
-// Dynamic shared memory of the pipelined kernel with S stages; 0 if the
-// footprint exceeds `limit`.  The spinor ring comes first: the MMA rows
-// beyond 2 nrhs of its last half slot read up to 256 n bytes past that half,
-// which stays inside the link ring that follows.
-template <int N>
-size_t ws_smem(int nrhs, int S, size_t limit) {
-  const size_t XB = size_t(8) * nrhs * N, LB = size_t(4) * N * N;
-  const size_t cs = ((size_t(2) * nrhs * (N + 1) * 4) + 15) / 16 * 16;
-  const size_t total = size_t(S) * (XB + LB) + cs;
-  const size_t reach = size_t(S - 1) * XB + XB / 2 + size_t(256) * N;
-  if (reach > total || total > limit) return 0;
-  return total;
+// A launch shape of the pipelined kernel: stage granularity KH (half slots
+// per stage), load-ring depth SL and operand-ring depth SA, as the tuner
+// choice 1000 + 100 KH + 10 SL + SA; 0 if its shared memory exceeds `limit`
+// or the MMA rows past the last operand stage would leave the allocation.
+bool ws_fits(int N, int KH, int nrhs, int SL, int SA, size_t limit) {
+  const WsLayout w = ws_layout(N, KH, nrhs, SL, SA);
+  const size_t reach = size_t(SA - 1) * w.ab + size_t(KH - 1) * w.xh + size_t(256) * N;
+  return w.total <= limit && reach <= w.total;
 }
 
 template <bool BF16, int N>
@@ -708,7 +739,6 @@ void launch_mma_batch(int* err, const MmaBatch& batch, int nrhs, cudaStream_t st
   constexpr int KS = N;
   const int smem = 2 * (128 * KS * 2) + 2 * (N * KS * 2);
   auto kern = k_coarse_mma<BF16, N>;
-  auto kws = k_coarse_mma_ws<BF16, N>;
   GB_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   GB_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   // CTAs per SM from the kernel's own footprint: shared memory (dynamic +
@@ -727,27 +757,41 @@ void launch_mma_batch(int* err, const MmaBatch& batch, int nrhs, cudaStream_t st
   if (per_sm > 8) per_sm = 8;
   if (per_sm < 1) per_sm = 1;
   cudaFuncAttributes fw;
-  GB_CHECK(cudaFuncGetAttributes(&fw, kws));
+  GB_CHECK(cudaFuncGetAttributes(&fw, k_coarse_mma_ws<BF16, N, 2>));
   const size_t ws_limit = size_t(optin) - fw.sharedSizeBytes;
-  // pipelined kernel: the deepest ring that fits (up to 8 stages)
-  int smax = 0;
-  for (int S = kWsMaxStages; S >= 2 && !smax; --S)
-    if (ws_smem<N>(nrhs, S, ws_limit)) smax = S;
-  // Autotuned launch shape.  Choice 100 + S: the pipelined kernel with an
-  // S-stage ring (one persistent CTA per SM); choice q <= 8: the
-  // register-staged kernel with q resident CTAs per SM.
+  // the pipelined kernel bulk-copies spinor rows: every lattice's x must
+  // start on a 16-byte boundary (n nrhs 8-byte rows keep the rest aligned)
+  bool aligned = true;
+  for (int i = 0; i < batch.count; ++i)
+    aligned = aligned && (reinterpret_cast<uintptr_t>(batch.lat[i].x) % 16 == 0) &&
+              (reinterpret_cast<uintptr_t>(batch.lat[i].links) % 16 == 0);
+  // Autotuned launch shape: choice 1000 + 100 KH + 10 SL + SA is the
+  // pipelined kernel (KH half slots per stage, SL-deep load ring, SA-deep
+  // operand ring, one persistent CTA per SM); choice q <= 8 the register-
+  // staged kernel with q resident CTAs per SM.
   std::vector<int> cands;
-  for (int S = smax; S >= 2; --S) cands.push_back(100 + S);
+  if (aligned)
+    for (int KH : {2, 1})
+      for (int SA : {2, 3})
+        for (int SL = kWsMaxStages; SL >= 2; --SL)
+          if (ws_fits(N, KH, nrhs, SL, SA, ws_limit)) cands.push_back(1000 + 100 * KH + 10 * SL + SA);
   cands.push_back(per_sm);
   if (per_sm > 1) cands.push_back(1);
   auto launch = [&](int q) {
-    if (q > 100) {
-      const int S = q - 100;
-      const size_t sm = ws_smem<N>(nrhs, S, ws_limit);
-      GB_CHECK(cudaFuncSetAttribute(kws, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
+    if (q > 1000) {
+      const int KH = (q / 100) % 10, SL = (q / 10) % 10, SA = q % 10;
+      const size_t sm = ws_layout(N, KH, nrhs, SL, SA).total;
       int grid = sms;
       if (grid > batch.total) grid = batch.total;
-      kws<<<grid, kWsThreads, sm, st>>>(batch, nrhs, S, err);
+      if (KH == 2) {
+        auto k2 = k_coarse_mma_ws<BF16, N, 2>;
+        GB_CHECK(cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
+        k2<<<grid, kWsThreads, sm, st>>>(batch, nrhs, SL, SA, err);
+      } else {
+        auto k1 = k_coarse_mma_ws<BF16, N, 1>;
+        GB_CHECK(cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
+        k1<<<grid, kWsThreads, sm, st>>>(batch, nrhs, SL, SA, err);
+      }
       return;
     }
     int grid = sms * q;

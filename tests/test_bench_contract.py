@@ -10,7 +10,7 @@ def test_reference_line_keys(monkeypatch, capsys):
     full = bench.oracle_coarse_apply_sample
 
     def short(**kw):
-        return full(sites=32, budget_s=0.05)
+        return full(n=8, cdims=(2, 2, 2, 4), budget_s=0.05, cores=2)
 
     monkeypatch.setattr(bench, "oracle_coarse_apply_sample", short)
     monkeypatch.delenv("RANK", raising=False)
@@ -25,7 +25,7 @@ def test_reference_line_keys(monkeypatch, capsys):
     assert d["value"] > 0 and d["ms_per_step"] > 0
     assert d["config"]["workload"] == bench.WORKLOAD
     cb = d["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["sample"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 2 and cb["sample"]
     assert cb["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "GB/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
@@ -41,16 +41,24 @@ def test_reference_arm_other_ranks_do_no_work(monkeypatch, capsys):
 
 
 def test_oracle_sample_counts_fp64_algorithmic_bytes(monkeypatch):
-    """GB/s = sites x (9 n^2 links + 2 n spinor) x 16 B x repetitions / s,
-    with a clock that advances one second per reading (one repetition)."""
+    """One process's chunk: sites x (9 n^2 links + 2 n spinor) x 16 B per
+    repetition, with a clock that advances one second per reading (one
+    repetition); the baseline sums the processes' rates."""
     import itertools
 
     import bench
     clock = itertools.count()
     monkeypatch.setattr(bench.time, "perf_counter", lambda: float(next(clock)))
-    r = bench.oracle_coarse_apply_sample(n=8, cdims=(2, 2, 2, 4), sites=8, budget_s=0.5)
-    assert r["value"] == 8 * (9 * 64 * 16 + 2 * 8 * 16) / 1e9
-    assert r["unit"] == "GB/s" and r["cores"] == 1 and "1 repetitions" in r["sample"]
+    reps, el, nbytes = bench._oracle_apply_worker((8, (2, 2, 2, 4), 0, 8, 0.5))
+    assert (reps, el) == (1, 1.0)
+    assert nbytes == 8 * (9 * 64 * 16 + 2 * 8 * 16)
+
+
+def test_oracle_sample_uses_every_requested_core():
+    import bench
+    r = bench.oracle_coarse_apply_sample(n=8, cdims=(2, 2, 2, 4), budget_s=0.2, cores=3)
+    assert r["unit"] == "GB/s" and r["cores"] == 3 and r["value"] > 0
+    assert "all 32 sites" in r["sample"] and "3 processes" in r["sample"]
 
 
 def test_clock_sampler_summary(tmp_path):

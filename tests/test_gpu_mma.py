@@ -37,16 +37,17 @@ def test_coarse_apply_tensor_cores(gpu_lib, prec, cdims, nv, nrhs):
 
 
 @pytest.mark.parametrize("cdims,nv,nrhs,choices", [
-    ((4, 4, 4, 8), 24, 8, (102, 105, 108, 1)),     # 512 sites: several per CTA
-    ((6, 4, 4, 6), 24, 64, (102, 104, 106)),
-    ((4, 4, 4, 8), 32, 32, (102, 106, 1)),
-    ((4, 4, 4, 8), 16, 4, (102, 108)),
+    ((4, 4, 4, 8), 24, 8, (1282, 1222, 1183, 1)),     # 512 sites: several per CTA
+    ((6, 4, 4, 6), 24, 64, (1242, 1222, 1182, 1)),
+    ((4, 4, 4, 8), 32, 32, (1252, 1222, 1182, 1)),
+    ((4, 4, 4, 8), 16, 4, (1282, 1183)),
 ])
 def test_every_launch_shape_on_many_sites(gpu_lib, cdims, nv, nrhs, choices):
-    """Each launch shape pinned in turn: the pipelined kernel with an S-deep
-    ring (choice 100 + S, S = 2 makes every slot wrap once per site) and the
-    register-staged kernel (choice = CTAs per SM), on lattices with more
-    sites than SMs, so the rings and both TMEM accumulators cycle."""
+    """Each launch shape pinned in turn: the pipelined kernel (choice
+    1000 + 100 KH + 10 SL + SA: KH half slots per stage, SL-deep load ring,
+    SA-deep operand ring; SL = SA = 2 wraps both rings four times per site)
+    and the register-staged kernel (choice = CTAs per SM), on lattices with
+    more sites than SMs, so the rings and both TMEM accumulators cycle."""
     gb = gpu_lib
     dims = tuple(c * 2 for c in cdims)
     mg, _ = make_ctx(gb, dims, [(2, 2, 2, 2)], [nv], prec_fine=1, prec_coarse=2)
