@@ -629,6 +629,8 @@ def gpu_main(args):
     learned_setup = run_learned(args, gb, torch, dev) if args.learned else None
     precision = run_precision(args, gb, torch, dev) if args.precision else None
     peak, peak_kind = peaks()
+    fma = {"fp32_tflops": gb.mg_fma_peak(gb.F32), "fp64_tflops": gb.mg_fma_peak(gb.F64),
+           "how": "mg_fma_peak: independent FMA chains on every SM, CUDA events"}
     solve_s = [s["seconds"] for s in stats]
     line = {
         "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -655,6 +657,7 @@ def gpu_main(args):
                   "forms": forms},
         "learned_setup": learned_setup,
         "precision": precision,
+        "measured_fma_peaks": fma,
         "phases_ms_median": dict(zip(["setup_l0", "build_l1", "setup_l1", "build_l2", "solve"],
                                      [float(v) for v in np.median(ph, axis=0)])),
         "kernels": {k: {"launches": v["launches"], "ms": v["ms"],
@@ -683,13 +686,14 @@ def gpu_main(args):
 
 
 def coarse_apply_main(args):
-    """Only the level-1 coarse apply (8^3x16 lattice, n = 48) with random
-    links: `steps` timed applies, each on the same 1.36 GB (FP32) link set."""
+    """Only the level-1 coarse apply (8^3x16 lattice, n = 48, or the coarse
+    lattice of --fine with 2^4 aggregates) with random links: `steps` timed
+    applies, each on the same 1.36 GB (FP32) link set."""
     import torch
 
     import paper_1612_07873_gb300 as gb
     prec = {"fp32": 1, "bf16": 2, "fp16": 3, "int16": 4}[args.form]
-    fine = (16, 16, 16, 32)
+    fine = tuple(int(v) for v in args.fine.split(",")) if args.fine else (16, 16, 16, 32)
     U = syn.gauge_field(fine, 0.0, 1)
     p = gb.default_params(dims=fine, block=[(2, 2, 2, 2)], nvec=[24], nlevels=2, prec_fine=1,
                           prec_coarse=prec, link_slots=args.slots)
@@ -778,7 +782,9 @@ def mma_sweep_main(args):
                              "tflops": q["flops"] / q["launches"] / (us * 1e-6) / 1e12}
                 out["bytes"] = q["bytes"] / q["launches"]
             if nrhs > 1:
-                out["launch_choice"] = gb.mg_tune_get(f"mma2/bf16/n{n}/r{nrhs}/v{vol}/b1")
+                key = f"mma2/bf16/n{n}/r{nrhs}/v{vol}/b1"
+                out["launch_choice"] = gb.mg_tune_get(key)
+                out["tuner_candidates_us"] = {str(c): 1e3 * t for c, t in gb.mg_tune_report(key)}
             rows.append(out)
             del x, y
         mg.close()

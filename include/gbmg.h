@@ -300,6 +300,11 @@ mg_status mg_load(mg_ctx* ctx, const char* path);
  * autotuning of launch parameters (Secs. 4 and 6) is the model.                  */
 mg_status mg_tune_set(const char* key, int choice);
 int mg_tune_get(const char* key);
+/* The candidates that the last tuning of `key` timed, with milliseconds per
+ * launch: fills up to `max` entries of choices / ms (either may be NULL) and
+ * returns the number of candidates (0 if the key was never tuned in this
+ * process, -1 for a NULL key).                                             */
+int mg_tune_report(const char* key, int* choices, float* ms, int max);
 
 /* Block orthonormalisation that allocates no device memory.  The paper has
  * no counterpart: this entry point exists for callers that cannot let a
@@ -451,6 +456,15 @@ mg_status mg_inner_product(mg_ctx* ctx, int level, const void* a, const void* b,
  * mg_device_status returns MG_ERR_TIMEOUT.  MG_ERR_ARG for another name or
  * count outside 0..1000; count = 0 cancels.                               */
 mg_status mg_inject_fault(mg_ctx* ctx, const char* what, int count);
+
+/* Measured CUDA-core peak of fused multiply-adds on the current device, in
+ * TFLOP/s (2 flops per FMA): prec = MG_F32 or MG_F64.  A kernel of
+ * independent FMA chains fills every SM; five launches are timed with CUDA
+ * events on `stream` (synchronised).  The roofline denominator of the
+ * kernels bound by the FP32 pipe (the Galerkin product) and the FP64 pipe
+ * (the block Gram-Schmidt, the FP64 fine operator); the paper has no
+ * counterpart.  MG_ERR_ARG for another precision or a null output.         */
+mg_status mg_fma_peak(int prec, double* tflops, void* stream);
 
 /* Number of kernels the library has launched since creation.              */
 long long mg_launch_count(mg_ctx* ctx);

@@ -100,6 +100,7 @@ def _load():
         "mg_wilson_clover_apply_bf16": (i, [vp, vp, vp, i, vp]),
         "mg_schur_apply": (i, [vp, i, vp, vp, i, vp]),
         "mg_tune_get": (i, [C.c_char_p]),
+        "mg_tune_report": (i, [C.c_char_p, C.POINTER(C.c_int), C.POINTER(C.c_float), i]),
         "mg_get_coarse_links": (i, [vp, i, vp, sz, vp]),
         "mg_set_coarse_links": (i, [vp, i, vp, sz, vp]),
         "mg_level_info": (i, [vp, i, C.POINTER(C.c_int), C.POINTER(C.c_int),
@@ -125,6 +126,7 @@ def _load():
                                  C.POINTER(d), vp]),
         "mg_cnn_adam_step": (i, [vp, C.c_float, vp]),
         "mg_launch_count": (C.c_longlong, [vp]),
+        "mg_fma_peak": (i, [i, C.POINTER(d), vp]),
         "mg_halo_plan": (i, [C.POINTER(C.c_int), C.POINTER(C.c_int), i, C.POINTER(C.c_int),
                              C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "mg_halo_face_sites": (i, [C.POINTER(C.c_int), i, i, C.POINTER(C.c_int)]),
@@ -301,6 +303,16 @@ def mg_tune_get(key):
     return LIB.mg_tune_get(key.encode())
 
 
+def mg_tune_report(key):
+    """[(choice, ms per launch)] of the last tuning of `key` in this process."""
+    n = LIB.mg_tune_report(key.encode(), None, None, 0)
+    if n <= 0:
+        return []
+    ch, ms = (C.c_int * n)(), (C.c_float * n)()
+    LIB.mg_tune_report(key.encode(), ch, ms, n)
+    return list(zip(list(ch), [float(v) for v in ms]))
+
+
 def mg_get_coarse_links(ctx, level, out, stream=None):
     _ok(LIB.mg_get_coarse_links(ctx, level, _ptr(out), out.numel() * out.element_size(),
                                 _stream(stream)), ctx)
@@ -444,6 +456,13 @@ def mg_cnn_loss_grad(net, dims, block, gauge, target, stream=None) -> float:
 
 def mg_cnn_adam_step(net, lr, stream=None):
     _ok(LIB.mg_cnn_adam_step(net, lr, _stream(stream)))
+
+
+def mg_fma_peak(prec, stream=None) -> float:
+    """Measured FP32 (prec = F32) or FP64 (F64) FMA peak in TFLOP/s."""
+    t = C.c_double()
+    _ok(LIB.mg_fma_peak(int(prec), C.byref(t), _stream(stream)), None)
+    return t.value
 
 
 def mg_launch_count(ctx) -> int:

@@ -367,6 +367,17 @@ mg_status mg_tune_set(const char* key, int choice) {
 
 int mg_tune_get(const char* key) { return key ? gbmg::Tuner::get().get(key) : -1; }
 
+int mg_tune_report(const char* key, int* choices, float* ms, int max) {
+  if (!key) return -1;
+  const auto t = gbmg::Tuner::get().report(key);
+  const int n = int(t.size());
+  for (int i = 0; i < n && i < max; ++i) {
+    if (choices) choices[i] = t[i].first;
+    if (ms) ms[i] = t[i].second;
+  }
+  return n;
+}
+
 mg_status mg_schur_apply(mg_ctx* c, int level, void* y, const void* x, int nrhs, void* stream) {
   return guarded(c, [&] {
     check_level(c, level, 0, c->nlevels - 1);

@@ -47,6 +47,7 @@ class Tuner {
     GB_CHECK(cudaEventCreate(&b));
     int pick = cands.front();
     float best_ms = 1e30f;
+    std::vector<std::pair<int, float>> times;
     for (int c : cands) {
       launch(c);  // warm-up
       GB_CHECK(cudaEventRecord(a, st));
@@ -55,6 +56,7 @@ class Tuner {
       GB_CHECK(cudaEventSynchronize(b));
       float ms = 0.f;
       GB_CHECK(cudaEventElapsedTime(&ms, a, b));
+      times.emplace_back(c, ms / 3.f);
       if (ms < best_ms) {
         best_ms = ms;
         pick = c;
@@ -63,6 +65,7 @@ class Tuner {
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     best_[key] = pick;
+    timings_[key] = times;
     if (!path_.empty()) {
       std::ofstream f(path_, std::ios::app);
       if (f) f << key << " " << pick << "\n";
@@ -85,6 +88,12 @@ class Tuner {
       best_.erase(key);
     else
       best_[key] = choice;
+  }
+  // the candidates timed when `key` was last tuned, with ms per launch
+  std::vector<std::pair<int, float>> report(const std::string& key) {
+    std::lock_guard<std::mutex> lk(mu_);
+    auto it = timings_.find(key);
+    return it == timings_.end() ? std::vector<std::pair<int, float>>{} : it->second;
   }
   int get(const std::string& key) {
     std::lock_guard<std::mutex> lk(mu_);
@@ -111,6 +120,7 @@ class Tuner {
   }
   std::mutex mu_;
   std::unordered_map<std::string, int> best_;
+  std::unordered_map<std::string, std::vector<std::pair<int, float>>> timings_;
   bool loaded_ = false;
   bool enabled_ = true;
   std::string path_;

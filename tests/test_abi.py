@@ -117,6 +117,14 @@ def test_noalloc_rejects_bad_arguments_without_a_gpu(lib):
         assert text in gb.LIB.mg_last_error(None), (args, gb.LIB.mg_last_error(None))
 
 
+def test_fma_peak_rejects_bad_arguments_without_a_gpu(lib):
+    import paper_1612_07873_gb300 as gb
+    t = C.c_double()
+    assert gb.LIB.mg_fma_peak(gb.BF16, C.byref(t), None) == gb.MG_ERR_ARG
+    assert b"prec" in gb.LIB.mg_last_error(None)
+    assert gb.LIB.mg_fma_peak(gb.F32, None, None) == gb.MG_ERR_ARG
+
+
 def test_tuner_cache_file_and_pins_without_a_gpu(lib, tmp_path):
     """The launch-policy cache (GBMG_TUNE_CACHE, "key value" lines) is read
     on first use; mg_tune_set pins or (choice < 0) clears a key.  Run in a
