@@ -439,9 +439,9 @@ __global__ void __launch_bounds__(128) k_coarse_mma(const MmaBatch batch, int nr
 //   warp 8     lane 0 issues the bulk copies
 //   warp 9     lane 0 issues the MMAs of each stage and commits them
 // Barriers: load_full (copy bytes) and load_empty (the stage's MMAs and
-// its 128 converting threads done) per load slot; a_full (128 converting
-// threads) and a_empty (MMAs done) per operand slot; acc_full (MMAs of the
-// site done) and acc_empty (128 epilogue threads done) per accumulator (two
+// its four converting warps done) per load slot; a_full (four converting
+// warps) and a_empty (MMAs done) per operand slot; acc_full (MMAs of the
+// site done) and acc_empty (four epilogue warps done) per accumulator (two
 // TMEM buffers of n columns, so the epilogue of one site overlaps the MMAs
 // of the next).  The A operand keeps only its 2 nrhs used rows; the MMA's
 // rows beyond them (M = 128) read whatever follows in shared memory and
@@ -518,15 +518,15 @@ __global__ void __launch_bounds__(kWsThreads, 1)
   if (tid == 0) {
     for (int q = 0; q < SL; ++q) {
       mbar_init(&load_full[q], 1);
-      mbar_init(&load_empty[q], 129);  // the MMA commit + 128 converting threads
+      mbar_init(&load_empty[q], 5);  // the MMA commit + one lane of each converting warp
     }
     for (int q = 0; q < SA; ++q) {
-      mbar_init(&a_full[q], 128);
+      mbar_init(&a_full[q], 4);
       mbar_init(&a_empty[q], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], 128);
+      mbar_init(&acc_empty[b], 4);
     }
     mbar_init(&fin, 1);
     mbar_init(&stall_bar, 1);  // the injected stall's barrier; never arrived at
@@ -555,9 +555,11 @@ __global__ void __launch_bounds__(kWsThreads, 1)
   if (warp < 4) {
     // ---- convert: element (k, j) of a half slot, k < N / 2 complex columns,
     // j < nrhs; lane l takes j = 8 jt + (l & 7), k = 4 kt + (l >> 3), so a
-    // warp's 32 four-byte stores fill one 8-row x 16-byte core matrix
-    const int jt_n = (nrhs + 7) >> 3;
-    const int ntiles = (N / 8) * jt_n;  // tiles of a half slot
+    // warp's 32 four-byte stores fill one 8-row x 16-byte core matrix.  The
+    // right-hand-side tile count is rounded up to a power of two (tiles past
+    // nrhs convert nothing) so the mapping is shifts.
+    const int jsh = nrhs <= 8 ? 0 : nrhs <= 16 ? 1 : nrhs <= 32 ? 2 : 3;
+    const int ntiles = (N / 8) << jsh;  // tiles of a half slot
     uint32_t q = 0;
     for (int gs = blockIdx.x; gs < batch.total && !abort_sh; gs += gridDim.x) {
       for (int d = 0; d < NST; ++d, ++q) {
@@ -571,8 +573,9 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         for (int h = 0; h < KH; ++h) {
           unsigned char* Ah = A + h * lay.xh;
           const cpx<float>* xh = xr + h * (N / 2) * nrhs;
+#pragma unroll 4
           for (int t = warp; t < ntiles; t += 4) {
-            const int j = 8 * (t % jt_n) + (lane & 7), k = 4 * (t / jt_n) + (lane >> 3);
+            const int j = 8 * (t & ((1 << jsh) - 1)) + (lane & 7), k = 4 * (t >> jsh) + (lane >> 3);
             if (j < nrhs) {
               const cpx<float> v = xh[k * nrhs + j];
               *reinterpret_cast<uint32_t*>(Ah + core_off(j, 2 * k, N)) = pack2<BF16>(v.re, -v.im);
@@ -581,9 +584,14 @@ __global__ void __launch_bounds__(kWsThreads, 1)
             }
           }
         }
+        // every thread's operand writes made visible to the tensor core, then
+        // one arrival per warp: the spinor rows are read, the operand is ready
         fence_proxy_async_smem();
-        mbar_arrive(&a_full[sa]);
-        mbar_arrive(&load_empty[sl]);  // this thread has read the spinor rows
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&a_full[sa]);
+          mbar_arrive(&load_empty[sl]);
+        }
       }
     }
   } else if (warp < 8) {
@@ -611,7 +619,8 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         }
       }
       tc_fence_before();
-      mbar_arrive(&acc_empty[b]);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[b]);
       asm volatile("bar.sync 1, 128;" ::: "memory");
       const float sc = cur.scales[site];
       cpx<float>* ys = cur.y + size_t(site) * N * nrhs;
