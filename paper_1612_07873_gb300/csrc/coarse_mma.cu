@@ -426,8 +426,8 @@ __global__ void __launch_bounds__(128) k_coarse_mma(const MmaBatch batch, int nr
 }
 
 // ---------------------------------------------------------------------------
-// Warp-specialised, pipelined form of the same GEMM (persistent, one CTA per
-// SM, 320 threads).  A pipeline stage is KH half slots of one stencil slot
+// Warp-specialised, pipelined form of the same GEMM (persistent, one to
+// three CTAs per SM, 320 threads each).  A pipeline stage is KH half slots of one stencil slot
 // (KH = 2: the whole slot, K = 2n; KH = 1: half of it, K = n).  Both inputs
 // of a stage are contiguous in global memory and arrive by bulk copies
 // (cp.async.bulk) into an SL-deep load ring: the stage's links (the tiled
@@ -489,7 +489,7 @@ __host__ __device__ inline WsLayout ws_layout(int N, int KH, int nrhs, int SL, i
 }
 
 template <bool BF16, int N, int KH>
-__global__ void __launch_bounds__(kWsThreads, 1)
+__global__ void __launch_bounds__(kWsThreads, 2)
     k_coarse_mma_ws(const MmaBatch batch, int nrhs, int SL, int SA, int* __restrict__ err) {
   constexpr int NST = 18 / KH;                         // stages per site
   constexpr int HB = 2 * N * N;                        // link bytes of a half slot
@@ -774,23 +774,28 @@ void launch_mma_batch(int* err, const MmaBatch& batch, int nrhs, cudaStream_t st
   for (int i = 0; i < batch.count; ++i)
     aligned = aligned && (reinterpret_cast<uintptr_t>(batch.lat[i].x) % 16 == 0) &&
               (reinterpret_cast<uintptr_t>(batch.lat[i].links) % 16 == 0);
-  // Autotuned launch shape: choice 1000 + 100 KH + 10 SL + SA is the
-  // pipelined kernel (KH half slots per stage, SL-deep load ring, SA-deep
-  // operand ring, one persistent CTA per SM); choice q <= 8 the register-
-  // staged kernel with q resident CTAs per SM.
+  // Autotuned launch shape: choice 1000 cps + 100 KH + 10 SL + SA is the
+  // pipelined kernel with cps persistent CTAs per SM (KH half slots per
+  // stage, SL-deep load ring, SA-deep operand ring); choice q <= 8 the
+  // register-staged kernel with q resident CTAs per SM.
   std::vector<int> cands;
   if (aligned)
-    for (int KH : {2, 1})
-      for (int SA : {2, 3})
-        for (int SL = kWsMaxStages; SL >= 2; --SL)
-          if (ws_fits(N, KH, nrhs, SL, SA, ws_limit)) cands.push_back(1000 + 100 * KH + 10 * SL + SA);
+    for (int cps : {1, 2, 3}) {
+      // shared memory of one SM split between cps CTAs (1 KB reserved each)
+      const size_t lim = std::min(ws_limit, size_t(smem_sm) / cps - 1024 - fw.sharedSizeBytes);
+      for (int KH : {2, 1})
+        for (int SA : {2, 3})
+          for (int SL = kWsMaxStages; SL >= 2; --SL)
+            if (ws_fits(N, KH, nrhs, SL, SA, lim))
+              cands.push_back(1000 * cps + 100 * KH + 10 * SL + SA);
+    }
   cands.push_back(per_sm);
   if (per_sm > 1) cands.push_back(1);
   auto launch = [&](int q) {
     if (q > 1000) {
-      const int KH = (q / 100) % 10, SL = (q / 10) % 10, SA = q % 10;
+      const int cps = q / 1000, KH = (q / 100) % 10, SL = (q / 10) % 10, SA = q % 10;
       const size_t sm = ws_layout(N, KH, nrhs, SL, SA).total;
-      int grid = sms;
+      int grid = sms * cps;
       if (grid > batch.total) grid = batch.total;
       if (KH == 2) {
         auto k2 = k_coarse_mma_ws<BF16, N, 2>;
