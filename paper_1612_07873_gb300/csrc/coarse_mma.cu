@@ -433,14 +433,15 @@ __global__ void __launch_bounds__(128) k_coarse_mma(const MmaBatch batch, int nr
 // (cp.async.bulk) into an SL-deep load ring: the stage's links (the tiled
 // store, L2 evict-first) and the rows of the neighbour's FP32 spinor the
 // stage needs.  Four warps convert the spinor rows into the 16-bit MMA
-// operand in shared memory (an SA-deep operand ring), and
+// operand in shared memory (an SA-deep operand ring), each warp a whole
+// stage (stage q: warp q mod 4), so four stages convert at once, and
 //   warps 0-3  convert (x(nbr) -> rows j, nrhs + j of the A operand)
 //   warps 4-7  epilogue: their TMEM lane quarter -> shared memory -> y
 //   warp 8     lane 0 issues the bulk copies
 //   warp 9     lane 0 issues the MMAs of each stage and commits them
 // Barriers: load_full (copy bytes) and load_empty (the stage's MMAs and
-// its four converting warps done) per load slot; a_full (four converting
-// warps) and a_empty (MMAs done) per operand slot; acc_full (MMAs of the
+// its converting warp done) per load slot; a_full (the converting warp)
+// and a_empty (MMAs done) per operand slot; acc_full (MMAs of the
 // site done) and acc_empty (four epilogue warps done) per accumulator (two
 // TMEM buffers of n columns, so the epilogue of one site overlaps the MMAs
 // of the next).  The A operand keeps only its 2 nrhs used rows; the MMA's
@@ -454,6 +455,7 @@ constexpr int kWsMaxStages = 8;
 __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity,
                                               volatile int* abort_flag, int* err) {
   constexpr uint64_t kBudgetNs = 1000000000ull;
+  if (mbar_try_wait(bar, parity)) return true;  // the common case: no timer read
   const uint64_t t0 = global_ns();
   for (uint32_t it = 0;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
@@ -489,7 +491,7 @@ __host__ __device__ inline WsLayout ws_layout(int N, int KH, int nrhs, int SL, i
 }
 
 template <bool BF16, int N, int KH>
-__global__ void __launch_bounds__(kWsThreads, 2)
+__global__ void __launch_bounds__(kWsThreads, 3)
     k_coarse_mma_ws(const MmaBatch batch, int nrhs, int SL, int SA, int* __restrict__ err) {
   constexpr int NST = 18 / KH;                         // stages per site
   constexpr int HB = 2 * N * N;                        // link bytes of a half slot
@@ -518,10 +520,10 @@ __global__ void __launch_bounds__(kWsThreads, 2)
   if (tid == 0) {
     for (int q = 0; q < SL; ++q) {
       mbar_init(&load_full[q], 1);
-      mbar_init(&load_empty[q], 5);  // the MMA commit + one lane of each converting warp
+      mbar_init(&load_empty[q], 2);  // the MMA commit + the converting warp
     }
     for (int q = 0; q < SA; ++q) {
-      mbar_init(&a_full[q], 4);
+      mbar_init(&a_full[q], 1);
       mbar_init(&a_empty[q], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -553,39 +555,54 @@ __global__ void __launch_bounds__(kWsThreads, 2)
   };
 
   if (warp < 4) {
-    // ---- convert: element (k, j) of a half slot, k < N / 2 complex columns,
-    // j < nrhs; lane l takes j = 8 jt + (l & 7), k = 4 kt + (l >> 3), so a
-    // warp's 32 four-byte stores fill one 8-row x 16-byte core matrix.  The
-    // right-hand-side tile count is rounded up to a power of two (tiles past
-    // nrhs convert nothing) so the mapping is shifts.
+    // ---- convert: warp w converts stages w, w + 4, ...  Element (k, j) of a
+    // half slot, k < N / 2 complex columns, j < nrhs; lane l takes
+    // j = 8 jt + (l & 7), k = 4 kt + (l >> 3), so the warp's 32 four-byte
+    // stores fill one 8-row x 16-byte core matrix.  The right-hand-side tile
+    // count is rounded up to a power of two (tiles past nrhs convert
+    // nothing) so the mapping is shifts; the tile values of a batch are all
+    // read before any is written.
     const int jsh = nrhs <= 8 ? 0 : nrhs <= 16 ? 1 : nrhs <= 32 ? 2 : 3;
     const int ntiles = (N / 8) << jsh;  // tiles of a half slot
+    const int jl = lane & 7, kl0 = lane >> 3;
     uint32_t q = 0;
     for (int gs = blockIdx.x; gs < batch.total && !abort_sh; gs += gridDim.x) {
       for (int d = 0; d < NST; ++d, ++q) {
+        if (int(q & 3u) != warp) continue;
         const uint32_t sl = q % uint32_t(SL), lph = (q / uint32_t(SL)) & 1u;
         const uint32_t sa = q % uint32_t(SA), aph = (q / uint32_t(SA)) & 1u;
         if (!wait_or_abort(&load_full[sl], lph, &abort_sh, err)) break;
         if (!wait_or_abort(&a_empty[sa], aph ^ 1u, &abort_sh, err)) break;
-        const cpx<float>* xr = reinterpret_cast<const cpx<float>*>(rring + size_t(sl) * lay.rb);
-        unsigned char* A = aring + size_t(sa) * lay.ab;
+        const cpx<float>* __restrict__ xr =
+            reinterpret_cast<const cpx<float>*>(rring + size_t(sl) * lay.rb);
+        unsigned char* __restrict__ A = aring + size_t(sa) * lay.ab;
 #pragma unroll
         for (int h = 0; h < KH; ++h) {
           unsigned char* Ah = A + h * lay.xh;
           const cpx<float>* xh = xr + h * (N / 2) * nrhs;
-#pragma unroll 4
-          for (int t = warp; t < ntiles; t += 4) {
-            const int j = 8 * (t & ((1 << jsh) - 1)) + (lane & 7), k = 4 * (t >> jsh) + (lane >> 3);
-            if (j < nrhs) {
-              const cpx<float> v = xh[k * nrhs + j];
-              *reinterpret_cast<uint32_t*>(Ah + core_off(j, 2 * k, N)) = pack2<BF16>(v.re, -v.im);
-              *reinterpret_cast<uint32_t*>(Ah + core_off(nrhs + j, 2 * k, N)) =
-                  pack2<BF16>(v.im, v.re);
+          for (int t0 = 0; t0 < ntiles; t0 += 8) {
+            cpx<float> v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int t = t0 + u;
+              const int j = 8 * (t & ((1 << jsh) - 1)) + jl, k = 4 * (t >> jsh) + kl0;
+              if (t < ntiles && j < nrhs) v[u] = xh[k * nrhs + j];
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int t = t0 + u;
+              const int j = 8 * (t & ((1 << jsh) - 1)) + jl, k = 4 * (t >> jsh) + kl0;
+              if (t < ntiles && j < nrhs) {
+                *reinterpret_cast<uint32_t*>(Ah + core_off(j, 2 * k, N)) =
+                    pack2<BF16>(v[u].re, -v[u].im);
+                *reinterpret_cast<uint32_t*>(Ah + core_off(nrhs + j, 2 * k, N)) =
+                    pack2<BF16>(v[u].im, v[u].re);
+              }
             }
           }
         }
-        // every thread's operand writes made visible to the tensor core, then
-        // one arrival per warp: the spinor rows are read, the operand is ready
+        // every lane's operand writes made visible to the tensor core, then
+        // one arrival: the spinor rows are read, the operand is ready
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) {
@@ -683,14 +700,16 @@ __global__ void __launch_bounds__(kWsThreads, 2)
             break;
           }
           tc_fence_after();
-          const uint32_t a0 = smem_u32(aring + size_t(sa) * lay.ab);
-          const uint32_t b0 = smem_u32(lring + size_t(sl) * lay.lb);
+          // descriptors of the stage's first K step; a step of 256 bytes
+          // adds 16 to the start-address field (addresses stay below 256 KB)
+          const uint64_t da = smem_desc(smem_u32(aring + size_t(sa) * lay.ab), LBO, SBO);
+          const uint64_t db = smem_desc(smem_u32(lring + size_t(sl) * lay.lb), LBO, SBO);
 #pragma unroll
           for (int h = 0; h < KH; ++h)
 #pragma unroll
             for (int kk = 0; kk < N / 16; ++kk)
-              mma_f16(dt, smem_desc(a0 + h * lay.xh + kk * 256, LBO, SBO),
-                      smem_desc(b0 + h * HB + kk * 256, LBO, SBO), IDESC,
+              mma_f16(dt, da + uint64_t((h * lay.xh + kk * 256) >> 4),
+                      db + uint64_t((h * HB + kk * 256) >> 4), IDESC,
                       (d > 0 || h > 0 || kk > 0) ? 1u : 0u);
           mma_commit(&load_empty[sl]);
           mma_commit(&a_empty[sa]);
@@ -784,7 +803,7 @@ void launch_mma_batch(int* err, const MmaBatch& batch, int nrhs, cudaStream_t st
       // shared memory of one SM split between cps CTAs (1 KB reserved each)
       const size_t lim = std::min(ws_limit, size_t(smem_sm) / cps - 1024 - fw.sharedSizeBytes);
       for (int KH : {2, 1})
-        for (int SA : {2, 3})
+        for (int SA : {4, 3, 2})
           for (int SL = kWsMaxStages; SL >= 2; --SL)
             if (ws_fits(N, KH, nrhs, SL, SA, lim))
               cands.push_back(1000 * cps + 100 * KH + 10 * SL + SA);
