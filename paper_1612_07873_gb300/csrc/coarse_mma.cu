@@ -506,6 +506,12 @@ __global__ void __launch_bounds__(kWsThreads, 3)
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int abort_sh;
   __shared__ int epi_ok;
+  // ring depths the host guarantees: 4 or 8 (multiples of the converting
+  // warps, see the converter) -- any other value would break the phase rule
+  if ((SL != 4 && SL != 8) || (SA != 4 && SA != 8)) {
+    if (threadIdx.x == 0) atomicOr(err, 1);
+    return;
+  }
   const WsLayout lay = ws_layout(N, KH, nrhs, SL, SA);
   unsigned char* aring = smem + lay.a_off;
   unsigned char* lring = smem + lay.l_off;
@@ -555,7 +561,11 @@ __global__ void __launch_bounds__(kWsThreads, 3)
   };
 
   if (warp < 4) {
-    // ---- convert: warp w converts stages w, w + 4, ...  Element (k, j) of a
+    // ---- convert: warp w converts stages w, w + 4, ...  SL and SA are
+    // multiples of 4, so every ring slot is always served by the same warp:
+    // when the warp waits for a slot's phase k, it has itself waited for
+    // phase k - 1 (the slot's previous use), so the parity test of
+    // mbarrier.try_wait cannot match a phase two back.  Element (k, j) of a
     // half slot, k < N / 2 complex columns, j < nrhs; lane l takes
     // j = 8 jt + (l & 7), k = 4 kt + (l >> 3), so the warp's 32 four-byte
     // stores fill one 8-row x 16-byte core matrix.  The right-hand-side tile
@@ -802,9 +812,11 @@ void launch_mma_batch(int* err, const MmaBatch& batch, int nrhs, cudaStream_t st
     for (int cps : {1, 2, 3}) {
       // shared memory of one SM split between cps CTAs (1 KB reserved each)
       const size_t lim = std::min(ws_limit, size_t(smem_sm) / cps - 1024 - fw.sharedSizeBytes);
+      // ring depths are multiples of the four converting warps (see the
+      // kernel's comment on barrier phases)
       for (int KH : {2, 1})
-        for (int SA : {4, 3, 2})
-          for (int SL = kWsMaxStages; SL >= 2; --SL)
+        for (int SA : {4, 8})
+          for (int SL : {8, 4})
             if (ws_fits(N, KH, nrhs, SL, SA, lim))
               cands.push_back(1000 * cps + 100 * KH + 10 * SL + SA);
     }

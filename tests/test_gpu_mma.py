@@ -37,17 +37,17 @@ def test_coarse_apply_tensor_cores(gpu_lib, prec, cdims, nv, nrhs):
 
 
 @pytest.mark.parametrize("cdims,nv,nrhs,choices", [
-    ((4, 4, 4, 8), 24, 8, (1282, 1222, 1183, 1)),     # 512 sites: several per CTA
-    ((6, 4, 4, 6), 24, 64, (1242, 1222, 1182, 1)),
-    ((4, 4, 4, 8), 32, 32, (1252, 1222, 1182, 1)),
-    ((4, 4, 4, 8), 16, 4, (1282, 1183)),
+    ((4, 4, 4, 8), 24, 8, (1284, 1244, 1144, 2244, 3248, 1)),  # 512 sites: several per CTA
+    ((6, 4, 4, 6), 24, 64, (1144, 1184, 1)),
+    ((4, 4, 4, 8), 32, 32, (1244, 1184, 1144, 2144, 1)),
+    ((4, 4, 4, 8), 16, 4, (1288, 1244, 3244, 1144)),
 ])
 def test_every_launch_shape_on_many_sites(gpu_lib, cdims, nv, nrhs, choices):
     """Each launch shape pinned in turn: the pipelined kernel (choice
-    1000 + 100 KH + 10 SL + SA: KH half slots per stage, SL-deep load ring,
-    SA-deep operand ring; SL = SA = 2 wraps both rings four times per site)
-    and the register-staged kernel (choice = CTAs per SM), on lattices with
-    more sites than SMs, so the rings and both TMEM accumulators cycle."""
+    1000 cps + 100 KH + 10 SL + SA: cps CTAs per SM, KH half slots per
+    stage, SL-deep load ring, SA-deep operand ring, SL and SA 4 or 8) and the
+    register-staged kernel (choice = CTAs per SM), on lattices with more
+    sites than SMs, so the rings and both TMEM accumulators cycle."""
     gb = gpu_lib
     dims = tuple(c * 2 for c in cdims)
     mg, _ = make_ctx(gb, dims, [(2, 2, 2, 2)], [nv], prec_fine=1, prec_coarse=2)
