@@ -37,7 +37,7 @@ def test_coarse_apply_tensor_cores(gpu_lib, prec, cdims, nv, nrhs):
 
 
 @pytest.mark.parametrize("cdims,nv,nrhs,choices", [
-    ((4, 4, 4, 8), 24, 8, (1284, 1244, 1144, 2244, 3248, 1)),  # 512 sites: several per CTA
+    ((4, 4, 4, 8), 24, 8, (1284, 1244, 1144, 2244, 3244, 1)),  # 512 sites: several per CTA
     ((6, 4, 4, 6), 24, 64, (1144, 1184, 1)),
     ((4, 4, 4, 8), 32, 32, (1244, 1184, 1144, 2144, 1)),
     ((4, 4, 4, 8), 16, 4, (1288, 1244, 3244, 1144)),
