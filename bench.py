@@ -695,8 +695,8 @@ def coarse_apply_main(args):
     prec = {"fp32": 1, "bf16": 2, "fp16": 3, "int16": 4}[args.form]
     fine = tuple(int(v) for v in args.fine.split(",")) if args.fine else (16, 16, 16, 32)
     U = syn.gauge_field(fine, 0.0, 1)
-    p = gb.default_params(dims=fine, block=[(2, 2, 2, 2)], nvec=[24], nlevels=2, prec_fine=1,
-                          prec_coarse=prec, link_slots=args.slots)
+    p = gb.default_params(dims=fine, block=[(2, 2, 2, 2)], nvec=[args.nvec], nlevels=2,
+                          prec_fine=1, prec_coarse=prec, link_slots=args.slots)
     mg = gb.Multigrid(p, torch.from_numpy(U).cuda())
     l1 = mg.levels[1]
     vol, n = l1["volume"], l1["ndof"]
@@ -704,6 +704,7 @@ def coarse_apply_main(args):
     links = torch.randn((vol, 9, n, n), dtype=torch.complex128, device="cuda", generator=g)
     gb.mg_set_coarse_links(mg.ctx, 1, links)
     del links
+    torch.cuda.empty_cache()  # the FP64 link copy is not needed on the device
     nrhs = args.nrhs
     shape = (vol, n) if nrhs == 1 else (vol, n, nrhs)
     x = torch.randn(shape, dtype=torch.complex64, device="cuda", generator=g)
@@ -924,6 +925,8 @@ def main():
                              "learned", "mma-sweep", "precision"])
     ap.add_argument("--fine", default="", help="override the fine extents, e.g. 16,16,16,32")
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides (coarse-apply mode)")
+    ap.add_argument("--nvec", type=int, default=24,
+                    help="null vectors, n = 2 nvec coarse dofs (coarse-apply mode)")
     ap.add_argument("--slots", type=int, default=9, choices=[5, 9],
                     help="coarse link blocks stored (coarse-apply mode)")
     ap.add_argument("--profile-range", action="store_true",
