@@ -319,7 +319,8 @@ int mg_tune_report(const char* key, int* choices, float* ms, int max);
  * overlap vecs_dev).  `bytes` is the size of each of the two arrays and must
  * equal nvec * V * ndof * 16 (MG_ERR_ARG otherwise).  No context is needed;
  * dims and block are host arrays.
- * Workspace: a file-scope device array of 2^21 complex doubles (32 MiB) that
+ * Workspace: a file-scope device array of 2^21 16-byte complex entries
+ * (float-float, 32 MiB) that
  * every GPU loading the library holds until exit; calls with
  * nvec * V * ndof > 2^21, nvec > 64 or an aggregate of more than 24576
  * rows per chirality fail with MG_ERR_ARG before any device work.  The

@@ -2,9 +2,10 @@
 // split of its footnote) and the transfer operators of Sec. 6.6.
 //
 // For aggregate A and chirality s the (|A| * nd/2) x Nv block of chirality-s
-// components is orthonormalised column by column by Gram-Schmidt in FP64
-// (projection repeated when the first one cancels more than half of the
-// column's squared norm; see k_block_qr).  Rows are ordered (site of A in
+// components is orthonormalised column by column by Gram-Schmidt at FP64
+// accuracy in float-float arithmetic on the FP32 pipe (projection repeated
+// when the first one cancels more than half of the column's squared norm;
+// see k_block_qr).  Rows are ordered (site of A in
 // lexicographic order, dof of chirality s).  The prolongator column (s, i)
 // is vector i of the result restricted to chirality s; coarse dof = s*Nv + i.
 //
@@ -57,9 +58,91 @@ AggMap make_map(const Level& f, const Level& c) {
   return m;
 }
 
-// raw [Nv][V][nd] -> W [agg][chi][Nv][rows]
+// ---------------------------------------------------------------------------
+// Float-float complex numbers: value = (rh + rl) + i (ih + il) with
+// |rl| <= ulp(rh) / 2 (likewise il) whenever one is stored.  About 48
+// significant bits: the block Gram-Schmidt keeps FP64-level accuracy while
+// running on the FP32 pipe (GB300's FP64 rate is a small fraction of it).
+// The products are exact (FMA-split TwoProduct of the high parts plus the
+// FP32 cross terms, whose own rounding is 2^-48 relative), the sums TwoSum.
+struct alignas(16) ffc {
+  float rh, rl, ih, il;
+};
+struct ff {
+  float hi, lo;  // accumulator: lo is renormalised by ff_norm / ff_add
+};
+
+__device__ __forceinline__ void ff_split(double x, float& h, float& l) {
+  h = __double2float_rn(x);
+  l = __double2float_rn(x - double(h));
+}
+__device__ __forceinline__ ffc ffc_from(double2 v) {
+  ffc r;
+  ff_split(v.x, r.rh, r.rl);
+  ff_split(v.y, r.ih, r.il);
+  return r;
+}
+__device__ __forceinline__ double2 ffc_to(const ffc& a) {
+  return make_double2(double(a.rh) + double(a.rl), double(a.ih) + double(a.il));
+}
+__device__ __forceinline__ double ff_to(ff a) { return double(a.hi) + double(a.lo); }
+// s += a b, a = (ah, al), b = (bh, bl)
+__device__ __forceinline__ void ff_mac(ff& s, float ah, float al, float bh, float bl) {
+  const float p = ah * bh;
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  const float t = s.hi + p;
+  const float bp = t - s.hi;
+  const float err = (s.hi - (t - bp)) + (p - bp);
+  s.hi = t;
+  s.lo += err + e;
+}
+// a + b, renormalised
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  const float t = a.hi + b.hi;
+  const float bp = t - a.hi;
+  const float err = (a.hi - (t - bp)) + (b.hi - bp);
+  const float lo = a.lo + b.lo + err;
+  ff r;
+  r.hi = t + lo;
+  r.lo = lo - (r.hi - t);
+  return r;
+}
+// (ah, al) -= (ch, cl) (qh, ql), renormalised
+__device__ __forceinline__ void ff_msub(float& ah, float& al, float ch, float cl, float qh,
+                                        float ql) {
+  const float p = ch * qh;
+  float e = fmaf(ch, qh, -p);
+  e = fmaf(ch, ql, e);
+  e = fmaf(cl, qh, e);
+  const float t = ah - p;
+  const float bp = t - ah;
+  const float err = (ah - (t - bp)) - (p + bp);
+  const float lo = al - e + err;
+  const float hi = t + lo;
+  al = lo - (hi - t);
+  ah = hi;
+}
+// (ah, al) *= (sh, sl), renormalised
+__device__ __forceinline__ void ff_scale(float& ah, float& al, float sh, float sl) {
+  const float p = ah * sh;
+  float e = fmaf(ah, sh, -p);
+  e = fmaf(ah, sl, e);
+  e = fmaf(al, sh, e);
+  ah = p + e;
+  al = e - (ah - p);
+}
+__device__ __forceinline__ ff ff_shfl_xor(ff a, int o) {
+  ff r;
+  r.hi = __shfl_xor_sync(0xffffffffu, a.hi, o);
+  r.lo = __shfl_xor_sync(0xffffffffu, a.lo, o);
+  return r;
+}
+
+// raw [Nv][V][nd] -> W [agg][chi][Nv][rows] (float-float)
 // Sec. 3.4 step 3: chirality-split aggregate blocks of the null vectors.
-__global__ void k_mgs_gather(double2* __restrict__ W, const double2* __restrict__ raw, AggMap m,
+__global__ void k_mgs_gather(ffc* __restrict__ W, const double2* __restrict__ raw, AggMap m,
                              int nd, int nv) {
   const int half = nd / 2;
   const int rows = m.per * half;
@@ -74,169 +157,179 @@ __global__ void k_mgs_gather(double2* __restrict__ W, const double2* __restrict_
     site_coords(m.fine, s, c);
     int ag = agg_of(m, c), ls = local_of(m, c);
     int chi = a / half, ad = a - chi * half;
-    W[((size_t(ag) * 2 + chi) * nv + i) * rows + size_t(ls) * half + ad] = raw[idx];
+    W[((size_t(ag) * 2 + chi) * nv + i) * rows + size_t(ls) * half + ad] = ffc_from(raw[idx]);
   }
 }
 
-__device__ __forceinline__ double2 blk_sum2(double2 v, double2* sh) {
-  for (int o = 16; o > 0; o >>= 1) {
-    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
-    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
-  }
+// sum of one float-float value per thread over the CTA; every thread gets
+// the total (FP64).  sh: at least 32 entries.
+__device__ __forceinline__ double blk_sum_ff(ff v, ff* sh) {
+  for (int o = 16; o > 0; o >>= 1) v = ff_add(v, ff_shfl_xor(v, o));
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
   __syncthreads();
   if (l == 0) sh[w] = v;
   __syncthreads();
-  double2 r = make_double2(0.0, 0.0);
-  for (int k = 0; k < nw; ++k) {
-    r.x += sh[k].x;
-    r.y += sh[k].y;
+  if (w == 0) {
+    ff t = l < nw ? sh[l] : ff{0.f, 0.f};
+    for (int o = 16; o > 0; o >>= 1) t = ff_add(t, ff_shfl_xor(t, o));
+    if (l == 0) sh[32] = t;
   }
-  return r;
+  __syncthreads();
+  return ff_to(sh[32]);
 }
 
-// One CTA per (aggregate, chirality) block of `rows` x nv, in place, FP64.
-// Gram-Schmidt in column order.  The projection of column i on the finished
-// columns 0..i-1 is formed as one classical step (all i coefficients reduced
-// together) rather than i sequential ones: the same Q in exact arithmetic,
-// with ~8 block barriers per column instead of ~4i.  The projection is
-// repeated ("twice is enough") when the first one removed more than half of
-// the column's squared norm (the Kahan-Parlett / Daniel-Gragg-Kaufman-
-// Stewart criterion, |v'| < |v| / sqrt 2); otherwise one pass already leaves
-// the column orthogonal to the others to working precision.
+// One CTA per (aggregate, chirality) block of `rows` x nv, in place,
+// float-float (see ffc).  Gram-Schmidt in column order.  The projection of
+// column i on the finished columns 0..i-1 is formed as one classical step
+// (all i coefficients reduced together) rather than i sequential ones: the
+// same Q in exact arithmetic, with ~8 block barriers per column instead of
+// ~4i.  The projection is repeated ("twice is enough") when the first one
+// removed more than half of the column's squared norm (the Kahan-Parlett /
+// Daniel-Gragg-Kaufman-Stewart criterion, |v'| < |v| / sqrt 2); otherwise
+// one pass already leaves the column orthogonal to the others to working
+// precision.
 constexpr int kQrMaxVec = 64;
 constexpr int kQrMaxWarps = 32;
 
 // Sec. 3.4 step 3: QR of every (aggregate, chirality) block.
-template <int RPT>
-__global__ void k_block_qr(double2* __restrict__ W, int rows, int nv, int* status) {
-  __shared__ double2 sh[32];
-  __shared__ double2 part[kQrMaxWarps][kQrMaxVec];
-  __shared__ double2 coef[kQrMaxVec];
-  double2* B = W + size_t(blockIdx.x) * nv * rows;
+template <int RPT, int NT>
+__global__ void __launch_bounds__(NT) k_block_qr(ffc* __restrict__ W, int rows, int nv,
+                                                 int* status) {
+  __shared__ ff sh[33];
+  __shared__ ff part[kQrMaxWarps][kQrMaxVec][2];
+  __shared__ ffc coef[kQrMaxVec];
+  ffc* B = W + size_t(blockIdx.x) * nv * rows;
   const int T = blockDim.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = T >> 5;
+  auto norm2 = [&](const ffc* v) {
+    ff s = {0.f, 0.f};
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      ff_mac(s, v[r].rh, v[r].rl, v[r].rh, v[r].rl);
+      ff_mac(s, v[r].ih, v[r].il, v[r].ih, v[r].il);
+    }
+    return s;
+  };
   // Frobenius norm of the block for the rank test
-  double2 f = make_double2(0.0, 0.0);
+  ff f = {0.f, 0.f};
   for (size_t k = threadIdx.x; k < size_t(nv) * rows; k += T) {
-    double2 v = B[k];
-    f.x += v.x * v.x + v.y * v.y;
+    const ffc v = B[k];
+    ff_mac(f, v.rh, v.rl, v.rh, v.rl);
+    ff_mac(f, v.ih, v.il, v.ih, v.il);
   }
-  const double scale = sqrt(blk_sum2(f, sh).x);
+  const double scale = sqrt(blk_sum_ff(f, sh));
   for (int i = 0; i < nv; ++i) {
-    double2 v[RPT];
+    ffc v[RPT];
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
       int row = threadIdx.x + r * T;
-      v[r] = row < rows ? B[size_t(i) * rows + row] : make_double2(0.0, 0.0);
+      v[r] = row < rows ? B[size_t(i) * rows + row] : ffc{0.f, 0.f, 0.f, 0.f};
     }
     double n0 = 0.0;  // squared norm before the first projection
-    if (i > 0) {
-      double2 nn0 = make_double2(0.0, 0.0);
-#pragma unroll
-      for (int r = 0; r < RPT; ++r) nn0.x += v[r].x * v[r].x + v[r].y * v[r].y;
-      n0 = blk_sum2(nn0, sh).x;
-    }
+    if (i > 0) n0 = blk_sum_ff(norm2(v), sh);
     for (int pass = 0; pass < 2 && i > 0; ++pass) {
       for (int j = 0; j < i; ++j) {
-        const double2* q = B + size_t(j) * rows;
-        double2 d = make_double2(0.0, 0.0);
+        const ffc* q = B + size_t(j) * rows;
+        // d = sum conj(q) v
+        ff dr = {0.f, 0.f}, di = {0.f, 0.f};
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
           int row = threadIdx.x + r * T;
           if (row < rows) {
-            // d += conj(q) v, four FP64 FMAs (the FP64 pipe bounds this kernel)
-            double2 qv = q[row];
-            d.x = fma(qv.x, v[r].x, d.x);
-            d.x = fma(qv.y, v[r].y, d.x);
-            d.y = fma(qv.x, v[r].y, d.y);
-            d.y = fma(-qv.y, v[r].x, d.y);
+            const ffc qv = q[row];
+            ff_mac(dr, qv.rh, qv.rl, v[r].rh, v[r].rl);
+            ff_mac(dr, qv.ih, qv.il, v[r].ih, v[r].il);
+            ff_mac(di, qv.rh, qv.rl, v[r].ih, v[r].il);
+            ff_mac(di, -qv.ih, -qv.il, v[r].rh, v[r].rl);
           }
         }
         for (int o = 16; o > 0; o >>= 1) {
-          d.x += __shfl_xor_sync(0xffffffffu, d.x, o);
-          d.y += __shfl_xor_sync(0xffffffffu, d.y, o);
+          dr = ff_add(dr, ff_shfl_xor(dr, o));
+          di = ff_add(di, ff_shfl_xor(di, o));
         }
-        if (lane == 0) part[warp][j] = d;
+        if (lane == 0) {
+          part[warp][j][0] = dr;
+          part[warp][j][1] = di;
+        }
       }
       __syncthreads();
       if (threadIdx.x < i) {
-        double2 c = make_double2(0.0, 0.0);
+        ff cr = {0.f, 0.f}, ci = {0.f, 0.f};
         for (int w = 0; w < nw; ++w) {
-          c.x += part[w][threadIdx.x].x;
-          c.y += part[w][threadIdx.x].y;
+          cr = ff_add(cr, part[w][threadIdx.x][0]);
+          ci = ff_add(ci, part[w][threadIdx.x][1]);
         }
-        coef[threadIdx.x] = c;
+        coef[threadIdx.x] = ffc{cr.hi, cr.lo, ci.hi, ci.lo};
       }
       __syncthreads();
       for (int j = 0; j < i; ++j) {
-        const double2* q = B + size_t(j) * rows;
-        const double2 c = coef[j];
+        const ffc* q = B + size_t(j) * rows;
+        const ffc c = coef[j];
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
           int row = threadIdx.x + r * T;
           if (row < rows) {
-            // v -= c q, four FP64 FMAs
-            double2 qv = q[row];
-            v[r].x = fma(-c.x, qv.x, v[r].x);
-            v[r].x = fma(c.y, qv.y, v[r].x);
-            v[r].y = fma(-c.x, qv.y, v[r].y);
-            v[r].y = fma(-c.y, qv.x, v[r].y);
+            // v -= c q
+            const ffc qv = q[row];
+            ff_msub(v[r].rh, v[r].rl, c.rh, c.rl, qv.rh, qv.rl);
+            ff_msub(v[r].rh, v[r].rl, -c.ih, -c.il, qv.ih, qv.il);
+            ff_msub(v[r].ih, v[r].il, c.rh, c.rl, qv.ih, qv.il);
+            ff_msub(v[r].ih, v[r].il, c.ih, c.il, qv.rh, qv.rl);
           }
         }
       }
       __syncthreads();  // coef / part are rewritten by the next pass
-      if (pass == 0) {
-        double2 nn1 = make_double2(0.0, 0.0);
-#pragma unroll
-        for (int r = 0; r < RPT; ++r) nn1.x += v[r].x * v[r].x + v[r].y * v[r].y;
-        // the same value in every thread: the whole CTA takes the same branch
-        if (blk_sum2(nn1, sh).x >= 0.5 * n0) break;
-      }
+      // the same value in every thread: the whole CTA takes the same branch
+      if (pass == 0 && blk_sum_ff(norm2(v), sh) >= 0.5 * n0) break;
     }
-    double2 nn = make_double2(0.0, 0.0);
-#pragma unroll
-    for (int r = 0; r < RPT; ++r) nn.x += v[r].x * v[r].x + v[r].y * v[r].y;
-    double nrm = sqrt(blk_sum2(nn, sh).x);
-    double inv = 0.0;
+    const double nrm = sqrt(blk_sum_ff(norm2(v), sh));
+    float sh_inv = 0.f, sl_inv = 0.f;
     if (nrm <= 1e-12 * scale) {
       if (threadIdx.x == 0) atomicOr(status, 1);
     } else {
-      inv = 1.0 / nrm;
+      ff_split(1.0 / nrm, sh_inv, sl_inv);
     }
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
       int row = threadIdx.x + r * T;
-      if (row < rows) B[size_t(i) * rows + row] = make_double2(v[r].x * inv, v[r].y * inv);
+      if (row < rows) {
+        ffc o = v[r];
+        ff_scale(o.rh, o.rl, sh_inv, sl_inv);
+        ff_scale(o.ih, o.il, sh_inv, sl_inv);
+        B[size_t(i) * rows + row] = o;
+      }
     }
     __syncthreads();
   }
 }
 
 // QR of every (aggregate, chirality) block of W; false if a block is too tall.
-bool launch_block_qr(double2* W, int rows, int nv, int nblk, int* status, cudaStream_t st) {
-  const int threads = rows <= 256 * 16 ? 256 : 1024;
-  const int rpt = (rows + threads - 1) / threads;
-  if (rpt > 24 || nv > kQrMaxVec) return false;
-  if (rpt <= 1)
-    k_block_qr<1><<<nblk, threads, 0, st>>>(W, rows, nv, status);
-  else if (rpt <= 2)
-    k_block_qr<2><<<nblk, threads, 0, st>>>(W, rows, nv, status);
-  else if (rpt <= 4)
-    k_block_qr<4><<<nblk, threads, 0, st>>>(W, rows, nv, status);
-  else if (rpt <= 8)
-    k_block_qr<8><<<nblk, threads, 0, st>>>(W, rows, nv, status);
-  else if (rpt <= 16)
-    k_block_qr<16><<<nblk, threads, 0, st>>>(W, rows, nv, status);
+bool launch_block_qr(ffc* W, int rows, int nv, int nblk, int* status, cudaStream_t st) {
+  // 256 threads up to 4096 rows (16 rows per thread), 1024 threads beyond
+  if (nv > kQrMaxVec || rows > 1024 * 24) return false;
+  if (rows <= 256)
+    k_block_qr<1, 256><<<nblk, 256, 0, st>>>(W, rows, nv, status);
+  else if (rows <= 512)
+    k_block_qr<2, 256><<<nblk, 256, 0, st>>>(W, rows, nv, status);
+  else if (rows <= 1024)
+    k_block_qr<4, 256><<<nblk, 256, 0, st>>>(W, rows, nv, status);
+  else if (rows <= 2048)
+    k_block_qr<8, 256><<<nblk, 256, 0, st>>>(W, rows, nv, status);
+  else if (rows <= 4096)
+    k_block_qr<16, 256><<<nblk, 256, 0, st>>>(W, rows, nv, status);
+  else if (rows <= 8192)
+    k_block_qr<8, 1024><<<nblk, 1024, 0, st>>>(W, rows, nv, status);
+  else if (rows <= 16384)
+    k_block_qr<16, 1024><<<nblk, 1024, 0, st>>>(W, rows, nv, status);
   else
-    k_block_qr<24><<<nblk, threads, 0, st>>>(W, rows, nv, status);
+    k_block_qr<24, 1024><<<nblk, 1024, 0, st>>>(W, rows, nv, status);
   return true;
 }
 
 // W -> Vp [V][nd][Nv] (R)
 // Sec. 3.4 step 3: the orthonormal blocks as prolongator rows.
 template <typename R>
-__global__ void k_mgs_scatter(cpx<R>* __restrict__ Vp, const double2* __restrict__ W, AggMap m,
+__global__ void k_mgs_scatter(cpx<R>* __restrict__ Vp, const ffc* __restrict__ W, AggMap m,
                               int nd, int nv) {
   const int half = nd / 2;
   const int rows = m.per * half;
@@ -252,7 +345,7 @@ __global__ void k_mgs_scatter(cpx<R>* __restrict__ Vp, const double2* __restrict
     site_coords(m.fine, s, c);
     int ag = agg_of(m, c), ls = local_of(m, c);
     int chi = a / half, ad = a - chi * half;
-    double2 v = W[((size_t(ag) * 2 + chi) * nv + i) * rows + size_t(ls) * half + ad];
+    const double2 v = ffc_to(W[((size_t(ag) * 2 + chi) * nv + i) * rows + size_t(ls) * half + ad]);
     Vp[idx] = cpx<R>(R(v.x), R(v.y));
   }
 }
@@ -511,7 +604,7 @@ __global__ void __launch_bounds__(256) k_prolong12(cpx<Rf>* __restrict__ fine,
 
 // W [agg][chi][Nv][rows] -> out [Nv][V][nd] (FP64)
 // Sec. 3.4 step 3: orthonormal blocks back to the null-vector layout.
-__global__ void k_blocked_to_vectors(double2* __restrict__ out, const double2* __restrict__ W,
+__global__ void k_blocked_to_vectors(double2* __restrict__ out, const ffc* __restrict__ W,
                                   AggMap m, int nd, int nv) {
   const int half = nd / 2;
   const int rows = m.per * half;
@@ -526,7 +619,7 @@ __global__ void k_blocked_to_vectors(double2* __restrict__ out, const double2* _
     site_coords(m.fine, s, c);
     int ag = agg_of(m, c), ls = local_of(m, c);
     int chi = a / half, ad = a - chi * half;
-    out[idx] = W[((size_t(ag) * 2 + chi) * nv + i) * rows + size_t(ls) * half + ad];
+    out[idx] = ffc_to(W[((size_t(ag) * 2 + chi) * nv + i) * rows + size_t(ls) * half + ad]);
   }
 }
 
@@ -547,10 +640,10 @@ void block_orthonormalise(mg_ctx* c, int level, cudaStream_t st) {
   const int rows = m.per * nd / 2;
   const size_t elems = size_t(nv) * F.g.vol * nd;
   // the orthonormal vectors are kept in the aggregate-blocked layout
-  // [agg][chi][Nv][rows] in which the QR runs in place
-  F.orth64.alloc(elems * sizeof(double2));
+  // [agg][chi][Nv][rows] in which the QR runs in place (float-float, 16 B)
+  F.orth64.alloc(elems * sizeof(ffc));
   F.Vp.alloc(elems * prec_bytes_complex(F.vprec));
-  double2* W = F.orth64.as<double2>();
+  ffc* W = F.orth64.as<ffc>();
   clear_status(c, st);
   k_mgs_gather<<<grid_for(elems), 256, 0, st>>>(W, F.raw.as<double2>(), m, nd, nv);
   GB_LAUNCH_CHECK();
@@ -776,7 +869,7 @@ void nullvecs_export(mg_ctx* c, int level, void* dst, cudaStream_t st) {
   GB_REQUIRE(F.have_V, MG_ERR_STATE, "get_nullvecs: not available");
   AggMap m = make_map(F, C);
   const size_t elems = size_t(F.nvec) * F.g.vol * F.nd;
-  k_blocked_to_vectors<<<grid_for(elems), 256, 0, st>>>((double2*)dst, F.orth64.as<double2>(), m,
+  k_blocked_to_vectors<<<grid_for(elems), 256, 0, st>>>((double2*)dst, F.orth64.as<ffc>(), m,
                                                        F.nd, F.nvec);
   GB_LAUNCH_CHECK();
   c->launches++;
@@ -795,9 +888,9 @@ void nullvecs_export(mg_ctx* c, int level, void* dst, cudaStream_t st) {
 // GPU that loads this library holds until the process exits.
 namespace {
 
-constexpr size_t kNoAllocMaxElems = size_t(1) << 21;  // complex doubles: 32 MiB
+constexpr size_t kNoAllocMaxElems = size_t(1) << 21;  // 16-byte complex entries: 32 MiB
 
-static __device__ __align__(256) double2 g_noalloc_scratch[kNoAllocMaxElems];
+static __device__ __align__(256) ffc g_noalloc_scratch[kNoAllocMaxElems];
 static __device__ __align__(256) int g_noalloc_status[64];
 
 // The device address of the workspace, looked up once per device and kept
@@ -806,7 +899,7 @@ static __device__ __align__(256) int g_noalloc_status[64];
 // kept address stale; calls after such a reset are not supported.
 struct NoAllocSlot {
   bool ready = false;
-  double2* scratch = nullptr;
+  ffc* scratch = nullptr;
   int* status = nullptr;
 };
 constexpr int kNoAllocMaxDevices = 64;
@@ -841,7 +934,7 @@ extern "C" mg_status mg_block_orthonormalise_noalloc(const void* vecs_dev, void*
     vol *= (unsigned long long)dims[m];
     if (vol * (unsigned long long)ndof * (unsigned long long)nvec > kNoAllocMaxElems)
       return fail(MG_ERR_ARG,
-                  "noalloc: nvec * volume * ndof exceeds the 2^21 complex-double workspace "
+                  "noalloc: nvec * volume * ndof exceeds the 2^21-entry workspace "
                   "(32 MiB)");
   }
   const unsigned long long elems = (unsigned long long)nvec * vol * ndof;
@@ -874,7 +967,7 @@ extern "C" mg_status mg_block_orthonormalise_noalloc(const void* vecs_dev, void*
         cudaGetLastError();
         return fail(MG_ERR_CUDA, "noalloc: cudaGetSymbolAddress failed");
       }
-      s.scratch = static_cast<double2*>(p);
+      s.scratch = static_cast<ffc*>(p);
       s.status = static_cast<int*>(q);
       s.ready = true;
     }

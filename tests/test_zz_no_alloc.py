@@ -69,7 +69,7 @@ def test_noalloc_coarse_level_vectors_match_oracle_twice(gpu_lib, dims, block, n
 
 def test_noalloc_rejects_oversize_and_reports_rank(gpu_lib):
     gb = gpu_lib
-    # 2^21 complex doubles is the workspace limit: 24 x 8^4 x 24 exceeds it
+    # 2^21 complex entries is the workspace limit: 24 x 8^4 x 24 exceeds it
     big = torch.zeros((24, 8 ** 4, 24), dtype=torch.complex128, device="cuda")
     with pytest.raises(gb.MGError) as e:
         gb.mg_block_orthonormalise_noalloc(big, torch.empty_like(big), (8, 8, 8, 8), (2, 2, 2, 2))
