@@ -108,7 +108,9 @@ struct Level {
   int nvec = 0;
   int block[4] = {1, 1, 1, 1};
   DevBuf raw;                  // FP64 [Nv][V][nd] raw null vectors
-  DevBuf orth64;               // FP64 block-orthonormalised, [agg][chi][Nv][rows]
+  DevBuf orth64;               // block-orthonormalised, [agg][chi][Nv][rows], 16-byte
+                               // complex entries: float-float (orth_ff) or FP64
+  bool orth_ff = true;
   DevBuf Vp;                   // vprec [V][nd][Nv] (transfer operator layout)
   DevBuf Vp16;                 // BF16 copy of Vp for the fine-level transfers (16-bit smoother)
 

@@ -140,9 +140,16 @@ __device__ __forceinline__ ff ff_shfl_xor(ff a, int o) {
   return r;
 }
 
-// raw [Nv][V][nd] -> W [agg][chi][Nv][rows] (float-float)
+// workspace entries: float-float (the fast path) or FP64 (the fallback)
+__device__ __forceinline__ void ws_store(ffc& d, double2 v) { d = ffc_from(v); }
+__device__ __forceinline__ void ws_store(double2& d, double2 v) { d = v; }
+__device__ __forceinline__ double2 ws_load(const ffc& a) { return ffc_to(a); }
+__device__ __forceinline__ double2 ws_load(const double2& a) { return a; }
+
+// raw [Nv][V][nd] -> W [agg][chi][Nv][rows]
 // Sec. 3.4 step 3: chirality-split aggregate blocks of the null vectors.
-__global__ void k_mgs_gather(ffc* __restrict__ W, const double2* __restrict__ raw, AggMap m,
+template <typename WT>
+__global__ void k_mgs_gather(WT* __restrict__ W, const double2* __restrict__ raw, AggMap m,
                              int nd, int nv) {
   const int half = nd / 2;
   const int rows = m.per * half;
@@ -157,7 +164,135 @@ __global__ void k_mgs_gather(ffc* __restrict__ W, const double2* __restrict__ ra
     site_coords(m.fine, s, c);
     int ag = agg_of(m, c), ls = local_of(m, c);
     int chi = a / half, ad = a - chi * half;
-    W[((size_t(ag) * 2 + chi) * nv + i) * rows + size_t(ls) * half + ad] = ffc_from(raw[idx]);
+    ws_store(W[((size_t(ag) * 2 + chi) * nv + i) * rows + size_t(ls) * half + ad], raw[idx]);
+  }
+}
+
+constexpr int kQrMaxVec = 64;
+constexpr int kQrMaxWarps = 32;
+
+__device__ __forceinline__ double2 blk_sum2(double2 v, double2* sh) {
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double2 r = make_double2(0.0, 0.0);
+  for (int k = 0; k < nw; ++k) {
+    r.x += sh[k].x;
+    r.y += sh[k].y;
+  }
+  return r;
+}
+
+// Sec. 3.4 step 3: the same QR in FP64 (the fallback for blocks whose first
+// projection cancels more than float-float can carry; see k_block_qr).
+template <int RPT, int NT>
+__global__ void __launch_bounds__(NT) k_block_qr64(double2* __restrict__ W, int rows, int nv,
+                                                   int* status) {
+  __shared__ double2 sh[32];
+  __shared__ double2 part[kQrMaxWarps][kQrMaxVec];
+  __shared__ double2 coef[kQrMaxVec];
+  double2* B = W + size_t(blockIdx.x) * nv * rows;
+  const int T = blockDim.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = T >> 5;
+  // Frobenius norm of the block for the rank test
+  double2 f = make_double2(0.0, 0.0);
+  for (size_t k = threadIdx.x; k < size_t(nv) * rows; k += T) {
+    double2 v = B[k];
+    f.x += v.x * v.x + v.y * v.y;
+  }
+  const double scale = sqrt(blk_sum2(f, sh).x);
+  for (int i = 0; i < nv; ++i) {
+    double2 v[RPT];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      int row = threadIdx.x + r * T;
+      v[r] = row < rows ? B[size_t(i) * rows + row] : make_double2(0.0, 0.0);
+    }
+    double n0 = 0.0;  // squared norm before the first projection
+    if (i > 0) {
+      double2 nn0 = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) nn0.x += v[r].x * v[r].x + v[r].y * v[r].y;
+      n0 = blk_sum2(nn0, sh).x;
+    }
+    for (int pass = 0; pass < 2 && i > 0; ++pass) {
+      for (int j = 0; j < i; ++j) {
+        const double2* q = B + size_t(j) * rows;
+        double2 d = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+          int row = threadIdx.x + r * T;
+          if (row < rows) {
+            // d += conj(q) v, four FP64 FMAs (the FP64 pipe bounds this kernel)
+            double2 qv = q[row];
+            d.x = fma(qv.x, v[r].x, d.x);
+            d.x = fma(qv.y, v[r].y, d.x);
+            d.y = fma(qv.x, v[r].y, d.y);
+            d.y = fma(-qv.y, v[r].x, d.y);
+          }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          d.x += __shfl_xor_sync(0xffffffffu, d.x, o);
+          d.y += __shfl_xor_sync(0xffffffffu, d.y, o);
+        }
+        if (lane == 0) part[warp][j] = d;
+      }
+      __syncthreads();
+      if (threadIdx.x < i) {
+        double2 c = make_double2(0.0, 0.0);
+        for (int w = 0; w < nw; ++w) {
+          c.x += part[w][threadIdx.x].x;
+          c.y += part[w][threadIdx.x].y;
+        }
+        coef[threadIdx.x] = c;
+      }
+      __syncthreads();
+      for (int j = 0; j < i; ++j) {
+        const double2* q = B + size_t(j) * rows;
+        const double2 c = coef[j];
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+          int row = threadIdx.x + r * T;
+          if (row < rows) {
+            // v -= c q, four FP64 FMAs
+            double2 qv = q[row];
+            v[r].x = fma(-c.x, qv.x, v[r].x);
+            v[r].x = fma(c.y, qv.y, v[r].x);
+            v[r].y = fma(-c.x, qv.y, v[r].y);
+            v[r].y = fma(-c.y, qv.x, v[r].y);
+          }
+        }
+      }
+      __syncthreads();  // coef / part are rewritten by the next pass
+      if (pass == 0) {
+        double2 nn1 = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) nn1.x += v[r].x * v[r].x + v[r].y * v[r].y;
+        // the same value in every thread: the whole CTA takes the same branch
+        if (blk_sum2(nn1, sh).x >= 0.5 * n0) break;
+      }
+    }
+    double2 nn = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) nn.x += v[r].x * v[r].x + v[r].y * v[r].y;
+    double nrm = sqrt(blk_sum2(nn, sh).x);
+    double inv = 0.0;
+    if (nrm <= 1e-12 * scale) {
+      if (threadIdx.x == 0) atomicOr(status, 1);
+    } else {
+      inv = 1.0 / nrm;
+    }
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      int row = threadIdx.x + r * T;
+      if (row < rows) B[size_t(i) * rows + row] = make_double2(v[r].x * inv, v[r].y * inv);
+    }
+    __syncthreads();
   }
 }
 
@@ -179,7 +314,10 @@ __device__ __forceinline__ double blk_sum_ff(ff v, ff* sh) {
 }
 
 // One CTA per (aggregate, chirality) block of `rows` x nv, in place,
-// float-float (see ffc).  Gram-Schmidt in column order.  The projection of
+// float-float (see ffc).  Gram-Schmidt in column order.  Status bit 1: a
+// rank-deficient column; bit 2: a first projection that kept less than 1 %
+// of a column's norm, which float-float cannot resolve to FP64 accuracy --
+// the caller then redoes the QR in FP64 (k_block_qr64).  The projection of
 // column i on the finished columns 0..i-1 is formed as one classical step
 // (all i coefficients reduced together) rather than i sequential ones: the
 // same Q in exact arithmetic, with ~8 block barriers per column instead of
@@ -188,9 +326,6 @@ __device__ __forceinline__ double blk_sum_ff(ff v, ff* sh) {
 // Daniel-Gragg-Kaufman-Stewart criterion, |v'| < |v| / sqrt 2); otherwise
 // one pass already leaves the column orthogonal to the others to working
 // precision.
-constexpr int kQrMaxVec = 64;
-constexpr int kQrMaxWarps = 32;
-
 // Sec. 3.4 step 3: QR of every (aggregate, chirality) block.
 template <int RPT, int NT>
 __global__ void __launch_bounds__(NT) k_block_qr(ffc* __restrict__ W, int rows, int nv,
@@ -279,8 +414,15 @@ __global__ void __launch_bounds__(NT) k_block_qr(ffc* __restrict__ W, int rows, 
         }
       }
       __syncthreads();  // coef / part are rewritten by the next pass
-      // the same value in every thread: the whole CTA takes the same branch
-      if (pass == 0 && blk_sum_ff(norm2(v), sh) >= 0.5 * n0) break;
+      if (pass == 0) {
+        // the same value in every thread: the whole CTA takes the same branch
+        const double n1 = blk_sum_ff(norm2(v), sh);
+        // a first projection that keeps less than 1 % of the column's norm
+        // amplifies the float-float representation error (2^-48 of the input)
+        // past FP64 accuracy: the block is redone in FP64 (status bit 2)
+        if (n1 < 1e-4 * n0 && threadIdx.x == 0) atomicOr(status, 2);
+        if (n1 >= 0.5 * n0) break;
+      }
     }
     const double nrm = sqrt(blk_sum_ff(norm2(v), sh));
     float sh_inv = 0.f, sl_inv = 0.f;
@@ -304,32 +446,37 @@ __global__ void __launch_bounds__(NT) k_block_qr(ffc* __restrict__ W, int rows, 
 }
 
 // QR of every (aggregate, chirality) block of W; false if a block is too tall.
-bool launch_block_qr(ffc* W, int rows, int nv, int nblk, int* status, cudaStream_t st) {
-  // 256 threads up to 4096 rows (16 rows per thread), 1024 threads beyond
-  if (nv > kQrMaxVec || rows > 1024 * 24) return false;
-  if (rows <= 256)
-    k_block_qr<1, 256><<<nblk, 256, 0, st>>>(W, rows, nv, status);
-  else if (rows <= 512)
-    k_block_qr<2, 256><<<nblk, 256, 0, st>>>(W, rows, nv, status);
-  else if (rows <= 1024)
-    k_block_qr<4, 256><<<nblk, 256, 0, st>>>(W, rows, nv, status);
-  else if (rows <= 2048)
-    k_block_qr<8, 256><<<nblk, 256, 0, st>>>(W, rows, nv, status);
-  else if (rows <= 4096)
-    k_block_qr<16, 256><<<nblk, 256, 0, st>>>(W, rows, nv, status);
-  else if (rows <= 8192)
-    k_block_qr<8, 1024><<<nblk, 1024, 0, st>>>(W, rows, nv, status);
-  else if (rows <= 16384)
-    k_block_qr<16, 1024><<<nblk, 1024, 0, st>>>(W, rows, nv, status);
-  else
-    k_block_qr<24, 1024><<<nblk, 1024, 0, st>>>(W, rows, nv, status);
-  return true;
-}
+#define GB_QR_LAUNCH(KERN, WT)                                                       \
+  bool launch_##KERN(WT* W, int rows, int nv, int nblk, int* status, cudaStream_t st) { \
+    if (nv > kQrMaxVec || rows > 1024 * 24) return false;                            \
+    if (rows <= 256)                                                                  \
+      KERN<1, 256><<<nblk, 256, 0, st>>>(W, rows, nv, status);                       \
+    else if (rows <= 512)                                                             \
+      KERN<2, 256><<<nblk, 256, 0, st>>>(W, rows, nv, status);                       \
+    else if (rows <= 1024)                                                            \
+      KERN<4, 256><<<nblk, 256, 0, st>>>(W, rows, nv, status);                       \
+    else if (rows <= 2048)                                                            \
+      KERN<8, 256><<<nblk, 256, 0, st>>>(W, rows, nv, status);                       \
+    else if (rows <= 4096)                                                            \
+      KERN<16, 256><<<nblk, 256, 0, st>>>(W, rows, nv, status);                      \
+    else if (rows <= 8192)                                                            \
+      KERN<8, 1024><<<nblk, 1024, 0, st>>>(W, rows, nv, status);                     \
+    else if (rows <= 16384)                                                           \
+      KERN<16, 1024><<<nblk, 1024, 0, st>>>(W, rows, nv, status);                    \
+    else                                                                              \
+      KERN<24, 1024><<<nblk, 1024, 0, st>>>(W, rows, nv, status);                    \
+    return true;                                                                      \
+  }
+// 256 threads up to 4096 rows (16 rows per thread), 1024 threads beyond;
+// false if a block is too tall or has too many vectors
+GB_QR_LAUNCH(k_block_qr, ffc)
+GB_QR_LAUNCH(k_block_qr64, double2)
+#undef GB_QR_LAUNCH
 
 // W -> Vp [V][nd][Nv] (R)
 // Sec. 3.4 step 3: the orthonormal blocks as prolongator rows.
-template <typename R>
-__global__ void k_mgs_scatter(cpx<R>* __restrict__ Vp, const ffc* __restrict__ W, AggMap m,
+template <typename R, typename WT>
+__global__ void k_mgs_scatter(cpx<R>* __restrict__ Vp, const WT* __restrict__ W, AggMap m,
                               int nd, int nv) {
   const int half = nd / 2;
   const int rows = m.per * half;
@@ -345,7 +492,7 @@ __global__ void k_mgs_scatter(cpx<R>* __restrict__ Vp, const ffc* __restrict__ W
     site_coords(m.fine, s, c);
     int ag = agg_of(m, c), ls = local_of(m, c);
     int chi = a / half, ad = a - chi * half;
-    const double2 v = ffc_to(W[((size_t(ag) * 2 + chi) * nv + i) * rows + size_t(ls) * half + ad]);
+    const double2 v = ws_load(W[((size_t(ag) * 2 + chi) * nv + i) * rows + size_t(ls) * half + ad]);
     Vp[idx] = cpx<R>(R(v.x), R(v.y));
   }
 }
@@ -604,7 +751,8 @@ __global__ void __launch_bounds__(256) k_prolong12(cpx<Rf>* __restrict__ fine,
 
 // W [agg][chi][Nv][rows] -> out [Nv][V][nd] (FP64)
 // Sec. 3.4 step 3: orthonormal blocks back to the null-vector layout.
-__global__ void k_blocked_to_vectors(double2* __restrict__ out, const ffc* __restrict__ W,
+template <typename WT>
+__global__ void k_blocked_to_vectors(double2* __restrict__ out, const WT* __restrict__ W,
                                   AggMap m, int nd, int nv) {
   const int half = nd / 2;
   const int rows = m.per * half;
@@ -619,7 +767,7 @@ __global__ void k_blocked_to_vectors(double2* __restrict__ out, const ffc* __res
     site_coords(m.fine, s, c);
     int ag = agg_of(m, c), ls = local_of(m, c);
     int chi = a / half, ad = a - chi * half;
-    out[idx] = ffc_to(W[((size_t(ag) * 2 + chi) * nv + i) * rows + size_t(ls) * half + ad]);
+    out[idx] = ws_load(W[((size_t(ag) * 2 + chi) * nv + i) * rows + size_t(ls) * half + ad]);
   }
 }
 
@@ -640,23 +788,42 @@ void block_orthonormalise(mg_ctx* c, int level, cudaStream_t st) {
   const int rows = m.per * nd / 2;
   const size_t elems = size_t(nv) * F.g.vol * nd;
   // the orthonormal vectors are kept in the aggregate-blocked layout
-  // [agg][chi][Nv][rows] in which the QR runs in place (float-float, 16 B)
+  // [agg][chi][Nv][rows] in which the QR runs in place: float-float, or FP64
+  // when a block's first projection cancels too much (16 B either way)
   F.orth64.alloc(elems * sizeof(ffc));
   F.Vp.alloc(elems * prec_bytes_complex(F.vprec));
-  ffc* W = F.orth64.as<ffc>();
-  clear_status(c, st);
-  k_mgs_gather<<<grid_for(elems), 256, 0, st>>>(W, F.raw.as<double2>(), m, nd, nv);
-  GB_LAUNCH_CHECK();
   const int nblk = C.g.vol * 2;
   ProfScope ps(c->prof, st, "block_orth", level, double(elems) * 16.0 * 2,
                8.0 * nv * (nv - 1) * 2.0 * rows * nblk);
-  GB_REQUIRE(launch_block_qr(W, rows, nv, nblk, c->status.as<int>(), st),
+  clear_status(c, st);
+  k_mgs_gather<ffc><<<grid_for(elems), 256, 0, st>>>(F.orth64.as<ffc>(), F.raw.as<double2>(), m,
+                                                     nd, nv);
+  GB_LAUNCH_CHECK();
+  GB_REQUIRE(launch_k_block_qr(F.orth64.as<ffc>(), rows, nv, nblk, c->status.as<int>(), st),
              MG_ERR_ARG, "aggregate block too large (rows > 24576 or nvec > 64)");
   GB_LAUNCH_CHECK();
-  if (F.vprec == MG_F64)
-    k_mgs_scatter<double><<<grid_for(elems), 256, 0, st>>>(F.Vp.as<cpx<double>>(), W, m, nd, nv);
+  int qs = read_status(c, st);
+  F.orth_ff = !(qs & 2);
+  if (!F.orth_ff) {
+    clear_status(c, st);
+    k_mgs_gather<double2><<<grid_for(elems), 256, 0, st>>>(F.orth64.as<double2>(),
+                                                           F.raw.as<double2>(), m, nd, nv);
+    GB_LAUNCH_CHECK();
+    launch_k_block_qr64(F.orth64.as<double2>(), rows, nv, nblk, c->status.as<int>(), st);
+    GB_LAUNCH_CHECK();
+    qs = read_status(c, st);
+    c->launches += 2;
+  }
+  auto scatter = [&](auto* W) {
+    if (F.vprec == MG_F64)
+      k_mgs_scatter<<<grid_for(elems), 256, 0, st>>>(F.Vp.as<cpx<double>>(), W, m, nd, nv);
+    else
+      k_mgs_scatter<<<grid_for(elems), 256, 0, st>>>(F.Vp.as<cpx<float>>(), W, m, nd, nv);
+  };
+  if (F.orth_ff)
+    scatter(F.orth64.as<ffc>());
   else
-    k_mgs_scatter<float><<<grid_for(elems), 256, 0, st>>>(F.Vp.as<cpx<float>>(), W, m, nd, nv);
+    scatter(F.orth64.as<double2>());
   GB_LAUNCH_CHECK();
   c->launches += 3;
   if (level == 0 && F.vprec == MG_F32 && smoother16_enabled(c)) {
@@ -672,7 +839,7 @@ void block_orthonormalise(mg_ctx* c, int level, cudaStream_t st) {
   } else {
     F.Vp16.release();
   }
-  if (read_status(c, st) & 1) {
+  if (qs & 1) {
     F.have_V = false;
     throw Error(MG_ERR_RANK, "rank-deficient null-vector aggregate block");
   }
@@ -869,8 +1036,12 @@ void nullvecs_export(mg_ctx* c, int level, void* dst, cudaStream_t st) {
   GB_REQUIRE(F.have_V, MG_ERR_STATE, "get_nullvecs: not available");
   AggMap m = make_map(F, C);
   const size_t elems = size_t(F.nvec) * F.g.vol * F.nd;
-  k_blocked_to_vectors<<<grid_for(elems), 256, 0, st>>>((double2*)dst, F.orth64.as<ffc>(), m,
-                                                       F.nd, F.nvec);
+  if (F.orth_ff)
+    k_blocked_to_vectors<<<grid_for(elems), 256, 0, st>>>((double2*)dst, F.orth64.as<ffc>(), m,
+                                                         F.nd, F.nvec);
+  else
+    k_blocked_to_vectors<<<grid_for(elems), 256, 0, st>>>((double2*)dst, F.orth64.as<double2>(),
+                                                         m, F.nd, F.nvec);
   GB_LAUNCH_CHECK();
   c->launches++;
 }
@@ -976,23 +1147,45 @@ extern "C" mg_status mg_block_orthonormalise_noalloc(const void* vecs_dev, void*
   // the workspace keeps the previous call's contents: clear the status word
   if (cudaMemsetAsync(slot.status, 0, sizeof(int), st) != cudaSuccess)
     return fail(MG_ERR_CUDA, "noalloc: cudaMemsetAsync failed");
-  k_mgs_gather<<<grid_for(elems), 256, 0, st>>>(slot.scratch, (const double2*)vecs_dev, m, ndof,
-                                                nvec);
+  auto read_back = [&](int& h) {
+    return cudaMemcpyAsync(&h, slot.status, sizeof(int), cudaMemcpyDeviceToHost, st) ==
+               cudaSuccess &&
+           cudaStreamSynchronize(st) == cudaSuccess;
+  };
+  k_mgs_gather<ffc><<<grid_for(elems), 256, 0, st>>>(slot.scratch, (const double2*)vecs_dev, m,
+                                                     ndof, nvec);
   if (cudaGetLastError() != cudaSuccess)
     return fail(MG_ERR_CUDA, "noalloc: gather launch failed");
   const int nblk = m.coarse.vol * 2;
-  if (!launch_block_qr(slot.scratch, rows, nvec, nblk, slot.status, st))
+  if (!launch_k_block_qr(slot.scratch, rows, nvec, nblk, slot.status, st))
     return fail(MG_ERR_ARG, "noalloc: aggregate block too large for the block QR");
   if (cudaGetLastError() != cudaSuccess)
     return fail(MG_ERR_CUDA, "noalloc: block QR launch failed");
-  k_blocked_to_vectors<<<grid_for(elems), 256, 0, st>>>((double2*)out_dev, slot.scratch, m, ndof,
-                                                     nvec);
+  int h = 0;
+  if (!read_back(h)) return fail(MG_ERR_CUDA, "noalloc: status read-back failed");
+  const bool fp64 = (h & 2) != 0;
+  if (fp64) {
+    // a block's first projection cancelled more than float-float carries:
+    // the same workspace (16-byte entries) redoes the QR in FP64
+    double2* scratch64 = reinterpret_cast<double2*>(slot.scratch);
+    if (cudaMemsetAsync(slot.status, 0, sizeof(int), st) != cudaSuccess)
+      return fail(MG_ERR_CUDA, "noalloc: cudaMemsetAsync failed");
+    k_mgs_gather<double2><<<grid_for(elems), 256, 0, st>>>(scratch64, (const double2*)vecs_dev,
+                                                           m, ndof, nvec);
+    if (cudaGetLastError() != cudaSuccess)
+      return fail(MG_ERR_CUDA, "noalloc: gather launch failed");
+    launch_k_block_qr64(scratch64, rows, nvec, nblk, slot.status, st);
+    if (cudaGetLastError() != cudaSuccess)
+      return fail(MG_ERR_CUDA, "noalloc: block QR launch failed");
+    k_blocked_to_vectors<<<grid_for(elems), 256, 0, st>>>((double2*)out_dev, scratch64, m, ndof,
+                                                         nvec);
+  } else {
+    k_blocked_to_vectors<<<grid_for(elems), 256, 0, st>>>((double2*)out_dev, slot.scratch, m,
+                                                         ndof, nvec);
+  }
   if (cudaGetLastError() != cudaSuccess)
     return fail(MG_ERR_CUDA, "noalloc: scatter launch failed");
-  int h = 0;
-  if (cudaMemcpyAsync(&h, slot.status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess)
-    return fail(MG_ERR_CUDA, "noalloc: status read-back failed");
+  if (!read_back(h)) return fail(MG_ERR_CUDA, "noalloc: status read-back failed");
   if (h & 1) return fail(MG_ERR_RANK, "noalloc: rank-deficient null-vector aggregate block");
   return MG_OK;
 }
