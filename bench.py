@@ -706,6 +706,8 @@ def coarse_apply_main(args):
     del links
     torch.cuda.empty_cache()  # the FP64 link copy is not needed on the device
     nrhs = args.nrhs
+    if args.launch_choice >= 0 and nrhs > 1:  # pin the autotuner's launch shape
+        gb.mg_tune_set(f"mma2/{args.form}/n{n}/r{nrhs}/v{vol}/b1", args.launch_choice)
     shape = (vol, n) if nrhs == 1 else (vol, n, nrhs)
     x = torch.randn(shape, dtype=torch.complex64, device="cuda", generator=g)
     y = torch.empty_like(x)
@@ -721,7 +723,9 @@ def coarse_apply_main(args):
     peak, kind = peaks()
     gbs = q["bytes"] / (q["ms"] * 1e-3) / 1e9
     tflops = q["flops"] / (q["ms"] * 1e-3) / 1e12
+    choice = gb.mg_tune_get(f"mma2/{args.form}/n{n}/r{nrhs}/v{vol}/b1") if nrhs > 1 else None
     print(json.dumps({"mode": "coarse-apply", "form": args.form, "slots": args.slots,
+                      "launch_choice": choice,
                       "lattice": list(l1["dims"]),
                       "ndof": n, "nrhs": nrhs, "launches": q["launches"],
                       "us_per_apply": 1e3 * q["ms"] / q["launches"],
@@ -925,6 +929,9 @@ def main():
                              "learned", "mma-sweep", "precision"])
     ap.add_argument("--fine", default="", help="override the fine extents, e.g. 16,16,16,32")
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides (coarse-apply mode)")
+    ap.add_argument("--launch-choice", type=int, default=-1,
+                    help="pin the tensor-core apply's launch shape (coarse-apply mode, "
+                         "nrhs > 1; see mg_tune_report)")
     ap.add_argument("--nvec", type=int, default=24,
                     help="null vectors, n = 2 nvec coarse dofs (coarse-apply mode)")
     ap.add_argument("--slots", type=int, default=9, choices=[5, 9],
