@@ -203,6 +203,144 @@ __global__ void __launch_bounds__(256) k_galerkin(Op op, const cpx<R>* __restric
   }
 }
 
+// Chunked form of the same product for 2Nv = 16 TILE: the fine sites that
+// contribute to (xc, d) -- every site of the aggregate for X, the sites on
+// the face d leaves through for Y_d -- are processed CH at a time.  Per
+// chunk the CTA stages P(x) of the CH sites, then every thread computes
+// columns of T(x) = sum_e H_e(x) P(x + e) for (site, column) items (all the
+// terms of one item in one thread, so no per-term slices are needed), then
+// the 16 x 16 thread grid accumulates P(x)^dag T(x) over the chunk's
+// K = CH x nf / 2 values of each chirality in TILE x TILE register tiles.
+// Three block barriers per chunk instead of three per fine site.
+template <typename R, typename Rout, typename Op, int TILE>
+__global__ void __launch_bounds__(256) k_galerkin_chunk(Op op, const cpx<R>* __restrict__ Vp,
+                                                        AggGeom m, int nf, int nv, int CH,
+                                                        cpx<Rout>* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n2 = 2 * nv;
+  const int halff = nf / 2;
+  cpx<R>* sV = reinterpret_cast<cpx<R>*>(smem_raw);  // [CH][nf][nv]
+  cpx<R>* sT = sV + size_t(CH) * nf * nv;             // [CH][nf][n2]
+  int* s_x = reinterpret_cast<int*>(sT + size_t(CH) * nf * n2);  // [CH] fine site
+  int* s_nb = s_x + CH;                                          // [CH][9] partners
+  int* s_act = s_nb + 9 * CH;                                    // [CH][9] active terms
+  int* s_list = s_act + 9 * CH;                                  // [per] contributing sites
+  __shared__ int s_cnt;
+
+  const int xc = blockIdx.x;
+  const int d = blockIdx.y;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    int cnt = 0;
+    for (int ls = 0; ls < m.per; ++ls) {
+      int lc[4];
+      fine_site(m, xc, ls, lc);
+      if (d == 0 || leaves(m, lc, d)) s_list[cnt++] = ls;
+    }
+    s_cnt = cnt;
+  }
+  __syncthreads();
+  const int cnt = s_cnt;
+  const int r0 = (tid >> 4) * TILE, c0 = (tid & 15) * TILE;
+  const int srow = r0 / nv, i0 = r0 - srow * nv;
+  cpx<R> acc[TILE * TILE];
+#pragma unroll
+  for (int k = 0; k < TILE * TILE; ++k) acc[k] = cpx<R>(R(0), R(0));
+
+  for (int k0 = 0; k0 < cnt; k0 += CH) {
+    const int nk = min(CH, cnt - k0);
+    __syncthreads();  // the previous chunk's tiles are consumed
+    if (tid < nk) {
+      int lc[4], c[4];
+      const int x = fine_site(m, xc, s_list[k0 + tid], lc);
+      site_coords(m.fine, x, c);
+      s_x[tid] = x;
+      for (int e = 0; e < 9; ++e) {
+        s_nb[tid * 9 + e] = neighbour(m.fine, x, c, e);
+        s_act[tid * 9 + e] = (d != 0) ? (e == d) : (e == 0 || !leaves(m, lc, e));
+      }
+    }
+    __syncthreads();
+    for (int k = tid; k < nk * nf * nv; k += 256) {
+      const int sk = k / (nf * nv), r = k - sk * nf * nv;
+      sV[k] = Vp[size_t(s_x[sk]) * nf * nv + r];
+    }
+    if constexpr (Op::wilson) {
+      // items (chunk site, column): T[site][.][col] = sum_e H_e P_col(x + e)
+      for (int it = tid; it < nk * n2; it += 256) {
+        const int sk = it / n2, col = it - sk * n2;
+        const int sp = col / nv, j = col - sp * nv;
+        const int x = s_x[sk];
+        cpx<R> o[12];
+#pragma unroll
+        for (int a = 0; a < 12; ++a) o[a] = cpx<R>(R(0), R(0));
+        for (int e = 0; e < 9; ++e) {
+          if (!s_act[sk * 9 + e]) continue;
+          const int xe = s_nb[sk * 9 + e];
+          const cpx<R>* src = Vp + size_t(xe) * 12 * nv + j;
+          cpx<R> psi[12];
+#pragma unroll
+          for (int a = 0; a < 12; ++a)
+            psi[a] = ((a / 6) == sp) ? src[a * nv] : cpx<R>(R(0), R(0));
+          if (e == 0) {
+            clover_accum(op.A + size_t(x) * 72, op.diag, psi, o);
+          } else {
+            const int mu = (e - 1) >> 1;
+            const bool fwd = ((e - 1) & 1) == 0;
+            const int ls_ = fwd ? x : xe;
+            hop_accum_rt(mu, fwd, op.U + (size_t(mu) * m.fine.vol + ls_) * 9, psi, o);
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < 12; ++a) sT[(size_t(sk) * 12 + a) * n2 + col] = o[a];
+      }
+    } else {
+      // T[site][a][col] = sum_e sum_{b in chi(col)} H_e(x)[a][b] P(x+e)[b][j]
+      for (int it = tid; it < nk * nf * n2; it += 256) {
+        const int sk = it / (nf * n2), rem = it - sk * nf * n2;
+        const int col = rem / nf, a = rem - col * nf;
+        const int sp = col / nv, j = col - sp * nv;
+        const int x = s_x[sk];
+        cpx<R> t(R(0), R(0));
+        for (int e = 0; e < 9; ++e) {
+          if (!s_act[sk * 9 + e]) continue;
+          const cpx<R>* H = op.links + (size_t(x) * 9 + e) * nf * nf + a;
+          const cpx<R>* src = Vp + size_t(s_nb[sk * 9 + e]) * nf * nv + j;
+          for (int b = sp * halff; b < (sp + 1) * halff; ++b)
+            cmac(t, H[size_t(b) * nf], src[size_t(b) * nv]);
+        }
+        sT[(size_t(sk) * nf + a) * n2 + col] = t;
+      }
+    }
+    __syncthreads();
+    // acc[(s,i),(s',j)] += sum_{site, a in chi s} conj(P(x)[a][i]) T(x)[a][(s',j)]
+    for (int sk = 0; sk < nk; ++sk) {
+      const cpx<R>* Vk = sV + size_t(sk) * nf * nv;
+      const cpx<R>* Tk = sT + size_t(sk) * nf * n2;
+#pragma unroll 2
+      for (int a = srow * halff; a < (srow + 1) * halff; ++a) {
+        cpx<R> pv[TILE], tv[TILE];
+#pragma unroll
+        for (int u = 0; u < TILE; ++u) {
+          pv[u] = Vk[a * nv + i0 + u];
+          tv[u] = Tk[a * n2 + c0 + u];
+        }
+#pragma unroll
+        for (int u = 0; u < TILE; ++u)
+#pragma unroll
+          for (int w = 0; w < TILE; ++w) cmac_conj(acc[u * TILE + w], pv[u], tv[w]);
+      }
+    }
+  }
+  // internal layout [xc][d][col][row]
+  cpx<Rout>* dst = out + (size_t(xc) * 9 + d) * n2 * n2;
+#pragma unroll
+  for (int u = 0; u < TILE; ++u)
+#pragma unroll
+    for (int w = 0; w < TILE; ++w)
+      dst[size_t(c0 + w) * n2 + r0 + u] = cpx<Rout>(acc[u * TILE + w]);
+}
+
 template <typename R, typename Rout, typename Op>
 void launch_galerkin(const Op& op, const cpx<R>* Vp, const AggGeom& m, int nf, int nv,
                      cpx<Rout>* out, cudaStream_t st) {
@@ -215,13 +353,26 @@ void launch_galerkin(const Op& op, const cpx<R>* Vp, const AggGeom& m, int nf, i
     GB_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     kern<<<grid, 256, smem, st>>>(op, Vp, m, nf, nv, out);
   };
-  if (n2 == 32)
-    go(k_galerkin<R, Rout, Op, 4, 2>);
-  else if (n2 == 48)
-    go(k_galerkin<R, Rout, Op, 9, 3>);
-  else if (n2 == 64)
-    go(k_galerkin<R, Rout, Op, 16, 4>);
-  else if (per_thread <= 4)
+  // chunked kernel: as many fine sites per chunk (up to 16) as two CTAs per
+  // SM leave room for
+  if (n2 == 32 || n2 == 48 || n2 == 64) {
+    const size_t per_site = (size_t(nf) * nv + size_t(nf) * n2) * sizeof(cpx<R>) + 19 * sizeof(int);
+    const size_t budget = 110 * 1024 - size_t(m.per) * sizeof(int);
+    int CH = int(budget / per_site);
+    if (CH > 16) CH = 16;
+    if (CH < 1) CH = 1;
+    const size_t csm = size_t(CH) * per_site + size_t(m.per) * sizeof(int);
+    auto goc = [&](auto kern) {
+      GB_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(csm)));
+      kern<<<grid, 256, csm, st>>>(op, Vp, m, nf, nv, CH, out);
+    };
+    if (n2 == 32)
+      goc(k_galerkin_chunk<R, Rout, Op, 2>);
+    else if (n2 == 48)
+      goc(k_galerkin_chunk<R, Rout, Op, 3>);
+    else
+      goc(k_galerkin_chunk<R, Rout, Op, 4>);
+  } else if (per_thread <= 4)
     go(k_galerkin<R, Rout, Op, 4, 0>);
   else if (per_thread <= 9)
     go(k_galerkin<R, Rout, Op, 9, 0>);
