@@ -435,14 +435,16 @@ __global__ void __launch_bounds__(128) k_coarse_mma(const MmaBatch batch, int nr
 // stage needs.  Four warps convert the spinor rows into the 16-bit MMA
 // operand in shared memory (an SA-deep operand ring), each warp a whole
 // stage (stage q: warp q mod 4), so four stages convert at once, and
-//   warps 0-3  convert (x(nbr) -> rows j, nrhs + j of the A operand)
-//   warps 4-7  epilogue: their TMEM lane quarter -> shared memory -> y
+//   warps 0-3  convert (x(nbr) -> rows 2j, 2j + 1 of the A operand)
+//   warps 4-7  epilogue: their TMEM lane quarter -> registers -> y, the
+//              real and imaginary rows of a right-hand side paired by a
+//              lane shuffle (rows 2j, 2j + 1 sit in adjacent lanes)
 //   warp 8     lane 0 issues the bulk copies
 //   warp 9     lane 0 issues the MMAs of each stage and commits them
 // Barriers: load_full (copy bytes) and load_empty (the stage's MMAs and
 // its converting warp done) per load slot; a_full (the converting warp)
 // and a_empty (MMAs done) per operand slot; acc_full (MMAs of the
-// site done) and acc_empty (four epilogue warps done) per accumulator (two
+// site done) and acc_empty (the four epilogue warps) per accumulator (two
 // TMEM buffers of n columns, so the epilogue of one site overlaps the MMAs
 // of the next).  The A operand keeps only its 2 nrhs used rows; the MMA's
 // rows beyond them (M = 128) read whatever follows in shared memory and
@@ -469,9 +471,8 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity,
 }
 
 // Shared-memory layout of the pipelined kernel: [A ring][link ring][spinor
-// ring][epilogue rows]; the A ring comes first, so the MMA rows beyond 2 nrhs
-// of its last half slot read up to 256 n bytes past it inside the rings that
-// follow.
+// ring]; the A ring comes first, so the MMA rows beyond 2 nrhs of its last
+// half slot read up to 256 n bytes past it inside the rings that follow.
 struct WsLayout {
   uint32_t xh, ab, lb, rb, a_off, l_off, r_off, c_off, total;
 };
@@ -485,8 +486,7 @@ __host__ __device__ inline WsLayout ws_layout(int N, int KH, int nrhs, int SL, i
   w.l_off = uint32_t(SA) * w.ab;
   w.r_off = w.l_off + uint32_t(SL) * w.lb;
   w.c_off = w.r_off + uint32_t(SL) * w.rb;
-  const uint32_t cs = (uint32_t(2 * nrhs * (N + 1) * 4) + 15u) / 16u * 16u;
-  w.total = w.c_off + cs;
+  w.total = w.c_off;
   return w;
 }
 
@@ -505,7 +505,6 @@ __global__ void __launch_bounds__(kWsThreads, 3)
   __shared__ uint64_t acc_full[2], acc_empty[2], fin, stall_bar;
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int abort_sh;
-  __shared__ int epi_ok;
   // ring depths the host guarantees: 4 or 8 (multiples of the converting
   // warps, see the converter) -- any other value would break the phase rule
   if ((SL != 4 && SL != 8) || (SA != 4 && SA != 8)) {
@@ -516,7 +515,6 @@ __global__ void __launch_bounds__(kWsThreads, 3)
   unsigned char* aring = smem + lay.a_off;
   unsigned char* lring = smem + lay.l_off;
   unsigned char* rring = smem + lay.r_off;
-  float* Cs = reinterpret_cast<float*>(smem + lay.c_off);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (warp == 0) {
@@ -603,9 +601,9 @@ __global__ void __launch_bounds__(kWsThreads, 3)
               const int t = t0 + u;
               const int j = 8 * (t & ((1 << jsh) - 1)) + jl, k = 4 * (t >> jsh) + kl0;
               if (t < ntiles && j < nrhs) {
-                *reinterpret_cast<uint32_t*>(Ah + core_off(j, 2 * k, N)) =
+                *reinterpret_cast<uint32_t*>(Ah + core_off(2 * j, 2 * k, N)) =
                     pack2<BF16>(v[u].re, -v[u].im);
-                *reinterpret_cast<uint32_t*>(Ah + core_off(nrhs + j, 2 * k, N)) =
+                *reinterpret_cast<uint32_t*>(Ah + core_off(2 * j + 1, 2 * k, N)) =
                     pack2<BF16>(v[u].im, v[u].re);
               }
             }
@@ -622,40 +620,42 @@ __global__ void __launch_bounds__(kWsThreads, 3)
       }
     }
   } else if (warp < 8) {
-    // ---- epilogue
-    const int e = tid - 128, ew = e >> 5;
+    // ---- epilogue: warp ew reads TMEM lanes 32 ew.. (accumulator rows);
+    // row 2j holds Re Y[.][j], row 2j + 1 Im Y[.][j], so lanes l and l ^ 1
+    // exchange their columns and each writes every other m of its pair
+    const int ew = warp - 4;
+    const int row = 32 * ew + lane;
+    const int j = row >> 1, part = row & 1;
     uint32_t it = 0;
     for (int gs = blockIdx.x; gs < batch.total; gs += gridDim.x, ++it) {
       const uint32_t b = it & 1u, ph = (it >> 1) & 1u;
-      if (e == 0) epi_ok = wait_or_abort(&acc_full[b], ph, &abort_sh, err) ? 1 : 0;
-      asm volatile("bar.sync 1, 128;" ::: "memory");
-      if (!epi_ok) break;
+      if (!wait_or_abort(&acc_full[b], ph, &abort_sh, err)) break;
       tc_fence_after();
       const MmaLattice& cur = batch.lat[lattice_of_site(gs)];
       const int site = gs - cur.site0;
-      const int row = 32 * ew + lane;
-      if (32 * ew < 2 * nrhs) {
+      const float sc = cur.scales[site];
+      cpx<float>* ys = cur.y + size_t(site) * N * nrhs;
+      if (32 * ew < 2 * nrhs) {  // warp-uniform: the warp holds live rows
 #pragma unroll
         for (int c0 = 0; c0 < N; c0 += 16) {
           float v[16];
           tmem_ld16(tmem + (uint32_t(32 * ew) << 16) + b * 64u + uint32_t(c0), v);
-          if (row < 2 * nrhs) {
 #pragma unroll
-            for (int q2 = 0; q2 < 16; ++q2) Cs[row * CS + c0 + q2] = v[q2];
+          for (int q = 0; q < 16; q += 2) {
+            // part 0 writes m = c0 + q, part 1 writes m = c0 + q + 1
+            const float mine = part ? v[q + 1] : v[q];
+            const float give = part ? v[q] : v[q + 1];
+            const float other = __shfl_xor_sync(0xffffffffu, give, 1);
+            const int m = c0 + q + part;
+            if (row < 2 * nrhs)
+              ys[size_t(m) * nrhs + j] =
+                  part ? cpx<float>(sc * other, sc * mine) : cpx<float>(sc * mine, sc * other);
           }
         }
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[b]);
-      asm volatile("bar.sync 1, 128;" ::: "memory");
-      const float sc = cur.scales[site];
-      cpx<float>* ys = cur.y + size_t(site) * N * nrhs;
-      for (int q2 = e; q2 < N * nrhs; q2 += 128) {
-        const int m = q2 / nrhs, j = q2 - m * nrhs;
-        ys[q2] = cpx<float>(sc * Cs[j * CS + m], sc * Cs[(nrhs + j) * CS + m]);
-      }
-      asm volatile("bar.sync 1, 128;" ::: "memory");
     }
   } else if (warp == 8) {
     // ---- bulk copies: the stage's links and the neighbour's spinor rows
