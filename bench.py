@@ -794,8 +794,11 @@ def mma_sweep_main(args):
             del x, y
         mg.close()
     print(json.dumps({"mode": "mma-sweep", "peak_gbs": peak, "peak_kind": kind,
-                      "choice_code": "100 + S: pipelined kernel, S-stage ring; q <= 8: "
-                                     "register-staged kernel, q CTAs per SM",
+                      "choice_code": "10000 IL + 1000 cps + 100 KH + 10 SL + SA: pipelined "
+                                     "kernel (IL 1: interleaved rows, register epilogue; 0: "
+                                     "split rows, staged epilogue), cps CTAs per SM, KH half "
+                                     "slots per stage, SL/SA load/operand ring depths; "
+                                     "q <= 8: register-staged kernel, q CTAs per SM",
                       "rows": rows}), flush=True)
     return 0
 

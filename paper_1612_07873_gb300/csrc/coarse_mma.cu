@@ -435,10 +435,11 @@ __global__ void __launch_bounds__(128) k_coarse_mma(const MmaBatch batch, int nr
 // stage needs.  Four warps convert the spinor rows into the 16-bit MMA
 // operand in shared memory (an SA-deep operand ring), each warp a whole
 // stage (stage q: warp q mod 4), so four stages convert at once, and
-//   warps 0-3  convert (x(nbr) -> rows 2j, 2j + 1 of the A operand)
-//   warps 4-7  epilogue: their TMEM lane quarter -> registers -> y, the
-//              real and imaginary rows of a right-hand side paired by a
-//              lane shuffle (rows 2j, 2j + 1 sit in adjacent lanes)
+//   warps 0-3  convert (x(nbr) -> the real and imaginary rows of right-
+//              hand side j: rows j and nrhs + j, or 2j and 2j + 1 when IL)
+//   warps 4-7  epilogue: their TMEM lane quarter -> y; IL: in registers,
+//              the two rows of a right-hand side paired by a lane shuffle;
+//              otherwise staged as FP32 rows in shared memory
 //   warp 8     lane 0 issues the bulk copies
 //   warp 9     lane 0 issues the MMAs of each stage and commits them
 // Barriers: load_full (copy bytes) and load_empty (the stage's MMAs and
@@ -471,12 +472,13 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity,
 }
 
 // Shared-memory layout of the pipelined kernel: [A ring][link ring][spinor
-// ring]; the A ring comes first, so the MMA rows beyond 2 nrhs of its last
-// half slot read up to 256 n bytes past it inside the rings that follow.
+// ring][epilogue rows (split rows only)]; the A ring comes first, so the MMA
+// rows beyond 2 nrhs of its last half slot read up to 256 n bytes past it
+// inside the rings that follow.
 struct WsLayout {
   uint32_t xh, ab, lb, rb, a_off, l_off, r_off, c_off, total;
 };
-__host__ __device__ inline WsLayout ws_layout(int N, int KH, int nrhs, int SL, int SA) {
+__host__ __device__ inline WsLayout ws_layout(int N, int KH, int nrhs, int SL, int SA, bool IL) {
   WsLayout w;
   w.xh = uint32_t(4 * nrhs * N);                 // A operand bytes of a half slot
   w.ab = uint32_t(KH) * w.xh;                    // A operand bytes of a stage
@@ -486,11 +488,13 @@ __host__ __device__ inline WsLayout ws_layout(int N, int KH, int nrhs, int SL, i
   w.l_off = uint32_t(SA) * w.ab;
   w.r_off = w.l_off + uint32_t(SL) * w.lb;
   w.c_off = w.r_off + uint32_t(SL) * w.rb;
-  w.total = w.c_off;
+  // split rows: the epilogue stages the accumulator rows, FP32 [2 nrhs][n + 1]
+  const uint32_t cs = IL ? 0u : (uint32_t(2 * nrhs * (N + 1) * 4) + 15u) / 16u * 16u;
+  w.total = w.c_off + cs;
   return w;
 }
 
-template <bool BF16, int N, int KH>
+template <bool BF16, int N, int KH, bool IL>
 __global__ void __launch_bounds__(kWsThreads, 3)
     k_coarse_mma_ws(const MmaBatch batch, int nrhs, int SL, int SA, int* __restrict__ err) {
   constexpr int NST = 18 / KH;                         // stages per site
@@ -505,16 +509,18 @@ __global__ void __launch_bounds__(kWsThreads, 3)
   __shared__ uint64_t acc_full[2], acc_empty[2], fin, stall_bar;
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int abort_sh;
+  __shared__ int epi_ok;
   // ring depths the host guarantees: 4 or 8 (multiples of the converting
   // warps, see the converter) -- any other value would break the phase rule
   if ((SL != 4 && SL != 8) || (SA != 4 && SA != 8)) {
     if (threadIdx.x == 0) atomicOr(err, 1);
     return;
   }
-  const WsLayout lay = ws_layout(N, KH, nrhs, SL, SA);
+  const WsLayout lay = ws_layout(N, KH, nrhs, SL, SA, IL);
   unsigned char* aring = smem + lay.a_off;
   unsigned char* lring = smem + lay.l_off;
   unsigned char* rring = smem + lay.r_off;
+  float* Cs = reinterpret_cast<float*>(smem + lay.c_off);  // split rows only
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (warp == 0) {
@@ -601,9 +607,10 @@ __global__ void __launch_bounds__(kWsThreads, 3)
               const int t = t0 + u;
               const int j = 8 * (t & ((1 << jsh) - 1)) + jl, k = 4 * (t >> jsh) + kl0;
               if (t < ntiles && j < nrhs) {
-                *reinterpret_cast<uint32_t*>(Ah + core_off(2 * j, 2 * k, N)) =
+                const int rre = IL ? 2 * j : j, rim = IL ? 2 * j + 1 : nrhs + j;
+                *reinterpret_cast<uint32_t*>(Ah + core_off(rre, 2 * k, N)) =
                     pack2<BF16>(v[u].re, -v[u].im);
-                *reinterpret_cast<uint32_t*>(Ah + core_off(2 * j + 1, 2 * k, N)) =
+                *reinterpret_cast<uint32_t*>(Ah + core_off(rim, 2 * k, N)) =
                     pack2<BF16>(v[u].im, v[u].re);
               }
             }
@@ -619,10 +626,11 @@ __global__ void __launch_bounds__(kWsThreads, 3)
         }
       }
     }
-  } else if (warp < 8) {
-    // ---- epilogue: warp ew reads TMEM lanes 32 ew.. (accumulator rows);
-    // row 2j holds Re Y[.][j], row 2j + 1 Im Y[.][j], so lanes l and l ^ 1
-    // exchange their columns and each writes every other m of its pair
+  } else if (warp < 8 && IL) {
+    // ---- epilogue, interleaved rows: warp ew reads TMEM lanes 32 ew..
+    // (accumulator rows); row 2j holds Re Y[.][j], row 2j + 1 Im Y[.][j], so
+    // lanes l and l ^ 1 exchange their columns and each writes every other
+    // m of its pair -- no staging rows, no barrier between the warps
     const int ew = warp - 4;
     const int row = 32 * ew + lane;
     const int j = row >> 1, part = row & 1;
@@ -656,6 +664,43 @@ __global__ void __launch_bounds__(kWsThreads, 3)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[b]);
+    }
+  } else if (warp < 8) {
+    // ---- epilogue, split rows (row j = Re Y[.][j], row nrhs + j = Im):
+    // TMEM -> FP32 rows in shared memory -> y, all four warps storing
+    const int e = tid - 128, ew = e >> 5;
+    uint32_t it = 0;
+    for (int gs = blockIdx.x; gs < batch.total; gs += gridDim.x, ++it) {
+      const uint32_t b = it & 1u, ph = (it >> 1) & 1u;
+      if (e == 0) epi_ok = wait_or_abort(&acc_full[b], ph, &abort_sh, err) ? 1 : 0;
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (!epi_ok) break;
+      tc_fence_after();
+      const MmaLattice& cur = batch.lat[lattice_of_site(gs)];
+      const int site = gs - cur.site0;
+      const int row = 32 * ew + lane;
+      if (32 * ew < 2 * nrhs) {
+#pragma unroll
+        for (int c0 = 0; c0 < N; c0 += 16) {
+          float v[16];
+          tmem_ld16(tmem + (uint32_t(32 * ew) << 16) + b * 64u + uint32_t(c0), v);
+          if (row < 2 * nrhs) {
+#pragma unroll
+            for (int q2 = 0; q2 < 16; ++q2) Cs[row * CS + c0 + q2] = v[q2];
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[b]);
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      const float sc = cur.scales[site];
+      cpx<float>* ys = cur.y + size_t(site) * N * nrhs;
+      for (int q2 = e; q2 < N * nrhs; q2 += 128) {
+        const int m = q2 / nrhs, jj = q2 - m * nrhs;
+        ys[q2] = cpx<float>(sc * Cs[jj * CS + m], sc * Cs[(nrhs + jj) * CS + m]);
+      }
+      asm volatile("bar.sync 1, 128;" ::: "memory");
     }
   } else if (warp == 8) {
     // ---- bulk copies: the stage's links and the neighbour's spinor rows
@@ -766,8 +811,8 @@ __global__ void k_links_tile_mma(uint32_t* __restrict__ out, const cpx<float>* _
 // per stage), load-ring depth SL and operand-ring depth SA, as the tuner
 // choice 1000 + 100 KH + 10 SL + SA; 0 if its shared memory exceeds `limit`
 // or the MMA rows past the last operand stage would leave the allocation.
-bool ws_fits(int N, int KH, int nrhs, int SL, int SA, size_t limit) {
-  const WsLayout w = ws_layout(N, KH, nrhs, SL, SA);
+bool ws_fits(int N, int KH, int nrhs, int SL, int SA, bool IL, size_t limit) {
+  const WsLayout w = ws_layout(N, KH, nrhs, SL, SA, IL);
   const size_t reach = size_t(SA - 1) * w.ab + size_t(KH - 1) * w.xh + size_t(256) * N;
   return w.total <= limit && reach <= w.total;
 }
@@ -795,7 +840,7 @@ void launch_mma_batch(int* err, const MmaBatch& batch, int nrhs, cudaStream_t st
   if (per_sm > 8) per_sm = 8;
   if (per_sm < 1) per_sm = 1;
   cudaFuncAttributes fw;
-  GB_CHECK(cudaFuncGetAttributes(&fw, k_coarse_mma_ws<BF16, N, 2>));
+  GB_CHECK(cudaFuncGetAttributes(&fw, k_coarse_mma_ws<BF16, N, 2, false>));
   const size_t ws_limit = size_t(optin) - fw.sharedSizeBytes;
   // the pipelined kernel bulk-copies spinor rows: every lattice's x must
   // start on a 16-byte boundary (n nrhs 8-byte rows keep the rest aligned)
@@ -803,40 +848,43 @@ void launch_mma_batch(int* err, const MmaBatch& batch, int nrhs, cudaStream_t st
   for (int i = 0; i < batch.count; ++i)
     aligned = aligned && (reinterpret_cast<uintptr_t>(batch.lat[i].x) % 16 == 0) &&
               (reinterpret_cast<uintptr_t>(batch.lat[i].links) % 16 == 0);
-  // Autotuned launch shape: choice 1000 cps + 100 KH + 10 SL + SA is the
-  // pipelined kernel with cps persistent CTAs per SM (KH half slots per
-  // stage, SL-deep load ring, SA-deep operand ring); choice q <= 8 the
-  // register-staged kernel with q resident CTAs per SM.
+  // Autotuned launch shape: choice 10000 IL + 1000 cps + 100 KH + 10 SL + SA
+  // is the pipelined kernel with cps persistent CTAs per SM (KH half slots
+  // per stage, SL-deep load ring, SA-deep operand ring, IL = 1: interleaved
+  // accumulator rows and the register epilogue, 0: split rows staged
+  // through shared memory); choice q <= 8 the register-staged kernel with q
+  // resident CTAs per SM.
   std::vector<int> cands;
   if (aligned)
-    for (int cps : {1, 2, 3}) {
-      // shared memory of one SM split between cps CTAs (1 KB reserved each)
-      const size_t lim = std::min(ws_limit, size_t(smem_sm) / cps - 1024 - fw.sharedSizeBytes);
-      // ring depths are multiples of the four converting warps (see the
-      // kernel's comment on barrier phases)
-      for (int KH : {2, 1})
-        for (int SA : {4, 8})
-          for (int SL : {8, 4})
-            if (ws_fits(N, KH, nrhs, SL, SA, lim))
-              cands.push_back(1000 * cps + 100 * KH + 10 * SL + SA);
-    }
+    for (int IL : {0, 1})
+      for (int cps : {1, 2, 3}) {
+        // shared memory of one SM split between cps CTAs (1 KB reserved each)
+        const size_t lim = std::min(ws_limit, size_t(smem_sm) / cps - 1024 - fw.sharedSizeBytes);
+        // ring depths are multiples of the four converting warps (see the
+        // kernel's comment on barrier phases)
+        for (int KH : {2, 1})
+          for (int SA : {4, 8})
+            for (int SL : {8, 4})
+              if (ws_fits(N, KH, nrhs, SL, SA, IL != 0, lim))
+                cands.push_back(10000 * IL + 1000 * cps + 100 * KH + 10 * SL + SA);
+      }
   cands.push_back(per_sm);
   if (per_sm > 1) cands.push_back(1);
   auto launch = [&](int q) {
     if (q > 1000) {
-      const int cps = q / 1000, KH = (q / 100) % 10, SL = (q / 10) % 10, SA = q % 10;
-      const size_t sm = ws_layout(N, KH, nrhs, SL, SA).total;
+      const bool IL = q >= 10000;
+      const int cps = (q / 1000) % 10, KH = (q / 100) % 10, SL = (q / 10) % 10, SA = q % 10;
+      const size_t sm = ws_layout(N, KH, nrhs, SL, SA, IL).total;
       int grid = sms * cps;
       if (grid > batch.total) grid = batch.total;
-      if (KH == 2) {
-        auto k2 = k_coarse_mma_ws<BF16, N, 2>;
-        GB_CHECK(cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
-        k2<<<grid, kWsThreads, sm, st>>>(batch, nrhs, SL, SA, err);
-      } else {
-        auto k1 = k_coarse_mma_ws<BF16, N, 1>;
-        GB_CHECK(cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
-        k1<<<grid, kWsThreads, sm, st>>>(batch, nrhs, SL, SA, err);
-      }
+      auto go = [&](auto kern) {
+        GB_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
+        kern<<<grid, kWsThreads, sm, st>>>(batch, nrhs, SL, SA, err);
+      };
+      if (KH == 2)
+        IL ? go(k_coarse_mma_ws<BF16, N, 2, true>) : go(k_coarse_mma_ws<BF16, N, 2, false>);
+      else
+        IL ? go(k_coarse_mma_ws<BF16, N, 1, true>) : go(k_coarse_mma_ws<BF16, N, 1, false>);
       return;
     }
     int grid = sms * q;
