@@ -200,6 +200,9 @@ struct MmaLattice {
   const float* scales;
   const cpx<float>* x;
   cpx<float>* y;
+  // x already in the 16-bit operand layout, [site][half][core(row, k)]
+  // (pre-converted launches only; written by k_spinor_tile_mma)
+  unsigned char* xc;
   Geom g;
   int site0;
 };
@@ -452,6 +455,10 @@ __global__ void __launch_bounds__(128) k_coarse_mma(const MmaBatch batch, int nr
 // produce accumulator rows that are never read.  Every wait is bounded; on
 // a timeout (or the injected stall) every role stops, the copy issuer waits
 // for its copies in flight, the MMA issuer for its MMAs, and TMEM is freed.
+// PC: x arrives already converted (k_spinor_tile_mma, one streaming pass
+// before the launch); the copy issuer bulk-copies each stage's operand rows
+// into the operand ring beside its links, the converting warps idle, and
+// one barrier pair per ring slot (SA = SL) carries both.
 constexpr int kWsThreads = 320;
 constexpr int kWsMaxStages = 8;
 
@@ -478,12 +485,14 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity,
 struct WsLayout {
   uint32_t xh, ab, lb, rb, a_off, l_off, r_off, c_off, total;
 };
-__host__ __device__ inline WsLayout ws_layout(int N, int KH, int nrhs, int SL, int SA, bool IL) {
+__host__ __device__ inline WsLayout ws_layout(int N, int KH, int nrhs, int SL, int SA, bool IL,
+                                              bool PC) {
   WsLayout w;
   w.xh = uint32_t(4 * nrhs * N);                 // A operand bytes of a half slot
   w.ab = uint32_t(KH) * w.xh;                    // A operand bytes of a stage
   w.lb = uint32_t(KH) * uint32_t(2 * N * N);     // link bytes of a stage
-  w.rb = uint32_t(KH) * uint32_t((N / 2) * nrhs * 8);  // spinor bytes of a stage
+  // spinor bytes of a stage (none when the operand arrives pre-converted)
+  w.rb = PC ? 0u : uint32_t(KH) * uint32_t((N / 2) * nrhs * 8);
   w.a_off = 0;
   w.l_off = uint32_t(SA) * w.ab;
   w.r_off = w.l_off + uint32_t(SL) * w.lb;
@@ -494,7 +503,7 @@ __host__ __device__ inline WsLayout ws_layout(int N, int KH, int nrhs, int SL, i
   return w;
 }
 
-template <bool BF16, int N, int KH, bool IL>
+template <bool BF16, int N, int KH, bool IL, bool PC>
 __global__ void __launch_bounds__(kWsThreads, 3)
     k_coarse_mma_ws(const MmaBatch batch, int nrhs, int SL, int SA, int* __restrict__ err) {
   constexpr int NST = 18 / KH;                         // stages per site
@@ -516,7 +525,12 @@ __global__ void __launch_bounds__(kWsThreads, 3)
     if (threadIdx.x == 0) atomicOr(err, 1);
     return;
   }
-  const WsLayout lay = ws_layout(N, KH, nrhs, SL, SA, IL);
+  // pre-converted operands travel with the links: one ring, SA == SL
+  if ((SL != 4 && SL != 8) || (SA != 4 && SA != 8) || (PC && SA != SL)) {
+    if (threadIdx.x == 0) atomicOr(err, 1);
+    return;
+  }
+  const WsLayout lay = ws_layout(N, KH, nrhs, SL, SA, IL, PC);
   unsigned char* aring = smem + lay.a_off;
   unsigned char* lring = smem + lay.l_off;
   unsigned char* rring = smem + lay.r_off;
@@ -530,7 +544,7 @@ __global__ void __launch_bounds__(kWsThreads, 3)
   if (tid == 0) {
     for (int q = 0; q < SL; ++q) {
       mbar_init(&load_full[q], 1);
-      mbar_init(&load_empty[q], 2);  // the MMA commit + the converting warp
+      mbar_init(&load_empty[q], PC ? 1 : 2);  // the MMA commit (+ the converting warp)
     }
     for (int q = 0; q < SA; ++q) {
       mbar_init(&a_full[q], 1);
@@ -564,7 +578,9 @@ __global__ void __launch_bounds__(kWsThreads, 3)
     return li;
   };
 
-  if (warp < 4) {
+  if (warp < 4 && PC) {
+    // the operand arrives pre-converted: the converting warps idle
+  } else if (warp < 4) {
     // ---- convert: warp w converts stages w, w + 4, ...  SL and SA are
     // multiples of 4, so every ring slot is always served by the same warp:
     // when the warp waits for a slot's phase k, it has itself waited for
@@ -722,12 +738,24 @@ __global__ void __launch_bounds__(kWsThreads, 3)
             break;
           }
           const int slot = (d * KH) >> 1, h0 = (d * KH) & 1;
-          const cpx<float>* xsrc = cur.x + size_t(neighbour(cur.g, site, c, slot)) * N * nrhs +
-                                   size_t(h0) * (N / 2) * nrhs;
-          mbar_arrive_expect_tx(&load_full[sl], lay.lb + lay.rb);
-          bulk_g2s(lring + size_t(sl) * lay.lb, lsrc + size_t(d) * lay.lb, lay.lb,
-                   &load_full[sl], pol);
-          bulk_g2s(rring + size_t(sl) * lay.rb, xsrc, lay.rb, &load_full[sl], pol_x);
+          const int nb = neighbour(cur.g, site, c, slot);
+          if (PC) {
+            // the stage's operand rows, already converted: straight into
+            // the operand ring (SA == SL, so slot sl)
+            const unsigned char* asrc =
+                cur.xc + size_t(nb) * 2 * lay.xh + size_t(h0) * lay.xh;
+            mbar_arrive_expect_tx(&load_full[sl], lay.lb + lay.ab);
+            bulk_g2s(lring + size_t(sl) * lay.lb, lsrc + size_t(d) * lay.lb, lay.lb,
+                     &load_full[sl], pol);
+            bulk_g2s(aring + size_t(sl) * lay.ab, asrc, lay.ab, &load_full[sl], pol_x);
+          } else {
+            const cpx<float>* xsrc =
+                cur.x + size_t(nb) * N * nrhs + size_t(h0) * (N / 2) * nrhs;
+            mbar_arrive_expect_tx(&load_full[sl], lay.lb + lay.rb);
+            bulk_g2s(lring + size_t(sl) * lay.lb, lsrc + size_t(d) * lay.lb, lay.lb,
+                     &load_full[sl], pol);
+            bulk_g2s(rring + size_t(sl) * lay.rb, xsrc, lay.rb, &load_full[sl], pol_x);
+          }
           ++q;
         }
       }
@@ -750,7 +778,7 @@ __global__ void __launch_bounds__(kWsThreads, 3)
           const uint32_t sl = q % uint32_t(SL), lph = (q / uint32_t(SL)) & 1u;
           const uint32_t sa = q % uint32_t(SA), aph = (q / uint32_t(SA)) & 1u;
           if (!wait_or_abort(&load_full[sl], lph, &abort_sh, err) ||
-              !wait_or_abort(&a_full[sa], aph, &abort_sh, err)) {
+              (!PC && !wait_or_abort(&a_full[sa], aph, &abort_sh, err))) {
             go = false;
             break;
           }
@@ -767,7 +795,7 @@ __global__ void __launch_bounds__(kWsThreads, 3)
                       db + uint64_t((h * HB + kk * 256) >> 4), IDESC,
                       (d > 0 || h > 0 || kk > 0) ? 1u : 0u);
           mma_commit(&load_empty[sl]);
-          mma_commit(&a_empty[sa]);
+          if (!PC) mma_commit(&a_empty[sa]);
           issued = true;
         }
         if (!go) break;
@@ -782,6 +810,71 @@ __global__ void __launch_bounds__(kWsThreads, 3)
   tc_fence_before();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+}
+
+// x [site][n][nrhs] (FP32) -> the pipelined kernel's 16-bit A operand,
+// [site][half h][core(row, k)]: half h holds complex columns h n/2 .. of
+// x's n rows, each right-hand side j as two operand rows (re, -im) and
+// (im, re) -- rows j and nrhs + j, or 2j and 2j + 1 when IL -- exactly the
+// tile the converting warps would build in shared memory.  A thread takes
+// one right-hand side j and four complex columns (one 16-byte row of a core
+// matrix in each of its two rows): four loads coalesced over j, two 16-byte
+// stores; two items in flight per thread; sites in descending order.
+template <bool BF16, int N, bool IL>
+__global__ void __launch_bounds__(256) k_spinor_tile_mma(const MmaBatch batch, int nrhs) {
+  constexpr int KT = N / 8;  // 4-column groups of a half slot
+  const size_t items = size_t(batch.total) * 2 * KT * nrhs;
+  const size_t xh = size_t(4) * nrhs * N;
+  const size_t stride = size_t(gridDim.x) * blockDim.x;
+  for (size_t e0 = size_t(blockIdx.x) * blockDim.x + threadIdx.x; e0 < items; e0 += 2 * stride) {
+    cpx<float> v[2][4];
+    unsigned char* dst[2];
+    int jj[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (e0 + u * stride >= items) {
+        dst[u] = nullptr;
+        continue;
+      }
+      // last sites first: the first sites the apply reads are the ones
+      // written last, still in L2 when it starts
+      const size_t e = items - 1 - (e0 + u * stride);
+      const size_t r = e / unsigned(nrhs);
+      const int j = int(e - r * unsigned(nrhs));
+      const size_t r2 = r / KT;
+      const int kt = int(r - r2 * KT);
+      const int h = int(r2 & 1), gs = int(r2 >> 1);
+      int li = 0;
+#pragma unroll
+      for (int q = 1; q < kMaxBatch; ++q)
+        if (q < batch.count && batch.lat[q].site0 <= gs) li = q;
+      const MmaLattice& cur = batch.lat[li];
+      const int site = gs - cur.site0;
+      const cpx<float>* src = cur.x + (size_t(site) * N + h * (N / 2) + 4 * kt) * nrhs + j;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) v[u][c] = src[c * nrhs];
+      dst[u] = cur.xc + size_t(site) * 2 * xh + size_t(h) * xh + size_t(kt) * 128;
+      jj[u] = j;
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (!dst[u]) continue;
+      const int j = jj[u];
+      const int rre = IL ? 2 * j : j, rim = IL ? 2 * j + 1 : nrhs + j;
+      uint4 a, b;
+      a.x = pack2<BF16>(v[u][0].re, -v[u][0].im);
+      a.y = pack2<BF16>(v[u][1].re, -v[u][1].im);
+      a.z = pack2<BF16>(v[u][2].re, -v[u][2].im);
+      a.w = pack2<BF16>(v[u][3].re, -v[u][3].im);
+      b.x = pack2<BF16>(v[u][0].im, v[u][0].re);
+      b.y = pack2<BF16>(v[u][1].im, v[u][1].re);
+      b.z = pack2<BF16>(v[u][2].im, v[u][2].re);
+      b.w = pack2<BF16>(v[u][3].im, v[u][3].re);
+      // core_off(row, 8 kt, N) = ((row / 8) KT + kt) 128 + (row % 8) 16
+      *reinterpret_cast<uint4*>(dst[u] + size_t(rre >> 3) * KT * 128 + (rre & 7) * 16) = a;
+      *reinterpret_cast<uint4*>(dst[u] + size_t(rim >> 3) * KT * 128 + (rim & 7) * 16) = b;
+    }
+  }
 }
 
 // FP32 internal links [V][9][col k][row m] (unscaled) -> tiled 16-bit MMA
@@ -811,14 +904,20 @@ __global__ void k_links_tile_mma(uint32_t* __restrict__ out, const cpx<float>* _
 // per stage), load-ring depth SL and operand-ring depth SA, as the tuner
 // choice 1000 + 100 KH + 10 SL + SA; 0 if its shared memory exceeds `limit`
 // or the MMA rows past the last operand stage would leave the allocation.
-bool ws_fits(int N, int KH, int nrhs, int SL, int SA, bool IL, size_t limit) {
-  const WsLayout w = ws_layout(N, KH, nrhs, SL, SA, IL);
+bool ws_fits(int N, int KH, int nrhs, int SL, int SA, bool IL, bool PC, size_t limit) {
+  const WsLayout w = ws_layout(N, KH, nrhs, SL, SA, IL, PC);
   const size_t reach = size_t(SA - 1) * w.ab + size_t(KH - 1) * w.xh + size_t(256) * N;
   return w.total <= limit && reach <= w.total;
 }
 
+// Pre-converted operand buffers of a context: the newest is the largest;
+// the ones it replaced stay allocated, so a CUDA graph captured with one
+// stays valid for the context's lifetime.
+using XcPool = std::vector<std::unique_ptr<DevBuf>>;
+
 template <bool BF16, int N>
-void launch_mma_batch(int* err, const MmaBatch& batch, int nrhs, cudaStream_t st, bool tune) {
+void launch_mma_batch(int* err, const MmaBatch& batch, int nrhs, cudaStream_t st, bool tune,
+                      XcPool* pool) {
   constexpr int KS = N;
   const int smem = 2 * (128 * KS * 2) + 2 * (N * KS * 2);
   auto kern = k_coarse_mma<BF16, N>;
@@ -840,7 +939,7 @@ void launch_mma_batch(int* err, const MmaBatch& batch, int nrhs, cudaStream_t st
   if (per_sm > 8) per_sm = 8;
   if (per_sm < 1) per_sm = 1;
   cudaFuncAttributes fw;
-  GB_CHECK(cudaFuncGetAttributes(&fw, k_coarse_mma_ws<BF16, N, 2, false>));
+  GB_CHECK(cudaFuncGetAttributes(&fw, k_coarse_mma_ws<BF16, N, 2, false, false>));
   const size_t ws_limit = size_t(optin) - fw.sharedSizeBytes;
   // the pipelined kernel bulk-copies spinor rows: every lattice's x must
   // start on a 16-byte boundary (n nrhs 8-byte rows keep the rest aligned)
@@ -848,14 +947,42 @@ void launch_mma_batch(int* err, const MmaBatch& batch, int nrhs, cudaStream_t st
   for (int i = 0; i < batch.count; ++i)
     aligned = aligned && (reinterpret_cast<uintptr_t>(batch.lat[i].x) % 16 == 0) &&
               (reinterpret_cast<uintptr_t>(batch.lat[i].links) % 16 == 0);
-  // Autotuned launch shape: choice 10000 IL + 1000 cps + 100 KH + 10 SL + SA
-  // is the pipelined kernel with cps persistent CTAs per SM (KH half slots
-  // per stage, SL-deep load ring, SA-deep operand ring, IL = 1: interleaved
-  // accumulator rows and the register epilogue, 0: split rows staged
-  // through shared memory); choice q <= 8 the register-staged kernel with q
-  // resident CTAs per SM.
+  // A pre-converted launch needs a buffer of the batch's operand tiles (as
+  // large as x); it is offered only when one exists or can be made now (not
+  // while the stream is being captured).
+  const size_t xc_bytes = size_t(batch.total) * size_t(8) * nrhs * N;
+  unsigned char* xc = nullptr;
+  if (pool && aligned) {
+    if (!pool->empty() && pool->back()->bytes >= xc_bytes) {
+      xc = pool->back()->as<unsigned char>();
+    } else {
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      GB_CHECK(cudaStreamIsCapturing(st, &cs));
+      if (cs == cudaStreamCaptureStatusNone) {
+        try {
+          auto b = std::make_unique<DevBuf>();
+          b->alloc(xc_bytes);
+          pool->push_back(std::move(b));
+          xc = pool->back()->as<unsigned char>();
+        } catch (const Error&) {
+          cudaGetLastError();  // no room: offer no pre-converted launch
+        }
+      }
+    }
+  }
+  MmaBatch pbatch = batch;
+  for (int i = 0; i < pbatch.count; ++i)
+    pbatch.lat[i].xc = xc ? xc + size_t(pbatch.lat[i].site0) * 8 * nrhs * N : nullptr;
+  // Autotuned launch shape: choice 100000 PC + 10000 IL + 1000 cps + 100 KH
+  // + 10 SL + SA is the pipelined kernel with cps persistent CTAs per SM (KH
+  // half slots per stage, SL-deep load ring, SA-deep operand ring, IL = 1:
+  // interleaved accumulator rows and the register epilogue, 0: split rows
+  // staged through shared memory; PC = 1: the operand pre-converted by
+  // k_spinor_tile_mma and bulk-copied with the links, SA = SL); choice
+  // q <= 8 the register-staged kernel with q resident CTAs per SM.
   std::vector<int> cands;
-  if (aligned)
+  for (int PC : {0, 1}) {
+    if (!aligned || (PC && !xc)) continue;
     for (int IL : {0, 1})
       for (int cps : {1, 2, 3}) {
         // shared memory of one SM split between cps CTAs (1 KB reserved each)
@@ -865,26 +992,43 @@ void launch_mma_batch(int* err, const MmaBatch& batch, int nrhs, cudaStream_t st
         for (int KH : {2, 1})
           for (int SA : {4, 8})
             for (int SL : {8, 4})
-              if (ws_fits(N, KH, nrhs, SL, SA, IL != 0, lim))
-                cands.push_back(10000 * IL + 1000 * cps + 100 * KH + 10 * SL + SA);
+              if ((!PC || SA == SL) && ws_fits(N, KH, nrhs, SL, SA, IL != 0, PC != 0, lim))
+                cands.push_back(100000 * PC + 10000 * IL + 1000 * cps + 100 * KH + 10 * SL + SA);
       }
+  }
   cands.push_back(per_sm);
   if (per_sm > 1) cands.push_back(1);
   auto launch = [&](int q) {
     if (q > 1000) {
-      const bool IL = q >= 10000;
+      const bool PC = q >= 100000, IL = (q / 10000) % 10 == 1;
       const int cps = (q / 1000) % 10, KH = (q / 100) % 10, SL = (q / 10) % 10, SA = q % 10;
-      const size_t sm = ws_layout(N, KH, nrhs, SL, SA, IL).total;
+      const size_t sm = ws_layout(N, KH, nrhs, SL, SA, IL, PC).total;
       int grid = sms * cps;
       if (grid > batch.total) grid = batch.total;
+      if (PC) {
+        const size_t items = size_t(batch.total) * 2 * (N / 8) * nrhs;
+        size_t blocks = (items + 511) / 512;
+        if (blocks > size_t(sms) * 8) blocks = size_t(sms) * 8;
+        if (IL)
+          k_spinor_tile_mma<BF16, N, true><<<int(blocks), 256, 0, st>>>(pbatch, nrhs);
+        else
+          k_spinor_tile_mma<BF16, N, false><<<int(blocks), 256, 0, st>>>(pbatch, nrhs);
+      }
       auto go = [&](auto kern) {
         GB_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
-        kern<<<grid, kWsThreads, sm, st>>>(batch, nrhs, SL, SA, err);
+        kern<<<grid, kWsThreads, sm, st>>>(pbatch, nrhs, SL, SA, err);
       };
-      if (KH == 2)
-        IL ? go(k_coarse_mma_ws<BF16, N, 2, true>) : go(k_coarse_mma_ws<BF16, N, 2, false>);
-      else
-        IL ? go(k_coarse_mma_ws<BF16, N, 1, true>) : go(k_coarse_mma_ws<BF16, N, 1, false>);
+      const int form = (KH == 2 ? 4 : 0) + (IL ? 2 : 0) + (PC ? 1 : 0);
+      switch (form) {
+        case 0: go(k_coarse_mma_ws<BF16, N, 1, false, false>); break;
+        case 1: go(k_coarse_mma_ws<BF16, N, 1, false, true>); break;
+        case 2: go(k_coarse_mma_ws<BF16, N, 1, true, false>); break;
+        case 3: go(k_coarse_mma_ws<BF16, N, 1, true, true>); break;
+        case 4: go(k_coarse_mma_ws<BF16, N, 2, false, false>); break;
+        case 5: go(k_coarse_mma_ws<BF16, N, 2, false, true>); break;
+        case 6: go(k_coarse_mma_ws<BF16, N, 2, true, false>); break;
+        default: go(k_coarse_mma_ws<BF16, N, 2, true, true>); break;
+      }
       return;
     }
     int grid = sms * q;
@@ -925,7 +1069,7 @@ void launch_mma(mg_ctx* c, const Level& L, void* y, const void* x, int nrhs, cud
   b.count = 1;
   b.total = L.g.vol;
   b.stall = take_injected_stall(c);
-  launch_mma_batch<BF16, N>(c->status.as<int>() + 1, b, nrhs, st, true);
+  launch_mma_batch<BF16, N>(c->status.as<int>() + 1, b, nrhs, st, true, &c->mma_xc);
 }
 
 }  // namespace
@@ -999,9 +1143,9 @@ extern "C" mg_status mg_coarse_apply_multi(mg_ctx* const* ctxs, const int* level
     int* err = ctxs[0]->status.as<int>() + 1;
     const bool bf16 = prec == MG_BF16;
     switch (n) {
-      case 32: bf16 ? launch_mma_batch<true, 32>(err, b, nrhs, st, true) : launch_mma_batch<false, 32>(err, b, nrhs, st, true); break;
-      case 48: bf16 ? launch_mma_batch<true, 48>(err, b, nrhs, st, true) : launch_mma_batch<false, 48>(err, b, nrhs, st, true); break;
-      default: bf16 ? launch_mma_batch<true, 64>(err, b, nrhs, st, true) : launch_mma_batch<false, 64>(err, b, nrhs, st, true); break;
+      case 32: bf16 ? launch_mma_batch<true, 32>(err, b, nrhs, st, true, &ctxs[0]->mma_xc) : launch_mma_batch<false, 32>(err, b, nrhs, st, true, &ctxs[0]->mma_xc); break;
+      case 48: bf16 ? launch_mma_batch<true, 48>(err, b, nrhs, st, true, &ctxs[0]->mma_xc) : launch_mma_batch<false, 48>(err, b, nrhs, st, true, &ctxs[0]->mma_xc); break;
+      default: bf16 ? launch_mma_batch<true, 64>(err, b, nrhs, st, true, &ctxs[0]->mma_xc) : launch_mma_batch<false, 64>(err, b, nrhs, st, true, &ctxs[0]->mma_xc); break;
     }
     GB_LAUNCH_CHECK();
     for (int i = 0; i < count; ++i) ctxs[i]->launches += (i == 0);

@@ -143,6 +143,9 @@ struct mg_ctx {
   gbmg::Profiler prof;
   long long launches = 0;
   int inject_mma_stall = 0;     // fault injection: stalled tensor-core launches to come
+  // tensor-core operand tiles of multi-RHS coarse applies (pre-converted x);
+  // grown by appending, earlier buffers kept for graphs captured with them
+  std::vector<std::unique_ptr<gbmg::DevBuf>> mma_xc;
   // reductions: per-block partials and final scalars (complex double)
   gbmg::DevBuf red_partials;   // [2][nrhs][max_blocks] double2
   gbmg::DevBuf scalars;        // [SC_COUNT][kMaxNrhs] double2

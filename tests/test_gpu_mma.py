@@ -44,11 +44,12 @@ def test_coarse_apply_tensor_cores(gpu_lib, prec, cdims, nv, nrhs):
 ])
 def test_every_launch_shape_on_many_sites(gpu_lib, cdims, nv, nrhs):
     """Every candidate launch shape of the autotuner, pinned in turn: the
-    pipelined kernel (choice 10000 IL + 1000 cps + 100 KH + 10 SL + SA:
-    interleaved or split accumulator rows, cps CTAs per SM, KH half slots per
-    stage, SL-deep load ring, SA-deep operand ring) and the register-staged
-    kernel (choice = CTAs per SM), on lattices with more sites than SMs, so
-    the rings and both TMEM accumulators cycle."""
+    pipelined kernel (choice 100000 PC + 10000 IL + 1000 cps + 100 KH +
+    10 SL + SA: operand converted in the kernel or pre-converted by a
+    streaming pass, interleaved or split accumulator rows, cps CTAs per SM,
+    KH half slots per stage, SL-deep load ring, SA-deep operand ring) and the
+    register-staged kernel (choice = CTAs per SM), on lattices with more
+    sites than SMs, so the rings and both TMEM accumulators cycle."""
     gb = gpu_lib
     dims = tuple(c * 2 for c in cdims)
     mg, _ = make_ctx(gb, dims, [(2, 2, 2, 2)], [nv], prec_fine=1, prec_coarse=2)
@@ -65,8 +66,10 @@ def test_every_launch_shape_on_many_sites(gpu_lib, cdims, nv, nrhs):
     gb.mg_coarse_apply(mg.ctx, 1, y, xd, nrhs=nrhs)  # tunes: times every candidate
     gb.mg_device_status(mg.ctx)
     choices = [c for c, _ in gb.mg_tune_report(key)]
-    assert any(1000 < c < 10000 for c in choices), choices
-    assert any(c > 10000 for c in choices) and any(c <= 8 for c in choices), choices
+    pc, inkernel = [c for c in choices if c >= 100000], [c for c in choices if c < 100000]
+    assert any(1000 < c < 10000 for c in inkernel), choices
+    assert any(c > 10000 for c in inkernel) and any(c <= 8 for c in choices), choices
+    assert any(c % 100000 < 10000 for c in pc) and any(c % 100000 > 10000 for c in pc), choices
     for choice in choices:
         gb.mg_tune_set(key, choice)
         y.fill_(float("nan"))
