@@ -830,9 +830,10 @@ def wilson_policies_main(args):
         gb.mg_wilson_clover_apply_multi(mg.ctx, y, x, nvec)
         torch.cuda.synchronize()
         pick = gb.mg_tune_get(key)
-        for pol in range(12):
+        for pol in range(14):
             if (6 <= pol < 10 and nvec == 1) or (pol == 6 and nvec % 2) or (pol == 7 and nvec % 4) \
-                    or (pol in (8, 9) and nvec < 4) or (pol >= 10 and not comp["eight_real"]):
+                    or (pol in (8, 9) and nvec < 4) or (pol in (10, 11) and not comp["eight_real"]) \
+                    or (pol >= 12 and not comp["two_row"]):
                 continue
             gb.mg_tune_set(key, pol)
             for _ in range(args.warmup):

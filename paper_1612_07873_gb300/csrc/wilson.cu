@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "async_copy.cuh"
 #include "kernels.cuh"
 #include "wilson_ops.cuh"
 #include "tune.cuh"
@@ -546,6 +547,239 @@ __global__ void __launch_bounds__(128) k_wilson_tile(cpx<float>* __restrict__ ou
   }
 }
 
+
+// Tiled form: one CTA per block of BX x BY x BZ x BT sites (one thread per
+// site).  Before any arithmetic, tensor copies (TMA) bring into shared
+// memory the block's spinors, the one-site-deep faces around it (eight
+// boxes at wrapped coordinates, so every neighbour of the block is
+// present), the block's two-row links in all four directions and the links
+// on its four backward faces (the U_mu(x - mu) of the boundary sites); a
+// neighbour spinor that nine sites share is read from L2 once per block
+// instead of once per site, and no thread waits on a dependent gather.  The
+// thread's clover stays in registers across the vectors; for several
+// vectors the links stay in shared memory and only the spinor tile is
+// copied again.  Smem layout (records of 96 B spinors / 48 B links, in the
+// boxes' own order, x fastest): [interior][x-][x+][y-][y+][z-][z+][t-][t+]
+// spinors, then [link mu interior] x 4, [x-][y-][z-][t-] links.
+// Tensor maps (innermost first): spinors (24 floats, Lx, Ly, Lz, Lt nvec),
+// links (12 floats, Lx, Ly, Lz, 4 Lt) -- direction mu as time slices
+// mu Lt.. of the [mu][site] store.  Index 0: the interior box, 1 + mu: the
+// face box of direction mu (extent 1 in mu).
+struct WilsonTileMaps {
+  CUtensorMap sp[5];
+  CUtensorMap lk[5];
+};
+
+template <int BX, int BY, int BZ, int BT>
+struct WilsonBlock {
+  static constexpr int NS = BX * BY * BZ * BT;
+  __host__ __device__ static constexpr int B(int mu) {
+    return mu == 0 ? BX : mu == 1 ? BY : mu == 2 ? BZ : BT;
+  }
+  __host__ __device__ static constexpr int F(int mu) { return NS / B(mu); }  // face records
+  static constexpr int NSP = NS + 2 * (F(0) + F(1) + F(2) + F(3));  // spinor records
+  static constexpr int NLK = 4 * NS + F(0) + F(1) + F(2) + F(3);      // link records
+  static constexpr size_t SMEM = size_t(NSP) * 96 + size_t(NLK) * 48;
+  // first record of spinor face (mu, side): side 0 at x_mu - 1, 1 at x_mu + B_mu
+  __host__ __device__ static constexpr int face_sp(int mu, int side) {
+    int o = NS;
+    for (int nu = 0; nu < mu; ++nu) o += 2 * F(nu);
+    return o + side * F(mu);
+  }
+  // first record of the backward link face of mu
+  __host__ __device__ static constexpr int face_lk(int mu) {
+    int o = 4 * NS;
+    for (int nu = 0; nu < mu; ++nu) o += F(nu);
+    return o;
+  }
+};
+
+template <int BX, int BY, int BZ, int BT>
+__global__ void __launch_bounds__(BX * BY * BZ * BT, 3)
+    k_wilson_blk(cpx<float>* __restrict__ out, const float* __restrict__ A, Geom g, float diag,
+                 size_t vstride, int nvec, int antiperiodic,
+                 const __grid_constant__ WilsonTileMaps maps, int* __restrict__ err) {
+  using WB = WilsonBlock<BX, BY, BZ, BT>;
+  constexpr int NS = WB::NS;
+  extern __shared__ __align__(128) unsigned char wsm[];
+  unsigned char* sp = wsm;                          // spinor records
+  unsigned char* lk = wsm + size_t(WB::NSP) * 96;   // link records
+  __shared__ uint64_t bar;
+  const int tid = threadIdx.x;
+  const int st = tid;  // the thread's site in the block
+  // block origin and this thread's site
+  int o[4];
+  {
+    int b = blockIdx.x;
+    const int n0 = g.L[0] / BX, n1 = g.L[1] / BY, n2 = g.L[2] / BZ;
+    o[0] = (b % n0) * BX;
+    b /= n0;
+    o[1] = (b % n1) * BY;
+    b /= n1;
+    o[2] = (b % n2) * BZ;
+    o[3] = (b / n2) * BT;
+  }
+  const int l[4] = {st % BX, (st / BX) % BY, (st / (BX * BY)) % BZ, st / (BX * BY * BZ)};
+  const int lstride[4] = {1, BX, BX * BY, BX * BY * BZ};
+  const int site = (o[0] + l[0]) + g.L[0] * ((o[1] + l[1]) + g.L[1] * ((o[2] + l[2]) + g.L[2] * (o[3] + l[3])));
+  // face index of this site in the face boxes of mu (the other three
+  // coordinates, in order)
+  auto fidx = [&](int mu) {
+    int f = 0, m = 1;
+#pragma unroll
+    for (int nu = 0; nu < 4; ++nu)
+      if (nu != mu) {
+        f += l[nu] * m;
+        m *= WB::B(nu);
+      }
+    return f;
+  };
+  int nf[4], nb[4], lb[4];
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    nf[mu] = l[mu] + 1 < WB::B(mu) ? st + lstride[mu] : WB::face_sp(mu, 1) + fidx(mu);
+    nb[mu] = l[mu] > 0 ? st - lstride[mu] : WB::face_sp(mu, 0) + fidx(mu);
+    lb[mu] = l[mu] > 0 ? mu * NS + st - lstride[mu] : WB::face_lk(mu) + fidx(mu);
+  }
+  const bool tlast = antiperiodic && o[3] + l[3] == g.L[3] - 1;
+  const bool tfirst = antiperiodic && o[3] + l[3] == 0;
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  // wrapped coordinates of the faces
+  int wm[4], wp[4];
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    wm[mu] = o[mu] == 0 ? g.L[mu] - 1 : o[mu] - 1;
+    wp[mu] = o[mu] + WB::B(mu) == g.L[mu] ? 0 : o[mu] + WB::B(mu);
+  }
+  // the site's clover, loaded while the first copies are in flight
+  float clv[72];
+  {
+    const uint4* p = reinterpret_cast<const uint4*>(A + size_t(site) * 72);
+#pragma unroll
+    for (int i = 0; i < 18; ++i) reinterpret_cast<uint4*>(clv)[i] = __ldg(p + i);
+  }
+  const int Lt = g.L[3];
+  for (int v = 0; v < nvec; ++v) {
+    if (tid == 0) {
+      // the previous vector's reads of the tile are ordered before the
+      // copies that overwrite it
+      fence_proxy_async_smem();
+      const uint32_t bytes = uint32_t(WB::NSP) * 96u + (v == 0 ? uint32_t(WB::NLK) * 48u : 0u);
+      mbar_arrive_expect_tx(&bar, bytes);
+      const int tv = v * Lt;
+      tma_load_5d(sp, &maps.sp[0], 0, o[0], o[1], o[2], o[3] + tv, &bar);
+#pragma unroll
+      for (int mu = 0; mu < 4; ++mu)
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+          int c[4] = {o[0], o[1], o[2], o[3]};
+          c[mu] = side ? wp[mu] : wm[mu];
+          tma_load_5d(sp + size_t(WB::face_sp(mu, side)) * 96, &maps.sp[1 + mu], 0, c[0], c[1],
+                      c[2], c[3] + tv, &bar);
+        }
+      if (v == 0) {
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu)
+          tma_load_5d(lk + size_t(mu) * NS * 48, &maps.lk[0], 0, o[0], o[1], o[2],
+                      o[3] + mu * Lt, &bar);
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+          int c[4] = {o[0], o[1], o[2], o[3]};
+          c[mu] = wm[mu];
+          tma_load_5d(lk + size_t(WB::face_lk(mu)) * 48, &maps.lk[1 + mu], 0, c[0], c[1], c[2],
+                      c[3] + mu * Lt, &bar);
+        }
+      }
+    }
+    if (!mbar_wait(&bar, uint32_t(v & 1))) {
+      // the copies did not land within the budget: record it, give the
+      // copies in flight a second bounded wait and leave
+      if (tid == 0) {
+        atomicOr(err, 1);
+        mbar_wait(&bar, uint32_t(v & 1));
+      }
+      return;
+    }
+    cpx<float> psi[12], acc[12], u[9];
+    auto load_spinor = [&](int rec) {
+      const uint4* q = reinterpret_cast<const uint4*>(sp + size_t(rec) * 96);
+#pragma unroll
+      for (int i = 0; i < 6; ++i) reinterpret_cast<uint4*>(psi)[i] = q[i];
+    };
+    auto load_link = [&](int rec, bool neg) {
+      const uint4* q = reinterpret_cast<const uint4*>(lk + size_t(rec) * 48);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) reinterpret_cast<uint4*>(u)[i] = q[i];
+      const float sg = neg ? -1.f : 1.f;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int b = (a + 1) % 3, cc = (a + 2) % 3;
+        u[6 + a] = sg * conj(u[b] * u[3 + cc] - u[cc] * u[3 + b]);
+      }
+    };
+    load_spinor(st);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) acc[i] = cpx<float>(0.f, 0.f);
+    clover_accum(clv, diag, psi, acc);
+#define GB_BLK_HOP(MU)                         \
+  {                                            \
+    load_spinor(nf[MU]);                       \
+    load_link(MU * NS + st, MU == 3 && tlast); \
+    hop_accum<MU, true>(u, psi, acc);          \
+    load_spinor(nb[MU]);                       \
+    load_link(lb[MU], MU == 3 && tfirst);      \
+    hop_accum<MU, false>(u, psi, acc);         \
+  }
+    GB_BLK_HOP(0) GB_BLK_HOP(1) GB_BLK_HOP(2) GB_BLK_HOP(3)
+#undef GB_BLK_HOP
+    uint4* op = reinterpret_cast<uint4*>(out + size_t(v) * vstride + size_t(site) * 12);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) op[i] = reinterpret_cast<const uint4*>(acc)[i];
+    // every thread is done with the tile before the next vector's copies
+    __syncthreads();
+  }
+}
+
+// Host side of k_wilson_blk: the ten tensor maps (spinors of `in` over
+// nvec vectors stored back to back, two-row links) and the launch.
+template <int BX, int BY, int BZ, int BT>
+void launch_wilson_blk(cpx<float>* out, const cpx<float>* in, const cpx<float>* U12,
+                       const float* A, const Geom& g, float diag, size_t vstride, int nvec,
+                       int ap, int* err, cudaStream_t st) {
+  using WB = WilsonBlock<BX, BY, BZ, BT>;
+  WilsonTileMaps m;
+  const cuuint64_t X = g.L[0], Y = g.L[1], Z = g.L[2], T = g.L[3];
+  const cuuint64_t sd[5] = {24, X, Y, Z, T * cuuint64_t(nvec)};
+  const cuuint64_t ss[4] = {96, 96 * X, 96 * X * Y, 96 * X * Y * Z};
+  const cuuint64_t ld[5] = {12, X, Y, Z, 4 * T};
+  const cuuint64_t ls[4] = {48, 48 * X, 48 * X * Y, 48 * X * Y * Z};
+  const cuuint32_t box[5] = {24, BX, BY, BZ, BT};
+  const cuuint32_t lbox[5] = {12, BX, BY, BZ, BT};
+  m.sp[0] = make_map_5d(in, sd, ss, box);
+  m.lk[0] = make_map_5d(U12, ld, ls, lbox);
+  for (int mu = 0; mu < 4; ++mu) {
+    cuuint32_t fb[5] = {24, BX, BY, BZ, BT}, fl[5] = {12, BX, BY, BZ, BT};
+    fb[1 + mu] = 1;
+    fl[1 + mu] = 1;
+    m.sp[1 + mu] = make_map_5d(in, sd, ss, fb);
+    m.lk[1 + mu] = make_map_5d(U12, ld, ls, fl);
+  }
+  auto k = k_wilson_blk<BX, BY, BZ, BT>;
+  GB_CHECK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(WB::SMEM)));
+  k<<<g.vol / WB::NS, WB::NS, WB::SMEM, st>>>(out, A, g, diag, vstride, nvec, ap, m, err);
+}
+
+// the tiled form needs block-divisible extents and 16-byte aligned operands
+bool wilson_blk_ok(const Geom& g, const int b[4], const void* in, const void* U, const void* A) {
+  for (int mu = 0; mu < 4; ++mu)
+    if (g.L[mu] % b[mu]) return false;
+  return reinterpret_cast<uintptr_t>(in) % 16 == 0 && reinterpret_cast<uintptr_t>(U) % 16 == 0 &&
+         reinterpret_cast<uintptr_t>(A) % 16 == 0;
+}
 }  // namespace
 
 void fine_operator_build(mg_ctx* c, const void* gauge_ext, cudaStream_t st) {
@@ -634,8 +868,10 @@ void wilson_apply(mg_ctx* c, Vec out, Vec in, int nvec, cudaStream_t st) {
     //   8 / 9   links (stored / two-row) and clover of 32 sites staged in
     //           shared memory, warps looping over the vectors (nvec >= 4)
     //   10 / 11 8-real links, default registers / at least 4 CTAs per SM
+    //   12 / 13 tiled: a 4x4x4x2 / 4x4x2x2 block with its halo staged in
+    //           shared memory by tensor copies (two-row links)
     // Two-row and 8-real policies are candidates only when the field allows
-    // them.
+    // them; tiled ones when the extents divide into blocks.
     GB_REQUIRE(L.gauge32.p, MG_ERR_STATE, "FP32 fine operator not built");
     const unsigned gx = ceil_div(L.g.vol, 128);
     const int ap = c->p.t_antiperiodic;
@@ -647,6 +883,7 @@ void wilson_apply(mg_ctx* c, Vec out, Vec in, int nvec, cudaStream_t st) {
     auto* i = (const cpx<float>*)in.p;
     const float dg = float(L.diag);
     const unsigned gt = ceil_div(L.g.vol, 32);
+    int* err = c->status.as<int>() + 1;
     auto launch = [&](int q) {
       switch (q) {
         case 1: k_wilson<float, 12, 0><<<grid, 128, 0, st>>>(o, i, U12, A, L.g, dg, vs, nvec, ap); break;
@@ -660,12 +897,19 @@ void wilson_apply(mg_ctx* c, Vec out, Vec in, int nvec, cudaStream_t st) {
         case 9: k_wilson_tile<true><<<gt, 128, 0, st>>>(o, i, U12, A, L.g, dg, vs, nvec, ap); break;
         case 10: k_wilson<float, 8, 0><<<grid, 128, 0, st>>>(o, i, U8, A, L.g, dg, vs, nvec, ap); break;
         case 11: k_wilson<float, 8, 4><<<grid, 128, 0, st>>>(o, i, U8, A, L.g, dg, vs, nvec, ap); break;
+        case 12: launch_wilson_blk<4, 4, 4, 2>(o, i, U12, A, L.g, dg, vs, nvec, ap, err, st); break;
+        case 13: launch_wilson_blk<4, 4, 2, 2>(o, i, U12, A, L.g, dg, vs, nvec, ap, err, st); break;
         default: k_wilson<float, 18, 0><<<grid, 128, 0, st>>>(o, i, U18, A, L.g, dg, vs, nvec, ap); break;
       }
     };
     std::vector<int> cands = {0, 2};
     if (L.gauge12_ok) cands.insert(cands.end(), {1, 3, 4, 5});
     if (L.gauge8_ok) cands.insert(cands.end(), {10, 11});
+    if (L.gauge12_ok) {
+      const int b12[4] = {4, 4, 4, 2}, b13[4] = {4, 4, 2, 2};
+      if (wilson_blk_ok(L.g, b12, i, U12, A)) cands.push_back(12);
+      if (wilson_blk_ok(L.g, b13, i, U12, A)) cands.push_back(13);
+    }
     if (nvec % 2 == 0) cands.push_back(6);
     if (nvec % 4 == 0) cands.push_back(7);
     if (nvec >= 4) {

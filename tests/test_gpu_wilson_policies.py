@@ -128,3 +128,77 @@ def test_apply_multi(gpu_lib, nrhs):
     with pytest.raises(gb.MGError):
         gb.mg_wilson_clover_apply_multi(mg.ctx, out, out, nrhs)
     mg.close()
+
+
+TILED = [12, 13]   # 4x4x4x2 / 4x4x2x2 block, its halo staged by tensor copies
+
+
+@pytest.mark.parametrize("antiperiodic", [1, 0])
+@pytest.mark.parametrize("dims", [(4, 4, 4, 8), (8, 4, 4, 6), (4, 8, 8, 4)])
+@pytest.mark.parametrize("policy", TILED)
+def test_tiled_policy(gpu_lib, policy, dims, antiperiodic):
+    """The block-tiled operator: every site of a block reads its neighbours
+    from the shared-memory tile (block interior plus one-site faces copied
+    at wrapped coordinates) -- lattices whose extent equals the block's
+    (the faces wrap onto the block itself) and several blocks per extent;
+    both time boundaries."""
+    gb = gpu_lib
+    vol = lat.volume(dims)
+    key = f"wilson/v{vol}/n1/c1"
+    gb.mg_tune_set(key, policy)
+    mg, U = make_ctx(gb, dims, [(2, 2, 2, 2)], [2], prec_fine=1, prec_coarse=1,
+                     antiperiodic=antiperiodic, eps=0.5)
+    psi = syn.gaussian_field((vol, 12), 76)
+    out = torch.full((vol, 12), float("nan"), dtype=torch.complex64, device="cuda")
+    gb.mg_wilson_clover_apply(mg.ctx, out, to_dev(psi, torch.complex64))
+    gb.mg_device_status(mg.ctx)
+    assert gb.mg_tune_get(key) == policy
+    op = dirac.wilson_clover_op(U, dims, -0.2, 1.0, antiperiodic=bool(antiperiodic))
+    err = rel_l2(to_np(out), op.apply(psi))
+    assert err < 1e-5, (policy, err)
+    gb.mg_tune_set(key, -1)
+    mg.close()
+
+
+@pytest.mark.parametrize("nrhs", [3, 8])
+@pytest.mark.parametrize("policy", TILED)
+def test_tiled_policy_many_vectors(gpu_lib, policy, nrhs):
+    """Several vectors in one tiled launch: the links stay in shared memory,
+    the spinor tile is copied again for every vector (the copies of vector
+    v + 1 wait until every thread has finished with vector v)."""
+    gb = gpu_lib
+    dims = (8, 4, 4, 6)
+    vol = lat.volume(dims)
+    key = f"wilson/v{vol}/n{nrhs}/c1"
+    gb.mg_tune_set(key, policy)
+    mg, U = make_ctx(gb, dims, [(2, 2, 2, 2)], [2], prec_fine=1, prec_coarse=1, eps=0.5)
+    psi = syn.gaussian_field((nrhs, vol, 12), 77)
+    out = torch.full(psi.shape, float("nan"), dtype=torch.complex64, device="cuda")
+    gb.mg_wilson_clover_apply_multi(mg.ctx, out, to_dev(psi, torch.complex64), nrhs)
+    gb.mg_device_status(mg.ctx)
+    assert gb.mg_tune_get(key) == policy
+    op = oracle_fine(U, dims)
+    err = rel_l2(to_np(out), np.stack([op.apply(p) for p in psi]))
+    assert err < 1e-5, (policy, err)
+    gb.mg_tune_set(key, -1)
+    mg.close()
+
+
+@pytest.mark.parametrize("policy", TILED)
+def test_tiled_policy_in_setup(gpu_lib, policy):
+    gb = gpu_lib
+    dims, nv, sweeps = (4, 4, 4, 8), 4, 3
+    vol = lat.volume(dims)
+    gb.mg_tune_set(f"wilson/v{vol}/n{nv}/c1", policy)
+    mg, U = make_ctx(gb, dims, [(2, 2, 2, 2)], [nv], sweeps=sweeps, prec_fine=1,
+                     prec_coarse=1)
+    x0 = syn.gaussian_field((nv, vol, 12), 78)
+    gb.mg_setup_nullvecs(mg.ctx, 0, to_dev(x0))
+    raw = torch.empty((nv, vol, 12), dtype=torch.complex128, device="cuda")
+    gb.mg_get_nullvecs(mg.ctx, 0, raw, kind=0)
+    gb.mg_device_status(mg.ctx)
+    assert gb.mg_tune_get(f"wilson/v{vol}/n{nv}/c1") == policy
+    err = rel_l2(to_np(raw), mgo.null_vectors(oracle_fine(U, dims), x0, sweeps))
+    assert err < 1e-5, (policy, err)
+    gb.mg_tune_set(f"wilson/v{vol}/n{nv}/c1", -1)
+    mg.close()
