@@ -211,7 +211,8 @@ __global__ void __launch_bounds__(256) k_galerkin(Op op, const cpx<R>* __restric
 // terms of one item in one thread, so no per-term slices are needed), then
 // the 16 x 16 thread grid accumulates P(x)^dag T(x) over the chunk's
 // K = CH x nf / 2 values of each chirality in TILE x TILE register tiles.
-// Three block barriers per chunk instead of three per fine site.
+// Three block barriers per chunk instead of three per fine site; the
+// contributing sites are enumerated from their index (no serial list).
 template <typename R, typename Rout, typename Op, int TILE>
 __global__ void __launch_bounds__(256) k_galerkin_chunk(Op op, const cpx<R>* __restrict__ Vp,
                                                         AggGeom m, int nf, int nv, int CH,
@@ -224,23 +225,32 @@ __global__ void __launch_bounds__(256) k_galerkin_chunk(Op op, const cpx<R>* __r
   int* s_x = reinterpret_cast<int*>(sT + size_t(CH) * nf * n2);  // [CH] fine site
   int* s_nb = s_x + CH;                                          // [CH][9] partners
   int* s_act = s_nb + 9 * CH;                                    // [CH][9] active terms
-  int* s_list = s_act + 9 * CH;                                  // [per] contributing sites
-  __shared__ int s_cnt;
-
   const int xc = blockIdx.x;
   const int d = blockIdx.y;
   const int tid = threadIdx.x;
-  if (tid == 0) {
-    int cnt = 0;
-    for (int ls = 0; ls < m.per; ++ls) {
-      int lc[4];
-      fine_site(m, xc, ls, lc);
-      if (d == 0 || leaves(m, lc, d)) s_list[cnt++] = ls;
+  // contributing fine sites: every site of the aggregate for X (d = 0);
+  // for Y_d the face that d leaves through (x_mu = b_mu - 1 forward, 0
+  // backward), enumerated over the other three coordinates in order
+  const int dmu = d > 0 ? (d - 1) >> 1 : 0;
+  const bool dfwd = d > 0 && ((d - 1) & 1) == 0;
+  // (a select, not m.b[dmu]: a kernel-parameter array indexed at run time
+  // would be copied to the stack)
+  const int bmu = dmu == 0 ? m.b[0] : dmu == 1 ? m.b[1] : dmu == 2 ? m.b[2] : m.b[3];
+  const int cnt = d == 0 ? m.per : m.per / bmu;
+  auto contrib_ls = [&](int q) {
+    if (d == 0) return q;
+    int lc[4];
+#pragma unroll
+    for (int nu = 0; nu < 4; ++nu) {
+      if (nu == dmu) {
+        lc[nu] = dfwd ? m.b[nu] - 1 : 0;
+      } else {
+        lc[nu] = q % m.b[nu];
+        q /= m.b[nu];
+      }
     }
-    s_cnt = cnt;
-  }
-  __syncthreads();
-  const int cnt = s_cnt;
+    return lc[0] + m.b[0] * (lc[1] + m.b[1] * (lc[2] + m.b[2] * lc[3]));
+  };
   const int r0 = (tid >> 4) * TILE, c0 = (tid & 15) * TILE;
   const int srow = r0 / nv, i0 = r0 - srow * nv;
   cpx<R> acc[TILE * TILE];
@@ -250,11 +260,14 @@ __global__ void __launch_bounds__(256) k_galerkin_chunk(Op op, const cpx<R>* __r
   for (int k0 = 0; k0 < cnt; k0 += CH) {
     const int nk = min(CH, cnt - k0);
     __syncthreads();  // the previous chunk's tiles are consumed
+    // one thread per chunk site: the site, its partner across each term and
+    // whether the term contributes to this block
     if (tid < nk) {
       int lc[4], c[4];
-      const int x = fine_site(m, xc, s_list[k0 + tid], lc);
+      const int x = fine_site(m, xc, contrib_ls(k0 + tid), lc);
       site_coords(m.fine, x, c);
       s_x[tid] = x;
+#pragma unroll
       for (int e = 0; e < 9; ++e) {
         s_nb[tid * 9 + e] = neighbour(m.fine, x, c, e);
         s_act[tid * 9 + e] = (d != 0) ? (e == d) : (e == 0 || !leaves(m, lc, e));
@@ -283,7 +296,11 @@ __global__ void __launch_bounds__(256) k_galerkin_chunk(Op op, const cpx<R>* __r
           for (int a = 0; a < 12; ++a)
             psi[a] = ((a / 6) == sp) ? src[a * nv] : cpx<R>(R(0), R(0));
           if (e == 0) {
-            clover_accum(op.A + size_t(x) * 72, op.diag, psi, o);
+            // the column lives on chirality sp: only that clover block acts
+            if (sp == 0)
+              clover_block_accum(op.A + size_t(x) * 72, op.diag, psi, o);
+            else
+              clover_block_accum(op.A + size_t(x) * 72 + 36, op.diag, psi + 6, o + 6);
           } else {
             const int mu = (e - 1) >> 1;
             const bool fwd = ((e - 1) & 1) == 0;
@@ -357,11 +374,11 @@ void launch_galerkin(const Op& op, const cpx<R>* Vp, const AggGeom& m, int nf, i
   // SM leave room for
   if (n2 == 32 || n2 == 48 || n2 == 64) {
     const size_t per_site = (size_t(nf) * nv + size_t(nf) * n2) * sizeof(cpx<R>) + 19 * sizeof(int);
-    const size_t budget = 110 * 1024 - size_t(m.per) * sizeof(int);
+    const size_t budget = 110 * 1024;
     int CH = int(budget / per_site);
     if (CH > 16) CH = 16;
     if (CH < 1) CH = 1;
-    const size_t csm = size_t(CH) * per_site + size_t(m.per) * sizeof(int);
+    const size_t csm = size_t(CH) * per_site;
     auto goc = [&](auto kern) {
       GB_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(csm)));
       kern<<<grid, 256, csm, st>>>(op, Vp, m, nf, nv, CH, out);
