@@ -240,7 +240,11 @@ __global__ void __launch_bounds__(CG*(N / Unpack<S>::RPC))
   __syncthreads();
   const int rp = tid % TPC;
   const int cg = tid / TPC;
-  // forward: X and Y_{+mu}(site)
+  // forward: X and Y_{+mu}(site).  The four Y_{+mu} blocks are read again
+  // by the +mu neighbours' CTAs (their backward terms): kept in L2 with an
+  // evict-last policy; X, read once, and the backward reads (the last use)
+  // evict first.
+  const uint64_t keep = l2_policy_evict_last(), drop = l2_policy_evict_first();
   cpx<R> acc[RPC];
 #pragma unroll
   for (int r = 0; r < RPC; ++r) acc[r] = cpx<R>(R(0), R(0));
@@ -248,7 +252,10 @@ __global__ void __launch_bounds__(CG*(N / Unpack<S>::RPC))
   for (int it = 0; it < ITER; it += U) {
     uint4 v[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) v[u] = ld_stream16(L + size_t(cg + (it + u) * CG) * TPC);
+    for (int u = 0; u < U; ++u) {
+      const int k = cg + (it + u) * CG;
+      v[u] = ld_stream16_hint(L + size_t(k) * TPC, k < N ? drop : keep);
+    }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       cpx<R> e[RPC];
@@ -268,7 +275,7 @@ __global__ void __launch_bounds__(CG*(N / Unpack<S>::RPC))
                      (size_t(nb[2 + 2 * mu]) * 5 + 1 + mu) * N * TPC + rp;
     uint4 v[CPT];
 #pragma unroll
-    for (int i = 0; i < CPT; ++i) v[i] = __ldg(F + size_t(cg + CG * i) * TPC);
+    for (int i = 0; i < CPT; ++i) v[i] = ld_stream16_hint(F + size_t(cg + CG * i) * TPC, drop);
 #pragma unroll
     for (int i = 0; i < CPT; ++i) {
       cpx<R> e[RPC];
