@@ -97,8 +97,11 @@ __global__ void __launch_bounds__(CG*(N / Unpack<S>::RPC))
 // NR x RPC complex multiply-adds.  The gathered neighbour values sit in
 // shared memory as xs[k][r] (k = slot*n + col); the same buffer then holds
 // the CG partial sums as red[cg][r][row].
+// UM caps the 16-byte link loads a thread keeps in flight (the batch U
+// divides the K / CG columns it walks); a larger batch takes registers
+// from occupancy, so the autotuner picks it per shape.
 // Eq. (3) on NR right-hand sides per link read.
-template <typename S, int N, int CG, int NR>
+template <typename S, int N, int CG, int NR, int UM = 4>
 __global__ void __launch_bounds__(CG*(N / Unpack<S>::RPC))
     k_coarse_stream_mr(cpx<typename StoreTraits<S>::real>* __restrict__ y,
                        const cpx<typename StoreTraits<S>::real>* __restrict__ x,
@@ -110,7 +113,7 @@ __global__ void __launch_bounds__(CG*(N / Unpack<S>::RPC))
   constexpr int K = 9 * N;
   constexpr int NT = CG * TPC;
   constexpr int ITER = K / CG;
-  constexpr int U = batch_of(ITER, 4);
+  constexpr int U = batch_of(ITER, UM);
   constexpr int XS = K * NR, RED = CG * NR * N;
   static_assert(N % RPC == 0 && K % CG == 0 && NR % 2 == 0 && ITER % U == 0, "tile shape");
   __shared__ __align__(16) cpx<R> buf[XS > RED ? XS : RED];
@@ -510,10 +513,33 @@ void launch_stream_mr(const Level& L, void* y, const void* x, const void* links,
   const S* lp = (const S*)links;
   const size_t rs = blocked ? size_t(L.g.vol) * N : 1;
   const size_t ss = blocked ? 1 : size_t(nrhs);
-  if (nrhs % 8 == 0)
-    k_coarse_stream_mr<S, N, CG, 8><<<dim3(nrhs / 8, L.g.vol), NT, 0, st>>>(
-        yp, xp, lp, L.scales.as<float>(), L.g, rs, ss);
-  else if (nrhs % 4 == 0)
+  if (nrhs % 8 == 0) {
+    // 8 right-hand sides per link read: the load batch is tuned (choice =
+    // its cap UM; caps giving the same batch are one candidate)
+    constexpr int ITER = 9 * N / CG;
+    std::vector<int> cands{4};
+    if (!std::is_same<S, cpx<double>>::value) {
+      if (batch_of(ITER, 6) != batch_of(ITER, 4)) cands.push_back(6);
+      if (batch_of(ITER, 9) != batch_of(ITER, 6) && batch_of(ITER, 9) != batch_of(ITER, 4))
+        cands.push_back(9);
+    }
+    auto launch = [&](int um) {
+      const dim3 grid(nrhs / 8, L.g.vol);
+      if (um == 9)
+        k_coarse_stream_mr<S, N, CG, 8, 9><<<grid, NT, 0, st>>>(yp, xp, lp, L.scales.as<float>(),
+                                                                 L.g, rs, ss);
+      else if (um == 6)
+        k_coarse_stream_mr<S, N, CG, 8, 6><<<grid, NT, 0, st>>>(yp, xp, lp, L.scales.as<float>(),
+                                                                 L.g, rs, ss);
+      else
+        k_coarse_stream_mr<S, N, CG, 8, 4><<<grid, NT, 0, st>>>(yp, xp, lp, L.scales.as<float>(),
+                                                                 L.g, rs, ss);
+    };
+    const std::string key = "stream_mr/p" + std::to_string(int(L.prec)) + "/n" +
+                            std::to_string(N) + "/v" + std::to_string(L.g.vol) + "/r" +
+                            std::to_string(nrhs) + "/b" + std::to_string(int(blocked));
+    launch(cands.size() == 1 ? cands.front() : Tuner::get().choose(key, cands, st, launch));
+  } else if (nrhs % 4 == 0)
     k_coarse_stream_mr<S, N, CG, 4><<<dim3(nrhs / 4, L.g.vol), NT, 0, st>>>(
         yp, xp, lp, L.scales.as<float>(), L.g, rs, ss);
   else

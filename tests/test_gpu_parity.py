@@ -111,6 +111,39 @@ def test_coarse_apply_multi_rhs(gpu_lib, cdims, nv, nrhs):
     mg.close()
 
 
+@pytest.mark.parametrize("cdims,nv,nrhs", [((4, 4, 2, 4), 24, 8), ((2, 2, 4, 2), 16, 16),
+                                           ((2, 4, 2, 2), 32, 8)])
+def test_coarse_apply_multi_rhs_every_load_batch(gpu_lib, cdims, nv, nrhs):
+    """The FP32 multi-RHS stream at 8 right-hand sides per link read, every
+    load batch the autotuner offers pinned in turn (choice = the cap on the
+    16-byte link loads a thread keeps in flight)."""
+    gb = gpu_lib
+    dims = tuple(c * 2 for c in cdims)
+    mg, U = make_ctx(gb, dims, [(2, 2, 2, 2)], [nv], prec_fine=1, prec_coarse=1)
+    n, vol = 2 * nv, lat.volume(cdims)
+    links = _random_links(vol, n, 15)
+    gb.mg_set_coarse_links(mg.ctx, 1, to_dev(links))
+    x = syn.gaussian_field((vol, n, nrhs), 16)
+    xd = to_dev(x, torch.complex64)
+    y = torch.empty((vol, n, nrhs), dtype=torch.complex64, device="cuda")
+    cop = dirac.StencilOp(cdims, links)
+    want = np.stack([cop.apply(x[:, :, k]) for k in range(nrhs)], axis=-1)
+    key = f"stream_mr/p1/n{n}/v{vol}/r{nrhs}/b0"
+    gb.mg_tune_set(key, -1)
+    gb.mg_coarse_apply(mg.ctx, 1, y, xd, nrhs=nrhs)  # tunes: times every candidate
+    choices = [c for c, _ in gb.mg_tune_report(key)]
+    assert 4 in choices and len(choices) >= 2, choices
+    for choice in choices:
+        gb.mg_tune_set(key, choice)
+        y.fill_(float("nan"))
+        gb.mg_coarse_apply(mg.ctx, 1, y, xd, nrhs=nrhs)
+        torch.cuda.synchronize()
+        assert gb.mg_tune_get(key) == choice
+        assert rel_l2(to_np(y), want) < 1e-5, choice
+    gb.mg_tune_set(key, -1)
+    mg.close()
+
+
 # ------------------------------------------------------------------ setup
 @pytest.mark.parametrize("dims,block,nv", [((4, 4, 4, 4), (2, 2, 2, 2), 6),
                                            ((4, 2, 4, 6), (2, 1, 2, 3), 4)])
