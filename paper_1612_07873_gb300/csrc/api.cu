@@ -626,7 +626,7 @@ mg_status mg_device_status(mg_ctx* c, void* stream) {
     if (h[1]) {
       GB_CHECK(cudaMemsetAsync(c->status.as<int>() + 1, 0, sizeof(int), S(stream)));
       GB_CHECK(cudaStreamSynchronize(S(stream)));
-      throw Error(MG_ERR_TIMEOUT, "a bounded device wait timed out (tensor-core coarse apply or tiled fine operator)");
+      throw Error(MG_ERR_TIMEOUT, "a bounded device wait timed out (tensor-core coarse apply, tiled fine operator or Galerkin build)");
     }
   });
 }

@@ -85,6 +85,16 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
+// the same copy with the default L2 policy
+__device__ __forceinline__ void bulk_g2s_plain(void* dst, const void* src, uint32_t bytes,
+                                               uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // tiled 5-D tensor copy global -> this CTA's shared memory (the box of
 // `map` at coordinates c0..c4, innermost first), completing its bytes on
 // the mbarrier; `map` lives in kernel-parameter space (__grid_constant__)

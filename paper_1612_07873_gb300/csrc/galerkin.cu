@@ -15,6 +15,7 @@
 // hop; terms go to separate shared slices and are summed in a fixed order,
 // so the result is deterministic.  Coarse level: T is a dense product with
 // the level's link blocks.
+#include "async_copy.cuh"
 #include "kernels.cuh"
 #include "wilson_ops.cuh"
 
@@ -213,11 +214,17 @@ __global__ void __launch_bounds__(256) k_galerkin(Op op, const cpx<R>* __restric
 // K = CH x nf / 2 values of each chirality in TILE x TILE register tiles.
 // Three block barriers per chunk instead of three per fine site; the
 // contributing sites are enumerated from their index (no serial list).
+// P(x) of the chunk's sites (contiguous rows of the prolongator) arrives by
+// bulk copies issued before the T products, so the copies overlap them;
+// the contraction waits on the copies' mbarrier (bounded: on a timeout the
+// CTA records it in *err and leaves).
 template <typename R, typename Rout, typename Op, int TILE>
 __global__ void __launch_bounds__(256) k_galerkin_chunk(Op op, const cpx<R>* __restrict__ Vp,
                                                         AggGeom m, int nf, int nv, int CH,
-                                                        cpx<Rout>* __restrict__ out) {
+                                                        cpx<Rout>* __restrict__ out,
+                                                        int* __restrict__ err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint64_t vbar;
   const int n2 = 2 * nv;
   const int halff = nf / 2;
   cpx<R>* sV = reinterpret_cast<cpx<R>*>(smem_raw);  // [CH][nf][nv]
@@ -256,6 +263,12 @@ __global__ void __launch_bounds__(256) k_galerkin_chunk(Op op, const cpx<R>* __r
   cpx<R> acc[TILE * TILE];
 #pragma unroll
   for (int k = 0; k < TILE * TILE; ++k) acc[k] = cpx<R>(R(0), R(0));
+  if (tid == 0) {
+    mbar_init(&vbar, 1);
+    fence_mbar_init();
+  }
+  const uint32_t pbytes = uint32_t(nf) * uint32_t(nv) * uint32_t(sizeof(cpx<R>));
+  uint32_t vphase = 0;
 
   for (int k0 = 0; k0 < cnt; k0 += CH) {
     const int nk = min(CH, cnt - k0);
@@ -274,9 +287,13 @@ __global__ void __launch_bounds__(256) k_galerkin_chunk(Op op, const cpx<R>* __r
       }
     }
     __syncthreads();
-    for (int k = tid; k < nk * nf * nv; k += 256) {
-      const int sk = k / (nf * nv), r = k - sk * nf * nv;
-      sV[k] = Vp[size_t(s_x[sk]) * nf * nv + r];
+    if (tid == 0) {
+      // the previous chunk's reads of sV are ordered before the copies that
+      // overwrite it
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&vbar, uint32_t(nk) * pbytes);
+      for (int sk = 0; sk < nk; ++sk)
+        bulk_g2s_plain(sV + size_t(sk) * nf * nv, Vp + size_t(s_x[sk]) * nf * nv, pbytes, &vbar);
     }
     if constexpr (Op::wilson) {
       // items (chunk site, column): T[site][.][col] = sum_e H_e P_col(x + e)
@@ -330,6 +347,16 @@ __global__ void __launch_bounds__(256) k_galerkin_chunk(Op op, const cpx<R>* __r
       }
     }
     __syncthreads();
+    if (!mbar_wait(&vbar, vphase)) {
+      // the copies did not land within the budget: record it, give them a
+      // second bounded wait and leave
+      if (tid == 0) {
+        atomicOr(err, 1);
+        mbar_wait(&vbar, vphase);
+      }
+      return;
+    }
+    vphase ^= 1u;
     // acc[(s,i),(s',j)] += sum_{site, a in chi s} conj(P(x)[a][i]) T(x)[a][(s',j)]
     for (int sk = 0; sk < nk; ++sk) {
       const cpx<R>* Vk = sV + size_t(sk) * nf * nv;
@@ -360,7 +387,7 @@ __global__ void __launch_bounds__(256) k_galerkin_chunk(Op op, const cpx<R>* __r
 
 template <typename R, typename Rout, typename Op>
 void launch_galerkin(const Op& op, const cpx<R>* Vp, const AggGeom& m, int nf, int nv,
-                     cpx<Rout>* out, cudaStream_t st) {
+                     cpx<Rout>* out, int* err, cudaStream_t st) {
   const int n2 = 2 * nv;
   size_t smem = size_t(nf) * nv * sizeof(cpx<R>) + size_t(nf) * n2 * sizeof(cpx<R>);
   if (Op::wilson) smem += size_t(9) * 12 * n2 * sizeof(cpx<R>);
@@ -372,7 +399,8 @@ void launch_galerkin(const Op& op, const cpx<R>* Vp, const AggGeom& m, int nf, i
   };
   // chunked kernel: as many fine sites per chunk (up to 16) as two CTAs per
   // SM leave room for
-  if (n2 == 32 || n2 == 48 || n2 == 64) {
+  // (the chunked kernel bulk-copies rows of Vp: 16-byte aligned)
+  if ((n2 == 32 || n2 == 48 || n2 == 64) && reinterpret_cast<uintptr_t>(Vp) % 16 == 0) {
     const size_t per_site = (size_t(nf) * nv + size_t(nf) * n2) * sizeof(cpx<R>) + 19 * sizeof(int);
     const size_t budget = 110 * 1024;
     int CH = int(budget / per_site);
@@ -381,7 +409,7 @@ void launch_galerkin(const Op& op, const cpx<R>* Vp, const AggGeom& m, int nf, i
     const size_t csm = size_t(CH) * per_site;
     auto goc = [&](auto kern) {
       GB_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(csm)));
-      kern<<<grid, 256, csm, st>>>(op, Vp, m, nf, nv, CH, out);
+      kern<<<grid, 256, csm, st>>>(op, Vp, m, nf, nv, CH, out, err);
     };
     if (n2 == 32)
       goc(k_galerkin_chunk<R, Rout, Op, 2>);
@@ -419,27 +447,28 @@ void galerkin_build(mg_ctx* c, int level, cudaStream_t st) {
   C.links.alloc(total * prec_bytes_complex(C.vprec));
   const double flops = 8.0 * F.g.vol * (9.0 * (2 * nv) * (2 * nv) * (nf / 2));
   ProfScope ps(c->prof, st, "galerkin", level, double(F.g.vol) * nf * nv * 16.0, flops);
+  int* err = c->status.as<int>() + 1;
   if (F.vprec == MG_F64) {
     GB_REQUIRE(C.vprec == MG_F64, MG_ERR_ARG, "FP64 level above an FP32 level is not supported");
     if (level == 0) {
       WilsonOp<double> op{F.gauge64.as<cpx<double>>(), F.clover64.as<double>(), F.diag};
       launch_galerkin<double, double>(op, F.Vp.as<cpx<double>>(), m, nf, nv,
-                                      C.links.as<cpx<double>>(), st);
+                                      C.links.as<cpx<double>>(), err, st);
     } else {
       CoarseOp<double> op{F.links.as<cpx<double>>()};
       launch_galerkin<double, double>(op, F.Vp.as<cpx<double>>(), m, nf, nv,
-                                      C.links.as<cpx<double>>(), st);
+                                      C.links.as<cpx<double>>(), err, st);
     }
   } else {
     GB_REQUIRE(C.vprec == MG_F32, MG_ERR_ARG, "FP64 level above an FP32 level is not supported");
     if (level == 0) {
       WilsonOp<float> op{F.gauge32.as<cpx<float>>(), F.clover32.as<float>(), float(F.diag)};
       launch_galerkin<float, float>(op, F.Vp.as<cpx<float>>(), m, nf, nv, C.links.as<cpx<float>>(),
-                                    st);
+                                    err, st);
     } else {
       CoarseOp<float> op{F.links.as<cpx<float>>()};
       launch_galerkin<float, float>(op, F.Vp.as<cpx<float>>(), m, nf, nv, C.links.as<cpx<float>>(),
-                                    st);
+                                    err, st);
     }
   }
   c->launches++;
