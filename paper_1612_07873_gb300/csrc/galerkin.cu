@@ -204,6 +204,91 @@ __global__ void __launch_bounds__(256) k_galerkin(Op op, const cpx<R>* __restric
   }
 }
 
+template <int E>
+struct TermIdx {
+  static constexpr int value = E;
+};
+
+// Column j of chirality SP of T(x) = sum_e H_e(x) P(x + e) at the fine
+// Wilson-clover level, for output block d: the single hop d for Y_d; for X
+// the clover block of chirality SP, then the eight hops (each applied when
+// it stays inside the aggregate), with the next hop's P entries and link
+// loaded before the current hop is applied.  P(x + e) of the column lives
+// on chirality SP only, so the other six spinor entries are zero.
+template <int SP, typename R>
+__device__ __forceinline__ void t_column(const WilsonOp<R>& op, const cpx<R>* __restrict__ Vp,
+                                         int vol, int nv, int x, const int* nbk, const int* ak,
+                                         int d, int j, cpx<R> o[12]) {
+  auto load_v = [&](int y, cpx<R> v[6]) {
+    const cpx<R>* src = Vp + (size_t(y) * 12 + 6 * SP) * nv + j;
+#pragma unroll
+    for (int a = 0; a < 6; ++a) v[a] = src[a * nv];
+  };
+  auto load_u = [&](int mu, int ls, cpx<R> u[9]) {
+    const cpx<R>* U = op.U + (size_t(mu) * vol + ls) * 9;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) u[k] = U[k];
+  };
+  auto spinor = [&](const cpx<R> v[6], cpx<R> psi[12]) {
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+      psi[6 * SP + a] = v[a];
+      psi[6 * (1 - SP) + a] = cpx<R>(R(0), R(0));
+    }
+  };
+#pragma unroll
+  for (int a = 0; a < 12; ++a) o[a] = cpx<R>(R(0), R(0));
+  if (d != 0) {
+    const int mu = (d - 1) >> 1;
+    const bool fwd = ((d - 1) & 1) == 0;
+    cpx<R> v[6], u[9], psi[12];
+    load_v(nbk[d], v);
+    load_u(mu, fwd ? x : nbk[d], u);
+    spinor(v, psi);
+    hop_accum_rt(mu, fwd, u, psi, o);
+    return;
+  }
+  {
+    // the column lives on chirality SP: only that clover block acts
+    cpx<R> v[6];
+    load_v(x, v);
+    clover_block_accum(op.A + size_t(x) * 72 + 36 * SP, op.diag, v, o + 6 * SP);
+  }
+  cpx<R> v[6], u[9];
+  load_v(nbk[1], v);
+  load_u(0, x, u);
+  auto step = [&](auto ic) {
+    constexpr int E = decltype(ic)::value;
+    constexpr int MU = (E - 1) >> 1;
+    constexpr bool FWD = ((E - 1) & 1) == 0;
+    cpx<R> vn[6], un[9];
+    if constexpr (E < 8) {
+      // hop E + 1: direction E / 2, forward when E is even
+      load_v(nbk[E + 1], vn);
+      load_u(E >> 1, (E & 1) == 0 ? x : nbk[E + 1], un);
+    }
+    if (ak[E]) {
+      cpx<R> psi[12];
+      spinor(v, psi);
+      hop_accum<MU, FWD>(u, psi, o);
+    }
+    if constexpr (E < 8) {
+#pragma unroll
+      for (int a = 0; a < 6; ++a) v[a] = vn[a];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) u[k] = un[k];
+    }
+  };
+  step(TermIdx<1>{});
+  step(TermIdx<2>{});
+  step(TermIdx<3>{});
+  step(TermIdx<4>{});
+  step(TermIdx<5>{});
+  step(TermIdx<6>{});
+  step(TermIdx<7>{});
+  step(TermIdx<8>{});
+}
+
 // Chunked form of the same product for 2Nv = 16 TILE: the fine sites that
 // contribute to (xc, d) -- every site of the aggregate for X, the sites on
 // the face d leaves through for Y_d -- are processed CH at a time.  Per
@@ -219,7 +304,8 @@ __global__ void __launch_bounds__(256) k_galerkin(Op op, const cpx<R>* __restric
 // the contraction waits on the copies' mbarrier (bounded: on a timeout the
 // CTA records it in *err and leaves).
 template <typename R, typename Rout, typename Op, int TILE>
-__global__ void __launch_bounds__(256) k_galerkin_chunk(Op op, const cpx<R>* __restrict__ Vp,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
+    k_galerkin_chunk(Op op, const cpx<R>* __restrict__ Vp,
                                                         AggGeom m, int nf, int nv, int CH,
                                                         cpx<Rout>* __restrict__ out,
                                                         int* __restrict__ err) {
@@ -296,35 +382,18 @@ __global__ void __launch_bounds__(256) k_galerkin_chunk(Op op, const cpx<R>* __r
         bulk_g2s_plain(sV + size_t(sk) * nf * nv, Vp + size_t(s_x[sk]) * nf * nv, pbytes, &vbar);
     }
     if constexpr (Op::wilson) {
-      // items (chunk site, column): T[site][.][col] = sum_e H_e P_col(x + e)
+      // items (chirality sp, chunk site, column j within sp), sp slowest so
+      // a warp's items share sp: T[site][.][sp nv + j] = sum_e H_e P_col(x + e)
       for (int it = tid; it < nk * n2; it += 256) {
-        const int sk = it / n2, col = it - sk * n2;
-        const int sp = col / nv, j = col - sp * nv;
-        const int x = s_x[sk];
+        const int sp = it / (nk * nv);
+        const int rem = it - sp * nk * nv;
+        const int sk = rem / nv, j = rem - sk * nv;
+        const int col = sp * nv + j;
         cpx<R> o[12];
-#pragma unroll
-        for (int a = 0; a < 12; ++a) o[a] = cpx<R>(R(0), R(0));
-        for (int e = 0; e < 9; ++e) {
-          if (!s_act[sk * 9 + e]) continue;
-          const int xe = s_nb[sk * 9 + e];
-          const cpx<R>* src = Vp + size_t(xe) * 12 * nv + j;
-          cpx<R> psi[12];
-#pragma unroll
-          for (int a = 0; a < 12; ++a)
-            psi[a] = ((a / 6) == sp) ? src[a * nv] : cpx<R>(R(0), R(0));
-          if (e == 0) {
-            // the column lives on chirality sp: only that clover block acts
-            if (sp == 0)
-              clover_block_accum(op.A + size_t(x) * 72, op.diag, psi, o);
-            else
-              clover_block_accum(op.A + size_t(x) * 72 + 36, op.diag, psi + 6, o + 6);
-          } else {
-            const int mu = (e - 1) >> 1;
-            const bool fwd = ((e - 1) & 1) == 0;
-            const int ls_ = fwd ? x : xe;
-            hop_accum_rt(mu, fwd, op.U + (size_t(mu) * m.fine.vol + ls_) * 9, psi, o);
-          }
-        }
+        if (sp == 0)
+          t_column<0>(op, Vp, m.fine.vol, nv, s_x[sk], s_nb + sk * 9, s_act + sk * 9, d, j, o);
+        else
+          t_column<1>(op, Vp, m.fine.vol, nv, s_x[sk], s_nb + sk * 9, s_act + sk * 9, d, j, o);
 #pragma unroll
         for (int a = 0; a < 12; ++a) sT[(size_t(sk) * 12 + a) * n2 + col] = o[a];
       }
