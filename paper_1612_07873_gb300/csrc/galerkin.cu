@@ -514,7 +514,16 @@ void galerkin_build(mg_ctx* c, int level, cudaStream_t st) {
   const int nf = F.nd, nv = F.nvec;
   const size_t total = size_t(C.g.vol) * 9 * C.nd * C.nd;
   C.links.alloc(total * prec_bytes_complex(C.vprec));
-  const double flops = 8.0 * F.g.vol * (9.0 * (2 * nv) * (2 * nv) * (nf / 2));
+  // arithmetic per fine site: the P^dag T contractions (8 n2 nv nf flop
+  // each) of X and of the exit-face Y blocks (1 + sum_mu 2 / b_mu per site),
+  // and the T = H P columns: at the Wilson-clover level the clover block of
+  // the column's chirality (270 flop) and eight hops (204 flop each), at a
+  // coarse level nine dense nf x nf/2 blocks (36 nf^2 flop)
+  double blocks = 1.0;
+  for (int mu = 0; mu < 4; ++mu) blocks += 2.0 / F.block[mu];
+  const double n2d = 2.0 * nv;
+  const double tcol = level == 0 ? 270.0 + 8.0 * 204.0 : 36.0 * nf * nf;
+  const double flops = double(F.g.vol) * (blocks * 8.0 * n2d * nv * nf + n2d * tcol);
   ProfScope ps(c->prof, st, "galerkin", level, double(F.g.vol) * nf * nv * 16.0, flops);
   int* err = c->status.as<int>() + 1;
   if (F.vprec == MG_F64) {

@@ -558,9 +558,11 @@ __global__ void __launch_bounds__(128) k_wilson_tile(cpx<float>* __restrict__ ou
 // instead of once per site, and no thread waits on a dependent gather.  The
 // thread's clover stays in registers across the vectors; for several
 // vectors the links stay in shared memory and only the spinor tile is
-// copied again.  Smem layout (records of 96 B spinors / 48 B links, in the
-// boxes' own order, x fastest): [interior][x-][x+][y-][y+][z-][z+][t-][t+]
-// spinors, then [link mu interior] x 4, [x-][y-][z-][t-] links.
+// copied again, into the other of two spinor buffers while the current
+// vector is computed.  Smem layout (records of 96 B spinors / 48 B links,
+// in the boxes' own order, x fastest): [interior][x-][x+][y-][y+][z-][z+]
+// [t-][t+] spinors, then [link mu interior] x 4, [x-][y-][z-][t-] links,
+// then (several vectors) the second spinor buffer.
 // Tensor maps (innermost first): spinors (24 floats, Lx, Ly, Lz, Lt nvec),
 // links (12 floats, Lx, Ly, Lz, 4 Lt) -- direction mu as time slices
 // mu Lt.. of the [mu][site] store.  Index 0: the interior box, 1 + mu: the
@@ -602,9 +604,11 @@ __global__ void __launch_bounds__(BX * BY * BZ * BT, 3)
   using WB = WilsonBlock<BX, BY, BZ, BT>;
   constexpr int NS = WB::NS;
   extern __shared__ __align__(128) unsigned char wsm[];
-  unsigned char* sp = wsm;                          // spinor records
   unsigned char* lk = wsm + size_t(WB::NSP) * 96;   // link records
-  __shared__ uint64_t bar;
+  // spinor buffers: vector v in buffer v & 1 (every offset a multiple of 128 B)
+  unsigned char* const sp0 = wsm;
+  unsigned char* const sp1 = lk + size_t(WB::NLK) * 48;
+  __shared__ uint64_t bar[2];
   const int tid = threadIdx.x;
   const int st = tid;  // the thread's site in the block
   // block origin and this thread's site
@@ -644,7 +648,8 @@ __global__ void __launch_bounds__(BX * BY * BZ * BT, 3)
   const bool tlast = antiperiodic && o[3] + l[3] == g.L[3] - 1;
   const bool tfirst = antiperiodic && o[3] + l[3] == 0;
   if (tid == 0) {
-    mbar_init(&bar, 1);
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
     fence_mbar_init();
   }
   __syncthreads();
@@ -663,44 +668,55 @@ __global__ void __launch_bounds__(BX * BY * BZ * BT, 3)
     for (int i = 0; i < 18; ++i) reinterpret_cast<uint4*>(clv)[i] = __ldg(p + i);
   }
   const int Lt = g.L[3];
-  for (int v = 0; v < nvec; ++v) {
-    if (tid == 0) {
-      // the previous vector's reads of the tile are ordered before the
-      // copies that overwrite it
-      fence_proxy_async_smem();
-      const uint32_t bytes = uint32_t(WB::NSP) * 96u + (v == 0 ? uint32_t(WB::NLK) * 48u : 0u);
-      mbar_arrive_expect_tx(&bar, bytes);
-      const int tv = v * Lt;
-      tma_load_5d(sp, &maps.sp[0], 0, o[0], o[1], o[2], o[3] + tv, &bar);
+  // thread 0: the tensor copies of vector v's spinor tile (and, for v = 0,
+  // of the links) into buffer v & 1, completing on barrier v & 1
+  auto issue = [&](int v) {
+    unsigned char* sp = (v & 1) ? sp1 : sp0;
+    uint64_t* b = (v & 1) ? &bar[1] : &bar[0];
+    // the reads of this buffer two vectors ago are ordered before the
+    // copies that overwrite it
+    fence_proxy_async_smem();
+    const uint32_t bytes = uint32_t(WB::NSP) * 96u + (v == 0 ? uint32_t(WB::NLK) * 48u : 0u);
+    mbar_arrive_expect_tx(b, bytes);
+    const int tv = v * Lt;
+    tma_load_5d(sp, &maps.sp[0], 0, o[0], o[1], o[2], o[3] + tv, b);
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu)
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        int c[4] = {o[0], o[1], o[2], o[3]};
+        c[mu] = side ? wp[mu] : wm[mu];
+        tma_load_5d(sp + size_t(WB::face_sp(mu, side)) * 96, &maps.sp[1 + mu], 0, c[0], c[1],
+                    c[2], c[3] + tv, b);
+      }
+    if (v == 0) {
 #pragma unroll
       for (int mu = 0; mu < 4; ++mu)
+        tma_load_5d(lk + size_t(mu) * NS * 48, &maps.lk[0], 0, o[0], o[1], o[2], o[3] + mu * Lt,
+                    b);
 #pragma unroll
-        for (int side = 0; side < 2; ++side) {
-          int c[4] = {o[0], o[1], o[2], o[3]};
-          c[mu] = side ? wp[mu] : wm[mu];
-          tma_load_5d(sp + size_t(WB::face_sp(mu, side)) * 96, &maps.sp[1 + mu], 0, c[0], c[1],
-                      c[2], c[3] + tv, &bar);
-        }
-      if (v == 0) {
-#pragma unroll
-        for (int mu = 0; mu < 4; ++mu)
-          tma_load_5d(lk + size_t(mu) * NS * 48, &maps.lk[0], 0, o[0], o[1], o[2],
-                      o[3] + mu * Lt, &bar);
-#pragma unroll
-        for (int mu = 0; mu < 4; ++mu) {
-          int c[4] = {o[0], o[1], o[2], o[3]};
-          c[mu] = wm[mu];
-          tma_load_5d(lk + size_t(WB::face_lk(mu)) * 48, &maps.lk[1 + mu], 0, c[0], c[1], c[2],
-                      c[3] + mu * Lt, &bar);
-        }
+      for (int mu = 0; mu < 4; ++mu) {
+        int c[4] = {o[0], o[1], o[2], o[3]};
+        c[mu] = wm[mu];
+        tma_load_5d(lk + size_t(WB::face_lk(mu)) * 48, &maps.lk[1 + mu], 0, c[0], c[1], c[2],
+                    c[3] + mu * Lt, b);
       }
     }
-    if (!mbar_wait(&bar, uint32_t(v & 1))) {
+  };
+  if (tid == 0) issue(0);
+  for (int v = 0; v < nvec; ++v) {
+    // buffer (v + 1) & 1 was last read for vector v - 1, before the block
+    // barrier that ended that vector
+    if (tid == 0 && v + 1 < nvec) issue(v + 1);
+    const unsigned char* sp = (v & 1) ? sp1 : sp0;
+    if (!mbar_wait(&bar[v & 1], uint32_t((v >> 1) & 1))) {
       // the copies did not land within the budget: record it, give the
-      // copies in flight a second bounded wait and leave
+      // copies in flight (this vector's and the next one's) a second
+      // bounded wait and leave
       if (tid == 0) {
         atomicOr(err, 1);
-        mbar_wait(&bar, uint32_t(v & 1));
+        mbar_wait(&bar[v & 1], uint32_t((v >> 1) & 1));
+        if (v + 1 < nvec) mbar_wait(&bar[(v + 1) & 1], uint32_t(((v + 1) >> 1) & 1));
       }
       return;
     }
@@ -769,8 +785,10 @@ void launch_wilson_blk(cpx<float>* out, const cpx<float>* in, const cpx<float>* 
     m.lk[1 + mu] = make_map_5d(U12, ld, ls, fl);
   }
   auto k = k_wilson_blk<BX, BY, BZ, BT>;
-  GB_CHECK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(WB::SMEM)));
-  k<<<g.vol / WB::NS, WB::NS, WB::SMEM, st>>>(out, A, g, diag, vstride, nvec, ap, m, err);
+  // several vectors: a second spinor buffer after the links
+  const size_t smem = WB::SMEM + (nvec > 1 ? size_t(WB::NSP) * 96 : 0);
+  GB_CHECK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  k<<<g.vol / WB::NS, WB::NS, smem, st>>>(out, A, g, diag, vstride, nvec, ap, m, err);
 }
 
 // the tiled form needs block-divisible extents and 16-byte aligned operands
