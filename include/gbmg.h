@@ -431,9 +431,10 @@ mg_status mg_halo_buffers(mg_halo* h, int rank, void** send_dev, void** recv_dev
 long long mg_halo_launch_count(mg_halo* h);
 
 /* Synchronise `stream` and report errors that kernels recorded on the
- * device: MG_ERR_TIMEOUT if a bounded wait inside a kernel (the tensor-core
- * multi-RHS apply's mbarrier waits) gave up since the last call; the record
- * is cleared.                                                              */
+ * device: MG_ERR_TIMEOUT if a bounded wait inside a kernel (the mbarrier
+ * waits of the tensor-core multi-RHS apply, of the tiled fine operator and
+ * of the Galerkin build) gave up since the last call; the record is
+ * cleared.                                                                 */
 mg_status mg_device_status(mg_ctx* ctx, void* stream);
 
 /* out[0] + i out[1] = sum_k conj(a_k) b_k over one vector of `level`
