@@ -204,6 +204,23 @@ __global__ void __launch_bounds__(256) k_galerkin(Op op, const cpx<R>* __restric
   }
 }
 
+// four consecutive complex numbers from a 16-byte aligned address
+__device__ __forceinline__ void load4c(const cpx<float>* p, cpx<float> v[4]) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+  const float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+  v[0] = cpx<float>(a.x, a.y);
+  v[1] = cpx<float>(a.z, a.w);
+  v[2] = cpx<float>(b.x, b.y);
+  v[3] = cpx<float>(b.z, b.w);
+}
+__device__ __forceinline__ void load4c(const cpx<double>* p, cpx<double> v[4]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(p) + k);
+    v[k] = cpx<double>(a.x, a.y);
+  }
+}
+
 template <int E>
 struct TermIdx {
   static constexpr int value = E;
@@ -396,6 +413,50 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
           t_column<1>(op, Vp, m.fine.vol, nv, s_x[sk], s_nb + sk * 9, s_act + sk * 9, d, j, o);
 #pragma unroll
         for (int a = 0; a < 12; ++a) sT[(size_t(sk) * 12 + a) * n2 + col] = o[a];
+      }
+    } else if (nf % 4 == 0 && nv % 4 == 0) {
+      // T[site][a][col] = sum_e sum_{b in chi(col)} H_e(x)[a][b] P(x+e)[b][j]
+      // in register tiles of 4 rows a x 4 columns j of one chirality: per
+      // (term, b) 16-byte loads of rows a0..a0+3 of H_e's column b (the
+      // [col][row] store keeps them contiguous) and of columns j0..j0+3 of
+      // P(x+e)'s row b, then 16 complex MACs.  Items (site, chirality, j
+      // tile, a tile), a tile fastest: a warp's H loads are one contiguous
+      // run, its P loads shared.
+      const int atn = nf / 4, jtn = nv / 4;
+      const int per_site = 2 * atn * jtn;
+      for (int it = tid; it < nk * per_site; it += 256) {
+        const int sk = it / per_site;
+        int rem = it - sk * per_site;
+        const int at = rem % atn;
+        rem /= atn;
+        const int jt = rem % jtn, sp = rem / jtn;
+        const int a0 = 4 * at, j0 = 4 * jt;
+        const int x = s_x[sk];
+        cpx<R> t[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int w = 0; w < 4; ++w) t[u][w] = cpx<R>(R(0), R(0));
+        for (int e = 0; e < 9; ++e) {
+          if (!s_act[sk * 9 + e]) continue;
+          const cpx<R>* H = op.links + (size_t(x) * 9 + e) * nf * nf + a0;
+          const cpx<R>* src = Vp + size_t(s_nb[sk * 9 + e]) * nf * nv + j0;
+#pragma unroll 2
+          for (int b = sp * halff; b < (sp + 1) * halff; ++b) {
+            cpx<R> h[4], q[4];
+            load4c(H + size_t(b) * nf, h);
+            load4c(src + size_t(b) * nv, q);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+              for (int w = 0; w < 4; ++w) cmac(t[u][w], h[u], q[w]);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int w = 0; w < 4; ++w)
+            sT[(size_t(sk) * nf + a0 + u) * n2 + sp * nv + j0 + w] = t[u][w];
       }
     } else {
       // T[site][a][col] = sum_e sum_{b in chi(col)} H_e(x)[a][b] P(x+e)[b][j]

@@ -299,15 +299,22 @@ def test_galerkin_fine_to_coarse(gpu_lib, dims, block, nv, prec):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-def test_galerkin_coarse_to_coarser(gpu_lib, prec):
+@pytest.mark.parametrize("nv1,nv2,b2", [
+    (6, 8, (2, 1, 1, 2)),    # n2 = 16: one fine site per pass
+    (6, 16, (2, 1, 1, 2)),   # n2 = 32: chunked, T products in 4 x 4 register tiles
+    (6, 24, (2, 2, 2, 2)),   # n2 = 48
+    (6, 32, (2, 2, 2, 2)),   # n2 = 64 (the shape of the 3-level workload's level 2)
+    (5, 16, (2, 1, 1, 2)),   # chunked, 10 dof per coarse site: one T entry per thread
+])
+def test_galerkin_coarse_to_coarser(gpu_lib, prec, nv1, nv2, b2):
     """Level 1 -> 2: the Galerkin product of a coarse operator (dense links).
     The GPU's level-2 links are P2^dag (A1 + dA1) P2 + R2, with dA1 the
     level-1 error (at most TOL |A1|, the bound of the fine-to-coarse test)
     and R2 the level-2 build's own rounding; P2 has orthonormal columns, so
     |dA2| / |A2| <= TOL (1 + |A1| / |A2|) in the Frobenius norm of the link
-    blocks (the ratio is 1.74 here)."""
+    blocks (the ratio is 1.74 for the first case)."""
     gb = gpu_lib
-    dims, b1, b2, nv1, nv2 = (8, 4, 4, 8), (2, 2, 2, 2), (2, 1, 1, 2), 6, 8
+    dims, b1 = (8, 4, 4, 8), (2, 2, 2, 2)
     mg, U = make_ctx(gb, dims, [b1, b2], [nv1, nv2], prec_fine=prec, prec_coarse=prec)
     v1 = syn.gaussian_field((nv1, lat.volume(dims), 12), 41)
     gb.mg_set_nullvecs(mg.ctx, 0, to_dev(v1))
