@@ -361,8 +361,17 @@ __global__ void __launch_bounds__(NT) k_block_qr(ffc* __restrict__ W, int rows, 
       v[r] = row < rows ? B[size_t(i) * rows + row] : ffc{0.f, 0.f, 0.f, 0.f};
     }
     double n0 = 0.0;  // squared norm before the first projection
-    if (i > 0) n0 = blk_sum_ff(norm2(v), sh);
+    double nn = -1.0;  // squared norm after the last projection, when known
     for (int pass = 0; pass < 2 && i > 0; ++pass) {
+      if (pass == 0) {
+        // the column's squared norm rides with the coefficients (slot i)
+        ff s = norm2(v);
+        for (int o = 16; o > 0; o >>= 1) s = ff_add(s, ff_shfl_xor(s, o));
+        if (lane == 0) {
+          part[warp][i][0] = s;
+          part[warp][i][1] = ff{0.f, 0.f};
+        }
+      }
       for (int j = 0; j < i; ++j) {
         const ffc* q = B + size_t(j) * rows;
         // d = sum conj(q) v
@@ -388,7 +397,7 @@ __global__ void __launch_bounds__(NT) k_block_qr(ffc* __restrict__ W, int rows, 
         }
       }
       __syncthreads();
-      if (threadIdx.x < i) {
+      if (threadIdx.x < i + (pass == 0 ? 1 : 0)) {
         ff cr = {0.f, 0.f}, ci = {0.f, 0.f};
         for (int w = 0; w < nw; ++w) {
           cr = ff_add(cr, part[w][threadIdx.x][0]);
@@ -397,6 +406,7 @@ __global__ void __launch_bounds__(NT) k_block_qr(ffc* __restrict__ W, int rows, 
         coef[threadIdx.x] = ffc{cr.hi, cr.lo, ci.hi, ci.lo};
       }
       __syncthreads();
+      if (pass == 0) n0 = ff_to(ff{coef[i].rh, coef[i].rl});
       for (int j = 0; j < i; ++j) {
         const ffc* q = B + size_t(j) * rows;
         const ffc c = coef[j];
@@ -421,10 +431,13 @@ __global__ void __launch_bounds__(NT) k_block_qr(ffc* __restrict__ W, int rows, 
         // amplifies the float-float representation error (2^-48 of the input)
         // past FP64 accuracy: the block is redone in FP64 (status bit 2)
         if (n1 < 1e-4 * n0 && threadIdx.x == 0) atomicOr(status, 2);
-        if (n1 >= 0.5 * n0) break;
+        if (n1 >= 0.5 * n0) {
+          nn = n1;  // one pass: the column's norm is already reduced
+          break;
+        }
       }
     }
-    const double nrm = sqrt(blk_sum_ff(norm2(v), sh));
+    const double nrm = sqrt(nn >= 0.0 ? nn : blk_sum_ff(norm2(v), sh));
     float sh_inv = 0.f, sl_inv = 0.f;
     if (nrm <= 1e-12 * scale) {
       if (threadIdx.x == 0) atomicOr(status, 1);
