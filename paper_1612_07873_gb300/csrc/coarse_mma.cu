@@ -650,6 +650,11 @@ __global__ void __launch_bounds__(kWsThreads, 3)
     // ---- bulk copies: the stage's links and the neighbour's spinor rows
     if (lane == 0) {
       const uint64_t pol = policy_evict_first(), pol_x = policy_evict_last();
+      // a pre-converted launch may start while the pre-pass that writes its
+      // operand is still running (programmatic dependent launch): wait for
+      // that grid's completion and memory before the first copy (a no-op
+      // when the launch has no such predecessor)
+      if (PC) asm volatile("griddepcontrol.wait;" ::: "memory");
       uint32_t q = 0;
       bool go = true;
       for (int gs = blockIdx.x; gs < batch.total && go && !abort_sh; gs += gridDim.x) {
@@ -750,6 +755,9 @@ __global__ void __launch_bounds__(kWsThreads, 3)
 // stores; two items in flight per thread; sites in descending order.
 template <bool BF16, int N, bool IL>
 __global__ void __launch_bounds__(256) k_spinor_tile_mma(const MmaBatch batch, int nrhs) {
+  // the apply launched after this pass may begin its set-up now; it reads
+  // the operand only after this grid has completed
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   constexpr int KT = N / 8;  // 4-column groups of a half slot
   const size_t items = size_t(batch.total) * 2 * KT * nrhs;
   const size_t xh = size_t(4) * nrhs * N;
@@ -944,7 +952,24 @@ void launch_mma_batch(int* err, const MmaBatch& batch, int nrhs, cudaStream_t st
       }
       auto go = [&](auto kern) {
         GB_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
-        kern<<<grid, kWsThreads, sm, st>>>(pbatch, nrhs, SL, SA, err);
+        if (PC) {
+          // programmatic dependent launch on the pre-pass: the apply's CTAs
+          // set up (TMEM, barriers) while the pre-pass drains; the copy
+          // issuer waits for the pre-pass before reading its operand
+          cudaLaunchConfig_t cfg = {};
+          cfg.gridDim = dim3(grid);
+          cfg.blockDim = dim3(kWsThreads);
+          cfg.dynamicSmemBytes = sm;
+          cfg.stream = st;
+          cudaLaunchAttribute at[1];
+          at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+          at[0].val.programmaticStreamSerializationAllowed = 1;
+          cfg.attrs = at;
+          cfg.numAttrs = 1;
+          GB_CHECK(cudaLaunchKernelEx(&cfg, kern, pbatch, nrhs, SL, SA, err));
+        } else {
+          kern<<<grid, kWsThreads, sm, st>>>(pbatch, nrhs, SL, SA, err);
+        }
       };
       const int form = (KH == 2 ? 4 : 0) + (IL ? 2 : 0) + (PC ? 1 : 0);
       switch (form) {
